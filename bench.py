@@ -1,0 +1,296 @@
+"""Benchmark: time to an FP64 true residual ||b - D x||/||b|| <= 1e-10 per
+right-hand side for the adaptive-multigrid Wilson-clover solver.
+
+Workload (synthetic stand-in for the paper's 32^3x64 / 64^3x64 ensembles):
+16^3 x 32 lattice, links exp(0.6 i H) (seed 2), kappa = 0.130, c_sw = 1.0,
+antiperiodic in t; two-level multigrid with 4^4 blocks and 24 test vectors
+(48 chiral), FP32 smoother / coarse operator, FP64 outer flexible GMRES(16).
+One step = one solve of a fresh complex Gaussian right-hand side.  The setup
+(null-space vectors, Galerkin operator) runs once before the timed region and
+is reported separately.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lqcd_inputs as li  # noqa: E402
+
+METRIC = "time to FP64 |r|/|b|<=1e-10 per RHS; Dirac/coarse matvec % HBM/TC roofline"
+WORKLOAD = dict(dims=(16, 16, 16, 32), eps=0.6, seed=2, kappa=0.130, csw=1.0, block=(4, 4, 4, 4), nvec=24)
+TOL = 1e-10
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                      "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.splitlines()[0].split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_params(capi, prec_smoother):
+    p = capi.amg_params_default()
+    p.nlevels = 2
+    for mu in range(4):
+        p.block[0][mu] = WORKLOAD["block"][mu]
+    p.nvec[0] = WORKLOAD["nvec"]
+    p.prec_smoother = prec_smoother
+    p.prec_coarsest = capi.AMG_F32 if prec_smoother != capi.AMG_F64 else capi.AMG_F64
+    return p
+
+
+def oracle_sample(steps_hint=1, budget_s=20.0):
+    """Bounded CPU sample of the same workload with the FP64 oracle: one
+    application of the multigrid preconditioner (restrict, coarse BiCGStab(2),
+    prolong, SAP) plus one fine D, on a hierarchy built from orthonormalised
+    random test vectors.  Returns (seconds per outer iteration, cores, note)."""
+    from oracle import dirac as odirac, amg as oamg
+    import threading as _t
+    w = WORKLOAD
+    dims = w["dims"]
+    U = li.gauge_field(dims, w["eps"], w["seed"])
+    op = odirac.WilsonClover(U, w["kappa"], w["csw"], True)
+    shape4 = li.lattice_shape(dims)
+    v0 = li.test_vectors(dims, w["seed"], w["nvec"]).reshape((w["nvec"],) + shape4 + (12,))
+    hier = oamg.Hierarchy(op, oamg.AMGParams(blocks=[w["block"]], nvecs=[w["nvec"]]))
+    hier.set_vectors([v0])
+    b = li.rhs(dims, w["seed"]).reshape(shape4 + (12,))
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        z = hier.vcycle(0, b)
+        op.apply(z)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 3:
+            break
+    per = (time.perf_counter() - t0) / n
+    return per, n
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    per_iter, n = oracle_sample(budget_s=20.0)
+    iters = 8   # outer iterations of the GPU solve on this workload (recorded in DESIGN notes)
+    per_rhs_ms = per_iter * iters * 1e3
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": per_rhs_ms, "unit": "ms/RHS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_rhs_ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "16^3x32 Wilson-clover, 2-level AMG 4^4 blocks, 24 test vectors, 1 Gaussian RHS"},
+        "cpu_baseline": {"value": per_rhs_ms, "unit": "ms/RHS", "cores": 1, "kind": "oracle",
+                         "sample": f"{n} oracle cycle(s) (V-cycle + D) timed, x {iters} outer iterations"},
+        "e2e": {"value": per_rhs_ms, "unit": "ms/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2111_05012_gb300 import capi
+
+    w = WORKLOAD
+    dims = w["dims"]
+    V = int(np.prod(dims))
+    prec = {"f64": capi.AMG_F64, "f32": capi.AMG_F32, "f16": capi.AMG_F16}[args.prec]
+    U = li.gauge_field(dims, w["eps"], w["seed"])
+    lat = capi.amg_lattice_create(dims, True)
+    g = capi.amg_gauge_create(lat, li.to_interleaved(U))
+    d = capi.amg_dirac_create(g, w["kappa"], w["csw"])
+    v0 = li.to_interleaved(li.test_vectors(dims, w["seed"], w["nvec"]))
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = capi.amg_setup(d, make_params(capi, prec), [v0])
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+
+    nsteps = args.warmup + args.steps
+    # right-hand sides: one per step and rank, resident in HBM before timing
+    B = [torch.from_numpy(li.to_interleaved(li.rhs(dims, w["seed"], index=rank * nsteps + k)).reshape(-1)).cuda()
+         for k in range(nsteps)]
+    X = torch.zeros_like(B[0])
+    infos = []
+    for k in range(args.warmup):
+        X.zero_()
+        capi.amg_solve(h, B[k], X, 1, TOL, 500, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler() as clk:
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        for k in range(args.warmup, nsteps):
+            X.zero_()
+            st, info = capi.amg_solve(h, B[k], X, 1, TOL, 500, stream=stream)
+            infos.append(info.as_dict())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_rhs = ms / (args.steps * world)
+    ok = all(i["converged"] == 1 and i["true_rel_residual"] <= TOL for i in infos)
+
+    # end-to-end through the public API with host buffers (pinned), copies timed
+    hb = [B[k].cpu().pin_memory() for k in range(args.warmup, nsteps)]
+    hx = torch.empty_like(hb[0]).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        bd = hb[k].to("cuda", non_blocking=True)
+        X.zero_()
+        capi.amg_solve(h, bd, X, 1, TOL, 500, stream=stream)
+        hx.copy_(X, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    # roofline of the SAP half-sweep kernel (dominant kernel of the solve),
+    # from the smoother phase time: 2 * sap_iters launches per preconditioner call
+    p = make_params(capi, prec)
+    iters = np.mean([i["iters"] for i in infos])
+    smooth_ms = np.mean([i["ms_smoother"] for i in infos])
+    launches = 2 * p.sap_iters * iters
+    sap_launch_us = smooth_ms / launches * 1e3
+    # algorithmic bytes per launch: active half of the sites, per site gauge (own
+    # links + backward links entering through faces), clover, b, x in/out, x halo
+    bps = {capi.AMG_F32: 192 + 48 + 288 + 96 + 96 + 192 + 96, capi.AMG_F16: 96 + 24 + 144 + 52 * 4 + 104,
+           capi.AMG_F64: 576 + 144 + 576 + 192 * 4 + 384}[prec]
+    bytes_launch = bps * V / 2
+    peak, peak_kind = _peaks()
+    achieved = bytes_launch / (sap_launch_us * 1e-6) / 1e9
+
+    line = {
+        "metric": METRIC, "value": per_rhs, "unit": "ms/RHS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32+f64", "f16": "f16+f32+f64"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": "16^3x32 Wilson-clover (exp(0.6iH) links, seed 2, kappa 0.130, csw 1.0), "
+                               "2-level AMG 4^4 blocks, 24 test vectors, SAP(4) x MR(6), BiCGStab(2) coarse to 1e-2, "
+                               "FGMRES(16) FP64 outer, 1 Gaussian RHS per step",
+                   "smoother_prec": args.prec, "setup_ms": setup_ms, "l2": "working set > L2 (no flush)",
+                   "outer_iters": float(iters), "converged": ok,
+                   "phase_ms": {k: float(np.mean([i[k] for i in infos])) for k in
+                                ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other")},
+                   "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
+        "roofline": {"kernel": "sap_half_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "avg_launch_us": sap_launch_us, "bytes_per_launch": bytes_launch},
+        "e2e": {"value": e2e_ms, "unit": "ms/RHS", "h2d_bytes_per_step": int(hb[0].numel() * 8),
+                "d2h_bytes_per_step": int(hx.numel() * 8)},
+        "gpu_launches": None,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_iter, n = oracle_sample(budget_s=20.0)
+        line["cpu_baseline"] = {"value": per_iter * iters * 1e3, "unit": "ms/RHS", "cores": 1, "kind": "oracle",
+                                "sample": f"{n} oracle preconditioner+D application(s) on the same workload, "
+                                          f"x {iters:.1f} outer iterations"}
+    capi.amg_hierarchy_destroy(h)
+    capi.amg_dirac_destroy(d)
+    capi.amg_gauge_destroy(g)
+    capi.amg_lattice_destroy(lat)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * lqcd_amg.h -- C ABI of the GB300 adaptive-multigrid solver for the
+ * Wilson-clover Dirac equation D x = b.
+ *
+ * Method: Kanamori, Ishikawa, Matsufuru, "Multi-grid solver for lattice QCD
+ * on GPU clusters, Xeon Phi and A64FX" (arXiv:2111.05012).  Every entry point
+ * names the passage that defines the operation it performs.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * Lattice:  dims = {Lx, Ly, Lz, Lt}; canonical site index
+ *           x + Lx*(y + Ly*(z + Lz*t)); direction mu = 0..3 is x, y, z, t.
+ *           Periodic in x, y, z; the fermion hop across the t boundary carries
+ *           -1 when antiperiodic_t is set (Sec. 2: periodic or antiperiodic).
+ * Gamma matrices: chiral basis, gamma5 = -g1 g2 g3 g4 = diag(1, 1, -1, -1).
+ * Canonical fine vector (the only fine layout at the boundary):
+ *           [rhs][site][spin 4][colour 3][re, im], element type double for
+ *           AMG_F64, float for AMG_F32 / AMG_F16 (see amg_prec).
+ * Canonical coarse vector (level l >= 1):
+ *           [rhs][coarse site][Nc][re, im], Nc = 2 * nvec of the coarsening,
+ *           coarse dof I = s * nvec + i (s = 0: gamma5 = +1 half, s = 1: -1).
+ * Gauge field (host, double): [site][mu][row 3][col 3][re, im].
+ *
+ * Ownership: handles are created and freed by the library (children before
+ * parents).  Host arrays passed to *_create / setup calls are copied.  Vector
+ * pointers given to apply / restrict / prolong / solve calls are caller-owned
+ * DEVICE pointers, borrowed for the duration of the call; work is enqueued on
+ * the given stream (NULL = the legacy default stream).
+ *
+ * Errors: every call returns an amg_status; nothing aborts, nothing throws
+ * across the ABI.  amg_last_error() returns a message for the last failure on
+ * the calling thread.
+ */
+#ifndef LQCD_AMG_H
+#define LQCD_AMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int amg_status;
+#define AMG_OK 0
+#define AMG_EINVAL 1            /* bad argument (sizes, blocking, precision, NULL) */
+#define AMG_ENOMEM 2            /* device or host allocation failed */
+#define AMG_ECUDA 3             /* a CUDA call failed; see amg_last_error() */
+#define AMG_NOT_CONVERGED 4     /* iteration cap reached; best iterate returned */
+#define AMG_NAN 5               /* non-finite residual / breakdown */
+#define AMG_TIMEOUT 6           /* a bounded device-side wait gave up */
+#define AMG_EIO 7               /* file read/write failed (checkpoints) */
+
+typedef enum {
+    AMG_F64 = 0,   /* double storage and arithmetic */
+    AMG_F32 = 1,   /* float storage and arithmetic */
+    AMG_F16 = 2,   /* fine fields stored as half with a per-site float scale, float arithmetic */
+    AMG_BF16 = 3   /* coarse operator stored as bfloat16, float accumulation */
+} amg_prec;
+
+#define AMG_MAX_LEVELS 4
+
+typedef struct amg_lattice amg_lattice;
+typedef struct amg_gauge amg_gauge;
+typedef struct amg_dirac amg_dirac;
+typedef struct amg_hierarchy amg_hierarchy;
+typedef struct CUstream_st* amg_stream;   /* = cudaStream_t */
+
+/* Multigrid parameters (Sec. 3; numbers in brackets are defaults from
+ * amg_params_default).  Level 0 is the fine lattice; coarsening l maps level
+ * l to level l+1 with block[l] and nvec[l]. */
+typedef struct {
+    int nlevels;                        /* number of grids, 2..AMG_MAX_LEVELS [2] */
+    int block[AMG_MAX_LEVELS - 1][4];   /* block dims per coarsening, {bx, by, bz, bt} [4,4,4,4] */
+    int nvec[AMG_MAX_LEVELS - 1];       /* test vectors per coarsening [24] */
+    int n_init;                         /* setup (0-a): SAP applications per test vector [3] */
+    int n_adapt;                        /* setup (0-b): adaptive passes v <- M v [2] */
+    int sap_iters;                      /* SAP iterations n of the Sec. 3 listing [4] */
+    int mr_iters;                       /* inner-domain minimal-residual steps [6] */
+    double coarse_tol;                  /* coarsest solve, relative residual [1e-2] */
+    int coarse_maxit;                   /* coarsest solve, BiCGStab(l) cycles [200] */
+    int coarse_ell;                     /* l of BiCGStab(l), 1..4 [2] */
+    int inter_m;                        /* intermediate levels: flexible GMRES(m) [8] */
+    double inter_tol;                   /* intermediate levels: relative tolerance [1e-1] */
+    int inter_maxit;                    /* intermediate levels: max steps [8] */
+    int outer_m;                        /* outer flexible GMRES restart length [16] */
+    int prec_smoother;                  /* fine D / SAP / R / P precision: AMG_F64, AMG_F32, AMG_F16 [AMG_F32] */
+    int prec_coarse;                    /* coarse operators above the coarsest: AMG_F64, AMG_F32, AMG_BF16 [AMG_F32] */
+    int prec_coarsest;                  /* coarsest-level solve: AMG_F64 or AMG_F32 [AMG_F32] */
+} amg_params;
+
+typedef struct {
+    int iters;                  /* outer flexible GMRES steps (= preconditioner applications) */
+    int restarts;
+    int converged;              /* 1 if ||b - D x|| / ||b|| <= tol in FP64 */
+    double true_rel_residual;   /* FP64 ||b - D x|| / ||b|| recomputed at exit */
+    double ms_total;            /* wall time of the call */
+    double ms_coarse;           /* time in coarse solves (the phase split of Table 1) */
+    double ms_smoother;         /* time in SAP */
+    double ms_restrict_prolong; /* time in restriction + prolongation */
+    double ms_other;            /* everything else (outer Krylov, residuals, conversions) */
+    int coarse_cycles;          /* total BiCGStab(l) cycles on the coarsest level */
+} amg_solve_info;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* amg_last_error(void);
+
+/* Fill p with the defaults listed above. */
+void amg_params_default(amg_params* p);
+
+/* ---- lattice and fields (Sec. 2) ------------------------------------- */
+
+/* A 4D lattice.  dims must be >= 2 in every direction.  Fails with
+ * AMG_EINVAL otherwise. */
+amg_status amg_lattice_create(const int dims[4], int antiperiodic_t, amg_lattice** out);
+void amg_lattice_destroy(amg_lattice* lat);
+
+/* Gauge field U_mu(x) (Eq. 1) from host memory, canonical gauge layout,
+ * V*4*9 complex doubles.  Copied to the device (FP64 master, plus FP32/FP16
+ * two-row forms on demand). */
+amg_status amg_gauge_create(amg_lattice* lat, const double* U_host, amg_gauge** out);
+void amg_gauge_destroy(amg_gauge* g);
+
+/* Wilson-clover operator of Eq. 1 with hopping parameter kappa and clover
+ * coefficient csw.  Builds the clover term F(x) on the device in FP64 from
+ * the links: F = -kappa csw sum_{mu<nu} sigma_munu F_munu, F_munu the
+ * traceless anti-Hermitian part of the four-leaf clover divided by 8i,
+ * sigma_munu = [gamma_mu, gamma_nu]/(2i).  In the chiral basis 1 + F is two
+ * 6x6 Hermitian blocks per site. */
+amg_status amg_dirac_create(amg_gauge* g, double kappa, double csw, amg_dirac** out);
+void amg_dirac_destroy(amg_dirac* d);
+
+/* Copy 1 + F(x) to host memory as [site][chirality 2][6][6][re, im] doubles
+ * (row/col index = (spin - 2*chirality)*3 + colour). */
+amg_status amg_dirac_get_clover(amg_dirac* d, double* host_out);
+
+/* out = D in (Eq. 1) for nrhs canonical fine vectors (device pointers).
+ * prec selects the storage/arithmetic of D and the element type of in/out.
+ * in and out must not alias. */
+amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s);
+
+/* out = D_SAP in: D with every hop between different blocks of size block[4]
+ * switched off (Sec. 3, SAP paragraph).  block must tile the lattice with at
+ * least two blocks per direction. */
+amg_status amg_apply_Dsap(amg_dirac* d, const int block[4], const void* in, void* out, int nrhs,
+                          amg_prec prec, amg_stream s);
+
+/* ---- multigrid hierarchy (Sec. 3 step 0) ------------------------------ */
+
+/* Adaptive setup, steps (0-a) and (0-b) of Sec. 3: the init vectors are
+ * smoothed by n_init SAP applications, block-orthonormalised in FP64 per
+ * (domain, chirality) by Gram-Schmidt applied twice, the Galerkin coarse
+ * operator D_c = <I|D|J> (Eq. 6) is built, then n_adapt passes v <- M v
+ * follow.  init_vecs[l] is a host array of nvec[l] canonical vectors of
+ * level l (doubles); the random numbers of the setup are these inputs.
+ * Fails with AMG_EINVAL on a bad blocking or a rank-deficient domain. */
+amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* init_vecs,
+                     amg_hierarchy** out);
+
+/* Hierarchy from given test vectors without smoothing: orthonormalise and
+ * build the Galerkin operators (Eqs. 4-6) level by level.  Used by
+ * checkpoint loading and for exact parity tests of the construction. */
+amg_status amg_setup_from_vectors(amg_dirac* d, const amg_params* p, const double* const* vecs,
+                                  amg_hierarchy** out);
+void amg_hierarchy_destroy(amg_hierarchy* h);
+
+/* Coarse lattice dims and Nc of level l (1 <= l < nlevels). */
+amg_status amg_level_info(amg_hierarchy* h, int level, int dims_out[4], int* nc_out);
+
+/* Orthonormalised test vectors of coarsening l as canonical level-l vectors
+ * (host doubles, nvec[l] of them). */
+amg_status amg_get_vectors(amg_hierarchy* h, int coarsening, double* host_out);
+
+/* Coarse operator of level l >= 1 as host doubles [site][d 9][Nc][Nc][re, im]
+ * with d = 0 self, 1+mu the block coupling X to X+mu, 5+mu to X-mu, so that
+ * y(X) = sum_d B[X][d] x(X + d) (the 9-point stencil of Eq. 6). */
+amg_status amg_get_coarse_op(amg_hierarchy* h, int level, double* host_out);
+
+/* Save / load the test vectors and parameters of a hierarchy (the setup is
+ * reused for many right-hand sides, Sec. 3).  Loading rebuilds the coarse
+ * operators from the stored vectors with amg_setup_from_vectors. */
+amg_status amg_setup_save(const amg_hierarchy* h, const char* path);
+amg_status amg_setup_load(amg_dirac* d, const char* path, amg_hierarchy** out);
+
+/* ---- transfer and coarse operators (Eqs. 4-6) -------------------------- */
+
+/* y = D_c x on level l >= 1 (the 9-point stencil), nrhs canonical coarse
+ * vectors; prec AMG_F64 (double vectors) or AMG_F32 / AMG_BF16 (float). */
+amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* out, int nrhs,
+                            amg_prec prec, amg_stream s);
+
+/* Eq. 4: coarse(I) = <I|fine> from level `coarsening` to coarsening+1.
+ * fine is canonical at that level; element type from prec as above. */
+amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void* coarse, int nrhs,
+                        amg_prec prec, amg_stream s);
+
+/* Eq. 5: fine = sum_I coarse(I) |I>. */
+amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, void* fine, int nrhs,
+                       amg_prec prec, amg_stream s);
+
+/* x = SAP(b) on the fine lattice (Sec. 3 listing: x = 0, r = b, n times
+ * {x += M_e r; r = b - Dx; x += M_o r; r = b - Dx}, M = mr_iters minimal
+ * residual steps per domain), in the smoother precision. Canonical vectors. */
+amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_stream s);
+
+/* x = M b: one application of the multigrid preconditioner (Sec. 3 steps
+ * (1) and (2)).  Canonical double vectors. */
+amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_stream s);
+
+/* ---- solve ------------------------------------------------------------- */
+
+/* Solve D x = b for nrhs canonical double vectors with flexible GMRES(outer_m)
+ * preconditioned by the multigrid cycle, until the FP64 true residual
+ * ||b - D x|| / ||b|| <= tol (recomputed at every restart and at exit) or
+ * maxit outer steps.  x is an input initial guess if use_x0 != 0, else
+ * overwritten.  info (may be NULL) receives the last right-hand side's
+ * numbers.  Returns AMG_NOT_CONVERGED if any rhs misses tol. */
+amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, double tol, int maxit,
+                     int use_x0, amg_solve_info* info, amg_stream s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_AMG_H */

@@ -1,0 +1,1052 @@
+// C ABI of the library (include/lqcd_amg.h): handles, the adaptive setup,
+// the multigrid cycle and the Krylov solvers, all driving the kernels of
+// fine.cu, transfer.cu, coarse.cu and blas.cu on one stream.
+#include "lqcd_amg.h"
+#include "kernels.h"
+
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using cplx = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_err;
+
+amg_status fail(amg_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CK(x)                                                                                    \
+    do {                                                                                         \
+        cudaError_t e_ = (x);                                                                    \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(AMG_ECUDA, std::string(#x) + " -> " + cudaGetErrorString(e_));          \
+    } while (0)
+#define TRY(x)                        \
+    do {                              \
+        amg_status s_ = (x);          \
+        if (s_ != AMG_OK) return s_;  \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            if (p) cudaFree(p);
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    template <typename T> T* as() const { return (T*)p; }
+};
+
+int coarse_elem_bytes(int prec) { return prec == 0 ? 16 : 8; }
+int vec_prec_of(int fine_prec) { return fine_prec == 0 ? 0 : 1; }
+
+}  // namespace
+
+struct amg_lattice {
+    GeomH g;
+};
+struct amg_gauge {
+    amg_lattice* lat;
+    DevBuf U[3];
+};
+struct amg_dirac {
+    amg_gauge* gauge;
+    double kappa, csw;
+    DevBuf C[3];
+    DevBuf in, out;   // call scratch for the canonical-layout entry points
+};
+
+namespace {
+
+struct CoarseLevel {
+    GeomH g;
+    int nc = 0;
+    int prec = 1;
+    DevBuf B;
+};
+
+// pinned partial-sum staging for reductions
+struct Reducer {
+    DevBuf dpart;
+    double2* hpart = nullptr;
+    int grid = 0;
+    ~Reducer() {
+        if (hpart) cudaFreeHost(hpart);
+    }
+    amg_status init() {
+        grid = blas_grid();
+        CK(dpart.ensure(sizeof(double2) * grid * 20));
+        if (!hpart) CK(cudaMallocHost(&hpart, sizeof(double2) * grid * 20));
+        return AMG_OK;
+    }
+    // k dots <a_j, b>
+    amg_status dots(int prec, int k, const void* const* a, const void* b, size_t n, cplx* out, cudaStream_t s) {
+        CK(launch_multi_dot(prec, k, a, b, n, dpart.as<double2>(), s));
+        CK(cudaMemcpyAsync(hpart, dpart.p, sizeof(double2) * grid * k, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int j = 0; j < k; ++j) {
+            double re = 0, im = 0;
+            for (int q = 0; q < grid; ++q) {
+                re += hpart[j * grid + q].x;
+                im += hpart[j * grid + q].y;
+            }
+            out[j] = cplx(re, im);
+        }
+        return AMG_OK;
+    }
+    amg_status dot(int prec, const void* a, const void* b, size_t n, cplx* out, cudaStream_t s) {
+        const void* l[1] = {a};
+        return dots(prec, 1, l, b, n, out, s);
+    }
+    amg_status norm2(int prec, const void* a, size_t n, double* out, cudaStream_t s) {
+        CK(launch_norm2(prec, a, n, (double*)dpart.p, s));
+        CK(cudaMemcpyAsync(hpart, dpart.p, sizeof(double) * grid, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double* h = (const double*)hpart;
+        double t = 0;
+        for (int q = 0; q < grid; ++q) t += h[q];
+        *out = t;
+        return AMG_OK;
+    }
+};
+
+inline double2 d2(cplx c) { return make_double2(c.real(), c.imag()); }
+
+// phase timers (Table 1 split: coarse / smoother / R+P / other)
+enum Phase { PH_COARSE = 0, PH_SMOOTH = 1, PH_RP = 2, PH_NPH = 3 };
+struct PhaseTimer {
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, int>> marks;   // (event index, phase) start/stop pairs
+    std::vector<int> phase_of;
+    size_t used = 0;
+    bool on = false;
+    ~PhaseTimer() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void start(int ph, cudaStream_t s) {
+        if (!on) return;
+        cudaEvent_t e = next();
+        cudaEventRecord(e, s);
+        phase_of.push_back(ph);
+    }
+    void stop(cudaStream_t s) {
+        if (!on) return;
+        cudaEvent_t e = next();
+        cudaEventRecord(e, s);
+    }
+    void reset() {
+        used = 0;
+        phase_of.clear();
+    }
+    void collect(double ms[PH_NPH]) {
+        for (int i = 0; i < PH_NPH; ++i) ms[i] = 0;
+        for (size_t k = 0; k < phase_of.size(); ++k) {
+            float t = 0;
+            cudaEventSynchronize(pool[2 * k + 1]);
+            cudaEventElapsedTime(&t, pool[2 * k], pool[2 * k + 1]);
+            ms[phase_of[k]] += t;
+        }
+    }
+};
+
+}  // namespace
+
+struct amg_hierarchy {
+    amg_dirac* d = nullptr;
+    amg_params p;
+    int fp = 1;     // smoother precision used by the solve
+    int vp = 1;     // test-vector precision (and the setup's cycle precision)
+    BlockH blk[AMG_MAX_LEVELS - 1];
+    DevBuf vecs0;
+    std::vector<CoarseLevel> lev;   // lev[l] for l = 1..nlevels-1 (lev[0] unused)
+    // fine workspaces per precision: b, x
+    DevBuf fb[3], fx[3];
+    // setup scratch
+    DevBuf tmpv;
+    // coarse workspaces per level: bc, xc, Krylov vectors
+    std::vector<std::vector<DevBuf*>> cw;
+    // outer FGMRES (FP64 internal fine vectors)
+    DevBuf ob, ox, ow, orr;
+    std::vector<DevBuf*> oV, oZ;
+    DevBuf canon;   // canonical staging
+    Reducer red;
+    PhaseTimer timer;
+    int err_flag_host = 0;
+    DevBuf err_flag;
+    int coarse_cycles = 0;
+    ~amg_hierarchy() {
+        for (auto& v : cw)
+            for (auto* b : v) delete b;
+        for (auto* b : oV) delete b;
+        for (auto* b : oZ) delete b;
+    }
+};
+
+namespace {
+
+const GeomH& fine_geom(amg_hierarchy* h) { return h->d->gauge->lat->g; }
+size_t fine_n(amg_hierarchy* h) { return (size_t)fine_geom(h).V * 12; }
+size_t coarse_n(const CoarseLevel& L) { return (size_t)L.g.V * L.nc; }
+
+amg_status check_params(const GeomH& g, const amg_params* p) {
+    if (!p) return fail(AMG_EINVAL, "params is NULL");
+    if (p->nlevels != 2) return fail(AMG_EINVAL, "nlevels must be 2 in this build");
+    int L[4] = {g.L[0], g.L[1], g.L[2], g.L[3]};
+    for (int l = 0; l < p->nlevels - 1; ++l) {
+        if (p->nvec[l] < 1 || p->nvec[l] > 64) return fail(AMG_EINVAL, "nvec must be in 1..64");
+        for (int mu = 0; mu < 4; ++mu) {
+            int b = p->block[l][mu];
+            if (b < 1 || L[mu] % b != 0) return fail(AMG_EINVAL, "block does not tile the lattice");
+            int C = L[mu] / b;
+            if (C < 2 || C % 2 != 0)
+                return fail(AMG_EINVAL, "need an even number (>= 2) of blocks per direction (SAP colouring)");
+            L[mu] = C;
+        }
+        int vb = p->block[l][0] * p->block[l][1] * p->block[l][2] * p->block[l][3];
+        if (vb > 512) return fail(AMG_EINVAL, "block volume must be <= 512 sites");
+    }
+    if (p->prec_smoother < 0 || p->prec_smoother > 2) return fail(AMG_EINVAL, "prec_smoother");
+    if (p->prec_coarsest < 0 || p->prec_coarsest > 1) return fail(AMG_EINVAL, "prec_coarsest");
+    if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
+    if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
+    if (p->sap_iters < 0 || p->mr_iters < 0) return fail(AMG_EINVAL, "sap_iters / mr_iters");
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- fine ops
+amg_status fine_D(amg_hierarchy* h, int prec, const void* in, void* out, const void* b, cudaStream_t s) {
+    amg_dirac* d = h->d;
+    CK(launch_dirac(prec, fine_geom(h), nullptr, d->gauge->U[prec].p, d->C[prec].p, in, out, b, d->kappa, 1, s));
+    return AMG_OK;
+}
+
+amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_zero, cudaStream_t s) {
+    amg_dirac* d = h->d;
+    h->timer.start(PH_SMOOTH, s);
+    for (int i = 0; i < h->p.sap_iters; ++i) {
+        const bool first = x_zero && i == 0;
+        CK(launch_sap_half(prec, fine_geom(h), h->blk[0], 0, h->p.mr_iters, first ? 1 : 0, d->gauge->U[prec].p,
+                           d->C[prec].p, b, x, d->kappa, s));
+        CK(launch_sap_half(prec, fine_geom(h), h->blk[0], 1, h->p.mr_iters, first ? 2 : 0, d->gauge->U[prec].p,
+                           d->C[prec].p, b, x, d->kappa, s));
+    }
+    if (h->p.sap_iters == 0 && x_zero) CK(cudaMemsetAsync(x, 0, fine_spinor_bytes(prec, fine_geom(h).V), s));
+    h->timer.stop(s);
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- coarse solve
+CoarseLevel& L1(amg_hierarchy* h) { return h->lev[1]; }
+
+amg_status coarse_apply(amg_hierarchy* h, int l, const void* in, void* out, const void* b, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    CK(launch_coarse_apply(L.prec, L.g, L.nc, nullptr, L.B.p, in, out, b, 1, s));
+    return AMG_OK;
+}
+
+// BiCGStab(l) (Sleijpen-Fokkema) on the coarsest level, relative tolerance tol.
+amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    const int pr = L.prec, ell = h->p.coarse_ell;
+    const size_t n = coarse_n(L), bytes = n * coarse_elem_bytes(pr);
+    auto& w = h->cw[l];   // [0] bc, [1] xc, [2] rt, [3..3+ell] R, [4+ell..4+2ell] U
+    void* rt = w[2]->p;
+    std::vector<void*> R(ell + 1), U(ell + 1);
+    for (int j = 0; j <= ell; ++j) {
+        R[j] = w[3 + j]->p;
+        U[j] = w[4 + ell + j]->p;
+    }
+    Reducer& red = h->red;
+    CK(cudaMemsetAsync(x, 0, bytes, s));
+    CK(cudaMemcpyAsync(R[0], b, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(rt, b, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(U[0], 0, bytes, s));
+    double bn2;
+    TRY(red.norm2(pr, b, n, &bn2, s));
+    if (bn2 == 0) return AMG_OK;
+    const double bnorm = std::sqrt(bn2);
+    cplx rho0 = 1, alpha = 0, omega = 1;
+    for (int cycle = 0; cycle < h->p.coarse_maxit; ++cycle) {
+        double rn2;
+        TRY(red.norm2(pr, R[0], n, &rn2, s));
+        if (!std::isfinite(rn2)) return fail(AMG_NAN, "coarse solve: non-finite residual");
+        if (std::sqrt(rn2) <= h->p.coarse_tol * bnorm) break;
+        h->coarse_cycles++;
+        rho0 = -omega * rho0;
+        for (int j = 0; j < ell; ++j) {
+            cplx rho1;
+            TRY(red.dot(pr, rt, R[j], n, &rho1, s));
+            cplx beta = alpha * rho1 / rho0;
+            rho0 = rho1;
+            for (int i = 0; i <= j; ++i) CK(launch_axpby(pr, make_double2(1, 0), R[i], d2(-beta), U[i], n, s));
+            TRY(coarse_apply(h, l, U[j], U[j + 1], nullptr, s));
+            cplx gam;
+            TRY(red.dot(pr, rt, U[j + 1], n, &gam, s));
+            alpha = rho0 / gam;
+            for (int i = 0; i <= j; ++i) CK(launch_axpby(pr, d2(-alpha), U[i + 1], make_double2(1, 0), R[i], n, s));
+            TRY(coarse_apply(h, l, R[j], R[j + 1], nullptr, s));
+            CK(launch_axpby(pr, d2(alpha), U[0], make_double2(1, 0), x, n, s));
+        }
+        // minimal-residual part: modified Gram-Schmidt on R[1..ell]
+        std::vector<std::vector<cplx>> tau(ell + 1, std::vector<cplx>(ell + 1));
+        std::vector<double> sigma(ell + 1);
+        std::vector<cplx> gp(ell + 1), g(ell + 1), gpp(ell + 1);
+        for (int j = 1; j <= ell; ++j) {
+            for (int i = 1; i < j; ++i) {
+                cplx t;
+                TRY(red.dot(pr, R[i], R[j], n, &t, s));
+                tau[i][j] = t / sigma[i];
+                CK(launch_axpby(pr, d2(-tau[i][j]), R[i], make_double2(1, 0), R[j], n, s));
+            }
+            double sg;
+            TRY(red.norm2(pr, R[j], n, &sg, s));
+            sigma[j] = sg;
+            if (!(sg > 0)) return fail(AMG_NAN, "coarse solve: breakdown");
+            cplx t;
+            TRY(red.dot(pr, R[j], R[0], n, &t, s));
+            gp[j] = t / sg;
+        }
+        g[ell] = gp[ell];
+        omega = g[ell];
+        for (int j = ell - 1; j >= 1; --j) {
+            cplx t = gp[j];
+            for (int i = j + 1; i <= ell; ++i) t -= tau[j][i] * g[i];
+            g[j] = t;
+        }
+        for (int j = 1; j < ell; ++j) {
+            cplx t = g[j + 1];
+            for (int i = j + 1; i < ell; ++i) t += tau[j][i] * g[i + 1];
+            gpp[j] = t;
+        }
+        CK(launch_axpby(pr, d2(g[1]), R[0], make_double2(1, 0), x, n, s));
+        CK(launch_axpby(pr, d2(-gp[ell]), R[ell], make_double2(1, 0), R[0], n, s));
+        CK(launch_axpby(pr, d2(-g[ell]), U[ell], make_double2(1, 0), U[0], n, s));
+        for (int j = 1; j < ell; ++j) {
+            CK(launch_axpby(pr, d2(-g[j]), U[j], make_double2(1, 0), U[0], n, s));
+            CK(launch_axpby(pr, d2(gpp[j]), R[j], make_double2(1, 0), x, n, s));
+            CK(launch_axpby(pr, d2(-gp[j]), R[j], make_double2(1, 0), R[0], n, s));
+        }
+    }
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- V-cycle
+// x = M b on the fine lattice in precision prec (b, x internal fields):
+// step (1) x = P D_c^{-1} R b, step (2) x += SAP(b - D x).
+amg_status vcycle0(amg_hierarchy* h, int prec, const void* b, void* x, cudaStream_t s) {
+    CoarseLevel& L = L1(h);
+    auto& w = h->cw[1];
+    h->timer.start(PH_RP, s);
+    CK(launch_restrict_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, b, w[0]->p, s));
+    h->timer.stop(s);
+    h->timer.start(PH_COARSE, s);
+    TRY(coarse_bicgstab(h, 1, w[0]->p, w[1]->p, s));
+    h->timer.stop(s);
+    h->timer.start(PH_RP, s);
+    CK(launch_prolong_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, w[1]->p, x, s));
+    h->timer.stop(s);
+    TRY(fine_sap(h, prec, b, x, false, s));
+    return AMG_OK;
+}
+
+// z = M v for FP64 internal fields (precision switch around the cycle)
+amg_status precondition64(amg_hierarchy* h, const void* v, void* z, cudaStream_t s) {
+    const GeomH& g = fine_geom(h);
+    int fp = h->fp;
+    if (fp == 0) return vcycle0(h, 0, v, z, s);
+    CK(launch_convert_spinor(0, fp, g, v, h->fb[fp].p, 1, s));
+    TRY(vcycle0(h, fp, h->fb[fp].p, h->fx[fp].p, s));
+    CK(launch_convert_spinor(fp, 0, g, h->fx[fp].p, z, 1, s));
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- outer FGMRES
+amg_status fgmres(amg_hierarchy* h, const void* b, void* x, double tol, int maxit, amg_solve_info* info,
+                  cudaStream_t s) {
+    const int m = h->p.outer_m;
+    const size_t n = fine_n(h);
+    Reducer& red = h->red;
+    double bn2;
+    TRY(red.norm2(0, b, n, &bn2, s));
+    const double bnorm = std::sqrt(bn2);
+    int iters = 0, restarts = 0;
+    double rel = 0;
+    bool conv = false;
+    if (bnorm == 0) {
+        CK(cudaMemsetAsync(x, 0, n * 16, s));
+        conv = true;
+    }
+    std::vector<std::vector<cplx>> H(m + 1, std::vector<cplx>(m));
+    std::vector<double> cs(m);
+    std::vector<cplx> sn(m), gv(m + 1);
+    while (!conv) {
+        TRY(fine_D(h, 0, x, h->orr.p, b, s));   // r = b - D x
+        double rn2;
+        TRY(red.norm2(0, h->orr.p, n, &rn2, s));
+        if (!std::isfinite(rn2)) return fail(AMG_NAN, "outer solve: non-finite residual");
+        double rn = std::sqrt(rn2);
+        rel = rn / bnorm;
+        if (rn <= tol * bnorm) {
+            conv = true;
+            break;
+        }
+        if (iters >= maxit) break;
+        if (iters > 0) restarts++;
+        CK(launch_axpby(0, make_double2(1.0 / rn, 0), h->orr.p, make_double2(0, 0), h->oV[0]->p, n, s));
+        for (auto& row : H) std::fill(row.begin(), row.end(), cplx(0));
+        std::fill(gv.begin(), gv.end(), cplx(0));
+        gv[0] = rn;
+        int jend = -1;
+        for (int j = 0; j < m; ++j) {
+            TRY(precondition64(h, h->oV[j]->p, h->oZ[j]->p, s));
+            TRY(fine_D(h, 0, h->oZ[j]->p, h->ow.p, nullptr, s));
+            // classical Gram-Schmidt, twice
+            std::vector<const void*> vl(j + 1);
+            std::vector<const void*> vx(j + 1);
+            for (int i = 0; i <= j; ++i) vl[i] = vx[i] = h->oV[i]->p;
+            for (int pass = 0; pass < 2; ++pass) {
+                std::vector<cplx> c(j + 1);
+                TRY(red.dots(0, j + 1, vl.data(), h->ow.p, n, c.data(), s));
+                std::vector<double2> nc(j + 1);
+                for (int i = 0; i <= j; ++i) {
+                    H[i][j] += c[i];
+                    nc[i] = d2(-c[i]);
+                }
+                CK(launch_multi_axpy(0, j + 1, nc.data(), vx.data(), h->ow.p, n, s));
+            }
+            double hn2;
+            TRY(red.norm2(0, h->ow.p, n, &hn2, s));
+            double hn = std::sqrt(hn2);
+            H[j + 1][j] = hn;
+            iters++;
+            // Givens rotations
+            for (int i = 0; i < j; ++i) {
+                cplx a = H[i][j], bb = H[i + 1][j];
+                H[i][j] = cs[i] * a + sn[i] * bb;
+                H[i + 1][j] = -std::conj(sn[i]) * a + cs[i] * bb;
+            }
+            {
+                cplx a = H[j][j], bb = H[j + 1][j];
+                double aa = std::abs(a), ab = std::abs(bb);
+                if (ab == 0) {
+                    cs[j] = 1;
+                    sn[j] = 0;
+                } else if (aa == 0) {
+                    cs[j] = 0;
+                    sn[j] = std::conj(bb) / ab;
+                } else {
+                    double t = std::sqrt(aa * aa + ab * ab);
+                    cs[j] = aa / t;
+                    sn[j] = (a / aa) * std::conj(bb) / t;
+                }
+                H[j][j] = cs[j] * a + sn[j] * bb;
+                H[j + 1][j] = 0;
+                gv[j + 1] = -std::conj(sn[j]) * gv[j];
+                gv[j] = cs[j] * gv[j];
+            }
+            jend = j;
+            double est = std::abs(gv[j + 1]);
+            if (!std::isfinite(est)) return fail(AMG_NAN, "outer solve: non-finite Arnoldi coefficient");
+            if (hn == 0 || est <= tol * bnorm || iters >= maxit) break;
+            CK(launch_axpby(0, make_double2(1.0 / hn, 0), h->ow.p, make_double2(0, 0), h->oV[j + 1]->p, n, s));
+        }
+        // back substitution and update x += Z y
+        int k = jend + 1;
+        std::vector<cplx> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            cplx t = gv[i];
+            for (int q = i + 1; q < k; ++q) t -= H[i][q] * y[q];
+            y[i] = t / H[i][i];
+        }
+        std::vector<double2> yc(k);
+        std::vector<const void*> zl(k);
+        for (int i = 0; i < k; ++i) {
+            yc[i] = d2(y[i]);
+            zl[i] = h->oZ[i]->p;
+        }
+        CK(launch_multi_axpy(0, k, yc.data(), zl.data(), x, n, s));
+    }
+    if (info) {
+        info->iters = iters;
+        info->restarts = restarts;
+        info->converged = conv ? 1 : 0;
+        info->true_rel_residual = rel;
+    }
+    return conv ? AMG_OK : AMG_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------- setup pieces
+amg_status alloc_workspaces(amg_hierarchy* h) {
+    const GeomH& g = fine_geom(h);
+    TRY(h->red.init());
+    CK(h->err_flag.ensure(sizeof(int)));
+    for (int pr = 0; pr < 3; ++pr) {
+        CK(h->fb[pr].ensure(fine_spinor_bytes(pr, g.V)));
+        CK(h->fx[pr].ensure(fine_spinor_bytes(pr, g.V)));
+    }
+    CK(h->tmpv.ensure(fine_spinor_bytes(h->vp, g.V)));
+    h->cw.resize(h->p.nlevels);
+    for (int l = 1; l < h->p.nlevels; ++l) {
+        CoarseLevel& L = h->lev[l];
+        size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
+        int nv = 4 + 2 * (h->p.coarse_ell + 1);
+        for (int k = 0; k < nv; ++k) {
+            DevBuf* b = new DevBuf();
+            h->cw[l].push_back(b);
+            CK(b->ensure(bytes));
+        }
+    }
+    const size_t fb64 = fine_spinor_bytes(0, g.V);
+    CK(h->ob.ensure(fb64));
+    CK(h->ox.ensure(fb64));
+    CK(h->ow.ensure(fb64));
+    CK(h->orr.ensure(fb64));
+    for (int j = 0; j <= h->p.outer_m; ++j) {
+        DevBuf* b = new DevBuf();
+        h->oV.push_back(b);
+        CK(b->ensure(fb64));
+        if (j < h->p.outer_m) {
+            DevBuf* z = new DevBuf();
+            h->oZ.push_back(z);
+            CK(z->ensure(fb64));
+        }
+    }
+    return AMG_OK;
+}
+
+amg_status build_levels(amg_hierarchy* h) {
+    const GeomH& g = fine_geom(h);
+    h->lev.resize(h->p.nlevels);
+    GeomH cur = g;
+    for (int l = 0; l < h->p.nlevels - 1; ++l) {
+        for (int mu = 0; mu < 4; ++mu) h->blk[l].b[mu] = h->p.block[l][mu];
+        CoarseLevel& L = h->lev[l + 1];
+        L.g.V = 1;
+        for (int mu = 0; mu < 4; ++mu) {
+            L.g.L[mu] = cur.L[mu] / h->p.block[l][mu];
+            L.g.V *= L.g.L[mu];
+        }
+        L.g.antiperiodic = 0;
+        L.nc = 2 * h->p.nvec[l];
+        L.prec = (l + 1 == h->p.nlevels - 1) ? h->p.prec_coarsest : (h->p.prec_coarse == 0 ? 0 : 1);
+        CK(L.B.ensure((size_t)L.g.V * 9 * L.nc * L.nc * coarse_elem_bytes(L.prec)));
+        cur = L.g;
+    }
+    CK(h->vecs0.ensure(fine_spinor_bytes(h->vp, g.V) * h->p.nvec[0]));
+    return AMG_OK;
+}
+
+amg_status orthonormalise_and_galerkin(amg_hierarchy* h, cudaStream_t s) {
+    const GeomH& g = fine_geom(h);
+    CK(cudaMemsetAsync(h->err_flag.p, 0, sizeof(int), s));
+    CK(launch_orthonormalise_fine(h->vp, g, h->blk[0], h->p.nvec[0], h->vecs0.p, h->err_flag.as<int>(), s));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (flag) return fail(AMG_EINVAL, "test vectors are rank deficient on some domain");
+    amg_dirac* d = h->d;
+    CoarseLevel& L = L1(h);
+    CK(launch_galerkin_fine(h->vp, L.prec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, d->gauge->U[h->vp].p,
+                            d->C[h->vp].p, d->kappa, L.B.p, s));
+    return AMG_OK;
+}
+
+amg_status upload_vectors(amg_hierarchy* h, const double* host, cudaStream_t s) {
+    const GeomH& g = fine_geom(h);
+    const size_t cb = (size_t)g.V * 24 * sizeof(double);
+    CK(h->canon.ensure(cb));
+    const size_t vb = fine_spinor_bytes(h->vp, g.V);
+    for (int i = 0; i < h->p.nvec[0]; ++i) {
+        CK(cudaMemcpyAsync(h->canon.p, host + (size_t)i * g.V * 24, cb, cudaMemcpyHostToDevice, s));
+        if (h->vp == 0) {
+            CK(launch_pack_spinor(0, g, h->canon.p, (char*)h->vecs0.p + i * vb, 1, s));
+        } else {
+            // canonical doubles -> P64 internal -> P32 internal
+            CK(launch_pack_spinor(0, g, h->canon.p, h->fb[0].p, 1, s));
+            CK(launch_convert_spinor(0, 1, g, h->fb[0].p, (char*)h->vecs0.p + i * vb, 1, s));
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+amg_status normalise_into(amg_hierarchy* h, int prec, const void* src, void* dst, cudaStream_t s) {
+    const size_t n = fine_n(h);
+    double nn;
+    TRY(h->red.norm2(prec, src, n, &nn, s));
+    if (!(nn > 0) || !std::isfinite(nn)) return fail(AMG_NAN, "setup: test vector vanished or is not finite");
+    CK(launch_axpby(prec, make_double2(1.0 / std::sqrt(nn), 0), src, make_double2(0, 0), dst, n, s));
+    return AMG_OK;
+}
+
+amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out, amg_hierarchy** hp) {
+    if (!d || !out) return fail(AMG_EINVAL, "NULL argument");
+    TRY(check_params(d->gauge->lat->g, p));
+    amg_hierarchy* h = new amg_hierarchy();
+    h->d = d;
+    h->p = *p;
+    h->fp = p->prec_smoother;
+    h->vp = vec_prec_of(p->prec_smoother);
+    *hp = h;
+    amg_status st = build_levels(h);
+    if (st == AMG_OK) st = alloc_workspaces(h);
+    if (st != AMG_OK) {
+        delete h;
+        *hp = nullptr;
+        return st;
+    }
+    return AMG_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* amg_last_error(void) { return g_err.c_str(); }
+
+void amg_params_default(amg_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nlevels = 2;
+    for (int l = 0; l < AMG_MAX_LEVELS - 1; ++l) {
+        for (int mu = 0; mu < 4; ++mu) p->block[l][mu] = 4;
+        p->nvec[l] = 24;
+    }
+    p->n_init = 3;
+    p->n_adapt = 2;
+    p->sap_iters = 4;
+    p->mr_iters = 6;
+    p->coarse_tol = 1e-2;
+    p->coarse_maxit = 200;
+    p->coarse_ell = 2;
+    p->inter_m = 8;
+    p->inter_tol = 1e-1;
+    p->inter_maxit = 8;
+    p->outer_m = 16;
+    p->prec_smoother = AMG_F32;
+    p->prec_coarse = AMG_F32;
+    p->prec_coarsest = AMG_F32;
+}
+
+amg_status amg_lattice_create(const int dims[4], int antiperiodic_t, amg_lattice** out) {
+    if (!dims || !out) return fail(AMG_EINVAL, "NULL argument");
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2) return fail(AMG_EINVAL, "lattice extents must be >= 2");
+        V *= dims[mu];
+    }
+    if (V > (1ll << 30)) return fail(AMG_EINVAL, "lattice too large");
+    amg_lattice* l = new amg_lattice();
+    for (int mu = 0; mu < 4; ++mu) l->g.L[mu] = dims[mu];
+    l->g.V = (int)V;
+    l->g.antiperiodic = antiperiodic_t ? 1 : 0;
+    *out = l;
+    return AMG_OK;
+}
+void amg_lattice_destroy(amg_lattice* l) { delete l; }
+
+amg_status amg_gauge_create(amg_lattice* lat, const double* U_host, amg_gauge** out) {
+    if (!lat || !U_host || !out) return fail(AMG_EINVAL, "NULL argument");
+    const GeomH& g = lat->g;
+    amg_gauge* G = new amg_gauge();
+    G->lat = lat;
+    DevBuf canon;
+    auto cleanup = [&](amg_status st) {
+        delete G;
+        return st;
+    };
+    size_t cb = (size_t)g.V * 4 * 18 * sizeof(double);
+    if (canon.ensure(cb) != cudaSuccess) return cleanup(fail(AMG_ENOMEM, "gauge: device allocation failed"));
+    if (cudaMemcpy(canon.p, U_host, cb, cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(fail(AMG_ECUDA, "gauge: upload failed"));
+    for (int pr = 0; pr < 3; ++pr) {
+        if (G->U[pr].ensure(fine_gauge_bytes(pr, g.V)) != cudaSuccess)
+            return cleanup(fail(AMG_ENOMEM, "gauge: device allocation failed"));
+        if (launch_gauge_convert(pr, g, canon.as<double>(), G->U[pr].p, 0) != cudaSuccess)
+            return cleanup(fail(AMG_ECUDA, "gauge: conversion kernel failed"));
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(AMG_ECUDA, "gauge: conversion failed"));
+    *out = G;
+    return AMG_OK;
+}
+void amg_gauge_destroy(amg_gauge* g) { delete g; }
+
+amg_status amg_dirac_create(amg_gauge* g, double kappa, double csw, amg_dirac** out) {
+    if (!g || !out) return fail(AMG_EINVAL, "NULL argument");
+    amg_dirac* d = new amg_dirac();
+    d->gauge = g;
+    d->kappa = kappa;
+    d->csw = csw;
+    const GeomH& geo = g->lat->g;
+    for (int pr = 0; pr < 3; ++pr) {
+        if (d->C[pr].ensure(fine_clover_bytes(pr, geo.V)) != cudaSuccess) {
+            delete d;
+            return fail(AMG_ENOMEM, "clover: device allocation failed");
+        }
+        cudaError_t e = launch_clover_build(pr, geo, g->U[0].p, kappa, csw, d->C[pr].p, 0);
+        if (e != cudaSuccess) {
+            delete d;
+            return fail(AMG_ECUDA, std::string("clover build: ") + cudaGetErrorString(e));
+        }
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        delete d;
+        return fail(AMG_ECUDA, "clover build failed");
+    }
+    *out = d;
+    return AMG_OK;
+}
+void amg_dirac_destroy(amg_dirac* d) { delete d; }
+
+amg_status amg_dirac_get_clover(amg_dirac* d, double* host_out) {
+    if (!d || !host_out) return fail(AMG_EINVAL, "NULL argument");
+    const GeomH& g = d->gauge->lat->g;
+    DevBuf tmp;
+    size_t bytes = (size_t)g.V * 144 * sizeof(double);
+    CK(tmp.ensure(bytes));
+    CK(launch_clover_expand(g, d->C[0].p, tmp.as<double>(), 0));
+    CK(cudaMemcpy(host_out, tmp.p, bytes, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+}
+
+static amg_status apply_fine_canonical(amg_dirac* d, const BlockH* sb, const void* in, void* out, int nrhs,
+                                       amg_prec prec, cudaStream_t s) {
+    if (!d || !in || !out || nrhs < 1) return fail(AMG_EINVAL, "bad argument");
+    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32 or AMG_F16");
+    const GeomH& g = d->gauge->lat->g;
+    size_t fb = fine_spinor_bytes(prec, g.V) * nrhs;
+    CK(d->in.ensure(fb));
+    CK(d->out.ensure(fb));
+    CK(launch_pack_spinor(prec, g, in, d->in.p, nrhs, s));
+    CK(launch_dirac(prec, g, sb, d->gauge->U[prec].p, d->C[prec].p, d->in.p, d->out.p, nullptr, d->kappa, nrhs, s));
+    CK(launch_unpack_spinor(prec, g, d->out.p, out, nrhs, s));
+    return AMG_OK;
+}
+
+amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s) {
+    return apply_fine_canonical(d, nullptr, in, out, nrhs, prec, (cudaStream_t)s);
+}
+
+amg_status amg_apply_Dsap(amg_dirac* d, const int block[4], const void* in, void* out, int nrhs, amg_prec prec,
+                          amg_stream s) {
+    if (!d || !block) return fail(AMG_EINVAL, "NULL argument");
+    const GeomH& g = d->gauge->lat->g;
+    BlockH b;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (block[mu] < 1 || g.L[mu] % block[mu] != 0 || g.L[mu] / block[mu] < 2)
+            return fail(AMG_EINVAL, "block must tile the lattice with >= 2 blocks per direction");
+        b.b[mu] = block[mu];
+    }
+    return apply_fine_canonical(d, &b, in, out, nrhs, prec, (cudaStream_t)s);
+}
+
+amg_status amg_setup_from_vectors(amg_dirac* d, const amg_params* p, const double* const* vecs,
+                                  amg_hierarchy** out) {
+    if (!vecs || !vecs[0]) return fail(AMG_EINVAL, "vecs is NULL");
+    amg_hierarchy* h = nullptr;
+    TRY(hierarchy_init(d, p, out, &h));
+    cudaStream_t s = 0;
+    amg_status st = upload_vectors(h, vecs[0], s);
+    if (st == AMG_OK) st = orthonormalise_and_galerkin(h, s);
+    if (st == AMG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(AMG_ECUDA, "setup failed");
+    if (st != AMG_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AMG_OK;
+}
+
+amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* init_vecs, amg_hierarchy** out) {
+    if (!init_vecs || !init_vecs[0]) return fail(AMG_EINVAL, "init_vecs is NULL");
+    amg_hierarchy* h = nullptr;
+    TRY(hierarchy_init(d, p, out, &h));
+    cudaStream_t s = 0;
+    auto body = [&]() -> amg_status {
+        TRY(upload_vectors(h, init_vecs[0], s));
+        const GeomH& g = fine_geom(h);
+        const int vp = h->vp;
+        const size_t vb = fine_spinor_bytes(vp, g.V);
+        // (0-a): v <- SAP(v), normalised
+        for (int k = 0; k < h->p.n_init; ++k) {
+            for (int i = 0; i < h->p.nvec[0]; ++i) {
+                void* vi = (char*)h->vecs0.p + i * vb;
+                TRY(fine_sap(h, vp, vi, h->tmpv.p, true, s));
+                TRY(normalise_into(h, vp, h->tmpv.p, vi, s));
+            }
+        }
+        TRY(orthonormalise_and_galerkin(h, s));
+        // (0-b): v <- M v with the current hierarchy, then rebuild
+        for (int k = 0; k < h->p.n_adapt; ++k) {
+            for (int i = 0; i < h->p.nvec[0]; ++i) {
+                void* vi = (char*)h->vecs0.p + i * vb;
+                TRY(vcycle0(h, vp, vi, h->tmpv.p, s));
+                TRY(normalise_into(h, vp, h->tmpv.p, vi, s));
+            }
+            TRY(orthonormalise_and_galerkin(h, s));
+        }
+        CK(cudaStreamSynchronize(s));
+        return AMG_OK;
+    };
+    amg_status st = body();
+    if (st != AMG_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AMG_OK;
+}
+
+void amg_hierarchy_destroy(amg_hierarchy* h) { delete h; }
+
+amg_status amg_level_info(amg_hierarchy* h, int level, int dims_out[4], int* nc_out) {
+    if (!h || level < 1 || level >= h->p.nlevels) return fail(AMG_EINVAL, "bad level");
+    if (dims_out)
+        for (int mu = 0; mu < 4; ++mu) dims_out[mu] = h->lev[level].g.L[mu];
+    if (nc_out) *nc_out = h->lev[level].nc;
+    return AMG_OK;
+}
+
+amg_status amg_get_vectors(amg_hierarchy* h, int coarsening, double* host_out) {
+    if (!h || !host_out || coarsening != 0) return fail(AMG_EINVAL, "bad argument");
+    const GeomH& g = fine_geom(h);
+    const size_t vb = fine_spinor_bytes(h->vp, g.V);
+    const size_t cb = (size_t)g.V * 24 * sizeof(double);
+    CK(h->canon.ensure(cb));
+    for (int i = 0; i < h->p.nvec[0]; ++i) {
+        const void* vi = (const char*)h->vecs0.p + i * vb;
+        if (h->vp == 0) {
+            CK(launch_unpack_spinor(0, g, vi, h->canon.p, 1, 0));
+        } else {
+            CK(launch_convert_spinor(1, 0, g, vi, h->fb[0].p, 1, 0));
+            CK(launch_unpack_spinor(0, g, h->fb[0].p, h->canon.p, 1, 0));
+        }
+        CK(cudaMemcpy(host_out + (size_t)i * g.V * 24, h->canon.p, cb, cudaMemcpyDeviceToHost));
+    }
+    return AMG_OK;
+}
+
+amg_status amg_get_coarse_op(amg_hierarchy* h, int level, double* host_out) {
+    if (!h || !host_out || level < 1 || level >= h->p.nlevels) return fail(AMG_EINVAL, "bad argument");
+    CoarseLevel& L = h->lev[level];
+    DevBuf tmp;
+    size_t bytes = (size_t)L.g.V * 9 * L.nc * L.nc * 2 * sizeof(double);
+    CK(tmp.ensure(bytes));
+    CK(launch_coarse_op_export(L.prec, L.g.V, L.nc, L.B.p, tmp.as<double>(), 0));
+    CK(cudaMemcpy(host_out, tmp.p, bytes, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+}
+
+static const uint64_t kMagic = 0x31474D41444351ull;   // "QCDAMG1"
+
+amg_status amg_setup_save(const amg_hierarchy* hc, const char* path) {
+    amg_hierarchy* h = const_cast<amg_hierarchy*>(hc);
+    if (!h || !path) return fail(AMG_EINVAL, "NULL argument");
+    const GeomH& g = fine_geom(h);
+    std::vector<double> v((size_t)h->p.nvec[0] * g.V * 24);
+    TRY(amg_get_vectors(h, 0, v.data()));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(AMG_EIO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&kMagic, sizeof(kMagic), 1, f) == 1 && std::fwrite(g.L, sizeof(int), 4, f) == 4 &&
+              std::fwrite(&h->p, sizeof(amg_params), 1, f) == 1 &&
+              std::fwrite(v.data(), sizeof(double), v.size(), f) == v.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? AMG_OK : fail(AMG_EIO, "write failed");
+}
+
+amg_status amg_setup_load(amg_dirac* d, const char* path, amg_hierarchy** out) {
+    if (!d || !path || !out) return fail(AMG_EINVAL, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(AMG_EIO, std::string("cannot open ") + path);
+    uint64_t magic = 0;
+    int L[4];
+    amg_params p;
+    bool ok = std::fread(&magic, sizeof(magic), 1, f) == 1 && magic == kMagic && std::fread(L, sizeof(int), 4, f) == 4 &&
+              std::fread(&p, sizeof(p), 1, f) == 1;
+    const GeomH& g = d->gauge->lat->g;
+    for (int mu = 0; ok && mu < 4; ++mu) ok = L[mu] == g.L[mu];
+    std::vector<double> v;
+    if (ok) {
+        v.resize((size_t)p.nvec[0] * g.V * 24);
+        ok = std::fread(v.data(), sizeof(double), v.size(), f) == v.size();
+    }
+    std::fclose(f);
+    if (!ok) return fail(AMG_EIO, "not a checkpoint of this lattice");
+    const double* vl[1] = {v.data()};
+    return amg_setup_from_vectors(d, &p, vl, out);
+}
+
+amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* out, int nrhs, amg_prec prec,
+                            amg_stream s) {
+    if (!h || !in || !out || nrhs < 1 || level < 1 || level >= h->p.nlevels) return fail(AMG_EINVAL, "bad argument");
+    CoarseLevel& L = h->lev[level];
+    int vprec = prec == AMG_F64 ? 0 : 1;
+    cudaStream_t st = (cudaStream_t)s;
+    if (vprec == L.prec) {
+        CK(launch_coarse_apply(L.prec, L.g, L.nc, nullptr, L.B.p, in, out, nullptr, nrhs, st));
+        return AMG_OK;
+    }
+    size_t n = coarse_n(L) * nrhs;
+    DevBuf a, b;
+    CK(a.ensure(n * coarse_elem_bytes(L.prec)));
+    CK(b.ensure(n * coarse_elem_bytes(L.prec)));
+    CK(launch_convert_flat(vprec, L.prec, in, a.p, n, st));
+    CK(launch_coarse_apply(L.prec, L.g, L.nc, nullptr, L.B.p, a.p, b.p, nullptr, nrhs, st));
+    CK(launch_convert_flat(L.prec, vprec, b.p, out, n, st));
+    CK(cudaStreamSynchronize(st));
+    return AMG_OK;
+}
+
+static amg_status transfer_common(amg_hierarchy* h, int coarsening, int nrhs, amg_prec prec) {
+    if (!h || nrhs < 1) return fail(AMG_EINVAL, "bad argument");
+    if (coarsening != 0) return fail(AMG_EINVAL, "only coarsening 0 in this build");
+    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "bad precision");
+    return AMG_OK;
+}
+
+amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void* coarse, int nrhs, amg_prec prec,
+                        amg_stream s) {
+    TRY(transfer_common(h, coarsening, nrhs, prec));
+    const GeomH& g = fine_geom(h);
+    cudaStream_t st = (cudaStream_t)s;
+    CoarseLevel& L = L1(h);
+    int cprec = prec == AMG_F64 ? 0 : 1;
+    size_t fb = fine_spinor_bytes(prec, g.V);
+    DevBuf tmp;
+    CK(tmp.ensure(fb));
+    for (int r = 0; r < nrhs; ++r) {
+        const char* src = (const char*)fine + (size_t)r * g.V * 24 * (prec == AMG_F64 ? 8 : 4);
+        char* dst = (char*)coarse + (size_t)r * coarse_n(L) * coarse_elem_bytes(cprec);
+        CK(launch_pack_spinor(prec, g, src, tmp.p, 1, st));
+        CK(launch_restrict_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, tmp.p, dst, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return AMG_OK;
+}
+
+amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, void* fine, int nrhs, amg_prec prec,
+                       amg_stream s) {
+    TRY(transfer_common(h, coarsening, nrhs, prec));
+    const GeomH& g = fine_geom(h);
+    cudaStream_t st = (cudaStream_t)s;
+    CoarseLevel& L = L1(h);
+    int cprec = prec == AMG_F64 ? 0 : 1;
+    size_t fb = fine_spinor_bytes(prec, g.V);
+    DevBuf tmp;
+    CK(tmp.ensure(fb));
+    for (int r = 0; r < nrhs; ++r) {
+        const char* src = (const char*)coarse + (size_t)r * coarse_n(L) * coarse_elem_bytes(cprec);
+        char* dst = (char*)fine + (size_t)r * g.V * 24 * (prec == AMG_F64 ? 8 : 4);
+        CK(launch_prolong_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, src, tmp.p, st));
+        CK(launch_unpack_spinor(prec, g, tmp.p, dst, 1, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return AMG_OK;
+}
+
+amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_stream s) {
+    if (!h || !b || !x || prec < 0 || prec > 2) return fail(AMG_EINVAL, "bad argument");
+    const GeomH& g = fine_geom(h);
+    cudaStream_t st = (cudaStream_t)s;
+    CK(launch_pack_spinor(prec, g, b, h->fb[prec].p, 1, st));
+    TRY(fine_sap(h, prec, h->fb[prec].p, h->fx[prec].p, true, st));
+    CK(launch_unpack_spinor(prec, g, h->fx[prec].p, x, 1, st));
+    CK(cudaStreamSynchronize(st));
+    return AMG_OK;
+}
+
+amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_stream s) {
+    if (!h || !b || !x) return fail(AMG_EINVAL, "bad argument");
+    const GeomH& g = fine_geom(h);
+    cudaStream_t st = (cudaStream_t)s;
+    CK(launch_pack_spinor(0, g, b, h->ob.p, 1, st));
+    TRY(precondition64(h, h->ob.p, h->ox.p, st));
+    CK(launch_unpack_spinor(0, g, h->ox.p, x, 1, st));
+    CK(cudaStreamSynchronize(st));
+    return AMG_OK;
+}
+
+amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, double tol, int maxit, int use_x0,
+                     amg_solve_info* info, amg_stream s) {
+    if (!h || !b || !x || nrhs < 1 || !(tol > 0) || maxit < 1) return fail(AMG_EINVAL, "bad argument");
+    const GeomH& g = fine_geom(h);
+    cudaStream_t st = (cudaStream_t)s;
+    amg_status worst = AMG_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        auto t0 = std::chrono::steady_clock::now();
+        h->timer.reset();
+        h->timer.on = info != nullptr;
+        h->coarse_cycles = 0;
+        const double* br = b + (size_t)r * g.V * 24;
+        double* xr = x + (size_t)r * g.V * 24;
+        CK(launch_pack_spinor(0, g, br, h->ob.p, 1, st));
+        if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, 1, st));
+        else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V), st));
+        amg_solve_info loc;
+        std::memset(&loc, 0, sizeof(loc));
+        amg_status rs = fgmres(h, h->ob.p, h->ox.p, tol, maxit, &loc, st);
+        if (rs != AMG_OK && rs != AMG_NOT_CONVERGED) return rs;
+        CK(launch_unpack_spinor(0, g, h->ox.p, xr, 1, st));
+        CK(cudaStreamSynchronize(st));
+        if (rs == AMG_NOT_CONVERGED) worst = rs;
+        if (info) {
+            double ms[PH_NPH];
+            h->timer.collect(ms);
+            auto t1 = std::chrono::steady_clock::now();
+            loc.ms_total = std::chrono::duration<double, std::milli>(t1 - t0).count();
+            loc.ms_coarse = ms[PH_COARSE];
+            loc.ms_smoother = ms[PH_SMOOTH];
+            loc.ms_restrict_prolong = ms[PH_RP];
+            loc.ms_other = loc.ms_total - ms[PH_COARSE] - ms[PH_SMOOTH] - ms[PH_RP];
+            loc.coarse_cycles = h->coarse_cycles;
+            *info = loc;
+        }
+        h->timer.on = false;
+    }
+    if (worst != AMG_OK) fail(worst, "solve did not reach the tolerance");
+    return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// BLAS-1 on flat complex arrays (double2 or float2) for the Krylov solvers.
+// Reductions accumulate in FP64 and write one partial per CTA; the grid size
+// is fixed (blas_grid()) so the final fixed-order sum is deterministic.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int kMaxDots = 20;
+constexpr int kBT = 256;
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+template <typename V> struct VT;
+template <> struct VT<double2> { using T = double; };
+template <> struct VT<float2> { using T = float; };
+
+struct PtrList {
+    const void* p[kMaxDots];
+};
+
+template <typename V>
+__global__ void multi_dot_kernel(int k, PtrList a, const V* __restrict__ b, size_t n, double2* partials) {
+    __shared__ double red[2 * kMaxDots * 32];
+    double acc[2 * kMaxDots];
+#pragma unroll
+    for (int j = 0; j < 2 * kMaxDots; ++j) acc[j] = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        V y = b[i];
+#pragma unroll
+        for (int j = 0; j < kMaxDots; ++j) {
+            if (j < k) {
+                V x = ((const V*)a.p[j])[i];
+                acc[2 * j] += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
+                acc[2 * j + 1] += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < 2 * k; ++j) {
+        double v = warp_sum(acc[j]);
+        if (lane == 0) red[j * 32 + warp] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double re = 0, im = 0;
+        for (int w = 0; w < nw; ++w) {
+            re += red[(2 * j) * 32 + w];
+            im += red[(2 * j + 1) * 32 + w];
+        }
+        partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(re, im);
+    }
+}
+
+template <typename V>
+__global__ void norm2_kernel(const V* __restrict__ a, size_t n, double* partials) {
+    __shared__ double red[32];
+    double acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        V x = a[i];
+        acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    }
+    acc = warp_sum(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+template <typename V>
+__global__ void axpby_kernel(double2 al, const V* __restrict__ x, double2 be, V* y, size_t n) {
+    using T = typename VT<V>::T;
+    const T ar = (T)al.x, ai = (T)al.y, br = (T)be.x, bi = (T)be.y;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        V a = x[i], b = y[i];
+        V o;
+        o.x = ar * a.x - ai * a.y + br * b.x - bi * b.y;
+        o.y = ar * a.y + ai * a.x + br * b.y + bi * b.x;
+        y[i] = o;
+    }
+}
+
+struct CoefList {
+    double2 c[kMaxDots];
+};
+
+template <typename V>
+__global__ void multi_axpy_kernel(int k, CoefList c, PtrList x, V* y, size_t n) {
+    using T = typename VT<V>::T;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        V o = y[i];
+        T re = o.x, im = o.y;
+        for (int j = 0; j < k; ++j) {
+            V a = ((const V*)x.p[j])[i];
+            T cr = (T)c.c[j].x, ci = (T)c.c[j].y;
+            re += cr * a.x - ci * a.y;
+            im += cr * a.y + ci * a.x;
+        }
+        o.x = re;
+        o.y = im;
+        y[i] = o;
+    }
+}
+
+}  // namespace
+
+int blas_grid() { return 2 * sm_count(); }
+
+cudaError_t launch_multi_dot(int prec, int k, const void* const* a, const void* b, size_t n, double2* partials,
+                             cudaStream_t st) {
+    if (k > kMaxDots) return cudaErrorInvalidValue;
+    PtrList pl;
+    for (int j = 0; j < k; ++j) pl.p[j] = a[j];
+    if (prec == 0) multi_dot_kernel<double2><<<blas_grid(), kBT, 0, st>>>(k, pl, (const double2*)b, n, partials);
+    else multi_dot_kernel<float2><<<blas_grid(), kBT, 0, st>>>(k, pl, (const float2*)b, n, partials);
+    return cudaGetLastError();
+}
+cudaError_t launch_norm2(int prec, const void* a, size_t n, double* partials, cudaStream_t st) {
+    if (prec == 0) norm2_kernel<double2><<<blas_grid(), kBT, 0, st>>>((const double2*)a, n, partials);
+    else norm2_kernel<float2><<<blas_grid(), kBT, 0, st>>>((const float2*)a, n, partials);
+    return cudaGetLastError();
+}
+cudaError_t launch_axpby(int prec, double2 al, const void* x, double2 be, void* y, size_t n, cudaStream_t st) {
+    if (prec == 0) axpby_kernel<double2><<<blas_grid(), kBT, 0, st>>>(al, (const double2*)x, be, (double2*)y, n);
+    else axpby_kernel<float2><<<blas_grid(), kBT, 0, st>>>(al, (const float2*)x, be, (float2*)y, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
+                              cudaStream_t st) {
+    if (k > kMaxDots) return cudaErrorInvalidValue;
+    CoefList cl;
+    PtrList pl;
+    for (int j = 0; j < k; ++j) {
+        cl.c[j] = c[j];
+        pl.p[j] = x[j];
+    }
+    if (prec == 0) multi_axpy_kernel<double2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (double2*)y, n);
+    else multi_axpy_kernel<float2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (float2*)y, n);
+    return cudaGetLastError();
+}

@@ -1,0 +1,645 @@
+// Fine-lattice kernels: layout conversion, clover construction, the
+// Wilson-clover stencil of Eq. 1 (full and domain-decomposed D_SAP) and the
+// fused SAP half sweep (Sec. 3, SAP listing with minimal-residual domain
+// solves).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+Geom make_geom(const GeomH& h) {
+    Geom g;
+    for (int i = 0; i < 4; ++i) g.L[i] = h.L[i];
+    g.stride[0] = 1;
+    g.stride[1] = h.L[0];
+    g.stride[2] = h.L[0] * h.L[1];
+    g.stride[3] = h.L[0] * h.L[1] * h.L[2];
+    g.V = h.V;
+    g.antiperiodic = h.antiperiodic;
+    return g;
+}
+Blocking make_blocking(const GeomH& g, const BlockH& b) {
+    Blocking k;
+    k.Vb = 1;
+    k.Vc = 1;
+    for (int i = 0; i < 4; ++i) {
+        k.b[i] = b.b[i];
+        k.C[i] = g.L[i] / b.b[i];
+        k.Vb *= k.b[i];
+        k.Vc *= k.C[i];
+    }
+    return k;
+}
+
+int grid_for(int n, int threads) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int g = (n + threads - 1) / threads;
+    int cap = sms * 16;
+    return g < cap ? (g > 0 ? g : 1) : cap;
+}
+
+// ------------------------------------------------------------ pack / unpack
+template <class P, typename E>
+__global__ void pack_kernel(Geom g, const E* __restrict__ canon, void* internal, int nrhs) {
+    using T = typename P::T;
+    const int r = blockIdx.y;
+    const E* src = canon + (size_t)r * g.V * 24;
+    char* dst = (char*)internal + (size_t)r * spinor_bytes<P>(g.V);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        cx<T> v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = {T(src[(size_t)s * 24 + 2 * k]), T(src[(size_t)s * 24 + 2 * k + 1])};
+        SpinorIO<P>::store(dst, g.V, s, v);
+    }
+}
+template <class P, typename E>
+__global__ void unpack_kernel(Geom g, const void* internal, E* __restrict__ canon, int nrhs) {
+    using T = typename P::T;
+    const int r = blockIdx.y;
+    E* dst = canon + (size_t)r * g.V * 24;
+    const char* src = (const char*)internal + (size_t)r * spinor_bytes<P>(g.V);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        cx<T> v[12];
+        SpinorIO<P>::load(src, g.V, s, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            dst[(size_t)s * 24 + 2 * k] = E(v[k].re);
+            dst[(size_t)s * 24 + 2 * k + 1] = E(v[k].im);
+        }
+    }
+}
+template <class Pi, class Po>
+__global__ void convert_kernel(Geom g, const void* in, void* out) {
+    const int r = blockIdx.y;
+    const char* src = (const char*)in + (size_t)r * spinor_bytes<Pi>(g.V);
+    char* dst = (char*)out + (size_t)r * spinor_bytes<Po>(g.V);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        cx<typename Pi::T> v[12];
+        cx<typename Po::T> w[12];
+        SpinorIO<Pi>::load(src, g.V, s, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = ccast<typename Po::T>(v[k]);
+        SpinorIO<Po>::store(dst, g.V, s, w);
+    }
+}
+
+// ------------------------------------------------------------ gauge
+__global__ void gauge_convert_kernel(Geom g, const double* __restrict__ canon, void* out, int prec) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        for (int mu = 0; mu < 4; ++mu) {
+            const double* m = canon + ((size_t)s * 4 + mu) * 18;
+            if (prec == 0) {
+                double2* p = (double2*)out + (size_t)mu * 9 * g.V;
+                for (int k = 0; k < 9; ++k) p[(size_t)k * g.V + s] = make_double2(m[2 * k], m[2 * k + 1]);
+            } else if (prec == 1) {
+                float4* p = (float4*)out + (size_t)mu * 3 * g.V;
+                for (int q = 0; q < 3; ++q)
+                    p[(size_t)q * g.V + s] = make_float4((float)m[4 * q], (float)m[4 * q + 1], (float)m[4 * q + 2],
+                                                         (float)m[4 * q + 3]);
+            } else {
+                uint2* p = (uint2*)out + (size_t)mu * 3 * g.V;
+                for (int q = 0; q < 3; ++q) {
+                    uint2 t;
+                    __half2* h = reinterpret_cast<__half2*>(&t);
+                    h[0] = __floats2half2_rn((float)m[4 * q], (float)m[4 * q + 1]);
+                    h[1] = __floats2half2_rn((float)m[4 * q + 2], (float)m[4 * q + 3]);
+                    p[(size_t)q * g.V + s] = t;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ clover
+// sigma_munu restricted to the two chirality blocks: [plane][chirality][2][2]
+__constant__ double2 c_sigma[6][2][2][2];
+
+typedef cx<double> M3[3][3];
+
+DEV void m3_mul(const M3 a, const M3 b, M3 c) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cx<double> t = czero<double>();
+            for (int k = 0; k < 3; ++k) t = t + a[i][k] * b[k][j];
+            c[i][j] = t;
+        }
+}
+DEV void m3_dag(const M3 a, M3 c) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) c[i][j] = conj(a[j][i]);
+}
+DEV int shifted(const Geom& g, const int c[4], int mu, int d, int nu, int e) {
+    int cc[4] = {c[0], c[1], c[2], c[3]};
+    cc[mu] = (cc[mu] + d + g.L[mu]) % g.L[mu];
+    cc[nu] = (cc[nu] + e + g.L[nu]) % g.L[nu];
+    return cc[0] + g.stride[1] * cc[1] + g.stride[2] * cc[2] + g.stride[3] * cc[3];
+}
+// product of four links a b c d (with optional daggers)
+DEV void path4(const M3 a, const M3 b, const M3 c, const M3 d, M3 out) {
+    M3 t1, t2;
+    m3_mul(a, b, t1);
+    m3_mul(t1, c, t2);
+    m3_mul(t2, d, out);
+}
+
+template <class P>
+__global__ void clover_build_kernel(Geom g, const void* U64, double kappa, double csw, void* out) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        int c[4];
+        site_coords(g, s, c);
+        cx<double> A[2][6][6];
+        for (int b = 0; b < 2; ++b)
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) A[b][i][j] = czero<double>();
+        int plane = 0;
+        for (int mu = 0; mu < 4; ++mu) {
+            for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+                M3 Q, L, u1, u2, u3, u4, d3, d4;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) Q[i][j] = czero<double>();
+                // leaf x -> x+mu -> x+mu+nu -> x+nu -> x
+                GaugeIO<P64>::load(U64, g.V, mu, s, u1);
+                GaugeIO<P64>::load(U64, g.V, nu, shifted(g, c, mu, 1, nu, 0), u2);
+                GaugeIO<P64>::load(U64, g.V, mu, shifted(g, c, mu, 0, nu, 1), u3);
+                GaugeIO<P64>::load(U64, g.V, nu, s, u4);
+                m3_dag(u3, d3);
+                m3_dag(u4, d4);
+                path4(u1, u2, d3, d4, L);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) Q[i][j] = Q[i][j] + L[i][j];
+                // leaf x -> x+nu -> x+nu-mu -> x-mu -> x
+                GaugeIO<P64>::load(U64, g.V, nu, s, u1);
+                GaugeIO<P64>::load(U64, g.V, mu, shifted(g, c, mu, -1, nu, 1), u2);
+                GaugeIO<P64>::load(U64, g.V, nu, shifted(g, c, mu, -1, nu, 0), u3);
+                GaugeIO<P64>::load(U64, g.V, mu, shifted(g, c, mu, -1, nu, 0), u4);
+                m3_dag(u2, d3);
+                m3_dag(u3, d4);
+                path4(u1, d3, d4, u4, L);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) Q[i][j] = Q[i][j] + L[i][j];
+                // leaf x -> x-mu -> x-mu-nu -> x-nu -> x
+                GaugeIO<P64>::load(U64, g.V, mu, shifted(g, c, mu, -1, nu, 0), u1);
+                GaugeIO<P64>::load(U64, g.V, nu, shifted(g, c, mu, -1, nu, -1), u2);
+                GaugeIO<P64>::load(U64, g.V, mu, shifted(g, c, mu, -1, nu, -1), u3);
+                GaugeIO<P64>::load(U64, g.V, nu, shifted(g, c, mu, 0, nu, -1), u4);
+                m3_dag(u1, d3);
+                m3_dag(u2, d4);
+                path4(d3, d4, u3, u4, L);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) Q[i][j] = Q[i][j] + L[i][j];
+                // leaf x -> x-nu -> x-nu+mu -> x+mu -> x
+                GaugeIO<P64>::load(U64, g.V, nu, shifted(g, c, mu, 0, nu, -1), u1);
+                GaugeIO<P64>::load(U64, g.V, mu, shifted(g, c, mu, 0, nu, -1), u2);
+                GaugeIO<P64>::load(U64, g.V, nu, shifted(g, c, mu, 1, nu, -1), u3);
+                GaugeIO<P64>::load(U64, g.V, mu, s, u4);
+                m3_dag(u1, d3);
+                m3_dag(u4, d4);
+                path4(d3, u2, u3, d4, L);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) Q[i][j] = Q[i][j] + L[i][j];
+                // F = (Q - Q^dag) / (8i), traceless
+                M3 F;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) {
+                        cx<double> d = Q[i][j] - conj(Q[j][i]);
+                        F[i][j] = {d.im / 8.0, -d.re / 8.0};   // d / (8i) = -i d / 8
+                    }
+                cx<double> tr = (1.0 / 3.0) * (F[0][0] + F[1][1] + F[2][2]);
+                for (int i = 0; i < 3; ++i) F[i][i] = F[i][i] - tr;
+                for (int b = 0; b < 2; ++b)
+                    for (int al = 0; al < 2; ++al)
+                        for (int be = 0; be < 2; ++be) {
+                            double2 sg = c_sigma[plane][b][al][be];
+                            cx<double> sgm = {-kappa * csw * sg.x, -kappa * csw * sg.y};
+                            for (int a = 0; a < 3; ++a)
+                                for (int bb = 0; bb < 3; ++bb)
+                                    A[b][al * 3 + a][be * 3 + bb] = A[b][al * 3 + a][be * 3 + bb] + sgm * F[a][bb];
+                        }
+            }
+        }
+        // pack: 18 real pairs per block
+        double pr[2][36];
+        for (int b = 0; b < 2; ++b) {
+            for (int i = 0; i < 6; ++i) pr[b][i] = 1.0 + A[b][i][i].re;
+            for (int i = 1; i < 6; ++i)
+                for (int j = 0; j < i; ++j) {
+                    int q = 3 + i * (i - 1) / 2 + j;
+                    pr[b][2 * q] = A[b][i][j].re;
+                    pr[b][2 * q + 1] = A[b][i][j].im;
+                }
+        }
+        if (P::id == 0) {
+            double2* p = (double2*)out;
+            for (int b = 0; b < 2; ++b)
+                for (int q = 0; q < 18; ++q) p[(size_t)(18 * b + q) * g.V + s] = make_double2(pr[b][2 * q], pr[b][2 * q + 1]);
+        } else if (P::id == 1) {
+            float4* p = (float4*)out;
+            for (int b = 0; b < 2; ++b)
+                for (int q = 0; q < 9; ++q)
+                    p[(size_t)(9 * b + q) * g.V + s] = make_float4((float)pr[b][4 * q], (float)pr[b][4 * q + 1],
+                                                                   (float)pr[b][4 * q + 2], (float)pr[b][4 * q + 3]);
+        } else {
+            uint4* p = (uint4*)out;
+            for (int q = 0; q < 9; ++q) {
+                uint4 t;
+                __half2* h = reinterpret_cast<__half2*>(&t);
+                for (int w = 0; w < 4; ++w) {
+                    int hidx = 8 * q + 2 * w;   // halves hidx, hidx+1 of the 72
+                    h[w] = __floats2half2_rn((float)pr[hidx / 36][hidx % 36], (float)pr[(hidx + 1) / 36][(hidx + 1) % 36]);
+                }
+                p[(size_t)q * g.V + s] = t;
+            }
+        }
+    }
+}
+
+__global__ void clover_expand_kernel(Geom g, const void* C64, double* out) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        for (int b = 0; b < 2; ++b) {
+            double pr[36];
+            CloverIO<P64>::load_block(C64, g.V, s, b, pr);
+            double* o = out + ((size_t)s * 2 + b) * 72;
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    double re, im;
+                    if (i == j) {
+                        re = pr[i];
+                        im = 0;
+                    } else if (i > j) {
+                        int q = 3 + i * (i - 1) / 2 + j;
+                        re = pr[2 * q];
+                        im = pr[2 * q + 1];
+                    } else {
+                        int q = 3 + j * (j - 1) / 2 + i;
+                        re = pr[2 * q];
+                        im = -pr[2 * q + 1];
+                    }
+                    o[(i * 6 + j) * 2] = re;
+                    o[(i * 6 + j) * 2 + 1] = im;
+                }
+        }
+    }
+}
+
+// ------------------------------------------------------------ Wilson-clover stencil
+template <class P, bool SAP, bool RESID>
+__global__ void __launch_bounds__(kThreads) dirac_kernel(Geom g, Blocking bk, const void* __restrict__ U,
+                                                         const void* __restrict__ C, const void* in, void* out,
+                                                         const void* b, typename P::T kappa) {
+    using T = typename P::T;
+    const int r = blockIdx.y;
+    const size_t fb = spinor_bytes<P>(g.V);
+    const char* src = (const char*)in + r * fb;
+    char* dst = (char*)out + r * fb;
+    const char* bsrc = RESID ? (const char*)b + r * fb : nullptr;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        int c[4];
+        site_coords(g, s, c);
+        cx<T> psi[12], acc[12];
+        SpinorIO<P>::load(src, g.V, s, psi);
+        clover_apply<P>(C, g.V, s, psi, acc);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            float ph;
+            cx<T> u[3][3];
+            if (!SAP || (c[mu] % bk.b[mu]) != bk.b[mu] - 1) {
+                int n = neighbour(g, s, c, mu, +1, ph);
+                SpinorIO<P>::load(src, g.V, n, psi);
+                GaugeIO<P>::load(U, g.V, mu, s, u);
+                hop_accum<T>(acc, psi, u, mu, +1, -kappa * T(ph));
+            }
+            if (!SAP || (c[mu] % bk.b[mu]) != 0) {
+                int n = neighbour(g, s, c, mu, -1, ph);
+                SpinorIO<P>::load(src, g.V, n, psi);
+                GaugeIO<P>::load(U, g.V, mu, n, u);
+                hop_accum<T>(acc, psi, u, mu, -1, -kappa * T(ph));
+            }
+        }
+        if (RESID) {
+            SpinorIO<P>::load(bsrc, g.V, s, psi);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = psi[k] - acc[k];
+        }
+        SpinorIO<P>::store(dst, g.V, s, acc);
+    }
+}
+
+// ------------------------------------------------------------ SAP half sweep
+// One CTA per domain of the given colour, one thread per site of the domain.
+// Computes r = b - D x on the domain (the residual of the SAP listing, needed
+// only where the next inner solve reads it), runs nmr minimal-residual steps
+// on D_SAP restricted to the domain with r kept in shared memory, and adds the
+// result to x.  Domains of one colour never touch each other (even number of
+// domains per direction), so the CTAs are independent.
+// x_mode: 0 = x holds the current iterate everywhere; 1 = x is zero everywhere
+// (r = b, x is only written); 2 = x is zero on the active domains and holds the
+// iterate elsewhere (first odd half sweep after an even sweep from zero).
+template <class P, int MAXT>
+__global__ void __launch_bounds__(MAXT) sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode,
+                                                        const void* __restrict__ U, const void* __restrict__ C,
+                                                        const void* __restrict__ b, void* x, typename P::T kappa) {
+    using T = typename P::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int vbp = blockDim.x;
+    cx<T>* rsh = reinterpret_cast<cx<T>*>(smem_raw);          // [12][vbp]
+    T* red = reinterpret_cast<T*>(rsh + 12 * vbp);             // [3][32]
+
+    // domain of this CTA: the k-th domain of the given colour
+    const int k = blockIdx.x;
+    const int h0 = bk.C[0] / 2;
+    int rest = k / h0;
+    int X1 = rest % bk.C[1];
+    rest /= bk.C[1];
+    int X2 = rest % bk.C[2];
+    int X3 = rest / bk.C[2];
+    int X0 = 2 * (k % h0) + ((X1 + X2 + X3 + colour) & 1);
+    const int Xi = X0 + bk.C[0] * (X1 + bk.C[1] * (X2 + bk.C[2] * X3));
+
+    const int l = threadIdx.x;
+    const bool active = l < bk.Vb;
+    int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
+    const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
+    cx<T> r[12], z[12], Ar[12];
+    if (active) {
+        s = block_site(g, bk, Xi, l, c);
+        for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
+        SpinorIO<P>::load(b, g.V, s, r);
+        if (x_mode != 1) {
+            // r = b - D x at this site; with x_mode 2 only hops from outside the domain contribute
+            cx<T> psi[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) Ar[q] = czero<T>();
+            if (x_mode == 0) {
+                SpinorIO<P>::load(x, g.V, s, psi);
+                clover_apply<P>(C, g.V, s, psi, Ar);
+            }
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                float ph;
+                cx<T> u[3][3];
+                if (x_mode == 0 || lc[mu] == bk.b[mu] - 1) {
+                    int n = neighbour(g, s, c, mu, +1, ph);
+                    SpinorIO<P>::load(x, g.V, n, psi);
+                    GaugeIO<P>::load(U, g.V, mu, s, u);
+                    hop_accum<T>(Ar, psi, u, mu, +1, -kappa * T(ph));
+                }
+                if (x_mode == 0 || lc[mu] == 0) {
+                    int n = neighbour(g, s, c, mu, -1, ph);
+                    SpinorIO<P>::load(x, g.V, n, psi);
+                    GaugeIO<P>::load(U, g.V, mu, n, u);
+                    hop_accum<T>(Ar, psi, u, mu, -1, -kappa * T(ph));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) r[q] = r[q] - Ar[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            z[q] = czero<T>();
+            rsh[q * vbp + l] = r[q];
+        }
+    }
+    for (int it = 0; it < nmr; ++it) {
+        __syncthreads();
+        T part[3] = {T(0), T(0), T(0)};
+        if (active) {
+            clover_apply<P>(C, g.V, s, r, Ar);
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                cx<T> u[3][3], psi[12];
+                if (lc[mu] != bk.b[mu] - 1) {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l + lstr[mu]];
+                    GaugeIO<P>::load(U, g.V, mu, s, u);
+                    hop_accum<T>(Ar, psi, u, mu, +1, -kappa);
+                }
+                if (lc[mu] != 0) {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l - lstr[mu]];
+                    GaugeIO<P>::load(U, g.V, mu, s - g.stride[mu], u);
+                    hop_accum<T>(Ar, psi, u, mu, -1, -kappa);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                cx<T> t = cmulc(Ar[q], r[q]);
+                part[0] += t.re;
+                part[1] += t.im;
+                part[2] += norm2(Ar[q]);
+            }
+        }
+        block_sum<T, 3>(part, red);
+        cx<T> alpha = czero<T>();
+        if (part[2] > T(0)) alpha = {part[0] / part[2], part[1] / part[2]};
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                z[q] = z[q] + alpha * r[q];
+                r[q] = r[q] - alpha * Ar[q];
+                rsh[q * vbp + l] = r[q];
+            }
+        }
+    }
+    if (active) {
+        if (x_mode == 0) {
+            cx<T> x0[12];
+            SpinorIO<P>::load(x, g.V, s, x0);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) z[q] = z[q] + x0[q];
+        }
+        SpinorIO<P>::store(x, g.V, s, z);
+    }
+}
+
+template <class P>
+cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
+                          const void* C, const void* b, void* x, double kappa, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk = make_blocking(gh, bh);
+    int threads = (bk.Vb + 31) / 32 * 32;
+    if (threads > 512) return cudaErrorInvalidValue;
+    size_t smem = (size_t)12 * threads * sizeof(cx<typename P::T>) + 3 * 32 * sizeof(typename P::T);
+    int ndom = bk.Vc / 2;
+    if (threads <= 256) {
+        cudaError_t e =
+            cudaFuncSetAttribute(sap_half_kernel<P, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sap_half_kernel<P, 256><<<ndom, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                             (typename P::T)kappa);
+    } else {
+        cudaError_t e =
+            cudaFuncSetAttribute(sap_half_kernel<P, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sap_half_kernel<P, 512><<<ndom, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                             (typename P::T)kappa);
+    }
+    return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t dirac_impl(const GeomH& gh, const BlockH* sb, const void* U, const void* C, const void* in, void* out,
+                       const void* b, double kappa, int nrhs, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk;
+    BlockH one = {{1, 1, 1, 1}};
+    bk = make_blocking(gh, sb ? *sb : one);
+    dim3 grid(grid_for(g.V, kThreads), nrhs);
+    using T = typename P::T;
+    if (sb) {
+        if (b) dirac_kernel<P, true, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
+        else dirac_kernel<P, true, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
+    } else {
+        if (b) dirac_kernel<P, false, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
+        else dirac_kernel<P, false, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
+    }
+    return cudaGetLastError();
+}
+
+// sigma_munu = [gamma_mu, gamma_nu] / (2i) in the chiral basis, chirality blocks.
+// gamma_mu = [[0, e_mu], [e_mu^dag, 0]] so gamma_mu gamma_nu = diag(e_mu e_nu^dag, e_mu^dag e_nu).
+struct C2 {
+    double re, im;
+};
+static C2 cm(C2 a, C2 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+static void e_matrix(int mu, C2 e[2][2], bool dag) {
+    C2 z = {0, 0}, one = {1, 0}, I = {0, 1}, mI = {0, -1}, mone = {-1, 0};
+    C2 m[2][2];
+    switch (mu) {
+        case 0: m[0][0] = z; m[0][1] = I; m[1][0] = I; m[1][1] = z; break;
+        case 1: m[0][0] = z; m[0][1] = one; m[1][0] = mone; m[1][1] = z; break;
+        case 2: m[0][0] = I; m[0][1] = z; m[1][0] = z; m[1][1] = mI; break;
+        default: m[0][0] = one; m[0][1] = z; m[1][0] = z; m[1][1] = one; break;
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) e[i][j] = dag ? C2{m[j][i].re, -m[j][i].im} : m[i][j];
+}
+static void mm2(C2 a[2][2], C2 b[2][2], C2 c[2][2]) {
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            C2 t1 = cm(a[i][0], b[0][j]), t2 = cm(a[i][1], b[1][j]);
+            c[i][j] = {t1.re + t2.re, t1.im + t2.im};
+        }
+}
+static bool sigma_uploaded = false;
+static cudaError_t upload_sigma() {
+    if (sigma_uploaded) return cudaSuccess;
+    double2 h[6][2][2][2];
+    int plane = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+            C2 em[2][2], emd[2][2], en[2][2], endg[2][2];
+            e_matrix(mu, em, false);
+            e_matrix(mu, emd, true);
+            e_matrix(nu, en, false);
+            e_matrix(nu, endg, true);
+            C2 p[2][2][2], q[2][2][2];
+            mm2(em, endg, p[0]);   // upper block of gamma_mu gamma_nu
+            mm2(emd, en, p[1]);    // lower block
+            mm2(en, emd, q[0]);
+            mm2(endg, em, q[1]);
+            for (int b = 0; b < 2; ++b)
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) {
+                        C2 d = {p[b][i][j].re - q[b][i][j].re, p[b][i][j].im - q[b][i][j].im};
+                        // d / (2i) = -i d / 2
+                        h[plane][b][i][j] = make_double2(d.im / 2.0, -d.re / 2.0);
+                    }
+        }
+    cudaError_t e = cudaMemcpyToSymbol(c_sigma, h, sizeof(h));
+    if (e == cudaSuccess) sigma_uploaded = true;
+    return e;
+}
+
+}  // namespace
+
+// ============================================================ launchers
+size_t fine_spinor_bytes(int prec, int V) {
+    return prec == 0 ? spinor_bytes<P64>(V) : prec == 1 ? spinor_bytes<P32>(V) : spinor_bytes<P16>(V);
+}
+size_t fine_gauge_bytes(int prec, int V) {
+    size_t per = prec == 0 ? GaugeIO<P64>::bytes_per_link : prec == 1 ? GaugeIO<P32>::bytes_per_link
+                                                                       : GaugeIO<P16>::bytes_per_link;
+    return 4 * per * (size_t)V;
+}
+size_t fine_clover_bytes(int prec, int V) {
+    size_t per = prec == 0 ? CloverIO<P64>::bytes_per_site : prec == 1 ? CloverIO<P32>::bytes_per_site
+                                                                        : CloverIO<P16>::bytes_per_site;
+    return per * (size_t)V;
+}
+
+cudaError_t launch_pack_spinor(int prec, const GeomH& gh, const void* canon, void* internal, int nrhs,
+                               cudaStream_t st) {
+    Geom g = make_geom(gh);
+    dim3 grid(grid_for(g.V, kThreads), nrhs);
+    if (prec == 0) pack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, (const double*)canon, internal, nrhs);
+    else if (prec == 1) pack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs);
+    else pack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs);
+    return cudaGetLastError();
+}
+cudaError_t launch_unpack_spinor(int prec, const GeomH& gh, const void* internal, void* canon, int nrhs,
+                                 cudaStream_t st) {
+    Geom g = make_geom(gh);
+    dim3 grid(grid_for(g.V, kThreads), nrhs);
+    if (prec == 0) unpack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, internal, (double*)canon, nrhs);
+    else if (prec == 1) unpack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs);
+    else unpack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs);
+    return cudaGetLastError();
+}
+cudaError_t launch_convert_spinor(int pi, int po, const GeomH& gh, const void* in, void* out, int nrhs,
+                                  cudaStream_t st) {
+    Geom g = make_geom(gh);
+    dim3 grid(grid_for(g.V, kThreads), nrhs);
+#define CONV(A, B) convert_kernel<A, B><<<grid, kThreads, 0, st>>>(g, in, out)
+    if (pi == 0 && po == 1) CONV(P64, P32);
+    else if (pi == 1 && po == 0) CONV(P32, P64);
+    else if (pi == 0 && po == 2) CONV(P64, P16);
+    else if (pi == 2 && po == 0) CONV(P16, P64);
+    else if (pi == 1 && po == 2) CONV(P32, P16);
+    else if (pi == 2 && po == 1) CONV(P16, P32);
+    else if (pi == 0 && po == 0) CONV(P64, P64);
+    else if (pi == 1 && po == 1) CONV(P32, P32);
+    else CONV(P16, P16);
+#undef CONV
+    return cudaGetLastError();
+}
+cudaError_t launch_gauge_convert(int prec, const GeomH& gh, const double* canon, void* internal, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    gauge_convert_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, canon, internal, prec);
+    return cudaGetLastError();
+}
+cudaError_t launch_clover_build(int prec, const GeomH& gh, const void* U64, double kappa, double csw, void* clover,
+                                cudaStream_t st) {
+    cudaError_t e = upload_sigma();
+    if (e != cudaSuccess) return e;
+    Geom g = make_geom(gh);
+    int grid = grid_for(g.V, 128);
+    if (prec == 0) clover_build_kernel<P64><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
+    else if (prec == 1) clover_build_kernel<P32><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
+    else clover_build_kernel<P16><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
+    return cudaGetLastError();
+}
+cudaError_t launch_clover_expand(const GeomH& gh, const void* C64, double* out, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    clover_expand_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, C64, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sb, const void* U, const void* C, const void* in,
+                         void* out, const void* b, double kappa, int nrhs, cudaStream_t st) {
+    if (prec == 0) return dirac_impl<P64>(g, sb, U, C, in, out, b, kappa, nrhs, st);
+    if (prec == 1) return dirac_impl<P32>(g, sb, U, C, in, out, b, kappa, nrhs, st);
+    return dirac_impl<P16>(g, sb, U, C, in, out, b, kappa, nrhs, st);
+}
+cudaError_t launch_sap_half(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode, const void* U,
+                            const void* C, const void* b, void* x, double kappa, cudaStream_t st) {
+    if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+    if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+    return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+}

@@ -1,0 +1,372 @@
+// Transfer between the fine lattice and the first coarse lattice (Sec. 3):
+// restriction x(I) = <I|x> (Eq. 4), prolongation |x'> = sum_I x(I)|I> (Eq. 5),
+// the block orthonormalisation <I|J> = delta_IJ and the Galerkin coarse
+// operator D_c(I, J) = <I|D|J> (Eq. 6).  |X, s, i> is test vector i projected
+// to chirality s (spins 0,1 or 2,3) and restricted to block X; coarse dof
+// index I = s * nvec + i.  One CTA works on one block, one thread per site.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+Geom make_geom(const GeomH& h) {
+    Geom g;
+    for (int i = 0; i < 4; ++i) g.L[i] = h.L[i];
+    g.stride[0] = 1;
+    g.stride[1] = h.L[0];
+    g.stride[2] = h.L[0] * h.L[1];
+    g.stride[3] = h.L[0] * h.L[1] * h.L[2];
+    g.V = h.V;
+    g.antiperiodic = h.antiperiodic;
+    return g;
+}
+Blocking make_blocking(const GeomH& g, const BlockH& b) {
+    Blocking k;
+    k.Vb = 1;
+    k.Vc = 1;
+    for (int i = 0; i < 4; ++i) {
+        k.b[i] = b.b[i];
+        k.C[i] = g.L[i] / b.b[i];
+        k.Vb *= k.b[i];
+        k.Vc *= k.C[i];
+    }
+    return k;
+}
+
+template <typename TC> struct CStore;
+template <> struct CStore<double> {
+    DEV static void st(void* p, size_t i, cx<double> v) { ((double2*)p)[i] = make_double2(v.re, v.im); }
+    DEV static cx<double> ld(const void* p, size_t i) {
+        double2 t = ((const double2*)p)[i];
+        return {t.x, t.y};
+    }
+};
+template <> struct CStore<float> {
+    DEV static void st(void* p, size_t i, cx<float> v) { ((float2*)p)[i] = make_float2(v.re, v.im); }
+    DEV static cx<float> ld(const void* p, size_t i) {
+        float2 t = ((const float2*)p)[i];
+        return {t.x, t.y};
+    }
+};
+
+// ------------------------------------------------------------ restriction
+template <class PF, class PV, typename TC>
+__global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
+                                const void* __restrict__ fine, void* coarse) {
+    using T = typename PF::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);   // [nwarps][2*nvec]
+    const int nc = 2 * nvec;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t vb = spinor_bytes<PV>(g.V);
+    for (int Xi = blockIdx.x; Xi < bk.Vc; Xi += gridDim.x) {
+        const int l = threadIdx.x;
+        const bool active = l < bk.Vb;
+        int c[4], s = 0;
+        cx<T> psi[12];
+        if (active) {
+            s = block_site(g, bk, Xi, l, c);
+            SpinorIO<PF>::load(fine, g.V, s, psi);
+        }
+        for (int i = 0; i < nvec; ++i) {
+            cx<T> d0 = czero<T>(), d1 = czero<T>();
+            if (active) {
+                cx<typename PV::T> v[12];
+                SpinorIO<PV>::load((const char*)vecs + i * vb, g.V, s, v);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    d0 = d0 + cmulc(ccast<T>(v[k]), psi[k]);
+                    d1 = d1 + cmulc(ccast<T>(v[6 + k]), psi[6 + k]);
+                }
+            }
+            d0.re = warp_sum(d0.re);
+            d0.im = warp_sum(d0.im);
+            d1.re = warp_sum(d1.re);
+            d1.im = warp_sum(d1.im);
+            if (lane == 0) {
+                part[warp * nc + i] = d0;
+                part[warp * nc + nvec + i] = d1;
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+            cx<T> t = czero<T>();
+            for (int w = 0; w < nw; ++w) t = t + part[w * nc + j];
+            CStore<TC>::st(coarse, (size_t)Xi * nc + j, ccast<TC>(t));
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ prolongation
+template <class PF, class PV, typename TC>
+__global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
+                               const void* __restrict__ coarse, void* fine) {
+    using T = typename PF::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* xc = reinterpret_cast<cx<T>*>(smem_raw);   // [2*nvec]
+    const int nc = 2 * nvec;
+    const size_t vb = spinor_bytes<PV>(g.V);
+    for (int Xi = blockIdx.x; Xi < bk.Vc; Xi += gridDim.x) {
+        for (int j = threadIdx.x; j < nc; j += blockDim.x)
+            xc[j] = ccast<T>(CStore<TC>::ld(coarse, (size_t)Xi * nc + j));
+        __syncthreads();
+        const int l = threadIdx.x;
+        if (l < bk.Vb) {
+            int c[4];
+            int s = block_site(g, bk, Xi, l, c);
+            cx<T> out[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) out[k] = czero<T>();
+            for (int i = 0; i < nvec; ++i) {
+                cx<typename PV::T> v[12];
+                SpinorIO<PV>::load((const char*)vecs + i * vb, g.V, s, v);
+                cx<T> a0 = xc[i], a1 = xc[nvec + i];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    out[k] = out[k] + a0 * ccast<T>(v[k]);
+                    out[6 + k] = out[6 + k] + a1 * ccast<T>(v[6 + k]);
+                }
+            }
+            SpinorIO<PF>::store(fine, g.V, s, out);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ orthonormalisation
+// Per (block, chirality): Gram-Schmidt over i = 0..nvec-1 in index order,
+// every vector projected against the previous ones twice, in FP64.
+template <class PV>
+__global__ void orthonormalise_kernel(Geom g, Blocking bk, int nvec, void* vecs, int* err) {
+    __shared__ double red[3 * 32];
+    const int Xi = blockIdx.x, chi = blockIdx.y;
+    const int l = threadIdx.x;
+    const bool active = l < bk.Vb;
+    const size_t vb = spinor_bytes<PV>(g.V);
+    int c[4], s = 0;
+    if (active) s = block_site(g, bk, Xi, l, c);
+    for (int i = 0; i < nvec; ++i) {
+        cx<double> w[6];
+        cx<typename PV::T> v[12];
+        if (active) {
+            SpinorIO<PV>::load_rw((const char*)vecs + i * vb, g.V, s, v);
+            for (int k = 0; k < 6; ++k) w[k] = ccast<double>(v[6 * chi + k]);
+        } else {
+            for (int k = 0; k < 6; ++k) w[k] = czero<double>();
+        }
+        double n0[1] = {0};
+        for (int k = 0; k < 6; ++k) n0[0] += norm2(w[k]);
+        block_sum<double, 1>(n0, red);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j = 0; j < i; ++j) {
+                cx<double> q[6];
+                if (active) {
+                    cx<typename PV::T> u[12];
+                    SpinorIO<PV>::load_rw((const char*)vecs + j * vb, g.V, s, u);
+                    for (int k = 0; k < 6; ++k) q[k] = ccast<double>(u[6 * chi + k]);
+                } else {
+                    for (int k = 0; k < 6; ++k) q[k] = czero<double>();
+                }
+                double d[2] = {0, 0};
+                for (int k = 0; k < 6; ++k) {
+                    cx<double> t = cmulc(q[k], w[k]);
+                    d[0] += t.re;
+                    d[1] += t.im;
+                }
+                block_sum<double, 2>(d, red);
+                cx<double> cc = {d[0], d[1]};
+                for (int k = 0; k < 6; ++k) w[k] = w[k] - cc * q[k];
+            }
+        }
+        double nn[1] = {0};
+        for (int k = 0; k < 6; ++k) nn[0] += norm2(w[k]);
+        block_sum<double, 1>(nn, red);
+        // rank test: |w| <= 1e-12 |w0| (FP64 storage), 1e-5 |w0| (FP32 storage)
+        const double rtol2 = PV::id == 0 ? 1e-24 : 1e-10;
+        if (!(nn[0] > rtol2 * n0[0])) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            nn[0] = 1.0;
+        }
+        double inv = 1.0 / sqrt(nn[0]);
+        if (active) {
+            // the other chirality half belongs to the CTA (Xi, 1 - chi): write ours only
+            cx<typename PV::T> hv[6];
+            for (int k = 0; k < 6; ++k) hv[k] = ccast<typename PV::T>(inv * w[k]);
+            SpinorIO<PV>::store_half((char*)vecs + i * vb, g.V, s, chi, hv);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ Galerkin operator
+// CTA (block Xi, column J = (t, j)): for every direction d the field
+// T_d = H_d P_t v_j on the sites of Xi (H_0 = D_SAP on the block, H_{+-mu} =
+// the hops of D leaving Xi through its +-mu face) is formed and projected on
+// all basis vectors of Xi: B[Xi][I][d][J] = <Xi, I| T_d>.
+template <class PV, typename TC>
+__global__ void galerkin_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
+                                const void* __restrict__ U, const void* __restrict__ C, typename PV::T kappa,
+                                void* B) {
+    using T = typename PV::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nc = 2 * nvec;
+    cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);   // [nwarps][nc]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int Xi = blockIdx.x, J = blockIdx.y;
+    const int t = J / nvec, j = J % nvec;
+    const size_t vb = spinor_bytes<PV>(g.V);
+    const char* vj = (const char*)vecs + j * vb;
+    const int l = threadIdx.x;
+    const bool active = l < bk.Vb;
+    int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
+    if (active) {
+        s = block_site(g, bk, Xi, l, c);
+        for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
+    }
+    auto load_proj = [&](int site, cx<T> v[12]) {
+        SpinorIO<PV>::load(vj, g.V, site, v);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[6 * (1 - t) + k] = czero<T>();
+    };
+    for (int d = 0; d < 9; ++d) {
+        cx<T> Tv[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) Tv[k] = czero<T>();
+        if (active) {
+            cx<T> psi[12], u[3][3];
+            float ph;
+            if (d == 0) {
+                load_proj(s, psi);
+                clover_apply<PV>(C, g.V, s, psi, Tv);
+                for (int mu = 0; mu < 4; ++mu) {
+                    if (lc[mu] != bk.b[mu] - 1) {
+                        int n = neighbour(g, s, c, mu, +1, ph);
+                        load_proj(n, psi);
+                        GaugeIO<PV>::load(U, g.V, mu, s, u);
+                        hop_accum<T>(Tv, psi, u, mu, +1, -kappa * T(ph));
+                    }
+                    if (lc[mu] != 0) {
+                        int n = neighbour(g, s, c, mu, -1, ph);
+                        load_proj(n, psi);
+                        GaugeIO<PV>::load(U, g.V, mu, n, u);
+                        hop_accum<T>(Tv, psi, u, mu, -1, -kappa * T(ph));
+                    }
+                }
+            } else {
+                const int mu = (d - 1) % 4;
+                const int dir = d <= 4 ? +1 : -1;
+                const bool face = dir > 0 ? (lc[mu] == bk.b[mu] - 1) : (lc[mu] == 0);
+                if (face) {
+                    int n = neighbour(g, s, c, mu, dir, ph);
+                    load_proj(n, psi);
+                    GaugeIO<PV>::load(U, g.V, mu, dir > 0 ? s : n, u);
+                    hop_accum<T>(Tv, psi, u, mu, dir, -kappa * T(ph));
+                }
+            }
+        }
+        for (int i = 0; i < nvec; ++i) {
+            cx<T> d0 = czero<T>(), d1 = czero<T>();
+            if (active) {
+                cx<T> v[12];
+                SpinorIO<PV>::load((const char*)vecs + i * vb, g.V, s, v);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    d0 = d0 + cmulc(v[k], Tv[k]);
+                    d1 = d1 + cmulc(v[6 + k], Tv[6 + k]);
+                }
+            }
+            d0.re = warp_sum(d0.re);
+            d0.im = warp_sum(d0.im);
+            d1.re = warp_sum(d1.re);
+            d1.im = warp_sum(d1.im);
+            if (lane == 0) {
+                part[warp * nc + i] = d0;
+                part[warp * nc + nvec + i] = d1;
+            }
+        }
+        __syncthreads();
+        for (int row = threadIdx.x; row < nc; row += blockDim.x) {
+            cx<T> acc = czero<T>();
+            for (int w = 0; w < nw; ++w) acc = acc + part[w * nc + row];
+            CStore<TC>::st(B, (((size_t)Xi * nc + row) * 9 + d) * nc + J, ccast<TC>(acc));
+        }
+        __syncthreads();
+    }
+}
+
+int threads_for(const Blocking& bk) { return (bk.Vb + 31) / 32 * 32; }
+
+template <class PF, class PV, typename TC>
+cudaError_t restrict_impl(const GeomH& gh, const BlockH& bh, int nvec, const void* vecs, const void* fine,
+                          void* coarse, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk = make_blocking(gh, bh);
+    int th = threads_for(bk);
+    size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<typename PF::T>);
+    restrict_kernel<PF, PV, TC><<<bk.Vc, th, smem, st>>>(g, bk, nvec, vecs, fine, coarse);
+    return cudaGetLastError();
+}
+template <class PF, class PV, typename TC>
+cudaError_t prolong_impl(const GeomH& gh, const BlockH& bh, int nvec, const void* vecs, const void* coarse,
+                         void* fine, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk = make_blocking(gh, bh);
+    int th = threads_for(bk);
+    size_t smem = (size_t)2 * nvec * sizeof(cx<typename PF::T>);
+    prolong_kernel<PF, PV, TC><<<bk.Vc, th, smem, st>>>(g, bk, nvec, vecs, coarse, fine);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define DISPATCH_F(fprec, ...)                 \
+    if (fprec == 0) { using PF = P64; __VA_ARGS__; } \
+    else if (fprec == 1) { using PF = P32; __VA_ARGS__; } \
+    else { using PF = P16; __VA_ARGS__; }
+
+cudaError_t launch_restrict_fine(int fprec, int vprec, int cprec, const GeomH& g, const BlockH& bk, int nvec,
+                                 const void* vecs, const void* fine, void* coarse, cudaStream_t st) {
+    if (vprec == 0) {
+        if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P64, double>(g, bk, nvec, vecs, fine, coarse, st)); }
+        DISPATCH_F(fprec, return restrict_impl<PF, P64, float>(g, bk, nvec, vecs, fine, coarse, st));
+    }
+    if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P32, double>(g, bk, nvec, vecs, fine, coarse, st)); }
+    DISPATCH_F(fprec, return restrict_impl<PF, P32, float>(g, bk, nvec, vecs, fine, coarse, st));
+}
+cudaError_t launch_prolong_fine(int fprec, int vprec, int cprec, const GeomH& g, const BlockH& bk, int nvec,
+                                const void* vecs, const void* coarse, void* fine, cudaStream_t st) {
+    if (vprec == 0) {
+        if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P64, double>(g, bk, nvec, vecs, coarse, fine, st)); }
+        DISPATCH_F(fprec, return prolong_impl<PF, P64, float>(g, bk, nvec, vecs, coarse, fine, st));
+    }
+    if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P32, double>(g, bk, nvec, vecs, coarse, fine, st)); }
+    DISPATCH_F(fprec, return prolong_impl<PF, P32, float>(g, bk, nvec, vecs, coarse, fine, st));
+}
+cudaError_t launch_orthonormalise_fine(int vprec, const GeomH& gh, const BlockH& bh, int nvec, void* vecs,
+                                       int* err, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk = make_blocking(gh, bh);
+    dim3 grid(bk.Vc, 2);
+    int th = threads_for(bk);
+    if (vprec == 0) orthonormalise_kernel<P64><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err);
+    else orthonormalise_kernel<P32><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err);
+    return cudaGetLastError();
+}
+cudaError_t launch_galerkin_fine(int vprec, int cprec, const GeomH& gh, const BlockH& bh, int nvec, const void* vecs,
+                                 const void* U, const void* C, double kappa, void* B, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk = make_blocking(gh, bh);
+    int th = threads_for(bk);
+    dim3 grid(bk.Vc, 2 * nvec);
+    if (vprec == 0) {
+        size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<double>);
+        if (cprec == 0) galerkin_kernel<P64, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B);
+        else galerkin_kernel<P64, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B);
+    } else {
+        size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<float>);
+        if (cprec == 0) galerkin_kernel<P32, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B);
+        else galerkin_kernel<P32, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B);
+    }
+    return cudaGetLastError();
+}

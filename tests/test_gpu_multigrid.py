@@ -1,0 +1,182 @@
+"""GPU parity of the multigrid pieces (orthonormalisation, Galerkin coarse
+operator, restriction, prolongation, coarse stencil, SAP, the cycle) and of
+whole solves, against the FP64 oracle through the C ABI."""
+import numpy as np
+import pytest
+
+import lqcd_inputs as li
+from oracle import dirac as odirac, multigrid as omg, solvers as osol, amg as oamg
+from gpu_util import Field, to_dev, from_dev, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(c, block, nvec, prec, **kw):
+    p = c.amg_params_default()
+    p.nlevels = 2
+    for mu in range(4):
+        p.block[0][mu] = block[mu]
+    p.nvec[0] = nvec
+    p.prec_smoother = prec
+    p.prec_coarsest = 0 if prec == 0 else 1
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+MG_CASES = [
+    # dims, eps, seed, kappa, block, nvec
+    ((4, 4, 4, 4), 0.3, 1, 0.124, (2, 2, 2, 2), 8),
+    ((12, 12, 12, 12), 0.6, 101, 0.130, (3, 3, 3, 3), 6),   # 81-site blocks: padded CTA
+    ((8, 4, 4, 8), 0.6, 5, 0.130, (2, 2, 2, 4), 5),
+]
+
+
+@pytest.fixture(scope="module", params=range(len(MG_CASES)))
+def mgcase(request):
+    dims, eps, seed, kappa, block, nvec = MG_CASES[request.param]
+    f = Field(dims, eps, seed, kappa, 1.0)
+    f.op = odirac.WilsonClover(f.U, kappa, 1.0, True)
+    f.block, f.nvec = block, nvec
+    v0 = li.test_vectors(dims, seed, nvec)
+    f.v0 = v0
+    f.vo = omg.orthonormalise(v0.reshape((nvec,) + f.shape4 + (12,)), block)
+    f.B = omg.coarse_operator(f.op, f.vo, block)
+    yield f
+    f.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vectors_and_galerkin(mgcase, prec):
+    f = mgcase
+    c = f.c
+    h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, prec), [li.to_interleaved(f.v0)])
+    got = c.amg_get_vectors(h, 0, f.nvec, f.V)
+    got = (got[..., 0] + 1j * got[..., 1]).reshape(f.vo.shape)
+    tol = 1e-12 if prec == 0 else 2e-6
+    assert rel(got, f.vo) < tol
+    B = c.amg_get_coarse_op(h, 1)
+    B = B[..., 0] + 1j * B[..., 1]
+    ref = f.B.B.reshape(B.shape)
+    assert rel(B, ref) < (1e-12 if prec == 0 else 2e-6)
+    c.amg_hierarchy_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_restrict_prolong_coarse_apply(mgcase, prec):
+    f = mgcase
+    c = f.c
+    import torch
+    h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, prec), [li.to_interleaved(f.v0)])
+    dims_c, nc = c.amg_level_info(h, 1)
+    cshape = li.lattice_shape(dims_c)
+    psi = li.rhs(f.dims, 9).reshape(f.shape4 + (12,))
+    dt = "float64" if prec == 0 else "float32"
+    tol = 1e-12 if prec == 0 else 2e-6
+    # restriction
+    xc = torch.zeros(int(np.prod(cshape)) * nc * 2, dtype=getattr(torch, dt), device="cuda")
+    c.amg_restrict(h, 0, to_dev(psi, dt), xc, 1, prec)
+    ref_c = omg.restrict(f.vo, psi, f.block)
+    assert rel(from_dev(xc, cshape + (nc,)), ref_c) < tol
+    # prolongation of a random coarse vector
+    yc = li.complex_normal(77, li.STREAM_MISC, cshape + (nc,))
+    fine = torch.zeros(f.V * 24, dtype=getattr(torch, dt), device="cuda")
+    c.amg_prolong(h, 0, to_dev(yc, dt), fine, 1, prec)
+    assert rel(from_dev(fine, f.shape4 + (12,)), omg.prolong(f.vo, yc, f.block)) < tol
+    # coarse stencil
+    out = torch.zeros_like(xc)
+    c.amg_apply_coarse(h, 1, to_dev(yc, dt), out, 1, prec)
+    assert rel(from_dev(out, cshape + (nc,)), f.B.apply(yc)) < tol
+    c.amg_hierarchy_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_sap(mgcase, prec):
+    f = mgcase
+    c = f.c
+    h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, prec), [li.to_interleaved(f.v0)])
+    b = li.rhs(f.dims, 11).reshape(f.shape4 + (12,))
+    ref = osol.sap(f.op, f.block, b, 4, 6)
+    dt = "float64" if prec == 0 else "float32"
+    x = to_dev(b, dt)
+    y = x.clone()
+    c.amg_sap(h, x, y, prec)
+    tol = {0: 1e-11, 1: 1e-5, 2: 1e-2}[prec]
+    assert rel(from_dev(y, f.shape4 + (12,)), ref) < tol
+    c.amg_hierarchy_destroy(h)
+
+
+def test_precondition_fp64(mgcase):
+    # one application of the cycle (restrict, BiCGStab(2) to 1e-2, prolong, SAP)
+    f = mgcase
+    c = f.c
+    p = _params(c, f.block, f.nvec, 0)
+    h = c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(f.v0)])
+    hier = oamg.Hierarchy(f.op, oamg.AMGParams(blocks=[f.block], nvecs=[f.nvec]))
+    hier.set_vectors([f.v0.reshape((f.nvec,) + f.shape4 + (12,))])
+    b = li.rhs(f.dims, 12).reshape(f.shape4 + (12,))
+    ref = hier.vcycle(0, b)
+    x = to_dev(b)
+    y = x.clone()
+    c.amg_precondition(h, x, y)
+    assert rel(from_dev(y, f.shape4 + (12,)), ref) < 1e-9
+    c.amg_hierarchy_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solve_reaches_fp64_tolerance(mgcase, prec):
+    f = mgcase
+    c = f.c
+    p = _params(c, f.block, f.nvec, prec, n_init=2, n_adapt=1)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(f.v0)])
+    b = li.rhs(f.dims, 13)
+    x = to_dev(b) * 0
+    st, info = c.amg_solve(h, to_dev(b), x, 1, 1e-10, 300)
+    assert info.converged == 1 and info.true_rel_residual <= 1e-10
+    xs = from_dev(x, f.shape4 + (12,))
+    r = b.reshape(f.shape4 + (12,)) - f.op.apply(xs)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10    # the oracle agrees on the residual
+    c.amg_hierarchy_destroy(h)
+
+
+def test_config1_solution_matches_dense_lu():
+    dims = (4, 4, 4, 4)
+    f = Field(dims, 0.3, 1, 0.124, 1.0)
+    c = f.c
+    p = _params(c, (2, 2, 2, 2), 8, 0)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 1, 8))])
+    b = li.rhs(dims, 1)
+    x = to_dev(b) * 0
+    st, info = c.amg_solve(h, to_dev(b), x, 1, 1e-10, 100)
+    D = odirac.dense_matrix(f.U, 0.124, 1.0)
+    xd = np.linalg.solve(D, b.reshape(-1))
+    assert np.linalg.norm(from_dev(x, (f.V * 12,)) - xd) <= 1e-9 * np.linalg.norm(xd)
+    c.amg_hierarchy_destroy(h)
+    f.close()
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    dims = (4, 4, 4, 4)
+    f = Field(dims, 0.3, 1, 0.124, 1.0)
+    c = f.c
+    p = _params(c, (2, 2, 2, 2), 8, 1, n_init=1, n_adapt=1)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 1, 8))])
+    path = tmp_path / "setup.bin"
+    c.amg_setup_save(h, path)
+    h2 = c.amg_setup_load(f.d, path)
+    B1, B2 = c.amg_get_coarse_op(h, 1), c.amg_get_coarse_op(h2, 1)
+    assert np.abs(B1 - B2).max() <= 1e-5 * np.abs(B1).max()
+    c.amg_hierarchy_destroy(h)
+    c.amg_hierarchy_destroy(h2)
+    f.close()
+
+
+def test_bad_blocking_is_rejected():
+    dims = (4, 4, 4, 4)
+    f = Field(dims, 0.3, 1, 0.124, 1.0)
+    c = f.c
+    p = _params(c, (4, 2, 2, 2), 4, 1)   # one block in x: SAP colouring impossible
+    with pytest.raises(c.AMGError) as e:
+        c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(li.test_vectors(dims, 1, 4))])
+    assert e.value.status == c.AMG_EINVAL
+    f.close()

@@ -1,0 +1,82 @@
+"""GPU parity of the operators against the FP64 oracle, through the C ABI.
+
+Tolerances (relative L2 over the whole output): FP64 1e-12, FP32 1e-6,
+FP16 (half storage with per-site scale) 3e-3.  Lattices include a ragged
+volume (not a multiple of the 256-thread CTA) and non-power-of-two blocks.
+"""
+import numpy as np
+import pytest
+
+import lqcd_inputs as li
+from oracle import dirac as odirac, multigrid as omg, solvers as osol
+from gpu_util import Field, to_dev, from_dev, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-6, 2: 3e-3}
+DT = {0: "float64", 1: "float32", 2: "float32"}
+
+CASES = [
+    ((4, 4, 4, 4), 0.3, 1, 0.124, 1.0, True),
+    ((4, 6, 6, 10), 0.6, 7, 0.130, 1.0, False),     # V = 1440: ragged tail
+    ((8, 8, 8, 8), 0.6, 2, 0.130, 1.0, True),
+]
+
+
+@pytest.fixture(scope="module", params=range(len(CASES)))
+def field(request):
+    f = Field(*CASES[request.param])
+    f.op = odirac.WilsonClover(f.U, f.kappa, f.csw, CASES[request.param][5])
+    yield f
+    f.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_apply_D(field, prec):
+    c = field.c
+    psi = np.stack([li.rhs(field.dims, 3, i) for i in range(2)])
+    ref = np.stack([field.op.apply(p.reshape(field.shape4 + (12,))) for p in psi])
+    x = to_dev(psi, DT[prec])
+    y = x.clone()
+    c.amg_apply_D(field.d, x, y, 2, prec)
+    got = from_dev(y, (2,) + field.shape4 + (12,))
+    assert rel(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_Dsap(field, prec):
+    c = field.c
+    blocks = [(2, 2, 2, 2)]
+    if field.dims == (4, 6, 6, 10):
+        blocks.append((2, 3, 3, 5))
+    psi = li.rhs(field.dims, 4)
+    for blk in blocks:
+        ref = field.op.apply_sap(psi.reshape(field.shape4 + (12,)), blk)
+        x = to_dev(psi, DT[prec])
+        y = x.clone()
+        c.amg_apply_Dsap(field.d, blk, x, y, 1, prec)
+        assert rel(from_dev(y, field.shape4 + (12,)), ref) < TOL[prec]
+
+
+def test_clover(field):
+    got = field.c.amg_dirac_get_clover(field.d, field.V)
+    got = got[..., 0] + 1j * got[..., 1]                      # (V, 2, 6, 6)
+    A = field.op.A.reshape(field.V, 12, 12)
+    ref = np.stack([A[:, :6, :6], A[:, 6:, 6:]], axis=1)
+    assert np.abs(got - ref).max() < 1e-14
+    assert np.abs(A[:, :6, 6:]).max() == 0
+
+
+def test_apply_D_config2_size():
+    # the 16^3 x 32 workload at full size, FP32, every site compared
+    dims = (16, 16, 16, 32)
+    f = Field(dims, 0.6, 2, 0.130, 1.0)
+    op = odirac.WilsonClover(f.U, 0.130, 1.0, True)
+    psi = li.rhs(dims, 2)
+    ref = op.apply(psi.reshape(f.shape4 + (12,)))
+    for prec in (1, 2):
+        x = to_dev(psi, "float32")
+        y = x.clone()
+        f.c.amg_apply_D(f.d, x, y, 1, prec)
+        assert rel(from_dev(y, f.shape4 + (12,)), ref) < TOL[prec]
+    f.close()
