@@ -96,6 +96,7 @@ struct CoarseLevel {
     int nc = 0;
     int prec = 1;
     DevBuf B;
+    DevBuf cs_part, cs_state;   // persistent coarse solver scratch
 };
 
 // pinned partial-sum staging for reductions
@@ -215,7 +216,9 @@ struct amg_hierarchy {
     int err_flag_host = 0;
     DevBuf err_flag;
     int coarse_cycles = 0;
+    int* hstate = nullptr;   // pinned mirror of the coarse solver state words
     ~amg_hierarchy() {
+        if (hstate) cudaFreeHost(hstate);
         for (auto& v : cw)
             for (auto* b : v) delete b;
         for (auto* b : oV) delete b;
@@ -285,89 +288,29 @@ amg_status coarse_apply(amg_hierarchy* h, int l, const void* in, void* out, cons
     return AMG_OK;
 }
 
-// BiCGStab(l) (Sleijpen-Fokkema) on the coarsest level, relative tolerance tol.
+// BiCGStab(l) (Sleijpen-Fokkema) on the coarsest level to relative tolerance
+// coarse_tol: one persistent cooperative launch, no host synchronisation.
 amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
-    const int pr = L.prec, ell = h->p.coarse_ell;
-    const size_t n = coarse_n(L), bytes = n * coarse_elem_bytes(pr);
+    const int ell = h->p.coarse_ell;
     auto& w = h->cw[l];   // [0] bc, [1] xc, [2] rt, [3..3+ell] R, [4+ell..4+2ell] U
-    void* rt = w[2]->p;
-    std::vector<void*> R(ell + 1), U(ell + 1);
+    void* R[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     for (int j = 0; j <= ell; ++j) {
         R[j] = w[3 + j]->p;
         U[j] = w[4 + ell + j]->p;
     }
-    Reducer& red = h->red;
-    CK(cudaMemsetAsync(x, 0, bytes, s));
-    CK(cudaMemcpyAsync(R[0], b, bytes, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(rt, b, bytes, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(U[0], 0, bytes, s));
-    double bn2;
-    TRY(red.norm2(pr, b, n, &bn2, s));
-    if (bn2 == 0) return AMG_OK;
-    const double bnorm = std::sqrt(bn2);
-    cplx rho0 = 1, alpha = 0, omega = 1;
-    for (int cycle = 0; cycle < h->p.coarse_maxit; ++cycle) {
-        double rn2;
-        TRY(red.norm2(pr, R[0], n, &rn2, s));
-        if (!std::isfinite(rn2)) return fail(AMG_NAN, "coarse solve: non-finite residual");
-        if (std::sqrt(rn2) <= h->p.coarse_tol * bnorm) break;
-        h->coarse_cycles++;
-        rho0 = -omega * rho0;
-        for (int j = 0; j < ell; ++j) {
-            cplx rho1;
-            TRY(red.dot(pr, rt, R[j], n, &rho1, s));
-            cplx beta = alpha * rho1 / rho0;
-            rho0 = rho1;
-            for (int i = 0; i <= j; ++i) CK(launch_axpby(pr, make_double2(1, 0), R[i], d2(-beta), U[i], n, s));
-            TRY(coarse_apply(h, l, U[j], U[j + 1], nullptr, s));
-            cplx gam;
-            TRY(red.dot(pr, rt, U[j + 1], n, &gam, s));
-            alpha = rho0 / gam;
-            for (int i = 0; i <= j; ++i) CK(launch_axpby(pr, d2(-alpha), U[i + 1], make_double2(1, 0), R[i], n, s));
-            TRY(coarse_apply(h, l, R[j], R[j + 1], nullptr, s));
-            CK(launch_axpby(pr, d2(alpha), U[0], make_double2(1, 0), x, n, s));
-        }
-        // minimal-residual part: modified Gram-Schmidt on R[1..ell]
-        std::vector<std::vector<cplx>> tau(ell + 1, std::vector<cplx>(ell + 1));
-        std::vector<double> sigma(ell + 1);
-        std::vector<cplx> gp(ell + 1), g(ell + 1), gpp(ell + 1);
-        for (int j = 1; j <= ell; ++j) {
-            for (int i = 1; i < j; ++i) {
-                cplx t;
-                TRY(red.dot(pr, R[i], R[j], n, &t, s));
-                tau[i][j] = t / sigma[i];
-                CK(launch_axpby(pr, d2(-tau[i][j]), R[i], make_double2(1, 0), R[j], n, s));
-            }
-            double sg;
-            TRY(red.norm2(pr, R[j], n, &sg, s));
-            sigma[j] = sg;
-            if (!(sg > 0)) return fail(AMG_NAN, "coarse solve: breakdown");
-            cplx t;
-            TRY(red.dot(pr, R[j], R[0], n, &t, s));
-            gp[j] = t / sg;
-        }
-        g[ell] = gp[ell];
-        omega = g[ell];
-        for (int j = ell - 1; j >= 1; --j) {
-            cplx t = gp[j];
-            for (int i = j + 1; i <= ell; ++i) t -= tau[j][i] * g[i];
-            g[j] = t;
-        }
-        for (int j = 1; j < ell; ++j) {
-            cplx t = g[j + 1];
-            for (int i = j + 1; i < ell; ++i) t += tau[j][i] * g[i + 1];
-            gpp[j] = t;
-        }
-        CK(launch_axpby(pr, d2(g[1]), R[0], make_double2(1, 0), x, n, s));
-        CK(launch_axpby(pr, d2(-gp[ell]), R[ell], make_double2(1, 0), R[0], n, s));
-        CK(launch_axpby(pr, d2(-g[ell]), U[ell], make_double2(1, 0), U[0], n, s));
-        for (int j = 1; j < ell; ++j) {
-            CK(launch_axpby(pr, d2(-g[j]), U[j], make_double2(1, 0), U[0], n, s));
-            CK(launch_axpby(pr, d2(gpp[j]), R[j], make_double2(1, 0), x, n, s));
-            CK(launch_axpby(pr, d2(-gp[j]), R[j], make_double2(1, 0), R[0], n, s));
-        }
-    }
+    CK(cudaMemsetAsync(L.cs_state.p, 0, 12, s));
+    CK(launch_coarse_bicgstab(L.prec, L.g, L.nc, L.B.p, b, x, w[2]->p, R, U, ell, h->p.coarse_tol,
+                              h->p.coarse_maxit, L.cs_part.p, L.cs_state.p, s));
+    CK(cudaMemcpyAsync(h->hstate, L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
+    return AMG_OK;
+}
+
+// status of the last coarse solve; valid after any stream synchronisation
+amg_status coarse_status(amg_hierarchy* h) {
+    if (h->hstate[2] == 1) return fail(AMG_TIMEOUT, "coarse solver: grid barrier timed out");
+    if (h->hstate[2] != 0) return fail(AMG_NAN, "coarse solver: breakdown or non-finite residual");
     return AMG_OK;
 }
 
@@ -402,8 +345,8 @@ amg_status precondition64(amg_hierarchy* h, const void* v, void* z, cudaStream_t
 }
 
 // ---------------------------------------------------------------- outer FGMRES
-amg_status fgmres(amg_hierarchy* h, const void* b, void* x, double tol, int maxit, amg_solve_info* info,
-                  cudaStream_t s) {
+amg_status fgmres(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, double tol, int maxit,
+                  amg_solve_info* info, cudaStream_t s) {
     const int m = h->p.outer_m;
     const size_t n = fine_n(h);
     Reducer& red = h->red;
@@ -420,10 +363,17 @@ amg_status fgmres(amg_hierarchy* h, const void* b, void* x, double tol, int maxi
     std::vector<std::vector<cplx>> H(m + 1, std::vector<cplx>(m));
     std::vector<double> cs(m);
     std::vector<cplx> sn(m), gv(m + 1);
+    bool x_is_zero = !x_nonzero;
     while (!conv) {
-        TRY(fine_D(h, 0, x, h->orr.p, b, s));   // r = b - D x
         double rn2;
-        TRY(red.norm2(0, h->orr.p, n, &rn2, s));
+        if (x_is_zero) {   // r = b: no FP64 stencil needed
+            CK(cudaMemcpyAsync(h->orr.p, b, n * 16, cudaMemcpyDeviceToDevice, s));
+            rn2 = bn2;
+            x_is_zero = false;
+        } else {
+            TRY(fine_D(h, 0, x, h->orr.p, b, s));   // r = b - D x
+            TRY(red.norm2(0, h->orr.p, n, &rn2, s));
+        }
         if (!std::isfinite(rn2)) return fail(AMG_NAN, "outer solve: non-finite residual");
         double rn = std::sqrt(rn2);
         rel = rn / bnorm;
@@ -448,6 +398,7 @@ amg_status fgmres(amg_hierarchy* h, const void* b, void* x, double tol, int maxi
             for (int pass = 0; pass < 2; ++pass) {
                 std::vector<cplx> c(j + 1);
                 TRY(red.dots(0, j + 1, vl.data(), h->ow.p, n, c.data(), s));
+                if (pass == 0) TRY(coarse_status(h));
                 std::vector<double2> nc(j + 1);
                 for (int i = 0; i <= j; ++i) {
                     H[i][j] += c[i];
@@ -526,9 +477,16 @@ amg_status alloc_workspaces(amg_hierarchy* h) {
         CK(h->fx[pr].ensure(fine_spinor_bytes(pr, g.V)));
     }
     CK(h->tmpv.ensure(fine_spinor_bytes(h->vp, g.V)));
+    if (!h->hstate) {
+        CK(cudaMallocHost(&h->hstate, 16));
+        std::memset(h->hstate, 0, 16);
+    }
     h->cw.resize(h->p.nlevels);
     for (int l = 1; l < h->p.nlevels; ++l) {
         CoarseLevel& L = h->lev[l];
+        CK(L.cs_part.ensure(coarse_solver_partial_bytes()));
+        CK(L.cs_state.ensure(coarse_solver_state_bytes()));
+        CK(cudaMemset(L.cs_state.p, 0, coarse_solver_state_bytes()));
         size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
         int nv = 4 + 2 * (h->p.coarse_ell + 1);
         for (int k = 0; k < nv; ++k) {
@@ -615,6 +573,7 @@ amg_status normalise_into(amg_hierarchy* h, int prec, const void* src, void* dst
     const size_t n = fine_n(h);
     double nn;
     TRY(h->red.norm2(prec, src, n, &nn, s));
+    TRY(coarse_status(h));
     if (!(nn > 0) || !std::isfinite(nn)) return fail(AMG_NAN, "setup: test vector vanished or is not finite");
     CK(launch_axpby(prec, make_double2(1.0 / std::sqrt(nn), 0), src, make_double2(0, 0), dst, n, s));
     return AMG_OK;
@@ -1005,7 +964,7 @@ amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_st
     TRY(precondition64(h, h->ob.p, h->ox.p, st));
     CK(launch_unpack_spinor(0, g, h->ox.p, x, 1, st));
     CK(cudaStreamSynchronize(st));
-    return AMG_OK;
+    return coarse_status(h);
 }
 
 amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, double tol, int maxit, int use_x0,
@@ -1019,6 +978,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         h->timer.reset();
         h->timer.on = info != nullptr;
         h->coarse_cycles = 0;
+        for (int l = 1; l < h->p.nlevels; ++l) CK(cudaMemsetAsync(h->lev[l].cs_state.p, 0, 16, st));
         const double* br = b + (size_t)r * g.V * 24;
         double* xr = x + (size_t)r * g.V * 24;
         CK(launch_pack_spinor(0, g, br, h->ob.p, 1, st));
@@ -1026,10 +986,13 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V), st));
         amg_solve_info loc;
         std::memset(&loc, 0, sizeof(loc));
-        amg_status rs = fgmres(h, h->ob.p, h->ox.p, tol, maxit, &loc, st);
+        amg_status rs = fgmres(h, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, &loc, st);
         if (rs != AMG_OK && rs != AMG_NOT_CONVERGED) return rs;
         CK(launch_unpack_spinor(0, g, h->ox.p, xr, 1, st));
+        CK(cudaMemcpyAsync(h->hstate, h->lev[h->p.nlevels - 1].cs_state.p, 16, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        TRY(coarse_status(h));
+        h->coarse_cycles = h->hstate[3];
         if (rs == AMG_NOT_CONVERGED) worst = rs;
         if (info) {
             double ms[PH_NPH];

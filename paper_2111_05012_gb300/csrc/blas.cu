@@ -20,6 +20,8 @@ int sm_count() {
     return sms;
 }
 
+int blas_grid_size() { return 2 * sm_count(); }
+
 template <typename V> struct VT;
 template <> struct VT<double2> { using T = double; };
 template <> struct VT<float2> { using T = float; };
@@ -28,30 +30,31 @@ struct PtrList {
     const void* p[kMaxDots];
 };
 
-template <typename V>
-__global__ void multi_dot_kernel(int k, PtrList a, const V* __restrict__ b, size_t n, double2* partials) {
-    __shared__ double red[2 * kMaxDots * 32];
-    double acc[2 * kMaxDots];
+// K dots <a_j, b>, K a compile-time constant so that only K accumulation
+// chains are issued (FP64 arithmetic is scarce on this part)
+template <typename V, int K>
+__global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, double2* partials) {
+    __shared__ double red[2 * K * 32];
+    double acc[2 * K];
 #pragma unroll
-    for (int j = 0; j < 2 * kMaxDots; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 2 * K; ++j) acc[j] = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         V y = b[i];
 #pragma unroll
-        for (int j = 0; j < kMaxDots; ++j) {
-            if (j < k) {
-                V x = ((const V*)a.p[j])[i];
-                acc[2 * j] += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
-                acc[2 * j + 1] += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
-            }
+        for (int j = 0; j < K; ++j) {
+            V x = ((const V*)a.p[j])[i];
+            acc[2 * j] += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
+            acc[2 * j + 1] += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < 2 * k; ++j) {
+#pragma unroll
+    for (int j = 0; j < 2 * K; ++j) {
         double v = warp_sum(acc[j]);
         if (lane == 0) red[j * 32 + warp] = v;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
         double re = 0, im = 0;
         for (int w = 0; w < nw; ++w) {
             re += red[(2 * j) * 32 + w];
@@ -59,6 +62,14 @@ __global__ void multi_dot_kernel(int k, PtrList a, const V* __restrict__ b, size
         }
         partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(re, im);
     }
+}
+
+template <typename V, int K>
+void multi_dot_launch(int k, const PtrList& pl, const V* b, size_t n, double2* partials, cudaStream_t st) {
+    if constexpr (K > 1) {
+        if (k < K) return multi_dot_launch<V, K - 1>(k, pl, b, n, partials, st);
+    }
+    multi_dot_kernel<V, K><<<blas_grid_size(), kBT, 0, st>>>(pl, b, n, partials);
 }
 
 template <typename V>
@@ -117,15 +128,16 @@ __global__ void multi_axpy_kernel(int k, CoefList c, PtrList x, V* y, size_t n) 
 
 }  // namespace
 
-int blas_grid() { return 2 * sm_count(); }
+int blas_grid() { return blas_grid_size(); }
 
 cudaError_t launch_multi_dot(int prec, int k, const void* const* a, const void* b, size_t n, double2* partials,
                              cudaStream_t st) {
     if (k > kMaxDots) return cudaErrorInvalidValue;
     PtrList pl;
     for (int j = 0; j < k; ++j) pl.p[j] = a[j];
-    if (prec == 0) multi_dot_kernel<double2><<<blas_grid(), kBT, 0, st>>>(k, pl, (const double2*)b, n, partials);
-    else multi_dot_kernel<float2><<<blas_grid(), kBT, 0, st>>>(k, pl, (const float2*)b, n, partials);
+    if (k < 1) return cudaErrorInvalidValue;
+    if (prec == 0) multi_dot_launch<double2, kMaxDots>(k, pl, (const double2*)b, n, partials, st);
+    else multi_dot_launch<float2, kMaxDots>(k, pl, (const float2*)b, n, partials, st);
     return cudaGetLastError();
 }
 cudaError_t launch_norm2(int prec, const void* a, size_t n, double* partials, cudaStream_t st) {

@@ -1,0 +1,537 @@
+// Persistent coarse-grid solver: BiCGStab(l) (Sleijpen-Fokkema) for the
+// coarse system D_c x = b of step (1b) in Sec. 3, run to a loose relative
+// tolerance entirely on the device in ONE cooperative launch.
+//
+// Every CTA owns a contiguous range of rows of the coarse system; a warp
+// computes one row of the 9-point stencil at a time and all elementwise
+// vector updates of a row are done by the CTA that owns it, so vector
+// dependencies only cross CTAs at the stencil's neighbour reads.  Grid-wide
+// reductions write one FP64 partial per CTA; after a grid barrier every CTA
+// sums the partials in the same fixed order, so all CTAs hold bit-identical
+// scalars and take identical branches.  The minimal-residual part uses the
+// Gram matrix of R_0..R_l (one reduction) instead of sequential projections.
+//
+// The stencil streams the CTA's contiguous slice of the coarse operator
+// through a 4-stage shared-memory ring filled by bulk asynchronous copies
+// (cp.async.bulk, completion counted on mbarriers); neighbour vector entries
+// are read through L2.
+//
+// Grid barriers and mbarrier waits spin with a bounded count; on timeout the
+// kernel records AMG_TIMEOUT in the status word and every CTA returns.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxEll = 4;
+constexpr int kMaxQ = (kMaxEll + 1) * (kMaxEll + 1) + 2;   // reduced quantities per barrier
+constexpr long long kSpinLimit = 40000000;                    // ~ seconds of polling
+constexpr int kStages = 4;                                    // bulk-copy ring depth
+constexpr int kChunkBytes = 27648;                            // target bytes per ring slot
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int cycles;
+};
+
+template <typename TC> struct V2;
+template <> struct V2<double> { using T = double2; };
+template <> struct V2<float> { using T = float2; };
+
+// vectors are written by other CTAs of the same grid: read them through L2
+// (ld.global.cg), never from a possibly stale L1 line
+template <typename TC> DEV cx<TC> ld(const void* p, size_t i) {
+    typename V2<TC>::T t = __ldcg((const typename V2<TC>::T*)p + i);
+    return {t.x, t.y};
+}
+template <typename TC> DEV cx<TC> ldg(const void* p, size_t i) {
+    typename V2<TC>::T t = __ldg((const typename V2<TC>::T*)p + i);
+    return {t.x, t.y};
+}
+template <typename TC> DEV void st(void* p, size_t i, cx<TC> v) { ((typename V2<TC>::T*)p)[i] = {v.re, v.im}; }
+
+// ---- mbarrier / bulk copy (inline PTX) ----
+DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+DEV void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+DEV void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+DEV void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+DEV void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+DEV bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false after kSpinLimit polls
+DEV bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (long long it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+struct Args {
+    int L[4];
+    int Vc, nc, ell, maxit;
+    double tol;
+    const void* B;
+    const void* b;
+    void* x;
+    void* rt;
+    void* R[kMaxEll + 1];
+    void* U[kMaxEll + 1];
+    double2* part;   // [kMaxQ][gridDim.x]
+    GridBar* bar;
+    int rows_per_chunk;   // rows of the operator per ring slot
+    int row_bytes;        // 9 * nc * sizeof(complex)
+};
+
+// ring state of one CTA (identical in all its threads)
+struct Ring {
+    unsigned char* buf;   // kStages slots of chunk bytes
+    uint64_t* full;       // kStages mbarriers
+    unsigned next;        // global index of the next chunk to consume
+};
+
+// grid barrier; returns false if it gave up (then the caller returns)
+DEV bool grid_sync(GridBar* gb) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &gb->gen;
+        volatile int* verr = &gb->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g) {
+                if (*verr) {
+                    ok = 0;
+                    break;
+                }
+                if (++it > kSpinLimit) {
+                    atomicExch(&gb->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// CTA-wide sum of nq complex values held per thread (accumulated in AT, the
+// solver's precision); thread 0 writes the CTA partials in FP64, the grid
+// barrier follows, then every CTA sums all partials in fixed order.  Results
+// land in `out` (shared) for all threads.
+template <int NQ, typename AT>
+DEV bool grid_reduce(const Args& a, cx<AT> (&v)[NQ], int nq, cx<double>* red_sh, cx<double>* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < nq; ++q) {
+        AT re = warp_sum(v[q].re), im = warp_sum(v[q].im);
+        if (lane == 0) red_sh[q * kWarps + warp] = {(double)re, (double)im};
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        cx<double> t = czero<double>();
+        for (int w = 0; w < kWarps; ++w) t = t + red_sh[threadIdx.x * kWarps + w];
+        a.part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = make_double2(t.re, t.im);
+    }
+    if (!grid_sync(a.bar)) return false;
+    if (warp == 0) {
+        for (int q = 0; q < nq; ++q) {
+            double re = 0, im = 0;
+            for (int i = lane; i < (int)gridDim.x; i += 32) {
+                double2 t = __ldcg(a.part + (size_t)q * gridDim.x + i);
+                re += t.x;
+                im += t.y;
+            }
+            re = warp_sum(re);
+            im = warp_sum(im);
+            if (lane == 0) out[q] = {re, im};
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// row range owned by this CTA
+DEV void my_rows(int nrows, int& r0, int& r1) {
+    int per = (nrows + gridDim.x - 1) / gridDim.x;
+    r0 = blockIdx.x * per;
+    r1 = min(nrows, r0 + per);
+    if (r0 > nrows) r0 = nrows;
+}
+
+// y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA
+// (one warp per row); returns per-thread partial <w, y> if w != nullptr.
+// two adjacent complex numbers: one 16-byte load (FP32) or two (FP64)
+DEV void ld_pair_g(const float* p, size_t i, cx<float>& a, cx<float>& b) {
+    float4 t = __ldg((const float4*)p + i);
+    a = {t.x, t.y};
+    b = {t.z, t.w};
+}
+DEV void ld_pair_g(const double* p, size_t i, cx<double>& a, cx<double>& b) {
+    double2 t0 = __ldg((const double2*)p + 2 * i), t1 = __ldg((const double2*)p + 2 * i + 1);
+    a = {t0.x, t0.y};
+    b = {t1.x, t1.y};
+}
+DEV void ld_pair_cg(const float* p, size_t i, cx<float>& a, cx<float>& b) {
+    float4 t = __ldcg((const float4*)p + i);
+    a = {t.x, t.y};
+    b = {t.z, t.w};
+}
+DEV void ld_pair_cg(const double* p, size_t i, cx<double>& a, cx<double>& b) {
+    double2 t0 = __ldcg((const double2*)p + 2 * i), t1 = __ldcg((const double2*)p + 2 * i + 1);
+    a = {t0.x, t0.y};
+    b = {t1.x, t1.y};
+}
+
+// issue the bulk copy of chunk c (rows r0 + c*rows_per_chunk ...) of this call
+DEV void ring_issue(const Args& a, Ring& rg, unsigned gidx, int r0, int r1, int c) {
+    const int rc0 = r0 + c * a.rows_per_chunk;
+    const int rows = min(r1 - rc0, a.rows_per_chunk);
+    const unsigned slot = gidx % kStages;
+    const unsigned bytes = (unsigned)rows * (unsigned)a.row_bytes;
+    mbar_expect_tx(&rg.full[slot], bytes);
+    bulk_g2s(rg.buf + (size_t)slot * kChunkBytes, (const unsigned char*)a.B + (size_t)rc0 * a.row_bytes, bytes,
+             &rg.full[slot]);
+}
+
+// y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA:
+// the operator rows arrive through the bulk-copy ring, one warp computes one
+// row (each lane two adjacent columns; nc is even so a pair never straddles
+// two neighbours); returns the per-thread partial <w, y> if w != nullptr.
+// Returns false if a ring wait timed out.
+template <typename TC>
+DEV bool stencil_rows(const Args& a, Ring& rg, const void* xin, void* yout, const void* w, int r0, int r1,
+                      cx<TC>& dotp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nc = a.nc, K2 = 9 * nc / 2;   // complex pairs per row
+    const int nch = (r1 - r0 + a.rows_per_chunk - 1) / a.rows_per_chunk;
+    const unsigned base = rg.next;
+    int issued = min(nch, kStages);
+    if (threadIdx.x == 0)
+        for (int c = 0; c < issued; ++c) ring_issue(a, rg, base + c, r0, r1, c);
+    bool ok = true;
+    // every issued chunk is waited for (bounded), even after a failure, so no
+    // bulk copy is left in flight when the CTA returns
+    for (int c = 0; c < issued; ++c) {
+        const unsigned gidx = base + c, slot = gidx % kStages;
+        const bool got = mbar_wait(&rg.full[slot], (gidx / kStages) & 1);
+        ok = __syncthreads_and(ok && got) != 0;   // CTA-uniform decision
+        const int rc0 = r0 + c * a.rows_per_chunk, rc1 = min(r1, rc0 + a.rows_per_chunk);
+        const unsigned char* sb = rg.buf + (size_t)slot * kChunkBytes;
+        for (int r = rc0 + warp; ok && r < rc1; r += kWarps) {
+            const int X = r / nc;
+            int cc4[4];
+            cc4[0] = X % a.L[0];
+            int t = X / a.L[0];
+            cc4[1] = t % a.L[1];
+            t /= a.L[1];
+            cc4[2] = t % a.L[2];
+            cc4[3] = t / a.L[2];
+            int nb[9];
+            nb[0] = X;
+#pragma unroll
+            for (int d = 1; d < 9; ++d) {
+                int mu = (d - 1) & 3, dir = d <= 4 ? 1 : -1;
+                int cc[4] = {cc4[0], cc4[1], cc4[2], cc4[3]};
+                cc[mu] = (cc[mu] + dir + a.L[mu]) % a.L[mu];
+                nb[d] = cc[0] + a.L[0] * (cc[1] + a.L[1] * (cc[2] + a.L[2] * cc[3]));
+            }
+            const cx<TC>* brow = (const cx<TC>*)(sb + (size_t)(r - rc0) * a.row_bytes);
+            cx<TC> acc0 = czero<TC>(), acc1 = czero<TC>();
+#pragma unroll 4
+            for (int j = lane; j < K2; j += 32) {
+                const int e = 2 * j, d = e / nc, col = e - d * nc;
+                cx<TC> x0, x1;
+                ld_pair_cg((const TC*)xin, ((size_t)nb[d] * nc + col) / 2, x0, x1);
+                acc0 = acc0 + brow[e] * x0;
+                acc1 = acc1 + brow[e + 1] * x1;
+            }
+            cx<TC> acc = acc0 + acc1;
+            acc.re = warp_sum(acc.re);
+            acc.im = warp_sum(acc.im);
+            if (lane == 0) {
+                st<TC>(yout, r, acc);
+                if (w) dotp = dotp + cmulc(ld<TC>(w, r), acc);
+            }
+        }
+        __syncthreads();   // slot free again
+        if (ok && c + kStages < nch) {
+            if (threadIdx.x == 0) ring_issue(a, rg, base + c + kStages, r0, r1, c + kStages);
+            ++issued;
+        }
+    }
+    rg.next = base + issued;
+    return ok;
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
+    __shared__ cx<double> red_sh[kMaxQ * kWarps];
+    __shared__ cx<double> res[kMaxQ];
+    __shared__ __align__(8) uint64_t full[kStages];
+    extern __shared__ __align__(128) unsigned char ring_buf[];
+    Ring rg{ring_buf, full, 0u};
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kStages; ++k) mbar_init(&full[k], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int ell = a.ell;
+    const int n = a.Vc * a.nc;
+    int r0, r1;
+    my_rows(n, r0, r1);
+    const int tid = threadIdx.x;
+    // initial state: x = 0, R0 = b, rt = b, U0 = 0
+    for (int i = r0 + tid; i < r1; i += kThreads) {
+        cx<TC> bi = ld<TC>(a.b, i);
+        st<TC>(a.x, i, czero<TC>());
+        st<TC>(a.R[0], i, bi);
+        st<TC>(a.rt, i, bi);
+        st<TC>(a.U[0], i, czero<TC>());
+    }
+    cx<double> rho0 = {1, 0}, alpha = {0, 0}, omega = {1, 0};
+    double bn2 = -1;
+    int cycle = 0;
+    for (;; ++cycle) {
+        // |R0|^2 and rho1 = <rt, R0> in one reduction
+        {
+            cx<TC> v[2] = {czero<TC>(), czero<TC>()};
+            for (int i = r0 + tid; i < r1; i += kThreads) {
+                cx<TC> ri = ld<TC>(a.R[0], i);
+                v[0].re += norm2(ri);
+                v[1] = v[1] + cmulc(ld<TC>(a.rt, i), ri);
+            }
+            if (!grid_reduce<2, TC>(a, v, 2, red_sh, res)) return;
+        }
+        const double rn2 = res[0].re;
+        if (bn2 < 0) bn2 = rn2;
+        if (!(rn2 == rn2)) {   // NaN
+            if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
+            return;
+        }
+        if (rn2 <= a.tol * a.tol * bn2 || cycle >= a.maxit) break;
+        cx<double> rho1 = res[1];
+        rho0 = -1.0 * omega * rho0;
+        for (int j = 0; j < ell; ++j) {
+            cx<double> beta = (alpha * rho1) * cx<double>{rho0.re / norm2(rho0), -rho0.im / norm2(rho0)};
+            rho0 = rho1;
+            for (int i = r0 + tid; i < r1; i += kThreads)
+                for (int q = 0; q <= j; ++q) {
+                    cx<TC> u = ld<TC>(a.U[q], i);
+                    st<TC>(a.U[q], i, ld<TC>(a.R[q], i) - ccast<TC>(beta) * u);
+                }
+            if (!grid_sync(a.bar)) return;
+            // U_{j+1} = A U_j and gamma = <rt, U_{j+1}>
+            {
+                cx<TC> v[1] = {czero<TC>()};
+                if (!stencil_rows<TC>(a, rg, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0])) {
+                    atomicExch(&a.bar->err, 1);
+                    return;
+                }
+                if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
+            }
+            cx<double> gam = res[0];
+            alpha = rho0 * cx<double>{gam.re / norm2(gam), -gam.im / norm2(gam)};
+            for (int i = r0 + tid; i < r1; i += kThreads) {
+                for (int q = 0; q <= j; ++q)
+                    st<TC>(a.R[q], i, ld<TC>(a.R[q], i) - ccast<TC>(alpha) * ld<TC>(a.U[q + 1], i));
+                st<TC>(a.x, i, ld<TC>(a.x, i) + ccast<TC>(alpha) * ld<TC>(a.U[0], i));
+            }
+            if (!grid_sync(a.bar)) return;
+            // R_{j+1} = A R_j; the next BiCG step needs rho1 = <rt, R_{j+1}>
+            {
+                cx<TC> v[1] = {czero<TC>()};
+                if (!stencil_rows<TC>(a, rg, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0])) {
+                    atomicExch(&a.bar->err, 1);
+                    return;
+                }
+                if (j + 1 < ell) {
+                    if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
+                    rho1 = res[0];
+                }
+            }
+        }
+        // minimal-residual part from the Gram matrix G_pq = <R_p, R_q>, p, q = 0..ell
+        {
+            cx<TC> v[kMaxQ];
+            int nq = (ell + 1) * (ell + 1);
+            for (int q = 0; q < nq; ++q) v[q] = czero<TC>();
+            for (int i = r0 + tid; i < r1; i += kThreads) {
+                cx<TC> rv[kMaxEll + 1];
+                for (int p = 0; p <= ell; ++p) rv[p] = ld<TC>(a.R[p], i);
+                for (int p = 0; p <= ell; ++p)
+                    for (int q = p; q <= ell; ++q) v[p * (ell + 1) + q] = v[p * (ell + 1) + q] + cmulc(rv[p], rv[q]);
+            }
+            if (!grid_reduce<kMaxQ, TC>(a, v, nq, red_sh, res)) return;
+        }
+        // Gram-Schmidt of R_1..R_ell expressed in the original basis:
+        // Rt_j = sum_k C[j][k] R_k (k = 1..j), tau_ij = <Rt_i, Rt_j>/sigma_i.
+        // One thread evaluates the scalar algebra; the update coefficients are
+        // broadcast through shared memory.
+        __shared__ cx<double> s_cx[kMaxEll + 1], s_cr[kMaxEll + 1], s_g[kMaxEll + 1];
+        __shared__ int s_bad;
+        if (tid == 0) {
+            cx<double> C[kMaxEll + 1][kMaxEll + 1];
+            double sigma[kMaxEll + 1];
+            cx<double> gp[kMaxEll + 1], g[kMaxEll + 1], gpp[kMaxEll + 1], tau[kMaxEll + 1][kMaxEll + 1];
+            auto G = [&](int p, int q) -> cx<double> {   // <R_p, R_q>
+                return p <= q ? res[p * (ell + 1) + q] : conj(res[q * (ell + 1) + p]);
+            };
+            for (int j = 0; j <= ell; ++j)
+                for (int k = 0; k <= ell; ++k) C[j][k] = czero<double>();
+            int bad = 0;
+            for (int j = 1; j <= ell; ++j) {
+                C[j][j] = {1, 0};
+                for (int i = 1; i < j; ++i) {
+                    cx<double> t = czero<double>();
+                    for (int p = 1; p <= i; ++p)
+                        for (int q = 1; q <= j; ++q) t = t + conj(C[i][p]) * C[j][q] * G(p, q);
+                    tau[i][j] = (1.0 / sigma[i]) * t;
+                    for (int k = 1; k <= i; ++k) C[j][k] = C[j][k] - tau[i][j] * C[i][k];
+                }
+                double sg = 0;
+                cx<double> t0 = czero<double>();
+                for (int p = 1; p <= j; ++p) {
+                    for (int q = 1; q <= j; ++q) sg += (conj(C[j][p]) * C[j][q] * G(p, q)).re;
+                    t0 = t0 + conj(C[j][p]) * G(p, 0);
+                }
+                sigma[j] = sg;
+                if (!(sg > 0)) bad = 1;
+                gp[j] = (1.0 / (sg > 0 ? sg : 1.0)) * t0;
+            }
+            g[ell] = gp[ell];
+            for (int j = ell - 1; j >= 1; --j) {
+                cx<double> t = gp[j];
+                for (int i = j + 1; i <= ell; ++i) t = t - tau[j][i] * g[i];
+                g[j] = t;
+            }
+            for (int j = 1; j < ell; ++j) {
+                cx<double> t = g[j + 1];
+                for (int i = j + 1; i < ell; ++i) t = t + tau[j][i] * g[i + 1];
+                gpp[j] = t;
+            }
+            // x += g1 R0 + sum_{j<ell} gpp_j Rt_j ; R0 -= sum_j gp_j Rt_j ; U0 -= sum_j g_j U_j
+            for (int k = 0; k <= ell; ++k) s_cx[k] = s_cr[k] = czero<double>();
+            s_cx[0] = g[1];
+            for (int j = 1; j < ell; ++j)
+                for (int k = 1; k <= j; ++k) s_cx[k] = s_cx[k] + gpp[j] * C[j][k];
+            for (int j = 1; j <= ell; ++j)
+                for (int k = 1; k <= j; ++k) s_cr[k] = s_cr[k] + gp[j] * C[j][k];
+            for (int k = 0; k <= ell; ++k) s_g[k] = g[k];
+            s_bad = bad;
+        }
+        __syncthreads();
+        if (s_bad) {
+            if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
+            return;
+        }
+        omega = s_g[ell];
+        cx<double> cx_[kMaxEll + 1], cr[kMaxEll + 1], g[kMaxEll + 1];
+        for (int k = 0; k <= ell; ++k) {
+            cx_[k] = s_cx[k];
+            cr[k] = s_cr[k];
+            g[k] = s_g[k];
+        }
+        for (int i = r0 + tid; i < r1; i += kThreads) {
+            cx<TC> xv = ld<TC>(a.x, i), r0v = ld<TC>(a.R[0], i), u0 = ld<TC>(a.U[0], i);
+            xv = xv + ccast<TC>(cx_[0]) * r0v;
+            for (int k = 1; k <= ell; ++k) {
+                cx<TC> rk = ld<TC>(a.R[k], i);
+                xv = xv + ccast<TC>(cx_[k]) * rk;
+                r0v = r0v - ccast<TC>(cr[k]) * rk;
+                u0 = u0 - ccast<TC>(g[k]) * ld<TC>(a.U[k], i);
+            }
+            st<TC>(a.x, i, xv);
+            st<TC>(a.R[0], i, r0v);
+            st<TC>(a.U[0], i, u0);
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0) a.bar->cycles += cycle;
+}
+
+// one CTA per SM (152 barrier participants on GB300), if the kernel fits
+int coop_grid(const void* fn, int smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem);
+    if (per < 1) return 0;
+    return sms;
+}
+
+}  // namespace
+
+size_t coarse_solver_state_bytes() { return sizeof(GridBar) + 64; }
+size_t coarse_solver_partial_bytes() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sizeof(double2) * (size_t)kMaxQ * sms;
+}
+
+cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
+                                   void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
+                                   void* part, void* state, cudaStream_t s) {
+    if (ell < 1 || ell > kMaxEll) return cudaErrorInvalidValue;
+    Args a;
+    for (int i = 0; i < 4; ++i) a.L[i] = gc.L[i];
+    a.Vc = gc.V;
+    a.nc = nc;
+    a.ell = ell;
+    a.maxit = maxit;
+    a.tol = tol;
+    a.B = B;
+    a.b = b;
+    a.x = x;
+    a.rt = rt;
+    for (int j = 0; j <= kMaxEll; ++j) {
+        a.R[j] = j <= ell ? R[j] : nullptr;
+        a.U[j] = j <= ell ? U[j] : nullptr;
+    }
+    a.part = (double2*)part;
+    a.bar = (GridBar*)state;
+    if (nc % 2 != 0) return cudaErrorInvalidValue;
+    a.row_bytes = 9 * nc * (cprec == 0 ? 16 : 8);
+    a.rows_per_chunk = kChunkBytes / a.row_bytes;
+    if (a.rows_per_chunk < 1) return cudaErrorInvalidValue;   // nc too large for a ring slot
+    const void* fn = cprec == 0 ? (const void*)coarse_bicgstab_kernel<double> : (const void*)coarse_bicgstab_kernel<float>;
+    const int smem = kStages * kChunkBytes;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int grid = coop_grid(fn, smem);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    void* params[] = {&a};
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), params, smem, s);
+}

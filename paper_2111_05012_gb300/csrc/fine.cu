@@ -342,8 +342,10 @@ __global__ void __launch_bounds__(kThreads) dirac_kernel(Geom g, Blocking bk, co
 // x_mode: 0 = x holds the current iterate everywhere; 1 = x is zero everywhere
 // (r = b, x is only written); 2 = x is zero on the active domains and holds the
 // iterate elsewhere (first odd half sweep after an even sweep from zero).
+// 256-thread FP32/FP16 variant: 128 registers, two CTAs per SM (no spills);
+// the FP64 variant keeps one CTA per SM (it would spill at 128 registers)
 template <class P, int MAXT>
-__global__ void __launch_bounds__(MAXT) sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode,
+__global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode,
                                                         const void* __restrict__ U, const void* __restrict__ C,
                                                         const void* __restrict__ b, void* x, typename P::T kappa) {
     using T = typename P::T;

@@ -70,6 +70,15 @@ cudaError_t launch_orthonormalise_coarse(int prec, const GeomH& gc, int nc, cons
                                          int* err_flag, cudaStream_t s);
 cudaError_t launch_galerkin_coarse(int prec, int cprec_out, const GeomH& gc, int nc, const BlockH& bk, int nvec,
                                    const void* vecs, const void* B, void* Bout, cudaStream_t s);
+// persistent BiCGStab(ell) on a coarse level (one cooperative launch); part and state are
+// device scratch of coarse_solver_partial_bytes() / coarse_solver_state_bytes(); the first 12
+// bytes of state must be zero before the launch; state word 3 accumulates the cycle count,
+// word 2 is nonzero on failure (1 = barrier timeout, 2 = breakdown / non-finite)
+size_t coarse_solver_state_bytes();
+size_t coarse_solver_partial_bytes();
+cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
+                                   void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
+                                   void* part, void* state, cudaStream_t s);
 // coarse op layout change: internal [Vc][Nc][9][Nc] -> canonical [Vc][9][Nc][Nc] doubles
 cudaError_t launch_coarse_op_export(int cprec, int Vc, int nc, const void* B, double* out, cudaStream_t s);
 // precision change of flat complex arrays (n complex numbers); prec 0 = double2, 1 = float2
