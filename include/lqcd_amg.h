@@ -55,7 +55,10 @@ typedef enum {
     AMG_F64 = 0,   /* double storage and arithmetic */
     AMG_F32 = 1,   /* float storage and arithmetic */
     AMG_F16 = 2,   /* fine fields stored as half with a per-site float scale, float arithmetic */
-    AMG_BF16 = 3   /* coarse operator stored as bfloat16, float accumulation */
+    AMG_BF16 = 3,  /* coarse operator stored as bfloat16, float accumulation */
+    AMG_F64X = 4   /* amg_apply_D only: float input (taken as exact), double output, FP64-accurate
+                      double-float arithmetic with FP64 links and clover (the outer solver's Arnoldi
+                      product for vectors produced by the FP32 preconditioner) */
 } amg_prec;
 
 #define AMG_MAX_LEVELS 4

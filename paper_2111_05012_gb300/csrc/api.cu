@@ -80,12 +80,12 @@ struct amg_lattice {
 };
 struct amg_gauge {
     amg_lattice* lat;
-    DevBuf U[3];
+    DevBuf U[4];   // by precision id: F64, F32, F16, FP64 as float hi/lo pairs
 };
 struct amg_dirac {
     amg_gauge* gauge;
     double kappa, csw;
-    DevBuf C[3];
+    DevBuf C[4];
     DevBuf in, out;   // call scratch for the canonical-layout entry points
 };
 
@@ -333,14 +333,26 @@ amg_status vcycle0(amg_hierarchy* h, int prec, const void* b, void* x, cudaStrea
     return AMG_OK;
 }
 
-// z = M v for FP64 internal fields (precision switch around the cycle)
+// z = M v for an FP64 internal field v; z is written in the outer solver's
+// Z precision (FP64 for the all-FP64 path, else FP32: the cycle's output is
+// exact in FP32, so nothing is lost)
+int zprec_of(amg_hierarchy* h) { return h->fp == 0 ? 0 : 1; }
 amg_status precondition64(amg_hierarchy* h, const void* v, void* z, cudaStream_t s) {
     const GeomH& g = fine_geom(h);
     int fp = h->fp;
     if (fp == 0) return vcycle0(h, 0, v, z, s);
     CK(launch_convert_spinor(0, fp, g, v, h->fb[fp].p, 1, s));
+    if (fp == 1) return vcycle0(h, 1, h->fb[1].p, z, s);
     TRY(vcycle0(h, fp, h->fb[fp].p, h->fx[fp].p, s));
-    CK(launch_convert_spinor(fp, 0, g, h->fx[fp].p, z, 1, s));
+    CK(launch_convert_spinor(fp, 1, g, h->fx[fp].p, z, 1, s));
+    return AMG_OK;
+}
+
+// w = D z for a Z-precision z (FP64 result)
+amg_status arnoldi_D(amg_hierarchy* h, const void* z, void* w, cudaStream_t s) {
+    if (zprec_of(h) == 0) return fine_D(h, 0, z, w, nullptr, s);
+    amg_dirac* d = h->d;
+    CK(launch_dirac_mixed(fine_geom(h), d->gauge->U[3].p, d->C[3].p, z, w, d->kappa, 1, s));
     return AMG_OK;
 }
 
@@ -390,7 +402,7 @@ amg_status fgmres(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, doub
         int jend = -1;
         for (int j = 0; j < m; ++j) {
             TRY(precondition64(h, h->oV[j]->p, h->oZ[j]->p, s));
-            TRY(fine_D(h, 0, h->oZ[j]->p, h->ow.p, nullptr, s));
+            TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, s));
             // classical Gram-Schmidt, twice
             std::vector<const void*> vl(j + 1);
             std::vector<const void*> vx(j + 1);
@@ -456,7 +468,8 @@ amg_status fgmres(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, doub
             yc[i] = d2(y[i]);
             zl[i] = h->oZ[i]->p;
         }
-        CK(launch_multi_axpy(0, k, yc.data(), zl.data(), x, n, s));
+        if (zprec_of(h) == 0) CK(launch_multi_axpy(0, k, yc.data(), zl.data(), x, n, s));
+        else CK(launch_spinor_axpy_mixed(fine_geom(h), k, yc.data(), zl.data(), x, s));
     }
     if (info) {
         info->iters = iters;
@@ -507,7 +520,7 @@ amg_status alloc_workspaces(amg_hierarchy* h) {
         if (j < h->p.outer_m) {
             DevBuf* z = new DevBuf();
             h->oZ.push_back(z);
-            CK(z->ensure(fb64));
+            CK(z->ensure(fine_spinor_bytes(h->fp == 0 ? 0 : 1, g.V)));
         }
     }
     return AMG_OK;
@@ -660,7 +673,7 @@ amg_status amg_gauge_create(amg_lattice* lat, const double* U_host, amg_gauge** 
     if (canon.ensure(cb) != cudaSuccess) return cleanup(fail(AMG_ENOMEM, "gauge: device allocation failed"));
     if (cudaMemcpy(canon.p, U_host, cb, cudaMemcpyHostToDevice) != cudaSuccess)
         return cleanup(fail(AMG_ECUDA, "gauge: upload failed"));
-    for (int pr = 0; pr < 3; ++pr) {
+    for (int pr = 0; pr < 4; ++pr) {
         if (G->U[pr].ensure(fine_gauge_bytes(pr, g.V)) != cudaSuccess)
             return cleanup(fail(AMG_ENOMEM, "gauge: device allocation failed"));
         if (launch_gauge_convert(pr, g, canon.as<double>(), G->U[pr].p, 0) != cudaSuccess)
@@ -679,7 +692,7 @@ amg_status amg_dirac_create(amg_gauge* g, double kappa, double csw, amg_dirac** 
     d->kappa = kappa;
     d->csw = csw;
     const GeomH& geo = g->lat->g;
-    for (int pr = 0; pr < 3; ++pr) {
+    for (int pr = 0; pr < 4; ++pr) {
         if (d->C[pr].ensure(fine_clover_bytes(pr, geo.V)) != cudaSuccess) {
             delete d;
             return fail(AMG_ENOMEM, "clover: device allocation failed");
@@ -713,8 +726,16 @@ amg_status amg_dirac_get_clover(amg_dirac* d, double* host_out) {
 static amg_status apply_fine_canonical(amg_dirac* d, const BlockH* sb, const void* in, void* out, int nrhs,
                                        amg_prec prec, cudaStream_t s) {
     if (!d || !in || !out || nrhs < 1) return fail(AMG_EINVAL, "bad argument");
-    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32 or AMG_F16");
     const GeomH& g = d->gauge->lat->g;
+    if (prec == AMG_F64X && !sb) {
+        CK(d->in.ensure(fine_spinor_bytes(1, g.V) * nrhs));
+        CK(d->out.ensure(fine_spinor_bytes(0, g.V) * nrhs));
+        CK(launch_pack_spinor(1, g, in, d->in.p, nrhs, s));
+        CK(launch_dirac_mixed(g, d->gauge->U[3].p, d->C[3].p, d->in.p, d->out.p, d->kappa, nrhs, s));
+        CK(launch_unpack_spinor(0, g, d->out.p, out, nrhs, s));
+        return AMG_OK;
+    }
+    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32, AMG_F16 (or AMG_F64X for D)");
     size_t fb = fine_spinor_bytes(prec, g.V) * nrhs;
     CK(d->in.ensure(fb));
     CK(d->out.ensure(fb));
@@ -961,8 +982,12 @@ amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_st
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
     CK(launch_pack_spinor(0, g, b, h->ob.p, 1, st));
-    TRY(precondition64(h, h->ob.p, h->ox.p, st));
-    CK(launch_unpack_spinor(0, g, h->ox.p, x, 1, st));
+    TRY(precondition64(h, h->ob.p, h->oZ[0]->p, st));
+    if (zprec_of(h) == 0) CK(launch_unpack_spinor(0, g, h->oZ[0]->p, x, 1, st));
+    else {
+        CK(launch_convert_spinor(1, 0, g, h->oZ[0]->p, h->ox.p, 1, st));
+        CK(launch_unpack_spinor(0, g, h->ox.p, x, 1, st));
+    }
     CK(cudaStreamSynchronize(st));
     return coarse_status(h);
 }

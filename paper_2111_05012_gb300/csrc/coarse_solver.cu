@@ -28,8 +28,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxEll = 4;
 constexpr int kMaxQ = (kMaxEll + 1) * (kMaxEll + 1) + 2;   // reduced quantities per barrier
 constexpr long long kSpinLimit = 40000000;                    // ~ seconds of polling
-constexpr int kStages = 4;                                    // bulk-copy ring depth
-constexpr int kChunkBytes = 27648;                            // target bytes per ring slot
+constexpr int kStages = 3;                                    // bulk-copy ring depth
+constexpr int kChunkBytes = 55296;                            // operator bytes per ring slot (16 FP32 rows, Nc 48)
 
 struct GridBar {
     unsigned count;
@@ -103,6 +103,9 @@ struct Args {
     GridBar* bar;
     int rows_per_chunk;   // rows of the operator per ring slot
     int row_bytes;        // 9 * nc * sizeof(complex)
+    int sites_per_chunk;  // coarse sites a chunk can touch: (rows_per_chunk - 1) / nc + 2
+    int xseg_bytes;       // nc * sizeof(complex): one neighbour vector segment
+    int slot_bytes;       // bytes per ring slot (kChunkBytes)
 };
 
 // ring state of one CTA (identical in all its threads)
@@ -112,23 +115,41 @@ struct Ring {
     unsigned next;        // global index of the next chunk to consume
 };
 
-// grid barrier; returns false if it gave up (then the caller returns)
+DEV unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+DEV unsigned atom_add_acqrel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+DEV void st_relaxed(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+DEV void red_release(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// grid barrier (sense by generation counter, acquire/release atomics); the
+// CTA's writes are published by __syncthreads + the releasing arrival.
+// Returns false if it gave up (then the caller returns).
 DEV bool grid_sync(GridBar* gb) {
     __shared__ int s_ok;
+    // vectors written here are read by bulk copies (async proxy) after the barrier
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = &gb->gen;
         volatile int* verr = &gb->err;
-        const unsigned g = *vgen;
-        __threadfence();
+        const unsigned g = ld_acquire(&gb->gen);
         int ok = 1;
-        if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
+        if (atom_add_acqrel(&gb->count, 1u) == gridDim.x - 1) {
+            st_relaxed(&gb->count, 0u);
+            red_release(&gb->gen, 1u);
         } else {
             long long it = 0;
-            while (*vgen == g) {
+            while (ld_acquire(&gb->gen) == g) {
                 if (*verr) {
                     ok = 0;
                     break;
@@ -138,10 +159,9 @@ DEV bool grid_sync(GridBar* gb) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(20);
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -166,18 +186,17 @@ DEV bool grid_reduce(const Args& a, cx<AT> (&v)[NQ], int nq, cx<double>* red_sh,
         a.part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = make_double2(t.re, t.im);
     }
     if (!grid_sync(a.bar)) return false;
-    if (warp == 0) {
-        for (int q = 0; q < nq; ++q) {
-            double re = 0, im = 0;
-            for (int i = lane; i < (int)gridDim.x; i += 32) {
-                double2 t = __ldcg(a.part + (size_t)q * gridDim.x + i);
-                re += t.x;
-                im += t.y;
-            }
-            re = warp_sum(re);
-            im = warp_sum(im);
-            if (lane == 0) out[q] = {re, im};
+    // one warp per quantity, lanes stride over the CTA partials (fixed order)
+    for (int q = warp; q < nq; q += kWarps) {
+        double re = 0, im = 0;
+        for (int i = lane; i < (int)gridDim.x; i += 32) {
+            double2 t = __ldcg(a.part + (size_t)q * gridDim.x + i);
+            re += t.x;
+            im += t.y;
         }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) out[q] = {re, im};
     }
     __syncthreads();
     return true;
@@ -215,7 +234,21 @@ DEV void ld_pair_cg(const double* p, size_t i, cx<double>& a, cx<double>& b) {
     b = {t1.x, t1.y};
 }
 
-// issue the bulk copy of chunk c (rows r0 + c*rows_per_chunk ...) of this call
+DEV int coarse_neighbour(const Args& a, int X, int d) {
+    if (d == 0) return X;
+    int c[4];
+    c[0] = X % a.L[0];
+    int t = X / a.L[0];
+    c[1] = t % a.L[1];
+    t /= a.L[1];
+    c[2] = t % a.L[2];
+    c[3] = t / a.L[2];
+    const int mu = (d - 1) & 3, dir = d <= 4 ? 1 : -1;
+    c[mu] = (c[mu] + dir + a.L[mu]) % a.L[mu];
+    return c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+}
+
+// issue the bulk copy of the operator rows of chunk c of this call into its ring slot
 DEV void ring_issue(const Args& a, Ring& rg, unsigned gidx, int r0, int r1, int c) {
     const int rc0 = r0 + c * a.rows_per_chunk;
     const int rows = min(r1 - rc0, a.rows_per_chunk);
@@ -226,57 +259,80 @@ DEV void ring_issue(const Args& a, Ring& rg, unsigned gidx, int r0, int r1, int 
              &rg.full[slot]);
 }
 
-// y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA:
-// the operator rows arrive through the bulk-copy ring, one warp computes one
-// row (each lane two adjacent columns; nc is even so a pair never straddles
-// two neighbours); returns the per-thread partial <w, y> if w != nullptr.
-// Returns false if a ring wait timed out.
+// neighbour segments of the sites of chunk c, as pairs of complex numbers:
+// pair p of site s (relative to the chunk's first site) and direction d holds
+// x[nbr(X, d)][2q .. 2q+1], p = (s * 9 + d) * nc/2 + q
 template <typename TC>
-DEV bool stencil_rows(const Args& a, Ring& rg, const void* xin, void* yout, const void* w, int r0, int r1,
-                      cx<TC>& dotp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nc = a.nc, K2 = 9 * nc / 2;   // complex pairs per row
+DEV int xseg_pairs(const Args& a, int r0, int r1, int c, int& X0) {
+    const int rc0 = r0 + c * a.rows_per_chunk, rc1 = min(r1, rc0 + a.rows_per_chunk);
+    X0 = rc0 / a.nc;
+    return ((rc1 - 1) / a.nc - X0 + 1) * 9 * (a.nc / 2);
+}
+template <typename TC>
+DEV void xseg_load(const Args& a, const void* xin, int X0, int p, cx<TC>& v0, cx<TC>& v1) {
+    const int h = a.nc / 2;
+    const int q = p % h, sd = p / h, d = sd % 9, sl = sd / 9;
+    ld_pair_cg((const TC*)xin, ((size_t)coarse_neighbour(a, X0 + sl, d) * a.nc) / 2 + q, v0, v1);
+}
+
+// y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA:
+// operator rows arrive by bulk copy through the ring, the chunk's neighbour
+// segments are gathered by the threads one chunk ahead (double buffer), and
+// one warp computes one row entirely from shared memory; returns the
+// per-thread partial <w, y> in dotp.  Returns false if a ring wait timed out.
+template <typename TC>
+DEV bool stencil_rows(const Args& a, Ring& rg, cx<TC>* xbuf, const void* xin, void* yout, const void* w, int r0,
+                      int r1, cx<TC>& dotp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int nc = a.nc, K = 9 * nc;
+    const int xcap = 9 * a.sites_per_chunk * nc;   // complex numbers per x buffer
     const int nch = (r1 - r0 + a.rows_per_chunk - 1) / a.rows_per_chunk;
     const unsigned base = rg.next;
     int issued = min(nch, kStages);
-    if (threadIdx.x == 0)
+    if (tid == 0)
         for (int c = 0; c < issued; ++c) ring_issue(a, rg, base + c, r0, r1, c);
+    // neighbour segments of chunk 0
+    if (nch > 0) {
+        int X0;
+        const int np = xseg_pairs<TC>(a, r0, r1, 0, X0);
+        for (int p = tid; p < np; p += kThreads) {
+            cx<TC> v0, v1;
+            xseg_load<TC>(a, xin, X0, p, v0, v1);
+            xbuf[2 * p] = v0;
+            xbuf[2 * p + 1] = v1;
+        }
+    }
     bool ok = true;
     // every issued chunk is waited for (bounded), even after a failure, so no
     // bulk copy is left in flight when the CTA returns
     for (int c = 0; c < issued; ++c) {
         const unsigned gidx = base + c, slot = gidx % kStages;
+        // prefetch the next chunk's segments into registers (they land during the compute)
+        constexpr int kPre = 2;
+        cx<TC> pv[2 * kPre];
+        int Xn = 0, npn = 0;
+        if (c + 1 < nch) {
+            npn = xseg_pairs<TC>(a, r0, r1, c + 1, Xn);
+#pragma unroll
+            for (int k = 0; k < kPre; ++k) {
+                const int p = tid + k * kThreads;
+                if (p < npn) xseg_load<TC>(a, xin, Xn, p, pv[2 * k], pv[2 * k + 1]);
+            }
+        }
         const bool got = mbar_wait(&rg.full[slot], (gidx / kStages) & 1);
-        ok = __syncthreads_and(ok && got) != 0;   // CTA-uniform decision
+        ok = __syncthreads_and(ok && got) != 0;   // CTA-uniform; also publishes xbuf of chunk c
         const int rc0 = r0 + c * a.rows_per_chunk, rc1 = min(r1, rc0 + a.rows_per_chunk);
         const unsigned char* sb = rg.buf + (size_t)slot * kChunkBytes;
+        const cx<TC>* xs = xbuf + (size_t)(c & 1) * xcap;
+        const int X0 = rc0 / nc;
         for (int r = rc0 + warp; ok && r < rc1; r += kWarps) {
-            const int X = r / nc;
-            int cc4[4];
-            cc4[0] = X % a.L[0];
-            int t = X / a.L[0];
-            cc4[1] = t % a.L[1];
-            t /= a.L[1];
-            cc4[2] = t % a.L[2];
-            cc4[3] = t / a.L[2];
-            int nb[9];
-            nb[0] = X;
-#pragma unroll
-            for (int d = 1; d < 9; ++d) {
-                int mu = (d - 1) & 3, dir = d <= 4 ? 1 : -1;
-                int cc[4] = {cc4[0], cc4[1], cc4[2], cc4[3]};
-                cc[mu] = (cc[mu] + dir + a.L[mu]) % a.L[mu];
-                nb[d] = cc[0] + a.L[0] * (cc[1] + a.L[1] * (cc[2] + a.L[2] * cc[3]));
-            }
             const cx<TC>* brow = (const cx<TC>*)(sb + (size_t)(r - rc0) * a.row_bytes);
+            const cx<TC>* xrow = xs + (size_t)(r / nc - X0) * K;   // the nine segments of this row's site
             cx<TC> acc0 = czero<TC>(), acc1 = czero<TC>();
 #pragma unroll 4
-            for (int j = lane; j < K2; j += 32) {
-                const int e = 2 * j, d = e / nc, col = e - d * nc;
-                cx<TC> x0, x1;
-                ld_pair_cg((const TC*)xin, ((size_t)nb[d] * nc + col) / 2, x0, x1);
-                acc0 = acc0 + brow[e] * x0;
-                acc1 = acc1 + brow[e + 1] * x1;
+            for (int j = lane; j < K / 2; j += 32) {
+                acc0 = acc0 + brow[2 * j] * xrow[2 * j];
+                acc1 = acc1 + brow[2 * j + 1] * xrow[2 * j + 1];
             }
             cx<TC> acc = acc0 + acc1;
             acc.re = warp_sum(acc.re);
@@ -286,9 +342,27 @@ DEV bool stencil_rows(const Args& a, Ring& rg, const void* xin, void* yout, cons
                 if (w) dotp = dotp + cmulc(ld<TC>(w, r), acc);
             }
         }
-        __syncthreads();   // slot free again
+        // store the prefetched segments for chunk c+1 (the other buffer)
+        if (c + 1 < nch) {
+            cx<TC>* xn = xbuf + (size_t)((c + 1) & 1) * xcap;
+#pragma unroll
+            for (int k = 0; k < kPre; ++k) {
+                const int p = tid + k * kThreads;
+                if (p < npn) {
+                    xn[2 * p] = pv[2 * k];
+                    xn[2 * p + 1] = pv[2 * k + 1];
+                }
+            }
+            for (int p = tid + kPre * kThreads; p < npn; p += kThreads) {   // rare: more segments than prefetched
+                cx<TC> v0, v1;
+                xseg_load<TC>(a, xin, Xn, p, v0, v1);
+                xn[2 * p] = v0;
+                xn[2 * p + 1] = v1;
+            }
+        }
+        __syncthreads();   // slot and x buffer free again
         if (ok && c + kStages < nch) {
-            if (threadIdx.x == 0) ring_issue(a, rg, base + c + kStages, r0, r1, c + kStages);
+            if (tid == 0) ring_issue(a, rg, base + c + kStages, r0, r1, c + kStages);
             ++issued;
         }
     }
@@ -303,6 +377,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
     __shared__ __align__(8) uint64_t full[kStages];
     extern __shared__ __align__(128) unsigned char ring_buf[];
     Ring rg{ring_buf, full, 0u};
+    cx<TC>* xbuf = (cx<TC>*)(ring_buf + (size_t)kStages * kChunkBytes);   // 2 x 9 * sites_per_chunk * nc
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStages; ++k) mbar_init(&full[k], 1);
         mbar_fence_init();
@@ -321,7 +396,13 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
         st<TC>(a.rt, i, bi);
         st<TC>(a.U[0], i, czero<TC>());
     }
-    cx<double> rho0 = {1, 0}, alpha = {0, 0}, omega = {1, 0};
+    // BiCG scalars in the solver's precision: identical in every thread
+    using SC = TC;
+    auto cdiv = [](cx<SC> n, cx<SC> d) -> cx<SC> {
+        const SC inv = SC(1) / norm2(d);
+        return {(n.re * d.re + n.im * d.im) * inv, (n.im * d.re - n.re * d.im) * inv};
+    };
+    cx<SC> rho0 = {SC(1), SC(0)}, alpha = {SC(0), SC(0)}, omega = {SC(1), SC(0)};
     double bn2 = -1;
     int cycle = 0;
     for (;; ++cycle) {
@@ -342,10 +423,10 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             return;
         }
         if (rn2 <= a.tol * a.tol * bn2 || cycle >= a.maxit) break;
-        cx<double> rho1 = res[1];
-        rho0 = -1.0 * omega * rho0;
+        cx<SC> rho1 = ccast<SC>(res[1]);
+        rho0 = SC(-1) * omega * rho0;
         for (int j = 0; j < ell; ++j) {
-            cx<double> beta = (alpha * rho1) * cx<double>{rho0.re / norm2(rho0), -rho0.im / norm2(rho0)};
+            const cx<SC> beta = cdiv(alpha * rho1, rho0);
             rho0 = rho1;
             for (int i = r0 + tid; i < r1; i += kThreads)
                 for (int q = 0; q <= j; ++q) {
@@ -356,14 +437,13 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             // U_{j+1} = A U_j and gamma = <rt, U_{j+1}>
             {
                 cx<TC> v[1] = {czero<TC>()};
-                if (!stencil_rows<TC>(a, rg, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0])) {
+                if (!stencil_rows<TC>(a, rg, xbuf, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0])) {
                     atomicExch(&a.bar->err, 1);
                     return;
                 }
                 if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
             }
-            cx<double> gam = res[0];
-            alpha = rho0 * cx<double>{gam.re / norm2(gam), -gam.im / norm2(gam)};
+            alpha = cdiv(rho0, ccast<SC>(res[0]));
             for (int i = r0 + tid; i < r1; i += kThreads) {
                 for (int q = 0; q <= j; ++q)
                     st<TC>(a.R[q], i, ld<TC>(a.R[q], i) - ccast<TC>(alpha) * ld<TC>(a.U[q + 1], i));
@@ -373,13 +453,13 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             // R_{j+1} = A R_j; the next BiCG step needs rho1 = <rt, R_{j+1}>
             {
                 cx<TC> v[1] = {czero<TC>()};
-                if (!stencil_rows<TC>(a, rg, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0])) {
+                if (!stencil_rows<TC>(a, rg, xbuf, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0])) {
                     atomicExch(&a.bar->err, 1);
                     return;
                 }
                 if (j + 1 < ell) {
                     if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
-                    rho1 = res[0];
+                    rho1 = ccast<SC>(res[0]);
                 }
             }
         }
@@ -402,54 +482,61 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
         // broadcast through shared memory.
         __shared__ cx<double> s_cx[kMaxEll + 1], s_cr[kMaxEll + 1], s_g[kMaxEll + 1];
         __shared__ int s_bad;
+        // scalars in the solver's precision (FP32 for the FP32 coarse solve)
+        using ST = TC;
         if (tid == 0) {
-            cx<double> C[kMaxEll + 1][kMaxEll + 1];
-            double sigma[kMaxEll + 1];
-            cx<double> gp[kMaxEll + 1], g[kMaxEll + 1], gpp[kMaxEll + 1], tau[kMaxEll + 1][kMaxEll + 1];
-            auto G = [&](int p, int q) -> cx<double> {   // <R_p, R_q>
-                return p <= q ? res[p * (ell + 1) + q] : conj(res[q * (ell + 1) + p]);
+            cx<ST> C[kMaxEll + 1][kMaxEll + 1];
+            ST sigma[kMaxEll + 1];
+            cx<ST> gp[kMaxEll + 1], g[kMaxEll + 1], gpp[kMaxEll + 1], tau[kMaxEll + 1][kMaxEll + 1];
+            auto G = [&](int p, int q) -> cx<ST> {   // <R_p, R_q>
+                return ccast<ST>(p <= q ? res[p * (ell + 1) + q] : conj(res[q * (ell + 1) + p]));
             };
             for (int j = 0; j <= ell; ++j)
-                for (int k = 0; k <= ell; ++k) C[j][k] = czero<double>();
+                for (int k = 0; k <= ell; ++k) C[j][k] = czero<ST>();
             int bad = 0;
             for (int j = 1; j <= ell; ++j) {
                 C[j][j] = {1, 0};
                 for (int i = 1; i < j; ++i) {
-                    cx<double> t = czero<double>();
+                    cx<ST> t = czero<ST>();
                     for (int p = 1; p <= i; ++p)
                         for (int q = 1; q <= j; ++q) t = t + conj(C[i][p]) * C[j][q] * G(p, q);
-                    tau[i][j] = (1.0 / sigma[i]) * t;
+                    tau[i][j] = (ST(1) / sigma[i]) * t;
                     for (int k = 1; k <= i; ++k) C[j][k] = C[j][k] - tau[i][j] * C[i][k];
                 }
-                double sg = 0;
-                cx<double> t0 = czero<double>();
+                ST sg = 0;
+                cx<ST> t0 = czero<ST>();
                 for (int p = 1; p <= j; ++p) {
                     for (int q = 1; q <= j; ++q) sg += (conj(C[j][p]) * C[j][q] * G(p, q)).re;
                     t0 = t0 + conj(C[j][p]) * G(p, 0);
                 }
                 sigma[j] = sg;
                 if (!(sg > 0)) bad = 1;
-                gp[j] = (1.0 / (sg > 0 ? sg : 1.0)) * t0;
+                gp[j] = (ST(1) / (sg > 0 ? sg : ST(1))) * t0;
             }
             g[ell] = gp[ell];
             for (int j = ell - 1; j >= 1; --j) {
-                cx<double> t = gp[j];
+                cx<ST> t = gp[j];
                 for (int i = j + 1; i <= ell; ++i) t = t - tau[j][i] * g[i];
                 g[j] = t;
             }
             for (int j = 1; j < ell; ++j) {
-                cx<double> t = g[j + 1];
+                cx<ST> t = g[j + 1];
                 for (int i = j + 1; i < ell; ++i) t = t + tau[j][i] * g[i + 1];
                 gpp[j] = t;
             }
             // x += g1 R0 + sum_{j<ell} gpp_j Rt_j ; R0 -= sum_j gp_j Rt_j ; U0 -= sum_j g_j U_j
-            for (int k = 0; k <= ell; ++k) s_cx[k] = s_cr[k] = czero<double>();
-            s_cx[0] = g[1];
+            cx<ST> tx[kMaxEll + 1], tr[kMaxEll + 1];
+            for (int k = 0; k <= ell; ++k) tx[k] = tr[k] = czero<ST>();
+            tx[0] = g[1];
             for (int j = 1; j < ell; ++j)
-                for (int k = 1; k <= j; ++k) s_cx[k] = s_cx[k] + gpp[j] * C[j][k];
+                for (int k = 1; k <= j; ++k) tx[k] = tx[k] + gpp[j] * C[j][k];
             for (int j = 1; j <= ell; ++j)
-                for (int k = 1; k <= j; ++k) s_cr[k] = s_cr[k] + gp[j] * C[j][k];
-            for (int k = 0; k <= ell; ++k) s_g[k] = g[k];
+                for (int k = 1; k <= j; ++k) tr[k] = tr[k] + gp[j] * C[j][k];
+            for (int k = 0; k <= ell; ++k) {
+                s_cx[k] = ccast<double>(tx[k]);
+                s_cr[k] = ccast<double>(tr[k]);
+                s_g[k] = ccast<double>(g[k]);
+            }
             s_bad = bad;
         }
         __syncthreads();
@@ -457,12 +544,12 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
             return;
         }
-        omega = s_g[ell];
-        cx<double> cx_[kMaxEll + 1], cr[kMaxEll + 1], g[kMaxEll + 1];
+        omega = ccast<SC>(s_g[ell]);
+        cx<SC> cx_[kMaxEll + 1], cr[kMaxEll + 1], g[kMaxEll + 1];
         for (int k = 0; k <= ell; ++k) {
-            cx_[k] = s_cx[k];
-            cr[k] = s_cr[k];
-            g[k] = s_g[k];
+            cx_[k] = ccast<SC>(s_cx[k]);
+            cr[k] = ccast<SC>(s_cr[k]);
+            g[k] = ccast<SC>(s_g[k]);
         }
         for (int i = r0 + tid; i < r1; i += kThreads) {
             cx<TC> xv = ld<TC>(a.x, i), r0v = ld<TC>(a.R[0], i), u0 = ld<TC>(a.U[0], i);
@@ -523,11 +610,16 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     a.part = (double2*)part;
     a.bar = (GridBar*)state;
     if (nc % 2 != 0) return cudaErrorInvalidValue;
-    a.row_bytes = 9 * nc * (cprec == 0 ? 16 : 8);
+    const int eb = cprec == 0 ? 16 : 8;
+    a.row_bytes = 9 * nc * eb;
     a.rows_per_chunk = kChunkBytes / a.row_bytes;
     if (a.rows_per_chunk < 1) return cudaErrorInvalidValue;   // nc too large for a ring slot
+    a.sites_per_chunk = (a.rows_per_chunk - 1) / nc + 2;
+    a.xseg_bytes = nc * eb;
+    a.slot_bytes = kChunkBytes;
     const void* fn = cprec == 0 ? (const void*)coarse_bicgstab_kernel<double> : (const void*)coarse_bicgstab_kernel<float>;
-    const int smem = kStages * kChunkBytes;
+    const int smem = kStages * kChunkBytes + 2 * 9 * a.sites_per_chunk * a.xseg_bytes;
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int grid = coop_grid(fn, smem);

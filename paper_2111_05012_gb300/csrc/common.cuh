@@ -34,12 +34,56 @@ template <typename T> HD T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 template <typename T> HD cx<T> czero() { return {T(0), T(0)}; }
 template <typename T, typename U> HD cx<T> ccast(cx<U> a) { return {T(a.re), T(a.im)}; }
 
+// ---------------------------------------------------------------- double-float
+// An unevaluated sum hi + lo of two floats (about 48 significant bits),
+// with Knuth's two-sum and the FMA-based exact product (Dekker's
+// splitting is not needed with a fused multiply-add).  Used where an FP64
+// accurate result is needed but the FP64 pipe (1/64 of FP32 on this part)
+// would be the bottleneck.
+struct dfloat {
+    float hi, lo;
+    HD dfloat() : hi(0.f), lo(0.f) {}
+    HD dfloat(float h) : hi(h), lo(0.f) {}
+    HD dfloat(float h, float l) : hi(h), lo(l) {}
+};
+DEV dfloat two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+DEV dfloat quick_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+DEV dfloat operator+(dfloat x, dfloat y) {
+    dfloat s = two_sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return quick_two_sum(s.hi, e);
+}
+DEV dfloat operator-(dfloat x) { return {-x.hi, -x.lo}; }
+DEV dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
+DEV dfloat operator*(dfloat x, dfloat y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return quick_two_sum(p, e);
+}
+DEV dfloat& operator+=(dfloat& x, dfloat y) { return x = x + y; }
+DEV double to_double(dfloat x) { return (double)x.hi + (double)x.lo; }
+HD dfloat split_double(double v) {
+    float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
 // ---------------------------------------------------------------- precision tags
 // A tag fixes the storage of fine fields (spinor, links, clover) and the
 // arithmetic type T.
 struct P64 { using T = double; static constexpr int id = 0; };
 struct P32 { using T = float; static constexpr int id = 1; };
 struct P16 { using T = float; static constexpr int id = 2; };
+// FP64-accurate links and clover stored as float hi/lo pairs, double-float arithmetic
+struct PDD { using T = dfloat; static constexpr int id = 3; };
 
 // ---------------------------------------------------------------- geometry
 struct Geom {
@@ -277,6 +321,19 @@ template <> struct GaugeIO<P16> {
     }
 };
 
+// PDD: [mu][9][V] float4 = (re.hi, re.lo, im.hi, im.lo), full matrix
+template <> struct GaugeIO<PDD> {
+    static constexpr size_t bytes_per_link = 144;
+    DEV static void load(const void* base, int V, int mu, int s, cx<dfloat> u[3][3]) {
+        const float4* p = (const float4*)base + (size_t)mu * 9 * V;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float4 t = __ldg(p + (size_t)k * V + s);
+            u[k / 3][k % 3] = {dfloat(t.x, t.y), dfloat(t.z, t.w)};
+        }
+    }
+};
+
 // ---------------------------------------------------------------- clover storage
 // Two 6x6 Hermitian blocks per site (chirality 0: spins 0,1; 1: spins 2,3).
 // Per block 18 real pairs: pairs 0..2 hold the six real diagonal entries,
@@ -324,6 +381,20 @@ template <> struct CloverIO<P16> {
             float2 f = __half22float2(h[(hidx % 8) / 2]);
             pr[k] = f.x;
             pr[k + 1] = f.y;
+        }
+    }
+};
+
+// PDD: [36][V] float4, pair q = (v0.hi, v0.lo, v1.hi, v1.lo)
+template <> struct CloverIO<PDD> {
+    static constexpr size_t bytes_per_site = 576;
+    DEV static void load_block(const void* base, int V, int s, int b, dfloat pr[36]) {
+        const float4* p = (const float4*)base + (size_t)18 * b * V;
+#pragma unroll
+        for (int q = 0; q < 18; ++q) {
+            float4 t = __ldg(p + (size_t)q * V + s);
+            pr[2 * q] = dfloat(t.x, t.y);
+            pr[2 * q + 1] = dfloat(t.z, t.w);
         }
     }
 };

@@ -104,6 +104,12 @@ __global__ void gauge_convert_kernel(Geom g, const double* __restrict__ canon, v
                 for (int q = 0; q < 3; ++q)
                     p[(size_t)q * g.V + s] = make_float4((float)m[4 * q], (float)m[4 * q + 1], (float)m[4 * q + 2],
                                                          (float)m[4 * q + 3]);
+            } else if (prec == 3) {
+                float4* p = (float4*)out + (size_t)mu * 9 * g.V;
+                for (int k = 0; k < 9; ++k) {
+                    dfloat re = split_double(m[2 * k]), im = split_double(m[2 * k + 1]);
+                    p[(size_t)k * g.V + s] = make_float4(re.hi, re.lo, im.hi, im.lo);
+                }
             } else {
                 uint2* p = (uint2*)out + (size_t)mu * 3 * g.V;
                 for (int q = 0; q < 3; ++q) {
@@ -240,6 +246,13 @@ __global__ void clover_build_kernel(Geom g, const void* U64, double kappa, doubl
             double2* p = (double2*)out;
             for (int b = 0; b < 2; ++b)
                 for (int q = 0; q < 18; ++q) p[(size_t)(18 * b + q) * g.V + s] = make_double2(pr[b][2 * q], pr[b][2 * q + 1]);
+        } else if (P::id == 3) {
+            float4* p = (float4*)out;
+            for (int b = 0; b < 2; ++b)
+                for (int q = 0; q < 18; ++q) {
+                    dfloat v0 = split_double(pr[b][2 * q]), v1 = split_double(pr[b][2 * q + 1]);
+                    p[(size_t)(18 * b + q) * g.V + s] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+                }
         } else if (P::id == 1) {
             float4* p = (float4*)out;
             for (int b = 0; b < 2; ++b)
@@ -329,6 +342,71 @@ __global__ void __launch_bounds__(kThreads) dirac_kernel(Geom g, Blocking bk, co
             for (int k = 0; k < 12; ++k) acc[k] = psi[k] - acc[k];
         }
         SpinorIO<P>::store(dst, g.V, s, acc);
+    }
+}
+
+// ------------------------------------------------------------ mixed stencil
+// out (FP64) = D in for an FP32 input whose values are exact: links and
+// clover are FP64 values held as float hi/lo pairs and all arithmetic is
+// double-float, so the result carries about 48 significant bits while the
+// work runs on the FP32 pipe.
+__global__ void __launch_bounds__(kThreads, 2) dirac_mixed_kernel(Geom g, const void* __restrict__ U,
+                                                               const void* __restrict__ C, const void* in,
+                                                               void* out, dfloat kappa) {
+    const int r = blockIdx.y;
+    const char* src = (const char*)in + r * spinor_bytes<P32>(g.V);
+    char* dst = (char*)out + r * spinor_bytes<P64>(g.V);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        int c[4];
+        site_coords(g, s, c);
+        cx<float> pf[12];
+        cx<dfloat> psi[12], acc[12];
+        SpinorIO<P32>::load(src, g.V, s, pf);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) psi[k] = {dfloat(pf[k].re), dfloat(pf[k].im)};
+        clover_apply<PDD>(C, g.V, s, psi, acc);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            float ph;
+            cx<dfloat> u[3][3];
+            int n = neighbour(g, s, c, mu, +1, ph);
+            SpinorIO<P32>::load(src, g.V, n, pf);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) psi[k] = {dfloat(pf[k].re), dfloat(pf[k].im)};
+            GaugeIO<PDD>::load(U, g.V, mu, s, u);
+            hop_accum<dfloat>(acc, psi, u, mu, +1, dfloat(ph) * (-kappa));
+            n = neighbour(g, s, c, mu, -1, ph);
+            SpinorIO<P32>::load(src, g.V, n, pf);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) psi[k] = {dfloat(pf[k].re), dfloat(pf[k].im)};
+            GaugeIO<PDD>::load(U, g.V, mu, n, u);
+            hop_accum<dfloat>(acc, psi, u, mu, -1, dfloat(ph) * (-kappa));
+        }
+        cx<double> o[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[k] = {to_double(acc[k].re), to_double(acc[k].im)};
+        SpinorIO<P64>::store(dst, g.V, s, o);
+    }
+}
+
+// x (FP64 internal) += sum_j c_j z_j for FP32 internal z_j: site by site,
+// because the two internal layouts order the complex components differently
+struct ZList {
+    const void* p[20];
+    double2 c[20];
+};
+__global__ void spinor_axpy_mixed_kernel(Geom g, int k, ZList z, void* x) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        cx<double> acc[12];
+        SpinorIO<P64>::load_rw(x, g.V, s, acc);
+        for (int j = 0; j < k; ++j) {
+            cx<float> v[12];
+            SpinorIO<P32>::load(z.p[j], g.V, s, v);
+            const cx<double> cj = {z.c[j].x, z.c[j].y};
+#pragma unroll
+            for (int q = 0; q < 12; ++q) acc[q] = acc[q] + cj * ccast<double>(v[q]);
+        }
+        SpinorIO<P64>::store(x, g.V, s, acc);
     }
 }
 
@@ -568,12 +646,14 @@ size_t fine_spinor_bytes(int prec, int V) {
 }
 size_t fine_gauge_bytes(int prec, int V) {
     size_t per = prec == 0 ? GaugeIO<P64>::bytes_per_link : prec == 1 ? GaugeIO<P32>::bytes_per_link
-                                                                       : GaugeIO<P16>::bytes_per_link;
+                                                       : prec == 3 ? GaugeIO<PDD>::bytes_per_link
+                                                                   : GaugeIO<P16>::bytes_per_link;
     return 4 * per * (size_t)V;
 }
 size_t fine_clover_bytes(int prec, int V) {
     size_t per = prec == 0 ? CloverIO<P64>::bytes_per_site : prec == 1 ? CloverIO<P32>::bytes_per_site
-                                                                        : CloverIO<P16>::bytes_per_site;
+                                                        : prec == 3 ? CloverIO<PDD>::bytes_per_site
+                                                                    : CloverIO<P16>::bytes_per_site;
     return per * (size_t)V;
 }
 
@@ -625,6 +705,7 @@ cudaError_t launch_clover_build(int prec, const GeomH& gh, const void* U64, doub
     int grid = grid_for(g.V, 128);
     if (prec == 0) clover_build_kernel<P64><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
     else if (prec == 1) clover_build_kernel<P32><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
+    else if (prec == 3) clover_build_kernel<PDD><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
     else clover_build_kernel<P16><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
     return cudaGetLastError();
 }
@@ -638,6 +719,25 @@ cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sb, const void*
     if (prec == 0) return dirac_impl<P64>(g, sb, U, C, in, out, b, kappa, nrhs, st);
     if (prec == 1) return dirac_impl<P32>(g, sb, U, C, in, out, b, kappa, nrhs, st);
     return dirac_impl<P16>(g, sb, U, C, in, out, b, kappa, nrhs, st);
+}
+cudaError_t launch_dirac_mixed(const GeomH& gh, const void* Udd, const void* Cdd, const void* in32, void* out64,
+                               double kappa, int nrhs, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    dim3 grid(grid_for(g.V, kThreads), nrhs);
+    dirac_mixed_kernel<<<grid, kThreads, 0, st>>>(g, Udd, Cdd, in32, out64, split_double(kappa));
+    return cudaGetLastError();
+}
+cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, const void* const* z, void* x,
+                                     cudaStream_t st) {
+    if (k < 1 || k > 20) return cudaErrorInvalidValue;
+    ZList zl;
+    for (int j = 0; j < k; ++j) {
+        zl.p[j] = z[j];
+        zl.c[j] = c[j];
+    }
+    Geom g = make_geom(gh);
+    spinor_axpy_mixed_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x);
+    return cudaGetLastError();
 }
 cudaError_t launch_sap_half(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode, const void* U,
                             const void* C, const void* b, void* x, double kappa, cudaStream_t st) {

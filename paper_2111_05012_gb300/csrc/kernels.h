@@ -13,7 +13,8 @@ struct BlockH {
     int b[4];
 };
 
-// precision ids: 0 = F64, 1 = F32, 2 = F16 (fine storage); coarse: 0 = F64, 1 = F32
+// precision ids: 0 = F64, 1 = F32, 2 = F16, 3 = FP64 values as float hi/lo pairs (links, clover);
+// coarse: 0 = F64, 1 = F32
 size_t fine_spinor_bytes(int prec, int V);
 size_t fine_gauge_bytes(int prec, int V);
 size_t fine_clover_bytes(int prec, int V);
@@ -35,6 +36,13 @@ cudaError_t launch_clover_expand(const GeomH& g, const void* C64, double* out, c
 // out = D in (sap_block != NULL: hops between blocks removed); if b != NULL, out = b - D in
 cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sap_block, const void* U, const void* C,
                          const void* in, void* out, const void* b, double kappa, int nrhs, cudaStream_t s);
+// out (FP64 internal) = D in (FP32 internal, exact values) with FP64-accurate double-float arithmetic;
+// Udd / Cdd are the prec-3 (float hi/lo pair) link and clover fields
+cudaError_t launch_dirac_mixed(const GeomH& g, const void* Udd, const void* Cdd, const void* in32, void* out64,
+                               double kappa, int nrhs, cudaStream_t s);
+// x (FP64 internal) += sum_j c[j] z[j] for k <= 20 FP32 internal fields z[j] (site-wise)
+cudaError_t launch_spinor_axpy_mixed(const GeomH& g, int k, const double2* c, const void* const* z, void* x,
+                                     cudaStream_t s);
 // one SAP half sweep on the domains of one colour (fused residual + MR):
 //   r = b - D x on the domain, z = MR_nmr(D_SAP, r), x += z
 //   x_mode 0: x holds the iterate; 1: x is zero everywhere; 2: x is zero on the active domains

@@ -43,6 +43,20 @@ def test_apply_D(field, prec):
     assert rel(got, ref) < TOL[prec]
 
 
+def test_apply_D_mixed_fp64_accurate(field):
+    # FP32 input taken as exact, FP64-accurate double-float stencil, double output:
+    # compared with the oracle applied to the same (FP32-rounded) input
+    c = field.c
+    psi = np.stack([li.rhs(field.dims, 5, i) for i in range(2)])
+    x = to_dev(psi, "float32")
+    exact_in = from_dev(x, (2,) + field.shape4 + (12,))
+    ref = np.stack([field.op.apply(p) for p in exact_in])
+    import torch
+    y = torch.zeros(x.numel(), dtype=torch.float64, device="cuda")
+    c.amg_apply_D(field.d, x, y, 2, c.AMG_F64X)
+    assert rel(from_dev(y, (2,) + field.shape4 + (12,)), ref) < 1e-13
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_apply_Dsap(field, prec):
     c = field.c
