@@ -256,20 +256,26 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
-    # roofline of the SAP half-sweep kernel (dominant kernel of the solve),
-    # from the smoother phase time: 2 * sap_iters launches per preconditioner call
+    # Roofline of the dominant kernel of the solve, the fused SAP half sweep
+    # (one launch = one colour of domains).  Average launch duration from the
+    # library's CUDA-event smoother timer: 2 * sap_iters launches per cycle.
+    # Algorithmic work per active site (standard Wilson-clover count, 1872
+    # flop per site for D): residual b - D x (1872 + 24) + 6 minimal-residual
+    # steps on D_SAP (1494 for the in-domain hops and clover of a 4^4 domain,
+    # + 336 for the two dot products and two updates) = 12876 flop; half the
+    # sites are active per launch.  12.8 flop/byte puts it on the ALU side of
+    # the ridge, so it is reported against the FP32 FMA peak:
+    # 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (nominal).
     p = make_params(capi, prec)
     iters = np.mean([i["iters"] for i in infos])
     smooth_ms = np.mean([i["ms_smoother"] for i in infos])
     launches = 2 * p.sap_iters * iters
     sap_launch_us = smooth_ms / launches * 1e3
-    # algorithmic bytes per launch: active half of the sites, per site gauge (own
-    # links + backward links entering through faces), clover, b, x in/out, x halo
-    bps = {capi.AMG_F32: 192 + 48 + 288 + 96 + 96 + 192 + 96, capi.AMG_F16: 96 + 24 + 144 + 52 * 4 + 104,
-           capi.AMG_F64: 576 + 144 + 576 + 192 * 4 + 384}[prec]
-    bytes_launch = bps * V / 2
-    peak, peak_kind = _peaks()
-    achieved = bytes_launch / (sap_launch_us * 1e-6) / 1e9
+    flop_site = 1872 + 24 + p.mr_iters * (1494 + 336)
+    flop_launch = flop_site * V / 2
+    achieved = flop_launch / (sap_launch_us * 1e-6) / 1e12
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    hbm_peak, peak_kind = _peaks()
 
     line = {
         "metric": METRIC, "value": per_rhs, "unit": "ms/RHS", "n_gpus": world, "steps": args.steps,
@@ -284,9 +290,11 @@ def main():
                    "phase_ms": {k: float(np.mean([i[k] for i in infos])) for k in
                                 ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other")},
                    "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
-        "roofline": {"kernel": "sap_half_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "avg_launch_us": sap_launch_us, "bytes_per_launch": bytes_launch},
+        "roofline": {"kernel": "sap_half_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": "FP32 FMA nominal from unit counts and 2.07 GHz",
+                     "avg_launch_us": sap_launch_us, "flop_per_launch": flop_launch,
+                     "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind},
         "e2e": {"value": e2e_ms, "unit": "ms/RHS", "h2d_bytes_per_step": int(hb[0].numel() * 8),
                 "d2h_bytes_per_step": int(hx.numel() * 8)},
         "gpu_launches": None,

@@ -90,6 +90,9 @@ typedef struct {
     int prec_smoother;                  /* fine D / SAP / R / P precision: AMG_F64, AMG_F32, AMG_F16 [AMG_F32] */
     int prec_coarse;                    /* coarse operators above the coarsest: AMG_F64, AMG_F32, AMG_BF16 [AMG_F32] */
     int prec_coarsest;                  /* coarsest-level solve: AMG_F64 or AMG_F32 [AMG_F32] */
+    int sap_variant;                    /* SAP kernel: -1 autotune at setup (times both, keeps the faster),
+                                           0 operator read from global memory, 1 operator staged in shared
+                                           memory (FP32/FP16, blocks <= 256 sites) [-1] */
 } amg_params;
 
 typedef struct {

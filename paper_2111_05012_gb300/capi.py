@@ -47,6 +47,7 @@ class amg_params(ctypes.Structure):
         ("prec_smoother", ctypes.c_int),
         ("prec_coarse", ctypes.c_int),
         ("prec_coarsest", ctypes.c_int),
+        ("sap_variant", ctypes.c_int),
     ]
 
 

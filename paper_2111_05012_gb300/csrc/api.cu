@@ -216,6 +216,7 @@ struct amg_hierarchy {
     int err_flag_host = 0;
     DevBuf err_flag;
     int coarse_cycles = 0;
+    int sap_variant[3] = {0, 0, 0};   // chosen SAP kernel per smoother precision
     int* hstate = nullptr;   // pinned mirror of the coarse solver state words
     ~amg_hierarchy() {
         if (hstate) cudaFreeHost(hstate);
@@ -267,12 +268,13 @@ amg_status fine_D(amg_hierarchy* h, int prec, const void* in, void* out, const v
 amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_zero, cudaStream_t s) {
     amg_dirac* d = h->d;
     h->timer.start(PH_SMOOTH, s);
+    const int var = h->sap_variant[prec];
     for (int i = 0; i < h->p.sap_iters; ++i) {
         const bool first = x_zero && i == 0;
-        CK(launch_sap_half(prec, fine_geom(h), h->blk[0], 0, h->p.mr_iters, first ? 1 : 0, d->gauge->U[prec].p,
-                           d->C[prec].p, b, x, d->kappa, s));
-        CK(launch_sap_half(prec, fine_geom(h), h->blk[0], 1, h->p.mr_iters, first ? 2 : 0, d->gauge->U[prec].p,
-                           d->C[prec].p, b, x, d->kappa, s));
+        CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], 0, h->p.mr_iters, first ? 1 : 0,
+                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, s));
+        CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], 1, h->p.mr_iters, first ? 2 : 0,
+                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, s));
     }
     if (h->p.sap_iters == 0 && x_zero) CK(cudaMemsetAsync(x, 0, fine_spinor_bytes(prec, fine_geom(h).V), s));
     h->timer.stop(s);
@@ -592,6 +594,53 @@ amg_status normalise_into(amg_hierarchy* h, int prec, const void* src, void* dst
     return AMG_OK;
 }
 
+// Autotuner: for every smoother precision the hierarchy uses, time the SAP
+// half-sweep variants on this lattice and blocking (zero fields, 3 timed
+// launches each after one warm-up) and keep the faster one.
+amg_status tune_kernels(amg_hierarchy* h) {
+    const GeomH& g = fine_geom(h);
+    amg_dirac* d = h->d;
+    int precs[2] = {h->fp, h->vp};
+    for (int pr : precs) {
+        if (h->p.sap_variant >= 0) {
+            h->sap_variant[pr] = sap_staged_supported(pr, h->blk[0]) ? h->p.sap_variant : 0;
+            continue;
+        }
+        if (!sap_staged_supported(pr, h->blk[0])) {
+            h->sap_variant[pr] = 0;
+            continue;
+        }
+        CK(cudaMemset(h->fb[pr].p, 0, fine_spinor_bytes(pr, g.V)));
+        CK(cudaMemset(h->fx[pr].p, 0, fine_spinor_bytes(pr, g.V)));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_v = 0;
+        for (int v = 0; v <= 1; ++v) {
+            float ms = 0;
+            for (int rep = 0; rep < 4; ++rep) {
+                CK(cudaEventRecord(e0, 0));
+                CK(launch_sap_half_variant(v, pr, g, h->blk[0], 0, h->p.mr_iters, 0, d->gauge->U[pr].p, d->C[pr].p,
+                                           h->fb[pr].p, h->fx[pr].p, d->kappa, 0));
+                CK(cudaEventRecord(e1, 0));
+                CK(cudaEventSynchronize(e1));
+                float t = 0;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                if (rep > 0) ms += t;
+            }
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->sap_variant[pr] = best_v;
+    }
+    return AMG_OK;
+}
+
 amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out, amg_hierarchy** hp) {
     if (!d || !out) return fail(AMG_EINVAL, "NULL argument");
     TRY(check_params(d->gauge->lat->g, p));
@@ -603,6 +652,7 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
     *hp = h;
     amg_status st = build_levels(h);
     if (st == AMG_OK) st = alloc_workspaces(h);
+    if (st == AMG_OK) st = tune_kernels(h);
     if (st != AMG_OK) {
         delete h;
         *hp = nullptr;
@@ -640,6 +690,7 @@ void amg_params_default(amg_params* p) {
     p->prec_smoother = AMG_F32;
     p->prec_coarse = AMG_F32;
     p->prec_coarsest = AMG_F32;
+    p->sap_variant = -1;
 }
 
 amg_status amg_lattice_create(const int dims[4], int antiperiodic_t, amg_lattice** out) {

@@ -539,6 +539,239 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
     }
 }
 
+// ------------------------------------------------------------ SAP half sweep, staged operator
+// Same algorithm as sap_half_kernel, but the domain's own forward links and
+// clover are copied to shared memory once, so the nmr minimal-residual steps
+// read the operator only from shared memory; the block reduction uses one
+// barrier per step (double-buffered partials).  FP32 and FP16 storage.
+template <class P> struct Staged;
+template <> struct Staged<P32> {
+    using LC = float4;   // link chunk: 3 per link
+    using CC = float4;   // clover chunk: 18 per site
+    static constexpr int kLinkChunks = 3, kCloverChunks = 18;
+    DEV static void link(const LC* sl, int vbp, int mu, int l, cx<float> u[3][3]) {
+        const LC* p = sl + (size_t)mu * 3 * vbp;
+        float4 a = p[l], b = p[vbp + l], c = p[2 * vbp + l];
+        u[0][0] = {a.x, a.y};
+        u[0][1] = {a.z, a.w};
+        u[0][2] = {b.x, b.y};
+        u[1][0] = {b.z, b.w};
+        u[1][1] = {c.x, c.y};
+        u[1][2] = {c.z, c.w};
+        reconstruct_row2(u);
+    }
+    DEV static void clover_block(const CC* sc, int vbp, int l, int b, float pr[36]) {
+        const CC* p = sc + (size_t)9 * b * vbp;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            float4 t = p[q * vbp + l];
+            pr[4 * q] = t.x;
+            pr[4 * q + 1] = t.y;
+            pr[4 * q + 2] = t.z;
+            pr[4 * q + 3] = t.w;
+        }
+    }
+};
+template <> struct Staged<P16> {
+    using LC = uint2;   // 3 per link
+    using CC = uint4;   // 9 per site
+    static constexpr int kLinkChunks = 3, kCloverChunks = 9;
+    DEV static void link(const LC* sl, int vbp, int mu, int l, cx<float> u[3][3]) {
+        const LC* p = sl + (size_t)mu * 3 * vbp;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            uint2 t = p[q * vbp + l];
+            const __half2* h = reinterpret_cast<const __half2*>(&t);
+            float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]);
+            int k0 = 2 * q, k1 = 2 * q + 1;
+            u[k0 / 3][k0 % 3] = {f0.x, f0.y};
+            u[k1 / 3][k1 % 3] = {f1.x, f1.y};
+        }
+        reconstruct_row2(u);
+    }
+    DEV static void clover_block(const CC* sc, int vbp, int l, int b, float pr[36]) {
+#pragma unroll
+        for (int k = 0; k < 36; k += 2) {
+            int hidx = 36 * b + k;
+            uint4 t = sc[(hidx / 8) * vbp + l];
+            const __half2* h = reinterpret_cast<const __half2*>(&t);
+            float2 f = __half22float2(h[(hidx % 8) / 2]);
+            pr[k] = f.x;
+            pr[k + 1] = f.y;
+        }
+    }
+};
+
+template <class P>
+__global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
+    sap_half_staged_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode, const void* __restrict__ U,
+                           const void* __restrict__ C, const void* __restrict__ b, void* x, float kappa) {
+    using S = Staged<P>;
+    using LC = typename S::LC;
+    using CC = typename S::CC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int vbp = blockDim.x;
+    LC* sl = reinterpret_cast<LC*>(smem_raw);                                     // [4*3][vbp]
+    CC* sc = reinterpret_cast<CC*>(sl + (size_t)4 * S::kLinkChunks * vbp);        // [kCloverChunks][vbp]
+    cx<float>* rsh = reinterpret_cast<cx<float>*>(sc + (size_t)S::kCloverChunks * vbp);   // [12][vbp]
+    float* red = reinterpret_cast<float*>(rsh + 12 * vbp);                      // [2][3][32]
+
+    const int k = blockIdx.x;
+    const int h0 = bk.C[0] / 2;
+    int rest = k / h0;
+    int X1 = rest % bk.C[1];
+    rest /= bk.C[1];
+    int X2 = rest % bk.C[2];
+    int X3 = rest / bk.C[2];
+    int X0 = 2 * (k % h0) + ((X1 + X2 + X3 + colour) & 1);
+    const int Xi = X0 + bk.C[0] * (X1 + bk.C[1] * (X2 + bk.C[2] * X3));
+
+    const int l = threadIdx.x, lane = l & 31, warp = l >> 5, nw = (blockDim.x + 31) >> 5;
+    const bool active = l < bk.Vb;
+    int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
+    const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
+    cx<float> r[12], z[12], Ar[12];
+    if (active) {
+        s = block_site(g, bk, Xi, l, c);
+        for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
+        // stage this site's forward links and clover
+        const LC* gl = (const LC*)U;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+            for (int q = 0; q < S::kLinkChunks; ++q)
+                sl[(mu * S::kLinkChunks + q) * vbp + l] = __ldg(gl + ((size_t)mu * S::kLinkChunks + q) * g.V + s);
+        const CC* gc = (const CC*)C;
+#pragma unroll
+        for (int q = 0; q < S::kCloverChunks; ++q) sc[q * vbp + l] = __ldg(gc + (size_t)q * g.V + s);
+        // r = b - D x at this site (global operator; hops may leave the domain)
+        SpinorIO<P>::load(b, g.V, s, r);
+        if (x_mode != 1) {
+            cx<float> psi[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) Ar[q] = czero<float>();
+            if (x_mode == 0) {
+                SpinorIO<P>::load(x, g.V, s, psi);
+                clover_apply<P>(C, g.V, s, psi, Ar);
+            }
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                float ph;
+                cx<float> u[3][3];
+                if (x_mode == 0 || lc[mu] == bk.b[mu] - 1) {
+                    int n = neighbour(g, s, c, mu, +1, ph);
+                    SpinorIO<P>::load(x, g.V, n, psi);
+                    GaugeIO<P>::load(U, g.V, mu, s, u);
+                    hop_accum<float>(Ar, psi, u, mu, +1, -kappa * ph);
+                }
+                if (x_mode == 0 || lc[mu] == 0) {
+                    int n = neighbour(g, s, c, mu, -1, ph);
+                    SpinorIO<P>::load(x, g.V, n, psi);
+                    GaugeIO<P>::load(U, g.V, mu, n, u);
+                    hop_accum<float>(Ar, psi, u, mu, -1, -kappa * ph);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) r[q] = r[q] - Ar[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            z[q] = czero<float>();
+            rsh[q * vbp + l] = r[q];
+        }
+    }
+    for (int it = 0; it < nmr; ++it) {
+        __syncthreads();   // r (and, first time, the staged operator) visible
+        float part[3] = {0.f, 0.f, 0.f};
+        if (active) {
+            float pr[36];
+            S::clover_block(sc, vbp, l, 0, pr);
+            clover_block_apply<float>(pr, r, Ar);
+            S::clover_block(sc, vbp, l, 1, pr);
+            clover_block_apply<float>(pr, r + 6, Ar + 6);
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                cx<float> u[3][3], psi[12];
+                if (lc[mu] != bk.b[mu] - 1) {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l + lstr[mu]];
+                    S::link(sl, vbp, mu, l, u);
+                    hop_accum<float>(Ar, psi, u, mu, +1, -kappa);
+                }
+                if (lc[mu] != 0) {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l - lstr[mu]];
+                    S::link(sl, vbp, mu, l - lstr[mu], u);
+                    hop_accum<float>(Ar, psi, u, mu, -1, -kappa);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                cx<float> t = cmulc(Ar[q], r[q]);
+                part[0] += t.re;
+                part[1] += t.im;
+                part[2] += norm2(Ar[q]);
+            }
+        }
+        // one-barrier block reduction into buffer (it & 1)
+        float* rb = red + (it & 1) * 96;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float v = warp_sum(part[q]);
+            if (lane == 0) rb[q * 32 + warp] = v;
+        }
+        __syncthreads();
+        float tot[3] = {0.f, 0.f, 0.f};
+        for (int w = 0; w < nw; ++w) {
+            tot[0] += rb[w];
+            tot[1] += rb[32 + w];
+            tot[2] += rb[64 + w];
+        }
+        cx<float> alpha = czero<float>();
+        if (tot[2] > 0.f) alpha = {tot[0] / tot[2], tot[1] / tot[2]};
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                z[q] = z[q] + alpha * r[q];
+                r[q] = r[q] - alpha * Ar[q];
+                rsh[q * vbp + l] = r[q];
+            }
+        }
+    }
+    if (active) {
+        if (x_mode == 0) {
+            cx<float> x0[12];
+            SpinorIO<P>::load(x, g.V, s, x0);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) z[q] = z[q] + x0[q];
+        }
+        SpinorIO<P>::store(x, g.V, s, z);
+    }
+}
+
+template <class P>
+size_t sap_staged_smem(int vbp) {
+    using S = Staged<P>;
+    return (size_t)vbp * (4 * S::kLinkChunks * sizeof(typename S::LC) + S::kCloverChunks * sizeof(typename S::CC) +
+                          12 * sizeof(cx<float>)) +
+           2 * 96 * sizeof(float);
+}
+
+template <class P>
+cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
+                                 const void* C, const void* b, void* x, double kappa, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk = make_blocking(gh, bh);
+    int threads = (bk.Vb + 31) / 32 * 32;
+    if (threads > 256) return cudaErrorInvalidValue;
+    size_t smem = sap_staged_smem<P>(threads);
+    cudaError_t e =
+        cudaFuncSetAttribute(sap_half_staged_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sap_half_staged_kernel<P><<<bk.Vc / 2, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x, (float)kappa);
+    return cudaGetLastError();
+}
+
 template <class P>
 cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
                           const void* C, const void* b, void* x, double kappa, cudaStream_t st) {
@@ -738,6 +971,17 @@ cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, c
     Geom g = make_geom(gh);
     spinor_axpy_mixed_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x);
     return cudaGetLastError();
+}
+cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const BlockH& bk, int colour, int nmr,
+                                    int x_mode, const void* U, const void* C, const void* b, void* x, double kappa,
+                                    cudaStream_t st) {
+    if (variant == 1 && prec == 1) return sap_half_staged_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+    if (variant == 1 && prec == 2) return sap_half_staged_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+    return launch_sap_half(prec, g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+}
+bool sap_staged_supported(int prec, const BlockH& bk) {
+    int vb = bk.b[0] * bk.b[1] * bk.b[2] * bk.b[3];
+    return (prec == 1 || prec == 2) && vb <= 256;
 }
 cudaError_t launch_sap_half(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode, const void* U,
                             const void* C, const void* b, void* x, double kappa, cudaStream_t st) {

@@ -49,6 +49,13 @@ cudaError_t launch_spinor_axpy_mixed(const GeomH& g, int k, const double2* c, co
 cudaError_t launch_sap_half(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode,
                             const void* U, const void* C, const void* b, void* x, double kappa, cudaStream_t s);
 
+// variant 0: operator read from global memory in every MR step (all precisions);
+// variant 1: domain operator staged in shared memory (FP32 / FP16, blocks <= 256 sites)
+cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const BlockH& bk, int colour, int nmr,
+                                    int x_mode, const void* U, const void* C, const void* b, void* x, double kappa,
+                                    cudaStream_t s);
+bool sap_staged_supported(int prec, const BlockH& bk);
+
 // ---- transfer (fine level 0 -> 1) ----
 // fprec: field precision (0/1/2), vprec: test-vector precision (0/1), cprec: coarse precision (0/1)
 cudaError_t launch_restrict_fine(int fprec, int vprec, int cprec, const GeomH& g, const BlockH& bk, int nvec,

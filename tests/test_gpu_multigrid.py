@@ -90,11 +90,13 @@ def test_restrict_prolong_coarse_apply(mgcase, prec):
     c.amg_hierarchy_destroy(h)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1, 2])
-def test_sap(mgcase, prec):
+def test_sap(mgcase, prec, variant):
     f = mgcase
     c = f.c
-    h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, prec), [li.to_interleaved(f.v0)])
+    h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, prec, sap_variant=variant),
+                                 [li.to_interleaved(f.v0)])
     b = li.rhs(f.dims, 11).reshape(f.shape4 + (12,))
     ref = osol.sap(f.op, f.block, b, 4, 6)
     dt = "float64" if prec == 0 else "float32"
