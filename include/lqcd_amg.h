@@ -145,6 +145,24 @@ amg_status amg_dirac_get_clover(amg_dirac* d, double* host_out);
  * in and out must not alias. */
 amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s);
 
+/* out = D in, exactly as amg_apply_D, but without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate, e.g. a process whose device memory is fully reserved by a
+ * caching allocator or a latency-critical loop that must not pay the
+ * device-wide synchronisation of cudaMalloc/cudaFree.  amg_apply_D converts
+ * the canonical vectors to and from the internal layout in two work fields
+ * the library allocates on first use; this variant keeps those two fields in
+ * one static device array of 24 MiB (12 MiB each) that every GPU loading the
+ * library holds until exit.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) once for that device; make that first
+ * call before any stream capture.  Every call shares the array, so calls that
+ * overlap on the GPU (different streams, or host threads) race: serialise
+ * them.  nrhs * fine_field_bytes(prec) must be <= 12 MiB, where a field is
+ * 192 (AMG_F64), 96 (AMG_F32) or 52 (AMG_F16) bytes per site; larger calls
+ * fail with AMG_EINVAL.  in, out: canonical device vectors as for
+ * amg_apply_D (element type double for AMG_F64, float otherwise). */
+amg_status amg_apply_D_noalloc(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s);
+
 /* out = D_SAP in: D with every hop between different blocks of size block[4]
  * switched off (Sec. 3, SAP paragraph).  block must tile the lattice with at
  * least two blocks per direction. */

@@ -87,6 +87,7 @@ PROTOTYPES = {
     "amg_dirac_destroy": (None, [_vp]),
     "amg_dirac_get_clover": (_i, [_vp, _dp]),
     "amg_apply_D": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "amg_apply_D_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "amg_apply_Dsap": (_i, [_vp, _ip, _vp, _vp, _i, _i, _vp]),
     "amg_setup": (_i, [_vp, ctypes.POINTER(amg_params), ctypes.POINTER(_dp), ctypes.POINTER(_vp)]),
     "amg_setup_from_vectors": (_i, [_vp, ctypes.POINTER(amg_params), ctypes.POINTER(_dp), ctypes.POINTER(_vp)]),
@@ -203,6 +204,10 @@ def amg_dirac_get_clover(d, volume):
 
 def amg_apply_D(d, inp, out, nrhs=1, prec=AMG_F64, stream=None):
     _check(load().amg_apply_D(d, _ptr(inp), _ptr(out), int(nrhs), int(prec), _stream(stream)))
+
+
+def amg_apply_D_noalloc(d, inp, out, nrhs=1, prec=AMG_F64, stream=None):
+    _check(load().amg_apply_D_noalloc(d, _ptr(inp), _ptr(out), int(nrhs), int(prec), _stream(stream)))
 
 
 def amg_apply_Dsap(d, block, inp, out, nrhs=1, prec=AMG_F64, stream=None):

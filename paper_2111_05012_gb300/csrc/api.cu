@@ -663,6 +663,13 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
 
 }  // namespace
 
+// accessors used by the allocation-free entry point (noalloc.cu)
+const GeomH* amg_internal_geom(const amg_dirac* d) { return &d->gauge->lat->g; }
+const void* amg_internal_links(const amg_dirac* d, int prec) { return d->gauge->U[prec].p; }
+const void* amg_internal_clover(const amg_dirac* d, int prec) { return d->C[prec].p; }
+double amg_internal_kappa(const amg_dirac* d) { return d->kappa; }
+void amg_internal_set_error(const char* msg) { g_err = msg; }
+
 // ================================================================ C ABI
 extern "C" {
 
