@@ -67,6 +67,7 @@ typedef struct amg_lattice amg_lattice;
 typedef struct amg_gauge amg_gauge;
 typedef struct amg_dirac amg_dirac;
 typedef struct amg_hierarchy amg_hierarchy;
+typedef struct amg_nn amg_nn;
 typedef struct CUstream_st* amg_stream;   /* = cudaStream_t */
 
 /* Multigrid parameters (Sec. 3; numbers in brackets are defaults from
@@ -106,6 +107,8 @@ typedef struct {
     double ms_restrict_prolong; /* time in restriction + prolongation */
     double ms_other;            /* everything else (outer Krylov, residuals, conversions) */
     int coarse_cycles;          /* total BiCGStab(l) cycles on the coarsest level */
+    int used_nn;                /* 1 if the learned correction was part of the preconditioner */
+    int nn_fallback;            /* 1 if the solve was redone with the plain cycle */
 } amg_solve_info;
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -230,6 +233,50 @@ amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_
 /* x = M b: one application of the multigrid preconditioner (Sec. 3 steps
  * (1) and (2)).  Canonical double vectors. */
 amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_stream s);
+
+/* ---- learned preconditioner -------------------------------------------- */
+/* The paper's preconditioner slot (Sec. 3 steps (1)-(2)) extended by a
+ * gauge-equivariant network of parallel-transport convolution layers
+ *   out^a(x) = sum_b sum_d W_d^{ab} (T_d in^b)(x),
+ * T_0 = 1, (T_{+mu} f)(x) = U_mu(x) f(x+mu), (T_{-mu} f)(x) = U_mu(x-mu)^dag f(x-mu)
+ * (fermion boundary phase as in Eq. 1), d = 0 self, 1+mu forward, 5+mu
+ * backward; W_d^{ab} a complex 4x4 spin matrix.  Weights are kept in FP32 on
+ * the host, applied in bfloat16 with FP32 accumulation. */
+
+/* Network with nlayers linear layers, channels[0] = channels[nlayers] = 1,
+ * 1..4 channels per layer.  weights: host floats, layer after layer,
+ * [C_out][C_in][9][4][4][re, im] (copied). */
+amg_status amg_nn_create(amg_dirac* d, int nlayers, const int* channels, const float* weights, amg_nn** out);
+void amg_nn_destroy(amg_nn* nn);
+
+/* Current weights in the layout of amg_nn_create; effective != 0 returns the
+ * bfloat16-rounded values the kernels apply. */
+amg_status amg_nn_get_weights(amg_nn* nn, int effective, float* host_out);
+
+/* One layer: in = C_in canonical float fields, out = C_out fields (device). */
+amg_status amg_nn_layer_forward(amg_nn* nn, int layer, const float* in, float* out, amg_stream s);
+
+/* Backward of one layer for an output gradient grad_out (dL/d conj(out)):
+ * grad_in (may be NULL) = L^dag grad_out (C_in fields, device), grad_w (host
+ * doubles, may be NULL) = dL/d conj(W) in the weight layout
+ * (d/dRe W = 2 Re, d/dIm W = 2 Im).  Synchronises the stream. */
+amg_status amg_nn_layer_backward(amg_nn* nn, int layer, const float* in, const float* grad_out, float* grad_in,
+                                 double* grad_w, amg_stream s);
+
+/* out = N(in) for one canonical float field. */
+amg_status amg_nn_apply(amg_nn* nn, const float* in, float* out, amg_stream s);
+
+/* One Adam step (lr, betas 0.9/0.999) on npairs (residual, error) pairs
+ * (canonical float fields, device) for the loss mean ||N(r) - e||^2/||e||^2;
+ * loss_out (may be NULL) receives the batch loss before the step. */
+amg_status amg_nn_train_step(amg_nn* nn, const float* r, const float* e, int npairs, double lr, double* loss_out,
+                             amg_stream s);
+
+/* Use the network inside the solve's preconditioner (NULL removes it):
+ * z = M v + N(v - D M v) with the FP32 cycle M.  If a solve with it misses
+ * the tolerance or breaks down, amg_solve redoes it with the plain cycle
+ * (info->nn_fallback = 1).  Requires prec_smoother = AMG_F32. */
+amg_status amg_hierarchy_set_nn(amg_hierarchy* h, amg_nn* nn);
 
 /* ---- solve ------------------------------------------------------------- */
 

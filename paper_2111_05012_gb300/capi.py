@@ -63,6 +63,8 @@ class amg_solve_info(ctypes.Structure):
         ("ms_restrict_prolong", ctypes.c_double),
         ("ms_other", ctypes.c_double),
         ("coarse_cycles", ctypes.c_int),
+        ("used_nn", ctypes.c_int),
+        ("nn_fallback", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -103,6 +105,14 @@ PROTOTYPES = {
     "amg_sap": (_i, [_vp, _vp, _vp, _i, _vp]),
     "amg_precondition": (_i, [_vp, _vp, _vp, _vp]),
     "amg_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, ctypes.POINTER(amg_solve_info), _vp]),
+    "amg_nn_create": (_i, [_vp, _i, _ip, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
+    "amg_nn_destroy": (None, [_vp]),
+    "amg_nn_get_weights": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_float)]),
+    "amg_nn_layer_forward": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "amg_nn_layer_backward": (_i, [_vp, _i, _vp, _vp, _vp, _dp, _vp]),
+    "amg_nn_apply": (_i, [_vp, _vp, _vp, _vp]),
+    "amg_nn_train_step": (_i, [_vp, _vp, _vp, _i, _d, _dp, _vp]),
+    "amg_hierarchy_set_nn": (_i, [_vp, _vp]),
 }
 
 _lib = None
@@ -301,3 +311,55 @@ def amg_solve(h, b, x, nrhs=1, tol=1e-10, maxit=500, use_x0=False, stream=None, 
     if st != AMG_OK and (st != AMG_NOT_CONVERGED or raise_on_nonconv):
         _check(st)
     return st, info
+
+
+# ---- learned preconditioner ----
+
+def nn_weight_sizes(channels):
+    return [channels[l + 1] * channels[l] * 9 * 16 * 2 for l in range(len(channels) - 1)]
+
+
+def amg_nn_create(d, channels, weights):
+    """channels e.g. [1, 4, 1]; weights: flat float array (layer after layer)."""
+    w = np.ascontiguousarray(weights, dtype=np.float32).reshape(-1)
+    assert w.size == sum(nn_weight_sizes(channels))
+    h = _vp()
+    _check(load().amg_nn_create(d, len(channels) - 1, (ctypes.c_int * len(channels))(*channels),
+                                w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(h)))
+    return h
+
+
+def amg_nn_destroy(nn):
+    load().amg_nn_destroy(nn)
+
+
+def amg_nn_get_weights(nn, channels, effective=True):
+    out = np.empty(sum(nn_weight_sizes(channels)), dtype=np.float32)
+    _check(load().amg_nn_get_weights(nn, int(bool(effective)), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def amg_nn_layer_forward(nn, layer, inp, out, stream=None):
+    _check(load().amg_nn_layer_forward(nn, int(layer), _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def amg_nn_layer_backward(nn, layer, inp, grad_out, grad_in=None, want_wgrad=True, wsize=None, stream=None):
+    gw = np.zeros(wsize, dtype=np.float64) if want_wgrad else None
+    _check(load().amg_nn_layer_backward(nn, int(layer), _ptr(inp), _ptr(grad_out), _ptr(grad_in),
+                                        gw.ctypes.data_as(_dp) if gw is not None else None, _stream(stream)))
+    return gw
+
+
+def amg_nn_apply(nn, inp, out, stream=None):
+    _check(load().amg_nn_apply(nn, _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def amg_nn_train_step(nn, r, e, npairs, lr=1e-3, stream=None):
+    loss = ctypes.c_double()
+    _check(load().amg_nn_train_step(nn, _ptr(r), _ptr(e), int(npairs), float(lr), ctypes.byref(loss),
+                                    _stream(stream)))
+    return loss.value
+
+
+def amg_hierarchy_set_nn(h, nn):
+    _check(load().amg_hierarchy_set_nn(h, nn))

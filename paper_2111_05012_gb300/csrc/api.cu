@@ -1,8 +1,9 @@
 // C ABI of the library (include/lqcd_amg.h): handles, the adaptive setup,
 // the multigrid cycle and the Krylov solvers, all driving the kernels of
 // fine.cu, transfer.cu, coarse.cu and blas.cu on one stream.
-#include "lqcd_amg.h"
+#include "internal.h"
 #include "kernels.h"
+#include "lqcd_amg.h"
 
 #include <chrono>
 #include <cmath>
@@ -34,41 +35,6 @@ amg_status fail(amg_status st, const std::string& msg) {
         amg_status s_ = (x);          \
         if (s_ != AMG_OK) return s_;  \
     } while (0)
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t n = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) {
-        o.p = nullptr;
-        o.n = 0;
-    }
-    DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) {
-            if (p) cudaFree(p);
-            p = o.p;
-            n = o.n;
-            o.p = nullptr;
-            o.n = 0;
-        }
-        return *this;
-    }
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    cudaError_t ensure(size_t bytes) {
-        if (bytes <= n) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
-        if (e == cudaSuccess) n = bytes;
-        return e;
-    }
-    template <typename T> T* as() const { return (T*)p; }
-};
 
 int coarse_elem_bytes(int prec) { return prec == 0 ? 16 : 8; }
 int vec_prec_of(int fine_prec) { return fine_prec == 0 ? 0 : 1; }
@@ -217,6 +183,8 @@ struct amg_hierarchy {
     DevBuf err_flag;
     int coarse_cycles = 0;
     int sap_variant[3] = {0, 0, 0};   // chosen SAP kernel per smoother precision
+    amg_nn* nn = nullptr;             // learned correction after the cycle (FP32 smoother only)
+    bool nn_off = false;              // set while falling back to the plain cycle
     int* hstate = nullptr;   // pinned mirror of the coarse solver state words
     ~amg_hierarchy() {
         if (hstate) cudaFreeHost(hstate);
@@ -344,7 +312,17 @@ amg_status precondition64(amg_hierarchy* h, const void* v, void* z, cudaStream_t
     int fp = h->fp;
     if (fp == 0) return vcycle0(h, 0, v, z, s);
     CK(launch_convert_spinor(0, fp, g, v, h->fb[fp].p, 1, s));
-    if (fp == 1) return vcycle0(h, 1, h->fb[1].p, z, s);
+    if (fp == 1) {
+        TRY(vcycle0(h, 1, h->fb[1].p, z, s));
+        if (h->nn && !h->nn_off) {
+            // learned correction of what the cycle leaves: z += N(v - D z)
+            amg_dirac* d = h->d;
+            CK(launch_dirac(1, g, nullptr, d->gauge->U[1].p, d->C[1].p, z, h->fx[1].p, h->fb[1].p, d->kappa, 1, s));
+            TRY(nn_forward_internal(h->nn, h->fx[1].p, h->nn->ework.p, s));
+            CK(launch_axpby(1, make_double2(1, 0), h->nn->ework.p, make_double2(1, 0), z, fine_n(h), s));
+        }
+        return AMG_OK;
+    }
     TRY(vcycle0(h, fp, h->fb[fp].p, h->fx[fp].p, s));
     CK(launch_convert_spinor(fp, 1, g, h->fx[fp].p, z, 1, s));
     return AMG_OK;
@@ -1035,6 +1013,14 @@ amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_
     return AMG_OK;
 }
 
+amg_status amg_hierarchy_set_nn(amg_hierarchy* h, amg_nn* nn) {
+    if (!h) return fail(AMG_EINVAL, "NULL hierarchy");
+    if (nn && h->fp != 1) return fail(AMG_EINVAL, "the learned correction needs the FP32 smoother");
+    if (nn && nn->d != h->d) return fail(AMG_EINVAL, "network and hierarchy belong to different operators");
+    h->nn = nn;
+    return AMG_OK;
+}
+
 amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_stream s) {
     if (!h || !b || !x) return fail(AMG_EINVAL, "bad argument");
     const GeomH& g = fine_geom(h);
@@ -1070,6 +1056,19 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         amg_solve_info loc;
         std::memset(&loc, 0, sizeof(loc));
         amg_status rs = fgmres(h, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, &loc, st);
+        loc.used_nn = (h->nn && !h->nn_off) ? 1 : 0;
+        if (loc.used_nn && (rs == AMG_NOT_CONVERGED || rs == AMG_NAN)) {
+            // the FP64 residual rejects the learned correction: solve again with the plain cycle
+            h->nn_off = true;
+            if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, 1, st));
+            else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V), st));
+            int prev_iters = loc.iters;
+            rs = fgmres(h, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, &loc, st);
+            h->nn_off = false;
+            loc.iters += prev_iters;
+            loc.used_nn = 0;
+            loc.nn_fallback = 1;
+        }
         if (rs != AMG_OK && rs != AMG_NOT_CONVERGED) return rs;
         CK(launch_unpack_spinor(0, g, h->ox.p, xr, 1, st));
         CK(cudaMemcpyAsync(h->hstate, h->lev[h->p.nlevels - 1].cs_state.p, 16, cudaMemcpyDeviceToHost, st));
