@@ -283,9 +283,13 @@ amg_status amg_hierarchy_set_nn(amg_hierarchy* h, amg_nn* nn);
 /* Solve D x = b for nrhs canonical double vectors with flexible GMRES(outer_m)
  * preconditioned by the multigrid cycle, until the FP64 true residual
  * ||b - D x|| / ||b|| <= tol (recomputed at every restart and at exit) or
- * maxit outer steps.  x is an input initial guess if use_x0 != 0, else
- * overwritten.  info (may be NULL) receives the last right-hand side's
- * numbers.  Returns AMG_NOT_CONVERGED if any rhs misses tol. */
+ * maxit outer steps.  Up to 12 right-hand sides are solved in lockstep: one
+ * batched cycle (restriction, coarse solves, prolongation, SAP over all of
+ * them) and one batched Arnoldi product per step.  x is an input initial
+ * guess if use_x0 != 0, else overwritten.  info (may be NULL) receives, over
+ * all right-hand sides, the largest iteration count and true residual, the
+ * summed phase times and whether all converged.  Returns AMG_NOT_CONVERGED
+ * if any rhs misses tol. */
 amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, double tol, int maxit,
                      int use_x0, amg_solve_info* info, amg_stream s);
 

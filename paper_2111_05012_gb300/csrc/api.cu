@@ -73,10 +73,15 @@ struct Reducer {
     ~Reducer() {
         if (hpart) cudaFreeHost(hpart);
     }
-    amg_status init() {
+    int cap = 0;
+    amg_status init(int nb) {
         grid = blas_grid();
-        CK(dpart.ensure(sizeof(double2) * grid * 20));
-        if (!hpart) CK(cudaMallocHost(&hpart, sizeof(double2) * grid * 20));
+        if (nb <= cap && hpart) return AMG_OK;
+        CK(dpart.ensure(sizeof(double2) * grid * 20 * nb));
+        if (hpart) cudaFreeHost(hpart);
+        hpart = nullptr;
+        CK(cudaMallocHost(&hpart, sizeof(double2) * grid * 20 * nb));
+        cap = nb;
         return AMG_OK;
     }
     // k dots <a_j, b>
@@ -185,7 +190,8 @@ struct amg_hierarchy {
     int sap_variant[3] = {0, 0, 0};   // chosen SAP kernel per smoother precision
     amg_nn* nn = nullptr;             // learned correction after the cycle (FP32 smoother only)
     bool nn_off = false;              // set while falling back to the plain cycle
-    int* hstate = nullptr;   // pinned mirror of the coarse solver state words
+    int* hstate = nullptr;   // pinned mirror of the coarse solver state words (16 x 4 ints)
+    int nb_cap = 0;          // batch width the workspaces are sized for
     ~amg_hierarchy() {
         if (hstate) cudaFreeHost(hstate);
         for (auto& v : cw)
@@ -227,24 +233,29 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
 }
 
 // ---------------------------------------------------------------- fine ops
-amg_status fine_D(amg_hierarchy* h, int prec, const void* in, void* out, const void* b, cudaStream_t s) {
+// Every operation below works on a batch of nb right-hand sides stored one
+// after another (field q at byte offset q * field size).
+size_t fsz(amg_hierarchy* h, int prec) { return fine_spinor_bytes(prec, fine_geom(h).V); }
+void* fld(const DevBuf& b, amg_hierarchy* h, int prec, int q) { return (char*)b.p + q * fsz(h, prec); }
+
+amg_status fine_D(amg_hierarchy* h, int prec, const void* in, void* out, const void* b, int nb, cudaStream_t s) {
     amg_dirac* d = h->d;
-    CK(launch_dirac(prec, fine_geom(h), nullptr, d->gauge->U[prec].p, d->C[prec].p, in, out, b, d->kappa, 1, s));
+    CK(launch_dirac(prec, fine_geom(h), nullptr, d->gauge->U[prec].p, d->C[prec].p, in, out, b, d->kappa, nb, s));
     return AMG_OK;
 }
 
-amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_zero, cudaStream_t s) {
+amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_zero, int nb, cudaStream_t s) {
     amg_dirac* d = h->d;
     h->timer.start(PH_SMOOTH, s);
     const int var = h->sap_variant[prec];
     for (int i = 0; i < h->p.sap_iters; ++i) {
         const bool first = x_zero && i == 0;
         CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], 0, h->p.mr_iters, first ? 1 : 0,
-                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, s));
+                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, nb, s));
         CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], 1, h->p.mr_iters, first ? 2 : 0,
-                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, s));
+                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, nb, s));
     }
-    if (h->p.sap_iters == 0 && x_zero) CK(cudaMemsetAsync(x, 0, fine_spinor_bytes(prec, fine_geom(h).V), s));
+    if (h->p.sap_iters == 0 && x_zero) CK(cudaMemsetAsync(x, 0, fsz(h, prec) * nb, s));
     h->timer.stop(s);
     return AMG_OK;
 }
@@ -259,250 +270,341 @@ amg_status coarse_apply(amg_hierarchy* h, int l, const void* in, void* out, cons
 }
 
 // BiCGStab(l) (Sleijpen-Fokkema) on the coarsest level to relative tolerance
-// coarse_tol: one persistent cooperative launch, no host synchronisation.
-amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, cudaStream_t s) {
+// coarse_tol: one persistent cooperative launch per right-hand side, no host
+// synchronisation.
+amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int nb, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
     const int ell = h->p.coarse_ell;
-    auto& w = h->cw[l];   // [0] bc, [1] xc, [2] rt, [3..3+ell] R, [4+ell..4+2ell] U
+    auto& w = h->cw[l];   // [0] bc, [1] xc (nb vectors each), [2] rt, [3..3+ell] R, [4+ell..4+2ell] U
     void* R[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     void* U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     for (int j = 0; j <= ell; ++j) {
         R[j] = w[3 + j]->p;
         U[j] = w[4 + ell + j]->p;
     }
-    CK(cudaMemsetAsync(L.cs_state.p, 0, 12, s));
-    CK(launch_coarse_bicgstab(L.prec, L.g, L.nc, L.B.p, b, x, w[2]->p, R, U, ell, h->p.coarse_tol,
-                              h->p.coarse_maxit, L.cs_part.p, L.cs_state.p, s));
-    CK(cudaMemcpyAsync(h->hstate, L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
+    const size_t cv = coarse_n(L) * coarse_elem_bytes(L.prec);
+    for (int q = 0; q < nb; ++q) {
+        CK(cudaMemsetAsync(L.cs_state.p, 0, 12, s));
+        CK(launch_coarse_bicgstab(L.prec, L.g, L.nc, L.B.p, (const char*)b + q * cv, (char*)x + q * cv, w[2]->p, R,
+                                  U, ell, h->p.coarse_tol, h->p.coarse_maxit, L.cs_part.p, L.cs_state.p, s));
+        // error word of this solve (a later one would overwrite it): fold into word 2 of the host mirror
+        CK(cudaMemcpyAsync(h->hstate + 4 * (q % 16), L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
+    }
     return AMG_OK;
 }
 
-// status of the last coarse solve; valid after any stream synchronisation
+// status of the last batch of coarse solves; valid after any stream synchronisation
 amg_status coarse_status(amg_hierarchy* h) {
-    if (h->hstate[2] == 1) return fail(AMG_TIMEOUT, "coarse solver: grid barrier timed out");
-    if (h->hstate[2] != 0) return fail(AMG_NAN, "coarse solver: breakdown or non-finite residual");
+    for (int q = 0; q < 16; ++q) {
+        if (h->hstate[4 * q + 2] == 1) return fail(AMG_TIMEOUT, "coarse solver: grid barrier timed out");
+        if (h->hstate[4 * q + 2] != 0) return fail(AMG_NAN, "coarse solver: breakdown or non-finite residual");
+    }
     return AMG_OK;
 }
 
 // ---------------------------------------------------------------- V-cycle
-// x = M b on the fine lattice in precision prec (b, x internal fields):
+// x = M b on the fine lattice in precision prec (b, x internal fields, nb of them):
 // step (1) x = P D_c^{-1} R b, step (2) x += SAP(b - D x).
-amg_status vcycle0(amg_hierarchy* h, int prec, const void* b, void* x, cudaStream_t s) {
+amg_status vcycle0(amg_hierarchy* h, int prec, const void* b, void* x, int nb, cudaStream_t s) {
     CoarseLevel& L = L1(h);
     auto& w = h->cw[1];
     h->timer.start(PH_RP, s);
-    CK(launch_restrict_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, b, w[0]->p, s));
+    CK(launch_restrict_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, b, w[0]->p, nb,
+                            s));
     h->timer.stop(s);
     h->timer.start(PH_COARSE, s);
-    TRY(coarse_bicgstab(h, 1, w[0]->p, w[1]->p, s));
+    TRY(coarse_bicgstab(h, 1, w[0]->p, w[1]->p, nb, s));
     h->timer.stop(s);
     h->timer.start(PH_RP, s);
-    CK(launch_prolong_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, w[1]->p, x, s));
+    CK(launch_prolong_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, w[1]->p, x, nb,
+                           s));
     h->timer.stop(s);
-    TRY(fine_sap(h, prec, b, x, false, s));
+    TRY(fine_sap(h, prec, b, x, false, nb, s));
     return AMG_OK;
 }
 
-// z = M v for an FP64 internal field v; z is written in the outer solver's
-// Z precision (FP64 for the all-FP64 path, else FP32: the cycle's output is
+// z = M v for FP64 internal fields v; z is written in the outer solver's Z
+// precision (FP64 for the all-FP64 path, else FP32: the cycle's output is
 // exact in FP32, so nothing is lost)
 int zprec_of(amg_hierarchy* h) { return h->fp == 0 ? 0 : 1; }
-amg_status precondition64(amg_hierarchy* h, const void* v, void* z, cudaStream_t s) {
+amg_status precondition64(amg_hierarchy* h, const void* v, void* z, int nb, cudaStream_t s) {
     const GeomH& g = fine_geom(h);
     int fp = h->fp;
-    if (fp == 0) return vcycle0(h, 0, v, z, s);
-    CK(launch_convert_spinor(0, fp, g, v, h->fb[fp].p, 1, s));
+    if (fp == 0) return vcycle0(h, 0, v, z, nb, s);
+    CK(launch_convert_spinor(0, fp, g, v, h->fb[fp].p, nb, s));
     if (fp == 1) {
-        TRY(vcycle0(h, 1, h->fb[1].p, z, s));
+        TRY(vcycle0(h, 1, h->fb[1].p, z, nb, s));
         if (h->nn && !h->nn_off) {
             // learned correction of what the cycle leaves: z += N(v - D z)
             amg_dirac* d = h->d;
-            CK(launch_dirac(1, g, nullptr, d->gauge->U[1].p, d->C[1].p, z, h->fx[1].p, h->fb[1].p, d->kappa, 1, s));
-            TRY(nn_forward_internal(h->nn, h->fx[1].p, h->nn->ework.p, s));
-            CK(launch_axpby(1, make_double2(1, 0), h->nn->ework.p, make_double2(1, 0), z, fine_n(h), s));
+            CK(launch_dirac(1, g, nullptr, d->gauge->U[1].p, d->C[1].p, z, h->fx[1].p, h->fb[1].p, d->kappa, nb,
+                            s));
+            for (int q = 0; q < nb; ++q) {
+                TRY(nn_forward_internal(h->nn, fld(h->fx[1], h, 1, q), h->nn->ework.p, s));
+                CK(launch_axpby(1, make_double2(1, 0), h->nn->ework.p, make_double2(1, 0),
+                                (char*)z + q * fsz(h, 1), fine_n(h), s));
+            }
         }
         return AMG_OK;
     }
-    TRY(vcycle0(h, fp, h->fb[fp].p, h->fx[fp].p, s));
-    CK(launch_convert_spinor(fp, 1, g, h->fx[fp].p, z, 1, s));
+    TRY(vcycle0(h, fp, h->fb[fp].p, h->fx[fp].p, nb, s));
+    CK(launch_convert_spinor(fp, 1, g, h->fx[fp].p, z, nb, s));
     return AMG_OK;
 }
 
-// w = D z for a Z-precision z (FP64 result)
-amg_status arnoldi_D(amg_hierarchy* h, const void* z, void* w, cudaStream_t s) {
-    if (zprec_of(h) == 0) return fine_D(h, 0, z, w, nullptr, s);
+// w = D z for Z-precision z (FP64 result)
+amg_status arnoldi_D(amg_hierarchy* h, const void* z, void* w, int nb, cudaStream_t s) {
+    if (zprec_of(h) == 0) return fine_D(h, 0, z, w, nullptr, nb, s);
     amg_dirac* d = h->d;
-    CK(launch_dirac_mixed(fine_geom(h), d->gauge->U[3].p, d->C[3].p, z, w, d->kappa, 1, s));
+    CK(launch_dirac_mixed(fine_geom(h), d->gauge->U[3].p, d->C[3].p, z, w, d->kappa, nb, s));
     return AMG_OK;
 }
 
 // ---------------------------------------------------------------- outer FGMRES
-amg_status fgmres(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, double tol, int maxit,
-                  amg_solve_info* info, cudaStream_t s) {
-    const int m = h->p.outer_m;
+// Flexible GMRES(m) in FP64 for nb right-hand sides in lockstep: one batched
+// preconditioner call and one batched Arnoldi product per step, per-RHS
+// Hessenberg / Givens / convergence; reductions of the whole batch share one
+// host synchronisation.  A right-hand side that has converged (or stopped)
+// rides along with a zero vector.
+struct RhsState {
+    double bnorm = 0, rn = 0, rel = 0;
+    bool done = false, conv = false, stop = false;
+    int iters = 0, restarts = 0, jend = -1;
+    std::vector<std::vector<cplx>> H;
+    std::vector<double> cs;
+    std::vector<cplx> sn, g;
+};
+
+amg_status batch_norms(amg_hierarchy* h, int nb, const DevBuf& base, std::vector<double>& out, cudaStream_t s) {
     const size_t n = fine_n(h);
     Reducer& red = h->red;
-    double bn2;
-    TRY(red.norm2(0, b, n, &bn2, s));
-    const double bnorm = std::sqrt(bn2);
-    int iters = 0, restarts = 0;
-    double rel = 0;
-    bool conv = false;
-    if (bnorm == 0) {
-        CK(cudaMemsetAsync(x, 0, n * 16, s));
-        conv = true;
+    for (int q = 0; q < nb; ++q)
+        CK(launch_norm2(0, fld(base, h, 0, q), n, (double*)red.dpart.p + (size_t)q * red.grid, s));
+    CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double) * red.grid * nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double* hp = (const double*)red.hpart;
+    out.assign(nb, 0.0);
+    for (int q = 0; q < nb; ++q)
+        for (int i = 0; i < red.grid; ++i) out[q] += hp[(size_t)q * red.grid + i];
+    return AMG_OK;
+}
+
+amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonzero, double tol, int maxit,
+                  std::vector<amg_solve_info>& infos, cudaStream_t s) {
+    const int m = h->p.outer_m;
+    const size_t n = fine_n(h), fs = fsz(h, 0);
+    Reducer& red = h->red;
+    auto F = [&](const void* base, int q) { return (char*)base + q * fs; };
+    std::vector<RhsState> st(nb);
+    // ||b|| for every right-hand side
+    {
+        CK(cudaMemcpyAsync(h->orr.p, b, fs * nb, cudaMemcpyDeviceToDevice, s));
+        std::vector<double> bn2;
+        TRY(batch_norms(h, nb, h->orr, bn2, s));
+        for (int q = 0; q < nb; ++q) {
+            st[q].bnorm = std::sqrt(bn2[q]);
+            if (st[q].bnorm == 0) {
+                CK(cudaMemsetAsync(F(x, q), 0, fs, s));
+                st[q].done = st[q].conv = true;
+            }
+        }
     }
-    std::vector<std::vector<cplx>> H(m + 1, std::vector<cplx>(m));
-    std::vector<double> cs(m);
-    std::vector<cplx> sn(m), gv(m + 1);
     bool x_is_zero = !x_nonzero;
-    while (!conv) {
-        double rn2;
-        if (x_is_zero) {   // r = b: no FP64 stencil needed
-            CK(cudaMemcpyAsync(h->orr.p, b, n * 16, cudaMemcpyDeviceToDevice, s));
-            rn2 = bn2;
+    while (true) {
+        // true FP64 residual of every right-hand side
+        std::vector<double> rn2(nb, 0.0);
+        if (x_is_zero) {
+            CK(cudaMemcpyAsync(h->orr.p, b, fs * nb, cudaMemcpyDeviceToDevice, s));
+            for (int q = 0; q < nb; ++q) rn2[q] = st[q].bnorm * st[q].bnorm;
             x_is_zero = false;
         } else {
-            TRY(fine_D(h, 0, x, h->orr.p, b, s));   // r = b - D x
-            TRY(red.norm2(0, h->orr.p, n, &rn2, s));
+            TRY(fine_D(h, 0, x, h->orr.p, b, nb, s));   // r = b - D x
+            TRY(batch_norms(h, nb, h->orr, rn2, s));
         }
-        if (!std::isfinite(rn2)) return fail(AMG_NAN, "outer solve: non-finite residual");
-        double rn = std::sqrt(rn2);
-        rel = rn / bnorm;
-        if (rn <= tol * bnorm) {
-            conv = true;
-            break;
+        bool any = false;
+        for (int q = 0; q < nb; ++q) {
+            RhsState& r = st[q];
+            if (r.bnorm == 0) continue;
+            if (!std::isfinite(rn2[q])) return fail(AMG_NAN, "outer solve: non-finite residual");
+            r.rn = std::sqrt(rn2[q]);
+            r.rel = r.rn / r.bnorm;
+            r.done = r.conv = r.rn <= tol * r.bnorm;
+            if (!r.conv && r.iters >= maxit) r.done = true;
+            if (!r.done) {
+                any = true;
+                if (r.iters > 0) r.restarts++;
+            }
         }
-        if (iters >= maxit) break;
-        if (iters > 0) restarts++;
-        CK(launch_axpby(0, make_double2(1.0 / rn, 0), h->orr.p, make_double2(0, 0), h->oV[0]->p, n, s));
-        for (auto& row : H) std::fill(row.begin(), row.end(), cplx(0));
-        std::fill(gv.begin(), gv.end(), cplx(0));
-        gv[0] = rn;
-        int jend = -1;
+        if (!any) break;
+        // V_0 = r / |r| (zero for finished right-hand sides)
+        for (int q = 0; q < nb; ++q) {
+            RhsState& r = st[q];
+            r.H.assign(m + 1, std::vector<cplx>(m, cplx(0)));
+            r.cs.assign(m, 0.0);
+            r.sn.assign(m, cplx(0));
+            r.g.assign(m + 1, cplx(0));
+            r.g[0] = r.rn;
+            r.jend = -1;
+            r.stop = r.done;
+            if (r.done) CK(cudaMemsetAsync(F(h->oV[0]->p, q), 0, fs, s));
+            else CK(launch_axpby(0, make_double2(1.0 / r.rn, 0), F(h->orr.p, q), make_double2(0, 0),
+                                 F(h->oV[0]->p, q), n, s));
+        }
         for (int j = 0; j < m; ++j) {
-            TRY(precondition64(h, h->oV[j]->p, h->oZ[j]->p, s));
-            TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, s));
-            // classical Gram-Schmidt, twice
-            std::vector<const void*> vl(j + 1);
-            std::vector<const void*> vx(j + 1);
-            for (int i = 0; i <= j; ++i) vl[i] = vx[i] = h->oV[i]->p;
+            TRY(precondition64(h, h->oV[j]->p, h->oZ[j]->p, nb, s));
+            TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, nb, s));
+            // classical Gram-Schmidt, twice, every right-hand side in one synchronisation per pass
             for (int pass = 0; pass < 2; ++pass) {
-                std::vector<cplx> c(j + 1);
-                TRY(red.dots(0, j + 1, vl.data(), h->ow.p, n, c.data(), s));
+                std::vector<const void*> vl(j + 1);
+                for (int q = 0; q < nb; ++q) {
+                    for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
+                    CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n,
+                                        red.dpart.as<double2>() + (size_t)q * 20 * red.grid, s));
+                }
+                CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double2) * 20 * red.grid * nb,
+                                   cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
                 if (pass == 0) TRY(coarse_status(h));
-                std::vector<double2> nc(j + 1);
-                for (int i = 0; i <= j; ++i) {
-                    H[i][j] += c[i];
-                    nc[i] = d2(-c[i]);
+                for (int q = 0; q < nb; ++q) {
+                    RhsState& r = st[q];
+                    std::vector<double2> nc(j + 1);
+                    for (int i = 0; i <= j; ++i) {
+                        double re = 0, im = 0;
+                        const double2* hp = red.hpart + (size_t)q * 20 * red.grid + (size_t)i * red.grid;
+                        for (int t = 0; t < red.grid; ++t) {
+                            re += hp[t].x;
+                            im += hp[t].y;
+                        }
+                        if (!r.stop) r.H[i][j] += cplx(re, im);
+                        nc[i] = r.stop ? make_double2(0, 0) : make_double2(-re, -im);
+                    }
+                    for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
+                    if (!r.stop) CK(launch_multi_axpy(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, s));
                 }
-                CK(launch_multi_axpy(0, j + 1, nc.data(), vx.data(), h->ow.p, n, s));
             }
-            double hn2;
-            TRY(red.norm2(0, h->ow.p, n, &hn2, s));
-            double hn = std::sqrt(hn2);
-            H[j + 1][j] = hn;
-            iters++;
-            // Givens rotations
-            for (int i = 0; i < j; ++i) {
-                cplx a = H[i][j], bb = H[i + 1][j];
-                H[i][j] = cs[i] * a + sn[i] * bb;
-                H[i + 1][j] = -std::conj(sn[i]) * a + cs[i] * bb;
-            }
-            {
-                cplx a = H[j][j], bb = H[j + 1][j];
-                double aa = std::abs(a), ab = std::abs(bb);
-                if (ab == 0) {
-                    cs[j] = 1;
-                    sn[j] = 0;
-                } else if (aa == 0) {
-                    cs[j] = 0;
-                    sn[j] = std::conj(bb) / ab;
+            std::vector<double> hn2;
+            TRY(batch_norms(h, nb, h->ow, hn2, s));
+            bool all_stopped = true;
+            for (int q = 0; q < nb; ++q) {
+                RhsState& r = st[q];
+                if (r.stop) {
+                    CK(cudaMemsetAsync(F(h->oV[j + 1]->p, q), 0, fs, s));
+                    continue;
+                }
+                const double hn = std::sqrt(hn2[q]);
+                auto& H = r.H;
+                H[j + 1][j] = hn;
+                r.iters++;
+                for (int i = 0; i < j; ++i) {
+                    cplx a = H[i][j], bb = H[i + 1][j];
+                    H[i][j] = r.cs[i] * a + r.sn[i] * bb;
+                    H[i + 1][j] = -std::conj(r.sn[i]) * a + r.cs[i] * bb;
+                }
+                {
+                    cplx a = H[j][j], bb = H[j + 1][j];
+                    double aa = std::abs(a), ab = std::abs(bb);
+                    if (ab == 0) {
+                        r.cs[j] = 1;
+                        r.sn[j] = 0;
+                    } else if (aa == 0) {
+                        r.cs[j] = 0;
+                        r.sn[j] = std::conj(bb) / ab;
+                    } else {
+                        double t = std::sqrt(aa * aa + ab * ab);
+                        r.cs[j] = aa / t;
+                        r.sn[j] = (a / aa) * std::conj(bb) / t;
+                    }
+                    H[j][j] = r.cs[j] * a + r.sn[j] * bb;
+                    H[j + 1][j] = 0;
+                    r.g[j + 1] = -std::conj(r.sn[j]) * r.g[j];
+                    r.g[j] = r.cs[j] * r.g[j];
+                }
+                r.jend = j;
+                const double est = std::abs(r.g[j + 1]);
+                if (!std::isfinite(est)) return fail(AMG_NAN, "outer solve: non-finite Arnoldi coefficient");
+                if (hn == 0 || est <= tol * r.bnorm || r.iters >= maxit) {
+                    r.stop = true;
+                    CK(cudaMemsetAsync(F(h->oV[j + 1]->p, q), 0, fs, s));
                 } else {
-                    double t = std::sqrt(aa * aa + ab * ab);
-                    cs[j] = aa / t;
-                    sn[j] = (a / aa) * std::conj(bb) / t;
+                    CK(launch_axpby(0, make_double2(1.0 / hn, 0), F(h->ow.p, q), make_double2(0, 0),
+                                    F(h->oV[j + 1]->p, q), n, s));
+                    all_stopped = false;
                 }
-                H[j][j] = cs[j] * a + sn[j] * bb;
-                H[j + 1][j] = 0;
-                gv[j + 1] = -std::conj(sn[j]) * gv[j];
-                gv[j] = cs[j] * gv[j];
             }
-            jend = j;
-            double est = std::abs(gv[j + 1]);
-            if (!std::isfinite(est)) return fail(AMG_NAN, "outer solve: non-finite Arnoldi coefficient");
-            if (hn == 0 || est <= tol * bnorm || iters >= maxit) break;
-            CK(launch_axpby(0, make_double2(1.0 / hn, 0), h->ow.p, make_double2(0, 0), h->oV[j + 1]->p, n, s));
+            if (all_stopped) break;
         }
-        // back substitution and update x += Z y
-        int k = jend + 1;
-        std::vector<cplx> y(k);
-        for (int i = k - 1; i >= 0; --i) {
-            cplx t = gv[i];
-            for (int q = i + 1; q < k; ++q) t -= H[i][q] * y[q];
-            y[i] = t / H[i][i];
+        // back substitution and x += Z y for every active right-hand side
+        for (int q = 0; q < nb; ++q) {
+            RhsState& r = st[q];
+            if (r.done || r.jend < 0) continue;
+            const int k = r.jend + 1;
+            std::vector<cplx> y(k);
+            for (int i = k - 1; i >= 0; --i) {
+                cplx t = r.g[i];
+                for (int c = i + 1; c < k; ++c) t -= r.H[i][c] * y[c];
+                y[i] = t / r.H[i][i];
+            }
+            std::vector<double2> yc(k);
+            std::vector<const void*> zl(k);
+            for (int i = 0; i < k; ++i) {
+                yc[i] = d2(y[i]);
+                zl[i] = (const char*)h->oZ[i]->p + q * fsz(h, zprec_of(h));
+            }
+            if (zprec_of(h) == 0) CK(launch_multi_axpy(0, k, yc.data(), zl.data(), F(x, q), n, s));
+            else CK(launch_spinor_axpy_mixed(fine_geom(h), k, yc.data(), zl.data(), F(x, q), s));
         }
-        std::vector<double2> yc(k);
-        std::vector<const void*> zl(k);
-        for (int i = 0; i < k; ++i) {
-            yc[i] = d2(y[i]);
-            zl[i] = h->oZ[i]->p;
-        }
-        if (zprec_of(h) == 0) CK(launch_multi_axpy(0, k, yc.data(), zl.data(), x, n, s));
-        else CK(launch_spinor_axpy_mixed(fine_geom(h), k, yc.data(), zl.data(), x, s));
     }
-    if (info) {
-        info->iters = iters;
-        info->restarts = restarts;
-        info->converged = conv ? 1 : 0;
-        info->true_rel_residual = rel;
+    infos.assign(nb, amg_solve_info());
+    bool all_conv = true;
+    for (int q = 0; q < nb; ++q) {
+        std::memset(&infos[q], 0, sizeof(amg_solve_info));
+        infos[q].iters = st[q].iters;
+        infos[q].restarts = st[q].restarts;
+        infos[q].converged = st[q].conv ? 1 : 0;
+        infos[q].true_rel_residual = st[q].bnorm == 0 ? 0.0 : st[q].rel;
+        all_conv = all_conv && st[q].conv;
     }
-    return conv ? AMG_OK : AMG_NOT_CONVERGED;
+    return all_conv ? AMG_OK : AMG_NOT_CONVERGED;
 }
 
 // ---------------------------------------------------------------- setup pieces
-amg_status alloc_workspaces(amg_hierarchy* h) {
+// (Re)size the batch-dependent workspaces for nb right-hand sides.
+amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
     const GeomH& g = fine_geom(h);
-    TRY(h->red.init());
+    TRY(h->red.init(nb));
     CK(h->err_flag.ensure(sizeof(int)));
     for (int pr = 0; pr < 3; ++pr) {
-        CK(h->fb[pr].ensure(fine_spinor_bytes(pr, g.V)));
-        CK(h->fx[pr].ensure(fine_spinor_bytes(pr, g.V)));
+        CK(h->fb[pr].ensure(fine_spinor_bytes(pr, g.V) * nb));
+        CK(h->fx[pr].ensure(fine_spinor_bytes(pr, g.V) * nb));
     }
     CK(h->tmpv.ensure(fine_spinor_bytes(h->vp, g.V)));
     if (!h->hstate) {
-        CK(cudaMallocHost(&h->hstate, 16));
-        std::memset(h->hstate, 0, 16);
+        CK(cudaMallocHost(&h->hstate, 16 * 16));
+        std::memset(h->hstate, 0, 16 * 16);
     }
     h->cw.resize(h->p.nlevels);
     for (int l = 1; l < h->p.nlevels; ++l) {
         CoarseLevel& L = h->lev[l];
         CK(L.cs_part.ensure(coarse_solver_partial_bytes()));
-        CK(L.cs_state.ensure(coarse_solver_state_bytes()));
-        CK(cudaMemset(L.cs_state.p, 0, coarse_solver_state_bytes()));
+        if (!L.cs_state.p) {
+            CK(L.cs_state.ensure(coarse_solver_state_bytes()));
+            CK(cudaMemset(L.cs_state.p, 0, coarse_solver_state_bytes()));
+        }
         size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
         int nv = 4 + 2 * (h->p.coarse_ell + 1);
-        for (int k = 0; k < nv; ++k) {
-            DevBuf* b = new DevBuf();
-            h->cw[l].push_back(b);
-            CK(b->ensure(bytes));
-        }
+        while ((int)h->cw[l].size() < nv) h->cw[l].push_back(new DevBuf());
+        for (int k = 0; k < nv; ++k) CK(h->cw[l][k]->ensure(bytes * (k < 2 ? nb : 1)));
     }
-    const size_t fb64 = fine_spinor_bytes(0, g.V);
+    const size_t fb64 = fine_spinor_bytes(0, g.V) * nb;
     CK(h->ob.ensure(fb64));
     CK(h->ox.ensure(fb64));
     CK(h->ow.ensure(fb64));
     CK(h->orr.ensure(fb64));
-    for (int j = 0; j <= h->p.outer_m; ++j) {
-        DevBuf* b = new DevBuf();
-        h->oV.push_back(b);
-        CK(b->ensure(fb64));
-        if (j < h->p.outer_m) {
-            DevBuf* z = new DevBuf();
-            h->oZ.push_back(z);
-            CK(z->ensure(fine_spinor_bytes(h->fp == 0 ? 0 : 1, g.V)));
-        }
-    }
+    while ((int)h->oV.size() < h->p.outer_m + 1) h->oV.push_back(new DevBuf());
+    while ((int)h->oZ.size() < h->p.outer_m) h->oZ.push_back(new DevBuf());
+    for (auto* v : h->oV) CK(v->ensure(fb64));
+    for (auto* z : h->oZ) CK(z->ensure(fine_spinor_bytes(h->fp == 0 ? 0 : 1, g.V) * nb));
+    h->nb_cap = nb > h->nb_cap ? nb : h->nb_cap;
     return AMG_OK;
 }
 
@@ -600,7 +702,7 @@ amg_status tune_kernels(amg_hierarchy* h) {
             for (int rep = 0; rep < 4; ++rep) {
                 CK(cudaEventRecord(e0, 0));
                 CK(launch_sap_half_variant(v, pr, g, h->blk[0], 0, h->p.mr_iters, 0, d->gauge->U[pr].p, d->C[pr].p,
-                                           h->fb[pr].p, h->fx[pr].p, d->kappa, 0));
+                                           h->fb[pr].p, h->fx[pr].p, d->kappa, 1, 0));
                 CK(cudaEventRecord(e1, 0));
                 CK(cudaEventSynchronize(e1));
                 float t = 0;
@@ -629,7 +731,7 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
     h->vp = vec_prec_of(p->prec_smoother);
     *hp = h;
     amg_status st = build_levels(h);
-    if (st == AMG_OK) st = alloc_workspaces(h);
+    if (st == AMG_OK) st = alloc_workspaces(h, 1);
     if (st == AMG_OK) st = tune_kernels(h);
     if (st != AMG_OK) {
         delete h;
@@ -829,7 +931,7 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
         for (int k = 0; k < h->p.n_init; ++k) {
             for (int i = 0; i < h->p.nvec[0]; ++i) {
                 void* vi = (char*)h->vecs0.p + i * vb;
-                TRY(fine_sap(h, vp, vi, h->tmpv.p, true, s));
+                TRY(fine_sap(h, vp, vi, h->tmpv.p, true, 1, s));
                 TRY(normalise_into(h, vp, h->tmpv.p, vi, s));
             }
         }
@@ -838,7 +940,7 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
         for (int k = 0; k < h->p.n_adapt; ++k) {
             for (int i = 0; i < h->p.nvec[0]; ++i) {
                 void* vi = (char*)h->vecs0.p + i * vb;
-                TRY(vcycle0(h, vp, vi, h->tmpv.p, s));
+                TRY(vcycle0(h, vp, vi, h->tmpv.p, 1, s));
                 TRY(normalise_into(h, vp, h->tmpv.p, vi, s));
             }
             TRY(orthonormalise_and_galerkin(h, s));
@@ -967,17 +1069,11 @@ amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void
     TRY(transfer_common(h, coarsening, nrhs, prec));
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
-    CoarseLevel& L = L1(h);
     int cprec = prec == AMG_F64 ? 0 : 1;
-    size_t fb = fine_spinor_bytes(prec, g.V);
     DevBuf tmp;
-    CK(tmp.ensure(fb));
-    for (int r = 0; r < nrhs; ++r) {
-        const char* src = (const char*)fine + (size_t)r * g.V * 24 * (prec == AMG_F64 ? 8 : 4);
-        char* dst = (char*)coarse + (size_t)r * coarse_n(L) * coarse_elem_bytes(cprec);
-        CK(launch_pack_spinor(prec, g, src, tmp.p, 1, st));
-        CK(launch_restrict_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, tmp.p, dst, st));
-    }
+    CK(tmp.ensure(fine_spinor_bytes(prec, g.V) * nrhs));
+    CK(launch_pack_spinor(prec, g, fine, tmp.p, nrhs, st));
+    CK(launch_restrict_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, tmp.p, coarse, nrhs, st));
     CK(cudaStreamSynchronize(st));
     return AMG_OK;
 }
@@ -987,17 +1083,11 @@ amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, voi
     TRY(transfer_common(h, coarsening, nrhs, prec));
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
-    CoarseLevel& L = L1(h);
     int cprec = prec == AMG_F64 ? 0 : 1;
-    size_t fb = fine_spinor_bytes(prec, g.V);
     DevBuf tmp;
-    CK(tmp.ensure(fb));
-    for (int r = 0; r < nrhs; ++r) {
-        const char* src = (const char*)coarse + (size_t)r * coarse_n(L) * coarse_elem_bytes(cprec);
-        char* dst = (char*)fine + (size_t)r * g.V * 24 * (prec == AMG_F64 ? 8 : 4);
-        CK(launch_prolong_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, src, tmp.p, st));
-        CK(launch_unpack_spinor(prec, g, tmp.p, dst, 1, st));
-    }
+    CK(tmp.ensure(fine_spinor_bytes(prec, g.V) * nrhs));
+    CK(launch_prolong_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, coarse, tmp.p, nrhs, st));
+    CK(launch_unpack_spinor(prec, g, tmp.p, fine, nrhs, st));
     CK(cudaStreamSynchronize(st));
     return AMG_OK;
 }
@@ -1007,7 +1097,7 @@ amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
     CK(launch_pack_spinor(prec, g, b, h->fb[prec].p, 1, st));
-    TRY(fine_sap(h, prec, h->fb[prec].p, h->fx[prec].p, true, st));
+    TRY(fine_sap(h, prec, h->fb[prec].p, h->fx[prec].p, true, 1, st));
     CK(launch_unpack_spinor(prec, g, h->fx[prec].p, x, 1, st));
     CK(cudaStreamSynchronize(st));
     return AMG_OK;
@@ -1026,7 +1116,7 @@ amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_st
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
     CK(launch_pack_spinor(0, g, b, h->ob.p, 1, st));
-    TRY(precondition64(h, h->ob.p, h->oZ[0]->p, st));
+    TRY(precondition64(h, h->ob.p, h->oZ[0]->p, 1, st));
     if (zprec_of(h) == 0) CK(launch_unpack_spinor(0, g, h->oZ[0]->p, x, 1, st));
     else {
         CK(launch_convert_spinor(1, 0, g, h->oZ[0]->p, h->ox.p, 1, st));
@@ -1041,55 +1131,69 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     if (!h || !b || !x || nrhs < 1 || !(tol > 0) || maxit < 1) return fail(AMG_EINVAL, "bad argument");
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
+    const int kMaxBatch = 12;   // right-hand sides solved in lockstep
     amg_status worst = AMG_OK;
-    for (int r = 0; r < nrhs; ++r) {
-        auto t0 = std::chrono::steady_clock::now();
-        h->timer.reset();
-        h->timer.on = info != nullptr;
-        h->coarse_cycles = 0;
+    amg_solve_info agg;
+    std::memset(&agg, 0, sizeof(agg));
+    agg.converged = 1;
+    auto t_all = std::chrono::steady_clock::now();
+    h->timer.reset();
+    h->timer.on = info != nullptr;
+    for (int r0 = 0; r0 < nrhs; r0 += kMaxBatch) {
+        const int nb = std::min(kMaxBatch, nrhs - r0);
+        TRY(alloc_workspaces(h, nb));
         for (int l = 1; l < h->p.nlevels; ++l) CK(cudaMemsetAsync(h->lev[l].cs_state.p, 0, 16, st));
-        const double* br = b + (size_t)r * g.V * 24;
-        double* xr = x + (size_t)r * g.V * 24;
-        CK(launch_pack_spinor(0, g, br, h->ob.p, 1, st));
-        if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, 1, st));
-        else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V), st));
-        amg_solve_info loc;
-        std::memset(&loc, 0, sizeof(loc));
-        amg_status rs = fgmres(h, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, &loc, st);
-        loc.used_nn = (h->nn && !h->nn_off) ? 1 : 0;
-        if (loc.used_nn && (rs == AMG_NOT_CONVERGED || rs == AMG_NAN)) {
+        std::memset(h->hstate, 0, 16 * 16);
+        const double* br = b + (size_t)r0 * g.V * 24;
+        double* xr = x + (size_t)r0 * g.V * 24;
+        CK(launch_pack_spinor(0, g, br, h->ob.p, nb, st));
+        if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
+        else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
+        std::vector<amg_solve_info> infos;
+        amg_status rs = fgmres(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
+        int used_nn = (h->nn && !h->nn_off) ? 1 : 0, fell_back = 0;
+        if (used_nn && (rs == AMG_NOT_CONVERGED || rs == AMG_NAN)) {
             // the FP64 residual rejects the learned correction: solve again with the plain cycle
+            int prev = 0;
+            for (auto& i : infos) prev = std::max(prev, i.iters);
             h->nn_off = true;
-            if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, 1, st));
-            else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V), st));
-            int prev_iters = loc.iters;
-            rs = fgmres(h, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, &loc, st);
+            if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
+            else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
+            std::memset(h->hstate, 0, 16 * 16);
+            rs = fgmres(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
             h->nn_off = false;
-            loc.iters += prev_iters;
-            loc.used_nn = 0;
-            loc.nn_fallback = 1;
+            for (auto& i : infos) i.iters += prev;
+            used_nn = 0;
+            fell_back = 1;
         }
         if (rs != AMG_OK && rs != AMG_NOT_CONVERGED) return rs;
-        CK(launch_unpack_spinor(0, g, h->ox.p, xr, 1, st));
-        CK(cudaMemcpyAsync(h->hstate, h->lev[h->p.nlevels - 1].cs_state.p, 16, cudaMemcpyDeviceToHost, st));
+        CK(launch_unpack_spinor(0, g, h->ox.p, xr, nb, st));
+        CK(cudaMemcpyAsync(h->hstate + 60, h->lev[h->p.nlevels - 1].cs_state.p, 16, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         TRY(coarse_status(h));
-        h->coarse_cycles = h->hstate[3];
+        h->coarse_cycles = h->hstate[63];
         if (rs == AMG_NOT_CONVERGED) worst = rs;
-        if (info) {
-            double ms[PH_NPH];
-            h->timer.collect(ms);
-            auto t1 = std::chrono::steady_clock::now();
-            loc.ms_total = std::chrono::duration<double, std::milli>(t1 - t0).count();
-            loc.ms_coarse = ms[PH_COARSE];
-            loc.ms_smoother = ms[PH_SMOOTH];
-            loc.ms_restrict_prolong = ms[PH_RP];
-            loc.ms_other = loc.ms_total - ms[PH_COARSE] - ms[PH_SMOOTH] - ms[PH_RP];
-            loc.coarse_cycles = h->coarse_cycles;
-            *info = loc;
+        for (auto& i : infos) {
+            agg.iters = std::max(agg.iters, i.iters);
+            agg.restarts = std::max(agg.restarts, i.restarts);
+            agg.converged = agg.converged && i.converged;
+            agg.true_rel_residual = std::max(agg.true_rel_residual, i.true_rel_residual);
         }
-        h->timer.on = false;
+        agg.coarse_cycles += h->coarse_cycles;
+        agg.used_nn = used_nn;
+        agg.nn_fallback = agg.nn_fallback || fell_back;
     }
+    if (info) {
+        double ms[PH_NPH];
+        h->timer.collect(ms);
+        agg.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_all).count();
+        agg.ms_coarse = ms[PH_COARSE];
+        agg.ms_smoother = ms[PH_SMOOTH];
+        agg.ms_restrict_prolong = ms[PH_RP];
+        agg.ms_other = agg.ms_total - ms[PH_COARSE] - ms[PH_SMOOTH] - ms[PH_RP];
+        *info = agg;
+    }
+    h->timer.on = false;
     if (worst != AMG_OK) fail(worst, "solve did not reach the tolerance");
     return worst;
 }

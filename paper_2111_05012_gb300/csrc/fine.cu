@@ -448,6 +448,9 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
     int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
     const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
     cx<T> r[12], z[12], Ar[12];
+    // right-hand side blockIdx.y of a batch
+    b = (const char*)b + blockIdx.y * spinor_bytes<P>(g.V);
+    x = (char*)x + blockIdx.y * spinor_bytes<P>(g.V);
     if (active) {
         s = block_site(g, bk, Xi, l, c);
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
@@ -631,6 +634,9 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
     int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
     const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
     cx<float> r[12], z[12], Ar[12];
+    // right-hand side blockIdx.y of a batch
+    b = (const char*)b + blockIdx.y * spinor_bytes<P>(g.V);
+    x = (char*)x + blockIdx.y * spinor_bytes<P>(g.V);
     if (active) {
         s = block_site(g, bk, Xi, l, c);
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
@@ -759,7 +765,7 @@ size_t sap_staged_smem(int vbp) {
 
 template <class P>
 cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
-                                 const void* C, const void* b, void* x, double kappa, cudaStream_t st) {
+                                 const void* C, const void* b, void* x, double kappa, int nrhs, cudaStream_t st) {
     Geom g = make_geom(gh);
     Blocking bk = make_blocking(gh, bh);
     int threads = (bk.Vb + 31) / 32 * 32;
@@ -768,13 +774,14 @@ cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, 
     cudaError_t e =
         cudaFuncSetAttribute(sap_half_staged_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sap_half_staged_kernel<P><<<bk.Vc / 2, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x, (float)kappa);
+    sap_half_staged_kernel<P><<<dim3(bk.Vc / 2, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                          (float)kappa);
     return cudaGetLastError();
 }
 
 template <class P>
 cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
-                          const void* C, const void* b, void* x, double kappa, cudaStream_t st) {
+                          const void* C, const void* b, void* x, double kappa, int nrhs, cudaStream_t st) {
     Geom g = make_geom(gh);
     Blocking bk = make_blocking(gh, bh);
     int threads = (bk.Vb + 31) / 32 * 32;
@@ -785,14 +792,14 @@ cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr
         cudaError_t e =
             cudaFuncSetAttribute(sap_half_kernel<P, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        sap_half_kernel<P, 256><<<ndom, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                             (typename P::T)kappa);
+        sap_half_kernel<P, 256><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                         (typename P::T)kappa);
     } else {
         cudaError_t e =
             cudaFuncSetAttribute(sap_half_kernel<P, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        sap_half_kernel<P, 512><<<ndom, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                             (typename P::T)kappa);
+        sap_half_kernel<P, 512><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                         (typename P::T)kappa);
     }
     return cudaGetLastError();
 }
@@ -974,10 +981,14 @@ cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, c
 }
 cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const BlockH& bk, int colour, int nmr,
                                     int x_mode, const void* U, const void* C, const void* b, void* x, double kappa,
-                                    cudaStream_t st) {
-    if (variant == 1 && prec == 1) return sap_half_staged_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
-    if (variant == 1 && prec == 2) return sap_half_staged_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
-    return launch_sap_half(prec, g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+                                    int nrhs, cudaStream_t st) {
+    if (variant == 1 && prec == 1)
+        return sap_half_staged_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
+    if (variant == 1 && prec == 2)
+        return sap_half_staged_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
+    if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
+    if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
+    return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
 }
 bool sap_staged_supported(int prec, const BlockH& bk) {
     int vb = bk.b[0] * bk.b[1] * bk.b[2] * bk.b[3];
@@ -985,7 +996,7 @@ bool sap_staged_supported(int prec, const BlockH& bk) {
 }
 cudaError_t launch_sap_half(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode, const void* U,
                             const void* C, const void* b, void* x, double kappa, cudaStream_t st) {
-    if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
-    if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
-    return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, st);
+    if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, 1, st);
+    if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, 1, st);
+    return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, 1, st);
 }

@@ -53,15 +53,16 @@ cudaError_t launch_sap_half(int prec, const GeomH& g, const BlockH& bk, int colo
 // variant 1: domain operator staged in shared memory (FP32 / FP16, blocks <= 256 sites)
 cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const BlockH& bk, int colour, int nmr,
                                     int x_mode, const void* U, const void* C, const void* b, void* x, double kappa,
-                                    cudaStream_t s);
+                                    int nrhs, cudaStream_t s);
 bool sap_staged_supported(int prec, const BlockH& bk);
 
 // ---- transfer (fine level 0 -> 1) ----
 // fprec: field precision (0/1/2), vprec: test-vector precision (0/1), cprec: coarse precision (0/1)
+// nrhs fields / coarse vectors one after another (blockIdx.y = right-hand side)
 cudaError_t launch_restrict_fine(int fprec, int vprec, int cprec, const GeomH& g, const BlockH& bk, int nvec,
-                                 const void* vecs, const void* fine, void* coarse, cudaStream_t s);
+                                 const void* vecs, const void* fine, void* coarse, int nrhs, cudaStream_t s);
 cudaError_t launch_prolong_fine(int fprec, int vprec, int cprec, const GeomH& g, const BlockH& bk, int nvec,
-                                const void* vecs, const void* coarse, void* fine, cudaStream_t s);
+                                const void* vecs, const void* coarse, void* fine, int nrhs, cudaStream_t s);
 // block Gram-Schmidt (twice) in FP64 on nvec internal fine vectors; *err_flag set to 1 on rank deficiency
 cudaError_t launch_orthonormalise_fine(int vprec, const GeomH& g, const BlockH& bk, int nvec, void* vecs,
                                        int* err_flag, cudaStream_t s);

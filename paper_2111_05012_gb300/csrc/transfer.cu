@@ -59,6 +59,8 @@ __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __res
     const int nc = 2 * nvec;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const size_t vb = spinor_bytes<PV>(g.V);
+    fine = (const char*)fine + blockIdx.y * spinor_bytes<PF>(g.V);
+    coarse = (char*)coarse + blockIdx.y * (size_t)bk.Vc * nc * sizeof(cx<TC>);
     for (int Xi = blockIdx.x; Xi < bk.Vc; Xi += gridDim.x) {
         const int l = threadIdx.x;
         const bool active = l < bk.Vb;
@@ -107,6 +109,8 @@ __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __rest
     cx<T>* xc = reinterpret_cast<cx<T>*>(smem_raw);   // [2*nvec]
     const int nc = 2 * nvec;
     const size_t vb = spinor_bytes<PV>(g.V);
+    coarse = (const char*)coarse + blockIdx.y * (size_t)bk.Vc * nc * sizeof(cx<TC>);
+    fine = (char*)fine + blockIdx.y * spinor_bytes<PF>(g.V);
     for (int Xi = blockIdx.x; Xi < bk.Vc; Xi += gridDim.x) {
         for (int j = threadIdx.x; j < nc; j += blockDim.x)
             xc[j] = ccast<T>(CStore<TC>::ld(coarse, (size_t)Xi * nc + j));
@@ -299,22 +303,22 @@ int threads_for(const Blocking& bk) { return (bk.Vb + 31) / 32 * 32; }
 
 template <class PF, class PV, typename TC>
 cudaError_t restrict_impl(const GeomH& gh, const BlockH& bh, int nvec, const void* vecs, const void* fine,
-                          void* coarse, cudaStream_t st) {
+                          void* coarse, int nrhs, cudaStream_t st) {
     Geom g = make_geom(gh);
     Blocking bk = make_blocking(gh, bh);
     int th = threads_for(bk);
     size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<typename PF::T>);
-    restrict_kernel<PF, PV, TC><<<bk.Vc, th, smem, st>>>(g, bk, nvec, vecs, fine, coarse);
+    restrict_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, fine, coarse);
     return cudaGetLastError();
 }
 template <class PF, class PV, typename TC>
 cudaError_t prolong_impl(const GeomH& gh, const BlockH& bh, int nvec, const void* vecs, const void* coarse,
-                         void* fine, cudaStream_t st) {
+                         void* fine, int nrhs, cudaStream_t st) {
     Geom g = make_geom(gh);
     Blocking bk = make_blocking(gh, bh);
     int th = threads_for(bk);
     size_t smem = (size_t)2 * nvec * sizeof(cx<typename PF::T>);
-    prolong_kernel<PF, PV, TC><<<bk.Vc, th, smem, st>>>(g, bk, nvec, vecs, coarse, fine);
+    prolong_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, coarse, fine);
     return cudaGetLastError();
 }
 
@@ -326,22 +330,22 @@ cudaError_t prolong_impl(const GeomH& gh, const BlockH& bh, int nvec, const void
     else { using PF = P16; __VA_ARGS__; }
 
 cudaError_t launch_restrict_fine(int fprec, int vprec, int cprec, const GeomH& g, const BlockH& bk, int nvec,
-                                 const void* vecs, const void* fine, void* coarse, cudaStream_t st) {
+                                 const void* vecs, const void* fine, void* coarse, int nrhs, cudaStream_t st) {
     if (vprec == 0) {
-        if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P64, double>(g, bk, nvec, vecs, fine, coarse, st)); }
-        DISPATCH_F(fprec, return restrict_impl<PF, P64, float>(g, bk, nvec, vecs, fine, coarse, st));
+        if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P64, double>(g, bk, nvec, vecs, fine, coarse, nrhs, st)); }
+        DISPATCH_F(fprec, return restrict_impl<PF, P64, float>(g, bk, nvec, vecs, fine, coarse, nrhs, st));
     }
-    if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P32, double>(g, bk, nvec, vecs, fine, coarse, st)); }
-    DISPATCH_F(fprec, return restrict_impl<PF, P32, float>(g, bk, nvec, vecs, fine, coarse, st));
+    if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P32, double>(g, bk, nvec, vecs, fine, coarse, nrhs, st)); }
+    DISPATCH_F(fprec, return restrict_impl<PF, P32, float>(g, bk, nvec, vecs, fine, coarse, nrhs, st));
 }
 cudaError_t launch_prolong_fine(int fprec, int vprec, int cprec, const GeomH& g, const BlockH& bk, int nvec,
-                                const void* vecs, const void* coarse, void* fine, cudaStream_t st) {
+                                const void* vecs, const void* coarse, void* fine, int nrhs, cudaStream_t st) {
     if (vprec == 0) {
-        if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P64, double>(g, bk, nvec, vecs, coarse, fine, st)); }
-        DISPATCH_F(fprec, return prolong_impl<PF, P64, float>(g, bk, nvec, vecs, coarse, fine, st));
+        if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P64, double>(g, bk, nvec, vecs, coarse, fine, nrhs, st)); }
+        DISPATCH_F(fprec, return prolong_impl<PF, P64, float>(g, bk, nvec, vecs, coarse, fine, nrhs, st));
     }
-    if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P32, double>(g, bk, nvec, vecs, coarse, fine, st)); }
-    DISPATCH_F(fprec, return prolong_impl<PF, P32, float>(g, bk, nvec, vecs, coarse, fine, st));
+    if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P32, double>(g, bk, nvec, vecs, coarse, fine, nrhs, st)); }
+    DISPATCH_F(fprec, return prolong_impl<PF, P32, float>(g, bk, nvec, vecs, coarse, fine, nrhs, st));
 }
 cudaError_t launch_orthonormalise_fine(int vprec, const GeomH& gh, const BlockH& bh, int nvec, void* vecs,
                                        int* err, cudaStream_t st) {

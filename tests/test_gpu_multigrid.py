@@ -182,3 +182,52 @@ def test_bad_blocking_is_rejected():
         c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(li.test_vectors(dims, 1, 4))])
     assert e.value.status == c.AMG_EINVAL
     f.close()
+
+
+def test_batched_restrict_prolong(mgcase):
+    import torch
+    f = mgcase
+    c = f.c
+    h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, 1), [li.to_interleaved(f.v0)])
+    dims_c, nc = c.amg_level_info(h, 1)
+    cshape = li.lattice_shape(dims_c)
+    vc = int(np.prod(cshape))
+    psi = np.stack([li.rhs(f.dims, 40 + i) for i in range(3)]).reshape((3,) + f.shape4 + (12,))
+    xc = torch.zeros(3 * vc * nc * 2, dtype=torch.float32, device="cuda")
+    c.amg_restrict(h, 0, to_dev(psi, "float32"), xc, 3, 1)
+    got = from_dev(xc, (3,) + cshape + (nc,))
+    for i in range(3):
+        assert rel(got[i], omg.restrict(f.vo, psi[i], f.block)) < 2e-6
+    fine = torch.zeros(3 * f.V * 24, dtype=torch.float32, device="cuda")
+    c.amg_prolong(h, 0, xc, fine, 3, 1)
+    gotf = from_dev(fine, (3,) + f.shape4 + (12,))
+    for i in range(3):
+        assert rel(gotf[i], omg.prolong(f.vo, got[i], f.block)) < 2e-6
+    c.amg_hierarchy_destroy(h)
+
+
+def test_twelve_point_sources_in_one_batched_solve():
+    import torch
+    dims = (8, 8, 8, 8)
+    f = Field(dims, 0.5, 4, 0.129, 1.0)
+    c = f.c
+    p = _params(c, (4, 4, 4, 4), 8, 1, n_init=2, n_adapt=1)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 4, 8))])
+    srcs = np.stack([li.point_source(dims, s, col) for s in range(4) for col in range(3)])
+    b = to_dev(srcs)
+    x = torch.zeros_like(b)
+    st, info = c.amg_solve(h, b, x, 12, 1e-10, 200)
+    assert info.converged == 1 and info.true_rel_residual <= 1e-10
+    xs = from_dev(x, (12,) + f.shape4 + (12,))
+    op = odirac.WilsonClover(f.U, 0.129, 1.0)
+    for k in range(12):
+        r = srcs[k].reshape(f.shape4 + (12,)) - op.apply(xs[k])
+        assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(srcs[k])
+    # the batch gives the solutions of one-at-a-time solves (to the tolerance)
+    for k in (0, 7):
+        xk = torch.zeros(f.V * 24, dtype=torch.float64, device="cuda")
+        c.amg_solve(h, b[k * f.V * 24:(k + 1) * f.V * 24].contiguous(), xk, 1, 1e-10, 200)
+        one = from_dev(xk, f.shape4 + (12,))
+        assert np.linalg.norm(one - xs[k]) <= 1e-8 * np.linalg.norm(one)
+    c.amg_hierarchy_destroy(h)
+    f.close()
