@@ -165,6 +165,190 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _setup_field(capi, dims, eps, seed, kappa, csw):
+    U = li.gauge_field(dims, eps, seed)
+    lat = capi.amg_lattice_create(dims, True)
+    g = capi.amg_gauge_create(lat, li.to_interleaved(U))
+    d = capi.amg_dirac_create(g, kappa, csw)
+    return U, lat, g, d
+
+
+def run_propagator(args):
+    """12 spin-colour point sources on 48^3x96 (links exp(0.5iH), seed 4,
+    kappa 0.129, c_sw 1.0), 2-level AMG 4^4 / 24 test vectors, FP32 smoother,
+    solved in lockstep batches; value = ms per right-hand side."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_05012_gb300 import capi
+    dims = (48, 48, 48, 96)
+    V = int(np.prod(dims))
+    t0 = time.perf_counter()
+    U, lat, g, d = _setup_field(capi, dims, 0.5, 4, 0.129, 1.0)
+    del U
+    gen_s = time.perf_counter() - t0
+    p = capi.amg_params_default()
+    p.nvec[0] = 24
+    p.outer_m = 8
+    v0 = li.to_interleaved(li.test_vectors(dims, 4, 24))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = capi.amg_setup(d, p, [v0])
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    del v0
+    srcs = np.stack([li.to_interleaved(li.point_source(dims, s, c)).reshape(-1) for s in range(4) for c in range(3)])
+    b = torch.from_numpy(srcs).cuda()
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    capi.amg_solve(h, b[:1].contiguous(), x[:1].contiguous(), 1, TOL, 200, stream=stream)   # warm-up
+    x.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler() as clk:
+        l0 = capi.amg_launch_count()
+        e0.record(stream)
+        st, info = capi.amg_solve(h, b, x, 12, TOL, 200, stream=stream)
+        e1.record(stream)
+        gpu_launches = capi.amg_launch_count() - l0
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    line = {"metric": METRIC, "value": ms / 12, "unit": "ms/RHS", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "48^3x96 Wilson-clover (exp(0.5iH) links, seed 4, kappa 0.129, csw 1.0), "
+                                   "12 spin-colour point sources at the origin, 2-level AMG 4^4 blocks, "
+                                   "24 test vectors, FP32 smoother, lockstep batched FGMRES(8)",
+                       "volume": V, "setup_ms": setup_ms, "field_generation_s": gen_s, "info": info.as_dict()},
+            "gpu_launches": gpu_launches, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args):
+    """Learned preconditioner on 24^3x48 (exp(0.6iH), seed 5, kappa 0.130):
+    train the 1-4-1 parallel-transport network on 4096 (residual, error)
+    pairs from the solver (e = (1 - M D) e0, r = D e), streamed in batches of
+    16, then solve 16 fresh Gaussian right-hand sides (seeds 5000-5015) with
+    and without it."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_05012_gb300 import capi
+    dims = (24, 24, 24, 48)
+    V = int(np.prod(dims))
+    U, lat, g, d = _setup_field(capi, dims, 0.6, 5, 0.130, 1.0)
+    p = capi.amg_params_default()
+    p.nvec[0] = 24
+    v0 = li.to_interleaved(li.test_vectors(dims, 5, 24))
+    h = capi.amg_setup(d, p, [v0])
+    channels = [1, 4, 1]
+    sizes = [channels[l + 1] * channels[l] * 9 * 16 for l in range(2)]
+    w = li.to_interleaved(li.complex_normal(5, li.STREAM_NN, (sum(sizes),)) * 0.02).astype(np.float32).reshape(-1)
+    W1 = np.zeros((4, 1, 9, 4, 4, 2), np.float32)
+    W2 = np.zeros((1, 4, 9, 4, 4, 2), np.float32)
+    for a in range(4):
+        W1[a, 0, 0, range(4), range(4), 0] = 0.5
+        W2[0, a, 0, range(4), range(4), 0] = 0.5
+    nn = capi.amg_nn_create(d, channels, w + np.concatenate([W1.reshape(-1), W2.reshape(-1)]))
+    npairs, batch = args.pairs, 16
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    t0 = time.perf_counter()
+    losses = []
+    De0 = torch.empty(V * 24, dtype=torch.float64, device="cuda")
+    Me = torch.empty_like(De0)
+    for step in range(npairs // batch):
+        rs, es = [], []
+        for k in range(batch):
+            e0 = torch.randn(V * 24, dtype=torch.float64, device="cuda", generator=gen)
+            capi.amg_apply_D(d, e0, De0, 1, capi.AMG_F64)
+            capi.amg_precondition(h, De0, Me)
+            e1 = e0 - Me
+            r1 = torch.empty_like(e1)
+            capi.amg_apply_D(d, e1, r1, 1, capi.AMG_F64)
+            es.append(e1.float())
+            rs.append(r1.float())
+        losses.append(capi.amg_nn_train_step(nn, torch.cat(rs), torch.cat(es), batch, 1e-3))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    res = {}
+    for mode in ("plain", "learned"):
+        capi.amg_hierarchy_set_nn(h, nn if mode == "learned" else None)
+        its, ms_l, rel = [], [], []
+        for k in range(16):
+            bb = torch.from_numpy(li.to_interleaved(li.rhs(dims, 5000 + k - 1000)).reshape(-1)).cuda()
+            x = torch.zeros_like(bb)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            st, info = capi.amg_solve(h, bb, x, 1, TOL, 300)
+            ev1.record()
+            torch.cuda.synchronize()
+            its.append(info.iters)
+            ms_l.append(ev0.elapsed_time(ev1))
+            rel.append(info.true_rel_residual)
+        res[mode] = {"ms_per_rhs": float(np.mean(ms_l)), "outer_iters": float(np.mean(its)),
+                     "max_true_rel_residual": float(np.max(rel)), "fallbacks": int(info.nn_fallback)}
+    line = {"metric": METRIC, "value": res["learned"]["ms_per_rhs"], "unit": "ms/RHS", "n_gpus": 1, "steps": 16,
+            "warmup": 0, "ms_per_step": res["learned"]["ms_per_rhs"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights + f32 + f64", "data": "synthetic",
+            "config": {"workload": "24^3x48 Wilson-clover (exp(0.6iH), seed 5, kappa 0.130, csw 1.0), 2-level AMG "
+                                   "4^4 / 24 test vectors + 1-4-1 PT-conv network",
+                       "pairs": npairs, "train_s": train_s, "loss_first": losses[0], "loss_last": losses[-1],
+                       "plain": res["plain"], "learned": res["learned"]}}
+    print(json.dumps(line), flush=True)
+
+
+def run_dirac(args):
+    """The Wilson-clover stencil alone (Eq. 1) on 32^3x64 (links exp(0.6iH),
+    seed 3, kappa 0.130, c_sw 1.0): mean kernel time per application in FP64,
+    FP32 and FP16, against the HBM roofline.  Compulsory bytes per site: input
+    and output spinor, the site's four links (each link is read by both of its
+    end points, once from HBM) and the clover term.  FP32: 96 + 96 + 4 x 48
+    (two-row links) + 288 = 672 B; FP16: 52 + 52 + 4 x 24 + 144 = 344 B
+    (per-site scale included); FP64: 192 + 192 + 4 x 144 + 576 = 1536 B."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_05012_gb300 import capi
+    dims = (32, 32, 32, 64)
+    V = int(np.prod(dims))
+    t0 = time.perf_counter()
+    U, lat, g, d = _setup_field(capi, dims, 0.6, 3, 0.130, 1.0)
+    del U
+    gen_s = time.perf_counter() - t0
+    psi = li.to_interleaved(li.rhs(dims, 3)).reshape(-1)
+    hbm, kind = _peaks()
+    stream = torch.cuda.current_stream()
+    per = {}
+    bytes_site = {"f64": 1536, "f32": 672, "f16": 344}
+    with ClockSampler() as clk:
+        for name, prec in (("f64", capi.AMG_F64), ("f32", capi.AMG_F32), ("f16", capi.AMG_F16)):
+            x = torch.from_numpy(psi).to(torch.float64 if name == "f64" else torch.float32).cuda()
+            capi.amg_dirac_time(d, x, 1, prec, args.warmup, stream=stream)          # warm-up launches
+            l0 = capi.amg_launch_count()
+            ms = capi.amg_dirac_time(d, x, 1, prec, args.steps, stream=stream)
+            launches = capi.amg_launch_count() - l0
+            gbs = bytes_site[name] * V / (ms * 1e-3) / 1e9
+            per[name] = {"ms_per_apply": ms, "gb_per_s": gbs, "frac_hbm": gbs / hbm, "bytes_per_site": bytes_site[name],
+                         "gflops": 1872 * V / (ms * 1e-3) / 1e9, "launches": launches}
+    f32 = per["f32"]
+    line = {"metric": "Wilson-clover D application, kernel time (HBM roofline)", "value": f32["ms_per_apply"],
+            "unit": "ms/apply", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": f32["ms_per_apply"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "32^3x64 Wilson-clover D (exp(0.6iH) links, seed 3, kappa 0.130, csw 1.0), "
+                                   "1 Gaussian field, internal layout", "volume": V,
+                       "l2": "working set > L2 (no flush)", "field_generation_s": gen_s, "per_precision": per},
+            "roofline": {"kernel": "dirac_kernel<P32>", "bound": "hbm", "achieved": f32["gb_per_s"], "peak": hbm,
+                         "unit": "GB/s", "frac": f32["frac_hbm"], "traffic": None, "peak_kind": kind},
+            "gpu_launches": per["f32"]["launches"], "clocks": clk.summary()}
+    capi.amg_dirac_destroy(d)
+    capi.amg_gauge_destroy(g)
+    capi.amg_lattice_destroy(lat)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,9 +357,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac"])
+    ap.add_argument("--pairs", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "propagator":
+        return run_propagator(args)
+    if args.workload == "learned":
+        return run_learned(args)
+    if args.workload == "dirac":
+        return run_dirac(args)
 
     import torch
     import torch.distributed as dist
@@ -223,12 +415,14 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler() as clk:
         torch.cuda.nvtx.range_push("timed")
+        launches0 = capi.amg_launch_count()
         ev0.record(stream)
         for k in range(args.warmup, nsteps):
             X.zero_()
             st, info = capi.amg_solve(h, B[k], X, 1, TOL, 500, stream=stream)
             infos.append(info.as_dict())
         ev1.record(stream)
+        gpu_launches = capi.amg_launch_count() - launches0
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     if world > 1:
@@ -297,7 +491,7 @@ def main():
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind},
         "e2e": {"value": e2e_ms, "unit": "ms/RHS", "h2d_bytes_per_step": int(hb[0].numel() * 8),
                 "d2h_bytes_per_step": int(hx.numel() * 8)},
-        "gpu_launches": None,
+        "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -90,7 +90,10 @@ typedef struct {
     int outer_m;                        /* outer flexible GMRES restart length [16] */
     int prec_smoother;                  /* fine D / SAP / R / P precision: AMG_F64, AMG_F32, AMG_F16 [AMG_F32] */
     int prec_coarse;                    /* coarse operators above the coarsest: AMG_F64, AMG_F32, AMG_BF16 [AMG_F32] */
-    int prec_coarsest;                  /* coarsest-level solve: AMG_F64 or AMG_F32 [AMG_F32] */
+    int prec_coarsest;                  /* coarsest-level solve: AMG_F64, AMG_F32, or AMG_BF16 =
+                                           FP32 vectors and arithmetic with the coarse operator
+                                           stored in bfloat16 (half the bytes per stencil sweep)
+                                           [AMG_F32] */
     int sap_variant;                    /* SAP kernel: -1 autotune at setup (times both, keeps the faster),
                                            0 operator read from global memory, 1 operator staged in shared
                                            memory (FP32/FP16, blocks <= 256 sites) [-1] */
@@ -113,6 +116,11 @@ typedef struct {
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* amg_last_error(void);
+
+/* Number of CUDA kernel launches this library has issued since it was loaded
+ * (all threads, all devices; a running total, never reset).  No counterpart in
+ * the paper: lets a caller count the kernels behind a call. */
+unsigned long long amg_launch_count(void);
 
 /* Fill p with the defaults listed above. */
 void amg_params_default(amg_params* p);
@@ -166,6 +174,16 @@ amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_pr
  * amg_apply_D (element type double for AMG_F64, float otherwise). */
 amg_status amg_apply_D_noalloc(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s);
 
+/* Timing of the Eq. 1 stencil alone: packs the canonical input `in` (nrhs
+ * fields, element type as for amg_apply_D) into the library's internal layout
+ * once, then applies D to it `reps` times on stream s, bracketed by CUDA
+ * events, and writes the mean milliseconds per application to *ms_per_apply.
+ * The result field is discarded.  Synchronises s.  prec AMG_F64 / AMG_F32 /
+ * AMG_F16.  No counterpart in the paper: the kernel-only time that the HBM
+ * roofline of the stencil is computed from. */
+amg_status amg_dirac_time(amg_dirac* d, const void* in, int nrhs, amg_prec prec, int reps, amg_stream s,
+                          float* ms_per_apply);
+
 /* out = D_SAP in: D with every hop between different blocks of size block[4]
  * switched off (Sec. 3, SAP paragraph).  block must tile the lattice with at
  * least two blocks per direction. */
@@ -179,7 +197,12 @@ amg_status amg_apply_Dsap(amg_dirac* d, const int block[4], const void* in, void
  * (domain, chirality) by Gram-Schmidt applied twice, the Galerkin coarse
  * operator D_c = <I|D|J> (Eq. 6) is built, then n_adapt passes v <- M v
  * follow.  init_vecs[l] is a host array of nvec[l] canonical vectors of
- * level l (doubles); the random numbers of the setup are these inputs.
+ * level l (doubles: fine [site][spin][colour][re, im], coarse
+ * [site][Nc][re, im]), one array for every level 0..nlevels-2; the random
+ * numbers of the setup are these inputs.  With three or more grids, level
+ * l >= 1 is set up the same way with its own SAP and cycle, right after its
+ * stencil is first built; every later change of level l's stencil rebuilds
+ * the stencils below it from their unchanged vectors.
  * Fails with AMG_EINVAL on a bad blocking or a rank-deficient domain. */
 amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* init_vecs,
                      amg_hierarchy** out);
@@ -200,7 +223,8 @@ amg_status amg_get_vectors(amg_hierarchy* h, int coarsening, double* host_out);
 
 /* Coarse operator of level l >= 1 as host doubles [site][d 9][Nc][Nc][re, im]
  * with d = 0 self, 1+mu the block coupling X to X+mu, 5+mu to X-mu, so that
- * y(X) = sum_d B[X][d] x(X + d) (the 9-point stencil of Eq. 6). */
+ * y(X) = sum_d B[X][d] x(X + d) (the 9-point stencil of Eq. 6).  Returned as
+ * computed (FP64 or FP32), before any bfloat16 storage rounding. */
 amg_status amg_get_coarse_op(amg_hierarchy* h, int level, double* host_out);
 
 /* Save / load the test vectors and parameters of a hierarchy (the setup is
@@ -212,12 +236,15 @@ amg_status amg_setup_load(amg_dirac* d, const char* path, amg_hierarchy** out);
 /* ---- transfer and coarse operators (Eqs. 4-6) -------------------------- */
 
 /* y = D_c x on level l >= 1 (the 9-point stencil), nrhs canonical coarse
- * vectors; prec AMG_F64 (double vectors) or AMG_F32 / AMG_BF16 (float). */
+ * vectors; prec AMG_F64 (double vectors) or AMG_F32 / AMG_BF16 (float).  The
+ * operator is applied as the level stores it (bfloat16 entries with FP32
+ * accumulation when the hierarchy was built with prec_coarsest = AMG_BF16). */
 amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* out, int nrhs,
                             amg_prec prec, amg_stream s);
 
 /* Eq. 4: coarse(I) = <I|fine> from level `coarsening` to coarsening+1.
- * fine is canonical at that level; element type from prec as above. */
+ * fine is canonical at that level (a fine field for coarsening 0, a coarse
+ * vector [site][Nc] for coarsening >= 1); element type from prec as above. */
 amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void* coarse, int nrhs,
                         amg_prec prec, amg_stream s);
 
@@ -229,6 +256,13 @@ amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, voi
  * {x += M_e r; r = b - Dx; x += M_o r; r = b - Dx}, M = mr_iters minimal
  * residual steps per domain), in the smoother precision. Canonical vectors. */
 amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_stream s);
+
+/* x = SAP(b) on coarse level 1 <= level <= nlevels-2 (three or more grids):
+ * the same listing with the level's blocks as domains and D_SAP the level's
+ * 9-point stencil without the hops between blocks.  nrhs canonical coarse
+ * vectors; prec AMG_F64 (double) or AMG_F32 / AMG_BF16 (float). */
+amg_status amg_sap_coarse(amg_hierarchy* h, int level, const void* b, void* x, int nrhs, amg_prec prec,
+                          amg_stream s);
 
 /* x = M b: one application of the multigrid preconditioner (Sec. 3 steps
  * (1) and (2)).  Canonical double vectors. */

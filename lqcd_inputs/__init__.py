@@ -160,6 +160,14 @@ def test_vectors(dims, seed: int, nvec: int) -> np.ndarray:
     return np.stack([gaussian_spinor(dims, seed + 2000, STREAM_TESTVEC, i) for i in range(nvec)])
 
 
+def coarse_test_vectors(cdims, seed: int, nvec: int, ndof: int, level: int = 1) -> np.ndarray:
+    """Initial random test vectors of coarse level ``level`` (three or more
+    grids): complex Gaussian, stream of seed + 2000 + 1000 * level,
+    shape (nvec, Lt, Lz, Ly, Lx, ndof)."""
+    shp = lattice_shape(cdims)
+    return complex_normal(seed + 2000 + 1000 * level, STREAM_TESTVEC, (nvec,) + shp + (ndof,))
+
+
 def point_source(dims, spin: int, colour: int, site=(0, 0, 0, 0)) -> np.ndarray:
     """Point source delta_{x,site} delta_{s,spin} delta_{c,colour}; site = (x, y, z, t)."""
     shp = lattice_shape(dims)

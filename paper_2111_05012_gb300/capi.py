@@ -80,6 +80,7 @@ _d = ctypes.c_double
 # name -> (restype, argtypes); the list mirrors include/lqcd_amg.h
 PROTOTYPES = {
     "amg_last_error": (ctypes.c_char_p, []),
+    "amg_launch_count": (ctypes.c_ulonglong, []),
     "amg_params_default": (None, [ctypes.POINTER(amg_params)]),
     "amg_lattice_create": (_i, [_ip, _i, ctypes.POINTER(_vp)]),
     "amg_lattice_destroy": (None, [_vp]),
@@ -91,6 +92,7 @@ PROTOTYPES = {
     "amg_apply_D": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "amg_apply_D_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "amg_apply_Dsap": (_i, [_vp, _ip, _vp, _vp, _i, _i, _vp]),
+    "amg_dirac_time": (_i, [_vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_float)]),
     "amg_setup": (_i, [_vp, ctypes.POINTER(amg_params), ctypes.POINTER(_dp), ctypes.POINTER(_vp)]),
     "amg_setup_from_vectors": (_i, [_vp, ctypes.POINTER(amg_params), ctypes.POINTER(_dp), ctypes.POINTER(_vp)]),
     "amg_hierarchy_destroy": (None, [_vp]),
@@ -103,6 +105,7 @@ PROTOTYPES = {
     "amg_restrict": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "amg_prolong": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "amg_sap": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "amg_sap_coarse": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "amg_precondition": (_i, [_vp, _vp, _vp, _vp]),
     "amg_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, ctypes.POINTER(amg_solve_info), _vp]),
     "amg_nn_create": (_i, [_vp, _i, _ip, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
@@ -168,6 +171,10 @@ def amg_last_error():
     return load().amg_last_error().decode()
 
 
+def amg_launch_count():
+    return int(load().amg_launch_count())
+
+
 def amg_params_default():
     p = amg_params()
     load().amg_params_default(ctypes.byref(p))
@@ -220,14 +227,24 @@ def amg_apply_D_noalloc(d, inp, out, nrhs=1, prec=AMG_F64, stream=None):
     _check(load().amg_apply_D_noalloc(d, _ptr(inp), _ptr(out), int(nrhs), int(prec), _stream(stream)))
 
 
+def amg_dirac_time(d, inp, nrhs=1, prec=AMG_F32, reps=20, stream=None):
+    """Mean milliseconds per application of D (internal layout, kernel only)."""
+    ms = ctypes.c_float()
+    _check(load().amg_dirac_time(d, _ptr(inp), int(nrhs), int(prec), int(reps), _stream(stream), ctypes.byref(ms)))
+    return float(ms.value)
+
+
 def amg_apply_Dsap(d, block, inp, out, nrhs=1, prec=AMG_F64, stream=None):
     _check(load().amg_apply_Dsap(d, (ctypes.c_int * 4)(*block), _ptr(inp), _ptr(out), int(nrhs), int(prec),
                                  _stream(stream)))
 
 
 def _vec_list(vecs):
+    """Pointer array of AMG_MAX_LEVELS entries (NULL past the given levels)."""
     arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in vecs]
-    lst = (_dp * len(arrs))(*[a.ctypes.data_as(_dp) for a in arrs])
+    if len(arrs) > AMG_MAX_LEVELS:
+        raise ValueError("more vector sets than levels")
+    lst = (_dp * AMG_MAX_LEVELS)(*[a.ctypes.data_as(_dp) for a in arrs])
     return arrs, lst
 
 
@@ -297,6 +314,10 @@ def amg_prolong(h, coarsening, coarse, fine, nrhs=1, prec=AMG_F64, stream=None):
 
 def amg_sap(h, b, x, prec=AMG_F32, stream=None):
     _check(load().amg_sap(h, _ptr(b), _ptr(x), int(prec), _stream(stream)))
+
+
+def amg_sap_coarse(h, level, b, x, nrhs=1, prec=AMG_F32, stream=None):
+    _check(load().amg_sap_coarse(h, int(level), _ptr(b), _ptr(x), int(nrhs), int(prec), _stream(stream)))
 
 
 def amg_precondition(h, b, x, stream=None):

@@ -5,6 +5,7 @@
 #include "kernels.h"
 #include "lqcd_amg.h"
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -60,9 +61,17 @@ namespace {
 struct CoarseLevel {
     GeomH g;
     int nc = 0;
-    int prec = 1;
-    DevBuf B;
+    int prec = 1;        // vector / arithmetic precision: 0 FP64, 1 FP32
+    bool opbf = false;   // operator additionally stored in bfloat16 (B16) and applied from there
+    DevBuf B, B16;
     DevBuf cs_part, cs_state;   // persistent coarse solver scratch
+    // levels between the fine and the coarsest grid: the level's own test
+    // vectors (coarsening to the next level) and its FGMRES(inter_m) space
+    DevBuf cvecs;
+    std::vector<DevBuf> gV, gZ;
+    DevBuf gw, gr, gt;
+    int kprec() const { return opbf ? 2 : prec; }   // precision code of the stencil kernels
+    const void* op() const { return opbf ? B16.p : B.p; }
 };
 
 // pinned partial-sum staging for reductions
@@ -209,7 +218,7 @@ size_t coarse_n(const CoarseLevel& L) { return (size_t)L.g.V * L.nc; }
 
 amg_status check_params(const GeomH& g, const amg_params* p) {
     if (!p) return fail(AMG_EINVAL, "params is NULL");
-    if (p->nlevels != 2) return fail(AMG_EINVAL, "nlevels must be 2 in this build");
+    if (p->nlevels < 2 || p->nlevels > AMG_MAX_LEVELS) return fail(AMG_EINVAL, "nlevels must be 2..4");
     int L[4] = {g.L[0], g.L[1], g.L[2], g.L[3]};
     for (int l = 0; l < p->nlevels - 1; ++l) {
         if (p->nvec[l] < 1 || p->nvec[l] > 64) return fail(AMG_EINVAL, "nvec must be in 1..64");
@@ -223,9 +232,30 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
         }
         int vb = p->block[l][0] * p->block[l][1] * p->block[l][2] * p->block[l][3];
         if (vb > 512) return fail(AMG_EINVAL, "block volume must be <= 512 sites");
+        if (l >= 1) {
+            // coarse-level Galerkin kernel: Nc_next = 2 nvec <= 64 and its shared-memory tiles
+            const int nc = 2 * p->nvec[l - 1], nv = p->nvec[l];
+            const size_t esz = p->prec_coarse == AMG_F64 ? 16 : 8;
+            if (nv > 32) return fail(AMG_EINVAL, "nvec of a coarse level must be <= 32");
+            if ((size_t)(4 * nc * nv + nc * nc) * esz > 200 * 1024)
+                return fail(AMG_EINVAL, "coarse level too wide for the Galerkin kernel's shared memory");
+        }
+    }
+    if (p->nlevels >= 3) {
+        if (p->prec_coarse != AMG_F64 && p->prec_coarse != AMG_F32 && p->prec_coarse != AMG_BF16)
+            return fail(AMG_EINVAL, "prec_coarse must be AMG_F64, AMG_F32 or AMG_BF16");
+        if ((p->prec_coarse == AMG_F64) != (p->prec_coarsest == AMG_F64))
+            return fail(AMG_EINVAL, "prec_coarse and prec_coarsest must both be FP64 or both not");
+        if (p->inter_m < 1 || p->inter_m > 19 || p->inter_maxit < 1 || !(p->inter_tol > 0))
+            return fail(AMG_EINVAL, "inter_m must be 1..19, inter_maxit >= 1, inter_tol > 0");
     }
     if (p->prec_smoother < 0 || p->prec_smoother > 2) return fail(AMG_EINVAL, "prec_smoother");
-    if (p->prec_coarsest < 0 || p->prec_coarsest > 1) return fail(AMG_EINVAL, "prec_coarsest");
+    if (p->prec_coarsest != AMG_F64 && p->prec_coarsest != AMG_F32 && p->prec_coarsest != AMG_BF16)
+        return fail(AMG_EINVAL, "prec_coarsest must be AMG_F64, AMG_F32 or AMG_BF16");
+    // the coarse solver streams operator rows with bulk copies that need 16-byte multiples:
+    // 9 * Nc bfloat16 pairs per row, so Nc = 2 nvec must be a multiple of 4
+    if (p->prec_coarsest == AMG_BF16 && p->nvec[p->nlevels - 2] % 2 != 0)
+        return fail(AMG_EINVAL, "a bfloat16 coarsest operator needs an even number of test vectors");
     if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
     if (p->sap_iters < 0 || p->mr_iters < 0) return fail(AMG_EINVAL, "sap_iters / mr_iters");
@@ -265,7 +295,7 @@ CoarseLevel& L1(amg_hierarchy* h) { return h->lev[1]; }
 
 amg_status coarse_apply(amg_hierarchy* h, int l, const void* in, void* out, const void* b, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
-    CK(launch_coarse_apply(L.prec, L.g, L.nc, nullptr, L.B.p, in, out, b, 1, s));
+    CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), in, out, b, 1, s));
     return AMG_OK;
 }
 
@@ -285,7 +315,7 @@ amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int 
     const size_t cv = coarse_n(L) * coarse_elem_bytes(L.prec);
     for (int q = 0; q < nb; ++q) {
         CK(cudaMemsetAsync(L.cs_state.p, 0, 12, s));
-        CK(launch_coarse_bicgstab(L.prec, L.g, L.nc, L.B.p, (const char*)b + q * cv, (char*)x + q * cv, w[2]->p, R,
+        CK(launch_coarse_bicgstab(L.kprec(), L.g, L.nc, L.op(), (const char*)b + q * cv, (char*)x + q * cv, w[2]->p, R,
                                   U, ell, h->p.coarse_tol, h->p.coarse_maxit, L.cs_part.p, L.cs_state.p, s));
         // error word of this solve (a later one would overwrite it): fold into word 2 of the host mirror
         CK(cudaMemcpyAsync(h->hstate + 4 * (q % 16), L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
@@ -302,6 +332,159 @@ amg_status coarse_status(amg_hierarchy* h) {
     return AMG_OK;
 }
 
+// ---------------------------------------------------------------- levels >= 1 of three or more grids
+amg_status coarse_solve(amg_hierarchy* h, int l, const void* b, void* x, int nb, cudaStream_t s);
+
+size_t cvec_bytes(const CoarseLevel& L) { return coarse_n(L) * coarse_elem_bytes(L.prec); }
+
+// SAP (Sec. 3 listing) on level l, started from x (or from zero), right-hand side b
+amg_status coarse_sap(amg_hierarchy* h, int l, const void* b, void* x, bool x_zero, int nb, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    for (int i = 0; i < h->p.sap_iters; ++i) {
+        const bool first = x_zero && i == 0;
+        CK(launch_coarse_sap_half(L.kprec(), L.g, h->blk[l], L.nc, 0, h->p.mr_iters, first ? 1 : 0, L.op(), b, x,
+                                  nb, s));
+        CK(launch_coarse_sap_half(L.kprec(), L.g, h->blk[l], L.nc, 1, h->p.mr_iters, first ? 2 : 0, L.op(), b, x,
+                                  nb, s));
+    }
+    if (h->p.sap_iters == 0 && x_zero) CK(cudaMemsetAsync(x, 0, cvec_bytes(L) * nb, s));
+    return AMG_OK;
+}
+
+// x = M_l b on level l >= 1: steps (1) and (2) of Sec. 3 one level down
+amg_status vcycle_c(amg_hierarchy* h, int l, const void* b, void* x, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    auto& w = h->cw[l + 1];
+    CK(launch_restrict_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, b, w[0]->p, 1, s));
+    TRY(coarse_solve(h, l + 1, w[0]->p, w[1]->p, 1, s));
+    CK(launch_prolong_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, w[1]->p, x, 1, s));
+    return coarse_sap(h, l, b, x, false, 1, s);
+}
+
+// one Givens step of the least-squares update of a flexible GMRES column j
+void givens_column(std::vector<std::vector<cplx>>& H, std::vector<double>& cs, std::vector<cplx>& sn,
+                   std::vector<cplx>& g, int j) {
+    for (int i = 0; i < j; ++i) {
+        cplx a = H[i][j], bb = H[i + 1][j];
+        H[i][j] = cs[i] * a + sn[i] * bb;
+        H[i + 1][j] = -std::conj(sn[i]) * a + cs[i] * bb;
+    }
+    cplx a = H[j][j], bb = H[j + 1][j];
+    double aa = std::abs(a), ab = std::abs(bb);
+    if (ab == 0) {
+        cs[j] = 1;
+        sn[j] = 0;
+    } else if (aa == 0) {
+        cs[j] = 0;
+        sn[j] = std::conj(bb) / ab;
+    } else {
+        double t = std::sqrt(aa * aa + ab * ab);
+        cs[j] = aa / t;
+        sn[j] = (a / aa) * std::conj(bb) / t;
+    }
+    H[j][j] = cs[j] * a + sn[j] * bb;
+    H[j + 1][j] = 0;
+    g[j + 1] = -std::conj(sn[j]) * g[j];
+    g[j] = cs[j] * g[j];
+}
+
+// Flexible GMRES(inter_m) on an intermediate level l, preconditioned by the
+// level's own cycle, from x = 0 until the residual is below inter_tol |b| or
+// inter_maxit steps were taken; the true residual b - D_l x is recomputed
+// after every cycle (reading C12).  Vectors in the level's precision,
+// reductions in FP64.
+amg_status fgmres_c(amg_hierarchy* h, int l, const void* b, void* x, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    const int m = h->p.inter_m, pr = L.prec;
+    const size_t n = coarse_n(L), vb = cvec_bytes(L);
+    const double tol = h->p.inter_tol;
+    Reducer& red = h->red;
+    CK(cudaMemsetAsync(x, 0, vb, s));
+    double bn2;
+    TRY(red.norm2(pr, b, n, &bn2, s));
+    TRY(coarse_status(h));
+    if (!std::isfinite(bn2)) return fail(AMG_NAN, "intermediate solve: non-finite right-hand side");
+    const double bn = std::sqrt(bn2);
+    if (bn == 0) return AMG_OK;
+    int iters = 0;
+    bool first = true;
+    std::vector<std::vector<cplx>> H(m + 1, std::vector<cplx>(m));
+    std::vector<double> cs(m);
+    std::vector<cplx> sn(m), g(m + 1);
+    while (true) {
+        double rn;
+        if (first) {   // x = 0: r = b
+            CK(cudaMemcpyAsync(L.gr.p, b, vb, cudaMemcpyDeviceToDevice, s));
+            rn = bn;
+            first = false;
+        } else {
+            CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), x, L.gr.p, b, 1, s));
+            double rn2;
+            TRY(red.norm2(pr, L.gr.p, n, &rn2, s));
+            TRY(coarse_status(h));
+            if (!std::isfinite(rn2)) return fail(AMG_NAN, "intermediate solve: non-finite residual");
+            rn = std::sqrt(rn2);
+        }
+        if (rn <= tol * bn || iters >= h->p.inter_maxit) return AMG_OK;
+        for (auto& row : H) std::fill(row.begin(), row.end(), cplx(0));
+        std::fill(g.begin(), g.end(), cplx(0));
+        g[0] = rn;
+        CK(launch_axpby(pr, make_double2(1.0 / rn, 0), L.gr.p, make_double2(0, 0), L.gV[0].p, n, s));
+        int jend = -1;
+        for (int j = 0; j < m; ++j) {
+            TRY(vcycle_c(h, l, L.gV[j].p, L.gZ[j].p, s));
+            CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), L.gZ[j].p, L.gw.p, nullptr, 1, s));
+            std::vector<const void*> vl(j + 1);
+            for (int i = 0; i <= j; ++i) vl[i] = L.gV[i].p;
+            std::vector<cplx> c(j + 1);
+            std::vector<double2> nc(j + 1);
+            for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+                TRY(red.dots(pr, j + 1, vl.data(), L.gw.p, n, c.data(), s));
+                if (pass == 0) TRY(coarse_status(h));
+                for (int i = 0; i <= j; ++i) {
+                    H[i][j] += c[i];
+                    nc[i] = make_double2(-c[i].real(), -c[i].imag());
+                }
+                CK(launch_multi_axpy(pr, j + 1, nc.data(), vl.data(), L.gw.p, n, s));
+            }
+            double hn2;
+            TRY(red.norm2(pr, L.gw.p, n, &hn2, s));
+            const double hn = std::sqrt(hn2);
+            H[j + 1][j] = hn;
+            ++iters;
+            givens_column(H, cs, sn, g, j);
+            jend = j;
+            const double est = std::abs(g[j + 1]);
+            if (!std::isfinite(est)) return fail(AMG_NAN, "intermediate solve: non-finite Arnoldi coefficient");
+            if (hn == 0 || est <= tol * bn || iters >= h->p.inter_maxit) break;
+            CK(launch_axpby(pr, make_double2(1.0 / hn, 0), L.gw.p, make_double2(0, 0), L.gV[j + 1].p, n, s));
+        }
+        const int k = jend + 1;
+        std::vector<cplx> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            cplx t = g[i];
+            for (int c = i + 1; c < k; ++c) t -= H[i][c] * y[c];
+            y[i] = t / H[i][i];
+        }
+        std::vector<double2> yc(k);
+        std::vector<const void*> zl(k);
+        for (int i = 0; i < k; ++i) {
+            yc[i] = d2(y[i]);
+            zl[i] = L.gZ[i].p;
+        }
+        CK(launch_multi_axpy(pr, k, yc.data(), zl.data(), x, n, s));
+    }
+}
+
+// loose solve on level l: BiCGStab(ell) on the coarsest level, else the
+// level's flexible GMRES (one right-hand side at a time)
+amg_status coarse_solve(amg_hierarchy* h, int l, const void* b, void* x, int nb, cudaStream_t s) {
+    if (l == h->p.nlevels - 1) return coarse_bicgstab(h, l, b, x, nb, s);
+    const size_t vb = cvec_bytes(h->lev[l]);
+    for (int q = 0; q < nb; ++q) TRY(fgmres_c(h, l, (const char*)b + q * vb, (char*)x + q * vb, s));
+    return AMG_OK;
+}
+
 // ---------------------------------------------------------------- V-cycle
 // x = M b on the fine lattice in precision prec (b, x internal fields, nb of them):
 // step (1) x = P D_c^{-1} R b, step (2) x += SAP(b - D x).
@@ -313,7 +496,7 @@ amg_status vcycle0(amg_hierarchy* h, int prec, const void* b, void* x, int nb, c
                             s));
     h->timer.stop(s);
     h->timer.start(PH_COARSE, s);
-    TRY(coarse_bicgstab(h, 1, w[0]->p, w[1]->p, nb, s));
+    TRY(coarse_solve(h, 1, w[0]->p, w[1]->p, nb, s));
     h->timer.stop(s);
     h->timer.start(PH_RP, s);
     CK(launch_prolong_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, w[1]->p, x, nb,
@@ -595,6 +778,18 @@ amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
         while ((int)h->cw[l].size() < nv) h->cw[l].push_back(new DevBuf());
         for (int k = 0; k < nv; ++k) CK(h->cw[l][k]->ensure(bytes * (k < 2 ? nb : 1)));
     }
+    for (int l = 1; l + 1 < h->p.nlevels; ++l) {
+        CoarseLevel& L = h->lev[l];
+        const size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
+        CK(L.cvecs.ensure(bytes * h->p.nvec[l]));
+        L.gV.resize(h->p.inter_m + 1);
+        L.gZ.resize(h->p.inter_m);
+        for (auto& v : L.gV) CK(v.ensure(bytes));
+        for (auto& z : L.gZ) CK(z.ensure(bytes));
+        CK(L.gw.ensure(bytes));
+        CK(L.gr.ensure(bytes));
+        CK(L.gt.ensure(bytes));
+    }
     const size_t fb64 = fine_spinor_bytes(0, g.V) * nb;
     CK(h->ob.ensure(fb64));
     CK(h->ox.ensure(fb64));
@@ -622,8 +817,12 @@ amg_status build_levels(amg_hierarchy* h) {
         }
         L.g.antiperiodic = 0;
         L.nc = 2 * h->p.nvec[l];
-        L.prec = (l + 1 == h->p.nlevels - 1) ? h->p.prec_coarsest : (h->p.prec_coarse == 0 ? 0 : 1);
-        CK(L.B.ensure((size_t)L.g.V * 9 * L.nc * L.nc * coarse_elem_bytes(L.prec)));
+        const bool last = l + 1 == h->p.nlevels - 1;
+        L.opbf = last ? h->p.prec_coarsest == AMG_BF16 : h->p.prec_coarse == AMG_BF16;
+        L.prec = last ? (h->p.prec_coarsest == AMG_F64 ? 0 : 1) : (h->p.prec_coarse == 0 ? 0 : 1);
+        const size_t ne = (size_t)L.g.V * 9 * L.nc * L.nc;
+        CK(L.B.ensure(ne * coarse_elem_bytes(L.prec)));
+        if (L.opbf) CK(L.B16.ensure(ne * 4));
         cur = L.g;
     }
     CK(h->vecs0.ensure(fine_spinor_bytes(h->vp, g.V) * h->p.nvec[0]));
@@ -642,6 +841,7 @@ amg_status orthonormalise_and_galerkin(amg_hierarchy* h, cudaStream_t s) {
     CoarseLevel& L = L1(h);
     CK(launch_galerkin_fine(h->vp, L.prec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, d->gauge->U[h->vp].p,
                             d->C[h->vp].p, d->kappa, L.B.p, s));
+    if (L.opbf) CK(launch_complex_to_bf16(L.B.p, L.B16.p, (size_t)L.g.V * 9 * L.nc * L.nc, s));
     return AMG_OK;
 }
 
@@ -671,6 +871,88 @@ amg_status normalise_into(amg_hierarchy* h, int prec, const void* src, void* dst
     TRY(coarse_status(h));
     if (!(nn > 0) || !std::isfinite(nn)) return fail(AMG_NAN, "setup: test vector vanished or is not finite");
     CK(launch_axpby(prec, make_double2(1.0 / std::sqrt(nn), 0), src, make_double2(0, 0), dst, n, s));
+    return AMG_OK;
+}
+
+// ---- setup of the levels between the fine and the coarsest grid
+// level-l test vectors from host doubles [nvec][V_l][nc][re, im]
+amg_status upload_cvecs(amg_hierarchy* h, int l, const double* host, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    const size_t n = coarse_n(L) * h->p.nvec[l];
+    if (L.prec == 0) {
+        CK(cudaMemcpyAsync(L.cvecs.p, host, n * 16, cudaMemcpyHostToDevice, s));
+    } else {
+        CK(h->canon.ensure(n * 16));
+        CK(cudaMemcpyAsync(h->canon.p, host, n * 16, cudaMemcpyHostToDevice, s));
+        CK(launch_convert_flat(0, 1, h->canon.p, L.cvecs.p, n, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+// Eq. 6 one level down: stencil of level l+1 from level l's stencil and vectors
+amg_status galerkin_c(amg_hierarchy* h, int l, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    CoarseLevel& N = h->lev[l + 1];
+    CK(launch_galerkin_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, L.B.p, N.B.p, s));
+    if (N.opbf) CK(launch_complex_to_bf16(N.B.p, N.B16.p, (size_t)N.g.V * 9 * N.nc * N.nc, s));
+    return AMG_OK;
+}
+
+amg_status ortho_galerkin_c(amg_hierarchy* h, int l, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    CK(cudaMemsetAsync(h->err_flag.p, 0, sizeof(int), s));
+    CK(launch_orthonormalise_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, h->err_flag.as<int>(),
+                                    s));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (flag) return fail(AMG_EINVAL, "coarse test vectors are rank deficient on some domain");
+    return galerkin_c(h, l, s);
+}
+
+// rebuild the stencils below level l after level l's stencil changed
+amg_status refresh_c(amg_hierarchy* h, int l, cudaStream_t s) {
+    for (int k = l; k + 1 < h->p.nlevels; ++k) TRY(galerkin_c(h, k, s));
+    return AMG_OK;
+}
+
+amg_status normalise_c(amg_hierarchy* h, int l, const void* src, void* dst, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    const size_t n = coarse_n(L);
+    double nn;
+    TRY(h->red.norm2(L.prec, src, n, &nn, s));
+    TRY(coarse_status(h));
+    if (!(nn > 0) || !std::isfinite(nn)) return fail(AMG_NAN, "setup: coarse test vector vanished or is not finite");
+    CK(launch_axpby(L.prec, make_double2(1.0 / std::sqrt(nn), 0), src, make_double2(0, 0), dst, n, s));
+    return AMG_OK;
+}
+
+// steps (0-a) and (0-b) on level l >= 1 (reading C6): smooth the level's
+// initial vectors with its SAP, orthonormalise, build the next stencil, set up
+// the next level, then n_adapt passes v <- M_l v with rebuilt stencils below
+amg_status setup_coarse_level(amg_hierarchy* h, int l, const double* const* init, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    if (!init[l]) return fail(AMG_EINVAL, "initial test vectors missing for a coarse level");
+    TRY(upload_cvecs(h, l, init[l], s));
+    const size_t vb = cvec_bytes(L);
+    for (int k = 0; k < h->p.n_init; ++k)
+        for (int i = 0; i < h->p.nvec[l]; ++i) {
+            void* vi = (char*)L.cvecs.p + i * vb;
+            TRY(coarse_sap(h, l, vi, L.gt.p, true, 1, s));
+            TRY(normalise_c(h, l, L.gt.p, vi, s));
+        }
+    TRY(ortho_galerkin_c(h, l, s));
+    if (l + 2 < h->p.nlevels) TRY(setup_coarse_level(h, l + 1, init, s));
+    for (int k = 0; k < h->p.n_adapt; ++k) {
+        for (int i = 0; i < h->p.nvec[l]; ++i) {
+            void* vi = (char*)L.cvecs.p + i * vb;
+            TRY(vcycle_c(h, l, vi, L.gt.p, s));
+            TRY(normalise_c(h, l, L.gt.p, vi, s));
+        }
+        TRY(ortho_galerkin_c(h, l, s));
+        TRY(refresh_c(h, l + 1, s));
+    }
     return AMG_OK;
 }
 
@@ -751,9 +1033,14 @@ double amg_internal_kappa(const amg_dirac* d) { return d->kappa; }
 void amg_internal_set_error(const char* msg) { g_err = msg; }
 
 // ================================================================ C ABI
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 extern "C" {
 
 const char* amg_last_error(void) { return g_err.c_str(); }
+
+unsigned long long amg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void amg_params_default(amg_params* p) {
     if (!p) return;
@@ -887,6 +1174,35 @@ amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_pr
     return apply_fine_canonical(d, nullptr, in, out, nrhs, prec, (cudaStream_t)s);
 }
 
+amg_status amg_dirac_time(amg_dirac* d, const void* in, int nrhs, amg_prec prec, int reps, amg_stream s,
+                          float* ms_per_apply) {
+    if (!d || !in || !ms_per_apply || nrhs < 1 || reps < 1) return fail(AMG_EINVAL, "bad argument");
+    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32 or AMG_F16");
+    const GeomH& g = d->gauge->lat->g;
+    cudaStream_t st = (cudaStream_t)s;
+    size_t fb = fine_spinor_bytes(prec, g.V) * nrhs;
+    CK(d->in.ensure(fb));
+    CK(d->out.ensure(fb));
+    CK(launch_pack_spinor(prec, g, in, d->in.p, nrhs, st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    amg_status rc = AMG_OK;
+    cudaError_t err = cudaEventRecord(e0, st);
+    for (int i = 0; err == cudaSuccess && i < reps; ++i)
+        err = launch_dirac(prec, g, nullptr, d->gauge->U[prec].p, d->C[prec].p, d->in.p, d->out.p, nullptr, d->kappa,
+                           nrhs, st);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err != cudaSuccess) rc = fail(AMG_ECUDA, cudaGetErrorString(err));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_apply = ms / reps;
+    return rc;
+}
+
 amg_status amg_apply_Dsap(amg_dirac* d, const int block[4], const void* in, void* out, int nrhs, amg_prec prec,
                           amg_stream s) {
     if (!d || !block) return fail(AMG_EINVAL, "NULL argument");
@@ -908,6 +1224,11 @@ amg_status amg_setup_from_vectors(amg_dirac* d, const amg_params* p, const doubl
     cudaStream_t s = 0;
     amg_status st = upload_vectors(h, vecs[0], s);
     if (st == AMG_OK) st = orthonormalise_and_galerkin(h, s);
+    for (int l = 1; st == AMG_OK && l + 1 < h->p.nlevels; ++l) {
+        if (!vecs[l]) st = fail(AMG_EINVAL, "test vectors missing for a coarse level");
+        if (st == AMG_OK) st = upload_cvecs(h, l, vecs[l], s);
+        if (st == AMG_OK) st = ortho_galerkin_c(h, l, s);
+    }
     if (st == AMG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(AMG_ECUDA, "setup failed");
     if (st != AMG_OK) {
         delete h;
@@ -936,6 +1257,7 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
             }
         }
         TRY(orthonormalise_and_galerkin(h, s));
+        if (h->p.nlevels > 2) TRY(setup_coarse_level(h, 1, init_vecs, s));
         // (0-b): v <- M v with the current hierarchy, then rebuild
         for (int k = 0; k < h->p.n_adapt; ++k) {
             for (int i = 0; i < h->p.nvec[0]; ++i) {
@@ -944,6 +1266,7 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
                 TRY(normalise_into(h, vp, h->tmpv.p, vi, s));
             }
             TRY(orthonormalise_and_galerkin(h, s));
+            TRY(refresh_c(h, 1, s));
         }
         CK(cudaStreamSynchronize(s));
         return AMG_OK;
@@ -968,7 +1291,19 @@ amg_status amg_level_info(amg_hierarchy* h, int level, int dims_out[4], int* nc_
 }
 
 amg_status amg_get_vectors(amg_hierarchy* h, int coarsening, double* host_out) {
-    if (!h || !host_out || coarsening != 0) return fail(AMG_EINVAL, "bad argument");
+    if (!h || !host_out || coarsening < 0 || coarsening > h->p.nlevels - 2) return fail(AMG_EINVAL, "bad argument");
+    if (coarsening > 0) {
+        CoarseLevel& L = h->lev[coarsening];
+        const size_t n = coarse_n(L) * h->p.nvec[coarsening];
+        const void* src = L.cvecs.p;
+        if (L.prec != 0) {
+            CK(h->canon.ensure(n * 16));
+            CK(launch_convert_flat(1, 0, L.cvecs.p, h->canon.p, n, 0));
+            src = h->canon.p;
+        }
+        CK(cudaMemcpy(host_out, src, n * 16, cudaMemcpyDeviceToHost));
+        return AMG_OK;
+    }
     const GeomH& g = fine_geom(h);
     const size_t vb = fine_spinor_bytes(h->vp, g.V);
     const size_t cb = (size_t)g.V * 24 * sizeof(double);
@@ -1003,13 +1338,18 @@ amg_status amg_setup_save(const amg_hierarchy* hc, const char* path) {
     amg_hierarchy* h = const_cast<amg_hierarchy*>(hc);
     if (!h || !path) return fail(AMG_EINVAL, "NULL argument");
     const GeomH& g = fine_geom(h);
-    std::vector<double> v((size_t)h->p.nvec[0] * g.V * 24);
-    TRY(amg_get_vectors(h, 0, v.data()));
+    // test vectors of every coarsening: fine [nvec][V][12][2], then coarse [nvec][V_l][nc][2]
+    std::vector<std::vector<double>> v(h->p.nlevels - 1);
+    for (int l = 0; l + 1 < h->p.nlevels; ++l) {
+        const size_t per = l == 0 ? (size_t)g.V * 24 : coarse_n(h->lev[l]) * 2;
+        v[l].resize(per * h->p.nvec[l]);
+        TRY(amg_get_vectors(h, l, v[l].data()));
+    }
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(AMG_EIO, std::string("cannot open ") + path);
     bool ok = std::fwrite(&kMagic, sizeof(kMagic), 1, f) == 1 && std::fwrite(g.L, sizeof(int), 4, f) == 4 &&
-              std::fwrite(&h->p, sizeof(amg_params), 1, f) == 1 &&
-              std::fwrite(v.data(), sizeof(double), v.size(), f) == v.size();
+              std::fwrite(&h->p, sizeof(amg_params), 1, f) == 1;
+    for (auto& vl : v) ok = ok && std::fwrite(vl.data(), sizeof(double), vl.size(), f) == vl.size();
     ok = (std::fclose(f) == 0) && ok;
     return ok ? AMG_OK : fail(AMG_EIO, "write failed");
 }
@@ -1025,14 +1365,22 @@ amg_status amg_setup_load(amg_dirac* d, const char* path, amg_hierarchy** out) {
               std::fread(&p, sizeof(p), 1, f) == 1;
     const GeomH& g = d->gauge->lat->g;
     for (int mu = 0; ok && mu < 4; ++mu) ok = L[mu] == g.L[mu];
-    std::vector<double> v;
+    ok = ok && p.nlevels >= 2 && p.nlevels <= AMG_MAX_LEVELS;
+    std::vector<std::vector<double>> v;
+    const double* vl[AMG_MAX_LEVELS] = {nullptr, nullptr, nullptr, nullptr};
     if (ok) {
-        v.resize((size_t)p.nvec[0] * g.V * 24);
-        ok = std::fread(v.data(), sizeof(double), v.size(), f) == v.size();
+        v.resize(p.nlevels - 1);
+        size_t sites = g.V;
+        for (int l = 0; ok && l + 1 < p.nlevels; ++l) {
+            const size_t per = l == 0 ? sites * 24 : sites * 2 * (2 * p.nvec[l - 1]);
+            v[l].resize(per * p.nvec[l]);
+            ok = std::fread(v[l].data(), sizeof(double), v[l].size(), f) == v[l].size();
+            vl[l] = v[l].data();
+            for (int mu = 0; mu < 4; ++mu) sites /= (p.block[l][mu] > 0 ? p.block[l][mu] : 1);
+        }
     }
     std::fclose(f);
     if (!ok) return fail(AMG_EIO, "not a checkpoint of this lattice");
-    const double* vl[1] = {v.data()};
     return amg_setup_from_vectors(d, &p, vl, out);
 }
 
@@ -1043,7 +1391,7 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
     int vprec = prec == AMG_F64 ? 0 : 1;
     cudaStream_t st = (cudaStream_t)s;
     if (vprec == L.prec) {
-        CK(launch_coarse_apply(L.prec, L.g, L.nc, nullptr, L.B.p, in, out, nullptr, nrhs, st));
+        CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), in, out, nullptr, nrhs, st));
         return AMG_OK;
     }
     size_t n = coarse_n(L) * nrhs;
@@ -1051,7 +1399,7 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
     CK(a.ensure(n * coarse_elem_bytes(L.prec)));
     CK(b.ensure(n * coarse_elem_bytes(L.prec)));
     CK(launch_convert_flat(vprec, L.prec, in, a.p, n, st));
-    CK(launch_coarse_apply(L.prec, L.g, L.nc, nullptr, L.B.p, a.p, b.p, nullptr, nrhs, st));
+    CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), a.p, b.p, nullptr, nrhs, st));
     CK(launch_convert_flat(L.prec, vprec, b.p, out, n, st));
     CK(cudaStreamSynchronize(st));
     return AMG_OK;
@@ -1059,14 +1407,44 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
 
 static amg_status transfer_common(amg_hierarchy* h, int coarsening, int nrhs, amg_prec prec) {
     if (!h || nrhs < 1) return fail(AMG_EINVAL, "bad argument");
-    if (coarsening != 0) return fail(AMG_EINVAL, "only coarsening 0 in this build");
-    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "bad precision");
+    if (coarsening < 0 || coarsening > h->p.nlevels - 2) return fail(AMG_EINVAL, "bad coarsening");
+    if (prec < 0 || prec > 3) return fail(AMG_EINVAL, "bad precision");
+    if (coarsening == 0 && prec == AMG_BF16) return fail(AMG_EINVAL, "bad precision for fine fields");
+    return AMG_OK;
+}
+
+// Eqs. 4-5 from coarse level l >= 1: canonical = internal coarse layout; vectors
+// converted around the kernel when the caller's precision is not the level's
+static amg_status coarse_transfer(amg_hierarchy* h, int l, bool restrict_dir, const void* in, void* out, int nrhs,
+                                  amg_prec prec, cudaStream_t st) {
+    CoarseLevel& L = h->lev[l];
+    CoarseLevel& N = h->lev[l + 1];
+    const int vprec = prec == AMG_F64 ? 0 : 1;
+    const size_t nin = (restrict_dir ? coarse_n(L) : coarse_n(N)) * nrhs;
+    const size_t nout = (restrict_dir ? coarse_n(N) : coarse_n(L)) * nrhs;
+    DevBuf a, b;
+    const void* src = in;
+    void* dst = out;
+    if (vprec != L.prec) {
+        CK(a.ensure(nin * coarse_elem_bytes(L.prec)));
+        CK(b.ensure(nout * coarse_elem_bytes(L.prec)));
+        CK(launch_convert_flat(vprec, L.prec, in, a.p, nin, st));
+        src = a.p;
+        dst = b.p;
+    }
+    if (restrict_dir)
+        CK(launch_restrict_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, src, dst, nrhs, st));
+    else
+        CK(launch_prolong_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, src, dst, nrhs, st));
+    if (vprec != L.prec) CK(launch_convert_flat(L.prec, vprec, b.p, out, nout, st));
+    CK(cudaStreamSynchronize(st));
     return AMG_OK;
 }
 
 amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void* coarse, int nrhs, amg_prec prec,
                         amg_stream s) {
     TRY(transfer_common(h, coarsening, nrhs, prec));
+    if (coarsening > 0) return coarse_transfer(h, coarsening, true, fine, coarse, nrhs, prec, (cudaStream_t)s);
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
     int cprec = prec == AMG_F64 ? 0 : 1;
@@ -1081,6 +1459,7 @@ amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void
 amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, void* fine, int nrhs, amg_prec prec,
                        amg_stream s) {
     TRY(transfer_common(h, coarsening, nrhs, prec));
+    if (coarsening > 0) return coarse_transfer(h, coarsening, false, coarse, fine, nrhs, prec, (cudaStream_t)s);
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
     int cprec = prec == AMG_F64 ? 0 : 1;
@@ -1099,6 +1478,30 @@ amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_
     CK(launch_pack_spinor(prec, g, b, h->fb[prec].p, 1, st));
     TRY(fine_sap(h, prec, h->fb[prec].p, h->fx[prec].p, true, 1, st));
     CK(launch_unpack_spinor(prec, g, h->fx[prec].p, x, 1, st));
+    CK(cudaStreamSynchronize(st));
+    return AMG_OK;
+}
+
+amg_status amg_sap_coarse(amg_hierarchy* h, int level, const void* b, void* x, int nrhs, amg_prec prec,
+                          amg_stream s) {
+    if (!h || !b || !x || nrhs < 1 || level < 1 || level > h->p.nlevels - 2 || prec < 0 || prec > 3)
+        return fail(AMG_EINVAL, "bad argument");
+    CoarseLevel& L = h->lev[level];
+    cudaStream_t st = (cudaStream_t)s;
+    const int vprec = prec == AMG_F64 ? 0 : 1;
+    const size_t n = coarse_n(L) * nrhs;
+    if (vprec == L.prec) {
+        TRY(coarse_sap(h, level, b, x, true, nrhs, st));
+    } else {
+        DevBuf a, c;
+        CK(a.ensure(n * coarse_elem_bytes(L.prec)));
+        CK(c.ensure(n * coarse_elem_bytes(L.prec)));
+        CK(launch_convert_flat(vprec, L.prec, b, a.p, n, st));
+        TRY(coarse_sap(h, level, a.p, c.p, true, nrhs, st));
+        CK(launch_convert_flat(L.prec, vprec, c.p, x, n, st));
+        CK(cudaStreamSynchronize(st));
+        return AMG_OK;
+    }
     CK(cudaStreamSynchronize(st));
     return AMG_OK;
 }
@@ -1131,7 +1534,23 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     if (!h || !b || !x || nrhs < 1 || !(tol > 0) || maxit < 1) return fail(AMG_EINVAL, "bad argument");
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
-    const int kMaxBatch = 12;   // right-hand sides solved in lockstep
+    // right-hand sides solved in lockstep: up to 12, fewer if the batch's
+    // workspaces (FGMRES basis, Z vectors, cycle fields) would not fit in 80%
+    // of the free device memory
+    int kMaxBatch = 12;
+    {
+        const size_t f64 = fine_spinor_bytes(0, g.V), fz = fine_spinor_bytes(zprec_of(h), g.V);
+        size_t per = f64 * (h->p.outer_m + 1 + 4) + fz * h->p.outer_m;
+        for (int pr = 0; pr < 3; ++pr) per += 2 * fine_spinor_bytes(pr, g.V);
+        size_t have = 0, total = 0;
+        if (cudaMemGetInfo(&have, &total) == cudaSuccess) {
+            // memory the current batch capacity already holds counts as available
+            size_t held = per * (size_t)h->nb_cap;
+            size_t fit = (size_t)((0.8 * (double)(have + held)) / (double)per);
+            if (fit < 1) fit = 1;
+            if ((size_t)kMaxBatch > fit) kMaxBatch = (int)fit;
+        }
+    }
     amg_status worst = AMG_OK;
     amg_solve_info agg;
     std::memset(&agg, 0, sizeof(agg));

@@ -69,7 +69,7 @@ void multi_dot_launch(int k, const PtrList& pl, const V* b, size_t n, double2* p
     if constexpr (K > 1) {
         if (k < K) return multi_dot_launch<V, K - 1>(k, pl, b, n, partials, st);
     }
-    multi_dot_kernel<V, K><<<blas_grid_size(), kBT, 0, st>>>(pl, b, n, partials);
+    (note_launch(), multi_dot_kernel<V, K><<<blas_grid_size(), kBT, 0, st>>>(pl, b, n, partials));
 }
 
 template <typename V>
@@ -141,13 +141,13 @@ cudaError_t launch_multi_dot(int prec, int k, const void* const* a, const void* 
     return cudaGetLastError();
 }
 cudaError_t launch_norm2(int prec, const void* a, size_t n, double* partials, cudaStream_t st) {
-    if (prec == 0) norm2_kernel<double2><<<blas_grid(), kBT, 0, st>>>((const double2*)a, n, partials);
-    else norm2_kernel<float2><<<blas_grid(), kBT, 0, st>>>((const float2*)a, n, partials);
+    if (prec == 0) (note_launch(), norm2_kernel<double2><<<blas_grid(), kBT, 0, st>>>((const double2*)a, n, partials));
+    else (note_launch(), norm2_kernel<float2><<<blas_grid(), kBT, 0, st>>>((const float2*)a, n, partials));
     return cudaGetLastError();
 }
 cudaError_t launch_axpby(int prec, double2 al, const void* x, double2 be, void* y, size_t n, cudaStream_t st) {
-    if (prec == 0) axpby_kernel<double2><<<blas_grid(), kBT, 0, st>>>(al, (const double2*)x, be, (double2*)y, n);
-    else axpby_kernel<float2><<<blas_grid(), kBT, 0, st>>>(al, (const float2*)x, be, (float2*)y, n);
+    if (prec == 0) (note_launch(), axpby_kernel<double2><<<blas_grid(), kBT, 0, st>>>(al, (const double2*)x, be, (double2*)y, n));
+    else (note_launch(), axpby_kernel<float2><<<blas_grid(), kBT, 0, st>>>(al, (const float2*)x, be, (float2*)y, n));
     return cudaGetLastError();
 }
 cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
@@ -159,7 +159,7 @@ cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* con
         cl.c[j] = c[j];
         pl.p[j] = x[j];
     }
-    if (prec == 0) multi_axpy_kernel<double2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (double2*)y, n);
-    else multi_axpy_kernel<float2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (float2*)y, n);
+    if (prec == 0) (note_launch(), multi_axpy_kernel<double2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (double2*)y, n));
+    else (note_launch(), multi_axpy_kernel<float2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (float2*)y, n));
     return cudaGetLastError();
 }

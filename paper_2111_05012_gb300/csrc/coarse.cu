@@ -35,7 +35,13 @@ DEV int cneighbour(const CGeom& g, int X, int d, int c[4]) {
 // One CTA per coarse site; the 9 neighbour vectors are gathered into shared
 // memory, each warp then produces output rows (lanes stride over 9*Nc).
 // sap: hops that cross a block boundary of size sb are dropped (D_SAP).
-template <typename TC, bool RESID>
+template <typename TC, bool BF> DEV cx<TC> ldb(const void* B, size_t i) { return ldc<TC>(B, i); }
+template <> DEV cx<float> ldb<float, true>(const void* B, size_t i) {
+    float2 f = __bfloat1622float2(__ldg((const __nv_bfloat162*)B + i));
+    return {f.x, f.y};
+}
+
+template <typename TC, bool RESID, bool BF = false>
 __global__ void coarse_apply_kernel(CGeom g, int nc, int sap, int4 sb, const void* __restrict__ B,
                                     const void* __restrict__ in, void* out, const void* __restrict__ b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -68,7 +74,7 @@ __global__ void coarse_apply_kernel(CGeom g, int nc, int sap, int4 sb, const voi
         for (int row = warp; row < nc; row += nw) {
             const size_t base = ((size_t)X * nc + row) * 9 * nc;
             cx<TC> acc = czero<TC>();
-            for (int j = lane; j < 9 * nc; j += 32) acc = acc + ldc<TC>(B, base + j) * xin[j];
+            for (int j = lane; j < 9 * nc; j += 32) acc = acc + ldb<TC, BF>(B, base + j) * xin[j];
             acc.re = warp_sum(acc.re);
             acc.im = warp_sum(acc.im);
             if (lane == 0) {
@@ -101,6 +107,11 @@ __global__ void convert_flat_kernel(const void* in, void* out, size_t n) {
         stc<TO>(out, i, ccast<TO>(ldc<TI>(in, i)));
 }
 
+__global__ void to_bf16_kernel(const float2* __restrict__ in, __nv_bfloat162* out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float22bfloat162_rn(in[i]);
+}
+
 int nsm() {
     static int sms = 0;
     if (!sms) {
@@ -125,28 +136,38 @@ cudaError_t launch_coarse_apply(int cprec, const GeomH& gh, int nc, const BlockH
     int th = 256;
     if (cprec == 0) {
         size_t smem = (size_t)9 * nc * sizeof(cx<double>);
-        if (b) coarse_apply_kernel<double, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b);
-        else coarse_apply_kernel<double, false><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b);
+        if (b) (note_launch(), coarse_apply_kernel<double, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+        else (note_launch(), coarse_apply_kernel<double, false><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
     } else {
         size_t smem = (size_t)9 * nc * sizeof(cx<float>);
-        if (b) coarse_apply_kernel<float, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b);
-        else coarse_apply_kernel<float, false><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b);
+        if (cprec == 2) {   // FP32 vectors, bfloat16 operator
+            if (b) (note_launch(), coarse_apply_kernel<float, true, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+            else (note_launch(), coarse_apply_kernel<float, false, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+        } else {
+            if (b) (note_launch(), coarse_apply_kernel<float, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+            else (note_launch(), coarse_apply_kernel<float, false><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+        }
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_op_export(int cprec, int Vc, int nc, const void* B, double* out, cudaStream_t st) {
     int grid = nsm() * 8;
-    if (cprec == 0) coarse_export_kernel<double><<<grid, 256, 0, st>>>(Vc, nc, B, out);
-    else coarse_export_kernel<float><<<grid, 256, 0, st>>>(Vc, nc, B, out);
+    if (cprec == 0) (note_launch(), coarse_export_kernel<double><<<grid, 256, 0, st>>>(Vc, nc, B, out));
+    else (note_launch(), coarse_export_kernel<float><<<grid, 256, 0, st>>>(Vc, nc, B, out));
     return cudaGetLastError();
 }
 
 cudaError_t launch_convert_flat(int pi, int po, const void* in, void* out, size_t n, cudaStream_t st) {
     int grid = nsm() * 8;
-    if (pi == 0 && po == 1) convert_flat_kernel<double, float><<<grid, 256, 0, st>>>(in, out, n);
-    else if (pi == 1 && po == 0) convert_flat_kernel<float, double><<<grid, 256, 0, st>>>(in, out, n);
-    else if (pi == 0) convert_flat_kernel<double, double><<<grid, 256, 0, st>>>(in, out, n);
-    else convert_flat_kernel<float, float><<<grid, 256, 0, st>>>(in, out, n);
+    if (pi == 0 && po == 1) (note_launch(), convert_flat_kernel<double, float><<<grid, 256, 0, st>>>(in, out, n));
+    else if (pi == 1 && po == 0) (note_launch(), convert_flat_kernel<float, double><<<grid, 256, 0, st>>>(in, out, n));
+    else if (pi == 0) (note_launch(), convert_flat_kernel<double, double><<<grid, 256, 0, st>>>(in, out, n));
+    else (note_launch(), convert_flat_kernel<float, float><<<grid, 256, 0, st>>>(in, out, n));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_complex_to_bf16(const void* in, void* out, size_t n, cudaStream_t st) {
+    (note_launch(), to_bf16_kernel<<<nsm() * 8, 256, 0, st>>>((const float2*)in, (__nv_bfloat162*)out, n));
     return cudaGetLastError();
 }

@@ -275,12 +275,27 @@ DEV void xseg_load(const Args& a, const void* xin, int X0, int p, cx<TC>& v0, cx
     ld_pair_cg((const TC*)xin, ((size_t)coarse_neighbour(a, X0 + sl, d) * a.nc) / 2 + q, v0, v1);
 }
 
+// operator entries in shared memory: complex in the solver precision, or
+// bfloat16 pairs (BF16 storage, FP32 arithmetic)
+template <typename TC, bool BF> struct OpElem;
+template <typename TC> struct OpElem<TC, false> {
+    static constexpr int bytes = (int)sizeof(cx<TC>);
+    DEV static cx<TC> get(const unsigned char* row, int e) { return ((const cx<TC>*)row)[e]; }
+};
+template <> struct OpElem<float, true> {
+    static constexpr int bytes = 4;
+    DEV static cx<float> get(const unsigned char* row, int e) {
+        float2 f = __bfloat1622float2(((const __nv_bfloat162*)row)[e]);
+        return {f.x, f.y};
+    }
+};
+
 // y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA:
 // operator rows arrive by bulk copy through the ring, the chunk's neighbour
 // segments are gathered by the threads one chunk ahead (double buffer), and
 // one warp computes one row entirely from shared memory; returns the
 // per-thread partial <w, y> in dotp.  Returns false if a ring wait timed out.
-template <typename TC>
+template <typename TC, bool BF>
 DEV bool stencil_rows(const Args& a, Ring& rg, cx<TC>* xbuf, const void* xin, void* yout, const void* w, int r0,
                       int r1, cx<TC>& dotp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
@@ -326,13 +341,13 @@ DEV bool stencil_rows(const Args& a, Ring& rg, cx<TC>* xbuf, const void* xin, vo
         const cx<TC>* xs = xbuf + (size_t)(c & 1) * xcap;
         const int X0 = rc0 / nc;
         for (int r = rc0 + warp; ok && r < rc1; r += kWarps) {
-            const cx<TC>* brow = (const cx<TC>*)(sb + (size_t)(r - rc0) * a.row_bytes);
+            const unsigned char* brow = sb + (size_t)(r - rc0) * a.row_bytes;
             const cx<TC>* xrow = xs + (size_t)(r / nc - X0) * K;   // the nine segments of this row's site
             cx<TC> acc0 = czero<TC>(), acc1 = czero<TC>();
 #pragma unroll 4
             for (int j = lane; j < K / 2; j += 32) {
-                acc0 = acc0 + brow[2 * j] * xrow[2 * j];
-                acc1 = acc1 + brow[2 * j + 1] * xrow[2 * j + 1];
+                acc0 = acc0 + OpElem<TC, BF>::get(brow, 2 * j) * xrow[2 * j];
+                acc1 = acc1 + OpElem<TC, BF>::get(brow, 2 * j + 1) * xrow[2 * j + 1];
             }
             cx<TC> acc = acc0 + acc1;
             acc.re = warp_sum(acc.re);
@@ -370,7 +385,7 @@ DEV bool stencil_rows(const Args& a, Ring& rg, cx<TC>* xbuf, const void* xin, vo
     return ok;
 }
 
-template <typename TC>
+template <typename TC, bool BF>
 __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
     __shared__ cx<double> red_sh[kMaxQ * kWarps];
     __shared__ cx<double> res[kMaxQ];
@@ -437,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             // U_{j+1} = A U_j and gamma = <rt, U_{j+1}>
             {
                 cx<TC> v[1] = {czero<TC>()};
-                if (!stencil_rows<TC>(a, rg, xbuf, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0])) {
+                if (!stencil_rows<TC, BF>(a, rg, xbuf, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0])) {
                     atomicExch(&a.bar->err, 1);
                     return;
                 }
@@ -453,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             // R_{j+1} = A R_j; the next BiCG step needs rho1 = <rt, R_{j+1}>
             {
                 cx<TC> v[1] = {czero<TC>()};
-                if (!stencil_rows<TC>(a, rg, xbuf, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0])) {
+                if (!stencil_rows<TC, BF>(a, rg, xbuf, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0])) {
                     atomicExch(&a.bar->err, 1);
                     return;
                 }
@@ -610,14 +625,18 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     a.part = (double2*)part;
     a.bar = (GridBar*)state;
     if (nc % 2 != 0) return cudaErrorInvalidValue;
+    // cprec: 0 FP64, 1 FP32, 2 FP32 vectors with a bfloat16 operator
     const int eb = cprec == 0 ? 16 : 8;
-    a.row_bytes = 9 * nc * eb;
+    a.row_bytes = 9 * nc * (cprec == 2 ? 4 : eb);
+    if (a.row_bytes % 16 != 0) return cudaErrorInvalidValue;   // bulk copies move 16-byte multiples
     a.rows_per_chunk = kChunkBytes / a.row_bytes;
     if (a.rows_per_chunk < 1) return cudaErrorInvalidValue;   // nc too large for a ring slot
     a.sites_per_chunk = (a.rows_per_chunk - 1) / nc + 2;
     a.xseg_bytes = nc * eb;
     a.slot_bytes = kChunkBytes;
-    const void* fn = cprec == 0 ? (const void*)coarse_bicgstab_kernel<double> : (const void*)coarse_bicgstab_kernel<float>;
+    const void* fn = cprec == 0   ? (const void*)coarse_bicgstab_kernel<double, false>
+                     : cprec == 1 ? (const void*)coarse_bicgstab_kernel<float, false>
+                                  : (const void*)coarse_bicgstab_kernel<float, true>;
     const int smem = kStages * kChunkBytes + 2 * 9 * a.sites_per_chunk * a.xseg_bytes;
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -625,5 +644,6 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     int grid = coop_grid(fn, smem);
     if (grid < 1) return cudaErrorInvalidConfiguration;
     void* params[] = {&a};
+    note_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), params, smem, s);
 }

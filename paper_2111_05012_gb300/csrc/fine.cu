@@ -774,8 +774,8 @@ cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, 
     cudaError_t e =
         cudaFuncSetAttribute(sap_half_staged_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sap_half_staged_kernel<P><<<dim3(bk.Vc / 2, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                          (float)kappa);
+    (note_launch(), sap_half_staged_kernel<P><<<dim3(bk.Vc / 2, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                          (float)kappa));
     return cudaGetLastError();
 }
 
@@ -792,14 +792,14 @@ cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr
         cudaError_t e =
             cudaFuncSetAttribute(sap_half_kernel<P, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        sap_half_kernel<P, 256><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                         (typename P::T)kappa);
+        (note_launch(), sap_half_kernel<P, 256><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                         (typename P::T)kappa));
     } else {
         cudaError_t e =
             cudaFuncSetAttribute(sap_half_kernel<P, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        sap_half_kernel<P, 512><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                         (typename P::T)kappa);
+        (note_launch(), sap_half_kernel<P, 512><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                         (typename P::T)kappa));
     }
     return cudaGetLastError();
 }
@@ -814,11 +814,11 @@ cudaError_t dirac_impl(const GeomH& gh, const BlockH* sb, const void* U, const v
     dim3 grid(grid_for(g.V, kThreads), nrhs);
     using T = typename P::T;
     if (sb) {
-        if (b) dirac_kernel<P, true, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
-        else dirac_kernel<P, true, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
+        if (b) (note_launch(), dirac_kernel<P, true, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+        else (note_launch(), dirac_kernel<P, true, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
     } else {
-        if (b) dirac_kernel<P, false, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
-        else dirac_kernel<P, false, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa);
+        if (b) (note_launch(), dirac_kernel<P, false, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+        else (note_launch(), dirac_kernel<P, false, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
     }
     return cudaGetLastError();
 }
@@ -901,25 +901,25 @@ cudaError_t launch_pack_spinor(int prec, const GeomH& gh, const void* canon, voi
                                cudaStream_t st) {
     Geom g = make_geom(gh);
     dim3 grid(grid_for(g.V, kThreads), nrhs);
-    if (prec == 0) pack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, (const double*)canon, internal, nrhs);
-    else if (prec == 1) pack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs);
-    else pack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs);
+    if (prec == 0) (note_launch(), pack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, (const double*)canon, internal, nrhs));
+    else if (prec == 1) (note_launch(), pack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs));
+    else (note_launch(), pack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs));
     return cudaGetLastError();
 }
 cudaError_t launch_unpack_spinor(int prec, const GeomH& gh, const void* internal, void* canon, int nrhs,
                                  cudaStream_t st) {
     Geom g = make_geom(gh);
     dim3 grid(grid_for(g.V, kThreads), nrhs);
-    if (prec == 0) unpack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, internal, (double*)canon, nrhs);
-    else if (prec == 1) unpack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs);
-    else unpack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs);
+    if (prec == 0) (note_launch(), unpack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, internal, (double*)canon, nrhs));
+    else if (prec == 1) (note_launch(), unpack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs));
+    else (note_launch(), unpack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs));
     return cudaGetLastError();
 }
 cudaError_t launch_convert_spinor(int pi, int po, const GeomH& gh, const void* in, void* out, int nrhs,
                                   cudaStream_t st) {
     Geom g = make_geom(gh);
     dim3 grid(grid_for(g.V, kThreads), nrhs);
-#define CONV(A, B) convert_kernel<A, B><<<grid, kThreads, 0, st>>>(g, in, out)
+#define CONV(A, B) (note_launch(), convert_kernel<A, B><<<grid, kThreads, 0, st>>>(g, in, out))
     if (pi == 0 && po == 1) CONV(P64, P32);
     else if (pi == 1 && po == 0) CONV(P32, P64);
     else if (pi == 0 && po == 2) CONV(P64, P16);
@@ -934,7 +934,7 @@ cudaError_t launch_convert_spinor(int pi, int po, const GeomH& gh, const void* i
 }
 cudaError_t launch_gauge_convert(int prec, const GeomH& gh, const double* canon, void* internal, cudaStream_t st) {
     Geom g = make_geom(gh);
-    gauge_convert_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, canon, internal, prec);
+    (note_launch(), gauge_convert_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, canon, internal, prec));
     return cudaGetLastError();
 }
 cudaError_t launch_clover_build(int prec, const GeomH& gh, const void* U64, double kappa, double csw, void* clover,
@@ -943,15 +943,15 @@ cudaError_t launch_clover_build(int prec, const GeomH& gh, const void* U64, doub
     if (e != cudaSuccess) return e;
     Geom g = make_geom(gh);
     int grid = grid_for(g.V, 128);
-    if (prec == 0) clover_build_kernel<P64><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
-    else if (prec == 1) clover_build_kernel<P32><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
-    else if (prec == 3) clover_build_kernel<PDD><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
-    else clover_build_kernel<P16><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover);
+    if (prec == 0) (note_launch(), clover_build_kernel<P64><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover));
+    else if (prec == 1) (note_launch(), clover_build_kernel<P32><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover));
+    else if (prec == 3) (note_launch(), clover_build_kernel<PDD><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover));
+    else (note_launch(), clover_build_kernel<P16><<<grid, 128, 0, st>>>(g, U64, kappa, csw, clover));
     return cudaGetLastError();
 }
 cudaError_t launch_clover_expand(const GeomH& gh, const void* C64, double* out, cudaStream_t st) {
     Geom g = make_geom(gh);
-    clover_expand_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, C64, out);
+    (note_launch(), clover_expand_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, C64, out));
     return cudaGetLastError();
 }
 cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sb, const void* U, const void* C, const void* in,
@@ -964,7 +964,7 @@ cudaError_t launch_dirac_mixed(const GeomH& gh, const void* Udd, const void* Cdd
                                double kappa, int nrhs, cudaStream_t st) {
     Geom g = make_geom(gh);
     dim3 grid(grid_for(g.V, kThreads), nrhs);
-    dirac_mixed_kernel<<<grid, kThreads, 0, st>>>(g, Udd, Cdd, in32, out64, split_double(kappa));
+    (note_launch(), dirac_mixed_kernel<<<grid, kThreads, 0, st>>>(g, Udd, Cdd, in32, out64, split_double(kappa)));
     return cudaGetLastError();
 }
 cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, const void* const* z, void* x,
@@ -976,7 +976,7 @@ cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, c
         zl.c[j] = c[j];
     }
     Geom g = make_geom(gh);
-    spinor_axpy_mixed_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x);
+    (note_launch(), spinor_axpy_mixed_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x));
     return cudaGetLastError();
 }
 cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const BlockH& bk, int colour, int nmr,

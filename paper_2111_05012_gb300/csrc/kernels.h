@@ -13,8 +13,12 @@ struct BlockH {
     int b[4];
 };
 
+// every kernel launch of the library goes through note_launch() (a relaxed
+// atomic increment); amg_launch_count() reports the running total
+void note_launch();
+
 // precision ids: 0 = F64, 1 = F32, 2 = F16, 3 = FP64 values as float hi/lo pairs (links, clover);
-// coarse: 0 = F64, 1 = F32
+// coarse: 0 = F64, 1 = F32, 2 = F32 vectors with a bfloat16 operator
 size_t fine_spinor_bytes(int prec, int V);
 size_t fine_gauge_bytes(int prec, int V);
 size_t fine_clover_bytes(int prec, int V);
@@ -71,21 +75,29 @@ cudaError_t launch_galerkin_fine(int vprec, int cprec, const GeomH& g, const Blo
                                  const void* U, const void* C, double kappa, void* B, cudaStream_t s);
 
 // ---- coarse level ----
-// y = D_c x (nrhs vectors [Vc][Nc]); b != NULL: y = b - D_c x; sap_block != NULL: hops between blocks removed
+// y = D_c x (nrhs vectors [Vc][Nc]); b != NULL: y = b - D_c x; sap_block != NULL: hops between blocks removed;
+// cprec 0: FP64, 1: FP32, 2: FP32 vectors with a bfloat16 operator
 cudaError_t launch_coarse_apply(int cprec, const GeomH& gc, int nc, const BlockH* sap_block, const void* B,
                                 const void* in, void* out, const void* b, int nrhs, cudaStream_t s);
-// coarse SAP half sweep (fused residual + MR) on level >= 1
-cudaError_t launch_coarse_sap_half(int cprec, const GeomH& gc, int nc, const BlockH& bk, int colour, int nmr,
-                                   int x_zero, const void* B, const void* b, void* x, cudaStream_t s);
-// coarse-level transfer (level l >= 1 -> l+1): fields [Vc][nc], vectors [nvec][Vc][nc]
-cudaError_t launch_restrict_coarse(int prec, const GeomH& gc, int nc, const BlockH& bk, int nvec, const void* vecs,
-                                   const void* fine, void* coarse, int cprec_out, cudaStream_t s);
-cudaError_t launch_prolong_coarse(int prec, const GeomH& gc, int nc, const BlockH& bk, int nvec, const void* vecs,
-                                  const void* coarse, int cprec_in, void* fine, cudaStream_t s);
-cudaError_t launch_orthonormalise_coarse(int prec, const GeomH& gc, int nc, const BlockH& bk, int nvec, void* vecs,
-                                         int* err_flag, cudaStream_t s);
-cudaError_t launch_galerkin_coarse(int prec, int cprec_out, const GeomH& gc, int nc, const BlockH& bk, int nvec,
-                                   const void* vecs, const void* B, void* Bout, cudaStream_t s);
+// ---- levels l >= 1 of a hierarchy with three or more grids (coarse_mg.cu) ----
+// vprec 0: FP64, 1: FP32 (vectors, test vectors and stencils of the level).
+// Vectors [V][nc] complex, test vectors [nvec][V][nc], nrhs vectors one after another.
+// Eq. 4 from level l (lattice g, blocks bh) to the [Vc][2 nvec] vectors of level l+1
+cudaError_t launch_restrict_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
+                                   const void* fine, void* coarse, int nrhs, cudaStream_t s);
+// Eq. 5 from level l+1 back to level l
+cudaError_t launch_prolong_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
+                                  const void* coarse, void* fine, int nrhs, cudaStream_t s);
+// block Gram-Schmidt of the level-l test vectors per (block, chirality half); *err = 1 on rank deficiency
+cudaError_t launch_orthonormalise_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, void* vecs,
+                                         int* err, cudaStream_t s);
+// Eq. 6: stencil of level l+1 ([Vc][2 nvec][9][2 nvec]) from the level-l stencil B ([V][nc][9][nc])
+cudaError_t launch_galerkin_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
+                                   const void* B, void* Bout, cudaStream_t s);
+// SAP half sweep on level l: domains of `colour`, fused residual + nmr MR steps; kprec 0 FP64,
+// 1 FP32, 2 FP32 vectors with a bfloat16 stencil; x_mode as for the fine half sweep
+cudaError_t launch_coarse_sap_half(int kprec, const GeomH& g, const BlockH& bh, int nc, int colour, int nmr,
+                                   int x_mode, const void* B, const void* b, void* x, int nrhs, cudaStream_t s);
 // persistent BiCGStab(ell) on a coarse level (one cooperative launch); part and state are
 // device scratch of coarse_solver_partial_bytes() / coarse_solver_state_bytes(); the first 12
 // bytes of state must be zero before the launch; state word 3 accumulates the cycle count,
@@ -95,6 +107,8 @@ size_t coarse_solver_partial_bytes();
 cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
                                    void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
                                    void* part, void* state, cudaStream_t s);
+// n complex FP32 -> bfloat16 pairs (coarse operator in BF16 storage)
+cudaError_t launch_complex_to_bf16(const void* in, void* out, size_t n, cudaStream_t s);
 // coarse op layout change: internal [Vc][Nc][9][Nc] -> canonical [Vc][9][Nc][Nc] doubles
 cudaError_t launch_coarse_op_export(int cprec, int Vc, int nc, const void* B, double* out, cudaStream_t s);
 // precision change of flat complex arrays (n complex numbers); prec 0 = double2, 1 = float2

@@ -188,10 +188,10 @@ cudaError_t launch_ptconv_forward(const GeomH& gh, int cin, int cout, const void
     if (grid > sms() * 16) grid = sms() * 16;
     const __nv_bfloat16* W = (const __nv_bfloat16*)Wbf16;
     switch (cout) {
-        case 1: ptconv_forward_kernel<1><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out); break;
-        case 2: ptconv_forward_kernel<2><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out); break;
-        case 3: ptconv_forward_kernel<3><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out); break;
-        default: ptconv_forward_kernel<4><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out); break;
+        case 1: (note_launch(), ptconv_forward_kernel<1><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out)); break;
+        case 2: (note_launch(), ptconv_forward_kernel<2><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out)); break;
+        case 3: (note_launch(), ptconv_forward_kernel<3><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out)); break;
+        default: (note_launch(), ptconv_forward_kernel<4><<<grid, kT, 0, st>>>(g, cin, U32, W, in, out)); break;
     }
     return cudaGetLastError();
 }
@@ -202,15 +202,15 @@ cudaError_t launch_ptconv_wgrad(const GeomH& gh, int cin, int cout, const void* 
     Geom g = make_geom(gh);
     dim3 grid(ptconv_grid(), cin * 9);
     switch (cout) {
-        case 1: ptconv_wgrad_kernel<1><<<grid, kT, 0, st>>>(g, U32, in, gout, part); break;
-        case 2: ptconv_wgrad_kernel<2><<<grid, kT, 0, st>>>(g, U32, in, gout, part); break;
-        case 3: ptconv_wgrad_kernel<3><<<grid, kT, 0, st>>>(g, U32, in, gout, part); break;
-        default: ptconv_wgrad_kernel<4><<<grid, kT, 0, st>>>(g, U32, in, gout, part); break;
+        case 1: (note_launch(), ptconv_wgrad_kernel<1><<<grid, kT, 0, st>>>(g, U32, in, gout, part)); break;
+        case 2: (note_launch(), ptconv_wgrad_kernel<2><<<grid, kT, 0, st>>>(g, U32, in, gout, part)); break;
+        case 3: (note_launch(), ptconv_wgrad_kernel<3><<<grid, kT, 0, st>>>(g, U32, in, gout, part)); break;
+        default: (note_launch(), ptconv_wgrad_kernel<4><<<grid, kT, 0, st>>>(g, U32, in, gout, part)); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual_scale(void* y, const void* e, size_t n, float scale, double* part, cudaStream_t st) {
-    residual_scale_kernel<<<ptconv_grid(), kT, 0, st>>>((float2*)y, (const float2*)e, n, scale, part);
+    (note_launch(), residual_scale_kernel<<<ptconv_grid(), kT, 0, st>>>((float2*)y, (const float2*)e, n, scale, part));
     return cudaGetLastError();
 }

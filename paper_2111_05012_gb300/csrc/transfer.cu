@@ -308,7 +308,7 @@ cudaError_t restrict_impl(const GeomH& gh, const BlockH& bh, int nvec, const voi
     Blocking bk = make_blocking(gh, bh);
     int th = threads_for(bk);
     size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<typename PF::T>);
-    restrict_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, fine, coarse);
+    (note_launch(), restrict_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, fine, coarse));
     return cudaGetLastError();
 }
 template <class PF, class PV, typename TC>
@@ -318,7 +318,7 @@ cudaError_t prolong_impl(const GeomH& gh, const BlockH& bh, int nvec, const void
     Blocking bk = make_blocking(gh, bh);
     int th = threads_for(bk);
     size_t smem = (size_t)2 * nvec * sizeof(cx<typename PF::T>);
-    prolong_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, coarse, fine);
+    (note_launch(), prolong_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, coarse, fine));
     return cudaGetLastError();
 }
 
@@ -353,8 +353,8 @@ cudaError_t launch_orthonormalise_fine(int vprec, const GeomH& gh, const BlockH&
     Blocking bk = make_blocking(gh, bh);
     dim3 grid(bk.Vc, 2);
     int th = threads_for(bk);
-    if (vprec == 0) orthonormalise_kernel<P64><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err);
-    else orthonormalise_kernel<P32><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err);
+    if (vprec == 0) (note_launch(), orthonormalise_kernel<P64><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err));
+    else (note_launch(), orthonormalise_kernel<P32><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err));
     return cudaGetLastError();
 }
 cudaError_t launch_galerkin_fine(int vprec, int cprec, const GeomH& gh, const BlockH& bh, int nvec, const void* vecs,
@@ -365,12 +365,12 @@ cudaError_t launch_galerkin_fine(int vprec, int cprec, const GeomH& gh, const Bl
     dim3 grid(bk.Vc, 2 * nvec);
     if (vprec == 0) {
         size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<double>);
-        if (cprec == 0) galerkin_kernel<P64, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B);
-        else galerkin_kernel<P64, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B);
+        if (cprec == 0) (note_launch(), galerkin_kernel<P64, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B));
+        else (note_launch(), galerkin_kernel<P64, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B));
     } else {
         size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<float>);
-        if (cprec == 0) galerkin_kernel<P32, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B);
-        else galerkin_kernel<P32, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B);
+        if (cprec == 0) (note_launch(), galerkin_kernel<P32, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B));
+        else (note_launch(), galerkin_kernel<P32, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B));
     }
     return cudaGetLastError();
 }

@@ -44,3 +44,12 @@ class Field:
         self.c.amg_dirac_destroy(self.d)
         self.c.amg_gauge_destroy(self.gauge)
         self.c.amg_lattice_destroy(self.lat)
+
+
+def bf16_round(a):
+    """Round FP32 values to the nearest bfloat16 (ties to even), kept as float64:
+    keep the top 16 bits of the FP32 word after adding half an ulp of the
+    16-bit truncation (plus one when the kept part is odd)."""
+    x = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (x + 0x7FFF + ((x >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)

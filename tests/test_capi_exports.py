@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "lqcd_amg.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:amg_status|void|const char\s*\*)\s*(amg_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:amg_status|void|unsigned long long|const char\s*\*)\s*(amg_\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")

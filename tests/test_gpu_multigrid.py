@@ -6,7 +6,7 @@ import pytest
 
 import lqcd_inputs as li
 from oracle import dirac as odirac, multigrid as omg, solvers as osol, amg as oamg
-from gpu_util import Field, to_dev, from_dev, rel
+from gpu_util import Field, to_dev, from_dev, rel, bf16_round
 
 pytestmark = pytest.mark.gpu
 
@@ -90,6 +90,41 @@ def test_restrict_prolong_coarse_apply(mgcase, prec):
     c.amg_hierarchy_destroy(h)
 
 
+def test_bf16_coarse_operator(mgcase):
+    # prec_coarsest = AMG_BF16: the Galerkin operator (FP32) is stored in
+    # bfloat16 and applied with FP32 accumulation.  Against the oracle stencil
+    # applied with the same bfloat16-rounded entries the difference is FP32
+    # arithmetic only; against the exact operator it is bfloat16 rounding.
+    import torch
+    from oracle.multigrid import CoarseStencil
+    f = mgcase
+    c = f.c
+    if f.nvec % 2:
+        pytest.skip("bfloat16 coarsest operator needs an even number of test vectors")
+    p = _params(c, f.block, f.nvec, 1)
+    p.prec_coarsest = c.AMG_BF16
+    h = c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(f.v0)])
+    dims_c, nc = c.amg_level_info(h, 1)
+    cshape = li.lattice_shape(dims_c)
+    B = c.amg_get_coarse_op(h, 1)
+    assert rel(B[..., 0] + 1j * B[..., 1], f.B.B.reshape(B.shape[:-1])) < 2e-6
+    Bq = bf16_round(B).reshape(f.B.B.shape + (2,))
+    stored = CoarseStencil(Bq[..., 0] + 1j * Bq[..., 1], f.nvec)
+    yc = li.complex_normal(78, li.STREAM_MISC, cshape + (nc,))
+    out = torch.zeros(int(np.prod(cshape)) * nc * 2, dtype=torch.float32, device="cuda")
+    yd = to_dev(yc, "float32")
+    c.amg_apply_coarse(h, 1, yd, out, 1, c.AMG_BF16)
+    y32 = from_dev(yd, cshape + (nc,))
+    got = from_dev(out, cshape + (nc,))
+    assert rel(got, stored.apply(y32)) < 1e-5
+    assert rel(got, f.B.apply(yc)) < 4e-3
+    # FP64 vectors through the same operator (converted around the stencil)
+    out64 = torch.zeros(out.numel(), dtype=torch.float64, device="cuda")
+    c.amg_apply_coarse(h, 1, to_dev(yc), out64, 1, c.AMG_F64)
+    assert rel(from_dev(out64, cshape + (nc,)), stored.apply(y32)) < 1e-5
+    c.amg_hierarchy_destroy(h)
+
+
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_sap(mgcase, prec, variant):
@@ -125,11 +160,20 @@ def test_precondition_fp64(mgcase):
     c.amg_hierarchy_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, "bf16"])
 def test_solve_reaches_fp64_tolerance(mgcase, prec):
     f = mgcase
     c = f.c
-    p = _params(c, f.block, f.nvec, prec, n_init=2, n_adapt=1)
+    if prec == "bf16":   # FP32 smoother, bfloat16 coarse operator
+        p = _params(c, f.block, f.nvec, 1, n_init=2, n_adapt=1)
+        p.prec_coarsest = c.AMG_BF16
+        if f.nvec % 2:   # rows of 9 * Nc bfloat16 pairs must be 16-byte multiples
+            with pytest.raises(c.AMGError) as e:
+                c.amg_setup(f.d, p, [li.to_interleaved(f.v0)])
+            assert "even number of test vectors" in str(e.value)
+            return
+    else:
+        p = _params(c, f.block, f.nvec, prec, n_init=2, n_adapt=1)
     h = c.amg_setup(f.d, p, [li.to_interleaved(f.v0)])
     b = li.rhs(f.dims, 13)
     x = to_dev(b) * 0
