@@ -349,6 +349,168 @@ def run_dirac(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed3(args):
+    """Three grids on 32^3x64 (links exp(0.6iH), seed 3, kappa 0.130, c_sw
+    1.0): 4^4 blocks / 24 test vectors, then 2^4 blocks / 32 test vectors;
+    FP16 fine smoother with per-site scale, bfloat16 stencils on both coarse
+    levels, FGMRES(8) to 1e-1 on level 1, BiCGStab(2) to 1e-2 on level 2,
+    FP64 outer flexible GMRES(16).  Fresh Gaussian right-hand sides; the same
+    hierarchy built all in FP64 is timed on the same right-hand sides."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_05012_gb300 import capi
+    dims = (32, 32, 32, 64)
+    V = int(np.prod(dims))
+    t0 = time.perf_counter()
+    U, lat, g, d = _setup_field(capi, dims, 0.6, 3, 0.130, 1.0)
+    del U
+    gen_s = time.perf_counter() - t0
+    blocks, nvec = [(4, 4, 4, 4), (2, 2, 2, 2)], [24, 32]
+    cdims1 = tuple(dims[mu] // blocks[0][mu] for mu in range(4))
+    init = [li.to_interleaved(li.test_vectors(dims, 3, nvec[0])),
+            li.to_interleaved(li.coarse_test_vectors(cdims1, 3, nvec[1], 2 * nvec[0]))]
+    nsolve = max(1, min(args.steps, 8))
+    B = [torch.from_numpy(li.to_interleaved(li.rhs(dims, 3, index=k)).reshape(-1)).cuda() for k in range(nsolve + 1)]
+    X = torch.zeros_like(B[0])
+    stream = torch.cuda.current_stream()
+    res = {}
+    variants = [("mixed", capi.AMG_F16, capi.AMG_BF16, capi.AMG_BF16)]
+    if not args.no_fp64_compare:
+        variants.append(("fp64", capi.AMG_F64, capi.AMG_F64, capi.AMG_F64))
+    clk_summary = None
+    gpu_launches = None
+    for name, ps, pc, pcc in variants:
+        p = capi.amg_params_default()
+        p.nlevels = 3
+        for l in range(2):
+            for mu in range(4):
+                p.block[l][mu] = blocks[l][mu]
+            p.nvec[l] = nvec[l]
+        p.prec_smoother, p.prec_coarse, p.prec_coarsest = ps, pc, pcc
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = capi.amg_setup(d, p, init)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        X.zero_()
+        capi.amg_solve(h, B[nsolve], X, 1, TOL, 500, stream=stream)   # warm-up
+        infos = []
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler() as clk:
+            l0 = capi.amg_launch_count()
+            e0.record(stream)
+            for k in range(nsolve):
+                X.zero_()
+                st, info = capi.amg_solve(h, B[k], X, 1, TOL, 500, stream=stream)
+                infos.append(info.as_dict())
+            e1.record(stream)
+            launches = capi.amg_launch_count() - l0
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsolve
+        res[name] = {"ms_per_rhs": ms, "setup_ms": setup_ms,
+                     "outer_iters": float(np.mean([i["iters"] for i in infos])),
+                     "max_true_rel_residual": float(max(i["true_rel_residual"] for i in infos)),
+                     "converged": all(i["converged"] == 1 for i in infos),
+                     "phase_ms": {k: float(np.mean([i[k] for i in infos])) for k in
+                                  ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other")}}
+        if name == "mixed":
+            clk_summary, gpu_launches = clk.summary(), launches
+        capi.amg_hierarchy_destroy(h)
+    line = {"metric": METRIC, "value": res["mixed"]["ms_per_rhs"], "unit": "ms/RHS", "n_gpus": 1, "steps": nsolve,
+            "warmup": 1, "ms_per_step": res["mixed"]["ms_per_rhs"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16+bf16+f32+f64", "data": "synthetic",
+            "config": {"workload": "32^3x64 Wilson-clover (exp(0.6iH) links, seed 3, kappa 0.130, csw 1.0), "
+                                   "3-level AMG 4^4/24 then 2^4/32, FP16 smoother, BF16 coarse stencils, "
+                                   "FGMRES(8) level 1, BiCGStab(2) level 2, FP64 outer FGMRES(16)",
+                       "volume": V, "field_generation_s": gen_s, "l2": "working set > L2 (no flush)",
+                       "variants": res},
+            "gpu_launches": gpu_launches, "clocks": clk_summary}
+    capi.amg_dirac_destroy(d)
+    capi.amg_gauge_destroy(g)
+    capi.amg_lattice_destroy(lat)
+    print(json.dumps(line), flush=True)
+
+
+def run_ragged(args):
+    """Ragged batch: 64 independent single-RHS solves, problem i (gauge seed
+    100 + i) on 8^4 (4^4 blocks), 12^4 (3^4 blocks) or 16^3x32 (4^4 blocks)
+    for i % 3 = 0, 1, 2; links exp(0.6iH), kappa 0.130, c_sw 1.0, 24 test
+    vectors, FP32 smoother.  The initial test vectors are drawn once per
+    lattice size.  One amg_solve_ragged call (graphs captured in a warm-up
+    call on other right-hand sides) against the same 64 solves issued one
+    after another through amg_solve."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_05012_gb300 import capi
+    shapes = [((8, 8, 8, 8), (4, 4, 4, 4)), ((12, 12, 12, 12), (3, 3, 3, 3)), ((16, 16, 16, 32), (4, 4, 4, 4))]
+    n = 64
+    init = {dims: li.to_interleaved(li.test_vectors(dims, 100 + k, 24)) for k, (dims, _) in enumerate(shapes)}
+    probs = []
+    t0 = time.perf_counter()
+    for i in range(n):
+        dims, block = shapes[i % 3]
+        U, lat, g, d = _setup_field(capi, dims, 0.6, 100 + i, 0.130, 1.0)
+        p = capi.amg_params_default()
+        for mu in range(4):
+            p.block[0][mu] = block[mu]
+        p.nvec[0] = 24
+        h = capi.amg_setup(d, p, [init[dims]])
+        probs.append((dims, lat, g, d, h))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    sites = sum(int(np.prod(pr[0])) for pr in probs)
+
+    def rhs_set(base):
+        return [torch.from_numpy(li.to_interleaved(li.rhs(pr[0], base + i)).reshape(-1)).cuda()
+                for i, pr in enumerate(probs)]
+    hs = [pr[4] for pr in probs]
+    warm_b = rhs_set(7000)
+    capi.amg_solve_ragged(hs, warm_b, [torch.zeros_like(b) for b in warm_b], TOL, 300)
+    B = rhs_set(8000)
+    X = [torch.zeros_like(b) for b in B]
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    with ClockSampler() as clk:
+        l0 = capi.amg_launch_count()
+        t0 = time.perf_counter()
+        st, infos = capi.amg_solve_ragged(hs, B, X, TOL, 300, stream=stream)
+        torch.cuda.synchronize()
+        ragged_ms = (time.perf_counter() - t0) * 1e3
+        launches = capi.amg_launch_count() - l0
+    ok = all(i.converged == 1 and i.true_rel_residual <= TOL for i in infos)
+    # the same solves one after another
+    for x in X:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = []
+    for h, b, x in zip(hs, B, X):
+        st, info = capi.amg_solve(h, b, x, 1, TOL, 300, stream=stream)
+        seq.append(info.converged == 1 and info.true_rel_residual <= TOL)
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3
+    line = {"metric": METRIC, "value": ragged_ms / n, "unit": "ms/RHS", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": ragged_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "ragged batch of 64 single-RHS solves on 8^4 / 12^4 / 16^3x32 (gauge seeds "
+                                   "100-163, exp(0.6iH), kappa 0.130, csw 1.0), 2-level AMG, 24 test vectors, "
+                                   "FP32 smoother, lockstep FGMRES(16) on 16 streams with CUDA-graph steps",
+                       "problems": n, "total_sites": sites, "setup_s": setup_s, "converged": ok,
+                       "ragged_ms": ragged_ms, "sequential_ms": seq_ms, "sequential_converged": all(seq),
+                       "speedup_vs_sequential": seq_ms / ragged_ms,
+                       "outer_iters": [int(i.iters) for i in infos]},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    for dims, lat, g, d, h in probs:
+        capi.amg_hierarchy_destroy(h)
+        capi.amg_dirac_destroy(d)
+        capi.amg_gauge_destroy(g)
+        capi.amg_lattice_destroy(lat)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,8 +519,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac"])
+    ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac", "mixed3", "ragged"])
     ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -368,6 +531,10 @@ def main():
         return run_learned(args)
     if args.workload == "dirac":
         return run_dirac(args)
+    if args.workload == "mixed3":
+        return run_mixed3(args)
+    if args.workload == "ragged":
+        return run_ragged(args)
 
     import torch
     import torch.distributed as dist

@@ -268,6 +268,22 @@ amg_status amg_sap_coarse(amg_hierarchy* h, int level, const void* b, void* x, i
  * (1) and (2)).  Canonical double vectors. */
 amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_stream s);
 
+/* Ragged batch: n independent problems (each its own lattice, operator and
+ * two-grid hierarchy; no hierarchy twice, none with a learned correction)
+ * solved to ||b_i - D_i x_i|| <= tol ||b_i|| in FP64 from x_i = 0, as
+ * amg_solve does for one right-hand side.  The problems' outer flexible
+ * GMRES steps run in lockstep on a pool of up to 16 streams with one host
+ * synchronisation per phase for all of them; each problem's preconditioner
+ * and Arnoldi product of step j are captured into a CUDA graph on first use
+ * (kept in the hierarchy until its workspaces grow or its learned correction
+ * changes) and replayed; the coarse BiCGStab(l) then runs as one
+ * thread-block cluster per problem.  b[i], x[i]: canonical double device
+ * vectors of problem i.  infos (may be NULL) receives n records.  Ordered
+ * after earlier work on stream s; synchronises.  No counterpart in the
+ * paper (a batch of independent solves of Sec. 3). */
+amg_status amg_solve_ragged(amg_hierarchy* const* h, const double* const* b, double* const* x, int n, double tol,
+                            int maxit, amg_solve_info* infos, amg_stream s);
+
 /* ---- learned preconditioner -------------------------------------------- */
 /* The paper's preconditioner slot (Sec. 3 steps (1)-(2)) extended by a
  * gauge-equivariant network of parallel-transport convolution layers

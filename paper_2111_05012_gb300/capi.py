@@ -108,6 +108,8 @@ PROTOTYPES = {
     "amg_sap_coarse": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "amg_precondition": (_i, [_vp, _vp, _vp, _vp]),
     "amg_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, ctypes.POINTER(amg_solve_info), _vp]),
+    "amg_solve_ragged": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _d, _i,
+                              ctypes.POINTER(amg_solve_info), _vp]),
     "amg_nn_create": (_i, [_vp, _i, _ip, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
     "amg_nn_destroy": (None, [_vp]),
     "amg_nn_get_weights": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_float)]),
@@ -332,6 +334,20 @@ def amg_solve(h, b, x, nrhs=1, tol=1e-10, maxit=500, use_x0=False, stream=None, 
     if st != AMG_OK and (st != AMG_NOT_CONVERGED or raise_on_nonconv):
         _check(st)
     return st, info
+
+
+def amg_solve_ragged(hs, bs, xs, tol=1e-10, maxit=500, stream=None, raise_on_nonconv=True):
+    """Independent problems hs[i] (hierarchies), bs[i] / xs[i] device tensors.
+    Returns (status, [amg_solve_info])."""
+    n = len(hs)
+    ha = (_vp * n)(*hs)
+    ba = (_vp * n)(*[_ptr(b) for b in bs])
+    xa = (_vp * n)(*[_ptr(x) for x in xs])
+    infos = (amg_solve_info * n)()
+    st = load().amg_solve_ragged(ha, ba, xa, n, float(tol), int(maxit), infos, _stream(stream))
+    if st != AMG_OK and (st != AMG_NOT_CONVERGED or raise_on_nonconv):
+        _check(st)
+    return st, list(infos)
 
 
 # ---- learned preconditioner ----

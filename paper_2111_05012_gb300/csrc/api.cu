@@ -201,7 +201,16 @@ struct amg_hierarchy {
     bool nn_off = false;              // set while falling back to the plain cycle
     int* hstate = nullptr;   // pinned mirror of the coarse solver state words (16 x 4 ints)
     int nb_cap = 0;          // batch width the workspaces are sized for
+    // ragged solves: step j of the outer solver (Z_j = M V_j, w = D Z_j) captured as a CUDA graph
+    bool graph_mode = false;   // set while capturing: coarse solves run as one cluster
+    std::vector<cudaGraphExec_t> gexec;
+    void clear_graphs() {
+        for (auto g : gexec)
+            if (g) cudaGraphExecDestroy(g);
+        gexec.clear();
+    }
     ~amg_hierarchy() {
+        clear_graphs();
         if (hstate) cudaFreeHost(hstate);
         for (auto& v : cw)
             for (auto* b : v) delete b;
@@ -316,7 +325,8 @@ amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int 
     for (int q = 0; q < nb; ++q) {
         CK(cudaMemsetAsync(L.cs_state.p, 0, 12, s));
         CK(launch_coarse_bicgstab(L.kprec(), L.g, L.nc, L.op(), (const char*)b + q * cv, (char*)x + q * cv, w[2]->p, R,
-                                  U, ell, h->p.coarse_tol, h->p.coarse_maxit, L.cs_part.p, L.cs_state.p, s));
+                                  U, ell, h->p.coarse_tol, h->p.coarse_maxit, L.cs_part.p, L.cs_state.p,
+                                  h->graph_mode ? 8 : 0, s));
         // error word of this solve (a later one would overwrite it): fold into word 2 of the host mirror
         CK(cudaMemcpyAsync(h->hstate + 4 * (q % 16), L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
     }
@@ -754,6 +764,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
 // (Re)size the batch-dependent workspaces for nb right-hand sides.
 amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
     const GeomH& g = fine_geom(h);
+    if (nb > h->nb_cap) h->clear_graphs();   // buffers may move: captured graphs would be stale
     TRY(h->red.init(nb));
     CK(h->err_flag.ensure(sizeof(int)));
     for (int pr = 0; pr < 3; ++pr) {
@@ -1019,6 +1030,208 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
         delete h;
         *hp = nullptr;
         return st;
+    }
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- ragged batch
+// Independent problems (each with its own lattice, operator and two-grid
+// hierarchy) solved together: every phase of the outer flexible GMRES is
+// issued for all active problems on a pool of streams before one host
+// synchronisation.  Step j of a problem (Z_j = M V_j and w = D Z_j, about
+// forty kernels) is replayed from a CUDA graph captured the first time; in it
+// the coarse BiCGStab(l) runs as one thread-block cluster, so the problems'
+// coarse solves overlap without a device-wide barrier.
+amg_status ragged_step(amg_hierarchy* h, int j, cudaStream_t st) {
+    if ((int)h->gexec.size() < h->p.outer_m) h->gexec.resize(h->p.outer_m, nullptr);
+    if (!h->gexec[j]) {
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        h->graph_mode = true;
+        amg_status rc = precondition64(h, h->oV[j]->p, h->oZ[j]->p, 1, st);
+        if (rc == AMG_OK) rc = arnoldi_D(h, h->oZ[j]->p, h->ow.p, 1, st);
+        h->graph_mode = false;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc != AMG_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (rc != AMG_OK) return rc;
+            CK(e);
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        h->gexec[j] = ex;
+    }
+    CK(cudaGraphLaunch(h->gexec[j], st));
+    return AMG_OK;
+}
+
+struct RaggedProb {
+    amg_hierarchy* h = nullptr;
+    cudaStream_t st = nullptr;
+    RhsState r;
+    bool started = false;   // true residual of x = 0 is b itself on the first cycle
+};
+
+// partial sums of the last reduction launched for problem p (k values)
+void ragged_sum(RaggedProb& p, int k, cplx* out) {
+    Reducer& red = p.h->red;
+    for (int i = 0; i < k; ++i) {
+        double re = 0, im = 0;
+        for (int t = 0; t < red.grid; ++t) {
+            re += red.hpart[(size_t)i * red.grid + t].x;
+            im += red.hpart[(size_t)i * red.grid + t].y;
+        }
+        out[i] = cplx(re, im);
+    }
+}
+amg_status ragged_norm_launch(RaggedProb& p, const void* v) {
+    Reducer& red = p.h->red;
+    CK(launch_norm2(0, v, fine_n(p.h), (double*)red.dpart.p, p.st));
+    CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double) * red.grid, cudaMemcpyDeviceToHost, p.st));
+    return AMG_OK;
+}
+double ragged_norm_value(RaggedProb& p) {
+    const double* hp = (const double*)p.h->red.hpart;
+    double t = 0;
+    for (int i = 0; i < p.h->red.grid; ++i) t += hp[i];
+    return t;
+}
+
+amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStream_t>& streams, double tol,
+                         int maxit) {
+    auto sync_all = [&]() -> amg_status {
+        for (auto st : streams) CK(cudaStreamSynchronize(st));
+        return AMG_OK;
+    };
+    int mmax = 0;
+    for (auto& p : P) mmax = std::max(mmax, p.h->p.outer_m);
+    // ||b||
+    for (auto& p : P) TRY(ragged_norm_launch(p, p.h->ob.p));
+    TRY(sync_all());
+    for (auto& p : P) {
+        p.r.bnorm = std::sqrt(ragged_norm_value(p));
+        if (!std::isfinite(p.r.bnorm)) return fail(AMG_NAN, "ragged solve: non-finite right-hand side");
+        if (p.r.bnorm == 0) p.r.done = p.r.conv = true;
+    }
+    while (true) {
+        // true FP64 residual of every unfinished problem
+        for (auto& p : P) {
+            if (p.r.done) continue;
+            if (!p.started) {
+                CK(cudaMemcpyAsync(p.h->orr.p, p.h->ob.p, fsz(p.h, 0), cudaMemcpyDeviceToDevice, p.st));
+            } else {
+                TRY(fine_D(p.h, 0, p.h->ox.p, p.h->orr.p, p.h->ob.p, 1, p.st));
+                TRY(ragged_norm_launch(p, p.h->orr.p));
+            }
+        }
+        TRY(sync_all());
+        bool any = false;
+        for (auto& p : P) {
+            RhsState& r = p.r;
+            if (r.done) continue;
+            TRY(coarse_status(p.h));
+            r.rn = p.started ? std::sqrt(ragged_norm_value(p)) : r.bnorm;
+            p.started = true;
+            if (!std::isfinite(r.rn)) return fail(AMG_NAN, "ragged solve: non-finite residual");
+            r.rel = r.rn / r.bnorm;
+            r.done = r.conv = r.rn <= tol * r.bnorm;
+            if (!r.conv && r.iters >= maxit) r.done = true;
+            if (r.done) continue;
+            any = true;
+            if (r.iters > 0) r.restarts++;
+            const int m = p.h->p.outer_m;
+            r.H.assign(m + 1, std::vector<cplx>(m, cplx(0)));
+            r.cs.assign(m, 0.0);
+            r.sn.assign(m, cplx(0));
+            r.g.assign(m + 1, cplx(0));
+            r.g[0] = r.rn;
+            r.jend = -1;
+            r.stop = false;
+            CK(launch_axpby(0, make_double2(1.0 / r.rn, 0), p.h->orr.p, make_double2(0, 0), p.h->oV[0]->p,
+                            fine_n(p.h), p.st));
+        }
+        if (!any) break;
+        for (int j = 0; j < mmax; ++j) {
+            bool active = false;
+            for (auto& p : P) {
+                if (p.r.done || p.r.stop) continue;
+                if (j >= p.h->p.outer_m) {
+                    p.r.stop = true;
+                    continue;
+                }
+                active = true;
+                TRY(ragged_step(p.h, j, p.st));
+            }
+            if (!active) break;
+            std::vector<cplx> c(j + 1);
+            for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+                for (auto& p : P) {
+                    if (p.r.done || p.r.stop) continue;
+                    std::vector<const void*> vl(j + 1);
+                    for (int i = 0; i <= j; ++i) vl[i] = p.h->oV[i]->p;
+                    CK(launch_multi_dot(0, j + 1, vl.data(), p.h->ow.p, fine_n(p.h), p.h->red.dpart.as<double2>(),
+                                        p.st));
+                    CK(cudaMemcpyAsync(p.h->red.hpart, p.h->red.dpart.p, sizeof(double2) * p.h->red.grid * (j + 1),
+                                       cudaMemcpyDeviceToHost, p.st));
+                }
+                TRY(sync_all());
+                for (auto& p : P) {
+                    if (p.r.done || p.r.stop) continue;
+                    if (pass == 0) TRY(coarse_status(p.h));
+                    ragged_sum(p, j + 1, c.data());
+                    std::vector<double2> nc(j + 1);
+                    std::vector<const void*> vl(j + 1);
+                    for (int i = 0; i <= j; ++i) {
+                        p.r.H[i][j] += c[i];
+                        nc[i] = make_double2(-c[i].real(), -c[i].imag());
+                        vl[i] = p.h->oV[i]->p;
+                    }
+                    CK(launch_multi_axpy(0, j + 1, nc.data(), vl.data(), p.h->ow.p, fine_n(p.h), p.st));
+                }
+            }
+            for (auto& p : P)
+                if (!(p.r.done || p.r.stop)) TRY(ragged_norm_launch(p, p.h->ow.p));
+            TRY(sync_all());
+            for (auto& p : P) {
+                RhsState& r = p.r;
+                if (r.done || r.stop) continue;
+                const double hn = std::sqrt(ragged_norm_value(p));
+                r.H[j + 1][j] = hn;
+                r.iters++;
+                givens_column(r.H, r.cs, r.sn, r.g, j);
+                r.jend = j;
+                const double est = std::abs(r.g[j + 1]);
+                if (!std::isfinite(est)) return fail(AMG_NAN, "ragged solve: non-finite Arnoldi coefficient");
+                if (hn == 0 || est <= tol * r.bnorm || r.iters >= maxit) {
+                    r.stop = true;
+                } else {
+                    CK(launch_axpby(0, make_double2(1.0 / hn, 0), p.h->ow.p, make_double2(0, 0),
+                                    p.h->oV[j + 1]->p, fine_n(p.h), p.st));
+                }
+            }
+        }
+        // x += Z y
+        for (auto& p : P) {
+            RhsState& r = p.r;
+            if (r.done || r.jend < 0) continue;
+            const int k = r.jend + 1;
+            std::vector<cplx> y(k);
+            for (int i = k - 1; i >= 0; --i) {
+                cplx t = r.g[i];
+                for (int cc = i + 1; cc < k; ++cc) t -= r.H[i][cc] * y[cc];
+                y[i] = t / r.H[i][i];
+            }
+            std::vector<double2> yc(k);
+            std::vector<const void*> zl(k);
+            for (int i = 0; i < k; ++i) {
+                yc[i] = d2(y[i]);
+                zl[i] = p.h->oZ[i]->p;
+            }
+            if (zprec_of(p.h) == 0) CK(launch_multi_axpy(0, k, yc.data(), zl.data(), p.h->ox.p, fine_n(p.h), p.st));
+            else CK(launch_spinor_axpy_mixed(fine_geom(p.h), k, yc.data(), zl.data(), p.h->ox.p, p.st));
+        }
     }
     return AMG_OK;
 }
@@ -1510,6 +1723,7 @@ amg_status amg_hierarchy_set_nn(amg_hierarchy* h, amg_nn* nn) {
     if (!h) return fail(AMG_EINVAL, "NULL hierarchy");
     if (nn && h->fp != 1) return fail(AMG_EINVAL, "the learned correction needs the FP32 smoother");
     if (nn && nn->d != h->d) return fail(AMG_EINVAL, "network and hierarchy belong to different operators");
+    if (nn != h->nn) h->clear_graphs();
     h->nn = nn;
     return AMG_OK;
 }
@@ -1615,6 +1829,77 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     h->timer.on = false;
     if (worst != AMG_OK) fail(worst, "solve did not reach the tolerance");
     return worst;
+}
+
+amg_status amg_solve_ragged(amg_hierarchy* const* hs, const double* const* b, double* const* x, int n, double tol,
+                            int maxit, amg_solve_info* infos, amg_stream s) {
+    if (!hs || !b || !x || n < 1 || !(tol > 0) || maxit < 1) return fail(AMG_EINVAL, "bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !b[i] || !x[i]) return fail(AMG_EINVAL, "NULL hierarchy or vector");
+        if (hs[i]->p.nlevels != 2) return fail(AMG_EINVAL, "ragged solves take two-grid hierarchies");
+        if (hs[i]->nn) return fail(AMG_EINVAL, "ragged solves take hierarchies without a learned correction");
+        for (int k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return fail(AMG_EINVAL, "a hierarchy appears twice in the ragged batch");
+    }
+    cudaStream_t user = (cudaStream_t)s;
+    const int ns = std::min(n, 16);
+    std::vector<cudaStream_t> streams(ns, nullptr);
+    std::vector<RaggedProb> P(n);
+    cudaEvent_t ev = nullptr;
+    auto t_all = std::chrono::steady_clock::now();
+    auto body = [&]() -> amg_status {
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, user));
+        for (auto& st : streams) {
+            CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            CK(cudaStreamWaitEvent(st, ev, 0));
+        }
+        for (int i = 0; i < n; ++i) {
+            RaggedProb& p = P[i];
+            p.h = hs[i];
+            p.st = streams[i % ns];
+            TRY(alloc_workspaces(p.h, 1));
+            p.h->timer.on = false;
+            for (int l = 1; l < p.h->p.nlevels; ++l) CK(cudaMemsetAsync(p.h->lev[l].cs_state.p, 0, 16, p.st));
+            std::memset(p.h->hstate, 0, 16 * 16);
+            const GeomH& g = fine_geom(p.h);
+            CK(launch_pack_spinor(0, g, b[i], p.h->ob.p, 1, p.st));
+            CK(cudaMemsetAsync(p.h->ox.p, 0, fine_spinor_bytes(0, g.V), p.st));
+        }
+        TRY(fgmres_ragged(P, streams, tol, maxit));
+        for (int i = 0; i < n; ++i) {
+            RaggedProb& p = P[i];
+            CK(launch_unpack_spinor(0, fine_geom(p.h), p.h->ox.p, x[i], 1, p.st));
+            CK(cudaMemcpyAsync(p.h->hstate + 60, p.h->lev[p.h->p.nlevels - 1].cs_state.p, 16,
+                               cudaMemcpyDeviceToHost, p.st));
+        }
+        for (auto st : streams) CK(cudaStreamSynchronize(st));
+        for (auto& p : P) TRY(coarse_status(p.h));
+        return AMG_OK;
+    };
+    amg_status st = body();
+    for (auto sm : streams)
+        if (sm) cudaStreamDestroy(sm);
+    if (ev) cudaEventDestroy(ev);
+    if (st != AMG_OK) return st;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_all).count();
+    bool all = true;
+    for (int i = 0; i < n; ++i) {
+        const RhsState& r = P[i].r;
+        all = all && r.conv;
+        if (infos) {
+            std::memset(&infos[i], 0, sizeof(amg_solve_info));
+            infos[i].iters = r.iters;
+            infos[i].restarts = r.restarts;
+            infos[i].converged = r.conv ? 1 : 0;
+            infos[i].true_rel_residual = r.bnorm == 0 ? 0.0 : r.rel;
+            infos[i].ms_total = ms;
+            infos[i].ms_other = ms;
+            infos[i].coarse_cycles = P[i].h->hstate[63];
+        }
+    }
+    if (!all) return fail(AMG_NOT_CONVERGED, "ragged solve: some problem did not reach the tolerance");
+    return AMG_OK;
 }
 
 }  // extern "C"

@@ -605,7 +605,7 @@ size_t coarse_solver_partial_bytes() {
 
 cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
                                    void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
-                                   void* part, void* state, cudaStream_t s) {
+                                   void* part, void* state, int cluster, cudaStream_t s) {
     if (ell < 1 || ell > kMaxEll) return cudaErrorInvalidValue;
     Args a;
     for (int i = 0; i < 4; ++i) a.L[i] = gc.L[i];
@@ -641,9 +641,36 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    void* params[] = {&a};
+    if (cluster > 0) {
+        // one thread-block cluster: its CTAs are co-scheduled by the hardware,
+        // so the kernel's grid barrier is safe next to other kernels (several
+        // such solves may run at once on different streams or graph branches)
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int cl = cluster > 8 ? 8 : cluster;
+        for (; cl > 1; cl /= 2) {   // largest power-of-two cluster that fits
+            at[0].val.clusterDim.x = cl;
+            cfg.gridDim = dim3(cl);
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0) break;
+            cudaGetLastError();
+        }
+        at[0].val.clusterDim.x = cl;
+        cfg.gridDim = dim3(cl);
+        note_launch();
+        return cudaLaunchKernelExC(&cfg, fn, params);
+    }
     int grid = coop_grid(fn, smem);
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    void* params[] = {&a};
     note_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), params, smem, s);
 }

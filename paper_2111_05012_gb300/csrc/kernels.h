@@ -98,7 +98,8 @@ cudaError_t launch_galerkin_coarse(int vprec, const GeomH& g, const BlockH& bh, 
 // 1 FP32, 2 FP32 vectors with a bfloat16 stencil; x_mode as for the fine half sweep
 cudaError_t launch_coarse_sap_half(int kprec, const GeomH& g, const BlockH& bh, int nc, int colour, int nmr,
                                    int x_mode, const void* B, const void* b, void* x, int nrhs, cudaStream_t s);
-// persistent BiCGStab(ell) on a coarse level (one cooperative launch); part and state are
+// persistent BiCGStab(ell) on a coarse level: one cooperative launch over every SM
+// (cluster = 0) or one thread-block cluster of up to `cluster` CTAs; part and state are
 // device scratch of coarse_solver_partial_bytes() / coarse_solver_state_bytes(); the first 12
 // bytes of state must be zero before the launch; state word 3 accumulates the cycle count,
 // word 2 is nonzero on failure (1 = barrier timeout, 2 = breakdown / non-finite)
@@ -106,7 +107,7 @@ size_t coarse_solver_state_bytes();
 size_t coarse_solver_partial_bytes();
 cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
                                    void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
-                                   void* part, void* state, cudaStream_t s);
+                                   void* part, void* state, int cluster, cudaStream_t s);
 // n complex FP32 -> bfloat16 pairs (coarse operator in BF16 storage)
 cudaError_t launch_complex_to_bf16(const void* in, void* out, size_t n, cudaStream_t s);
 // coarse op layout change: internal [Vc][Nc][9][Nc] -> canonical [Vc][9][Nc][Nc] doubles
