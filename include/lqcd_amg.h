@@ -236,9 +236,14 @@ amg_status amg_setup_load(amg_dirac* d, const char* path, amg_hierarchy** out);
 /* ---- transfer and coarse operators (Eqs. 4-6) -------------------------- */
 
 /* y = D_c x on level l >= 1 (the 9-point stencil), nrhs canonical coarse
- * vectors; prec AMG_F64 (double vectors) or AMG_F32 / AMG_BF16 (float).  The
- * operator is applied as the level stores it (bfloat16 entries with FP32
- * accumulation when the hierarchy was built with prec_coarsest = AMG_BF16). */
+ * vectors (element type double for AMG_F64, float otherwise).  AMG_F64 /
+ * AMG_F32: the operator is applied as the level stores it (bfloat16 entries
+ * with FP32 accumulation when the level was built with a bfloat16 stencil).
+ * AMG_BF16: the tensor-core path for levels with a bfloat16 stencil and
+ * Nc % 16 == 0 (AMG_EINVAL otherwise): the vectors are rounded to bfloat16
+ * and each coarse site's rows are one dense contraction over up to 16
+ * right-hand sides at a time (tcgen05 MMA, FP32 accumulation in tensor
+ * memory); AMG_TIMEOUT if a bounded wait in the kernel gave up. */
 amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* out, int nrhs,
                             amg_prec prec, amg_stream s);
 

@@ -64,6 +64,7 @@ struct CoarseLevel {
     int prec = 1;        // vector / arithmetic precision: 0 FP64, 1 FP32
     bool opbf = false;   // operator additionally stored in bfloat16 (B16) and applied from there
     DevBuf B, B16;
+    DevBuf tci;                 // bfloat16 stencil in the tensor-core operand layout (multi-RHS apply)
     DevBuf cs_part, cs_state;   // persistent coarse solver scratch
     // levels between the fine and the coarsest grid: the level's own test
     // vectors (coarsening to the next level) and its FGMRES(inter_m) space
@@ -853,6 +854,10 @@ amg_status orthonormalise_and_galerkin(amg_hierarchy* h, cudaStream_t s) {
     CK(launch_galerkin_fine(h->vp, L.prec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, d->gauge->U[h->vp].p,
                             d->C[h->vp].p, d->kappa, L.B.p, s));
     if (L.opbf) CK(launch_complex_to_bf16(L.B.p, L.B16.p, (size_t)L.g.V * 9 * L.nc * L.nc, s));
+    if (L.opbf && coarse_tc_supported(L.nc)) {
+        CK(L.tci.ensure(coarse_tc_image_bytes(L.g.V, L.nc)));
+        CK(launch_coarse_tc_image(L.g.V, L.nc, L.B.p, L.tci.p, s));
+    }
     return AMG_OK;
 }
 
@@ -907,6 +912,10 @@ amg_status galerkin_c(amg_hierarchy* h, int l, cudaStream_t s) {
     CoarseLevel& N = h->lev[l + 1];
     CK(launch_galerkin_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, L.B.p, N.B.p, s));
     if (N.opbf) CK(launch_complex_to_bf16(N.B.p, N.B16.p, (size_t)N.g.V * 9 * N.nc * N.nc, s));
+    if (N.opbf && coarse_tc_supported(N.nc)) {
+        CK(N.tci.ensure(coarse_tc_image_bytes(N.g.V, N.nc)));
+        CK(launch_coarse_tc_image(N.g.V, N.nc, N.B.p, N.tci.p, s));
+    }
     return AMG_OK;
 }
 
@@ -1603,6 +1612,23 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
     CoarseLevel& L = h->lev[level];
     int vprec = prec == AMG_F64 ? 0 : 1;
     cudaStream_t st = (cudaStream_t)s;
+    if (prec == AMG_BF16) {
+        // bfloat16 operands on the tensor cores, up to 16 right-hand sides per launch
+        if (!L.opbf || !L.tci.p) return fail(AMG_EINVAL, "AMG_BF16 apply needs a bfloat16 stencil with Nc % 16 == 0");
+        const size_t cv = coarse_n(L) * sizeof(float2);
+        CK(h->err_flag.ensure(sizeof(int)));
+        CK(cudaMemsetAsync(h->err_flag.p, 0, sizeof(int), st));
+        for (int r0 = 0; r0 < nrhs; r0 += 16) {
+            const int nr = std::min(16, nrhs - r0);
+            CK(launch_coarse_apply_tc(L.g, L.nc, L.tci.p, (const char*)in + r0 * cv, (char*)out + r0 * cv, nullptr, nr,
+                                      h->err_flag.as<int>(), st));
+        }
+        int flag = 0;
+        CK(cudaMemcpyAsync(&flag, h->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (flag) return fail(AMG_TIMEOUT, "tensor-core coarse stencil: a wait timed out");
+        return AMG_OK;
+    }
     if (vprec == L.prec) {
         CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), in, out, nullptr, nrhs, st));
         return AMG_OK;
