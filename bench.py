@@ -511,6 +511,69 @@ def run_ragged(args):
     print(json.dumps(line), flush=True)
 
 
+def run_coarse_tc(args):
+    """The coarse 9-point stencil alone on an 8^3x16 coarse lattice with
+    Nc = 48 (16^3x32 fine lattice, links exp(0.6iH), seed 2, kappa 0.130,
+    c_sw 1.0, 2^4 blocks, 24 test vectors), stencil stored in bfloat16:
+    the tensor-core path (bfloat16 operands, FP32 accumulation, 16 and 8
+    right-hand sides per launch) against the SIMT path (FP32 vectors).
+    Compulsory bytes per tensor-core launch: the operand image of the stencil
+    (2 Nc x 9 Nc bfloat16 per coarse site, 83 KB) plus the nrhs input and
+    output vectors (Nc FP32 complex per site each)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_05012_gb300 import capi
+    dims = (16, 16, 16, 32)
+    U, lat, g, d = _setup_field(capi, dims, 0.6, 2, 0.130, 1.0)
+    del U
+    p = capi.amg_params_default()
+    for mu in range(4):
+        p.block[0][mu] = 2
+    p.nvec[0] = 24
+    p.prec_coarsest = capi.AMG_BF16
+    h = capi.amg_setup_from_vectors(d, p, [li.to_interleaved(li.test_vectors(dims, 2, 24))])
+    cdims, nc = capi.amg_level_info(h, 1)
+    Vc = int(np.prod(cdims))
+    hbm, kind = _peaks()
+    x = li.complex_normal(5, li.STREAM_MISC, (16, Vc, nc))
+    xd = torch.from_numpy(li.to_interleaved(x).reshape(-1)).float().cuda()
+    stream = torch.cuda.current_stream()
+    img_bytes = Vc * 2 * nc * 9 * nc * 2
+    res = {}
+    with ClockSampler() as clk:
+        for name, prec, nrhs in (("tc16", capi.AMG_BF16, 16), ("tc8", capi.AMG_BF16, 8),
+                                 ("simt16", capi.AMG_F32, 16), ("simt1", capi.AMG_F32, 1)):
+            capi.amg_coarse_time(h, 1, xd, nrhs, prec, args.warmup, stream=stream)
+            l0 = capi.amg_launch_count()
+            ms = capi.amg_coarse_time(h, 1, xd, nrhs, prec, args.steps, stream=stream)
+            launches = capi.amg_launch_count() - l0
+            op_bytes = img_bytes if prec == capi.AMG_BF16 else Vc * 9 * nc * nc * 4
+            byts = op_bytes + 2 * nrhs * Vc * nc * 8
+            flops = 8.0 * 9 * nc * nc * nrhs * Vc
+            res[name] = {"nrhs": nrhs, "ms_per_launch": ms, "us_per_rhs": ms * 1e3 / nrhs,
+                         "gb_per_s": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+                         "useful_tflops": flops / (ms * 1e-3) / 1e12, "bytes_per_launch": byts,
+                         "launches": launches}
+    t = res["tc16"]
+    line = {"metric": "coarse 9-point stencil, kernel time per right-hand side (HBM roofline)",
+            "value": t["us_per_rhs"], "unit": "us/RHS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t["ms_per_launch"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
+            "config": {"workload": "coarse stencil, 8^3x16 coarse sites x Nc 48 (16^3x32 fine, 2^4 blocks, 24 test "
+                                   "vectors), bfloat16 stencil, 16 right-hand sides per tensor-core launch",
+                       "coarse_sites": Vc, "nc": nc, "l2": "operator image 680 MB > L2 (no flush)",
+                       "variants": res},
+            "roofline": {"kernel": "coarse_tc_kernel<32>", "bound": "hbm", "achieved": t["gb_per_s"], "peak": hbm,
+                         "unit": "GB/s", "frac": t["frac_hbm"], "traffic": None, "peak_kind": kind},
+            "gpu_launches": t["launches"], "clocks": clk.summary()}
+    capi.amg_hierarchy_destroy(h)
+    capi.amg_dirac_destroy(d)
+    capi.amg_gauge_destroy(g)
+    capi.amg_lattice_destroy(lat)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,7 +582,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac", "mixed3", "ragged"])
+    ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
@@ -535,6 +598,8 @@ def main():
         return run_mixed3(args)
     if args.workload == "ragged":
         return run_ragged(args)
+    if args.workload == "coarse_tc":
+        return run_coarse_tc(args)
 
     import torch
     import torch.distributed as dist

@@ -117,9 +117,10 @@ typedef struct {
 /* Message of the last failed call on this thread ("" if none). */
 const char* amg_last_error(void);
 
-/* Number of CUDA kernel launches this library has issued since it was loaded
- * (all threads, all devices; a running total, never reset).  No counterpart in
- * the paper: lets a caller count the kernels behind a call. */
+/* Number of CUDA kernels this library has run since it was loaded (all
+ * threads, all devices; a running total, never reset): direct launches, plus
+ * every kernel of a captured CUDA graph each time the graph is replayed.  No
+ * counterpart in the paper: lets a caller count the kernels behind a call. */
 unsigned long long amg_launch_count(void);
 
 /* Fill p with the defaults listed above. */
@@ -246,6 +247,15 @@ amg_status amg_setup_load(amg_dirac* d, const char* path, amg_hierarchy** out);
  * memory); AMG_TIMEOUT if a bounded wait in the kernel gave up. */
 amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* out, int nrhs,
                             amg_prec prec, amg_stream s);
+
+/* Timing of the coarse stencil alone: applies it `reps` times to the nrhs
+ * canonical coarse vectors `in` on stream s (results discarded), bracketed by
+ * CUDA events, and writes the mean milliseconds per application.  prec: the
+ * level's vector precision (AMG_F64 / AMG_F32: the SIMT stencil) or AMG_BF16
+ * (the tensor-core path, nrhs <= 16).  Synchronises s.  No counterpart in the
+ * paper: the kernel-only time behind the roofline of the coarse stencil. */
+amg_status amg_coarse_time(amg_hierarchy* h, int level, const void* in, int nrhs, amg_prec prec, int reps,
+                           amg_stream s, float* ms_per_apply);
 
 /* Eq. 4: coarse(I) = <I|fine> from level `coarsening` to coarsening+1.
  * fine is canonical at that level (a fine field for coarsening 0, a coarse

@@ -93,6 +93,7 @@ PROTOTYPES = {
     "amg_apply_D_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "amg_apply_Dsap": (_i, [_vp, _ip, _vp, _vp, _i, _i, _vp]),
     "amg_dirac_time": (_i, [_vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "amg_coarse_time": (_i, [_vp, _i, _vp, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_float)]),
     "amg_setup": (_i, [_vp, ctypes.POINTER(amg_params), ctypes.POINTER(_dp), ctypes.POINTER(_vp)]),
     "amg_setup_from_vectors": (_i, [_vp, ctypes.POINTER(amg_params), ctypes.POINTER(_dp), ctypes.POINTER(_vp)]),
     "amg_hierarchy_destroy": (None, [_vp]),
@@ -233,6 +234,14 @@ def amg_dirac_time(d, inp, nrhs=1, prec=AMG_F32, reps=20, stream=None):
     """Mean milliseconds per application of D (internal layout, kernel only)."""
     ms = ctypes.c_float()
     _check(load().amg_dirac_time(d, _ptr(inp), int(nrhs), int(prec), int(reps), _stream(stream), ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def amg_coarse_time(h, level, inp, nrhs=1, prec=AMG_F32, reps=20, stream=None):
+    """Mean milliseconds per application of the coarse stencil (kernel only)."""
+    ms = ctypes.c_float()
+    _check(load().amg_coarse_time(h, int(level), _ptr(inp), int(nrhs), int(prec), int(reps), _stream(stream),
+                                  ctypes.byref(ms)))
     return float(ms.value)
 
 

@@ -14,6 +14,9 @@
 #include <string>
 #include <vector>
 
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 using cplx = std::complex<double>;
 
 namespace {
@@ -205,10 +208,12 @@ struct amg_hierarchy {
     // ragged solves: step j of the outer solver (Z_j = M V_j, w = D Z_j) captured as a CUDA graph
     bool graph_mode = false;   // set while capturing: coarse solves run as one cluster
     std::vector<cudaGraphExec_t> gexec;
+    std::vector<unsigned long long> gkernels;   // kernels in each captured graph (counted per replay)
     void clear_graphs() {
         for (auto g : gexec)
             if (g) cudaGraphExecDestroy(g);
         gexec.clear();
+        gkernels.clear();
     }
     ~amg_hierarchy() {
         clear_graphs();
@@ -1052,8 +1057,12 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
 // the coarse BiCGStab(l) runs as one thread-block cluster, so the problems'
 // coarse solves overlap without a device-wide barrier.
 amg_status ragged_step(amg_hierarchy* h, int j, cudaStream_t st) {
-    if ((int)h->gexec.size() < h->p.outer_m) h->gexec.resize(h->p.outer_m, nullptr);
+    if ((int)h->gexec.size() < h->p.outer_m) {
+        h->gexec.resize(h->p.outer_m, nullptr);
+        h->gkernels.resize(h->p.outer_m, 0);
+    }
     if (!h->gexec[j]) {
+        const unsigned long long k0 = g_launches.load(std::memory_order_relaxed);
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
         h->graph_mode = true;
         amg_status rc = precondition64(h, h->oV[j]->p, h->oZ[j]->p, 1, st);
@@ -1071,8 +1080,12 @@ amg_status ragged_step(amg_hierarchy* h, int j, cudaStream_t st) {
         cudaGraphDestroy(g);
         CK(e);
         h->gexec[j] = ex;
+        // kernels recorded during the capture ran no work: count them at every replay instead
+        h->gkernels[j] = g_launches.load(std::memory_order_relaxed) - k0;
+        g_launches.fetch_sub(h->gkernels[j], std::memory_order_relaxed);
     }
     CK(cudaGraphLaunch(h->gexec[j], st));
+    g_launches.fetch_add(h->gkernels[j], std::memory_order_relaxed);
     return AMG_OK;
 }
 
@@ -1255,8 +1268,6 @@ double amg_internal_kappa(const amg_dirac* d) { return d->kappa; }
 void amg_internal_set_error(const char* msg) { g_err = msg; }
 
 // ================================================================ C ABI
-static std::atomic<unsigned long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" {
 
@@ -1641,6 +1652,42 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
     CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), a.p, b.p, nullptr, nrhs, st));
     CK(launch_convert_flat(L.prec, vprec, b.p, out, n, st));
     CK(cudaStreamSynchronize(st));
+    return AMG_OK;
+}
+
+amg_status amg_coarse_time(amg_hierarchy* h, int level, const void* in, int nrhs, amg_prec prec, int reps,
+                           amg_stream s, float* ms_per_apply) {
+    if (!h || !in || !ms_per_apply || nrhs < 1 || reps < 1 || level < 1 || level >= h->p.nlevels)
+        return fail(AMG_EINVAL, "bad argument");
+    CoarseLevel& L = h->lev[level];
+    const bool tc = prec == AMG_BF16;
+    if (tc && (!L.opbf || !L.tci.p)) return fail(AMG_EINVAL, "AMG_BF16 needs a bfloat16 stencil with Nc % 16 == 0");
+    if (!tc && ((prec == AMG_F64 ? 0 : 1) != L.prec || prec < 0 || prec > 1))
+        return fail(AMG_EINVAL, "prec must be the level's vector precision or AMG_BF16");
+    if (tc && nrhs > 16) return fail(AMG_EINVAL, "at most 16 right-hand sides per tensor-core launch");
+    cudaStream_t st = (cudaStream_t)s;
+    DevBuf out;
+    CK(out.ensure(coarse_n(L) * coarse_elem_bytes(L.prec) * nrhs));
+    CK(h->err_flag.ensure(sizeof(int)));
+    CK(cudaMemsetAsync(h->err_flag.p, 0, sizeof(int), st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaError_t err = cudaEventRecord(e0, st);
+    for (int i = 0; err == cudaSuccess && i < reps; ++i)
+        err = tc ? launch_coarse_apply_tc(L.g, L.nc, L.tci.p, in, out.p, nullptr, nrhs, h->err_flag.as<int>(), st)
+                 : launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), in, out.p, nullptr, nrhs, st);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return fail(AMG_ECUDA, cudaGetErrorString(err));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(AMG_TIMEOUT, "tensor-core coarse stencil: a wait timed out");
+    *ms_per_apply = ms / reps;
     return AMG_OK;
 }
 
