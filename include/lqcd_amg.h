@@ -196,7 +196,7 @@ amg_status amg_apply_Dsap(amg_dirac* d, const int block[4], const void* in, void
 /* Adaptive setup, steps (0-a) and (0-b) of Sec. 3: the init vectors are
  * smoothed by n_init SAP applications, block-orthonormalised in FP64 per
  * (domain, chirality) by Gram-Schmidt applied twice, the Galerkin coarse
- * operator D_c = <I|D|J> (Eq. 6) is built, then n_adapt passes v <- M v
+ * operator D_c = <I|D|J> (Eq. 7) is built, then n_adapt passes v <- M v
  * follow.  init_vecs[l] is a host array of nvec[l] canonical vectors of
  * level l (doubles: fine [site][spin][colour][re, im], coarse
  * [site][Nc][re, im]), one array for every level 0..nlevels-2; the random
@@ -209,7 +209,7 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
                      amg_hierarchy** out);
 
 /* Hierarchy from given test vectors without smoothing: orthonormalise and
- * build the Galerkin operators (Eqs. 4-6) level by level.  Used by
+ * build the Galerkin operators (Eqs. 5-7) level by level.  Used by
  * checkpoint loading and for exact parity tests of the construction. */
 amg_status amg_setup_from_vectors(amg_dirac* d, const amg_params* p, const double* const* vecs,
                                   amg_hierarchy** out);
@@ -224,7 +224,7 @@ amg_status amg_get_vectors(amg_hierarchy* h, int coarsening, double* host_out);
 
 /* Coarse operator of level l >= 1 as host doubles [site][d 9][Nc][Nc][re, im]
  * with d = 0 self, 1+mu the block coupling X to X+mu, 5+mu to X-mu, so that
- * y(X) = sum_d B[X][d] x(X + d) (the 9-point stencil of Eq. 6).  Returned as
+ * y(X) = sum_d B[X][d] x(X + d) (the 9-point stencil of Eq. 7).  Returned as
  * computed (FP64 or FP32), before any bfloat16 storage rounding. */
 amg_status amg_get_coarse_op(amg_hierarchy* h, int level, double* host_out);
 
@@ -234,7 +234,7 @@ amg_status amg_get_coarse_op(amg_hierarchy* h, int level, double* host_out);
 amg_status amg_setup_save(const amg_hierarchy* h, const char* path);
 amg_status amg_setup_load(amg_dirac* d, const char* path, amg_hierarchy** out);
 
-/* ---- transfer and coarse operators (Eqs. 4-6) -------------------------- */
+/* ---- transfer and coarse operators (Eqs. 5-7) -------------------------- */
 
 /* y = D_c x on level l >= 1 (the 9-point stencil), nrhs canonical coarse
  * vectors (element type double for AMG_F64, float otherwise).  AMG_F64 /
@@ -257,13 +257,13 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
 amg_status amg_coarse_time(amg_hierarchy* h, int level, const void* in, int nrhs, amg_prec prec, int reps,
                            amg_stream s, float* ms_per_apply);
 
-/* Eq. 4: coarse(I) = <I|fine> from level `coarsening` to coarsening+1.
+/* Eq. 5: coarse(I) = <I|fine> from level `coarsening` to coarsening+1.
  * fine is canonical at that level (a fine field for coarsening 0, a coarse
  * vector [site][Nc] for coarsening >= 1); element type from prec as above. */
 amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void* coarse, int nrhs,
                         amg_prec prec, amg_stream s);
 
-/* Eq. 5: fine = sum_I coarse(I) |I>. */
+/* Eq. 6: fine = sum_I coarse(I) |I>. */
 amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, void* fine, int nrhs,
                        amg_prec prec, amg_stream s);
 

@@ -12,7 +12,7 @@ Every function follows a named passage of Kanamori, Ishikawa, Matsufuru,
 
   dirac.py      Eq. 1 (Wilson-clover D), Eq. 2 (gamma5-hermiticity), the
                 domain-decomposed D_SAP of Sec. 3 (SAP paragraph)
-  multigrid.py  Eqs. 4-6 (restriction, prolongation, Galerkin coarse matrix),
+  multigrid.py  Eqs. 5-7 (restriction, prolongation, Galerkin coarse matrix),
                 the chiral doubling of the footnote in Sec. 3, the
                 orthonormalisation <I|J> = delta_IJ
   solvers.py    the SAP listing and its inner-domain minimal-residual solver

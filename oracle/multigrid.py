@@ -1,4 +1,4 @@
-"""Restriction, prolongation and the Galerkin coarse operator (Sec. 3, Eqs. 4-6).
+"""Restriction, prolongation and the Galerkin coarse operator (Sec. 3, Eqs. 5-7).
 
 Basis (Sec. 3 and its footnote): for each domain X, chirality s in {+, -} and
 test vector i, |X, s, i> is the i-th test vector projected by P_s and
@@ -8,9 +8,9 @@ coarse degrees of freedom and P_- the second half (reading C14).  In both cases
 the chirality halves are the first and second half of the dof axis, so one
 code serves every level.  Coarse dof index: I = s * Nnv + i.
 
-Eq. 4 (restriction):  x(I) = <I|x>
-Eq. 5 (prolongation): |x'> = sum_I x(I) |I>
-Eq. 6 (coarse matrix): D_c(I, J) = <I|D|J>
+Eq. 5 (restriction):  x(I) = <I|x>
+Eq. 6 (prolongation): |x'> = sum_I x(I) |I>
+Eq. 7 (coarse matrix): D_c(I, J) = <I|D|J>
 
 The coarse operator is stored as a 9-point block stencil (S7): for each coarse
 site X, B[X, 0] = <X|D|X>, B[X, 1+mu] = <X|D|X+mu> (hops that leave X forwards
@@ -48,7 +48,7 @@ def coarse_shape(shape4, block):
 
 
 def restrict(vecs: np.ndarray, psi: np.ndarray, block) -> np.ndarray:
-    """Eq. 4: x_c(X, s, i) = sum_{x in X} (P_s v_i)(x)^dag psi(x)."""
+    """Eq. 5: x_c(X, s, i) = sum_{x in X} (P_s v_i)(x)^dag psi(x)."""
     n = vecs.shape[0]
     shape4 = psi.shape[:4]
     vb = np.stack([_blocked(v, block) for v in vecs])        # (n, C, Vb, 2, h)
@@ -58,7 +58,7 @@ def restrict(vecs: np.ndarray, psi: np.ndarray, block) -> np.ndarray:
 
 
 def prolong(vecs: np.ndarray, xc: np.ndarray, block) -> np.ndarray:
-    """Eq. 5: psi'(x) = sum_{s,i} x_c(X(x), s, i) (P_s v_i)(x)."""
+    """Eq. 6: psi'(x) = sum_{s,i} x_c(X(x), s, i) (P_s v_i)(x)."""
     n = vecs.shape[0]
     shape4 = vecs.shape[1:5]
     vb = np.stack([_blocked(v, block) for v in vecs])        # (n, C, Vb, 2, h)
@@ -101,7 +101,7 @@ def chiral_column(v: np.ndarray, t: int) -> np.ndarray:
 
 
 def coarse_operator(op, vecs: np.ndarray, block) -> "CoarseStencil":
-    """Eq. 6 by domain faces: <X,I|D|X+d,J> for the self block (intra-domain
+    """Eq. 7 by domain faces: <X,I|D|X+d,J> for the self block (intra-domain
     part of D) and the eight hop blocks (the hops of D that cross a face)."""
     check_blocking(op.dims, block)
     n = vecs.shape[0]
@@ -132,7 +132,7 @@ def basis_vector(vecs: np.ndarray, block, X, col) -> np.ndarray:
 
 
 def coarse_dense_bruteforce(op, vecs: np.ndarray, block) -> np.ndarray:
-    """Eq. 6 by brute force: D applied to every prolonged unit coarse vector,
+    """Eq. 7 by brute force: D applied to every prolonged unit coarse vector,
     then restricted.  Index = coarse_site * Nc + I (coarse site lexicographic)."""
     n = vecs.shape[0]
     nc = 2 * n

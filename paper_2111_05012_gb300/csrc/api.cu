@@ -911,7 +911,7 @@ amg_status upload_cvecs(amg_hierarchy* h, int l, const double* host, cudaStream_
     return AMG_OK;
 }
 
-// Eq. 6 one level down: stencil of level l+1 from level l's stencil and vectors
+// Eq. 7 one level down: stencil of level l+1 from level l's stencil and vectors
 amg_status galerkin_c(amg_hierarchy* h, int l, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
     CoarseLevel& N = h->lev[l + 1];
@@ -1699,7 +1699,7 @@ static amg_status transfer_common(amg_hierarchy* h, int coarsening, int nrhs, am
     return AMG_OK;
 }
 
-// Eqs. 4-5 from coarse level l >= 1: canonical = internal coarse layout; vectors
+// Eqs. 5-6 from coarse level l >= 1: canonical = internal coarse layout; vectors
 // converted around the kernel when the caller's precision is not the level's
 static amg_status coarse_transfer(amg_hierarchy* h, int l, bool restrict_dir, const void* in, void* out, int nrhs,
                                   amg_prec prec, cudaStream_t st) {

@@ -1,5 +1,5 @@
 // Coarse-lattice kernels: the 9-point block stencil y(X) = sum_d B[X][d] x(X+d)
-// of the Galerkin operator (Eq. 6) and precision conversion of flat complex
+// of the Galerkin operator (Eq. 7) and precision conversion of flat complex
 // arrays.  Internal stencil layout [X][row][d][col] (complex, row-major) so
 // that one output row reads one contiguous run of 9 * Nc entries.
 #include "common.cuh"

@@ -1,8 +1,8 @@
 // Multigrid kernels on coarse lattices, used when the hierarchy has three or
-// more grids: restriction and prolongation from level l >= 1 to l+1 (Eqs. 4-5
+// more grids: restriction and prolongation from level l >= 1 to l+1 (Eqs. 5-6
 // with the chirality halves of the coarse dof axis), block Gram-Schmidt of the
 // level-l test vectors, the Galerkin stencil of level l+1 built from the
-// 9-point stencil of level l (Eq. 6), and the SAP half sweep with
+// 9-point stencil of level l (Eq. 7), and the SAP half sweep with
 // minimal-residual domain solves on a coarse lattice (Sec. 3 listing).
 //
 // Layouts: coarse vectors [site][nc] complex; test vectors [nvec][site][nc];
@@ -101,7 +101,7 @@ template <> DEV cx<float> ldop<float, true>(const void* B, size_t i) {
     return {f.x, f.y};
 }
 
-// ------------------------------------------------------------ Eq. 4
+// ------------------------------------------------------------ Eq. 5
 // out(X, s*nv + i) = sum_{x in X} sum_{a in half s} conj(v_i(x)[a]) in(x)[a]
 // grid (Vc, nrhs); a warp per output, lanes over the block's terms
 template <typename TC>
@@ -127,7 +127,7 @@ __global__ void crestrict_kernel(CB k, int nc, int nv, const void* __restrict__ 
     }
 }
 
-// ------------------------------------------------------------ Eq. 5
+// ------------------------------------------------------------ Eq. 6
 // out(x)[a] = sum_i v_i(x)[a] in(X(x), s(a)*nv + i); grid (Vc, nrhs)
 template <typename TC>
 __global__ void cprolong_kernel(CB k, int nc, int nv, const void* __restrict__ vecs, const void* __restrict__ in,
@@ -217,7 +217,7 @@ __global__ void cortho_kernel(CB k, int nc, int nv, void* vecs, int* err) {
     }
 }
 
-// ------------------------------------------------------------ Eq. 6 on a coarse level
+// ------------------------------------------------------------ Eq. 7 on a coarse level
 // Bout[X][I][d][J] = sum over the hops x -> x+d1 of level l that couple block X
 // to block X+d of  conj(v_I(x)) . B_l[x][d1] . v_J(x+d1),
 // v_I = P_s v_i (I = s*nv + i).  d = 0 collects d1 = 0 and the hops that stay

@@ -82,16 +82,16 @@ cudaError_t launch_coarse_apply(int cprec, const GeomH& gc, int nc, const BlockH
 // ---- levels l >= 1 of a hierarchy with three or more grids (coarse_mg.cu) ----
 // vprec 0: FP64, 1: FP32 (vectors, test vectors and stencils of the level).
 // Vectors [V][nc] complex, test vectors [nvec][V][nc], nrhs vectors one after another.
-// Eq. 4 from level l (lattice g, blocks bh) to the [Vc][2 nvec] vectors of level l+1
+// Eq. 5 from level l (lattice g, blocks bh) to the [Vc][2 nvec] vectors of level l+1
 cudaError_t launch_restrict_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
                                    const void* fine, void* coarse, int nrhs, cudaStream_t s);
-// Eq. 5 from level l+1 back to level l
+// Eq. 6 from level l+1 back to level l
 cudaError_t launch_prolong_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
                                   const void* coarse, void* fine, int nrhs, cudaStream_t s);
 // block Gram-Schmidt of the level-l test vectors per (block, chirality half); *err = 1 on rank deficiency
 cudaError_t launch_orthonormalise_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, void* vecs,
                                          int* err, cudaStream_t s);
-// Eq. 6: stencil of level l+1 ([Vc][2 nvec][9][2 nvec]) from the level-l stencil B ([V][nc][9][nc])
+// Eq. 7: stencil of level l+1 ([Vc][2 nvec][9][2 nvec]) from the level-l stencil B ([V][nc][9][nc])
 cudaError_t launch_galerkin_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
                                    const void* B, void* Bout, cudaStream_t s);
 // SAP half sweep on level l: domains of `colour`, fused residual + nmr MR steps; kprec 0 FP64,

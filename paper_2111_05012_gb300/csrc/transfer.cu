@@ -1,7 +1,7 @@
 // Transfer between the fine lattice and the first coarse lattice (Sec. 3):
-// restriction x(I) = <I|x> (Eq. 4), prolongation |x'> = sum_I x(I)|I> (Eq. 5),
+// restriction x(I) = <I|x> (Eq. 5), prolongation |x'> = sum_I x(I)|I> (Eq. 6),
 // the block orthonormalisation <I|J> = delta_IJ and the Galerkin coarse
-// operator D_c(I, J) = <I|D|J> (Eq. 6).  |X, s, i> is test vector i projected
+// operator D_c(I, J) = <I|D|J> (Eq. 7).  |X, s, i> is test vector i projected
 // to chirality s (spins 0,1 or 2,3) and restricted to block X; coarse dof
 // index I = s * nvec + i.  One CTA works on one block, one thread per site.
 #include "common.cuh"
