@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
 constexpr long long kTcSpin = 20000000;
 
 DEV uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -136,24 +136,35 @@ DEV int tc_nbr(const TcArgs& a, int X, int d) {
     return c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
 }
 
+// Shared-memory plan of one CTA (byte offsets; see coarse_tc_plan).  A
+// descriptor always spans 16 row groups (M = 128), but only the first 2Nc/8
+// hold operator rows: the rest of the span may overlap the next buffer, and
+// the accumulator rows it produces (2Nc..127) are never read.
+struct TcPlan {
+    int a0, a1;        // operator buffers (a1 == a0: single buffer)
+    int bsm, dsm, bar; // gathered vectors, accumulator staging, mbarriers
+    int bytes;         // dynamic shared memory to request
+};
+
 template <int NP>   // NP = 2P accumulator columns (16 or 32)
-__global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a, TcPlan pl) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int nc = a.nc, K = 9 * nc, kg = K / 8, mgv = 2 * nc / 8;
-    const unsigned a_bytes = (unsigned)(2 * nc) * K * 2;   // valid rows of A for one site
-    __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem_raw);                 // 16 row groups
-    __nv_bfloat16* Bs = As + (size_t)16 * kg * 64;                                     // NP / 8 row groups
-    float* Ds = reinterpret_cast<float*>(Bs + (size_t)(NP / 8) * kg * 64);             // [128][NP]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Ds + 128 * NP);                       // [0] A copy, [1] MMA
-    uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2);
+    const int nc = a.nc, K = 9 * nc, kg = K / 8, pairs = nc / 2;
+    const unsigned a_bytes = (unsigned)(2 * nc) * K * 2;   // operator rows of one site
+    unsigned char* Abuf[2] = {smem_raw + pl.a0, smem_raw + pl.a1};
+    const bool dbl = pl.a1 != pl.a0;
+    __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(smem_raw + pl.bsm);
+    float* Ds = reinterpret_cast<float*>(smem_raw + pl.dsm);   // [128][NP]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + pl.bar);   // [0], [1] operator copies, [2] MMA
+    uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
     int* fail = reinterpret_cast<int*>(slot + 1);
+    int* nbr = fail + 1;   // [9] neighbour sites of the current coarse site
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // rows 2nc..127 of A stay zero
-    for (size_t i = (size_t)mgv * kg * 64 + tid; i < (size_t)16 * kg * 64; i += kTcThreads) As[i] = __float2bfloat16(0.f);
     if (tid == 0) {
         mb_init(&bars[0], 1);
         mb_init(&bars[1], 1);
+        mb_init(&bars[2], 1);
         mb_fence_init();
         *fail = 0;
     }
@@ -167,51 +178,75 @@ __global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a) {
     const uint32_t tmem = *slot;
     const uint32_t idesc = idesc_bf16(128, NP);
     const uint32_t lbo = 128, sbo = (uint32_t)kg * 128;
-    unsigned ph_a = 0, ph_m = 0;
-    bool copy_pending = false;
+    unsigned ph[2] = {0, 0}, ph_m = 0;
+    bool pend[2] = {false, false};   // meaningful in thread 0 only
+    auto issue = [&](int X, int b) {
+        mb_expect_tx(&bars[b], a_bytes);
+        bulk_load(Abuf[b], a.img + (size_t)X * (2 * nc) * K, a_bytes, &bars[b]);
+        pend[b] = true;
+    };
+    if (tid == 0 && blockIdx.x < a.V) issue(blockIdx.x, 0);
 
-    for (int X = blockIdx.x; X < a.V; X += gridDim.x) {
-        if (tid == 0) {
-            mb_expect_tx(&bars[0], a_bytes);
-            bulk_load(As, a.img + (size_t)X * (2 * nc) * K, a_bytes, &bars[0]);
-        }
-        copy_pending = true;
-        // gather G: row r = Re x_r, row P + r = Im x_r, column k = d * nc + b
-        for (int idx = tid; idx < a.P * K; idx += kTcThreads) {
-            const int r = idx / K, k = idx - r * K;
-            const int d = k / nc, bb = k - d * nc;
-            float2 v = make_float2(0.f, 0.f);
-            if (r < a.nrhs) v = a.x[((size_t)r * a.V + tc_nbr(a, X, d)) * nc + bb];
-            Bs[core_off(r, k, kg)] = __float2bfloat16(v.x);
-            Bs[core_off(a.P + r, k, kg)] = __float2bfloat16(v.y);
+    int it = 0;
+    for (int X = blockIdx.x; X < a.V; X += gridDim.x, ++it) {
+        const int sel = dbl ? (it & 1) : 0;
+        const int Xn = X + gridDim.x;
+        if (dbl && tid == 0 && Xn < a.V) issue(Xn, sel ^ 1);   // its buffer was last read by the previous MMA
+        if (tid < 9) nbr[tid] = tc_nbr(a, X, tid);
+        __syncthreads();
+        // gather G: row r = Re x_r, row P + r = Im x_r, column k = d * nc + b, two complex per load
+        const int items = a.P * 9 * pairs;
+        for (int base = tid; base < items; base += kTcThreads * 4) {
+            float4 v[4];
+            int rr[4], kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * kTcThreads;
+                rr[u] = -1;
+                if (idx < items) {
+                    const int r = idx / (9 * pairs), rem = idx - r * 9 * pairs;
+                    const int d = rem / pairs, c2 = rem - d * pairs;
+                    rr[u] = r;
+                    kk[u] = d * nc + 2 * c2;
+                    v[u] = r < a.nrhs ? __ldg(reinterpret_cast<const float4*>(a.x) +
+                                              ((size_t)r * a.V + nbr[d]) * pairs + c2)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (rr[u] < 0) continue;
+                *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(rr[u], kk[u], kg)) = __floats2bfloat162_rn(v[u].x, v[u].z);
+                *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(a.P + rr[u], kk[u], kg)) =
+                    __floats2bfloat162_rn(v[u].y, v[u].w);
+            }
         }
         proxy_fence();
         __syncthreads();
         if (tid == 0) {
-            if (mb_wait(&bars[0], ph_a)) {
-                copy_pending = false;
+            if (mb_wait(&bars[sel], ph[sel])) {
+                pend[sel] = false;
+                ph[sel] ^= 1;
                 tc_after();
-                const uint32_t a0 = su32(As), b0 = su32(Bs);
-                for (int kk = 0; kk < K / 16; ++kk)
-                    mma_bf16(tmem, smem_desc(a0 + kk * 256, lbo, sbo), smem_desc(b0 + kk * 256, lbo, sbo), idesc,
-                             kk > 0 ? 1u : 0u);
-                mma_commit(&bars[1]);
+                const uint32_t a0 = su32(Abuf[sel]), b0 = su32(Bs);
+                for (int q = 0; q < K / 16; ++q)
+                    mma_bf16(tmem, smem_desc(a0 + q * 256, lbo, sbo), smem_desc(b0 + q * 256, lbo, sbo), idesc,
+                             q > 0 ? 1u : 0u);
+                mma_commit(&bars[2]);
             } else {
                 *fail = 1;
             }
         }
         __syncthreads();
         if (*fail) break;
-        copy_pending = false;
-        ph_a ^= 1;
-        if (!mb_wait(&bars[1], ph_m)) {
-            atomicExch(fail, 2);
-        }
+        if (!mb_wait(&bars[2], ph_m)) atomicExch(fail, 2);
         ph_m ^= 1;
         __syncthreads();
         if (*fail) break;
         tc_after();
-        {
+        // the operator buffer is free again: fetch the next site's rows during the epilogue
+        if (!dbl && tid == 0 && Xn < a.V) issue(Xn, 0);
+        if (warp < 4) {
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
             const int row = warp * 32 + lane;
             if (NP == 32) {
@@ -243,9 +278,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a) {
         __syncthreads();
     }
     if (*fail) {
-        // drain our own bulk copy before the shared memory goes away
-        if (tid == 0 && *fail == 1 && copy_pending) mb_wait(&bars[0], ph_a);
-        if (tid == 0) atomicExch(a.err, 1);
+        if (tid == 0) {
+            // drain our own bulk copies before the shared memory goes away
+            for (int b = 0; b < 2; ++b)
+                if (pend[b]) mb_wait(&bars[b], ph[b]);
+            atomicExch(a.err, 1);
+        }
     }
     tc_before();
     __syncthreads();
@@ -305,12 +343,29 @@ cudaError_t launch_coarse_apply_tc(const GeomH& g, int nc, const void* img, cons
     a.b = (const float2*)b;
     a.err = err;
     const int K = 9 * nc, kg = K / 8, NP = 2 * a.P;
-    const size_t smem = (size_t)16 * kg * 128 + (size_t)(NP / 8) * kg * 128 + 128 * NP * 4 + 64;
+    const int a_data = 2 * nc * K * 2, a_span = 16 * kg * 128;
+    const int b_bytes = (NP / 8) * kg * 128, d_bytes = 128 * NP * 4, tail = 3 * 8 + 4 + 4 + 9 * 4;
+    const int kMax = 227 * 1024;
+    auto plan = [&](bool dbl) {
+        TcPlan p;
+        p.a0 = 0;
+        p.a1 = dbl ? a_data : 0;
+        p.bsm = (dbl ? 2 * a_data : a_data);
+        p.dsm = p.bsm + b_bytes;
+        p.bar = p.dsm + d_bytes;
+        const int end = p.bar + tail;
+        const int span = p.a1 + a_span;   // the last operator descriptor's reach
+        p.bytes = ((end > span ? end : span) + 127) / 128 * 128;
+        return p;
+    };
+    TcPlan pl = plan(true);
+    if (pl.bytes > kMax) pl = plan(false);
+    if (pl.bytes > kMax) return cudaErrorInvalidValue;
     const void* fn = NP == 32 ? (const void*)coarse_tc_kernel<32> : (const void*)coarse_tc_kernel<16>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.bytes);
     if (e != cudaSuccess) return e;
     const int grid = g.V < tc_sms() ? g.V : tc_sms();
-    void* params[] = {&a};
+    void* params[] = {&a, &pl};
     note_launch();
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kTcThreads), params, smem, st);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kTcThreads), params, pl.bytes, st);
 }

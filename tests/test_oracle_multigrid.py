@@ -11,7 +11,7 @@ DIMS = (4, 4, 4, 4)
 BLOCK = (2, 2, 2, 2)
 
 
-pytest.fixture(scope="module")
+@pytest.fixture(scope="module")
 def setup4():
     U = li.gauge_field(DIMS, 0.3, 1)
     op = dirac.WilsonClover(U, 0.124, 1.0)
@@ -49,15 +49,15 @@ def test_orthonormalise_rank_deficiency():
 def test_prolongator_orthonormal_and_restriction_adjoint(setup4):
     op, v, vo = setup4
     P = mg.prolongator_matrix(vo, BLOCK)
-    assert np.abs(P.conj().T  P - np.eye(P.shape[1])).max() < 1e-14
+    assert np.abs(P.conj().T @ P - np.eye(P.shape[1])).max() < 1e-14
     psi = li.rhs(DIMS, 5).reshape(op.shape4 + (12,))
     xc = mg.restrict(vo, psi, BLOCK)
-    assert np.abs(P.conj().T  psi.reshape(-1) - xc.reshape(-1)).max() < 1e-14   # R = P^dag
-    assert np.abs(P  xc.reshape(-1) - mg.prolong(vo, xc, BLOCK).reshape(-1)).max() < 1e-14
+    assert np.abs(P.conj().T @ psi.reshape(-1) - xc.reshape(-1)).max() < 1e-14   # R = P^dag
+    assert np.abs(P @ xc.reshape(-1) - mg.prolong(vo, xc, BLOCK).reshape(-1)).max() < 1e-14
     # gamma5 P = P gamma5_c
     g5 = np.kron(np.eye(256), np.kron(np.diag([1, 1, -1, -1]), np.eye(3)))
     g5c = np.kron(np.eye(16), np.diag([1.0] * 8 + [-1.0] * 8))
-    assert np.abs(g5  P - P  g5c).max() < 1e-15
+    assert np.abs(g5 @ P - P @ g5c).max() < 1e-15
 
 
 def test_galerkin_stencil_equals_bruteforce(setup4):
@@ -67,10 +67,10 @@ def test_galerkin_stencil_equals_bruteforce(setup4):
     assert np.abs(Dc - mg.coarse_dense_bruteforce(op, vo, BLOCK)).max() < 1e-14
     P = mg.prolongator_matrix(vo, BLOCK)
     D = dirac.sparse_matrix(op.U, op.kappa, op.csw, op.antiperiodic_t)
-    assert np.abs(P.conj().T  (D  P) - Dc).max() < 1e-14
+    assert np.abs(P.conj().T @ (D @ P) - Dc).max() < 1e-14
     # coarse gamma5-hermiticity
     g5c = np.kron(np.eye(16), np.diag([1.0] * 8 + [-1.0] * 8))
-    assert np.abs(g5c  Dc  g5c - Dc.conj().T).max() < 1e-14
+    assert np.abs(g5c @ Dc @ g5c - Dc.conj().T).max() < 1e-14
     # extent-2 coarse lattice: forward and backward hop blocks are different
     assert np.abs(B.B[..., 1, :, :] - B.B[..., 5, :, :]).max() > 1e-3
 
@@ -83,7 +83,7 @@ def test_galerkin_odd_shape():
     vo = mg.orthonormalise(li.test_vectors(dims, 7, 3).reshape((3,) + U.shape[:4] + (12,)), block)
     P = mg.prolongator_matrix(vo, block)
     D = dirac.sparse_matrix(U, 0.12, 1.0, True)
-    assert np.abs(P.conj().T  (D  P) - mg.coarse_operator(op, vo, block).dense()).max() < 1e-14
+    assert np.abs(P.conj().T @ (D @ P) - mg.coarse_operator(op, vo, block).dense()).max() < 1e-14
 
 
 def test_petrov_galerkin_orthogonality(setup4):
@@ -109,7 +109,7 @@ def test_square_prolongator_two_grid_is_exact():
     assert P.shape[0] == P.shape[1]
     Dc = mg.coarse_operator(op, vo, block).dense()
     D = dirac.dense_matrix(U, 0.13, 1.0)
-    assert np.abs(P  Dc  P.conj().T - D).max() < 1e-13
+    assert np.abs(P @ Dc @ P.conj().T - D).max() < 1e-13
     b = li.rhs(dims, 3).reshape(op.shape4 + (12,))
     xc = np.linalg.solve(Dc, mg.restrict(vo, b, block).reshape(-1))
     x = mg.prolong(vo, xc.reshape((2, 2, 2, 2, 12)), block)
@@ -129,4 +129,4 @@ def test_coarse_level_galerkin_recursion(setup4):
     wo = mg.orthonormalise(w, (2, 2, 2, 2))
     C2 = mg.coarse_operator(C1, wo, (2, 2, 2, 2))
     P2 = mg.prolongator_matrix(wo, (2, 2, 2, 2))
-    assert np.abs(P2.conj().T  C1.dense()  P2 - C2.dense()).max() < 1e-13
+    assert np.abs(P2.conj().T @ C1.dense() @ P2 - C2.dense()).max() < 1e-13
