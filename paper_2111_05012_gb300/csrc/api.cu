@@ -68,6 +68,7 @@ struct CoarseLevel {
     bool opbf = false;   // operator additionally stored in bfloat16 (B16) and applied from there
     DevBuf B, B16;
     DevBuf tci;                 // bfloat16 stencil in the tensor-core operand layout (multi-RHS apply)
+    DevBuf tcx;                 // packed bfloat16 vectors of one tensor-core launch
     DevBuf cs_part, cs_state;   // persistent coarse solver scratch
     // levels between the fine and the coarsest grid: the level's own test
     // vectors (coarsening to the next level) and its FGMRES(inter_m) space
@@ -1651,8 +1652,9 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
         CK(cudaMemsetAsync(h->err_flag.p, 0, sizeof(int), st));
         for (int r0 = 0; r0 < nrhs; r0 += 16) {
             const int nr = std::min(16, nrhs - r0);
+            CK(L.tcx.ensure(coarse_tc_pack_bytes(L.g.V, L.nc)));
             CK(launch_coarse_apply_tc(L.g, L.nc, L.tci.p, (const char*)in + r0 * cv, (char*)out + r0 * cv, nullptr, nr,
-                                      h->err_flag.as<int>(), st));
+                                      L.tcx.p, h->err_flag.as<int>(), st));
         }
         int flag = 0;
         CK(cudaMemcpyAsync(&flag, h->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1688,6 +1690,7 @@ amg_status amg_coarse_time(amg_hierarchy* h, int level, const void* in, int nrhs
     cudaStream_t st = (cudaStream_t)s;
     DevBuf out;
     CK(out.ensure(coarse_n(L) * coarse_elem_bytes(L.prec) * nrhs));
+    if (tc) CK(L.tcx.ensure(coarse_tc_pack_bytes(L.g.V, L.nc)));
     CK(h->err_flag.ensure(sizeof(int)));
     CK(cudaMemsetAsync(h->err_flag.p, 0, sizeof(int), st));
     cudaEvent_t e0, e1;
@@ -1695,7 +1698,8 @@ amg_status amg_coarse_time(amg_hierarchy* h, int level, const void* in, int nrhs
     CK(cudaEventCreate(&e1));
     cudaError_t err = cudaEventRecord(e0, st);
     for (int i = 0; err == cudaSuccess && i < reps; ++i)
-        err = tc ? launch_coarse_apply_tc(L.g, L.nc, L.tci.p, in, out.p, nullptr, nrhs, h->err_flag.as<int>(), st)
+        err = tc ? launch_coarse_apply_tc(L.g, L.nc, L.tci.p, in, out.p, nullptr, nrhs, L.tcx.p, h->err_flag.as<int>(),
+                                          st)
                  : launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), in, out.p, nullptr, nrhs, st);
     if (err == cudaSuccess) err = cudaEventRecord(e1, st);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);

@@ -3,25 +3,33 @@
 // with bfloat16 operands and FP32 accumulation in tensor memory (tcgen05).
 //
 // Per coarse site X the stencil is one dense complex contraction of the
-// Nc x 9Nc row block [B_0(X) ... B_8(X)] with the 9Nc x n_rhs gathered
-// neighbour vectors.  It runs as one real GEMM
-//   D (128 x 2P) = A (128 x 9Nc) . G^T,   A = [Re B; Im B] (rows 2Nc..127 zero),
-//   G = [Re x; Im x] (2P rows, P = n_rhs padded to 8 or 16),
-// after which y_re = D[a][r] - D[Nc+a][P+r] and y_im = D[Nc+a][r] + D[a][P+r].
-// A is streamed from a copy of the operator stored in the tensor-core
-// operand layout (8 x 8 core matrices, K-major, no swizzle) by one bulk copy
-// per site; G is gathered by the CTA into the same layout; one thread issues
-// the 9Nc/16 MMAs (M 128, N 2P, K 16) and commits them to an mbarrier; four
-// warps read the accumulator rows back with tcgen05.ld.
+// Nc x 9Nc row block [B_0(X) ... B_8(X)] with the 9Nc x n_rhs neighbour
+// vectors.  It runs as one real GEMM
+//   D (128 x 2P) = A (128 x 9Nc) . G^T,   G = [Re x; Im x] (2P rows),
+// P = n_rhs padded to 8 or 16.  A holds the rows Re B(a) and Im B(a) of
+// output a, ordered so that within every 32-row quarter lane l < 16 carries
+// Re B(16w + l) and lane l + 16 carries Im B(16w + l): after tcgen05.ld each
+// pair of lanes (l, l ^ 16) combines its rows with one warp shuffle,
+//   y_re = Re B . Re x - Im B . Im x,   y_im = Im B . Re x + Re B . Im x.
+// Rows 2Nc..127 of the M = 128 tile are never read back, so their part of
+// the shared-memory span is not filled.
+//
+// Both operands arrive by bulk copies: A from a copy of the operator in the
+// 8 x 8 core-matrix operand layout (K-major, no swizzle), one copy per site;
+// G as nine copies (one per direction d) of the neighbours' vectors, packed
+// once per call into the same layout with the k-groups outermost, so that
+// the nine pieces concatenate along K.  Copies of the next site overlap the
+// MMAs and the epilogue of the current one (two stages).  One thread issues
+// the 9Nc/16 MMAs (M 128, N 2P, K 16) and commits them to an mbarrier.
 //
 // All waits are bounded: on a timeout the kernel records an error, waits
-// (bounded) for its own bulk copy, releases its tensor memory and returns.
+// (bounded) for its own bulk copies, releases its tensor memory and returns.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 128;
 constexpr long long kTcSpin = 20000000;
 
 DEV uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -115,8 +123,8 @@ struct TcArgs {
     int L[4];
     int V, nc, nrhs, P;   // P: right-hand sides padded to 8 or 16
     const __nv_bfloat16* img;   // [V][2nc rows][9nc] in core-matrix order
-    const float2* x;            // [nrhs][V][nc]
-    float2* y;
+    const __nv_bfloat16* xp;    // [V][nc/8][2P/8][8][8]: packed neighbour vectors
+    float2* y;                  // [nrhs][V][nc]
     const float2* b;            // residual form y = b - D x when non-null
     int* err;
 };
@@ -136,35 +144,53 @@ DEV int tc_nbr(const TcArgs& a, int X, int d) {
     return c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
 }
 
-// Shared-memory plan of one CTA (byte offsets; see coarse_tc_plan).  A
-// descriptor always spans 16 row groups (M = 128), but only the first 2Nc/8
-// hold operator rows: the rest of the span may overlap the next buffer, and
-// the accumulator rows it produces (2Nc..127) are never read.
+// Shared-memory plan of one CTA (byte offsets).  An operator descriptor spans
+// 16 row groups (M = 128) but only the first 2Nc/8 hold operator rows: the
+// rest of the span may overlap the next buffer.
 struct TcPlan {
-    int a0, a1;        // operator buffers (a1 == a0: single buffer)
-    int bsm, dsm, bar; // gathered vectors, accumulator staging, mbarriers
-    int bytes;         // dynamic shared memory to request
+    int a0, a1;   // operator buffers (a1 == a0: one buffer)
+    int b0, b1;   // packed-vector buffers
+    int bar;      // mbarriers
+    int bytes;
 };
+
+// x [nrhs][V][nc] FP32 complex -> xp [V][nc/8][2P/8][8][8] bfloat16, row n = r (Re) / P + r (Im)
+__global__ void tc_pack_kernel(int V, int nc, int nrhs, int P, const float2* __restrict__ x, __nv_bfloat16* xp) {
+    const int NG = 2 * P / 8;
+    const size_t per = (size_t)nc * 2 * P;
+    const size_t n = (size_t)V * nc * P;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % nc);
+        const size_t t = i / nc;
+        const int Y = (int)(t % V), r = (int)(t / V);
+        const float2 v = r < nrhs ? x[((size_t)r * V + Y) * nc + k] : make_float2(0.f, 0.f);
+        __nv_bfloat16* o = xp + Y * per;
+        const int re = r, im = P + r;
+        o[((size_t)(k >> 3) * NG + (re >> 3)) * 64 + (re & 7) * 8 + (k & 7)] = __float2bfloat16(v.x);
+        o[((size_t)(k >> 3) * NG + (im >> 3)) * 64 + (im & 7) * 8 + (k & 7)] = __float2bfloat16(v.y);
+    }
+}
 
 template <int NP>   // NP = 2P accumulator columns (16 or 32)
 __global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a, TcPlan pl) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int nc = a.nc, K = 9 * nc, kg = K / 8, pairs = nc / 2;
-    const unsigned a_bytes = (unsigned)(2 * nc) * K * 2;   // operator rows of one site
-    unsigned char* Abuf[2] = {smem_raw + pl.a0, smem_raw + pl.a1};
-    const bool dbl = pl.a1 != pl.a0;
-    __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(smem_raw + pl.bsm);
-    float* Ds = reinterpret_cast<float*>(smem_raw + pl.dsm);   // [128][NP]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + pl.bar);   // [0], [1] operator copies, [2] MMA
-    uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
+    constexpr int P = NP / 2, NG = NP / 8;
+    const int nc = a.nc, K = 9 * nc, kg = K / 8;
+    const unsigned a_bytes = (unsigned)(2 * nc) * K * 2;        // operator rows of one site
+    const unsigned x_site = (unsigned)nc * NP * 2;              // packed vectors of one site
+    unsigned char* Ab[2] = {smem_raw + pl.a0, smem_raw + pl.a1};
+    unsigned char* Bb[2] = {smem_raw + pl.b0, smem_raw + pl.b1};
+    const bool dblA = pl.a1 != pl.a0;
+    uint64_t* barA = reinterpret_cast<uint64_t*>(smem_raw + pl.bar);   // [2]
+    uint64_t* barB = barA + 2;                                           // [2]
+    uint64_t* barM = barA + 4;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(barA + 5);
     int* fail = reinterpret_cast<int*>(slot + 1);
-    int* nbr = fail + 1;   // [9] neighbour sites of the current coarse site
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nq = 2 * nc / 32;   // quarters of the accumulator holding operator rows
 
     if (tid == 0) {
-        mb_init(&bars[0], 1);
-        mb_init(&bars[1], 1);
-        mb_init(&bars[2], 1);
+        for (int i = 0; i < 5; ++i) mb_init(&barA[i], 1);
         mb_fence_init();
         *fail = 0;
     }
@@ -177,113 +203,88 @@ __global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a, TcPl
     tc_after();
     const uint32_t tmem = *slot;
     const uint32_t idesc = idesc_bf16(128, NP);
-    const uint32_t lbo = 128, sbo = (uint32_t)kg * 128;
-    unsigned ph[2] = {0, 0}, ph_m = 0;
-    bool pend[2] = {false, false};   // meaningful in thread 0 only
-    auto issue = [&](int X, int b) {
-        mb_expect_tx(&bars[b], a_bytes);
-        bulk_load(Abuf[b], a.img + (size_t)X * (2 * nc) * K, a_bytes, &bars[b]);
-        pend[b] = true;
+    const uint32_t a_lbo = 128, a_sbo = (uint32_t)kg * 128;   // A: [m group][k group][8][8]
+    const uint32_t b_lbo = NG * 128, b_sbo = 128;             // G: [k group][n group][8][8]
+    unsigned phA[2] = {0, 0}, phB[2] = {0, 0}, phM = 0;
+    bool pendA[2] = {false, false}, pendB[2] = {false, false};   // thread 0 only
+    auto issueA = [&](int X, int s) {
+        mb_expect_tx(&barA[s], a_bytes);
+        bulk_load(Ab[s], a.img + (size_t)X * (2 * nc) * K, a_bytes, &barA[s]);
+        pendA[s] = true;
     };
-    if (tid == 0 && blockIdx.x < a.V) issue(blockIdx.x, 0);
-
+    auto issueB = [&](int X, int s) {
+        mb_expect_tx(&barB[s], 9 * x_site);
+        for (int d = 0; d < 9; ++d)
+            bulk_load(Bb[s] + d * x_site, a.xp + (size_t)tc_nbr(a, X, d) * (x_site / 2), x_site, &barB[s]);
+        pendB[s] = true;
+    };
+    if (tid == 0 && (int)blockIdx.x < a.V) {
+        issueA(blockIdx.x, 0);
+        issueB(blockIdx.x, 0);
+    }
     int it = 0;
     for (int X = blockIdx.x; X < a.V; X += gridDim.x, ++it) {
-        const int sel = dbl ? (it & 1) : 0;
+        const int sB = it & 1, sA = dblA ? (it & 1) : 0;
         const int Xn = X + gridDim.x;
-        if (dbl && tid == 0 && Xn < a.V) issue(Xn, sel ^ 1);   // its buffer was last read by the previous MMA
-        if (tid < 9) nbr[tid] = tc_nbr(a, X, tid);
-        __syncthreads();
-        // gather G: row r = Re x_r, row P + r = Im x_r, column k = d * nc + b, two complex per load
-        const int items = a.P * 9 * pairs;
-        for (int base = tid; base < items; base += kTcThreads * 4) {
-            float4 v[4];
-            int rr[4], kk[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = base + u * kTcThreads;
-                rr[u] = -1;
-                if (idx < items) {
-                    const int r = idx / (9 * pairs), rem = idx - r * 9 * pairs;
-                    const int d = rem / pairs, c2 = rem - d * pairs;
-                    rr[u] = r;
-                    kk[u] = d * nc + 2 * c2;
-                    v[u] = r < a.nrhs ? __ldg(reinterpret_cast<const float4*>(a.x) +
-                                              ((size_t)r * a.V + nbr[d]) * pairs + c2)
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (rr[u] < 0) continue;
-                *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(rr[u], kk[u], kg)) = __floats2bfloat162_rn(v[u].x, v[u].z);
-                *reinterpret_cast<__nv_bfloat162*>(Bs + core_off(a.P + rr[u], kk[u], kg)) =
-                    __floats2bfloat162_rn(v[u].y, v[u].w);
-            }
-        }
-        proxy_fence();
-        __syncthreads();
         if (tid == 0) {
-            if (mb_wait(&bars[sel], ph[sel])) {
-                pend[sel] = false;
-                ph[sel] ^= 1;
+            // the other stage's buffers were last read by the previous site's MMAs, which completed
+            if (Xn < a.V) {
+                issueB(Xn, sB ^ 1);
+                if (dblA) issueA(Xn, sA ^ 1);
+            }
+            if (mb_wait(&barA[sA], phA[sA]) && mb_wait(&barB[sB], phB[sB])) {
+                pendA[sA] = pendB[sB] = false;
+                phA[sA] ^= 1;
+                phB[sB] ^= 1;
                 tc_after();
-                const uint32_t a0 = su32(Abuf[sel]), b0 = su32(Bs);
+                const uint32_t a0 = su32(Ab[sA]), b0 = su32(Bb[sB]);
                 for (int q = 0; q < K / 16; ++q)
-                    mma_bf16(tmem, smem_desc(a0 + q * 256, lbo, sbo), smem_desc(b0 + q * 256, lbo, sbo), idesc,
-                             q > 0 ? 1u : 0u);
-                mma_commit(&bars[2]);
+                    mma_bf16(tmem, smem_desc(a0 + q * 256, a_lbo, a_sbo), smem_desc(b0 + q * 2 * NG * 128, b_lbo, b_sbo),
+                             idesc, q > 0 ? 1u : 0u);
+                mma_commit(barM);
             } else {
                 *fail = 1;
             }
         }
         __syncthreads();
         if (*fail) break;
-        if (!mb_wait(&bars[2], ph_m)) atomicExch(fail, 2);
-        ph_m ^= 1;
+        if (!mb_wait(barM, phM)) atomicExch(fail, 2);
+        phM ^= 1;
         __syncthreads();
         if (*fail) break;
         tc_after();
-        // the operator buffer is free again: fetch the next site's rows during the epilogue
-        if (!dbl && tid == 0 && Xn < a.V) issue(Xn, 0);
-        if (warp < 4) {
+        if (!dblA && tid == 0 && Xn < a.V) issueA(Xn, 0);   // the single operator buffer is free again
+        if (warp < nq) {
+            uint32_t v[NP];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-            const int row = warp * 32 + lane;
-            if (NP == 32) {
-                uint32_t r[32];
-                tm_ld32(taddr, r);
+            if constexpr (NP == 32) tm_ld32(taddr, v);
+            else tm_ld16(taddr, v);
+            const int aa = warp * 16 + (lane & 15);
+            const bool im = lane >= 16;
 #pragma unroll
-                for (int c = 0; c < 32; ++c) Ds[row * NP + c] = __uint_as_float(r[c]);
-            } else {
-                uint32_t r[16];
-                tm_ld16(taddr, r);
-#pragma unroll
-                for (int c = 0; c < 16; ++c) Ds[row * NP + c] = __uint_as_float(r[c]);
+            for (int r = 0; r < P; ++r) {
+                // Re row: y_re = ReB.Re x - ImB.Im x; Im row: y_im = ImB.Re x + ReB.Im x
+                const float pv = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[P + r]), 16);
+                float val = im ? __uint_as_float(v[r]) + pv : __uint_as_float(v[r]) - pv;
+                if (r < a.nrhs) {
+                    const size_t o = ((size_t)r * a.V + X) * nc + aa;
+                    float* yo = reinterpret_cast<float*>(a.y + o) + (im ? 1 : 0);
+                    if (a.b) val = reinterpret_cast<const float*>(a.b + o)[im ? 1 : 0] - val;
+                    *yo = val;
+                }
             }
         }
         tc_before();
         __syncthreads();
-        for (int idx = tid; idx < nc * a.nrhs; idx += kTcThreads) {
-            const int r = idx / nc, aa = idx - r * nc;
-            float yr = Ds[aa * NP + r] - Ds[(nc + aa) * NP + a.P + r];
-            float yi = Ds[(nc + aa) * NP + r] + Ds[aa * NP + a.P + r];
-            const size_t o = ((size_t)r * a.V + X) * nc + aa;
-            if (a.b) {
-                const float2 bv = a.b[o];
-                yr = bv.x - yr;
-                yi = bv.y - yi;
-            }
-            a.y[o] = make_float2(yr, yi);
-        }
-        __syncthreads();
+        tc_after();
     }
-    if (*fail) {
-        if (tid == 0) {
-            // drain our own bulk copies before the shared memory goes away
-            for (int b = 0; b < 2; ++b)
-                if (pend[b]) mb_wait(&bars[b], ph[b]);
-            atomicExch(a.err, 1);
+    if (*fail && tid == 0) {
+        // drain our own bulk copies before the shared memory goes away
+        for (int s2 = 0; s2 < 2; ++s2) {
+            if (pendA[s2]) mb_wait(&barA[s2], phA[s2]);
+            if (pendB[s2]) mb_wait(&barB[s2], phB[s2]);
         }
+        atomicExch(a.err, 1);
     }
     tc_before();
     __syncthreads();
@@ -291,7 +292,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a, TcPl
     if (warp == 0) tm_dealloc(tmem, 32);
 }
 
-// operator image: row m < nc: Re B[X][m][d][col], m >= nc: Im B[X][m - nc][d][col], k = d * nc + col
+// operator image: row m = 32 w + l holds Re (l < 16) or Im (l >= 16) of
+// B[X][16 w + l % 16][d][col], column k = d * nc + col
 __global__ void tc_image_kernel(int V, int nc, const float2* __restrict__ B, __nv_bfloat16* img) {
     const int K = 9 * nc, kg = K / 8;
     const size_t per = (size_t)2 * nc * K;
@@ -300,9 +302,9 @@ __global__ void tc_image_kernel(int V, int nc, const float2* __restrict__ B, __n
         const size_t X = i / per;
         const int e = (int)(i - X * per);
         const int m = e / K, k = e - m * K;
-        const int row = m < nc ? m : m - nc;
+        const int row = (m >> 5) * 16 + (m & 15);
         const float2 v = B[((size_t)X * nc + row) * K + k];   // [X][row][d][col] = [X][row][k]
-        img[X * per + core_off(m, k, kg)] = __float2bfloat16(m < nc ? v.x : v.y);
+        img[X * per + core_off(m, k, kg)] = __float2bfloat16((m & 16) ? v.y : v.x);
     }
 }
 
@@ -328,8 +330,10 @@ cudaError_t launch_coarse_tc_image(int V, int nc, const void* B32, void* img, cu
     return cudaGetLastError();
 }
 
+size_t coarse_tc_pack_bytes(int V, int nc) { return (size_t)V * nc * 32 * 2; }
+
 cudaError_t launch_coarse_apply_tc(const GeomH& g, int nc, const void* img, const void* x, void* y, const void* b,
-                                   int nrhs, int* err, cudaStream_t st) {
+                                   int nrhs, void* xpack, int* err, cudaStream_t st) {
     if (!coarse_tc_supported(nc) || nrhs < 1 || nrhs > 16) return cudaErrorInvalidValue;
     TcArgs a;
     for (int i = 0; i < 4; ++i) a.L[i] = g.L[i];
@@ -338,29 +342,30 @@ cudaError_t launch_coarse_apply_tc(const GeomH& g, int nc, const void* img, cons
     a.nrhs = nrhs;
     a.P = nrhs <= 8 ? 8 : 16;
     a.img = (const __nv_bfloat16*)img;
-    a.x = (const float2*)x;
+    a.xp = (const __nv_bfloat16*)xpack;
     a.y = (float2*)y;
     a.b = (const float2*)b;
     a.err = err;
     const int K = 9 * nc, kg = K / 8, NP = 2 * a.P;
-    const int a_data = 2 * nc * K * 2, a_span = 16 * kg * 128;
-    const int b_bytes = (NP / 8) * kg * 128, d_bytes = 128 * NP * 4, tail = 3 * 8 + 4 + 4 + 9 * 4;
+    const int a_data = 2 * nc * K * 2, a_span = 16 * kg * 128, b_bytes = K * NP * 2;
     const int kMax = 227 * 1024;
     auto plan = [&](bool dbl) {
         TcPlan p;
         p.a0 = 0;
         p.a1 = dbl ? a_data : 0;
-        p.bsm = (dbl ? 2 * a_data : a_data);
-        p.dsm = p.bsm + b_bytes;
-        p.bar = p.dsm + d_bytes;
-        const int end = p.bar + tail;
-        const int span = p.a1 + a_span;   // the last operator descriptor's reach
+        p.b0 = p.a1 + a_data;
+        p.b1 = p.b0 + b_bytes;
+        p.bar = p.b1 + b_bytes;
+        const int end = p.bar + 5 * 8 + 8;
+        const int span = p.a1 + a_span;   // reach of the last operator descriptor
         p.bytes = ((end > span ? end : span) + 127) / 128 * 128;
         return p;
     };
     TcPlan pl = plan(true);
     if (pl.bytes > kMax) pl = plan(false);
     if (pl.bytes > kMax) return cudaErrorInvalidValue;
+    (note_launch(), tc_pack_kernel<<<tc_sms() * 8, 256, 0, st>>>(g.V, nc, nrhs, a.P, (const float2*)x,
+                                                                 (__nv_bfloat16*)xpack));
     const void* fn = NP == 32 ? (const void*)coarse_tc_kernel<32> : (const void*)coarse_tc_kernel<16>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.bytes);
     if (e != cudaSuccess) return e;

@@ -111,13 +111,15 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
 // multi-RHS coarse stencil on the tensor cores (coarse_tc.cu): bfloat16 operands, FP32
 // accumulation; needs Nc % 16 == 0 and Nc <= 64.  The operator is first copied into the
 // tensor-core operand image ([V][2Nc][9Nc] bfloat16 in 8 x 8 core-matrix order) from its
-// FP32 internal form; x, y, b are FP32 [nrhs][V][Nc] complex with 1 <= nrhs <= 16; *err
-// is set to 1 if a wait timed out
+// FP32 internal form; x, y, b are FP32 [nrhs][V][Nc] complex with 1 <= nrhs <= 16; xpack
+// is scratch of coarse_tc_pack_bytes(V, Nc) (the packed bfloat16 vectors); *err is set
+// to 1 if a wait timed out
 bool coarse_tc_supported(int nc);
 size_t coarse_tc_image_bytes(int V, int nc);
+size_t coarse_tc_pack_bytes(int V, int nc);
 cudaError_t launch_coarse_tc_image(int V, int nc, const void* B32, void* img, cudaStream_t s);
 cudaError_t launch_coarse_apply_tc(const GeomH& g, int nc, const void* img, const void* x, void* y, const void* b,
-                                   int nrhs, int* err, cudaStream_t s);
+                                   int nrhs, void* xpack, int* err, cudaStream_t s);
 // n complex FP32 -> bfloat16 pairs (coarse operator in BF16 storage)
 cudaError_t launch_complex_to_bf16(const void* in, void* out, size_t n, cudaStream_t s);
 // coarse op layout change: internal [Vc][Nc][9][Nc] -> canonical [Vc][9][Nc][Nc] doubles
