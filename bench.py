@@ -321,9 +321,11 @@ def run_dirac(args):
     hbm, kind = _peaks()
     stream = torch.cuda.current_stream()
     per = {}
-    bytes_site = {"f64": 1536, "f32": 672, "f16": 344}
+    # f64x: float input, FP64 output, links / clover as float hi/lo pairs (full 3x3: 4 x 144 B)
+    bytes_site = {"f64": 1536, "f32": 672, "f16": 344, "f64x": 96 + 192 + 4 * 144 + 576}
     with ClockSampler() as clk:
-        for name, prec in (("f64", capi.AMG_F64), ("f32", capi.AMG_F32), ("f16", capi.AMG_F16)):
+        for name, prec in (("f64", capi.AMG_F64), ("f32", capi.AMG_F32), ("f16", capi.AMG_F16),
+                           ("f64x", capi.AMG_F64X)):
             x = torch.from_numpy(psi).to(torch.float64 if name == "f64" else torch.float32).cuda()
             capi.amg_dirac_time(d, x, 1, prec, args.warmup, stream=stream)          # warm-up launches
             l0 = capi.amg_launch_count()

@@ -180,8 +180,9 @@ amg_status amg_apply_D_noalloc(amg_dirac* d, const void* in, void* out, int nrhs
  * once, then applies D to it `reps` times on stream s, bracketed by CUDA
  * events, and writes the mean milliseconds per application to *ms_per_apply.
  * The result field is discarded.  Synchronises s.  prec AMG_F64 / AMG_F32 /
- * AMG_F16.  No counterpart in the paper: the kernel-only time that the HBM
- * roofline of the stencil is computed from. */
+ * AMG_F16, or AMG_F64X (float input, the FP64-accurate double-float kernel
+ * of the outer solver's Arnoldi product).  No counterpart in the paper: the
+ * kernel-only time that the roofline of the stencil is computed from. */
 amg_status amg_dirac_time(amg_dirac* d, const void* in, int nrhs, amg_prec prec, int reps, amg_stream s,
                           float* ms_per_apply);
 

@@ -1431,21 +1431,23 @@ amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_pr
 amg_status amg_dirac_time(amg_dirac* d, const void* in, int nrhs, amg_prec prec, int reps, amg_stream s,
                           float* ms_per_apply) {
     if (!d || !in || !ms_per_apply || nrhs < 1 || reps < 1) return fail(AMG_EINVAL, "bad argument");
-    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32 or AMG_F16");
+    if (prec < 0 || prec > 4 || prec == AMG_BF16) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32, AMG_F16 or AMG_F64X");
     const GeomH& g = d->gauge->lat->g;
     cudaStream_t st = (cudaStream_t)s;
-    size_t fb = fine_spinor_bytes(prec, g.V) * nrhs;
-    CK(d->in.ensure(fb));
-    CK(d->out.ensure(fb));
-    CK(launch_pack_spinor(prec, g, in, d->in.p, nrhs, st));
+    const bool mixed = prec == AMG_F64X;
+    const int pin = mixed ? 1 : prec, pout = mixed ? 0 : prec;
+    CK(d->in.ensure(fine_spinor_bytes(pin, g.V) * nrhs));
+    CK(d->out.ensure(fine_spinor_bytes(pout, g.V) * nrhs));
+    CK(launch_pack_spinor(pin, g, in, d->in.p, nrhs, st));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     amg_status rc = AMG_OK;
     cudaError_t err = cudaEventRecord(e0, st);
     for (int i = 0; err == cudaSuccess && i < reps; ++i)
-        err = launch_dirac(prec, g, nullptr, d->gauge->U[prec].p, d->C[prec].p, d->in.p, d->out.p, nullptr, d->kappa,
-                           nrhs, st);
+        err = mixed ? launch_dirac_mixed(g, d->gauge->U[3].p, d->C[3].p, d->in.p, d->out.p, d->kappa, nrhs, st)
+                    : launch_dirac(prec, g, nullptr, d->gauge->U[prec].p, d->C[prec].p, d->in.p, d->out.p, nullptr,
+                                   d->kappa, nrhs, st);
     if (err == cudaSuccess) err = cudaEventRecord(e1, st);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 0;

@@ -303,8 +303,10 @@ __global__ void clover_expand_kernel(Geom g, const void* C64, double* out) {
 }
 
 // ------------------------------------------------------------ Wilson-clover stencil
+// FP32 / FP16: three CTAs per SM (the stencil streams from HBM and needs the
+// warps); FP64: two (register cap 128)
 template <class P, bool SAP, bool RESID>
-__global__ void __launch_bounds__(kThreads) dirac_kernel(Geom g, Blocking bk, const void* __restrict__ U,
+__global__ void __launch_bounds__(kThreads, P::id == 0 ? 2 : 3) dirac_kernel(Geom g, Blocking bk, const void* __restrict__ U,
                                                          const void* __restrict__ C, const void* in, void* out,
                                                          const void* b, typename P::T kappa) {
     using T = typename P::T;
@@ -346,10 +348,86 @@ __global__ void __launch_bounds__(kThreads) dirac_kernel(Geom g, Blocking bk, co
 }
 
 // ------------------------------------------------------------ mixed stencil
-// out (FP64) = D in for an FP32 input whose values are exact: links and
-// clover are FP64 values held as float hi/lo pairs and all arithmetic is
-// double-float, so the result carries about 48 significant bits while the
-// work runs on the FP32 pipe.
+// out (FP64) = D in for an FP32 input whose values are exact; links and
+// clover are FP64 values held as float hi/lo pairs.  Every product of a
+// float pair u = u_hi + u_lo with a float pair h = h_hi + h_lo is split
+// into its exact leading part p = fl(u_hi h_hi) and a small correction
+// (the FMA residual u_hi h_hi - p plus u_lo h_hi + u_hi h_lo); leading parts
+// are summed with Knuth's two-sum (the rounding error of each addition is
+// kept), corrections are summed in plain FP32.  The result carries about 46
+// significant bits at roughly a third of the cost of full double-float
+// arithmetic, and the work stays on the FP32 pipe.
+struct fa {   // unevaluated sum hi + lo
+    float hi, lo;
+};
+DEV fa fa_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+DEV void fa_add(fa& acc, fa v) {
+    const fa t = fa_two_sum(acc.hi, v.hi);
+    acc.hi = t.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t.lo, v.lo));
+}
+DEV fa fa_neg(fa v) { return {-v.hi, -v.lo}; }
+// acc += u * h
+DEV void fa_mac(fa& acc, dfloat u, fa h) {
+    const float p = __fmul_rn(u.hi, h.hi);
+    float e = fmaf(u.hi, h.hi, -p);
+    e = fmaf(u.lo, h.hi, e);
+    e = fmaf(u.hi, h.lo, e);
+    const fa t = fa_two_sum(acc.hi, p);
+    acc.hi = t.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t.lo, e));
+}
+// u * h as a pair (leading product and its correction)
+DEV fa fa_mul(dfloat u, fa h) {
+    const float p = __fmul_rn(u.hi, h.hi);
+    float e = fmaf(u.hi, h.hi, -p);
+    e = fmaf(u.lo, h.hi, e);
+    e = fmaf(u.hi, h.lo, e);
+    return {p, e};
+}
+struct cfa {
+    fa re, im;
+};
+DEV cfa cfa_exact(cx<float> v) { return {{v.re, 0.f}, {v.im, 0.f}}; }
+DEV void cfa_add(cfa& a, cfa b) {
+    fa_add(a.re, b.re);
+    fa_add(a.im, b.im);
+}
+// a += u h (conj(u) h when CONJ)
+template <bool CONJ> DEV void cfa_mac(cfa& a, cx<dfloat> u, cfa h) {
+    const dfloat ui = CONJ ? dfloat(-u.im.hi, -u.im.lo) : u.im;
+    fa_mac(a.re, u.re, h.re);
+    fa_mac(a.re, dfloat(-ui.hi, -ui.lo), h.im);
+    fa_mac(a.im, u.re, h.im);
+    fa_mac(a.im, ui, h.re);
+}
+// exact multiples: i v, -v
+DEV cfa cfa_i(cfa v) { return {fa_neg(v.im), v.re}; }
+DEV cfa cfa_neg(cfa v) { return {fa_neg(v.re), fa_neg(v.im)}; }
+// y = e_mu v and y = e_mu^dag v for a spin pair (exact: signs and swaps)
+DEV void cfa_e(int mu, cfa v0, cfa v1, cfa& y0, cfa& y1) {
+    switch (mu) {
+        case 0: y0 = cfa_i(v1); y1 = cfa_i(v0); break;
+        case 1: y0 = v1; y1 = cfa_neg(v0); break;
+        case 2: y0 = cfa_i(v0); y1 = cfa_neg(cfa_i(v1)); break;
+        default: y0 = v0; y1 = v1; break;
+    }
+}
+DEV void cfa_edag(int mu, cfa v0, cfa v1, cfa& y0, cfa& y1) {
+    switch (mu) {
+        case 0: y0 = cfa_neg(cfa_i(v1)); y1 = cfa_neg(cfa_i(v0)); break;
+        case 1: y0 = cfa_neg(v1); y1 = v0; break;
+        case 2: y0 = cfa_neg(cfa_i(v0)); y1 = cfa_i(v1); break;
+        default: y0 = v0; y1 = v1; break;
+    }
+}
+// sum of two exact-float complex values as an exact pair per component
+DEV cfa cfa_sum(cfa a, cfa b) { return {fa_two_sum(a.re.hi, b.re.hi), fa_two_sum(a.im.hi, b.im.hi)}; }
+
 __global__ void __launch_bounds__(kThreads, 2) dirac_mixed_kernel(Geom g, const void* __restrict__ U,
                                                                const void* __restrict__ C, const void* in,
                                                                void* out, dfloat kappa) {
@@ -360,31 +438,88 @@ __global__ void __launch_bounds__(kThreads, 2) dirac_mixed_kernel(Geom g, const 
         int c[4];
         site_coords(g, s, c);
         cx<float> pf[12];
-        cx<dfloat> psi[12], acc[12];
+        cfa acc[12];
         SpinorIO<P32>::load(src, g.V, s, pf);
+        // clover: two packed Hermitian 6x6 blocks
 #pragma unroll
-        for (int k = 0; k < 12; ++k) psi[k] = {dfloat(pf[k].re), dfloat(pf[k].im)};
-        clover_apply<PDD>(C, g.V, s, psi, acc);
+        for (int b = 0; b < 2; ++b) {
+            dfloat pr[36];
+            CloverIO<PDD>::load_block(C, g.V, s, b, pr);
+            cfa* o = acc + 6 * b;
+            const cx<float>* z = pf + 6 * b;
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            float ph;
-            cx<dfloat> u[3][3];
-            int n = neighbour(g, s, c, mu, +1, ph);
-            SpinorIO<P32>::load(src, g.V, n, pf);
+            for (int i = 0; i < 6; ++i) o[i] = {fa_mul(pr[i], fa{z[i].re, 0.f}), fa_mul(pr[i], fa{z[i].im, 0.f})};
 #pragma unroll
-            for (int k = 0; k < 12; ++k) psi[k] = {dfloat(pf[k].re), dfloat(pf[k].im)};
-            GaugeIO<PDD>::load(U, g.V, mu, s, u);
-            hop_accum<dfloat>(acc, psi, u, mu, +1, dfloat(ph) * (-kappa));
-            n = neighbour(g, s, c, mu, -1, ph);
-            SpinorIO<P32>::load(src, g.V, n, pf);
+            for (int i = 1; i < 6; ++i)
 #pragma unroll
-            for (int k = 0; k < 12; ++k) psi[k] = {dfloat(pf[k].re), dfloat(pf[k].im)};
-            GaugeIO<PDD>::load(U, g.V, mu, n, u);
-            hop_accum<dfloat>(acc, psi, u, mu, -1, dfloat(ph) * (-kappa));
+                for (int j = 0; j < i; ++j) {
+                    const int q = 3 + i * (i - 1) / 2 + j;
+                    const cx<dfloat> l = {pr[2 * q], pr[2 * q + 1]};
+                    cfa_mac<false>(o[i], l, cfa_exact(z[j]));
+                    cfa_mac<true>(o[j], l, cfa_exact(z[i]));
+                }
+        }
+        // hops: h = (exact) projected half spinor, w = W h, out += -kappa * phase * (w, -/+ e^dag w);
+        // the loop over the eight hops stays rolled: unrolled, the kernel body
+        // does not fit the instruction cache
+#pragma unroll 1
+        for (int hop = 0; hop < 8; ++hop) {
+            const int mu = hop >> 1, dir = (hop & 1) ? -1 : 1;
+            {
+                float ph;
+                const int n = neighbour(g, s, c, mu, dir, ph);
+                SpinorIO<P32>::load(src, g.V, n, pf);
+                cx<dfloat> u[3][3];
+                GaugeIO<PDD>::load(U, g.V, mu, dir > 0 ? s : n, u);
+                const dfloat kc = dfloat(-ph * kappa.hi, -ph * kappa.lo);   // exact: ph = +-1
+                cfa h[2][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cfa e0, e1;
+                    cfa_e(mu, cfa_exact(pf[6 + a]), cfa_exact(pf[9 + a]), e0, e1);
+                    if (dir < 0) {
+                        h[0][a] = cfa_sum(cfa_exact(pf[a]), e0);
+                        h[1][a] = cfa_sum(cfa_exact(pf[3 + a]), e1);
+                    } else {
+                        h[0][a] = cfa_sum(cfa_exact(pf[a]), cfa_neg(e0));
+                        h[1][a] = cfa_sum(cfa_exact(pf[3 + a]), cfa_neg(e1));
+                    }
+                    // scale by -kappa * phase once, before the link
+#pragma unroll
+                    for (int sp = 0; sp < 2; ++sp)
+                        h[sp][a] = {fa_mul(kc, h[sp][a].re), fa_mul(kc, h[sp][a].im)};
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cfa w0 = {{0.f, 0.f}, {0.f, 0.f}}, w1 = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        if (dir > 0) {
+                            cfa_mac<false>(w0, u[a][b], h[0][b]);
+                            cfa_mac<false>(w1, u[a][b], h[1][b]);
+                        } else {
+                            cfa_mac<true>(w0, u[b][a], h[0][b]);
+                            cfa_mac<true>(w1, u[b][a], h[1][b]);
+                        }
+                    }
+                    cfa l0, l1;
+                    cfa_edag(mu, w0, w1, l0, l1);
+                    cfa_add(acc[a], w0);
+                    cfa_add(acc[3 + a], w1);
+                    if (dir > 0) {
+                        cfa_add(acc[6 + a], cfa_neg(l0));
+                        cfa_add(acc[9 + a], cfa_neg(l1));
+                    } else {
+                        cfa_add(acc[6 + a], l0);
+                        cfa_add(acc[9 + a], l1);
+                    }
+                }
+            }
         }
         cx<double> o[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) o[k] = {to_double(acc[k].re), to_double(acc[k].im)};
+        for (int k = 0; k < 12; ++k)
+            o[k] = {(double)acc[k].re.hi + (double)acc[k].re.lo, (double)acc[k].im.hi + (double)acc[k].im.lo};
         SpinorIO<P64>::store(dst, g.V, s, o);
     }
 }
