@@ -106,14 +106,17 @@ def dist_info():
     return rank, world, local
 
 
-def make_params(capi, prec_smoother):
+def make_params(capi, prec_smoother, coarse="f32"):
     p = capi.amg_params_default()
     p.nlevels = 2
     for mu in range(4):
         p.block[0][mu] = WORKLOAD["block"][mu]
     p.nvec[0] = WORKLOAD["nvec"]
     p.prec_smoother = prec_smoother
-    p.prec_coarsest = capi.AMG_F32 if prec_smoother != capi.AMG_F64 else capi.AMG_F64
+    if prec_smoother == capi.AMG_F64:
+        p.prec_coarsest = capi.AMG_F64
+    else:
+        p.prec_coarsest = capi.AMG_BF16 if coarse == "bf16" else capi.AMG_F32
     return p
 
 
@@ -587,6 +590,8 @@ def main():
     ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--coarse-prec", default="f32", choices=["f32", "bf16"],
+                    help="coarsest stencil storage of the solve16 workload (bf16: bfloat16 entries, FP32 arithmetic)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -629,7 +634,7 @@ def main():
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = capi.amg_setup(d, make_params(capi, prec), [v0])
+    h = capi.amg_setup(d, make_params(capi, prec, args.coarse_prec), [v0])
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
 
@@ -694,7 +699,7 @@ def main():
     # sites are active per launch.  12.8 flop/byte puts it on the ALU side of
     # the ridge, so it is reported against the FP32 FMA peak:
     # 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (nominal).
-    p = make_params(capi, prec)
+    p = make_params(capi, prec, args.coarse_prec)
     iters = np.mean([i["iters"] for i in infos])
     smooth_ms = np.mean([i["ms_smoother"] for i in infos])
     launches = 2 * p.sap_iters * iters
@@ -713,7 +718,7 @@ def main():
         "config": {"workload": "16^3x32 Wilson-clover (exp(0.6iH) links, seed 2, kappa 0.130, csw 1.0), "
                                "2-level AMG 4^4 blocks, 24 test vectors, SAP(4) x MR(6), BiCGStab(2) coarse to 1e-2, "
                                "FGMRES(16) FP64 outer, 1 Gaussian RHS per step",
-                   "smoother_prec": args.prec, "setup_ms": setup_ms, "l2": "working set > L2 (no flush)",
+                   "smoother_prec": args.prec, "coarse_prec": args.coarse_prec, "setup_ms": setup_ms, "l2": "working set > L2 (no flush)",
                    "outer_iters": float(iters), "converged": ok,
                    "phase_ms": {k: float(np.mean([i[k] for i in infos])) for k in
                                 ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other")},

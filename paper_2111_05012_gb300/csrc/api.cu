@@ -673,20 +673,28 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             for (int q = 0; q < nb; ++q)
                 if (!st[q].stop) relax = relax && relaxed_product(std::abs(st[q].g[j]) / st[q].bnorm, tol);
             TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, nb, s, relax));
-            // classical Gram-Schmidt, twice, every right-hand side in one synchronisation per pass
-            for (int pass = 0; pass < 2; ++pass) {
-                std::vector<const void*> vl(j + 1);
-                for (int q = 0; q < nb; ++q) {
-                    for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
-                    CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n,
-                                        red.dpart.as<double2>() + (size_t)q * 20 * red.grid, s));
-                }
-                CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double2) * 20 * red.grid * nb,
-                                   cudaMemcpyDeviceToHost, s));
+            // classical Gram-Schmidt, twice, every right-hand side in one synchronisation per
+            // reduction: dots; (update, dots of the updated w) in one pass; (update, |w|^2) in one pass
+            std::vector<const void*> vl(j + 1);
+            double2* const dp = red.dpart.as<double2>();
+            auto region = [&](int q) { return dp + (size_t)q * 20 * red.grid; };
+            auto fetch = [&](int k) -> amg_status {   // k quantities per right-hand side
+                const size_t cnt = nb == 1 ? (size_t)k * red.grid : (size_t)20 * red.grid * nb;
+                CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double2) * cnt, cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
-                if (pass == 0) TRY(coarse_status(h));
+                return AMG_OK;
+            };
+            for (int q = 0; q < nb; ++q) {
+                for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
+                CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n, region(q), s));
+            }
+            TRY(fetch(j + 1));
+            TRY(coarse_status(h));
+            std::vector<double> hn2(nb, 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
                 for (int q = 0; q < nb; ++q) {
                     RhsState& r = st[q];
+                    if (r.stop) continue;
                     std::vector<double2> nc(j + 1);
                     for (int i = 0; i <= j; ++i) {
                         double re = 0, im = 0;
@@ -695,15 +703,19 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
                             re += hp[t].x;
                             im += hp[t].y;
                         }
-                        if (!r.stop) r.H[i][j] += cplx(re, im);
-                        nc[i] = r.stop ? make_double2(0, 0) : make_double2(-re, -im);
+                        r.H[i][j] += cplx(re, im);
+                        nc[i] = make_double2(-re, -im);
                     }
                     for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
-                    if (!r.stop) CK(launch_multi_axpy(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, s));
+                    CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, pass == 0, region(q),
+                                                s));
                 }
+                TRY(fetch(pass == 0 ? j + 1 : 1));
             }
-            std::vector<double> hn2;
-            TRY(batch_norms(h, nb, h->ow, hn2, s));
+            for (int q = 0; q < nb; ++q) {
+                const double* hp = (const double*)(red.hpart + (size_t)q * 20 * red.grid);
+                for (int t = 0; t < red.grid; ++t) hn2[q] += hp[t];
+            }
             bool all_stopped = true;
             for (int q = 0; q < nb; ++q) {
                 RhsState& r = st[q];
@@ -1208,21 +1220,22 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
                 TRY(ragged_step(p.h, j, p.st));
             }
             if (!active) break;
+            // classical Gram-Schmidt, twice: dots; (update, dots of the updated w); (update, |w|^2)
             std::vector<cplx> c(j + 1);
-            for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+            for (auto& p : P) {
+                if (p.r.done || p.r.stop) continue;
+                std::vector<const void*> vl(j + 1);
+                for (int i = 0; i <= j; ++i) vl[i] = p.h->oV[i]->p;
+                CK(launch_multi_dot(0, j + 1, vl.data(), p.h->ow.p, fine_n(p.h), p.h->red.dpart.as<double2>(), p.st));
+                CK(cudaMemcpyAsync(p.h->red.hpart, p.h->red.dpart.p, sizeof(double2) * p.h->red.grid * (j + 1),
+                                   cudaMemcpyDeviceToHost, p.st));
+            }
+            TRY(sync_all());
+            for (auto& p : P)
+                if (!(p.r.done || p.r.stop)) TRY(coarse_status(p.h));
+            for (int pass = 0; pass < 2; ++pass) {
                 for (auto& p : P) {
                     if (p.r.done || p.r.stop) continue;
-                    std::vector<const void*> vl(j + 1);
-                    for (int i = 0; i <= j; ++i) vl[i] = p.h->oV[i]->p;
-                    CK(launch_multi_dot(0, j + 1, vl.data(), p.h->ow.p, fine_n(p.h), p.h->red.dpart.as<double2>(),
-                                        p.st));
-                    CK(cudaMemcpyAsync(p.h->red.hpart, p.h->red.dpart.p, sizeof(double2) * p.h->red.grid * (j + 1),
-                                       cudaMemcpyDeviceToHost, p.st));
-                }
-                TRY(sync_all());
-                for (auto& p : P) {
-                    if (p.r.done || p.r.stop) continue;
-                    if (pass == 0) TRY(coarse_status(p.h));
                     ragged_sum(p, j + 1, c.data());
                     std::vector<double2> nc(j + 1);
                     std::vector<const void*> vl(j + 1);
@@ -1231,12 +1244,14 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
                         nc[i] = make_double2(-c[i].real(), -c[i].imag());
                         vl[i] = p.h->oV[i]->p;
                     }
-                    CK(launch_multi_axpy(0, j + 1, nc.data(), vl.data(), p.h->ow.p, fine_n(p.h), p.st));
+                    CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), p.h->ow.p, fine_n(p.h), pass == 0,
+                                                p.h->red.dpart.as<double2>(), p.st));
+                    CK(cudaMemcpyAsync(p.h->red.hpart, p.h->red.dpart.p,
+                                       sizeof(double2) * p.h->red.grid * (pass == 0 ? j + 1 : 1),
+                                       cudaMemcpyDeviceToHost, p.st));
                 }
+                TRY(sync_all());
             }
-            for (auto& p : P)
-                if (!(p.r.done || p.r.stop)) TRY(ragged_norm_launch(p, p.h->ow.p));
-            TRY(sync_all());
             for (auto& p : P) {
                 RhsState& r = p.r;
                 if (r.done || r.stop) continue;

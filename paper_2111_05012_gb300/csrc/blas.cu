@@ -20,7 +20,7 @@ int sm_count() {
     return sms;
 }
 
-int blas_grid_size() { return 2 * sm_count(); }
+int blas_grid_size() { return 8 * sm_count(); }
 
 template <typename V> struct VT;
 template <> struct VT<double2> { using T = double; };
@@ -28,6 +28,9 @@ template <> struct VT<float2> { using T = float; };
 
 struct PtrList {
     const void* p[kMaxDots];
+};
+struct CoefList {
+    double2 c[kMaxDots];
 };
 
 // K dots <a_j, b>, K a compile-time constant so that only K accumulation
@@ -72,6 +75,74 @@ void multi_dot_launch(int k, const PtrList& pl, const V* b, size_t n, double2* p
     (note_launch(), multi_dot_kernel<V, K><<<blas_grid_size(), kBT, 0, st>>>(pl, b, n, partials));
 }
 
+// y += sum_{j<K} c_j x_j, then partial dots <x_j, y_new> (DOT) or partial |y_new|^2:
+// one pass over the vectors for the update of a Gram-Schmidt pass and the
+// reduction of the next one
+template <typename V, int K, bool DOT>
+__global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, double2* partials) {
+    using T = typename VT<V>::T;
+    constexpr int NA = DOT ? 2 * K : 1;
+    __shared__ double red[NA * 32];
+    double acc[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) acc[j] = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        V xs[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) xs[j] = ((const V*)x.p[j])[i];
+        V o = y[i];
+        T re = o.x, im = o.y;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const T cr = (T)c.c[j].x, ci = (T)c.c[j].y;
+            re += cr * xs[j].x - ci * xs[j].y;
+            im += cr * xs[j].y + ci * xs[j].x;
+        }
+        o.x = re;
+        o.y = im;
+        y[i] = o;
+        if constexpr (DOT) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                acc[2 * j] += (double)xs[j].x * (double)re + (double)xs[j].y * (double)im;
+                acc[2 * j + 1] += (double)xs[j].x * (double)im - (double)xs[j].y * (double)re;
+            }
+        } else {
+            acc[0] += (double)re * (double)re + (double)im * (double)im;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        double v = warp_sum(acc[j]);
+        if (lane == 0) red[j * 32 + warp] = v;
+    }
+    __syncthreads();
+    if (DOT) {
+        for (int j = threadIdx.x; j < K; j += blockDim.x) {
+            double re = 0, im = 0;
+            for (int w = 0; w < nw; ++w) {
+                re += red[(2 * j) * 32 + w];
+                im += red[(2 * j + 1) * 32 + w];
+            }
+            partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(re, im);
+        }
+    } else if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        reinterpret_cast<double*>(partials)[blockIdx.x] = t;
+    }
+}
+
+template <typename V, int K, bool DOT>
+void multi_axpy_reduce_launch(int k, const CoefList& cl, const PtrList& pl, V* y, size_t n, double2* partials,
+                              cudaStream_t st) {
+    if constexpr (K > 1) {
+        if (k < K) return multi_axpy_reduce_launch<V, K - 1, DOT>(k, cl, pl, y, n, partials, st);
+    }
+    (note_launch(), multi_axpy_reduce_kernel<V, K, DOT><<<blas_grid_size(), kBT, 0, st>>>(cl, pl, y, n, partials));
+}
+
 template <typename V>
 __global__ void norm2_kernel(const V* __restrict__ a, size_t n, double* partials) {
     __shared__ double red[32];
@@ -103,10 +174,6 @@ __global__ void axpby_kernel(double2 al, const V* __restrict__ x, double2 be, V*
         y[i] = o;
     }
 }
-
-struct CoefList {
-    double2 c[kMaxDots];
-};
 
 template <typename V>
 __global__ void multi_axpy_kernel(int k, CoefList c, PtrList x, V* y, size_t n) {
@@ -161,5 +228,24 @@ cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* con
     }
     if (prec == 0) (note_launch(), multi_axpy_kernel<double2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (double2*)y, n));
     else (note_launch(), multi_axpy_kernel<float2><<<blas_grid(), kBT, 0, st>>>(k, cl, pl, (float2*)y, n));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
+                                     bool dots, double2* partials, cudaStream_t st) {
+    if (k < 1 || k > kMaxDots) return cudaErrorInvalidValue;
+    CoefList cl;
+    PtrList pl;
+    for (int j = 0; j < k; ++j) {
+        cl.c[j] = c[j];
+        pl.p[j] = x[j];
+    }
+    if (prec == 0) {
+        if (dots) multi_axpy_reduce_launch<double2, kMaxDots, true>(k, cl, pl, (double2*)y, n, partials, st);
+        else multi_axpy_reduce_launch<double2, kMaxDots, false>(k, cl, pl, (double2*)y, n, partials, st);
+    } else {
+        if (dots) multi_axpy_reduce_launch<float2, kMaxDots, true>(k, cl, pl, (float2*)y, n, partials, st);
+        else multi_axpy_reduce_launch<float2, kMaxDots, false>(k, cl, pl, (float2*)y, n, partials, st);
+    }
     return cudaGetLastError();
 }

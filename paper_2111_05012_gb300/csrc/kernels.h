@@ -138,3 +138,7 @@ cudaError_t launch_axpby(int prec, double2 alpha, const void* x, double2 beta, v
 // y += sum_j c[j] * x[j]  (k vectors, coefficients host-side)
 cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
                               cudaStream_t s);
+// y += sum_{j<k} c_j x_j (k <= 20), then per-CTA partials of <x_j, y_new> (dots, double2 [k][grid])
+// or of |y_new|^2 (double [grid]) in the same pass
+cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
+                                     bool dots, double2* partials, cudaStream_t s);
