@@ -5,6 +5,7 @@
 #include "kernels.h"
 #include "lqcd_amg.h"
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -260,8 +261,8 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
     if (p->nlevels >= 3) {
         if (p->prec_coarse != AMG_F64 && p->prec_coarse != AMG_F32 && p->prec_coarse != AMG_BF16)
             return fail(AMG_EINVAL, "prec_coarse must be AMG_F64, AMG_F32 or AMG_BF16");
-        if ((p->prec_coarse == AMG_F64) != (p->prec_coarsest == AMG_F64))
-            return fail(AMG_EINVAL, "prec_coarse and prec_coarsest must both be FP64 or both not");
+        if (p->prec_coarse == AMG_F64 && p->prec_coarsest != AMG_F64)
+            return fail(AMG_EINVAL, "an FP64 intermediate level needs an FP64 coarsest level");
         if (p->inter_m < 1 || p->inter_m > 19 || p->inter_maxit < 1 || !(p->inter_tol > 0))
             return fail(AMG_EINVAL, "inter_m must be 1..19, inter_maxit >= 1, inter_tol > 0");
     }
@@ -368,13 +369,21 @@ amg_status coarse_sap(amg_hierarchy* h, int l, const void* b, void* x, bool x_ze
     return AMG_OK;
 }
 
-// x = M_l b on level l >= 1: steps (1) and (2) of Sec. 3 one level down
+// x = M_l b on level l >= 1: steps (1) and (2) of Sec. 3 one level down.  When
+// the next level solves in FP64 while this one works in FP32, the restricted
+// vector is widened before the solve and the solution narrowed after it
+// (through the next level's shadow vector, free outside its solve).
 amg_status vcycle_c(amg_hierarchy* h, int l, const void* b, void* x, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
+    CoarseLevel& N = h->lev[l + 1];
     auto& w = h->cw[l + 1];
-    CK(launch_restrict_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, b, w[0]->p, 1, s));
+    const bool widen = N.prec != L.prec;
+    void* rc = widen ? w[2]->p : w[0]->p;
+    CK(launch_restrict_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, b, rc, 1, s));
+    if (widen) CK(launch_convert_flat(L.prec, N.prec, rc, w[0]->p, coarse_n(N), s));
     TRY(coarse_solve(h, l + 1, w[0]->p, w[1]->p, 1, s));
-    CK(launch_prolong_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, w[1]->p, x, 1, s));
+    if (widen) CK(launch_convert_flat(N.prec, L.prec, w[1]->p, rc, coarse_n(N), s));
+    CK(launch_prolong_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, widen ? rc : w[1]->p, x, 1, s));
     return coarse_sap(h, l, b, x, false, 1, s);
 }
 
@@ -673,8 +682,10 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             for (int q = 0; q < nb; ++q)
                 if (!st[q].stop) relax = relax && relaxed_product(std::abs(st[q].g[j]) / st[q].bnorm, tol);
             TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, nb, s, relax));
-            // classical Gram-Schmidt, twice, every right-hand side in one synchronisation per
-            // reduction: dots; (update, dots of the updated w) in one pass; (update, |w|^2) in one pass
+            // classical Gram-Schmidt with the Daniel-Gragg-Kaufman-Stewart test: the projection is
+            // repeated only where it removed more than half of |w|^2 (cancellation); one host
+            // synchronisation per reduction for every right-hand side.  Pass 1: dots and |w|^2;
+            // pass 2: update fused with the new dots and |w|^2; pass 3 (if needed): update + |w|^2
             std::vector<const void*> vl(j + 1);
             double2* const dp = red.dpart.as<double2>();
             auto region = [&](int q) { return dp + (size_t)q * 20 * red.grid; };
@@ -684,37 +695,59 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
                 CK(cudaStreamSynchronize(s));
                 return AMG_OK;
             };
+            auto quantity = [&](int q, int i) {   // host sum of quantity i of right-hand side q
+                double re = 0, im = 0;
+                const double2* hp = red.hpart + (size_t)q * 20 * red.grid + (size_t)i * red.grid;
+                for (int t = 0; t < red.grid; ++t) {
+                    re += hp[t].x;
+                    im += hp[t].y;
+                }
+                return cplx(re, im);
+            };
+            // subtract the projections just summed from w_q, fused with the next reduction
+            auto project = [&](int q, int mode) -> amg_status {
+                RhsState& r = st[q];
+                std::vector<double2> nc(j + 1);
+                for (int i = 0; i <= j; ++i) {
+                    const cplx c = quantity(q, i);
+                    r.H[i][j] += c;
+                    nc[i] = make_double2(-c.real(), -c.imag());
+                    vl[i] = F(h->oV[i]->p, q);
+                }
+                CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, mode, region(q), s));
+                return AMG_OK;
+            };
             for (int q = 0; q < nb; ++q) {
                 for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
-                CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n, region(q), s));
+                CK(launch_multi_dot_norm(0, j + 1, vl.data(), F(h->ow.p, q), n, region(q), s));
             }
-            TRY(fetch(j + 1));
+            TRY(fetch(j + 2));
             TRY(coarse_status(h));
-            std::vector<double> hn2(nb, 0.0);
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int q = 0; q < nb; ++q) {
-                    RhsState& r = st[q];
-                    if (r.stop) continue;
-                    std::vector<double2> nc(j + 1);
-                    for (int i = 0; i <= j; ++i) {
-                        double re = 0, im = 0;
-                        const double2* hp = red.hpart + (size_t)q * 20 * red.grid + (size_t)i * red.grid;
-                        for (int t = 0; t < red.grid; ++t) {
-                            re += hp[t].x;
-                            im += hp[t].y;
-                        }
-                        r.H[i][j] += cplx(re, im);
-                        nc[i] = make_double2(-re, -im);
-                    }
-                    for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
-                    CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, pass == 0, region(q),
-                                                s));
-                }
-                TRY(fetch(pass == 0 ? j + 1 : 1));
-            }
+            std::vector<double> nw0(nb, 0.0), hn2(nb, 0.0);
             for (int q = 0; q < nb; ++q) {
-                const double* hp = (const double*)(red.hpart + (size_t)q * 20 * red.grid);
-                for (int t = 0; t < red.grid; ++t) hn2[q] += hp[t];
+                if (st[q].stop) continue;
+                nw0[q] = quantity(q, j + 1).real();
+                TRY(project(q, 2));
+            }
+            TRY(fetch(j + 2));
+            std::vector<char> again(nb, 0);
+            bool any_again = false;
+            for (int q = 0; q < nb; ++q) {
+                if (st[q].stop) continue;
+                hn2[q] = quantity(q, j + 1).real();
+                again[q] = hn2[q] < 0.5 * nw0[q];
+                any_again = any_again || again[q];
+            }
+            if (any_again) {
+                for (int q = 0; q < nb; ++q)
+                    if (!st[q].stop && again[q]) TRY(project(q, 0));
+                TRY(fetch(j + 2));
+                for (int q = 0; q < nb; ++q) {
+                    if (st[q].stop || !again[q]) continue;
+                    const double* hp = (const double*)(red.hpart + (size_t)q * 20 * red.grid);
+                    hn2[q] = 0;
+                    for (int t = 0; t < red.grid; ++t) hn2[q] += hp[t];
+                }
             }
             bool all_stopped = true;
             for (int q = 0; q < nb; ++q) {
@@ -948,7 +981,7 @@ amg_status upload_cvecs(amg_hierarchy* h, int l, const double* host, cudaStream_
 amg_status galerkin_c(amg_hierarchy* h, int l, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
     CoarseLevel& N = h->lev[l + 1];
-    CK(launch_galerkin_coarse(L.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, L.B.p, N.B.p, s));
+    CK(launch_galerkin_coarse(L.prec, N.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, L.B.p, N.B.p, s));
     if (N.opbf) CK(launch_complex_to_bf16(N.B.p, N.B16.p, (size_t)N.g.V * 9 * N.nc * N.nc, s));
     if (N.opbf && coarse_tc_supported(N.nc)) {
         CK(N.tci.ensure(coarse_tc_image_bytes(N.g.V, N.nc)));
@@ -1035,25 +1068,24 @@ amg_status tune_kernels(amg_hierarchy* h) {
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        float best = 1e30f;
-        int best_v = 0;
-        for (int v = 0; v <= 1; ++v) {
-            float ms = 0;
-            for (int rep = 0; rep < 4; ++rep) {
+        // the two variants alternate (one full SAP iteration, both colours, per sample) so that
+        // drifts of clock or cache state hit both alike; the median of 9 samples decides
+        std::vector<float> t[2];
+        for (int rep = 0; rep < 10; ++rep) {
+            for (int v = 0; v <= 1; ++v) {
                 CK(cudaEventRecord(e0, 0));
-                CK(launch_sap_half_variant(v, pr, g, h->blk[0], 0, h->p.mr_iters, 0, d->gauge->U[pr].p, d->C[pr].p,
-                                           h->fb[pr].p, h->fx[pr].p, d->kappa, 1, 0));
+                for (int colour = 0; colour < 2; ++colour)
+                    CK(launch_sap_half_variant(v, pr, g, h->blk[0], colour, h->p.mr_iters, 0, d->gauge->U[pr].p,
+                                               d->C[pr].p, h->fb[pr].p, h->fx[pr].p, d->kappa, 1, 0));
                 CK(cudaEventRecord(e1, 0));
                 CK(cudaEventSynchronize(e1));
-                float t = 0;
-                CK(cudaEventElapsedTime(&t, e0, e1));
-                if (rep > 0) ms += t;
-            }
-            if (ms < best) {
-                best = ms;
-                best_v = v;
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) t[v].push_back(ms);
             }
         }
+        for (auto& tv : t) std::sort(tv.begin(), tv.end());
+        const int best_v = t[1][t[1].size() / 2] < t[0][t[0].size() / 2] ? 1 : 0;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         h->sap_variant[pr] = best_v;

@@ -35,12 +35,14 @@ struct CoefList {
 
 // K dots <a_j, b>, K a compile-time constant so that only K accumulation
 // chains are issued (FP64 arithmetic is scarce on this part)
-template <typename V, int K>
+// K dots <a_j, b> (quantities 0..K-1) and, with NB, |b|^2 as quantity K (imaginary part 0)
+template <typename V, int K, bool NB>
 __global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, double2* partials) {
-    __shared__ double red[2 * K * 32];
-    double acc[2 * K];
+    constexpr int NQ = K + (NB ? 1 : 0);
+    __shared__ double red[2 * NQ * 32];
+    double acc[2 * NQ];
 #pragma unroll
-    for (int j = 0; j < 2 * K; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 2 * NQ; ++j) acc[j] = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         V y = b[i];
 #pragma unroll
@@ -49,15 +51,16 @@ __global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, d
             acc[2 * j] += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
             acc[2 * j + 1] += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
         }
+        if (NB) acc[2 * K] += (double)y.x * (double)y.x + (double)y.y * (double)y.y;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int j = 0; j < 2 * K; ++j) {
+    for (int j = 0; j < 2 * NQ; ++j) {
         double v = warp_sum(acc[j]);
         if (lane == 0) red[j * 32 + warp] = v;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    for (int j = threadIdx.x; j < NQ; j += blockDim.x) {
         double re = 0, im = 0;
         for (int w = 0; w < nw; ++w) {
             re += red[(2 * j) * 32 + w];
@@ -68,20 +71,22 @@ __global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, d
 }
 
 template <typename V, int K>
-void multi_dot_launch(int k, const PtrList& pl, const V* b, size_t n, double2* partials, cudaStream_t st) {
+void multi_dot_launch(int k, bool nb, const PtrList& pl, const V* b, size_t n, double2* partials, cudaStream_t st) {
     if constexpr (K > 1) {
-        if (k < K) return multi_dot_launch<V, K - 1>(k, pl, b, n, partials, st);
+        if (k < K) return multi_dot_launch<V, K - 1>(k, nb, pl, b, n, partials, st);
     }
-    (note_launch(), multi_dot_kernel<V, K><<<blas_grid_size(), kBT, 0, st>>>(pl, b, n, partials));
+    if (nb) (note_launch(), multi_dot_kernel<V, K, true><<<blas_grid_size(), kBT, 0, st>>>(pl, b, n, partials));
+    else (note_launch(), multi_dot_kernel<V, K, false><<<blas_grid_size(), kBT, 0, st>>>(pl, b, n, partials));
 }
 
 // y += sum_{j<K} c_j x_j, then partial dots <x_j, y_new> (DOT) or partial |y_new|^2:
 // one pass over the vectors for the update of a Gram-Schmidt pass and the
 // reduction of the next one
-template <typename V, int K, bool DOT>
+template <typename V, int K, int MODE>   // MODE 0: |y|^2; 1: dots; 2: dots and |y|^2 (quantity K)
 __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, double2* partials) {
     using T = typename VT<V>::T;
-    constexpr int NA = DOT ? 2 * K : 1;
+    constexpr bool DOT = MODE >= 1, NRM = MODE != 1;
+    constexpr int NA = (DOT ? 2 * K : 0) + (NRM ? (DOT ? 2 : 1) : 0);
     __shared__ double red[NA * 32];
     double acc[NA];
 #pragma unroll
@@ -107,9 +112,8 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
                 acc[2 * j] += (double)xs[j].x * (double)re + (double)xs[j].y * (double)im;
                 acc[2 * j + 1] += (double)xs[j].x * (double)im - (double)xs[j].y * (double)re;
             }
-        } else {
-            acc[0] += (double)re * (double)re + (double)im * (double)im;
         }
+        if constexpr (NRM) acc[DOT ? 2 * K : 0] += (double)re * (double)re + (double)im * (double)im;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -119,7 +123,8 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
     }
     __syncthreads();
     if (DOT) {
-        for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        constexpr int NQ = K + (NRM ? 1 : 0);   // the norm pair is (|y|^2, 0)
+        for (int j = threadIdx.x; j < NQ; j += blockDim.x) {
             double re = 0, im = 0;
             for (int w = 0; w < nw; ++w) {
                 re += red[(2 * j) * 32 + w];
@@ -134,13 +139,13 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
     }
 }
 
-template <typename V, int K, bool DOT>
+template <typename V, int K, int MODE>
 void multi_axpy_reduce_launch(int k, const CoefList& cl, const PtrList& pl, V* y, size_t n, double2* partials,
                               cudaStream_t st) {
     if constexpr (K > 1) {
-        if (k < K) return multi_axpy_reduce_launch<V, K - 1, DOT>(k, cl, pl, y, n, partials, st);
+        if (k < K) return multi_axpy_reduce_launch<V, K - 1, MODE>(k, cl, pl, y, n, partials, st);
     }
-    (note_launch(), multi_axpy_reduce_kernel<V, K, DOT><<<blas_grid_size(), kBT, 0, st>>>(cl, pl, y, n, partials));
+    (note_launch(), multi_axpy_reduce_kernel<V, K, MODE><<<blas_grid_size(), kBT, 0, st>>>(cl, pl, y, n, partials));
 }
 
 template <typename V>
@@ -203,8 +208,17 @@ cudaError_t launch_multi_dot(int prec, int k, const void* const* a, const void* 
     PtrList pl;
     for (int j = 0; j < k; ++j) pl.p[j] = a[j];
     if (k < 1) return cudaErrorInvalidValue;
-    if (prec == 0) multi_dot_launch<double2, kMaxDots>(k, pl, (const double2*)b, n, partials, st);
-    else multi_dot_launch<float2, kMaxDots>(k, pl, (const float2*)b, n, partials, st);
+    if (prec == 0) multi_dot_launch<double2, kMaxDots>(k, false, pl, (const double2*)b, n, partials, st);
+    else multi_dot_launch<float2, kMaxDots>(k, false, pl, (const float2*)b, n, partials, st);
+    return cudaGetLastError();
+}
+cudaError_t launch_multi_dot_norm(int prec, int k, const void* const* a, const void* b, size_t n, double2* partials,
+                                  cudaStream_t st) {
+    if (k < 1 || k >= kMaxDots) return cudaErrorInvalidValue;
+    PtrList pl;
+    for (int j = 0; j < k; ++j) pl.p[j] = a[j];
+    if (prec == 0) multi_dot_launch<double2, kMaxDots - 1>(k, true, pl, (const double2*)b, n, partials, st);
+    else multi_dot_launch<float2, kMaxDots - 1>(k, true, pl, (const float2*)b, n, partials, st);
     return cudaGetLastError();
 }
 cudaError_t launch_norm2(int prec, const void* a, size_t n, double* partials, cudaStream_t st) {
@@ -232,20 +246,24 @@ cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* con
 }
 
 cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
-                                     bool dots, double2* partials, cudaStream_t st) {
-    if (k < 1 || k > kMaxDots) return cudaErrorInvalidValue;
+                                     int mode, double2* partials, cudaStream_t st) {
+    if (k < 1 || k > kMaxDots || (mode == 2 && k >= kMaxDots)) return cudaErrorInvalidValue;
     CoefList cl;
     PtrList pl;
     for (int j = 0; j < k; ++j) {
         cl.c[j] = c[j];
         pl.p[j] = x[j];
     }
+#define MAR(V, M) multi_axpy_reduce_launch<V, (M == 2 ? kMaxDots - 1 : kMaxDots), M>(k, cl, pl, (V*)y, n, partials, st)
     if (prec == 0) {
-        if (dots) multi_axpy_reduce_launch<double2, kMaxDots, true>(k, cl, pl, (double2*)y, n, partials, st);
-        else multi_axpy_reduce_launch<double2, kMaxDots, false>(k, cl, pl, (double2*)y, n, partials, st);
+        if (mode == 0) MAR(double2, 0);
+        else if (mode == 1) MAR(double2, 1);
+        else MAR(double2, 2);
     } else {
-        if (dots) multi_axpy_reduce_launch<float2, kMaxDots, true>(k, cl, pl, (float2*)y, n, partials, st);
-        else multi_axpy_reduce_launch<float2, kMaxDots, false>(k, cl, pl, (float2*)y, n, partials, st);
+        if (mode == 0) MAR(float2, 0);
+        else if (mode == 1) MAR(float2, 1);
+        else MAR(float2, 2);
     }
+#undef MAR
     return cudaGetLastError();
 }

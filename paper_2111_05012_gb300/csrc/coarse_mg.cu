@@ -422,8 +422,8 @@ cudaError_t launch_orthonormalise_coarse(int vprec, const GeomH& g, const BlockH
     return cudaGetLastError();
 }
 
-cudaError_t launch_galerkin_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
-                                   const void* B, void* Bout, cudaStream_t st) {
+cudaError_t launch_galerkin_coarse(int vprec, int oprec, const GeomH& g, const BlockH& bh, int nc, int nvec,
+                                   const void* vecs, const void* B, void* Bout, cudaStream_t st) {
     CB k = make_cb(g, bh);
     const int th = 256;
     if (4 * nvec * nvec > 16 * th || nc % 2 != 0) return cudaErrorInvalidValue;
@@ -436,11 +436,12 @@ cudaError_t launch_galerkin_coarse(int vprec, const GeomH& g, const BlockH& bh, 
         if (e != cudaSuccess) return e;
         (note_launch(), cgalerkin_kernel<double, double><<<grid, th, smem, st>>>(k, nc, nvec, vecs, B, Bout));
     } else {
+        // FP32 level; the next level's stencil is stored in FP32 or (oprec 0) widened to FP64
         const size_t smem = elems * sizeof(cx<float>);
-        cudaError_t e = cudaFuncSetAttribute(cgalerkin_kernel<float, float>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto fn = oprec == 0 ? cgalerkin_kernel<float, double> : cgalerkin_kernel<float, float>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        (note_launch(), cgalerkin_kernel<float, float><<<grid, th, smem, st>>>(k, nc, nvec, vecs, B, Bout));
+        (note_launch(), fn<<<grid, th, smem, st>>>(k, nc, nvec, vecs, B, Bout));
     }
     return cudaGetLastError();
 }

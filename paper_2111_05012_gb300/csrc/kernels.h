@@ -91,9 +91,10 @@ cudaError_t launch_prolong_coarse(int vprec, const GeomH& g, const BlockH& bh, i
 // block Gram-Schmidt of the level-l test vectors per (block, chirality half); *err = 1 on rank deficiency
 cudaError_t launch_orthonormalise_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, void* vecs,
                                          int* err, cudaStream_t s);
-// Eq. 7: stencil of level l+1 ([Vc][2 nvec][9][2 nvec]) from the level-l stencil B ([V][nc][9][nc])
-cudaError_t launch_galerkin_coarse(int vprec, const GeomH& g, const BlockH& bh, int nc, int nvec, const void* vecs,
-                                   const void* B, void* Bout, cudaStream_t s);
+// Eq. 7: stencil of level l+1 ([Vc][2 nvec][9][2 nvec]) from the level-l stencil B ([V][nc][9][nc]);
+// computed in vprec, stored in oprec (oprec 0 with vprec 1: FP32 arithmetic widened to FP64)
+cudaError_t launch_galerkin_coarse(int vprec, int oprec, const GeomH& g, const BlockH& bh, int nc, int nvec,
+                                   const void* vecs, const void* B, void* Bout, cudaStream_t s);
 // SAP half sweep on level l: domains of `colour`, fused residual + nmr MR steps; kprec 0 FP64,
 // 1 FP32, 2 FP32 vectors with a bfloat16 stencil; x_mode as for the fine half sweep
 cudaError_t launch_coarse_sap_half(int kprec, const GeomH& g, const BlockH& bh, int nc, int colour, int nmr,
@@ -138,7 +139,11 @@ cudaError_t launch_axpby(int prec, double2 alpha, const void* x, double2 beta, v
 // y += sum_j c[j] * x[j]  (k vectors, coefficients host-side)
 cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
                               cudaStream_t s);
-// y += sum_{j<k} c_j x_j (k <= 20), then per-CTA partials of <x_j, y_new> (dots, double2 [k][grid])
-// or of |y_new|^2 (double [grid]) in the same pass
+// y += sum_{j<k} c_j x_j (k <= 20), then in the same pass per-CTA partials of
+// mode 0: |y_new|^2 (double [grid]); 1: <x_j, y_new> (double2 [k][grid]);
+// 2: both, |y_new|^2 as quantity k (double2 (n2, 0), k <= 19)
 cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
-                                     bool dots, double2* partials, cudaStream_t s);
+                                     int mode, double2* partials, cudaStream_t s);
+// multi_dot plus |b|^2 as quantity k (double2 (n2, 0)), k <= 19
+cudaError_t launch_multi_dot_norm(int prec, int k, const void* const* a, const void* b, size_t n, double2* partials,
+                                  cudaStream_t s);

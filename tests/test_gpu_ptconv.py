@@ -114,7 +114,7 @@ def test_training_reduces_the_loss_and_the_solve_uses_the_network():
     nn = c.amg_nn_create(f.d, channels, w)
     # (residual, error) pairs from the solver: e = (1 - M D) e0, r = D e
     losses = []
-    for step in range(12):
+    for step in range(30):
         es, rs = [], []
         for k in range(4):
             e0 = li.rhs(dims, 100 + step * 4 + k)
@@ -131,7 +131,21 @@ def test_training_reduces_the_loss_and_the_solve_uses_the_network():
         loss = c.amg_nn_train_step(nn, torch.cat(rs), torch.cat(es), 4, 1e-3)
         losses.append(loss)
     assert np.mean(losses[-3:]) < np.mean(losses[:3])
+    # what the trained network gains: the error left by one application of the
+    # preconditioner, |(1 - M' D) e0| with M' = M + N (1 - D M), against the
+    # plain cycle's |(1 - M D) e0|, on fresh error vectors
+    def left_error(k):
+        e0d = to_dev(li.rhs(dims, 900 + k))
+        De0 = torch.empty_like(e0d)
+        c.amg_apply_D(f.d, e0d, De0, 1, c.AMG_F64)
+        Me = torch.empty_like(e0d)
+        c.amg_precondition(h, De0, Me)
+        return float(torch.linalg.norm(e0d - Me) / torch.linalg.norm(e0d))
+    plain = [left_error(k) for k in range(3)]
     c.amg_hierarchy_set_nn(h, nn)
+    learned = [left_error(k) for k in range(3)]
+    print("error left by one preconditioner application: plain", plain, "learned", learned)
+    assert np.mean(learned) < np.mean(plain)
     b = to_dev(li.rhs(dims, 1))
     x = torch.zeros_like(b)
     st, info = c.amg_solve(h, b, x, 1, 1e-10, 200)

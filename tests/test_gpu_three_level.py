@@ -101,6 +101,20 @@ def test_second_coarsening_transfer_and_sap(three, prec):
     c.amg_hierarchy_destroy(h)
 
 
+def test_fp64_coarsest_below_fp32_level(three):
+    # level 2 in FP64 under an FP32 level 1: its stencil is the FP32 Galerkin
+    # product widened to FP64, so it matches the oracle to FP32 accuracy
+    f = three
+    c = f.c
+    p = _params(c, 1)
+    p.prec_coarsest = c.AMG_F64
+    h = c.amg_setup_from_vectors(f.d, p, f.init)
+    B = c.amg_get_coarse_op(h, 2)
+    B = B[..., 0] + 1j * B[..., 1]
+    assert rel(B, f.hier.levels[2].op.B.reshape(B.shape)) < 5e-6
+    c.amg_hierarchy_destroy(h)
+
+
 def test_three_level_cycle_fp64(three):
     # x = M b: restrict, FGMRES(8) to 1e-1 on level 1 (its cycle: restrict,
     # BiCGStab(2) to 1e-2 on level 2, prolong, SAP), prolong, SAP
@@ -116,7 +130,7 @@ def test_three_level_cycle_fp64(three):
     c.amg_hierarchy_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, "bf16"])
+@pytest.mark.parametrize("prec", [0, 1, 2, "bf16", "bf16+f64"])
 def test_three_level_solve(three, prec):
     f = three
     c = f.c
@@ -124,6 +138,10 @@ def test_three_level_solve(three, prec):
         p = _params(c, 1, n_init=2, n_adapt=1)
         p.prec_coarse = c.AMG_BF16
         p.prec_coarsest = c.AMG_BF16
+    elif prec == "bf16+f64":   # bfloat16 level-1 stencil, FP64 solve on level 2
+        p = _params(c, 1, n_init=2, n_adapt=1)
+        p.prec_coarse = c.AMG_BF16
+        p.prec_coarsest = c.AMG_F64
     else:
         p = _params(c, prec, n_init=2, n_adapt=1)
     h = c.amg_setup(f.d, p, f.init)
