@@ -682,10 +682,10 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             for (int q = 0; q < nb; ++q)
                 if (!st[q].stop) relax = relax && relaxed_product(std::abs(st[q].g[j]) / st[q].bnorm, tol);
             TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, nb, s, relax));
-            // classical Gram-Schmidt with the Daniel-Gragg-Kaufman-Stewart test: the projection is
-            // repeated only where it removed more than half of |w|^2 (cancellation); one host
-            // synchronisation per reduction for every right-hand side.  Pass 1: dots and |w|^2;
-            // pass 2: update fused with the new dots and |w|^2; pass 3 (if needed): update + |w|^2
+            // classical Gram-Schmidt, twice (with a good preconditioner w = D M v lies close to
+            // span V, so a second projection is always needed); one host synchronisation per
+            // reduction for every right-hand side: dots; update fused with the new dots; update
+            // fused with |w|^2
             std::vector<const void*> vl(j + 1);
             double2* const dp = red.dpart.as<double2>();
             auto region = [&](int q) { return dp + (size_t)q * 20 * red.grid; };
@@ -704,50 +704,32 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
                 }
                 return cplx(re, im);
             };
-            // subtract the projections just summed from w_q, fused with the next reduction
-            auto project = [&](int q, int mode) -> amg_status {
-                RhsState& r = st[q];
-                std::vector<double2> nc(j + 1);
-                for (int i = 0; i <= j; ++i) {
-                    const cplx c = quantity(q, i);
-                    r.H[i][j] += c;
-                    nc[i] = make_double2(-c.real(), -c.imag());
-                    vl[i] = F(h->oV[i]->p, q);
-                }
-                CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, mode, region(q), s));
-                return AMG_OK;
-            };
             for (int q = 0; q < nb; ++q) {
                 for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
-                CK(launch_multi_dot_norm(0, j + 1, vl.data(), F(h->ow.p, q), n, region(q), s));
+                CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n, region(q), s));
             }
-            TRY(fetch(j + 2));
+            TRY(fetch(j + 1));
             TRY(coarse_status(h));
-            std::vector<double> nw0(nb, 0.0), hn2(nb, 0.0);
-            for (int q = 0; q < nb; ++q) {
-                if (st[q].stop) continue;
-                nw0[q] = quantity(q, j + 1).real();
-                TRY(project(q, 2));
-            }
-            TRY(fetch(j + 2));
-            std::vector<char> again(nb, 0);
-            bool any_again = false;
-            for (int q = 0; q < nb; ++q) {
-                if (st[q].stop) continue;
-                hn2[q] = quantity(q, j + 1).real();
-                again[q] = hn2[q] < 0.5 * nw0[q];
-                any_again = any_again || again[q];
-            }
-            if (any_again) {
-                for (int q = 0; q < nb; ++q)
-                    if (!st[q].stop && again[q]) TRY(project(q, 0));
-                TRY(fetch(j + 2));
+            for (int pass = 0; pass < 2; ++pass) {
                 for (int q = 0; q < nb; ++q) {
-                    if (st[q].stop || !again[q]) continue;
-                    const double* hp = (const double*)(red.hpart + (size_t)q * 20 * red.grid);
-                    hn2[q] = 0;
-                    for (int t = 0; t < red.grid; ++t) hn2[q] += hp[t];
+                    RhsState& r = st[q];
+                    if (r.stop) continue;
+                    std::vector<double2> nc(j + 1);
+                    for (int i = 0; i <= j; ++i) {
+                        const cplx c = quantity(q, i);
+                        r.H[i][j] += c;
+                        nc[i] = make_double2(-c.real(), -c.imag());
+                        vl[i] = F(h->oV[i]->p, q);
+                    }
+                    CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, pass == 0 ? 1 : 0,
+                                                region(q), s));
                 }
+                TRY(fetch(pass == 0 ? j + 1 : 1));
+            }
+            std::vector<double> hn2(nb, 0.0);
+            for (int q = 0; q < nb; ++q) {
+                const double* hp = (const double*)(red.hpart + (size_t)q * 20 * red.grid);
+                for (int t = 0; t < red.grid; ++t) hn2[q] += hp[t];
             }
             bool all_stopped = true;
             for (int q = 0; q < nb; ++q) {

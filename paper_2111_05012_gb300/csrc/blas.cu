@@ -20,7 +20,7 @@ int sm_count() {
     return sms;
 }
 
-int blas_grid_size() { return 8 * sm_count(); }
+int blas_grid_size() { return 2 * sm_count(); }
 
 template <typename V> struct VT;
 template <> struct VT<double2> { using T = double; };
