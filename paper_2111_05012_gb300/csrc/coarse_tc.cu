@@ -14,14 +14,13 @@
 // Rows 2Nc..127 of the M = 128 tile are never read back, so their part of
 // the shared-memory span is not filled.
 //
-// Both operands arrive by bulk copies, one chunk per direction d: the rows
-// of B_d(X) from a copy of the operator in the 8 x 8 core-matrix operand
-// layout (K-major, no swizzle, k groups outermost within a chunk), and the
-// neighbour's vectors x(X + d), packed once per call into the same layout.
-// A producer warp streams chunks into a ring of shared-memory slots, an MMA
-// warp issues each chunk's Nc/16 MMAs (M 128, N 2P, K 16) into one of two
-// tensor-memory accumulators and frees the slot by tcgen05.commit, and four
-// epilogue warps drain the other accumulator meanwhile.
+// Both operands arrive by bulk copies: A from a copy of the operator in the
+// 8 x 8 core-matrix operand layout (K-major, no swizzle), one copy per site;
+// G as nine copies (one per direction d) of the neighbours' vectors, packed
+// once per call into the same layout with the k-groups outermost, so that
+// the nine pieces concatenate along K.  Copies of the next site overlap the
+// MMAs and the epilogue of the current one (two stages).  One thread issues
+// the 9Nc/16 MMAs (M 128, N 2P, K 16) and commits them to an mbarrier.
 //
 // All waits are bounded: on a timeout the kernel records an error, waits
 // (bounded) for its own bulk copies, releases its tensor memory and returns.
@@ -30,6 +29,7 @@
 
 namespace {
 
+constexpr int kTcThreads = 128;
 constexpr long long kTcSpin = 20000000;
 
 DEV uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -144,16 +144,13 @@ DEV int tc_nbr(const TcArgs& a, int X, int d) {
     return c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
 }
 
-// Ring plan: R slots, each one direction's operator rows (A_d, 2Nc x Nc) and
-// packed vectors (G_d, 2P x Nc).  An operator descriptor spans 16 row groups
-// (M = 128); past the 2Nc/8 groups of A_d it reads (16 - 2Nc/8) x 128 bytes
-// of whatever follows (G_d or padding), so each slot reserves that much.
+// Shared-memory plan of one CTA (byte offsets).  An operator descriptor spans
+// 16 row groups (M = 128) but only the first 2Nc/8 hold operator rows: the
+// rest of the span may overlap the next buffer.
 struct TcPlan {
-    int slots;      // R
-    int stride;     // bytes per slot
-    int a_chunk;    // bytes of A_d
-    int b_chunk;    // bytes of G_d
-    int bar;        // offset of the mbarriers
+    int a0, a1;   // operator buffers (a1 == a0: one buffer)
+    int b0, b1;   // packed-vector buffers
+    int bar;      // mbarriers
     int bytes;
 };
 
@@ -174,167 +171,140 @@ __global__ void tc_pack_kernel(int V, int nc, int nrhs, int P, const float2* __r
     }
 }
 
-DEV bool mb_wait_or_fail(uint64_t* bar, unsigned parity, volatile int* fail) {
-    for (long long i = 0; i < kTcSpin; ++i) {
-        if (mb_try(bar, parity)) return true;
-        if ((i & 1023) == 1023 && *fail) return false;
-    }
-    return false;
-}
-DEV void mb_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
-}
-
-// Warp-specialised persistent kernel: warp 4 streams chunks (one coarse site
-// = nine chunks, one per direction d) into a ring of shared-memory slots by
-// bulk copies; warp 5 issues the Nc/16 MMAs of each chunk into one of two
-// tensor-memory accumulators and frees the slot when they complete; warps
-// 0..3 drain the other accumulator (tcgen05.ld, shuffle, store) meanwhile.
 template <int NP>   // NP = 2P accumulator columns (16 or 32)
-__global__ void __launch_bounds__(192, 1) coarse_tc_kernel(TcArgs a, TcPlan pl) {
+__global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a, TcPlan pl) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int P = NP / 2, NG = NP / 8;
-    const int nc = a.nc, mgv = 2 * nc / 8, R = pl.slots;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + pl.bar);   // [R]
-    uint64_t* empty = full + R;                                         // [R]
-    uint64_t* accfull = empty + R;                                      // [2]
-    uint64_t* accfree = accfull + 2;                                    // [2]
-    uint32_t* slot_t = reinterpret_cast<uint32_t*>(accfree + 2);
-    volatile int* fail = reinterpret_cast<volatile int*>(slot_t + 1);
+    const int nc = a.nc, K = 9 * nc, kg = K / 8;
+    const unsigned a_bytes = (unsigned)(2 * nc) * K * 2;        // operator rows of one site
+    const unsigned x_site = (unsigned)nc * NP * 2;              // packed vectors of one site
+    unsigned char* Ab[2] = {smem_raw + pl.a0, smem_raw + pl.a1};
+    unsigned char* Bb[2] = {smem_raw + pl.b0, smem_raw + pl.b1};
+    const bool dblA = pl.a1 != pl.a0;
+    uint64_t* barA = reinterpret_cast<uint64_t*>(smem_raw + pl.bar);   // [2]
+    uint64_t* barB = barA + 2;                                           // [2]
+    uint64_t* barM = barA + 4;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(barA + 5);
+    int* fail = reinterpret_cast<int*>(slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nsites = (int)blockIdx.x < a.V ? (a.V - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int total = nsites * 9;
-    const int nq = 2 * nc / 32;
+    const int nq = 2 * nc / 32;   // quarters of the accumulator holding operator rows
 
     if (tid == 0) {
-        for (int i = 0; i < R; ++i) {
-            mb_init(&full[i], 1);
-            mb_init(&empty[i], 1);
-        }
-        mb_init(&accfull[0], 1);
-        mb_init(&accfull[1], 1);
-        mb_init(&accfree[0], 4);
-        mb_init(&accfree[1], 4);
+        for (int i = 0; i < 5; ++i) mb_init(&barA[i], 1);
         mb_fence_init();
         *fail = 0;
     }
-    if (warp == 5) {
-        tm_alloc(slot_t, 64);
+    if (warp == 0) {
+        tm_alloc(slot, 32);
         tm_relinquish();
     }
     tc_before();
     __syncthreads();
     tc_after();
-    const uint32_t tmem = *slot_t;
-
-    if (warp == 4 && lane == 0) {
-        // ---- producer
-        int issued = 0;
-        for (int gc = 0; gc < total; ++gc) {
-            const int s = gc % R, round = gc / R;
-            if (round > 0 && !mb_wait_or_fail(&empty[s], (round - 1) & 1, fail)) {
-                *fail = 1;
-                break;
-            }
-            const int X = blockIdx.x + (gc / 9) * gridDim.x, d = gc % 9;
-            unsigned char* base = smem_raw + (size_t)s * pl.stride;
-            mb_expect_tx(&full[s], pl.a_chunk + pl.b_chunk);
-            bulk_load(base, a.img + ((size_t)X * 9 + d) * (pl.a_chunk / 2), pl.a_chunk, &full[s]);
-            bulk_load(base + pl.a_chunk, a.xp + (size_t)tc_nbr(a, X, d) * (pl.b_chunk / 2), pl.b_chunk, &full[s]);
-            ++issued;
-        }
-        // our copies must land before the shared memory goes away
-        for (int gc = issued - 1; gc >= 0 && gc >= issued - R; --gc) mb_wait(&full[gc % R], (gc / R) & 1);
-    } else if (warp == 5 && lane == 0) {
-        // ---- MMA issuer
-        const uint32_t idesc = idesc_bf16(128, NP);
-        const uint32_t a_lbo = (uint32_t)mgv * 128, b_lbo = NG * 128;
-        int done = 0;
-        for (int it = 0; it < nsites && !*fail; ++it) {
-            const int acc = it & 1;
-            if (it >= 2 && !mb_wait_or_fail(&accfree[acc], ((it >> 1) - 1) & 1, fail)) {
-                *fail = 2;
-                break;
-            }
-            tc_after();
-            for (int d = 0; d < 9; ++d) {
-                const int gc = it * 9 + d, s = gc % R;
-                if (!mb_wait_or_fail(&full[s], (gc / R) & 1, fail)) {
-                    *fail = 3;
-                    break;
-                }
-                tc_after();
-                const uint32_t a0 = su32(smem_raw + (size_t)s * pl.stride), b0 = a0 + pl.a_chunk;
-                for (int q = 0; q < nc / 16; ++q)
-                    mma_bf16(tmem + acc * 32, smem_desc(a0 + q * 2 * mgv * 128, a_lbo, 128),
-                             smem_desc(b0 + q * 2 * NG * 128, b_lbo, 128), idesc, (d > 0 || q > 0) ? 1u : 0u);
-                mma_commit(&empty[s]);
-                done = gc + 1;
-            }
-            if (*fail) break;
-            mma_commit(&accfull[acc]);
-        }
-        // the tensor core must be done with our operands and accumulators before we leave
-        if (done > 0) mb_wait(&empty[(done - 1) % R], ((done - 1) / R) & 1);
-    } else if (warp < 4) {
-        // ---- epilogue
-        for (int it = 0; it < nsites; ++it) {
-            const int acc = it & 1;
-            // warp-uniform decision: tcgen05.ld below needs all 32 lanes
-            const bool ok = __all_sync(0xffffffffu, mb_wait_or_fail(&accfull[acc], (it >> 1) & 1, fail));
-            if (!ok) {
-                if (lane == 0) *fail = 4;
-                break;
-            }
-            tc_after();
-            if (warp < nq) {
-                uint32_t v[NP];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + acc * 32;
-                if constexpr (NP == 32) tm_ld32(taddr, v);
-                else tm_ld16(taddr, v);
-                const int X = blockIdx.x + it * gridDim.x;
-                const int aa = warp * 16 + (lane & 15);
-                const bool im = lane >= 16;
-#pragma unroll
-                for (int r = 0; r < P; ++r) {
-                    // Re row: y_re = ReB.Re x - ImB.Im x; Im row: y_im = ImB.Re x + ReB.Im x
-                    const float pv = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[P + r]), 16);
-                    float val = im ? __uint_as_float(v[r]) + pv : __uint_as_float(v[r]) - pv;
-                    if (r < a.nrhs) {
-                        const size_t o = ((size_t)r * a.V + X) * nc + aa;
-                        if (a.b) val = reinterpret_cast<const float*>(a.b + o)[im ? 1 : 0] - val;
-                        reinterpret_cast<float*>(a.y + o)[im ? 1 : 0] = val;
-                    }
-                }
-            }
-            tc_before();
-            __syncwarp();
-            if (lane == 0) mb_arrive(&accfree[acc]);
-        }
+    const uint32_t tmem = *slot;
+    const uint32_t idesc = idesc_bf16(128, NP);
+    const uint32_t a_lbo = 128, a_sbo = (uint32_t)kg * 128;   // A: [m group][k group][8][8]
+    const uint32_t b_lbo = NG * 128, b_sbo = 128;             // G: [k group][n group][8][8]
+    unsigned phA[2] = {0, 0}, phB[2] = {0, 0}, phM = 0;
+    bool pendA[2] = {false, false}, pendB[2] = {false, false};   // thread 0 only
+    auto issueA = [&](int X, int s) {
+        mb_expect_tx(&barA[s], a_bytes);
+        bulk_load(Ab[s], a.img + (size_t)X * (2 * nc) * K, a_bytes, &barA[s]);
+        pendA[s] = true;
+    };
+    auto issueB = [&](int X, int s) {
+        mb_expect_tx(&barB[s], 9 * x_site);
+        for (int d = 0; d < 9; ++d)
+            bulk_load(Bb[s] + d * x_site, a.xp + (size_t)tc_nbr(a, X, d) * (x_site / 2), x_site, &barB[s]);
+        pendB[s] = true;
+    };
+    if (tid == 0 && (int)blockIdx.x < a.V) {
+        issueA(blockIdx.x, 0);
+        issueB(blockIdx.x, 0);
     }
-    __syncthreads();
-    if (*fail && tid == 0) atomicExch(a.err, 1);
+    int it = 0;
+    for (int X = blockIdx.x; X < a.V; X += gridDim.x, ++it) {
+        const int sB = it & 1, sA = dblA ? (it & 1) : 0;
+        const int Xn = X + gridDim.x;
+        if (tid == 0) {
+            // the other stage's buffers were last read by the previous site's MMAs, which completed
+            if (Xn < a.V) {
+                issueB(Xn, sB ^ 1);
+                if (dblA) issueA(Xn, sA ^ 1);
+            }
+            if (mb_wait(&barA[sA], phA[sA]) && mb_wait(&barB[sB], phB[sB])) {
+                pendA[sA] = pendB[sB] = false;
+                phA[sA] ^= 1;
+                phB[sB] ^= 1;
+                tc_after();
+                const uint32_t a0 = su32(Ab[sA]), b0 = su32(Bb[sB]);
+                for (int q = 0; q < K / 16; ++q)
+                    mma_bf16(tmem, smem_desc(a0 + q * 256, a_lbo, a_sbo), smem_desc(b0 + q * 2 * NG * 128, b_lbo, b_sbo),
+                             idesc, q > 0 ? 1u : 0u);
+                mma_commit(barM);
+            } else {
+                *fail = 1;
+            }
+        }
+        __syncthreads();
+        if (*fail) break;
+        if (!mb_wait(barM, phM)) atomicExch(fail, 2);
+        phM ^= 1;
+        __syncthreads();
+        if (*fail) break;
+        tc_after();
+        if (!dblA && tid == 0 && Xn < a.V) issueA(Xn, 0);   // the single operator buffer is free again
+        if (warp < nq) {
+            uint32_t v[NP];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            if constexpr (NP == 32) tm_ld32(taddr, v);
+            else tm_ld16(taddr, v);
+            const int aa = warp * 16 + (lane & 15);
+            const bool im = lane >= 16;
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+                // Re row: y_re = ReB.Re x - ImB.Im x; Im row: y_im = ImB.Re x + ReB.Im x
+                const float pv = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[P + r]), 16);
+                float val = im ? __uint_as_float(v[r]) + pv : __uint_as_float(v[r]) - pv;
+                if (r < a.nrhs) {
+                    const size_t o = ((size_t)r * a.V + X) * nc + aa;
+                    float* yo = reinterpret_cast<float*>(a.y + o) + (im ? 1 : 0);
+                    if (a.b) val = reinterpret_cast<const float*>(a.b + o)[im ? 1 : 0] - val;
+                    *yo = val;
+                }
+            }
+        }
+        tc_before();
+        __syncthreads();
+        tc_after();
+    }
+    if (*fail && tid == 0) {
+        // drain our own bulk copies before the shared memory goes away
+        for (int s2 = 0; s2 < 2; ++s2) {
+            if (pendA[s2]) mb_wait(&barA[s2], phA[s2]);
+            if (pendB[s2]) mb_wait(&barB[s2], phB[s2]);
+        }
+        atomicExch(a.err, 1);
+    }
     tc_before();
     __syncthreads();
     tc_after();
-    if (warp == 5) tm_dealloc(tmem, 64);
+    if (warp == 0) tm_dealloc(tmem, 32);
 }
 
-// operator image, per site nine chunks (direction d), each [k group][row group][8][8]:
-// row m = 32 w + l holds Re (l < 16) or Im (l >= 16) of B[X][16 w + l % 16][d][col]
+// operator image: row m = 32 w + l holds Re (l < 16) or Im (l >= 16) of
+// B[X][16 w + l % 16][d][col], column k = d * nc + col
 __global__ void tc_image_kernel(int V, int nc, const float2* __restrict__ B, __nv_bfloat16* img) {
-    const int K = 9 * nc, mgv = 2 * nc / 8;
+    const int K = 9 * nc, kg = K / 8;
     const size_t per = (size_t)2 * nc * K;
     const size_t n = (size_t)V * per;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t X = i / per;
         const int e = (int)(i - X * per);
         const int m = e / K, k = e - m * K;
-        const int d = k / nc, col = k - d * nc;
         const int row = (m >> 5) * 16 + (m & 15);
         const float2 v = B[((size_t)X * nc + row) * K + k];   // [X][row][d][col] = [X][row][k]
-        const size_t off = (size_t)d * 2 * nc * nc + ((size_t)(col >> 3) * mgv + (m >> 3)) * 64 + (m & 7) * 8 + (col & 7);
-        img[X * per + off] = __float2bfloat16((m & 16) ? v.y : v.x);
+        img[X * per + core_off(m, k, kg)] = __float2bfloat16((m & 16) ? v.y : v.x);
     }
 }
 
@@ -376,18 +346,24 @@ cudaError_t launch_coarse_apply_tc(const GeomH& g, int nc, const void* img, cons
     a.y = (float2*)y;
     a.b = (const float2*)b;
     a.err = err;
-    const int NP = 2 * a.P, mgv = 2 * nc / 8;
-    TcPlan pl;
-    pl.a_chunk = 2 * nc * nc * 2;
-    pl.b_chunk = nc * NP * 2;
-    const int over = (16 - mgv) * 128;   // reach of an operator descriptor past A_d
-    pl.stride = (pl.a_chunk + (pl.b_chunk > over ? pl.b_chunk : over) + 127) / 128 * 128;
-    const int kBudget = 200 * 1024;
-    pl.slots = kBudget / pl.stride;
-    if (pl.slots > 24) pl.slots = 24;
-    if (pl.slots < 2) return cudaErrorInvalidValue;
-    pl.bar = pl.slots * pl.stride;
-    pl.bytes = pl.bar + (2 * pl.slots + 4) * 8 + 16;
+    const int K = 9 * nc, kg = K / 8, NP = 2 * a.P;
+    const int a_data = 2 * nc * K * 2, a_span = 16 * kg * 128, b_bytes = K * NP * 2;
+    const int kMax = 227 * 1024;
+    auto plan = [&](bool dbl) {
+        TcPlan p;
+        p.a0 = 0;
+        p.a1 = dbl ? a_data : 0;
+        p.b0 = p.a1 + a_data;
+        p.b1 = p.b0 + b_bytes;
+        p.bar = p.b1 + b_bytes;
+        const int end = p.bar + 5 * 8 + 8;
+        const int span = p.a1 + a_span;   // reach of the last operator descriptor
+        p.bytes = ((end > span ? end : span) + 127) / 128 * 128;
+        return p;
+    };
+    TcPlan pl = plan(true);
+    if (pl.bytes > kMax) pl = plan(false);
+    if (pl.bytes > kMax) return cudaErrorInvalidValue;
     (note_launch(), tc_pack_kernel<<<tc_sms() * 8, 256, 0, st>>>(g.V, nc, nrhs, a.P, (const float2*)x,
                                                                  (__nv_bfloat16*)xpack));
     const void* fn = NP == 32 ? (const void*)coarse_tc_kernel<32> : (const void*)coarse_tc_kernel<16>;
@@ -396,5 +372,5 @@ cudaError_t launch_coarse_apply_tc(const GeomH& g, int nc, const void* img, cons
     const int grid = g.V < tc_sms() ? g.V : tc_sms();
     void* params[] = {&a, &pl};
     note_launch();
-    return cudaLaunchKernel(fn, dim3(grid), dim3(192), params, pl.bytes, st);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kTcThreads), params, pl.bytes, st);
 }
