@@ -9,9 +9,11 @@
   x = 0, r = b, then n times {x += M_e r; r = b - Dx; x += M_o r; r = b - Dx}.
 * ``bicgstab_l``: BiCGStab(l) of Sleijpen and Fokkema, the coarse solver of
   step (1b).
-* ``fgmres``: flexible GMRES(m) (Saad 1993), the outer solver (the paper's
-  flexible BiCGStab is replaced by flexible GMRES(16); the true residual
-  b - Dx is recomputed at every restart, reading C13).
+* ``fgmres``: flexible GMRES(m) (Saad 1993), the default outer solver (the
+  true residual b - Dx is recomputed at every restart, reading C13).
+* ``fbicgstab``: the paper's outer solver, BiCGStab with flexible
+  preconditioning (Sec. 3), its listing's two misprints read as in the
+  standard method (reading C11).
 
 Inner products are <a, b> = a^dag b (numpy ``vdot``).
 """
@@ -192,6 +194,59 @@ def fgmres(apply_A, b, apply_M=None, m: int = 16, tol: float = 1e-10, maxit: int
             V.append(w / H[j + 1, j])
         for i, yi in enumerate(y):
             x = x + yi * Z[i]
+
+
+def fbicgstab(apply_A, b, apply_M=None, tol: float = 1e-10, maxit: int = 1000, x0=None):
+    """BiCGStab with flexible (right) preconditioning, the paper's outer
+    solver (Sec. 3), with the two misprints of its listing read as in the
+    standard method (reading C11): the second update of x adds omega M|s>,
+    and the new direction is |p> = |r'> + beta (|p> - omega D M |p>).
+    The recursive residual stops an iteration early ("small enough" =
+    relative tolerance tol); the true residual b - D x is then recomputed and
+    the method restarts from it if it is not yet below tol |b| (reading
+    C13).  info.iters counts iterations (two preconditioner calls each)."""
+    info = SolveInfo()
+    if apply_M is None:
+        apply_M = lambda v: v
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0:
+        info.converged = True
+        info.true_rel_residual = 0.0
+        return x, info
+    while True:
+        r = b - apply_A(x)
+        rn = np.linalg.norm(r)
+        info.true_rel_residual = rn / bnorm
+        info.history.append(rn / bnorm)
+        if rn <= tol * bnorm:
+            info.converged = True
+            return x, info
+        if info.iters >= maxit:
+            return x, info
+        rt = r.copy()
+        p = r.copy()
+        rho = np.vdot(rt, r)
+        while info.iters < maxit:
+            Mp = apply_M(p)
+            DMp = apply_A(Mp)
+            alpha = rho / np.vdot(rt, DMp)
+            x = x + alpha * Mp
+            s = r - alpha * DMp
+            info.iters += 1
+            if np.linalg.norm(s) <= tol * bnorm:
+                break
+            Ms = apply_M(s)
+            t = apply_A(Ms)
+            omega = np.vdot(t, s) / np.vdot(t, t)
+            x = x + omega * Ms
+            r = s - omega * t
+            if np.linalg.norm(r) <= tol * bnorm:
+                break
+            rho_new = np.vdot(rt, r)
+            beta = (alpha / omega) * rho_new / rho
+            rho = rho_new
+            p = r + beta * (p - omega * DMp)
 
 
 def gmres_dense_reference(A: np.ndarray, b: np.ndarray, k: int) -> np.ndarray:

@@ -47,6 +47,29 @@ def test_fgmres_restarts_to_tolerance():
     assert info.iters > 4   # it needed restarts
 
 
+def test_fbicgstab_matches_right_preconditioned_library_bicgstab():
+    # with a fixed linear M, the flexible iterates are M y_k where y_k are
+    # BiCGStab's iterates on A M y = b (scipy's implementation, x0 = 0)
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    A, b = _rand_system(80, 4)
+    rng = np.random.default_rng(9)
+    M = np.eye(80) + 0.2 * (rng.standard_normal((80, 80)) + 1j * rng.standard_normal((80, 80))) / np.sqrt(80)
+    for k in (1, 2, 3):
+        x, info = solvers.fbicgstab(lambda v: A @ v, b, lambda v: M @ v, tol=0.0, maxit=k)
+        y, _ = sla.bicgstab(A @ M, b, rtol=0.0, atol=0.0, maxiter=k)
+        assert np.linalg.norm(x - M @ y) <= 1e-11 * np.linalg.norm(x)
+
+
+def test_fbicgstab_converges_and_exact_preconditioner_one_step():
+    A, b = _rand_system(120, 5)
+    x, info = solvers.fbicgstab(lambda v: A @ v, b, None, tol=1e-12, maxit=500)
+    assert info.converged and info.true_rel_residual <= 1e-12
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(x)
+    Ainv = np.linalg.inv(A)
+    x, info = solvers.fbicgstab(lambda v: A @ v, b, lambda v: Ainv @ v, tol=1e-12, maxit=10)
+    assert info.converged and info.iters == 1
+
+
 def _dsap_domain_dense(op, block, mask):
     """D_SAP restricted to the sites in mask, as a dense matrix (unit vectors)."""
     idx = np.flatnonzero(np.repeat(mask.reshape(-1), 12))
