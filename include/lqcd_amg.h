@@ -97,6 +97,9 @@ typedef struct {
     int sap_variant;                    /* SAP kernel: -1 autotune at setup (times both, keeps the faster),
                                            0 operator read from global memory, 1 operator staged in shared
                                            memory (FP32/FP16, blocks <= 256 sites) [-1] */
+    int outer_solver;                   /* 0: flexible GMRES(outer_m) [0]; 1: the paper's BiCGStab with
+                                           flexible preconditioning (Sec. 3), one right-hand side at a
+                                           time; both stop on the FP64 true residual */
 } amg_params;
 
 typedef struct {
@@ -112,6 +115,8 @@ typedef struct {
     int coarse_cycles;          /* total BiCGStab(l) cycles on the coarsest level */
     int used_nn;                /* 1 if the learned correction was part of the preconditioner */
     int nn_fallback;            /* 1 if the solve was redone with the plain cycle */
+    int cycles;                 /* preconditioner applications (= iters for flexible GMRES, two per
+                                   iteration for flexible BiCGStab); largest over a batch */
 } amg_solve_info;
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -48,6 +48,7 @@ class amg_params(ctypes.Structure):
         ("prec_coarse", ctypes.c_int),
         ("prec_coarsest", ctypes.c_int),
         ("sap_variant", ctypes.c_int),
+        ("outer_solver", ctypes.c_int),
     ]
 
 
@@ -65,6 +66,7 @@ class amg_solve_info(ctypes.Structure):
         ("coarse_cycles", ctypes.c_int),
         ("used_nn", ctypes.c_int),
         ("nn_fallback", ctypes.c_int),
+        ("cycles", ctypes.c_int),
     ]
 
     def as_dict(self):

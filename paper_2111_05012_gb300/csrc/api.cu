@@ -196,6 +196,7 @@ struct amg_hierarchy {
     // outer FGMRES (FP64 internal fine vectors)
     DevBuf ob, ox, ow, orr;
     std::vector<DevBuf*> oV, oZ;
+    DevBuf bv[6], bz[2];   // flexible BiCGStab: r, r~, p, s, t, D M p (FP64); M p, M s (Z precision)
     DevBuf canon;   // canonical staging
     Reducer red;
     PhaseTimer timer;
@@ -275,6 +276,7 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
         return fail(AMG_EINVAL, "a bfloat16 coarsest operator needs an even number of test vectors");
     if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
+    if (p->outer_solver != 0 && p->outer_solver != 1) return fail(AMG_EINVAL, "outer_solver must be 0 or 1");
     if (p->sap_iters < 0 || p->mr_iters < 0) return fail(AMG_EINVAL, "sap_iters / mr_iters");
     return AMG_OK;
 }
@@ -806,6 +808,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
     for (int q = 0; q < nb; ++q) {
         std::memset(&infos[q], 0, sizeof(amg_solve_info));
         infos[q].iters = st[q].iters;
+        infos[q].cycles = st[q].iters;
         infos[q].restarts = st[q].restarts;
         infos[q].converged = st[q].conv ? 1 : 0;
         infos[q].true_rel_residual = st[q].bnorm == 0 ? 0.0 : st[q].rel;
@@ -864,6 +867,10 @@ amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
     while ((int)h->oZ.size() < h->p.outer_m) h->oZ.push_back(new DevBuf());
     for (auto* v : h->oV) CK(v->ensure(fb64));
     for (auto* z : h->oZ) CK(z->ensure(fine_spinor_bytes(h->fp == 0 ? 0 : 1, g.V) * nb));
+    if (h->p.outer_solver == 1) {
+        for (auto& v : h->bv) CK(v.ensure(fine_spinor_bytes(0, g.V)));
+        for (auto& z : h->bz) CK(z.ensure(fine_spinor_bytes(h->fp == 0 ? 0 : 1, g.V)));
+    }
     h->nb_cap = nb > h->nb_cap ? nb : h->nb_cap;
     return AMG_OK;
 }
@@ -1093,6 +1100,126 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
         return st;
     }
     return AMG_OK;
+}
+
+// ---------------------------------------------------------------- flexible BiCGStab
+// The paper's outer solver (Sec. 3): BiCGStab with the multigrid cycle as a
+// flexible right preconditioner, two cycles and two Arnoldi-accurate products
+// per iteration; the listing's misprints are read as in the standard method
+// (x += omega M s, p = r + beta (p - omega D M p); reading C11).  The
+// recursive residual ends an iteration sequence; the FP64 true residual
+// b - D x then decides, and the method restarts from it if needed (C13).
+// One right-hand side (field 0 of the outer workspaces).
+amg_status fbicgstab(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, double tol, int maxit,
+                     amg_solve_info& info, cudaStream_t s) {
+    const size_t n = fine_n(h), fs = fsz(h, 0);
+    Reducer& red = h->red;
+    void *r = h->bv[0].p, *rt = h->bv[1].p, *p = h->bv[2].p, *sv = h->bv[3].p, *t = h->bv[4].p, *dmp = h->bv[5].p;
+    void *Mp = h->bz[0].p, *Ms = h->bz[1].p;
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+    auto add_z = [&](cplx c, const void* z) -> amg_status {   // x += c z
+        double2 cc = d2(c);
+        const void* zl[1] = {z};
+        if (zprec_of(h) == 0) CK(launch_multi_axpy(0, 1, &cc, zl, x, n, s));
+        else CK(launch_spinor_axpy_mixed(fine_geom(h), 1, &cc, zl, x, s));
+        return AMG_OK;
+    };
+    std::memset(&info, 0, sizeof(info));
+    double bn2;
+    TRY(red.norm2(0, b, n, &bn2, s));
+    if (!std::isfinite(bn2)) return fail(AMG_NAN, "outer solve: non-finite right-hand side");
+    const double bn = std::sqrt(bn2);
+    if (bn == 0) {
+        CK(cudaMemsetAsync(x, 0, fs, s));
+        info.converged = 1;
+        return AMG_OK;
+    }
+    bool x_is_zero = !x_nonzero;
+    int iters = 0;
+    while (true) {
+        double rn;
+        if (x_is_zero) {
+            CK(cudaMemcpyAsync(r, b, fs, cudaMemcpyDeviceToDevice, s));
+            rn = bn;
+            x_is_zero = false;
+        } else {
+            TRY(fine_D(h, 0, x, r, b, 1, s));
+            double rn2;
+            TRY(red.norm2(0, r, n, &rn2, s));
+            rn = std::sqrt(rn2);
+        }
+        if (!std::isfinite(rn)) return fail(AMG_NAN, "outer solve: non-finite residual");
+        info.true_rel_residual = rn / bn;
+        if (rn <= tol * bn) {
+            info.converged = 1;
+            break;
+        }
+        if (iters >= maxit) break;
+        if (iters > 0) info.restarts++;
+        CK(cudaMemcpyAsync(rt, r, fs, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(p, r, fs, cudaMemcpyDeviceToDevice, s));
+        cplx rho = cplx(rn * rn, 0);
+        while (iters < maxit) {
+            TRY(precondition64(h, p, Mp, 1, s));
+            ++info.cycles;
+            TRY(arnoldi_D(h, Mp, dmp, 1, s));
+            cplx den;
+            TRY(red.dot(0, rt, dmp, n, &den, s));
+            TRY(coarse_status(h));
+            const cplx alpha = rho / den;
+            if (!std::isfinite(alpha.real()) || !std::isfinite(alpha.imag()))
+                return fail(AMG_NAN, "outer solve: BiCGStab breakdown");
+            TRY(add_z(alpha, Mp));
+            CK(cudaMemcpyAsync(sv, r, fs, cudaMemcpyDeviceToDevice, s));
+            CK(launch_axpby(0, d2(-alpha), dmp, one, sv, n, s));
+            ++iters;
+            double sn2;
+            TRY(red.norm2(0, sv, n, &sn2, s));
+            if (std::sqrt(sn2) <= tol * bn) break;
+            TRY(precondition64(h, sv, Ms, 1, s));
+            ++info.cycles;
+            TRY(arnoldi_D(h, Ms, t, 1, s));
+            cplx ts;
+            double tt;
+            TRY(red.dot(0, t, sv, n, &ts, s));
+            TRY(red.norm2(0, t, n, &tt, s));
+            TRY(coarse_status(h));
+            const cplx omega = ts / tt;
+            if (!(tt > 0) || !std::isfinite(omega.real())) return fail(AMG_NAN, "outer solve: BiCGStab breakdown");
+            TRY(add_z(omega, Ms));
+            CK(cudaMemcpyAsync(r, sv, fs, cudaMemcpyDeviceToDevice, s));
+            CK(launch_axpby(0, d2(-omega), t, one, r, n, s));
+            // <r~, r> and |r|^2 in one pass
+            const void* al[1] = {rt};
+            CK(launch_multi_dot_norm(0, 1, al, r, n, red.dpart.as<double2>(), s));
+            CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double2) * 2 * red.grid, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            cplx rho_new(0, 0);
+            double rr = 0;
+            for (int q = 0; q < red.grid; ++q) {
+                rho_new += cplx(red.hpart[q].x, red.hpart[q].y);
+                rr += red.hpart[red.grid + q].x;
+            }
+            if (std::sqrt(rr) <= tol * bn) break;
+            const cplx beta = (alpha / omega) * (rho_new / rho);
+            rho = rho_new;
+            // p = r + beta (p - omega D M p)
+            CK(launch_axpby(0, d2(-beta * omega), dmp, d2(beta), p, n, s));
+            CK(launch_axpby(0, one, r, one, p, n, s));
+            (void)zero;
+        }
+    }
+    info.iters = iters;
+    return info.converged ? AMG_OK : AMG_NOT_CONVERGED;
+}
+
+// the outer solver chosen by the parameters (flexible BiCGStab: nb == 1)
+amg_status outer_solve(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonzero, double tol, int maxit,
+                       std::vector<amg_solve_info>& infos, cudaStream_t s) {
+    if (h->p.outer_solver == 0) return fgmres(h, nb, b, x, x_nonzero, tol, maxit, infos, s);
+    if (nb != 1) return fail(AMG_EINVAL, "flexible BiCGStab solves one right-hand side at a time");
+    infos.assign(1, amg_solve_info());
+    return fbicgstab(h, b, x, x_nonzero, tol, maxit, infos[0], s);
 }
 
 // ---------------------------------------------------------------- ragged batch
@@ -1348,6 +1475,7 @@ void amg_params_default(amg_params* p) {
     p->prec_coarse = AMG_F32;
     p->prec_coarsest = AMG_F32;
     p->sap_variant = -1;
+    p->outer_solver = 0;
 }
 
 amg_status amg_lattice_create(const int dims[4], int antiperiodic_t, amg_lattice** out) {
@@ -1879,7 +2007,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     // right-hand sides solved in lockstep: up to 12, fewer if the batch's
     // workspaces (FGMRES basis, Z vectors, cycle fields) would not fit in 80%
     // of the free device memory
-    int kMaxBatch = 12;
+    int kMaxBatch = h->p.outer_solver == 1 ? 1 : 12;
     {
         const size_t f64 = fine_spinor_bytes(0, g.V), fz = fine_spinor_bytes(zprec_of(h), g.V);
         size_t per = f64 * (h->p.outer_m + 1 + 4) + fz * h->p.outer_m;
@@ -1911,7 +2039,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
         else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
         std::vector<amg_solve_info> infos;
-        amg_status rs = fgmres(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
+        amg_status rs = outer_solve(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
         int used_nn = (h->nn && !h->nn_off) ? 1 : 0, fell_back = 0;
         if (used_nn && (rs == AMG_NOT_CONVERGED || rs == AMG_NAN)) {
             // the FP64 residual rejects the learned correction: solve again with the plain cycle
@@ -1921,7 +2049,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
             if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
             else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
             std::memset(h->hstate, 0, 16 * 16);
-            rs = fgmres(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
+            rs = outer_solve(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
             h->nn_off = false;
             for (auto& i : infos) i.iters += prev;
             used_nn = 0;
@@ -1936,6 +2064,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         if (rs == AMG_NOT_CONVERGED) worst = rs;
         for (auto& i : infos) {
             agg.iters = std::max(agg.iters, i.iters);
+            agg.cycles = std::max(agg.cycles, i.cycles);
             agg.restarts = std::max(agg.restarts, i.restarts);
             agg.converged = agg.converged && i.converged;
             agg.true_rel_residual = std::max(agg.true_rel_residual, i.true_rel_residual);
@@ -1966,6 +2095,7 @@ amg_status amg_solve_ragged(amg_hierarchy* const* hs, const double* const* b, do
         if (!hs[i] || !b[i] || !x[i]) return fail(AMG_EINVAL, "NULL hierarchy or vector");
         if (hs[i]->p.nlevels != 2) return fail(AMG_EINVAL, "ragged solves take two-grid hierarchies");
         if (hs[i]->nn) return fail(AMG_EINVAL, "ragged solves take hierarchies without a learned correction");
+        if (hs[i]->p.outer_solver != 0) return fail(AMG_EINVAL, "ragged solves use the flexible GMRES outer solver");
         for (int k = 0; k < i; ++k)
             if (hs[k] == hs[i]) return fail(AMG_EINVAL, "a hierarchy appears twice in the ragged batch");
     }
@@ -2018,6 +2148,7 @@ amg_status amg_solve_ragged(amg_hierarchy* const* hs, const double* const* b, do
         if (infos) {
             std::memset(&infos[i], 0, sizeof(amg_solve_info));
             infos[i].iters = r.iters;
+            infos[i].cycles = r.iters;
             infos[i].restarts = r.restarts;
             infos[i].converged = r.conv ? 1 : 0;
             infos[i].true_rel_residual = r.bnorm == 0 ? 0.0 : r.rel;

@@ -275,3 +275,32 @@ def test_twelve_point_sources_in_one_batched_solve():
         assert np.linalg.norm(one - xs[k]) <= 1e-8 * np.linalg.norm(one)
     c.amg_hierarchy_destroy(h)
     f.close()
+
+
+def test_flexible_bicgstab_outer_solver(mgcase):
+    # the paper's outer solver: FP64 iterates after two iterations match the
+    # oracle's flexible BiCGStab preconditioned by its own cycle; solves reach
+    # the FP64 tolerance in every precision
+    import torch
+    f = mgcase
+    c = f.c
+    p = _params(c, f.block, f.nvec, 0, outer_solver=1)
+    h = c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(f.v0)])
+    hier = oamg.Hierarchy(f.op, oamg.AMGParams(blocks=[f.block], nvecs=[f.nvec]))
+    hier.set_vectors([f.v0.reshape((f.nvec,) + f.shape4 + (12,))])
+    b = li.rhs(f.dims, 21).reshape(f.shape4 + (12,))
+    ref, _ = osol.fbicgstab(f.op.apply, b, lambda v: hier.vcycle(0, v), tol=1e-10, maxit=2)
+    x = to_dev(b) * 0
+    st, info = c.amg_solve(h, to_dev(b), x, 1, 1e-10, 2, raise_on_nonconv=False)
+    assert info.iters == 2
+    assert rel(from_dev(x, f.shape4 + (12,)), ref) < 1e-8
+    c.amg_hierarchy_destroy(h)
+    for prec in (0, 1, 2):
+        p = _params(c, f.block, f.nvec, prec, outer_solver=1)
+        h = c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(f.v0)])
+        x = to_dev(b) * 0
+        st, info = c.amg_solve(h, to_dev(b), x, 1, 1e-10, 100)
+        assert info.converged == 1 and info.true_rel_residual <= 1e-10
+        r = b - f.op.apply(from_dev(x, f.shape4 + (12,)))
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
+        c.amg_hierarchy_destroy(h)
