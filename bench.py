@@ -106,9 +106,10 @@ def dist_info():
     return rank, world, local
 
 
-def make_params(capi, prec_smoother, coarse="f32", outer="fgmres"):
+def make_params(capi, prec_smoother, coarse="f32", outer="fgmres", sap_variant=-1):
     p = capi.amg_params_default()
     p.outer_solver = 1 if outer == "fbicgstab" else 0
+    p.sap_variant = sap_variant
     p.nlevels = 2
     for mu in range(4):
         p.block[0][mu] = WORKLOAD["block"][mu]
@@ -591,6 +592,8 @@ def main():
     ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--sap-variant", type=int, default=-1, choices=[-1, 0, 1],
+                    help="SAP kernel of the solve16 workload: -1 autotune, 0 operator from global memory, 1 staged")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "fbicgstab"],
                     help="outer solver of the solve16 workload (fbicgstab: the paper's flexible BiCGStab)")
     ap.add_argument("--coarse-prec", default="f32", choices=["f32", "bf16"],
@@ -637,7 +640,7 @@ def main():
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = capi.amg_setup(d, make_params(capi, prec, args.coarse_prec, args.outer), [v0])
+    h = capi.amg_setup(d, make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant), [v0])
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
 
@@ -702,7 +705,7 @@ def main():
     # sites are active per launch.  12.8 flop/byte puts it on the ALU side of
     # the ridge, so it is reported against the FP32 FMA peak:
     # 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (nominal).
-    p = make_params(capi, prec, args.coarse_prec, args.outer)
+    p = make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant)
     iters = np.mean([i["iters"] for i in infos])
     smooth_ms = np.mean([i["ms_smoother"] for i in infos])
     cycles = np.mean([i["cycles"] for i in infos])

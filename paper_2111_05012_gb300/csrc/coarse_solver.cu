@@ -413,9 +413,15 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
     }
     // BiCG scalars in the solver's precision: identical in every thread
     using SC = TC;
+    // n / d with both scaled by max(|d.re|, |d.im|) first: the BiCG scalars are
+    // squares of the residual scale, so |d|^2 would underflow (FP32) for the
+    // small right-hand sides a non-normalising outer solver hands down
     auto cdiv = [](cx<SC> n, cx<SC> d) -> cx<SC> {
-        const SC inv = SC(1) / norm2(d);
-        return {(n.re * d.re + n.im * d.im) * inv, (n.im * d.re - n.re * d.im) * inv};
+        const SC m = fmax(fabs(d.re), fabs(d.im));
+        const SC sc = m > SC(0) ? SC(1) / m : SC(1);
+        const cx<SC> ds = {d.re * sc, d.im * sc}, ns = {n.re * sc, n.im * sc};
+        const SC inv = SC(1) / norm2(ds);
+        return {(ns.re * ds.re + ns.im * ds.im) * inv, (ns.im * ds.re - ns.re * ds.im) * inv};
     };
     cx<SC> rho0 = {SC(1), SC(0)}, alpha = {SC(0), SC(0)}, omega = {SC(1), SC(0)};
     double bn2 = -1;
