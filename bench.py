@@ -571,8 +571,10 @@ def run_coarse_tc(args):
                                    "vectors), bfloat16 stencil, 16 right-hand sides per tensor-core launch",
                        "coarse_sites": Vc, "nc": nc, "l2": "operator image 680 MB > L2 (no flush)",
                        "variants": res},
+            # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one coarse_tc_kernel<32> launch (16 RHS)
+            # on this workload from an ncu --set full capture (708.8 + 47.6 MB)
             "roofline": {"kernel": "coarse_tc_kernel<32>", "bound": "hbm", "achieved": t["gb_per_s"], "peak": hbm,
-                         "unit": "GB/s", "frac": t["frac_hbm"], "traffic": None, "peak_kind": kind},
+                         "unit": "GB/s", "frac": t["frac_hbm"], "traffic": 756.4e6, "peak_kind": kind},
             "gpu_launches": t["launches"], "clocks": clk.summary()}
     capi.amg_hierarchy_destroy(h)
     capi.amg_dirac_destroy(d)
@@ -592,8 +594,9 @@ def main():
     ap.add_argument("--workload", default="solve16", choices=["solve16", "propagator", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--sap-variant", type=int, default=-1, choices=[-1, 0, 1],
-                    help="SAP kernel of the solve16 workload: -1 autotune, 0 operator from global memory, 1 staged")
+    ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1],
+                    help="SAP kernel of the solve16 workload: 0 operator through L1/L2 (default; the two "
+                         "measure within 1 %% on this workload), 1 staged in shared memory, -1 autotune")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "fbicgstab"],
                     help="outer solver of the solve16 workload (fbicgstab: the paper's flexible BiCGStab)")
     ap.add_argument("--coarse-prec", default="f32", choices=["f32", "bf16"],
@@ -731,8 +734,12 @@ def main():
                    "phase_ms": {k: float(np.mean([i[k] for i in infos])) for k in
                                 ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other")},
                    "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
-        "roofline": {"kernel": "sap_half_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one sap_half_kernel<P32,256> launch on this
+        # workload, from an ncu --set full capture of this kernel (91.14 + 3.06 MB); only for variant 0
+        "roofline": {"kernel": "sap_half_kernel<P32,256>" if args.sap_variant == 0 else "sap_half (autotuned)",
+                     "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": 94.2e6 if (args.sap_variant == 0 and args.prec == "f32") else None,
                      "peak_kind": "FP32 FMA nominal from unit counts and 2.07 GHz",
                      "avg_launch_us": sap_launch_us, "flop_per_launch": flop_launch,
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind},
