@@ -106,10 +106,13 @@ def dist_info():
     return rank, world, local
 
 
-def make_params(capi, prec_smoother, coarse="f32", outer="fgmres", sap_variant=-1):
+def make_params(capi, prec_smoother, coarse="f32", outer="fgmres", sap_variant=-1, setup=None):
     p = capi.amg_params_default()
     p.outer_solver = 1 if outer == "fbicgstab" else 0
     p.sap_variant = sap_variant
+    for k, v in (setup or {}).items():
+        if v is not None:
+            setattr(p, k, v)
     p.nlevels = 2
     for mu in range(4):
         p.block[0][mu] = WORKLOAD["block"][mu]
@@ -597,6 +600,9 @@ def main():
     ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1],
                     help="SAP kernel of the solve16 workload: 0 operator through L1/L2 (default; the two "
                          "measure within 1 %% on this workload), 1 staged in shared memory, -1 autotune")
+    ap.add_argument("--n-init", type=int, default=None, help="setup (0-a) SAP applications (default: library's)")
+    ap.add_argument("--n-adapt", type=int, default=None, help="setup (0-b) adaptive passes (default: library's)")
+    ap.add_argument("--coarse-tol", type=float, default=None, help="coarsest solve tolerance (default: library's)")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "fbicgstab"],
                     help="outer solver of the solve16 workload (fbicgstab: the paper's flexible BiCGStab)")
     ap.add_argument("--coarse-prec", default="f32", choices=["f32", "bf16"],
@@ -643,7 +649,8 @@ def main():
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = capi.amg_setup(d, make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant), [v0])
+    setup_kw = {"n_init": args.n_init, "n_adapt": args.n_adapt, "coarse_tol": args.coarse_tol}
+    h = capi.amg_setup(d, make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant, setup_kw), [v0])
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
 
@@ -708,7 +715,7 @@ def main():
     # sites are active per launch.  12.8 flop/byte puts it on the ALU side of
     # the ridge, so it is reported against the FP32 FMA peak:
     # 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (nominal).
-    p = make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant)
+    p = make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant, setup_kw)
     iters = np.mean([i["iters"] for i in infos])
     smooth_ms = np.mean([i["ms_smoother"] for i in infos])
     cycles = np.mean([i["cycles"] for i in infos])
@@ -729,6 +736,7 @@ def main():
                                "2-level AMG 4^4 blocks, 24 test vectors, SAP(4) x MR(6), BiCGStab(2) coarse to 1e-2, "
                                "FGMRES(16) FP64 outer, 1 Gaussian RHS per step",
                    "smoother_prec": args.prec, "coarse_prec": args.coarse_prec, "outer_solver": args.outer,
+                   "n_init": p.n_init, "n_adapt": p.n_adapt, "coarse_tol": p.coarse_tol,
                    "setup_ms": setup_ms, "l2": "working set > L2 (no flush)",
                    "outer_iters": float(iters), "cycles": float(cycles), "converged": ok,
                    "phase_ms": {k: float(np.mean([i[k] for i in infos])) for k in
