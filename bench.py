@@ -236,8 +236,8 @@ def run_learned(args):
     """Learned preconditioner on 24^3x48 (exp(0.6iH), seed 5, kappa 0.130):
     train the 1-4-1 parallel-transport network on 4096 (residual, error)
     pairs from the solver (e = (1 - M D) e0, r = D e), streamed in batches of
-    16, then solve 16 fresh Gaussian right-hand sides (seeds 5000-5015) with
-    and without it."""
+    16, then solve 16 fresh Gaussian right-hand sides (seeds 4000-4015) with
+    and without it, and with the same method all in FP64."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -280,8 +280,20 @@ def run_learned(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     res = {}
-    for mode in ("plain", "learned"):
-        capi.amg_hierarchy_set_nn(h, nn if mode == "learned" else None)
+    modes = [("plain", h), ("learned", h)]
+    if not args.no_fp64_compare:
+        # the same method all in FP64 (smoother, coarse operator and solve), same initial test vectors
+        p64 = capi.amg_params_default()
+        p64.nvec[0] = 24
+        p64.prec_smoother = p64.prec_coarsest = capi.AMG_F64
+        t0 = time.perf_counter()
+        h64 = capi.amg_setup(d, p64, [v0])
+        torch.cuda.synchronize()
+        res["fp64_setup_s"] = time.perf_counter() - t0
+        modes.append(("plain_fp64", h64))
+    for mode, hh in modes:
+        if mode != "plain_fp64":
+            capi.amg_hierarchy_set_nn(hh, nn if mode == "learned" else None)
         its, ms_l, rel = [], [], []
         for k in range(16):
             bb = torch.from_numpy(li.to_interleaved(li.rhs(dims, 5000 + k - 1000)).reshape(-1)).cuda()
@@ -289,7 +301,7 @@ def run_learned(args):
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
-            st, info = capi.amg_solve(h, bb, x, 1, TOL, 300)
+            st, info = capi.amg_solve(hh, bb, x, 1, TOL, 300)
             ev1.record()
             torch.cuda.synchronize()
             its.append(info.iters)
@@ -297,13 +309,16 @@ def run_learned(args):
             rel.append(info.true_rel_residual)
         res[mode] = {"ms_per_rhs": float(np.mean(ms_l)), "outer_iters": float(np.mean(its)),
                      "max_true_rel_residual": float(np.max(rel)), "fallbacks": int(info.nn_fallback)}
+        if mode == "plain_fp64":
+            capi.amg_hierarchy_destroy(hh)
     line = {"metric": METRIC, "value": res["learned"]["ms_per_rhs"], "unit": "ms/RHS", "n_gpus": 1, "steps": 16,
             "warmup": 0, "ms_per_step": res["learned"]["ms_per_rhs"], "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights + f32 + f64", "data": "synthetic",
             "config": {"workload": "24^3x48 Wilson-clover (exp(0.6iH), seed 5, kappa 0.130, csw 1.0), 2-level AMG "
                                    "4^4 / 24 test vectors + 1-4-1 PT-conv network",
                        "pairs": npairs, "train_s": train_s, "loss_first": losses[0], "loss_last": losses[-1],
-                       "plain": res["plain"], "learned": res["learned"]}}
+                       "plain": res["plain"], "learned": res["learned"],
+                       "plain_fp64": res.get("plain_fp64"), "fp64_setup_s": res.get("fp64_setup_s")}}
     print(json.dumps(line), flush=True)
 
 
@@ -502,6 +517,32 @@ def run_ragged(args):
         seq.append(info.converged == 1 and info.true_rel_residual <= TOL)
     torch.cuda.synchronize()
     seq_ms = (time.perf_counter() - t0) * 1e3
+    # the plain method all in FP64 on a sample of the batch (two problems of each size), one after another
+    fp64 = None
+    if not args.no_fp64_compare:
+        sample = list(range(6))
+        h64 = []
+        for i in sample:
+            dims, block = shapes[i % 3]
+            p = capi.amg_params_default()
+            for mu in range(4):
+                p.block[0][mu] = block[mu]
+            p.nvec[0] = 24
+            p.prec_smoother = p.prec_coarsest = capi.AMG_F64
+            h64.append(capi.amg_setup(probs[i][3], p, [init[dims]]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok64 = []
+        for i, hh in zip(sample, h64):
+            x = torch.zeros_like(B[i])
+            st, info = capi.amg_solve(hh, B[i], x, 1, TOL, 300, stream=stream)
+            ok64.append(info.converged == 1 and info.true_rel_residual <= TOL)
+        torch.cuda.synchronize()
+        ms64 = (time.perf_counter() - t0) * 1e3
+        for hh in h64:
+            capi.amg_hierarchy_destroy(hh)
+        fp64 = {"problems": sample, "ms_per_rhs": ms64 / len(sample), "converged": all(ok64),
+                "ragged_ms_per_rhs_same_mix": ragged_ms / n}
     line = {"metric": METRIC, "value": ragged_ms / n, "unit": "ms/RHS", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": ragged_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
@@ -510,7 +551,7 @@ def run_ragged(args):
                                    "FP32 smoother, lockstep FGMRES(16) on 16 streams with CUDA-graph steps",
                        "problems": n, "total_sites": sites, "setup_s": setup_s, "converged": ok,
                        "ragged_ms": ragged_ms, "sequential_ms": seq_ms, "sequential_converged": all(seq),
-                       "speedup_vs_sequential": seq_ms / ragged_ms,
+                       "speedup_vs_sequential": seq_ms / ragged_ms, "plain_fp64_sequential_sample": fp64,
                        "outer_iters": [int(i.iters) for i in infos]},
             "gpu_launches": launches, "clocks": clk.summary()}
     for dims, lat, g, d, h in probs:
@@ -744,7 +785,8 @@ def main():
                    "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one sap_half_kernel<P32,256> launch on this
         # workload, from an ncu --set full capture of this kernel (91.14 + 3.06 MB); only for variant 0
-        "roofline": {"kernel": "sap_half_kernel<P32,256>" if args.sap_variant == 0 else "sap_half (autotuned)",
+        "roofline": {"kernel": {0: "sap_half_kernel<P32,256>",
+                                1: "sap_half_staged_kernel<P32>"}.get(args.sap_variant, "sap_half (autotuned)"),
                      "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": 94.2e6 if (args.sap_variant == 0 and args.prec == "f32") else None,
