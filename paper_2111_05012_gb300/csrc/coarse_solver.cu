@@ -12,9 +12,10 @@
 // Gram matrix of R_0..R_l (one reduction) instead of sequential projections.
 //
 // The stencil streams the CTA's contiguous slice of the coarse operator
-// through a 4-stage shared-memory ring filled by bulk asynchronous copies
-// (cp.async.bulk, completion counted on mbarriers); neighbour vector entries
-// are read through L2.
+// through a 3-stage shared-memory ring filled by bulk asynchronous copies
+// (cp.async.bulk, completion counted on mbarriers); the neighbour vector
+// segments a chunk needs ride in the same ring slot, one bulk copy per
+// (site, direction).
 //
 // Grid barriers and mbarrier waits spin with a bounded count; on timeout the
 // kernel records AMG_TIMEOUT in the status word and every CTA returns.
@@ -30,6 +31,7 @@ constexpr int kMaxQ = (kMaxEll + 1) * (kMaxEll + 1) + 2;   // reduced quantities
 constexpr long long kSpinLimit = 40000000;                    // ~ seconds of polling
 constexpr int kStages = 3;                                    // bulk-copy ring depth
 constexpr int kChunkBytes = 55296;                            // operator bytes per ring slot (16 FP32 rows, Nc 48)
+constexpr int kMaxRowsPerWarp = 4;                            // rows of one chunk per warp (the launcher checks)
 
 struct GridBar {
     unsigned count;
@@ -189,10 +191,24 @@ DEV bool grid_reduce(const Args& a, cx<AT> (&v)[NQ], int nq, cx<double>* red_sh,
     // one warp per quantity, lanes stride over the CTA partials (fixed order)
     for (int q = warp; q < nq; q += kWarps) {
         double re = 0, im = 0;
-        for (int i = lane; i < (int)gridDim.x; i += 32) {
-            double2 t = __ldcg(a.part + (size_t)q * gridDim.x + i);
-            re += t.x;
-            im += t.y;
+        // up to 8 partials per lane (grids of <= 256 CTAs), loaded before any is summed so
+        // that the L2 round trips overlap; the order of the sum is fixed
+        constexpr int kPer = 8;
+        double2 t[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = lane + 32 * k;
+            t[k] = i < (int)gridDim.x ? __ldcg(a.part + (size_t)q * gridDim.x + i) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            re += t[k].x;
+            im += t[k].y;
+        }
+        for (int i = lane + 32 * kPer; i < (int)gridDim.x; i += 32) {
+            double2 u = __ldcg(a.part + (size_t)q * gridDim.x + i);
+            re += u.x;
+            im += u.y;
         }
         re = warp_sum(re);
         im = warp_sum(im);
@@ -212,28 +228,6 @@ DEV void my_rows(int nrows, int& r0, int& r1) {
 
 // y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA
 // (one warp per row); returns per-thread partial <w, y> if w != nullptr.
-// two adjacent complex numbers: one 16-byte load (FP32) or two (FP64)
-DEV void ld_pair_g(const float* p, size_t i, cx<float>& a, cx<float>& b) {
-    float4 t = __ldg((const float4*)p + i);
-    a = {t.x, t.y};
-    b = {t.z, t.w};
-}
-DEV void ld_pair_g(const double* p, size_t i, cx<double>& a, cx<double>& b) {
-    double2 t0 = __ldg((const double2*)p + 2 * i), t1 = __ldg((const double2*)p + 2 * i + 1);
-    a = {t0.x, t0.y};
-    b = {t1.x, t1.y};
-}
-DEV void ld_pair_cg(const float* p, size_t i, cx<float>& a, cx<float>& b) {
-    float4 t = __ldcg((const float4*)p + i);
-    a = {t.x, t.y};
-    b = {t.z, t.w};
-}
-DEV void ld_pair_cg(const double* p, size_t i, cx<double>& a, cx<double>& b) {
-    double2 t0 = __ldcg((const double2*)p + 2 * i), t1 = __ldcg((const double2*)p + 2 * i + 1);
-    a = {t0.x, t0.y};
-    b = {t1.x, t1.y};
-}
-
 DEV int coarse_neighbour(const Args& a, int X, int d) {
     if (d == 0) return X;
     int c[4];
@@ -248,31 +242,35 @@ DEV int coarse_neighbour(const Args& a, int X, int d) {
     return c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
 }
 
-// issue the bulk copy of the operator rows of chunk c of this call into its ring slot
-DEV void ring_issue(const Args& a, Ring& rg, unsigned gidx, int r0, int r1, int c) {
+// issue, from warp 0, the bulk copies of chunk c of this call into its ring
+// slot: the chunk's operator rows, and the nine neighbour segments (nc
+// entries each) of every coarse site the chunk touches, laid out as segment
+// (s * 9 + d) for site X0 + s and direction d.  All complete on the slot's
+// mbarrier, so the vector gather is as asynchronous as the operator stream.
+template <typename TC>
+DEV void ring_issue(const Args& a, Ring& rg, unsigned gidx, int r0, int r1, int c, const void* xin, cx<TC>* xbuf,
+                    int xcap) {
+    const int lane = threadIdx.x & 31;
     const int rc0 = r0 + c * a.rows_per_chunk;
     const int rows = min(r1 - rc0, a.rows_per_chunk);
     const unsigned slot = gidx % kStages;
-    const unsigned bytes = (unsigned)rows * (unsigned)a.row_bytes;
-    mbar_expect_tx(&rg.full[slot], bytes);
-    bulk_g2s(rg.buf + (size_t)slot * kChunkBytes, (const unsigned char*)a.B + (size_t)rc0 * a.row_bytes, bytes,
-             &rg.full[slot]);
-}
-
-// neighbour segments of the sites of chunk c, as pairs of complex numbers:
-// pair p of site s (relative to the chunk's first site) and direction d holds
-// x[nbr(X, d)][2q .. 2q+1], p = (s * 9 + d) * nc/2 + q
-template <typename TC>
-DEV int xseg_pairs(const Args& a, int r0, int r1, int c, int& X0) {
-    const int rc0 = r0 + c * a.rows_per_chunk, rc1 = min(r1, rc0 + a.rows_per_chunk);
-    X0 = rc0 / a.nc;
-    return ((rc1 - 1) / a.nc - X0 + 1) * 9 * (a.nc / 2);
-}
-template <typename TC>
-DEV void xseg_load(const Args& a, const void* xin, int X0, int p, cx<TC>& v0, cx<TC>& v1) {
-    const int h = a.nc / 2;
-    const int q = p % h, sd = p / h, d = sd % 9, sl = sd / 9;
-    ld_pair_cg((const TC*)xin, ((size_t)coarse_neighbour(a, X0 + sl, d) * a.nc) / 2 + q, v0, v1);
+    const int X0 = rc0 / a.nc, ns = (rc0 + rows - 1) / a.nc - X0 + 1;
+    const unsigned seg = (unsigned)a.xseg_bytes;
+    if (lane == 0) {
+        // the transaction count is raised before any copy of this phase can complete
+        mbar_expect_tx(&rg.full[slot], (unsigned)rows * (unsigned)a.row_bytes + (unsigned)(ns * 9) * seg);
+        bulk_g2s(rg.buf + (size_t)slot * kChunkBytes, (const unsigned char*)a.B + (size_t)rc0 * a.row_bytes,
+                 (unsigned)rows * (unsigned)a.row_bytes, &rg.full[slot]);
+    }
+    __syncwarp();
+    // the vector was written through the generic proxy before the grid barrier
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    cx<TC>* xs = xbuf + (size_t)slot * xcap;
+    for (int j = lane; j < ns * 9; j += 32) {
+        const int sl = j / 9, d = j - 9 * sl;
+        bulk_g2s(xs + (size_t)j * a.nc, (const cx<TC>*)xin + (size_t)coarse_neighbour(a, X0 + sl, d) * a.nc, seg,
+                 &rg.full[slot]);
+    }
 }
 
 // operator entries in shared memory: complex in the solver precision, or
@@ -291,56 +289,47 @@ template <> struct OpElem<float, true> {
 };
 
 // y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA:
-// operator rows arrive by bulk copy through the ring, the chunk's neighbour
-// segments are gathered by the threads one chunk ahead (double buffer), and
-// one warp computes one row entirely from shared memory; returns the
-// per-thread partial <w, y> in dotp.  Returns false if a ring wait timed out.
+// operator rows and the neighbour segments of their sites arrive by bulk copy
+// through the ring (kStages chunks in flight), and one warp computes one row
+// entirely from shared memory; returns the per-thread partial <w, y> in dotp.
+// Returns false if a ring wait timed out.  xin must have been made visible to
+// the async proxy (fence.proxy.async before the grid barrier that precedes).
 template <typename TC, bool BF>
 DEV bool stencil_rows(const Args& a, Ring& rg, cx<TC>* xbuf, const void* xin, void* yout, const void* w, int r0,
                       int r1, cx<TC>& dotp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nc = a.nc, K = 9 * nc;
-    const int xcap = 9 * a.sites_per_chunk * nc;   // complex numbers per x buffer
+    const int xcap = 9 * a.sites_per_chunk * nc;   // complex numbers per slot's segment buffer
     const int nch = (r1 - r0 + a.rows_per_chunk - 1) / a.rows_per_chunk;
     const unsigned base = rg.next;
     int issued = min(nch, kStages);
-    if (tid == 0)
-        for (int c = 0; c < issued; ++c) ring_issue(a, rg, base + c, r0, r1, c);
-    // neighbour segments of chunk 0
-    if (nch > 0) {
-        int X0;
-        const int np = xseg_pairs<TC>(a, r0, r1, 0, X0);
-        for (int p = tid; p < np; p += kThreads) {
-            cx<TC> v0, v1;
-            xseg_load<TC>(a, xin, X0, p, v0, v1);
-            xbuf[2 * p] = v0;
-            xbuf[2 * p + 1] = v1;
-        }
-    }
+    if (warp == 0)
+        for (int c = 0; c < issued; ++c) ring_issue<TC>(a, rg, base + c, r0, r1, c, xin, xbuf, xcap);
     bool ok = true;
     // every issued chunk is waited for (bounded), even after a failure, so no
     // bulk copy is left in flight when the CTA returns
     for (int c = 0; c < issued; ++c) {
         const unsigned gidx = base + c, slot = gidx % kStages;
-        // prefetch the next chunk's segments into registers (they land during the compute)
-        constexpr int kPre = 2;
-        cx<TC> pv[2 * kPre];
-        int Xn = 0, npn = 0;
-        if (c + 1 < nch) {
-            npn = xseg_pairs<TC>(a, r0, r1, c + 1, Xn);
+        const int rc0 = r0 + c * a.rows_per_chunk, rc1 = min(r1, rc0 + a.rows_per_chunk);
+        // w at this warp's rows of the chunk, loaded before the wait so that the
+        // L2 round trip overlaps it (a chunk has at most kMaxRowsPerWarp rows per warp)
+        cx<TC> wv[kMaxRowsPerWarp];
+        if (w && lane == 0) {
 #pragma unroll
-            for (int k = 0; k < kPre; ++k) {
-                const int p = tid + k * kThreads;
-                if (p < npn) xseg_load<TC>(a, xin, Xn, p, pv[2 * k], pv[2 * k + 1]);
+            for (int k = 0; k < kMaxRowsPerWarp; ++k) {
+                const int r = rc0 + warp + k * kWarps;
+                wv[k] = r < rc1 ? ld<TC>(w, r) : czero<TC>();
             }
         }
         const bool got = mbar_wait(&rg.full[slot], (gidx / kStages) & 1);
-        ok = __syncthreads_and(ok && got) != 0;   // CTA-uniform; also publishes xbuf of chunk c
-        const int rc0 = r0 + c * a.rows_per_chunk, rc1 = min(r1, rc0 + a.rows_per_chunk);
+        ok = __syncthreads_and(ok && got) != 0;   // CTA-uniform
         const unsigned char* sb = rg.buf + (size_t)slot * kChunkBytes;
-        const cx<TC>* xs = xbuf + (size_t)(c & 1) * xcap;
+        const cx<TC>* xs = xbuf + (size_t)slot * xcap;
         const int X0 = rc0 / nc;
-        for (int r = rc0 + warp; ok && r < rc1; r += kWarps) {
+#pragma unroll 1
+        for (int k = 0; k < kMaxRowsPerWarp; ++k) {
+            const int r = rc0 + warp + k * kWarps;
+            if (!ok || r >= rc1) break;
             const unsigned char* brow = sb + (size_t)(r - rc0) * a.row_bytes;
             const cx<TC>* xrow = xs + (size_t)(r / nc - X0) * K;   // the nine segments of this row's site
             cx<TC> acc0 = czero<TC>(), acc1 = czero<TC>();
@@ -354,30 +343,18 @@ DEV bool stencil_rows(const Args& a, Ring& rg, cx<TC>* xbuf, const void* xin, vo
             acc.im = warp_sum(acc.im);
             if (lane == 0) {
                 st<TC>(yout, r, acc);
-                if (w) dotp = dotp + cmulc(ld<TC>(w, r), acc);
-            }
-        }
-        // store the prefetched segments for chunk c+1 (the other buffer)
-        if (c + 1 < nch) {
-            cx<TC>* xn = xbuf + (size_t)((c + 1) & 1) * xcap;
+                if (w) {
+                    cx<TC> wr = wv[0];
 #pragma unroll
-            for (int k = 0; k < kPre; ++k) {
-                const int p = tid + k * kThreads;
-                if (p < npn) {
-                    xn[2 * p] = pv[2 * k];
-                    xn[2 * p + 1] = pv[2 * k + 1];
+                    for (int q = 1; q < kMaxRowsPerWarp; ++q)
+                        if (k == q) wr = wv[q];
+                    dotp = dotp + cmulc(wr, acc);
                 }
             }
-            for (int p = tid + kPre * kThreads; p < npn; p += kThreads) {   // rare: more segments than prefetched
-                cx<TC> v0, v1;
-                xseg_load<TC>(a, xin, Xn, p, v0, v1);
-                xn[2 * p] = v0;
-                xn[2 * p + 1] = v1;
-            }
         }
-        __syncthreads();   // slot and x buffer free again
+        __syncthreads();   // slot free again
         if (ok && c + kStages < nch) {
-            if (tid == 0) ring_issue(a, rg, base + c + kStages, r0, r1, c + kStages);
+            if (warp == 0) ring_issue<TC>(a, rg, base + c + kStages, r0, r1, c + kStages, xin, xbuf, xcap);
             ++issued;
         }
     }
@@ -392,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
     __shared__ __align__(8) uint64_t full[kStages];
     extern __shared__ __align__(128) unsigned char ring_buf[];
     Ring rg{ring_buf, full, 0u};
-    cx<TC>* xbuf = (cx<TC>*)(ring_buf + (size_t)kStages * kChunkBytes);   // 2 x 9 * sites_per_chunk * nc
+    cx<TC>* xbuf = (cx<TC>*)(ring_buf + (size_t)kStages * kChunkBytes);   // kStages x 9 * sites_per_chunk * nc
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStages; ++k) mbar_init(&full[k], 1);
         mbar_fence_init();
@@ -512,21 +489,33 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             auto G = [&](int p, int q) -> cx<ST> {   // <R_p, R_q>
                 return ccast<ST>(p <= q ? res[p * (ell + 1) + q] : conj(res[q * (ell + 1) + p]));
             };
-            for (int j = 0; j <= ell; ++j)
-                for (int k = 0; k <= ell; ++k) C[j][k] = czero<ST>();
+            // loops run to the compile-time bound kMaxEll with guards, in the same order as
+            // the algorithm's loops to ell, so that every array lives in registers
+#pragma unroll
+            for (int j = 0; j <= kMaxEll; ++j)
+#pragma unroll
+                for (int k = 0; k <= kMaxEll; ++k) C[j][k] = czero<ST>();
             int bad = 0;
-            for (int j = 1; j <= ell; ++j) {
+#pragma unroll
+            for (int j = 1; j <= kMaxEll; ++j) {
+                if (j > ell) break;
                 C[j][j] = {1, 0};
+#pragma unroll
                 for (int i = 1; i < j; ++i) {
                     cx<ST> t = czero<ST>();
+#pragma unroll
                     for (int p = 1; p <= i; ++p)
+#pragma unroll
                         for (int q = 1; q <= j; ++q) t = t + conj(C[i][p]) * C[j][q] * G(p, q);
                     tau[i][j] = (ST(1) / sigma[i]) * t;
+#pragma unroll
                     for (int k = 1; k <= i; ++k) C[j][k] = C[j][k] - tau[i][j] * C[i][k];
                 }
                 ST sg = 0;
                 cx<ST> t0 = czero<ST>();
+#pragma unroll
                 for (int p = 1; p <= j; ++p) {
+#pragma unroll
                     for (int q = 1; q <= j; ++q) sg += (conj(C[j][p]) * C[j][q] * G(p, q)).re;
                     t0 = t0 + conj(C[j][p]) * G(p, 0);
                 }
@@ -534,26 +523,47 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
                 if (!(sg > 0)) bad = 1;
                 gp[j] = (ST(1) / (sg > 0 ? sg : ST(1))) * t0;
             }
-            g[ell] = gp[ell];
-            for (int j = ell - 1; j >= 1; --j) {
+#pragma unroll
+            for (int j = 0; j <= kMaxEll; ++j) g[j] = gpp[j] = czero<ST>();
+#pragma unroll
+            for (int j = 1; j <= kMaxEll; ++j)
+                if (j == ell) g[j] = gp[j];
+#pragma unroll
+            for (int j = kMaxEll - 1; j >= 1; --j) {
+                if (j >= ell) continue;
                 cx<ST> t = gp[j];
-                for (int i = j + 1; i <= ell; ++i) t = t - tau[j][i] * g[i];
+#pragma unroll
+                for (int i = j + 1; i <= kMaxEll; ++i)
+                    if (i <= ell) t = t - tau[j][i] * g[i];
                 g[j] = t;
             }
-            for (int j = 1; j < ell; ++j) {
+#pragma unroll
+            for (int j = 1; j < kMaxEll; ++j) {
+                if (j >= ell) break;
                 cx<ST> t = g[j + 1];
-                for (int i = j + 1; i < ell; ++i) t = t + tau[j][i] * g[i + 1];
+#pragma unroll
+                for (int i = j + 1; i < kMaxEll; ++i)
+                    if (i < ell) t = t + tau[j][i] * g[i + 1];
                 gpp[j] = t;
             }
             // x += g1 R0 + sum_{j<ell} gpp_j Rt_j ; R0 -= sum_j gp_j Rt_j ; U0 -= sum_j g_j U_j
             cx<ST> tx[kMaxEll + 1], tr[kMaxEll + 1];
-            for (int k = 0; k <= ell; ++k) tx[k] = tr[k] = czero<ST>();
+#pragma unroll
+            for (int k = 0; k <= kMaxEll; ++k) tx[k] = tr[k] = czero<ST>();
             tx[0] = g[1];
-            for (int j = 1; j < ell; ++j)
-                for (int k = 1; k <= j; ++k) tx[k] = tx[k] + gpp[j] * C[j][k];
-            for (int j = 1; j <= ell; ++j)
-                for (int k = 1; k <= j; ++k) tr[k] = tr[k] + gp[j] * C[j][k];
-            for (int k = 0; k <= ell; ++k) {
+#pragma unroll
+            for (int j = 1; j < kMaxEll; ++j)
+#pragma unroll
+                for (int k = 1; k <= j; ++k)
+                    if (j < ell) tx[k] = tx[k] + gpp[j] * C[j][k];
+#pragma unroll
+            for (int j = 1; j <= kMaxEll; ++j)
+#pragma unroll
+                for (int k = 1; k <= j; ++k)
+                    if (j <= ell) tr[k] = tr[k] + gp[j] * C[j][k];
+#pragma unroll
+            for (int k = 0; k <= kMaxEll; ++k) {
+                if (k > ell) break;
                 s_cx[k] = ccast<double>(tx[k]);
                 s_cr[k] = ccast<double>(tr[k]);
                 s_g[k] = ccast<double>(g[k]);
@@ -567,15 +577,18 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
         }
         omega = ccast<SC>(s_g[ell]);
         cx<SC> cx_[kMaxEll + 1], cr[kMaxEll + 1], g[kMaxEll + 1];
-        for (int k = 0; k <= ell; ++k) {
-            cx_[k] = ccast<SC>(s_cx[k]);
-            cr[k] = ccast<SC>(s_cr[k]);
-            g[k] = ccast<SC>(s_g[k]);
+#pragma unroll
+        for (int k = 0; k <= kMaxEll; ++k) {
+            cx_[k] = k <= ell ? ccast<SC>(s_cx[k]) : czero<SC>();
+            cr[k] = k <= ell ? ccast<SC>(s_cr[k]) : czero<SC>();
+            g[k] = k <= ell ? ccast<SC>(s_g[k]) : czero<SC>();
         }
         for (int i = r0 + tid; i < r1; i += kThreads) {
             cx<TC> xv = ld<TC>(a.x, i), r0v = ld<TC>(a.R[0], i), u0 = ld<TC>(a.U[0], i);
             xv = xv + ccast<TC>(cx_[0]) * r0v;
-            for (int k = 1; k <= ell; ++k) {
+#pragma unroll
+            for (int k = 1; k <= kMaxEll; ++k) {
+                if (k > ell) break;
                 cx<TC> rk = ld<TC>(a.R[k], i);
                 xv = xv + ccast<TC>(cx_[k]) * rk;
                 r0v = r0v - ccast<TC>(cr[k]) * rk;
@@ -637,13 +650,14 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     if (a.row_bytes % 16 != 0) return cudaErrorInvalidValue;   // bulk copies move 16-byte multiples
     a.rows_per_chunk = kChunkBytes / a.row_bytes;
     if (a.rows_per_chunk < 1) return cudaErrorInvalidValue;   // nc too large for a ring slot
+    if (a.rows_per_chunk > kMaxRowsPerWarp * kWarps) a.rows_per_chunk = kMaxRowsPerWarp * kWarps;
     a.sites_per_chunk = (a.rows_per_chunk - 1) / nc + 2;
     a.xseg_bytes = nc * eb;
     a.slot_bytes = kChunkBytes;
     const void* fn = cprec == 0   ? (const void*)coarse_bicgstab_kernel<double, false>
                      : cprec == 1 ? (const void*)coarse_bicgstab_kernel<float, false>
                                   : (const void*)coarse_bicgstab_kernel<float, true>;
-    const int smem = kStages * kChunkBytes + 2 * 9 * a.sites_per_chunk * a.xseg_bytes;
+    const int smem = kStages * (kChunkBytes + 9 * a.sites_per_chunk * a.xseg_bytes);
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
