@@ -12,12 +12,12 @@
 // Gram matrix of R_0..R_l (one reduction) instead of sequential projections.
 //
 // The stencil streams the CTA's contiguous slice of the coarse operator
-// through a 3-stage shared-memory ring filled by bulk asynchronous copies
-// (cp.async.bulk, completion counted on mbarriers); the neighbour vector
-// segments a chunk needs ride in the same ring slot, one bulk copy per
-// (site, direction).
+// straight from global memory into registers (coalesced 16-byte words, two
+// rows per warp in flight), so the operator never passes through shared
+// memory; the neighbour blocks of the CTA's coarse sites are gathered into
+// shared memory once per pass.
 //
-// Grid barriers and mbarrier waits spin with a bounded count; on timeout the
+// Grid barriers spin with a bounded count; on timeout the
 // kernel records AMG_TIMEOUT in the status word and every CTA returns.
 #include "common.cuh"
 #include "kernels.h"
@@ -29,9 +29,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxEll = 4;
 constexpr int kMaxQ = (kMaxEll + 1) * (kMaxEll + 1) + 2;   // reduced quantities per barrier
 constexpr long long kSpinLimit = 40000000;                    // ~ seconds of polling
-constexpr int kStages = 3;                                    // bulk-copy ring depth
-constexpr int kChunkBytes = 55296;                            // operator bytes per ring slot (16 FP32 rows, Nc 48)
-constexpr int kMaxRowsPerWarp = 4;                            // rows of one chunk per warp (the launcher checks)
+constexpr int kU = 7;                                         // 16-byte operator words per lane in flight per row
+constexpr int kXBytes = 96 * 1024;                            // shared memory for one group's neighbour blocks
 
 struct GridBar {
     unsigned count;
@@ -56,41 +55,6 @@ template <typename TC> DEV cx<TC> ldg(const void* p, size_t i) {
 }
 template <typename TC> DEV void st(void* p, size_t i, cx<TC> v) { ((typename V2<TC>::T*)p)[i] = {v.re, v.im}; }
 
-// ---- mbarrier / bulk copy (inline PTX) ----
-DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-DEV void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-DEV void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-DEV void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-DEV void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-DEV bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait: false after kSpinLimit polls
-DEV bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (long long it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
 struct Args {
     int L[4];
     int Vc, nc, ell, maxit;
@@ -103,18 +67,8 @@ struct Args {
     void* U[kMaxEll + 1];
     double2* part;   // [kMaxQ][gridDim.x]
     GridBar* bar;
-    int rows_per_chunk;   // rows of the operator per ring slot
-    int row_bytes;        // 9 * nc * sizeof(complex)
-    int sites_per_chunk;  // coarse sites a chunk can touch: (rows_per_chunk - 1) / nc + 2
-    int xseg_bytes;       // nc * sizeof(complex): one neighbour vector segment
-    int slot_bytes;       // bytes per ring slot (kChunkBytes)
-};
-
-// ring state of one CTA (identical in all its threads)
-struct Ring {
-    unsigned char* buf;   // kStages slots of chunk bytes
-    uint64_t* full;       // kStages mbarriers
-    unsigned next;        // global index of the next chunk to consume
+    int row_bytes;   // 9 * nc * (bytes per operator entry), a multiple of 16
+    int xgroup;      // coarse sites whose neighbour blocks are staged in shared memory at once
 };
 
 DEV unsigned ld_acquire(const unsigned* p) {
@@ -139,8 +93,6 @@ DEV void red_release(unsigned* p, unsigned v) {
 // Returns false if it gave up (then the caller returns).
 DEV bool grid_sync(GridBar* gb) {
     __shared__ int s_ok;
-    // vectors written here are read by bulk copies (async proxy) after the barrier
-    asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile int* verr = &gb->err;
@@ -242,139 +194,125 @@ DEV int coarse_neighbour(const Args& a, int X, int d) {
     return c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
 }
 
-// issue, from warp 0, the bulk copies of chunk c of this call into its ring
-// slot: the chunk's operator rows, and the nine neighbour segments (nc
-// entries each) of every coarse site the chunk touches, laid out as segment
-// (s * 9 + d) for site X0 + s and direction d.  All complete on the slot's
-// mbarrier, so the vector gather is as asynchronous as the operator stream.
-template <typename TC>
-DEV void ring_issue(const Args& a, Ring& rg, unsigned gidx, int r0, int r1, int c, const void* xin, cx<TC>* xbuf,
-                    int xcap) {
-    const int lane = threadIdx.x & 31;
-    const int rc0 = r0 + c * a.rows_per_chunk;
-    const int rows = min(r1 - rc0, a.rows_per_chunk);
-    const unsigned slot = gidx % kStages;
-    const int X0 = rc0 / a.nc, ns = (rc0 + rows - 1) / a.nc - X0 + 1;
-    const unsigned seg = (unsigned)a.xseg_bytes;
-    if (lane == 0) {
-        // the transaction count is raised before any copy of this phase can complete
-        mbar_expect_tx(&rg.full[slot], (unsigned)rows * (unsigned)a.row_bytes + (unsigned)(ns * 9) * seg);
-        bulk_g2s(rg.buf + (size_t)slot * kChunkBytes, (const unsigned char*)a.B + (size_t)rc0 * a.row_bytes,
-                 (unsigned)rows * (unsigned)a.row_bytes, &rg.full[slot]);
-    }
-    __syncwarp();
-    // the vector was written through the generic proxy before the grid barrier
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    cx<TC>* xs = xbuf + (size_t)slot * xcap;
-    for (int j = lane; j < ns * 9; j += 32) {
-        const int sl = j / 9, d = j - 9 * sl;
-        bulk_g2s(xs + (size_t)j * a.nc, (const cx<TC>*)xin + (size_t)coarse_neighbour(a, X0 + sl, d) * a.nc, seg,
-                 &rg.full[slot]);
-    }
-}
-
-// operator entries in shared memory: complex in the solver precision, or
-// bfloat16 pairs (BF16 storage, FP32 arithmetic)
-template <typename TC, bool BF> struct OpElem;
-template <typename TC> struct OpElem<TC, false> {
-    static constexpr int bytes = (int)sizeof(cx<TC>);
-    DEV static cx<TC> get(const unsigned char* row, int e) { return ((const cx<TC>*)row)[e]; }
-};
-template <> struct OpElem<float, true> {
-    static constexpr int bytes = 4;
-    DEV static cx<float> get(const unsigned char* row, int e) {
-        float2 f = __bfloat1622float2(((const __nv_bfloat162*)row)[e]);
-        return {f.x, f.y};
+// one 16-byte word of an operator row: 2 FP32 complex entries, 4 bfloat16
+// complex entries (BF16 storage, FP32 arithmetic) or 1 FP64 complex entry,
+// multiplied into acc with the matching entries x[0 .. per-1] of the row's
+// neighbour block (shared memory, 16-byte aligned)
+template <typename TC, bool BF> struct OpWord;
+template <> struct OpWord<float, false> {
+    static constexpr int per = 2;
+    DEV static void mac(uint4 v, const cx<float>* x, cx<float>& acc) {
+        const float4 o = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
+                                     __uint_as_float(v.w));
+        const float4 xv = *reinterpret_cast<const float4*>(x);
+        acc = acc + cx<float>{o.x, o.y} * cx<float>{xv.x, xv.y};
+        acc = acc + cx<float>{o.z, o.w} * cx<float>{xv.z, xv.w};
     }
 };
-
-// y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows of this CTA:
-// operator rows and the neighbour segments of their sites arrive by bulk copy
-// through the ring (kStages chunks in flight), and one warp computes one row
-// entirely from shared memory; returns the per-thread partial <w, y> in dotp.
-// Returns false if a ring wait timed out.  xin must have been made visible to
-// the async proxy (fence.proxy.async before the grid barrier that precedes).
-template <typename TC, bool BF>
-DEV bool stencil_rows(const Args& a, Ring& rg, cx<TC>* xbuf, const void* xin, void* yout, const void* w, int r0,
-                      int r1, cx<TC>& dotp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nc = a.nc, K = 9 * nc;
-    const int xcap = 9 * a.sites_per_chunk * nc;   // complex numbers per slot's segment buffer
-    const int nch = (r1 - r0 + a.rows_per_chunk - 1) / a.rows_per_chunk;
-    const unsigned base = rg.next;
-    int issued = min(nch, kStages);
-    if (warp == 0)
-        for (int c = 0; c < issued; ++c) ring_issue<TC>(a, rg, base + c, r0, r1, c, xin, xbuf, xcap);
-    bool ok = true;
-    // every issued chunk is waited for (bounded), even after a failure, so no
-    // bulk copy is left in flight when the CTA returns
-    for (int c = 0; c < issued; ++c) {
-        const unsigned gidx = base + c, slot = gidx % kStages;
-        const int rc0 = r0 + c * a.rows_per_chunk, rc1 = min(r1, rc0 + a.rows_per_chunk);
-        // w at this warp's rows of the chunk, loaded before the wait so that the
-        // L2 round trip overlaps it (a chunk has at most kMaxRowsPerWarp rows per warp)
-        cx<TC> wv[kMaxRowsPerWarp];
-        if (w && lane == 0) {
+template <> struct OpWord<float, true> {
+    static constexpr int per = 4;
+    DEV static void mac(uint4 v, const cx<float>* x, cx<float>& acc) {
+        const unsigned u[4] = {v.x, v.y, v.z, v.w};
+        const float4 x01 = *reinterpret_cast<const float4*>(x), x23 = *reinterpret_cast<const float4*>(x + 2);
+        const float xs[8] = {x01.x, x01.y, x01.z, x01.w, x23.x, x23.y, x23.z, x23.w};
 #pragma unroll
-            for (int k = 0; k < kMaxRowsPerWarp; ++k) {
-                const int r = rc0 + warp + k * kWarps;
-                wv[k] = r < rc1 ? ld<TC>(w, r) : czero<TC>();
+        for (int e = 0; e < 4; ++e) {
+            const float2 o = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[e]));
+            acc = acc + cx<float>{o.x, o.y} * cx<float>{xs[2 * e], xs[2 * e + 1]};
+        }
+    }
+};
+template <> struct OpWord<double, false> {
+    static constexpr int per = 1;
+    DEV static void mac(uint4 v, const cx<double>* x, cx<double>& acc) {
+        const double2 o = make_double2(__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z));
+        const double2 xv = *reinterpret_cast<const double2*>(x);
+        acc = acc + cx<double>{o.x, o.y} * cx<double>{xv.x, xv.y};
+    }
+};
+
+// y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows [r0, r1)
+// of this CTA; returns the per-thread partial <w, y> in dotp (w != nullptr).
+// The CTA's sites are taken in groups of a.xgroup: the nine neighbour blocks
+// of every site of the group are gathered into shared memory (generic loads
+// through L2, since other CTAs wrote the vector), then each warp computes two
+// rows at a time, streaming their operator words straight from global memory
+// into registers (kU coalesced 16-byte loads per lane and row in flight) --
+// the operator is read exactly once and never passes through shared memory.
+// Contains __syncthreads(): called by all threads of the CTA.
+template <typename TC, bool BF>
+DEV void stencil_rows(const Args& a, cx<TC>* xbuf, int* nbr, const void* xin, void* yout, const void* w, int r0,
+                      int r1, cx<TC>& dotp) {
+    using W = OpWord<TC, BF>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int nc = a.nc, K = 9 * nc, nw = K / W::per;
+    const int wseg = nc * (int)sizeof(cx<TC>) / 16;   // 16-byte words per neighbour segment
+    const int Xa = r0 / nc, Xb = r1 > r0 ? (r1 - 1) / nc : Xa - 1;
+    for (int Xg = Xa; Xg <= Xb; Xg += a.xgroup) {
+        const int gs = min(a.xgroup, Xb - Xg + 1);
+        __syncthreads();   // the previous group's blocks are no longer read
+        for (int t = tid; t < gs * 9; t += kThreads) nbr[t] = coarse_neighbour(a, Xg + t / 9, t % 9);
+        __syncthreads();
+        {
+            const uint4* xg = (const uint4*)xin;
+            uint4* xs = (uint4*)xbuf;
+            for (int p = tid; p < gs * 9 * wseg; p += kThreads) {
+                const int sd = p / wseg, q = p - sd * wseg;
+                xs[p] = __ldcg(xg + (size_t)nbr[sd] * wseg + q);
             }
         }
-        const bool got = mbar_wait(&rg.full[slot], (gidx / kStages) & 1);
-        ok = __syncthreads_and(ok && got) != 0;   // CTA-uniform
-        const unsigned char* sb = rg.buf + (size_t)slot * kChunkBytes;
-        const cx<TC>* xs = xbuf + (size_t)slot * xcap;
-        const int X0 = rc0 / nc;
-#pragma unroll 1
-        for (int k = 0; k < kMaxRowsPerWarp; ++k) {
-            const int r = rc0 + warp + k * kWarps;
-            if (!ok || r >= rc1) break;
-            const unsigned char* brow = sb + (size_t)(r - rc0) * a.row_bytes;
-            const cx<TC>* xrow = xs + (size_t)(r / nc - X0) * K;   // the nine segments of this row's site
-            cx<TC> acc0 = czero<TC>(), acc1 = czero<TC>();
-#pragma unroll 4
-            for (int j = lane; j < K / 2; j += 32) {
-                acc0 = acc0 + OpElem<TC, BF>::get(brow, 2 * j) * xrow[2 * j];
-                acc1 = acc1 + OpElem<TC, BF>::get(brow, 2 * j + 1) * xrow[2 * j + 1];
+        __syncthreads();
+        const int ra = max(r0, Xg * nc), rb = min(r1, (Xg + gs) * nc);
+        for (int rA = ra + 2 * warp; rA < rb; rA += 2 * kWarps) {
+            const int rB = rA + 1;
+            const bool hasB = rB < rb;
+            cx<TC> wA = czero<TC>(), wB = czero<TC>();
+            if (w && lane == 0) {   // loaded now, used after the row sums
+                wA = ld<TC>(w, rA);
+                if (hasB) wB = ld<TC>(w, rB);
             }
-            cx<TC> acc = acc0 + acc1;
-            acc.re = warp_sum(acc.re);
-            acc.im = warp_sum(acc.im);
-            if (lane == 0) {
-                st<TC>(yout, r, acc);
-                if (w) {
-                    cx<TC> wr = wv[0];
+            const uint4* opA = (const uint4*)((const unsigned char*)a.B + (size_t)rA * a.row_bytes);
+            const uint4* opB = opA + nw;
+            const cx<TC>* xA = xbuf + (size_t)(rA / nc - Xg) * K;
+            const cx<TC>* xB = xbuf + (size_t)(rB / nc - Xg) * K;
+            cx<TC> accA = czero<TC>(), accB = czero<TC>();
+            for (int k0 = 0; k0 < nw; k0 += 32 * kU) {
+                uint4 va[kU], vb[kU];
 #pragma unroll
-                    for (int q = 1; q < kMaxRowsPerWarp; ++q)
-                        if (k == q) wr = wv[q];
-                    dotp = dotp + cmulc(wr, acc);
+                for (int u = 0; u < kU; ++u) {
+                    const int k = k0 + lane + 32 * u;
+                    va[u] = k < nw ? __ldg(opA + k) : make_uint4(0u, 0u, 0u, 0u);
+                    vb[u] = (hasB && k < nw) ? __ldg(opB + k) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int k = k0 + lane + 32 * u;
+                    if (k < nw) {
+                        W::mac(va[u], xA + (size_t)k * W::per, accA);
+                        if (hasB) W::mac(vb[u], xB + (size_t)k * W::per, accB);
+                    }
                 }
             }
-        }
-        __syncthreads();   // slot free again
-        if (ok && c + kStages < nch) {
-            if (warp == 0) ring_issue<TC>(a, rg, base + c + kStages, r0, r1, c + kStages, xin, xbuf, xcap);
-            ++issued;
+            accA.re = warp_sum(accA.re);
+            accA.im = warp_sum(accA.im);
+            accB.re = warp_sum(accB.re);
+            accB.im = warp_sum(accB.im);
+            if (lane == 0) {
+                st<TC>(yout, rA, accA);
+                if (hasB) st<TC>(yout, rB, accB);
+                if (w) dotp = dotp + cmulc(wA, accA) + cmulc(wB, accB);
+            }
         }
     }
-    rg.next = base + issued;
-    return ok;
 }
 
 template <typename TC, bool BF>
 __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
     __shared__ cx<double> red_sh[kMaxQ * kWarps];
     __shared__ cx<double> res[kMaxQ];
-    __shared__ __align__(8) uint64_t full[kStages];
-    extern __shared__ __align__(128) unsigned char ring_buf[];
-    Ring rg{ring_buf, full, 0u};
-    cx<TC>* xbuf = (cx<TC>*)(ring_buf + (size_t)kStages * kChunkBytes);   // kStages x 9 * sites_per_chunk * nc
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < kStages; ++k) mbar_init(&full[k], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    cx<TC>* xbuf = (cx<TC>*)dyn_smem;                                    // xgroup x 9 neighbour blocks
+    int* nbr = (int*)(dyn_smem + (size_t)a.xgroup * 9 * a.nc * sizeof(cx<TC>));   // their sites
     const int ell = a.ell;
     const int n = a.Vc * a.nc;
     int r0, r1;
@@ -435,10 +373,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             // U_{j+1} = A U_j and gamma = <rt, U_{j+1}>
             {
                 cx<TC> v[1] = {czero<TC>()};
-                if (!stencil_rows<TC, BF>(a, rg, xbuf, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0])) {
-                    atomicExch(&a.bar->err, 1);
-                    return;
-                }
+                stencil_rows<TC, BF>(a, xbuf, nbr, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0]);
                 if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
             }
             alpha = cdiv(rho0, ccast<SC>(res[0]));
@@ -451,10 +386,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             // R_{j+1} = A R_j; the next BiCG step needs rho1 = <rt, R_{j+1}>
             {
                 cx<TC> v[1] = {czero<TC>()};
-                if (!stencil_rows<TC, BF>(a, rg, xbuf, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0])) {
-                    atomicExch(&a.bar->err, 1);
-                    return;
-                }
+                stencil_rows<TC, BF>(a, xbuf, nbr, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0]);
                 if (j + 1 < ell) {
                     if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
                     rho1 = ccast<SC>(res[0]);
@@ -647,17 +579,14 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     // cprec: 0 FP64, 1 FP32, 2 FP32 vectors with a bfloat16 operator
     const int eb = cprec == 0 ? 16 : 8;
     a.row_bytes = 9 * nc * (cprec == 2 ? 4 : eb);
-    if (a.row_bytes % 16 != 0) return cudaErrorInvalidValue;   // bulk copies move 16-byte multiples
-    a.rows_per_chunk = kChunkBytes / a.row_bytes;
-    if (a.rows_per_chunk < 1) return cudaErrorInvalidValue;   // nc too large for a ring slot
-    if (a.rows_per_chunk > kMaxRowsPerWarp * kWarps) a.rows_per_chunk = kMaxRowsPerWarp * kWarps;
-    a.sites_per_chunk = (a.rows_per_chunk - 1) / nc + 2;
-    a.xseg_bytes = nc * eb;
-    a.slot_bytes = kChunkBytes;
+    if (a.row_bytes % 16 != 0) return cudaErrorInvalidValue;   // rows are read in 16-byte words
+    const int block_bytes = 9 * nc * eb;                                  // one site's neighbour blocks
+    a.xgroup = kXBytes / block_bytes;
+    if (a.xgroup < 1) return cudaErrorInvalidValue;
     const void* fn = cprec == 0   ? (const void*)coarse_bicgstab_kernel<double, false>
                      : cprec == 1 ? (const void*)coarse_bicgstab_kernel<float, false>
                                   : (const void*)coarse_bicgstab_kernel<float, true>;
-    const int smem = kStages * (kChunkBytes + 9 * a.sites_per_chunk * a.xseg_bytes);
+    const int smem = a.xgroup * (block_bytes + 9 * (int)sizeof(int));
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
