@@ -33,8 +33,8 @@ constexpr int kU = 7;                                         // 16-byte operato
 constexpr int kXBytes = 96 * 1024;                            // shared memory for one group's neighbour blocks
 
 struct GridBar {
-    unsigned count;
-    unsigned gen;
+    unsigned count;   // barrier word: arrivals in the low bits, a phase bit on top
+    unsigned pad;
     int err;
     int cycles;
 };
@@ -81,40 +81,33 @@ DEV unsigned atom_add_acqrel(unsigned* p, unsigned v) {
     asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
-DEV void st_relaxed(unsigned* p, unsigned v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-DEV void red_release(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
-// grid barrier (sense by generation counter, acquire/release atomics); the
-// CTA's writes are published by __syncthreads + the releasing arrival.
+// grid barrier on one word: CTA 0 adds 2^31 - (nCTA - 1), every other CTA
+// adds 1, so the top bit flips exactly when the last CTA arrives and the low
+// bits return to their value (the scheme of cooperative groups' grid sync).
+// One acquire-release atomic per CTA, then a bounded spin on the top bit; the
+// CTA's writes are published by __syncthreads + the releasing atomic.
 // Returns false if it gave up (then the caller returns).
 DEV bool grid_sync(GridBar* gb) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile int* verr = &gb->err;
-        const unsigned g = ld_acquire(&gb->gen);
+        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        const unsigned old = atom_add_acqrel(&gb->count, inc);
         int ok = 1;
-        if (atom_add_acqrel(&gb->count, 1u) == gridDim.x - 1) {
-            st_relaxed(&gb->count, 0u);
-            red_release(&gb->gen, 1u);
-        } else {
-            long long it = 0;
-            while (ld_acquire(&gb->gen) == g) {
-                if (*verr) {
-                    ok = 0;
-                    break;
-                }
-                if (++it > kSpinLimit) {
-                    atomicExch(&gb->err, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(20);
+        long long it = 0;
+        while (((ld_acquire(&gb->count) ^ old) & 0x80000000u) == 0) {
+            if (*verr) {
+                ok = 0;
+                break;
             }
+            if (++it > kSpinLimit) {
+                atomicExch(&gb->err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
         }
         s_ok = ok;
     }
