@@ -106,8 +106,10 @@ def dist_info():
     return rank, world, local
 
 
-def make_params(capi, prec_smoother, coarse="f32", outer="fgmres", sap_variant=-1, setup=None):
+def make_params(capi, prec_smoother, coarse="f32", outer="fgmres", sap_variant=-1, setup=None, vec="f32"):
     p = capi.amg_params_default()
+    if vec == "f16":
+        p.prec_vectors = capi.AMG_F16
     p.outer_solver = 1 if outer == "fbicgstab" else 0
     p.sap_variant = sap_variant
     for k, v in (setup or {}).items():
@@ -646,6 +648,9 @@ def main():
     ap.add_argument("--coarse-tol", type=float, default=None, help="coarsest solve tolerance (default: library's)")
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "fbicgstab"],
                     help="outer solver of the solve16 workload (fbicgstab: the paper's flexible BiCGStab)")
+    ap.add_argument("--vec-prec", default="f16", choices=["f32", "f16"],
+                    help="test vectors as restriction and prolongation read them (f16, the default: half "
+                         "storage with a per-site scale, FP32 arithmetic; f32: the setup's precision)")
     ap.add_argument("--coarse-prec", default="f32", choices=["f32", "bf16"],
                     help="coarsest stencil storage of the solve16 workload (bf16: bfloat16 entries, FP32 arithmetic)")
     args = ap.parse_args()
@@ -691,7 +696,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     setup_kw = {"n_init": args.n_init, "n_adapt": args.n_adapt, "coarse_tol": args.coarse_tol}
-    h = capi.amg_setup(d, make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant, setup_kw), [v0])
+    h = capi.amg_setup(d, make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant, setup_kw,
+                                      args.vec_prec), [v0])
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
 
@@ -756,7 +762,7 @@ def main():
     # sites are active per launch.  12.8 flop/byte puts it on the ALU side of
     # the ridge, so it is reported against the FP32 FMA peak:
     # 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (nominal).
-    p = make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant, setup_kw)
+    p = make_params(capi, prec, args.coarse_prec, args.outer, args.sap_variant, setup_kw, args.vec_prec)
     iters = np.mean([i["iters"] for i in infos])
     smooth_ms = np.mean([i["ms_smoother"] for i in infos])
     cycles = np.mean([i["cycles"] for i in infos])
@@ -776,7 +782,8 @@ def main():
         "config": {"workload": "16^3x32 Wilson-clover (exp(0.6iH) links, seed 2, kappa 0.130, csw 1.0), "
                                "2-level AMG 4^4 blocks, 24 test vectors, SAP(4) x MR(6), BiCGStab(2) coarse to 1e-2, "
                                "FGMRES(16) FP64 outer, 1 Gaussian RHS per step",
-                   "smoother_prec": args.prec, "coarse_prec": args.coarse_prec, "outer_solver": args.outer,
+                   "smoother_prec": args.prec, "coarse_prec": args.coarse_prec, "vector_prec": args.vec_prec,
+                   "outer_solver": args.outer,
                    "n_init": p.n_init, "n_adapt": p.n_adapt, "coarse_tol": p.coarse_tol,
                    "setup_ms": setup_ms, "l2": "working set > L2 (no flush)",
                    "outer_iters": float(iters), "cycles": float(cycles), "converged": ok,

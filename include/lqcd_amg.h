@@ -100,6 +100,14 @@ typedef struct {
     int outer_solver;                   /* 0: flexible GMRES(outer_m) [0]; 1: the paper's BiCGStab with
                                            flexible preconditioning (Sec. 3), one right-hand side at a
                                            time; both stop on the FP64 true residual */
+    int prec_vectors;                   /* fine test vectors as read by restriction and prolongation
+                                           (Eqs. 5, 6): AMG_F16 stores them in half precision with a
+                                           per-site scale (about half the bytes of each transfer); the
+                                           setup rounds the orthonormalised vectors to it and builds the
+                                           Galerkin operator (Eq. 7) from the rounded ones, so R, P and
+                                           D_c stay consistent.  Any other value keeps the setup's
+                                           precision (FP64 with an FP64 smoother, else FP32).  AMG_F16
+                                           needs an FP32 or FP16 smoother [AMG_F32] */
 } amg_params;
 
 typedef struct {

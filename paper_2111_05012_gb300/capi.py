@@ -49,6 +49,7 @@ class amg_params(ctypes.Structure):
         ("prec_coarsest", ctypes.c_int),
         ("sap_variant", ctypes.c_int),
         ("outer_solver", ctypes.c_int),
+        ("prec_vectors", ctypes.c_int),
     ]
 
 

@@ -184,8 +184,10 @@ struct amg_hierarchy {
     amg_params p;
     int fp = 1;     // smoother precision used by the solve
     int vp = 1;     // test-vector precision (and the setup's cycle precision)
+    int rp = 1;     // precision of the test vectors restriction and prolongation read (vp, or 2 = FP16)
     BlockH blk[AMG_MAX_LEVELS - 1];
     DevBuf vecs0;
+    DevBuf vecs16;   // half-precision copy of vecs0 for restriction / prolongation (rp == 2)
     std::vector<CoarseLevel> lev;   // lev[l] for l = 1..nlevels-1 (lev[0] unused)
     // fine workspaces per precision: b, x
     DevBuf fb[3], fx[3];
@@ -233,6 +235,8 @@ namespace {
 const GeomH& fine_geom(amg_hierarchy* h) { return h->d->gauge->lat->g; }
 size_t fine_n(amg_hierarchy* h) { return (size_t)fine_geom(h).V * 12; }
 size_t coarse_n(const CoarseLevel& L) { return (size_t)L.g.V * L.nc; }
+// the test vectors restriction and prolongation read (precision h->rp)
+const void* rp_vecs(amg_hierarchy* h) { return h->rp == 2 ? h->vecs16.p : h->vecs0.p; }
 
 amg_status check_params(const GeomH& g, const amg_params* p) {
     if (!p) return fail(AMG_EINVAL, "params is NULL");
@@ -277,6 +281,8 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
     if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
     if (p->outer_solver != 0 && p->outer_solver != 1) return fail(AMG_EINVAL, "outer_solver must be 0 or 1");
+    if (p->prec_vectors == AMG_F16 && p->prec_smoother == AMG_F64)
+        return fail(AMG_EINVAL, "half-precision test vectors need an FP32 or FP16 smoother");
     if (p->sap_iters < 0 || p->mr_iters < 0) return fail(AMG_EINVAL, "sap_iters / mr_iters");
     return AMG_OK;
 }
@@ -520,14 +526,14 @@ amg_status vcycle0(amg_hierarchy* h, int prec, const void* b, void* x, int nb, c
     CoarseLevel& L = L1(h);
     auto& w = h->cw[1];
     h->timer.start(PH_RP, s);
-    CK(launch_restrict_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, b, w[0]->p, nb,
+    CK(launch_restrict_fine(prec, h->rp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], rp_vecs(h), b, w[0]->p, nb,
                             s));
     h->timer.stop(s);
     h->timer.start(PH_COARSE, s);
     TRY(coarse_solve(h, 1, w[0]->p, w[1]->p, nb, s));
     h->timer.stop(s);
     h->timer.start(PH_RP, s);
-    CK(launch_prolong_fine(prec, h->vp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], h->vecs0.p, w[1]->p, x, nb,
+    CK(launch_prolong_fine(prec, h->rp, L.prec, fine_geom(h), h->blk[0], h->p.nvec[0], rp_vecs(h), w[1]->p, x, nb,
                            s));
     h->timer.stop(s);
     TRY(fine_sap(h, prec, b, x, false, nb, s));
@@ -909,6 +915,14 @@ amg_status orthonormalise_and_galerkin(amg_hierarchy* h, cudaStream_t s) {
     CK(cudaMemcpyAsync(&flag, h->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (flag) return fail(AMG_EINVAL, "test vectors are rank deficient on some domain");
+    if (h->rp == 2) {
+        // round the orthonormalised vectors to half precision (per-site scale) and carry the
+        // rounded values back, so that the Galerkin operator below, the restriction and the
+        // prolongation all use the same vectors
+        CK(h->vecs16.ensure(fine_spinor_bytes(2, g.V) * h->p.nvec[0]));
+        CK(launch_convert_spinor(h->vp, 2, g, h->vecs0.p, h->vecs16.p, h->p.nvec[0], s));
+        CK(launch_convert_spinor(2, h->vp, g, h->vecs16.p, h->vecs0.p, h->p.nvec[0], s));
+    }
     amg_dirac* d = h->d;
     CoarseLevel& L = L1(h);
     CK(launch_galerkin_fine(h->vp, L.prec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, d->gauge->U[h->vp].p,
@@ -1090,6 +1104,7 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
     h->p = *p;
     h->fp = p->prec_smoother;
     h->vp = vec_prec_of(p->prec_smoother);
+    h->rp = p->prec_vectors == AMG_F16 ? 2 : h->vp;
     *hp = h;
     amg_status st = build_levels(h);
     if (st == AMG_OK) st = alloc_workspaces(h, 1);
@@ -1476,6 +1491,7 @@ void amg_params_default(amg_params* p) {
     p->prec_coarsest = AMG_F32;
     p->sap_variant = -1;
     p->outer_solver = 0;
+    p->prec_vectors = AMG_F32;
 }
 
 amg_status amg_lattice_create(const int dims[4], int antiperiodic_t, amg_lattice** out) {
@@ -1920,7 +1936,7 @@ amg_status amg_restrict(amg_hierarchy* h, int coarsening, const void* fine, void
     DevBuf tmp;
     CK(tmp.ensure(fine_spinor_bytes(prec, g.V) * nrhs));
     CK(launch_pack_spinor(prec, g, fine, tmp.p, nrhs, st));
-    CK(launch_restrict_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, tmp.p, coarse, nrhs, st));
+    CK(launch_restrict_fine(prec, h->rp, cprec, g, h->blk[0], h->p.nvec[0], rp_vecs(h), tmp.p, coarse, nrhs, st));
     CK(cudaStreamSynchronize(st));
     return AMG_OK;
 }
@@ -1934,7 +1950,7 @@ amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, voi
     int cprec = prec == AMG_F64 ? 0 : 1;
     DevBuf tmp;
     CK(tmp.ensure(fine_spinor_bytes(prec, g.V) * nrhs));
-    CK(launch_prolong_fine(prec, h->vp, cprec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, coarse, tmp.p, nrhs, st));
+    CK(launch_prolong_fine(prec, h->rp, cprec, g, h->blk[0], h->p.nvec[0], rp_vecs(h), coarse, tmp.p, nrhs, st));
     CK(launch_unpack_spinor(prec, g, tmp.p, fine, nrhs, st));
     CK(cudaStreamSynchronize(st));
     return AMG_OK;

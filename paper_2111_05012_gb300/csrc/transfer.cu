@@ -335,6 +335,10 @@ cudaError_t launch_restrict_fine(int fprec, int vprec, int cprec, const GeomH& g
         if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P64, double>(g, bk, nvec, vecs, fine, coarse, nrhs, st)); }
         DISPATCH_F(fprec, return restrict_impl<PF, P64, float>(g, bk, nvec, vecs, fine, coarse, nrhs, st));
     }
+    if (vprec == 2) {   // half-precision test vectors with a per-site scale
+        if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P16, double>(g, bk, nvec, vecs, fine, coarse, nrhs, st)); }
+        DISPATCH_F(fprec, return restrict_impl<PF, P16, float>(g, bk, nvec, vecs, fine, coarse, nrhs, st));
+    }
     if (cprec == 0) { DISPATCH_F(fprec, return restrict_impl<PF, P32, double>(g, bk, nvec, vecs, fine, coarse, nrhs, st)); }
     DISPATCH_F(fprec, return restrict_impl<PF, P32, float>(g, bk, nvec, vecs, fine, coarse, nrhs, st));
 }
@@ -343,6 +347,10 @@ cudaError_t launch_prolong_fine(int fprec, int vprec, int cprec, const GeomH& g,
     if (vprec == 0) {
         if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P64, double>(g, bk, nvec, vecs, coarse, fine, nrhs, st)); }
         DISPATCH_F(fprec, return prolong_impl<PF, P64, float>(g, bk, nvec, vecs, coarse, fine, nrhs, st));
+    }
+    if (vprec == 2) {
+        if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P16, double>(g, bk, nvec, vecs, coarse, fine, nrhs, st)); }
+        DISPATCH_F(fprec, return prolong_impl<PF, P16, float>(g, bk, nvec, vecs, coarse, fine, nrhs, st));
     }
     if (cprec == 0) { DISPATCH_F(fprec, return prolong_impl<PF, P32, double>(g, bk, nvec, vecs, coarse, fine, nrhs, st)); }
     DISPATCH_F(fprec, return prolong_impl<PF, P32, float>(g, bk, nvec, vecs, coarse, fine, nrhs, st));

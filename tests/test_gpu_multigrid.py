@@ -160,11 +160,49 @@ def test_precondition_fp64(mgcase):
     c.amg_hierarchy_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, "bf16"])
+def test_half_precision_test_vectors(mgcase):
+    # prec_vectors = AMG_F16: the orthonormalised vectors are rounded to half precision
+    # with a per-site scale (the largest of the 24 real components of the site), and the
+    # Galerkin operator, the restriction and the prolongation all use the rounded vectors
+    import torch
+    f = mgcase
+    c = f.c
+    h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, 1, prec_vectors=c.AMG_F16),
+                                 [li.to_interleaved(f.v0)])
+    got = c.amg_get_vectors(h, 0, f.nvec, f.V)
+    vr = (got[..., 0] + 1j * got[..., 1]).reshape(f.vo.shape)
+    comp = lambda v: np.stack([v.real, v.imag], -1).reshape(f.nvec, f.V, 24)
+    m = np.abs(comp(f.vo)).max(-1, keepdims=True)
+    err = np.abs(comp(vr) - comp(f.vo))
+    assert (err <= 2.0 ** -11 * m).all()          # half rounding, relative to the site's scale
+    assert err.max() > 1e-5 * m.max()             # ... and the vectors were rounded
+    B = c.amg_get_coarse_op(h, 1)
+    B = B[..., 0] + 1j * B[..., 1]
+    assert rel(B, omg.coarse_operator(f.op, vr, f.block).B.reshape(B.shape)) < 2e-6
+    dims_c, nc = c.amg_level_info(h, 1)
+    cshape = li.lattice_shape(dims_c)
+    psi = li.rhs(f.dims, 9).reshape(f.shape4 + (12,))
+    xc = torch.zeros(int(np.prod(cshape)) * nc * 2, dtype=torch.float32, device="cuda")
+    c.amg_restrict(h, 0, to_dev(psi, "float32"), xc, 1, 1)
+    assert rel(from_dev(xc, cshape + (nc,)), omg.restrict(vr, psi, f.block)) < 2e-6
+    yc = li.complex_normal(77, li.STREAM_MISC, cshape + (nc,))
+    fine = torch.zeros(f.V * 24, dtype=torch.float32, device="cuda")
+    c.amg_prolong(h, 0, to_dev(yc, "float32"), fine, 1, 1)
+    assert rel(from_dev(fine, f.shape4 + (12,)), omg.prolong(vr, yc, f.block)) < 2e-6
+    c.amg_hierarchy_destroy(h)
+    with pytest.raises(c.AMGError) as e:   # an FP64 smoother keeps FP64 vectors
+        c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, 0, prec_vectors=c.AMG_F16),
+                                 [li.to_interleaved(f.v0)])
+    assert e.value.status == c.AMG_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, "bf16", "f16vec"])
 def test_solve_reaches_fp64_tolerance(mgcase, prec):
     f = mgcase
     c = f.c
-    if prec == "bf16":   # FP32 smoother, bfloat16 coarse operator
+    if prec == "f16vec":   # FP32 smoother, half-precision test vectors in R and P
+        p = _params(c, f.block, f.nvec, 1, n_init=2, n_adapt=1, prec_vectors=c.AMG_F16)
+    elif prec == "bf16":   # FP32 smoother, bfloat16 coarse operator
         p = _params(c, f.block, f.nvec, 1, n_init=2, n_adapt=1)
         p.prec_coarsest = c.AMG_BF16
         if f.nvec % 2:   # rows of 9 * Nc bfloat16 pairs must be 16-byte multiples
@@ -172,7 +210,7 @@ def test_solve_reaches_fp64_tolerance(mgcase, prec):
                 c.amg_setup(f.d, p, [li.to_interleaved(f.v0)])
             assert "even number of test vectors" in str(e.value)
             return
-    else:
+    if prec not in ("bf16", "f16vec"):
         p = _params(c, f.block, f.nvec, prec, n_init=2, n_adapt=1)
     h = c.amg_setup(f.d, p, [li.to_interleaved(f.v0)])
     b = li.rhs(f.dims, 13)
