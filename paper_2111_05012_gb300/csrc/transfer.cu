@@ -49,18 +49,97 @@ template <> struct CStore<float> {
     }
 };
 
+// ------------------------------------------------------------ raw vector loads
+// A test vector at one site as loaded from memory, unpacked only when used, so
+// that the loads of several vectors can be in flight together without holding
+// all of them unpacked in registers.
+template <class PV> struct RawSite;
+template <> struct RawSite<P64> {
+    double2 r[12];
+    DEV void load(const void* base, int V, int s) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r[k] = __ldg((const double2*)base + (size_t)k * V + s);
+    }
+    DEV cx<double> get(int k) const { return {r[k].x, r[k].y}; }
+};
+template <> struct RawSite<P32> {
+    float4 r[6];
+    DEV void load(const void* base, int V, int s) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) r[c] = __ldg((const float4*)base + (size_t)c * V + s);
+    }
+    DEV cx<float> get(int k) const {
+        const float4 t = r[k >> 1];
+        return (k & 1) ? cx<float>{t.z, t.w} : cx<float>{t.x, t.y};
+    }
+};
+template <> struct RawSite<P16> {   // three uint4 of halves, then the per-site scale (SpinorIO<P16> layout)
+    uint4 r[3];
+    float sc;
+    DEV void load(const void* base, int V, int s) {
+        const uint4* p = (const uint4*)base;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = __ldg(p + (size_t)c * V + s);
+        sc = __ldg((const float*)(p + (size_t)3 * V) + s);
+    }
+    DEV cx<float> get(int k) const {
+        const uint4 t = r[k >> 2];
+        const unsigned w = (k & 3) == 0 ? t.x : (k & 3) == 1 ? t.y : (k & 3) == 2 ? t.z : t.w;
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+        return {f.x * sc, f.y * sc};
+    }
+};
+// vectors whose loads a thread keeps in flight together
+template <class PV> constexpr int kVecGroup = PV::id == 2 ? 4 : 2;
+
+// Warp sums of N values per lane (N a power of two, N <= 32) with 2N - 1 + log2(32/N)
+// shuffles instead of 5N: each halving step pairs lanes l and l^off, every lane keeping
+// one half of its values (the lower half if its bit off is clear) plus the partner's
+// copy of that half.  Afterwards lane l holds the total of value sum_t bit(l, 4-t) * N/2^(t+1)
+// (see transposed_index), duplicated over the lanes that differ only in the low bits.
+template <int N, typename T> DEV T transposed_warp_sum(T (&v)[N], int lane) {
+#pragma unroll
+    for (int t = 0, h = N / 2, off = 16; h >= 1; ++t, h /= 2, off /= 2) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const T keep = up ? v[k + h] : v[k];
+            const T give = up ? v[k] : v[k + h];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, give, off);
+        }
+    }
+    T r = v[0];
+#pragma unroll
+    for (int off = 16 / N; off >= 1; off /= 2) r += __shfl_xor_sync(0xffffffffu, r, off);
+    return r;
+}
+template <int N> DEV int transposed_index(int lane) {
+    int idx = 0;
+#pragma unroll
+    for (int t = 0, h = N / 2, off = 16; h >= 1; ++t, h /= 2, off /= 2)
+        if (lane & off) idx += h;
+    return idx;
+}
+
 // ------------------------------------------------------------ restriction
+// One CTA per block, one thread per site: the site's share of <X,s,i|psi> for a
+// group of test vectors (their loads in flight together), summed over the warp
+// by transposed shuffles and over the warps in shared memory.
 template <class PF, class PV, typename TC>
 __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
                                 const void* __restrict__ fine, void* coarse) {
     using T = typename PF::T;
+    constexpr int G = kVecGroup<PV>, NQ = 4 * G;   // per vector: d0.re, d0.im, d1.re, d1.im
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);   // [nwarps][2*nvec]
+    T* partf = reinterpret_cast<T*>(smem_raw);
     const int nc = 2 * nvec;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const size_t vb = spinor_bytes<PV>(g.V);
     fine = (const char*)fine + blockIdx.y * spinor_bytes<PF>(g.V);
     coarse = (char*)coarse + blockIdx.y * (size_t)bk.Vc * nc * sizeof(cx<TC>);
+    const int qi = transposed_index<NQ>(lane);
+    const bool writer = (lane & (32 / NQ - 1)) == 0;
     for (int Xi = blockIdx.x; Xi < bk.Vc; Xi += gridDim.x) {
         const int l = threadIdx.x;
         const bool active = l < bk.Vb;
@@ -70,25 +149,32 @@ __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __res
             s = block_site(g, bk, Xi, l, c);
             SpinorIO<PF>::load(fine, g.V, s, psi);
         }
-        for (int i = 0; i < nvec; ++i) {
-            cx<T> d0 = czero<T>(), d1 = czero<T>();
+        for (int i0 = 0; i0 < nvec; i0 += G) {
+            RawSite<PV> raw[G];
             if (active) {
-                cx<typename PV::T> v[12];
-                SpinorIO<PV>::load((const char*)vecs + i * vb, g.V, s, v);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    d0 = d0 + cmulc(ccast<T>(v[k]), psi[k]);
-                    d1 = d1 + cmulc(ccast<T>(v[6 + k]), psi[6 + k]);
+                for (int u = 0; u < G; ++u)
+                    if (i0 + u < nvec) raw[u].load((const char*)vecs + (size_t)(i0 + u) * vb, g.V, s);
+            }
+            T q[NQ];
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                cx<T> d0 = czero<T>(), d1 = czero<T>();
+                if (active && i0 + u < nvec) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        d0 = d0 + cmulc(ccast<T>(raw[u].get(k)), psi[k]);
+                        d1 = d1 + cmulc(ccast<T>(raw[u].get(6 + k)), psi[6 + k]);
+                    }
                 }
+                q[4 * u] = d0.re;
+                q[4 * u + 1] = d0.im;
+                q[4 * u + 2] = d1.re;
+                q[4 * u + 3] = d1.im;
             }
-            d0.re = warp_sum(d0.re);
-            d0.im = warp_sum(d0.im);
-            d1.re = warp_sum(d1.re);
-            d1.im = warp_sum(d1.im);
-            if (lane == 0) {
-                part[warp * nc + i] = d0;
-                part[warp * nc + nvec + i] = d1;
-            }
+            const T tot = transposed_warp_sum<NQ>(q, lane);
+            const int u = qi >> 2, comp = qi & 3, i = i0 + u;
+            if (writer && i < nvec) partf[2 * (warp * nc + (comp < 2 ? i : nvec + i)) + (comp & 1)] = tot;
         }
         __syncthreads();
         for (int j = threadIdx.x; j < nc; j += blockDim.x) {
@@ -101,10 +187,13 @@ __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __res
 }
 
 // ------------------------------------------------------------ prolongation
+// One CTA per block, one thread per site: psi'(x) = sum_{s,i} x_c(X, s, i) P_s v_i(x)
+// with the loads of a group of test vectors in flight together.
 template <class PF, class PV, typename TC>
 __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
                                const void* __restrict__ coarse, void* fine) {
     using T = typename PF::T;
+    constexpr int G = kVecGroup<PV>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* xc = reinterpret_cast<cx<T>*>(smem_raw);   // [2*nvec]
     const int nc = 2 * nvec;
@@ -122,14 +211,20 @@ __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __rest
             cx<T> out[12];
 #pragma unroll
             for (int k = 0; k < 12; ++k) out[k] = czero<T>();
-            for (int i = 0; i < nvec; ++i) {
-                cx<typename PV::T> v[12];
-                SpinorIO<PV>::load((const char*)vecs + i * vb, g.V, s, v);
-                cx<T> a0 = xc[i], a1 = xc[nvec + i];
+            for (int i0 = 0; i0 < nvec; i0 += G) {
+                RawSite<PV> raw[G];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    out[k] = out[k] + a0 * ccast<T>(v[k]);
-                    out[6 + k] = out[6 + k] + a1 * ccast<T>(v[6 + k]);
+                for (int u = 0; u < G; ++u)
+                    if (i0 + u < nvec) raw[u].load((const char*)vecs + (size_t)(i0 + u) * vb, g.V, s);
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    if (i0 + u >= nvec) break;
+                    const cx<T> a0 = xc[i0 + u], a1 = xc[nvec + i0 + u];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        out[k] = out[k] + a0 * ccast<T>(raw[u].get(k));
+                        out[6 + k] = out[6 + k] + a1 * ccast<T>(raw[u].get(6 + k));
+                    }
                 }
             }
             SpinorIO<PF>::store(fine, g.V, s, out);
