@@ -201,6 +201,11 @@ struct amg_hierarchy {
     DevBuf bv[6], bz[2];   // flexible BiCGStab: r, r~, p, s, t, D M p (FP64); M p, M s (Z precision)
     DevBuf canon;   // canonical staging
     Reducer red;
+    // outer Gram-Schmidt with device-side coefficients: per right-hand side three regions of
+    // 20 x blas_grid() partials and 64 coefficient slots (pass-1 dots, pass-2 dots at 32, |w| at 63)
+    DevBuf gs_part, gs_coef;
+    double2* gs_hcoef = nullptr;
+    int gs_cap = 0;
     PhaseTimer timer;
     int err_flag_host = 0;
     DevBuf err_flag;
@@ -223,6 +228,7 @@ struct amg_hierarchy {
     ~amg_hierarchy() {
         clear_graphs();
         if (hstate) cudaFreeHost(hstate);
+        if (gs_hcoef) cudaFreeHost(gs_hcoef);
         for (auto& v : cw)
             for (auto* b : v) delete b;
         for (auto* b : oV) delete b;
@@ -681,8 +687,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             r.jend = -1;
             r.stop = r.done;
             if (r.done) CK(cudaMemsetAsync(F(h->oV[0]->p, q), 0, fs, s));
-            else CK(launch_axpby(0, make_double2(1.0 / r.rn, 0), F(h->orr.p, q), make_double2(0, 0),
-                                 F(h->oV[0]->p, q), n, s));
+            else CK(launch_scale_real(0, 1.0 / r.rn, F(h->orr.p, q), F(h->oV[0]->p, q), n, s));
         }
         for (int j = 0; j < m; ++j) {
             TRY(precondition64(h, h->oV[j]->p, h->oZ[j]->p, nb, s));
@@ -691,53 +696,36 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
                 if (!st[q].stop) relax = relax && relaxed_product(std::abs(st[q].g[j]) / st[q].bnorm, tol);
             TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, nb, s, relax));
             // classical Gram-Schmidt, twice (with a good preconditioner w = D M v lies close to
-            // span V, so a second projection is always needed); one host synchronisation per
-            // reduction for every right-hand side: dots; update fused with the new dots; update
-            // fused with |w|^2
+            // span V, so a second projection is always needed), with the coefficients summed
+            // on the device: the dots, the first update fused with the second pass's dots, the
+            // second update fused with |w|^2, and the normalisation v_{j+1} = w / |w| run back
+            // to back; one host synchronisation per step fetches the Hessenberg column
             std::vector<const void*> vl(j + 1);
-            double2* const dp = red.dpart.as<double2>();
-            auto region = [&](int q) { return dp + (size_t)q * 20 * red.grid; };
-            auto fetch = [&](int k) -> amg_status {   // k quantities per right-hand side
-                const size_t cnt = nb == 1 ? (size_t)k * red.grid : (size_t)20 * red.grid * nb;
-                CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double2) * cnt, cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-                return AMG_OK;
-            };
-            auto quantity = [&](int q, int i) {   // host sum of quantity i of right-hand side q
-                double re = 0, im = 0;
-                const double2* hp = red.hpart + (size_t)q * 20 * red.grid + (size_t)i * red.grid;
-                for (int t = 0; t < red.grid; ++t) {
-                    re += hp[t].x;
-                    im += hp[t].y;
-                }
-                return cplx(re, im);
-            };
+            const size_t R = (size_t)20 * red.grid;
+            double2* const gp = h->gs_part.as<double2>();
+            double2* const gc = h->gs_coef.as<double2>();
             for (int q = 0; q < nb; ++q) {
+                if (st[q].stop) continue;
                 for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
-                CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n, region(q), s));
+                double2 *A = gp + (3 * q) * R, *B = gp + (3 * q + 1) * R, *C = gp + (3 * q + 2) * R;
+                double2* cu = gc + 64 * q;
+                CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n, A, s));
+                CK(launch_multi_axpy_reduce_dev(0, j + 1, A, cu, vl.data(), F(h->ow.p, q), n, 1, B, s));
+                CK(launch_multi_axpy_reduce_dev(0, j + 1, B, cu + 32, vl.data(), F(h->ow.p, q), n, 0, C, s));
+                CK(launch_normalise(0, (const double*)C, (double*)(cu + 63), F(h->ow.p, q), F(h->oV[j + 1]->p, q), n,
+                                    s));
             }
-            TRY(fetch(j + 1));
+            CK(cudaMemcpyAsync(h->gs_hcoef, gc, sizeof(double2) * 64 * nb, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
             TRY(coarse_status(h));
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int q = 0; q < nb; ++q) {
-                    RhsState& r = st[q];
-                    if (r.stop) continue;
-                    std::vector<double2> nc(j + 1);
-                    for (int i = 0; i <= j; ++i) {
-                        const cplx c = quantity(q, i);
-                        r.H[i][j] += c;
-                        nc[i] = make_double2(-c.real(), -c.imag());
-                        vl[i] = F(h->oV[i]->p, q);
-                    }
-                    CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), F(h->ow.p, q), n, pass == 0 ? 1 : 0,
-                                                region(q), s));
-                }
-                TRY(fetch(pass == 0 ? j + 1 : 1));
-            }
-            std::vector<double> hn2(nb, 0.0);
+            std::vector<double> hnv(nb, 0.0);   // |w| exactly as the normalisation used it
             for (int q = 0; q < nb; ++q) {
-                const double* hp = (const double*)(red.hpart + (size_t)q * 20 * red.grid);
-                for (int t = 0; t < red.grid; ++t) hn2[q] += hp[t];
+                RhsState& r = st[q];
+                if (r.stop) continue;
+                const double2* hc = h->gs_hcoef + 64 * q;
+                for (int i = 0; i <= j; ++i) r.H[i][j] += cplx(hc[i].x, hc[i].y);
+                for (int i = 0; i <= j; ++i) r.H[i][j] += cplx(hc[32 + i].x, hc[32 + i].y);
+                hnv[q] = reinterpret_cast<const double*>(hc + 63)[0];
             }
             bool all_stopped = true;
             for (int q = 0; q < nb; ++q) {
@@ -746,7 +734,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
                     CK(cudaMemsetAsync(F(h->oV[j + 1]->p, q), 0, fs, s));
                     continue;
                 }
-                const double hn = std::sqrt(hn2[q]);
+                const double hn = hnv[q];
                 auto& H = r.H;
                 H[j + 1][j] = hn;
                 r.iters++;
@@ -781,9 +769,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
                     r.stop = true;
                     CK(cudaMemsetAsync(F(h->oV[j + 1]->p, q), 0, fs, s));
                 } else {
-                    CK(launch_axpby(0, make_double2(1.0 / hn, 0), F(h->ow.p, q), make_double2(0, 0),
-                                    F(h->oV[j + 1]->p, q), n, s));
-                    all_stopped = false;
+                    all_stopped = false;   // v_{j+1} = w / |w| is already in place
                 }
             }
             if (all_stopped) break;
@@ -829,6 +815,14 @@ amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
     const GeomH& g = fine_geom(h);
     if (nb > h->nb_cap) h->clear_graphs();   // buffers may move: captured graphs would be stale
     TRY(h->red.init(nb));
+    if (nb > h->gs_cap || !h->gs_hcoef) {
+        CK(h->gs_part.ensure(sizeof(double2) * 3 * 20 * (size_t)blas_grid() * nb));
+        CK(h->gs_coef.ensure(sizeof(double2) * 64 * nb));
+        if (h->gs_hcoef) cudaFreeHost(h->gs_hcoef);
+        h->gs_hcoef = nullptr;
+        CK(cudaMallocHost(&h->gs_hcoef, sizeof(double2) * 64 * nb));
+        h->gs_cap = nb;
+    }
     CK(h->err_flag.ensure(sizeof(int)));
     for (int pr = 0; pr < 3; ++pr) {
         CK(h->fb[pr].ensure(fine_spinor_bytes(pr, g.V) * nb));

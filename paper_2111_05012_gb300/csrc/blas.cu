@@ -82,12 +82,47 @@ void multi_dot_launch(int k, bool nb, const PtrList& pl, const V* b, size_t n, d
 // y += sum_{j<K} c_j x_j, then partial dots <x_j, y_new> (DOT) or partial |y_new|^2:
 // one pass over the vectors for the update of a Gram-Schmidt pass and the
 // reduction of the next one
+// the sum of the gridDim.x partials of each of k quantities ([j][gridDim.x]),
+// one warp per quantity, lanes striding (fixed order: every CTA of the launch
+// gets bitwise the same sums); out[j] = -sum (the update coefficient), and CTA
+// 0 stores +sum in used[j] for the host's Hessenberg column
+DEV void coefficients_from_partials(const double2* src, int k, double2* out, double2* used) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < k; j += nw) {
+        double re = 0, im = 0;
+        for (int t = lane; t < (int)gridDim.x; t += 32) {
+            const double2 v = __ldcg(src + (size_t)j * gridDim.x + t);
+            re += v.x;
+            im += v.y;
+        }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) {
+            out[j] = make_double2(-re, -im);
+            if (blockIdx.x == 0 && used) used[j] = make_double2(re, im);
+        }
+    }
+    __syncthreads();
+}
+
 template <typename V, int K, int MODE>   // MODE 0: |y|^2; 1: dots; 2: dots and |y|^2 (quantity K)
-__global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, double2* partials) {
+__global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, double2* partials,
+                                         const double2* csrc, double2* cused) {
     using T = typename VT<V>::T;
     constexpr bool DOT = MODE >= 1, NRM = MODE != 1;
     constexpr int NA = (DOT ? 2 * K : 0) + (NRM ? (DOT ? 2 : 1) : 0);
     __shared__ double red[NA * 32];
+    __shared__ double2 cdev[K];
+    // coefficients: from the launch (host sums) or, with csrc, minus the sums of the
+    // partials a previous reduction left there (no host round trip)
+    if (csrc) coefficients_from_partials(csrc, K, cdev, cused);
+    T cre[K], cim[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const double2 cj = csrc ? cdev[j] : c.c[j];
+        cre[j] = (T)cj.x;
+        cim[j] = (T)cj.y;
+    }
     double acc[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) acc[j] = 0.0;
@@ -99,7 +134,7 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
         T re = o.x, im = o.y;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const T cr = (T)c.c[j].x, ci = (T)c.c[j].y;
+            const T cr = cre[j], ci = cim[j];
             re += cr * xs[j].x - ci * xs[j].y;
             im += cr * xs[j].y + ci * xs[j].x;
         }
@@ -141,11 +176,12 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
 
 template <typename V, int K, int MODE>
 void multi_axpy_reduce_launch(int k, const CoefList& cl, const PtrList& pl, V* y, size_t n, double2* partials,
-                              cudaStream_t st) {
+                              const double2* csrc, double2* cused, cudaStream_t st) {
     if constexpr (K > 1) {
-        if (k < K) return multi_axpy_reduce_launch<V, K - 1, MODE>(k, cl, pl, y, n, partials, st);
+        if (k < K) return multi_axpy_reduce_launch<V, K - 1, MODE>(k, cl, pl, y, n, partials, csrc, cused, st);
     }
-    (note_launch(), multi_axpy_reduce_kernel<V, K, MODE><<<blas_grid_size(), kBT, 0, st>>>(cl, pl, y, n, partials));
+    (note_launch(), multi_axpy_reduce_kernel<V, K, MODE><<<blas_grid_size(), kBT, 0, st>>>(cl, pl, y, n, partials,
+                                                                                           csrc, cused));
 }
 
 template <typename V>
@@ -177,6 +213,46 @@ __global__ void axpby_kernel(double2 al, const V* __restrict__ x, double2 be, V*
         o.x = ar * a.x - ai * a.y + br * b.x - bi * b.y;
         o.y = ar * a.y + ai * a.x + br * b.y + bi * b.x;
         y[i] = o;
+    }
+}
+
+// y = x / |x| with |x|^2 the sum of the gridDim.x partials in src (left by a
+// norm reduction of the same grid); y = 0 if |x| = 0.  CTA 0 stores |x| in hn.
+// Two multiplications per complex entry.
+template <typename V>
+__global__ void normalise_kernel(const double* src, double* hn, const V* __restrict__ x, V* y, size_t n) {
+    using T = typename VT<V>::T;
+    __shared__ double s_inv;
+    if (threadIdx.x < 32) {
+        double t = 0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) t += __ldcg(src + k);
+        t = warp_sum(t);
+        if (threadIdx.x == 0) {
+            const double h = sqrt(t);
+            s_inv = h > 0 ? 1.0 / h : 0.0;
+            if (blockIdx.x == 0) *hn = h;
+        }
+    }
+    __syncthreads();
+    const T a = (T)s_inv;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        V v = x[i];
+        v.x *= a;
+        v.y *= a;
+        y[i] = v;
+    }
+}
+
+// y = a x for a real a (two multiplications per complex entry)
+template <typename V>
+__global__ void scale_real_kernel(double a, const V* __restrict__ x, V* y, size_t n) {
+    using T = typename VT<V>::T;
+    const T ar = (T)a;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        V v = x[i];
+        v.x *= ar;
+        v.y *= ar;
+        y[i] = v;
     }
 }
 
@@ -245,6 +321,44 @@ cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* con
     return cudaGetLastError();
 }
 
+cudaError_t launch_normalise(int prec, const double* norm_partials, double* hn, const void* x, void* y, size_t n,
+                             cudaStream_t st) {
+    if (prec == 0)
+        (note_launch(), normalise_kernel<double2><<<blas_grid(), kBT, 0, st>>>(norm_partials, hn, (const double2*)x,
+                                                                            (double2*)y, n));
+    else
+        (note_launch(), normalise_kernel<float2><<<blas_grid(), kBT, 0, st>>>(norm_partials, hn, (const float2*)x,
+                                                                           (float2*)y, n));
+    return cudaGetLastError();
+}
+cudaError_t launch_scale_real(int prec, double a, const void* x, void* y, size_t n, cudaStream_t st) {
+    if (prec == 0)
+        (note_launch(), scale_real_kernel<double2><<<blas_grid(), kBT, 0, st>>>(a, (const double2*)x, (double2*)y, n));
+    else (note_launch(), scale_real_kernel<float2><<<blas_grid(), kBT, 0, st>>>(a, (const float2*)x, (float2*)y, n));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy_reduce_dev(int prec, int k, const double2* csrc, double2* cused, const void* const* x,
+                                         void* y, size_t n, int mode, double2* partials, cudaStream_t st) {
+    if (k < 1 || k > kMaxDots || (mode == 2 && k >= kMaxDots) || !csrc) return cudaErrorInvalidValue;
+    CoefList cl;
+    PtrList pl;
+    for (int j = 0; j < k; ++j) pl.p[j] = x[j];
+#define MAR(V, M) \
+    multi_axpy_reduce_launch<V, (M == 2 ? kMaxDots - 1 : kMaxDots), M>(k, cl, pl, (V*)y, n, partials, csrc, cused, st)
+    if (prec == 0) {
+        if (mode == 0) MAR(double2, 0);
+        else if (mode == 1) MAR(double2, 1);
+        else MAR(double2, 2);
+    } else {
+        if (mode == 0) MAR(float2, 0);
+        else if (mode == 1) MAR(float2, 1);
+        else MAR(float2, 2);
+    }
+#undef MAR
+    return cudaGetLastError();
+}
+
 cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
                                      int mode, double2* partials, cudaStream_t st) {
     if (k < 1 || k > kMaxDots || (mode == 2 && k >= kMaxDots)) return cudaErrorInvalidValue;
@@ -254,7 +368,8 @@ cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const vo
         cl.c[j] = c[j];
         pl.p[j] = x[j];
     }
-#define MAR(V, M) multi_axpy_reduce_launch<V, (M == 2 ? kMaxDots - 1 : kMaxDots), M>(k, cl, pl, (V*)y, n, partials, st)
+#define MAR(V, M) \
+    multi_axpy_reduce_launch<V, (M == 2 ? kMaxDots - 1 : kMaxDots), M>(k, cl, pl, (V*)y, n, partials, nullptr, nullptr, st)
     if (prec == 0) {
         if (mode == 0) MAR(double2, 0);
         else if (mode == 1) MAR(double2, 1);
