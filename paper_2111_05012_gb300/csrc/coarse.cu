@@ -74,7 +74,7 @@ __global__ void coarse_apply_kernel(CGeom g, int nc, int sap, int4 sb, const voi
         for (int row = warp; row < nc; row += nw) {
             const size_t base = ((size_t)X * nc + row) * 9 * nc;
             cx<TC> acc = czero<TC>();
-            for (int j = lane; j < 9 * nc; j += 32) acc = acc + ldb<TC, BF>(B, base + j) * xin[j];
+            for (int j = lane; j < 9 * nc; j += 32) cfma(acc, ldb<TC, BF>(B, base + j), xin[j]);
             acc.re = warp_sum(acc.re);
             acc.im = warp_sum(acc.im);
             if (lane == 0) {

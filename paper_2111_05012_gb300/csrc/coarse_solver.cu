@@ -198,8 +198,8 @@ template <> struct OpWord<float, false> {
         const float4 o = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
                                      __uint_as_float(v.w));
         const float4 xv = *reinterpret_cast<const float4*>(x);
-        acc = acc + cx<float>{o.x, o.y} * cx<float>{xv.x, xv.y};
-        acc = acc + cx<float>{o.z, o.w} * cx<float>{xv.z, xv.w};
+        cfma(acc, cx<float>{o.x, o.y}, cx<float>{xv.x, xv.y});
+        cfma(acc, cx<float>{o.z, o.w}, cx<float>{xv.z, xv.w});
     }
 };
 template <> struct OpWord<float, true> {
@@ -211,7 +211,7 @@ template <> struct OpWord<float, true> {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float2 o = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[e]));
-            acc = acc + cx<float>{o.x, o.y} * cx<float>{xs[2 * e], xs[2 * e + 1]};
+            cfma(acc, cx<float>{o.x, o.y}, cx<float>{xs[2 * e], xs[2 * e + 1]});
         }
     }
 };
@@ -220,7 +220,7 @@ template <> struct OpWord<double, false> {
     DEV static void mac(uint4 v, const cx<double>* x, cx<double>& acc) {
         const double2 o = make_double2(__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z));
         const double2 xv = *reinterpret_cast<const double2*>(x);
-        acc = acc + cx<double>{o.x, o.y} * cx<double>{xv.x, xv.y};
+        cfma(acc, cx<double>{o.x, o.y}, cx<double>{xv.x, xv.y});
     }
 };
 

@@ -32,6 +32,25 @@ template <typename T> HD cx<T> cmulc(cx<T> a, cx<T> b) {
 template <typename T> HD cx<T> timesI(cx<T> a) { return {-a.im, a.re}; }
 template <typename T> HD T norm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 template <typename T> HD cx<T> czero() { return {T(0), T(0)}; }
+// acc += a b, acc += conj(a) b and acc += s a (s real) as fused multiply-adds:
+// written as acc + a * b the product is formed first and then added, two
+// extra instructions per complex multiply-accumulate
+template <typename T> HD void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+template <typename T> HD void cfmac(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename T> HD void rfma(cx<T>& acc, T s, cx<T> a) {
+    acc.re = fma(s, a.re, acc.re);
+    acc.im = fma(s, a.im, acc.im);
+}
 template <typename T, typename U> HD cx<T> ccast(cx<U> a) { return {T(a.re), T(a.im)}; }
 
 // ---------------------------------------------------------------- double-float
@@ -273,9 +292,13 @@ template <class P> HD size_t spinor_bytes(int V) { return SpinorIO<P>::bytes_per
 //   P32: [mu][3][V] float4  (rows 0 and 1; row 2 = conj(row0 x row1))
 //   P16: [mu][3][V] uint2   (rows 0 and 1 as halves)
 template <typename T> DEV void reconstruct_row2(cx<T> u[3][3]) {
-    u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-    u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-    u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    cx<T> t0 = u[0][1] * u[1][2], t1 = u[0][2] * u[1][0], t2 = u[0][0] * u[1][1];
+    cfma(t0, -u[0][2], u[1][1]);
+    cfma(t1, -u[0][0], u[1][2]);
+    cfma(t2, -u[0][1], u[1][0]);
+    u[2][0] = conj(t0);
+    u[2][1] = conj(t1);
+    u[2][2] = conj(t2);
 }
 
 template <class P> struct GaugeIO;
@@ -409,8 +432,8 @@ template <typename T> DEV void clover_block_apply(const T pr[36], const cx<T>* i
         for (int j = 0; j < i; ++j) {
             int q = 3 + i * (i - 1) / 2 + j;
             cx<T> l = {pr[2 * q], pr[2 * q + 1]};
-            out[i] = out[i] + l * in[j];
-            out[j] = out[j] + cmulc(l, in[i]);
+            cfma(out[i], l, in[j]);
+            cfmac(out[j], l, in[i]);
         }
     }
 }
@@ -468,35 +491,32 @@ DEV void hop_accum(cx<T> out[12], const cx<T> psi[12], const cx<T> u[3][3], int 
             h[1][a] = psi[3 + a] + e1;
         }
     }
-    cx<T> w[2][3];
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            cx<T> acc = czero<T>();
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                if (dir > 0)
-                    acc = acc + u[a][b] * h[sp][b];
-                else
-                    acc = acc + cmulc(u[b][a], h[sp][b]);
-            }
-            w[sp][a] = coeff * acc;
-        }
-    }
+    // W h for both spin components, then out_upper += coeff W h, out_lower -/+= coeff e^dag W h
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        cx<T> l0, l1;
-        edag_mul(mu, w[0][a], w[1][a], l0, l1);
-        out[a] = out[a] + w[0][a];
-        out[3 + a] = out[3 + a] + w[1][a];
+        cx<T> w0, w1;
         if (dir > 0) {
-            out[6 + a] = out[6 + a] - l0;
-            out[9 + a] = out[9 + a] - l1;
+            w0 = u[a][0] * h[0][0];
+            w1 = u[a][0] * h[1][0];
+            cfma(w0, u[a][1], h[0][1]);
+            cfma(w1, u[a][1], h[1][1]);
+            cfma(w0, u[a][2], h[0][2]);
+            cfma(w1, u[a][2], h[1][2]);
         } else {
-            out[6 + a] = out[6 + a] + l0;
-            out[9 + a] = out[9 + a] + l1;
+            w0 = cmulc(u[0][a], h[0][0]);
+            w1 = cmulc(u[0][a], h[1][0]);
+            cfmac(w0, u[1][a], h[0][1]);
+            cfmac(w1, u[1][a], h[1][1]);
+            cfmac(w0, u[2][a], h[0][2]);
+            cfmac(w1, u[2][a], h[1][2]);
         }
+        cx<T> l0, l1;
+        edag_mul(mu, w0, w1, l0, l1);
+        rfma(out[a], coeff, w0);
+        rfma(out[3 + a], coeff, w1);
+        const T cl = dir > 0 ? -coeff : coeff;
+        rfma(out[6 + a], cl, l0);
+        rfma(out[9 + a], cl, l1);
     }
 }
 

@@ -648,10 +648,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
             }
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
-                cx<T> t = cmulc(Ar[q], r[q]);
-                part[0] += t.re;
-                part[1] += t.im;
-                part[2] += norm2(Ar[q]);
+                // <Ar, r> and |Ar|^2 as fused multiply-adds
+                part[0] = fma(Ar[q].re, r[q].re, part[0]);
+                part[0] = fma(Ar[q].im, r[q].im, part[0]);
+                part[1] = fma(Ar[q].re, r[q].im, part[1]);
+                part[1] = fma(-Ar[q].im, r[q].re, part[1]);
+                part[2] = fma(Ar[q].re, Ar[q].re, part[2]);
+                part[2] = fma(Ar[q].im, Ar[q].im, part[2]);
             }
         }
         block_sum<T, 3>(part, red);
@@ -660,8 +663,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
         if (active) {
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
-                z[q] = z[q] + alpha * r[q];
-                r[q] = r[q] - alpha * Ar[q];
+                cfma(z[q], alpha, r[q]);
+                cfma(r[q], -alpha, Ar[q]);
                 rsh[q * vbp + l] = r[q];
             }
         }
@@ -848,10 +851,13 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
             }
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
-                cx<float> t = cmulc(Ar[q], r[q]);
-                part[0] += t.re;
-                part[1] += t.im;
-                part[2] += norm2(Ar[q]);
+                // <Ar, r> and |Ar|^2 as fused multiply-adds
+                part[0] = fma(Ar[q].re, r[q].re, part[0]);
+                part[0] = fma(Ar[q].im, r[q].im, part[0]);
+                part[1] = fma(Ar[q].re, r[q].im, part[1]);
+                part[1] = fma(-Ar[q].im, r[q].re, part[1]);
+                part[2] = fma(Ar[q].re, Ar[q].re, part[2]);
+                part[2] = fma(Ar[q].im, Ar[q].im, part[2]);
             }
         }
         // one-barrier block reduction into buffer (it & 1)
@@ -873,8 +879,8 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
         if (active) {
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
-                z[q] = z[q] + alpha * r[q];
-                r[q] = r[q] - alpha * Ar[q];
+                cfma(z[q], alpha, r[q]);
+                cfma(r[q], -alpha, Ar[q]);
                 rsh[q * vbp + l] = r[q];
             }
         }

@@ -163,8 +163,8 @@ __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __res
                 if (active && i0 + u < nvec) {
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
-                        d0 = d0 + cmulc(ccast<T>(raw[u].get(k)), psi[k]);
-                        d1 = d1 + cmulc(ccast<T>(raw[u].get(6 + k)), psi[6 + k]);
+                        cfmac(d0, ccast<T>(raw[u].get(k)), psi[k]);
+                        cfmac(d1, ccast<T>(raw[u].get(6 + k)), psi[6 + k]);
                     }
                 }
                 q[4 * u] = d0.re;
@@ -222,8 +222,8 @@ __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __rest
                     const cx<T> a0 = xc[i0 + u], a1 = xc[nvec + i0 + u];
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
-                        out[k] = out[k] + a0 * ccast<T>(raw[u].get(k));
-                        out[6 + k] = out[6 + k] + a1 * ccast<T>(raw[u].get(6 + k));
+                        cfma(out[k], a0, ccast<T>(raw[u].get(k)));
+                        cfma(out[6 + k], a1, ccast<T>(raw[u].get(6 + k)));
                     }
                 }
             }
