@@ -545,6 +545,40 @@ __global__ void spinor_axpy_mixed_kernel(Geom g, int k, ZList z, void* x) {
     }
 }
 
+// ------------------------------------------------------------ domain vector in shared memory
+// The residual of a domain, one site per thread: FP32 as [6][vbp] float4 (two
+// complex numbers per 16-byte access), FP64 as [12][vbp] complex; 96 / 192
+// bytes per site either way.
+template <typename T> struct DomainVec;
+template <> struct DomainVec<float> {
+    DEV static void put(void* sh, int vbp, int l, const cx<float> v[12]) {
+        float4* p = (float4*)sh;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) p[c * vbp + l] = make_float4(v[2 * c].re, v[2 * c].im, v[2 * c + 1].re, v[2 * c + 1].im);
+    }
+    DEV static void get(const void* sh, int vbp, int l, cx<float> v[12]) {
+        const float4* p = (const float4*)sh;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float4 t = p[c * vbp + l];
+            v[2 * c] = {t.x, t.y};
+            v[2 * c + 1] = {t.z, t.w};
+        }
+    }
+};
+template <> struct DomainVec<double> {
+    DEV static void put(void* sh, int vbp, int l, const cx<double> v[12]) {
+        cx<double>* p = (cx<double>*)sh;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) p[q * vbp + l] = v[q];
+    }
+    DEV static void get(const void* sh, int vbp, int l, cx<double> v[12]) {
+        const cx<double>* p = (const cx<double>*)sh;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) v[q] = p[q * vbp + l];
+    }
+};
+
 // ------------------------------------------------------------ SAP half sweep
 // One CTA per domain of the given colour, one thread per site of the domain.
 // Computes r = b - D x on the domain (the residual of the SAP listing, needed
@@ -620,10 +654,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
             for (int q = 0; q < 12; ++q) r[q] = r[q] - Ar[q];
         }
 #pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            z[q] = czero<T>();
-            rsh[q * vbp + l] = r[q];
-        }
+        for (int q = 0; q < 12; ++q) z[q] = czero<T>();
+        DomainVec<T>::put(rsh, vbp, l, r);
     }
     for (int it = 0; it < nmr; ++it) {
         __syncthreads();
@@ -634,14 +666,12 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
             for (int mu = 0; mu < 4; ++mu) {
                 cx<T> u[3][3], psi[12];
                 if (lc[mu] != bk.b[mu] - 1) {
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l + lstr[mu]];
+                    DomainVec<T>::get(rsh, vbp, l + lstr[mu], psi);
                     GaugeIO<P>::load(U, g.V, mu, s, u);
                     hop_accum<T>(Ar, psi, u, mu, +1, -kappa);
                 }
                 if (lc[mu] != 0) {
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l - lstr[mu]];
+                    DomainVec<T>::get(rsh, vbp, l - lstr[mu], psi);
                     GaugeIO<P>::load(U, g.V, mu, s - g.stride[mu], u);
                     hop_accum<T>(Ar, psi, u, mu, -1, -kappa);
                 }
@@ -665,8 +695,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
             for (int q = 0; q < 12; ++q) {
                 cfma(z[q], alpha, r[q]);
                 cfma(r[q], -alpha, Ar[q]);
-                rsh[q * vbp + l] = r[q];
             }
+            DomainVec<T>::put(rsh, vbp, l, r);
         }
     }
     if (active) {
@@ -819,10 +849,8 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
             for (int q = 0; q < 12; ++q) r[q] = r[q] - Ar[q];
         }
 #pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            z[q] = czero<float>();
-            rsh[q * vbp + l] = r[q];
-        }
+        for (int q = 0; q < 12; ++q) z[q] = czero<float>();
+        DomainVec<float>::put(rsh, vbp, l, r);
     }
     for (int it = 0; it < nmr; ++it) {
         __syncthreads();   // r (and, first time, the staged operator) visible
@@ -837,14 +865,12 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
             for (int mu = 0; mu < 4; ++mu) {
                 cx<float> u[3][3], psi[12];
                 if (lc[mu] != bk.b[mu] - 1) {
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l + lstr[mu]];
+                    DomainVec<float>::get(rsh, vbp, l + lstr[mu], psi);
                     S::link(sl, vbp, mu, l, u);
                     hop_accum<float>(Ar, psi, u, mu, +1, -kappa);
                 }
                 if (lc[mu] != 0) {
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) psi[q] = rsh[q * vbp + l - lstr[mu]];
+                    DomainVec<float>::get(rsh, vbp, l - lstr[mu], psi);
                     S::link(sl, vbp, mu, l - lstr[mu], u);
                     hop_accum<float>(Ar, psi, u, mu, -1, -kappa);
                 }
@@ -881,8 +907,8 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
             for (int q = 0; q < 12; ++q) {
                 cfma(z[q], alpha, r[q]);
                 cfma(r[q], -alpha, Ar[q]);
-                rsh[q * vbp + l] = r[q];
             }
+            DomainVec<float>::put(rsh, vbp, l, r);
         }
     }
     if (active) {
