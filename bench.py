@@ -788,7 +788,8 @@ def main():
                    "setup_ms": setup_ms, "l2": "working set > L2 (no flush)",
                    "outer_iters": float(iters), "cycles": float(cycles), "converged": ok,
                    "phase_ms": {k: float(np.mean([i[k] for i in infos])) for k in
-                                ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other")},
+                                ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other", "ms_products",
+                                 "ms_orthogonalisation", "ms_true_residual")},
                    "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one sap_half_kernel<P32,256> launch on this
         # workload, from an ncu --set full capture of this kernel (91.14 + 3.06 MB); only for variant 0

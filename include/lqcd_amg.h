@@ -125,6 +125,9 @@ typedef struct {
     int nn_fallback;            /* 1 if the solve was redone with the plain cycle */
     int cycles;                 /* preconditioner applications (= iters for flexible GMRES, two per
                                    iteration for flexible BiCGStab); largest over a batch */
+    double ms_products;         /* part of ms_other: the outer solver's products D z (FP64-accurate) */
+    double ms_orthogonalisation;/* part of ms_other: FP64 Gram-Schmidt and normalisation (GPU time) */
+    double ms_true_residual;    /* part of ms_other: FP64 b - D x at restarts and exit */
 } amg_solve_info;
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -68,6 +68,9 @@ class amg_solve_info(ctypes.Structure):
         ("used_nn", ctypes.c_int),
         ("nn_fallback", ctypes.c_int),
         ("cycles", ctypes.c_int),
+        ("ms_products", ctypes.c_double),
+        ("ms_orthogonalisation", ctypes.c_double),
+        ("ms_true_residual", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -133,7 +133,7 @@ struct Reducer {
 inline double2 d2(cplx c) { return make_double2(c.real(), c.imag()); }
 
 // phase timers (Table 1 split: coarse / smoother / R+P / other)
-enum Phase { PH_COARSE = 0, PH_SMOOTH = 1, PH_RP = 2, PH_NPH = 3 };
+enum Phase { PH_COARSE = 0, PH_SMOOTH = 1, PH_RP = 2, PH_PROD = 3, PH_ORTH = 4, PH_RESID = 5, PH_NPH = 6 };
 struct PhaseTimer {
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, int>> marks;   // (event index, phase) start/stop pairs
@@ -600,6 +600,10 @@ amg_status arnoldi_D(amg_hierarchy* h, const void* z, void* w, int nb, cudaStrea
 // FP64 true residual at the end of the cycle still decides convergence.
 bool relaxed_product(double rel_residual, double tol) { return rel_residual <= 1e-3 * tol / 6e-8; }
 
+// largest loss of orthogonality (eps |w| / |w'|) one classical Gram-Schmidt pass may leave
+// before the outer solver projects a second time
+constexpr double kReorthLoss = 1e-9;
+
 // ---------------------------------------------------------------- outer FGMRES
 // Flexible GMRES(m) in FP64 for nb right-hand sides in lockstep: one batched
 // preconditioner call and one batched Arnoldi product per step, per-RHS
@@ -658,7 +662,9 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             for (int q = 0; q < nb; ++q) rn2[q] = st[q].bnorm * st[q].bnorm;
             x_is_zero = false;
         } else {
+            h->timer.start(PH_RESID, s);
             TRY(fine_D(h, 0, x, h->orr.p, b, nb, s));   // r = b - D x
+            h->timer.stop(s);
             TRY(batch_norms(h, nb, h->orr, rn2, s));
         }
         bool any = false;
@@ -694,38 +700,57 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             bool relax = true;
             for (int q = 0; q < nb; ++q)
                 if (!st[q].stop) relax = relax && relaxed_product(std::abs(st[q].g[j]) / st[q].bnorm, tol);
+            h->timer.start(PH_PROD, s);
             TRY(arnoldi_D(h, h->oZ[j]->p, h->ow.p, nb, s, relax));
-            // classical Gram-Schmidt, twice (with a good preconditioner w = D M v lies close to
-            // span V, so a second projection is always needed), with the coefficients summed
-            // on the device: the dots, the first update fused with the second pass's dots, the
-            // second update fused with |w|^2, and the normalisation v_{j+1} = w / |w| run back
-            // to back; one host synchronisation per step fetches the Hessenberg column
+            h->timer.stop(s);
+            // classical Gram-Schmidt in FP64 with the coefficients summed on the device: the
+            // dots, the update fused with |w'|^2, and the normalisation v_{j+1} = w' / |w'| run
+            // back to back, and one host synchronisation per step fetches the Hessenberg
+            // column.  One pass leaves v_{j+1} orthogonal to V up to about eps |w| / |w'|
+            // (|w|^2 = |w'|^2 + sum |h_ij|^2); only if that exceeds kReorthLoss does a second
+            // pass run (the Arnoldi relation D Z = V H holds to rounding either way, since every
+            // update uses exactly the coefficients that enter H).
             std::vector<const void*> vl(j + 1);
             const size_t R = (size_t)20 * red.grid;
             double2* const gp = h->gs_part.as<double2>();
             double2* const gc = h->gs_coef.as<double2>();
-            for (int q = 0; q < nb; ++q) {
-                if (st[q].stop) continue;
-                for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
-                double2 *A = gp + (3 * q) * R, *B = gp + (3 * q + 1) * R, *C = gp + (3 * q + 2) * R;
-                double2* cu = gc + 64 * q;
-                CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n, A, s));
-                CK(launch_multi_axpy_reduce_dev(0, j + 1, A, cu, vl.data(), F(h->ow.p, q), n, 1, B, s));
-                CK(launch_multi_axpy_reduce_dev(0, j + 1, B, cu + 32, vl.data(), F(h->ow.p, q), n, 0, C, s));
-                CK(launch_normalise(0, (const double*)C, (double*)(cu + 63), F(h->ow.p, q), F(h->oV[j + 1]->p, q), n,
-                                    s));
-            }
-            CK(cudaMemcpyAsync(h->gs_hcoef, gc, sizeof(double2) * 64 * nb, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            TRY(coarse_status(h));
-            std::vector<double> hnv(nb, 0.0);   // |w| exactly as the normalisation used it
-            for (int q = 0; q < nb; ++q) {
-                RhsState& r = st[q];
-                if (r.stop) continue;
-                const double2* hc = h->gs_hcoef + 64 * q;
-                for (int i = 0; i <= j; ++i) r.H[i][j] += cplx(hc[i].x, hc[i].y);
-                for (int i = 0; i <= j; ++i) r.H[i][j] += cplx(hc[32 + i].x, hc[32 + i].y);
-                hnv[q] = reinterpret_cast<const double*>(hc + 63)[0];
+            std::vector<double> hnv(nb, 0.0);   // |w'| exactly as the normalisation used it
+            std::vector<char> again(nb, 0);
+            for (int pass = 0; pass < 2; ++pass) {
+                h->timer.start(PH_ORTH, s);
+                bool any = false;
+                for (int q = 0; q < nb; ++q) {
+                    if (st[q].stop || (pass == 1 && !again[q])) continue;
+                    any = true;
+                    for (int i = 0; i <= j; ++i) vl[i] = F(h->oV[i]->p, q);
+                    double2 *A = gp + (3 * q) * R, *C = gp + (3 * q + 2) * R;
+                    double2* cu = gc + 64 * q + 32 * pass;
+                    CK(launch_multi_dot(0, j + 1, vl.data(), F(h->ow.p, q), n, A, s));
+                    CK(launch_multi_axpy_reduce_dev(0, j + 1, A, cu, vl.data(), F(h->ow.p, q), n, 0, C, s));
+                    CK(launch_normalise(0, (const double*)C, (double*)(gc + 64 * q + 63), F(h->ow.p, q),
+                                        F(h->oV[j + 1]->p, q), n, s));
+                }
+                h->timer.stop(s);
+                if (!any) break;
+                CK(cudaMemcpyAsync(h->gs_hcoef, gc, sizeof(double2) * 64 * nb, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                TRY(coarse_status(h));
+                bool more = false;
+                for (int q = 0; q < nb; ++q) {
+                    RhsState& r = st[q];
+                    if (r.stop || (pass == 1 && !again[q])) continue;
+                    const double2* hc = h->gs_hcoef + 64 * q + 32 * pass;
+                    double c2 = 0;
+                    for (int i = 0; i <= j; ++i) {
+                        r.H[i][j] += cplx(hc[i].x, hc[i].y);
+                        c2 += hc[i].x * hc[i].x + hc[i].y * hc[i].y;
+                    }
+                    hnv[q] = reinterpret_cast<const double*>(h->gs_hcoef + 64 * q + 63)[0];
+                    again[q] = pass == 0 && hnv[q] > 0 &&
+                               2.2e-16 * std::sqrt(hnv[q] * hnv[q] + c2) > kReorthLoss * hnv[q];
+                    more = more || again[q];
+                }
+                if (!more) break;
             }
             bool all_stopped = true;
             for (int q = 0; q < nb; ++q) {
@@ -1152,7 +1177,9 @@ amg_status fbicgstab(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, d
             rn = bn;
             x_is_zero = false;
         } else {
+            h->timer.start(PH_RESID, s);
             TRY(fine_D(h, 0, x, r, b, 1, s));
+            h->timer.stop(s);
             double rn2;
             TRY(red.norm2(0, r, n, &rn2, s));
             rn = std::sqrt(rn2);
@@ -1171,7 +1198,9 @@ amg_status fbicgstab(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, d
         while (iters < maxit) {
             TRY(precondition64(h, p, Mp, 1, s));
             ++info.cycles;
+            h->timer.start(PH_PROD, s);
             TRY(arnoldi_D(h, Mp, dmp, 1, s));
+            h->timer.stop(s);
             cplx den;
             TRY(red.dot(0, rt, dmp, n, &den, s));
             TRY(coarse_status(h));
@@ -1187,7 +1216,9 @@ amg_status fbicgstab(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, d
             if (std::sqrt(sn2) <= tol * bn) break;
             TRY(precondition64(h, sv, Ms, 1, s));
             ++info.cycles;
+            h->timer.start(PH_PROD, s);
             TRY(arnoldi_D(h, Ms, t, 1, s));
+            h->timer.stop(s);
             cplx ts;
             double tt;
             TRY(red.dot(0, t, sv, n, &ts, s));
@@ -2090,6 +2121,9 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         agg.ms_coarse = ms[PH_COARSE];
         agg.ms_smoother = ms[PH_SMOOTH];
         agg.ms_restrict_prolong = ms[PH_RP];
+        agg.ms_products = ms[PH_PROD];
+        agg.ms_orthogonalisation = ms[PH_ORTH];
+        agg.ms_true_residual = ms[PH_RESID];
         agg.ms_other = agg.ms_total - ms[PH_COARSE] - ms[PH_SMOOTH] - ms[PH_RP];
         *info = agg;
     }
