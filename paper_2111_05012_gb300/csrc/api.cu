@@ -619,11 +619,11 @@ struct RhsState {
     std::vector<cplx> sn, g;
 };
 
-amg_status batch_norms(amg_hierarchy* h, int nb, const DevBuf& base, std::vector<double>& out, cudaStream_t s) {
+amg_status batch_norms(amg_hierarchy* h, int nb, const void* base, std::vector<double>& out, cudaStream_t s) {
     const size_t n = fine_n(h);
     Reducer& red = h->red;
     for (int q = 0; q < nb; ++q)
-        CK(launch_norm2(0, fld(base, h, 0, q), n, (double*)red.dpart.p + (size_t)q * red.grid, s));
+        CK(launch_norm2(0, (const char*)base + q * fsz(h, 0), n, (double*)red.dpart.p + (size_t)q * red.grid, s));
     CK(cudaMemcpyAsync(red.hpart, red.dpart.p, sizeof(double) * red.grid * nb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double* hp = (const double*)red.hpart;
@@ -642,9 +642,8 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
     std::vector<RhsState> st(nb);
     // ||b|| for every right-hand side
     {
-        CK(cudaMemcpyAsync(h->orr.p, b, fs * nb, cudaMemcpyDeviceToDevice, s));
         std::vector<double> bn2;
-        TRY(batch_norms(h, nb, h->orr, bn2, s));
+        TRY(batch_norms(h, nb, b, bn2, s));
         for (int q = 0; q < nb; ++q) {
             st[q].bnorm = std::sqrt(bn2[q]);
             if (st[q].bnorm == 0) {
@@ -657,15 +656,16 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
     while (true) {
         // true FP64 residual of every right-hand side
         std::vector<double> rn2(nb, 0.0);
+        const void* rv = h->orr.p;   // the residual the cycle restarts from
         if (x_is_zero) {
-            CK(cudaMemcpyAsync(h->orr.p, b, fs * nb, cudaMemcpyDeviceToDevice, s));
+            rv = b;   // r = b
             for (int q = 0; q < nb; ++q) rn2[q] = st[q].bnorm * st[q].bnorm;
             x_is_zero = false;
         } else {
             h->timer.start(PH_RESID, s);
             TRY(fine_D(h, 0, x, h->orr.p, b, nb, s));   // r = b - D x
             h->timer.stop(s);
-            TRY(batch_norms(h, nb, h->orr, rn2, s));
+            TRY(batch_norms(h, nb, h->orr.p, rn2, s));
         }
         bool any = false;
         for (int q = 0; q < nb; ++q) {
@@ -693,7 +693,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             r.jend = -1;
             r.stop = r.done;
             if (r.done) CK(cudaMemsetAsync(F(h->oV[0]->p, q), 0, fs, s));
-            else CK(launch_scale_real(0, 1.0 / r.rn, F(h->orr.p, q), F(h->oV[0]->p, q), n, s));
+            else CK(launch_scale_real(0, 1.0 / r.rn, F(rv, q), F(h->oV[0]->p, q), n, s));
         }
         for (int j = 0; j < m; ++j) {
             TRY(precondition64(h, h->oV[j]->p, h->oZ[j]->p, nb, s));
