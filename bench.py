@@ -792,12 +792,12 @@ def main():
                                  "ms_orthogonalisation", "ms_true_residual")},
                    "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one sap_half_kernel<P32,256> launch on this
-        # workload, from an ncu --set full capture of this kernel (91.14 + 3.06 MB); only for variant 0
+        # workload, from an ncu --set full capture of this kernel (91.18 + 2.66 MB); only for variant 0
         "roofline": {"kernel": {0: "sap_half_kernel<P32,256>",
                                 1: "sap_half_staged_kernel<P32>"}.get(args.sap_variant, "sap_half (autotuned)"),
                      "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": 94.2e6 if (args.sap_variant == 0 and args.prec == "f32") else None,
+                     "traffic": 93.8e6 if (args.sap_variant == 0 and args.prec == "f32") else None,
                      "peak_kind": "FP32 FMA nominal from unit counts and 2.07 GHz",
                      "avg_launch_us": sap_launch_us, "flop_per_launch": flop_launch,
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind},
