@@ -1355,9 +1355,7 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
         // true FP64 residual of every unfinished problem
         for (auto& p : P) {
             if (p.r.done) continue;
-            if (!p.started) {
-                CK(cudaMemcpyAsync(p.h->orr.p, p.h->ob.p, fsz(p.h, 0), cudaMemcpyDeviceToDevice, p.st));
-            } else {
+            if (p.started) {
                 TRY(fine_D(p.h, 0, p.h->ox.p, p.h->orr.p, p.h->ob.p, 1, p.st));
                 TRY(ragged_norm_launch(p, p.h->orr.p));
             }
@@ -1368,6 +1366,7 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
             RhsState& r = p.r;
             if (r.done) continue;
             TRY(coarse_status(p.h));
+            const bool first = !p.started;   // x = 0: r = b
             r.rn = p.started ? std::sqrt(ragged_norm_value(p)) : r.bnorm;
             p.started = true;
             if (!std::isfinite(r.rn)) return fail(AMG_NAN, "ragged solve: non-finite residual");
@@ -1385,8 +1384,8 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
             r.g[0] = r.rn;
             r.jend = -1;
             r.stop = false;
-            CK(launch_axpby(0, make_double2(1.0 / r.rn, 0), p.h->orr.p, make_double2(0, 0), p.h->oV[0]->p,
-                            fine_n(p.h), p.st));
+            CK(launch_scale_real(0, 1.0 / r.rn, first ? p.h->ob.p : p.h->orr.p, p.h->oV[0]->p, fine_n(p.h),
+                                 p.st));
         }
         if (!any) break;
         for (int j = 0; j < mmax; ++j) {
@@ -1401,54 +1400,64 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
                 TRY(ragged_step(p.h, j, p.st));
             }
             if (!active) break;
-            // classical Gram-Schmidt, twice: dots; (update, dots of the updated w); (update, |w|^2)
-            std::vector<cplx> c(j + 1);
-            for (auto& p : P) {
-                if (p.r.done || p.r.stop) continue;
-                std::vector<const void*> vl(j + 1);
-                for (int i = 0; i <= j; ++i) vl[i] = p.h->oV[i]->p;
-                CK(launch_multi_dot(0, j + 1, vl.data(), p.h->ow.p, fine_n(p.h), p.h->red.dpart.as<double2>(), p.st));
-                CK(cudaMemcpyAsync(p.h->red.hpart, p.h->red.dpart.p, sizeof(double2) * p.h->red.grid * (j + 1),
-                                   cudaMemcpyDeviceToHost, p.st));
-            }
-            TRY(sync_all());
-            for (auto& p : P)
-                if (!(p.r.done || p.r.stop)) TRY(coarse_status(p.h));
+            // classical Gram-Schmidt in FP64 with device-side coefficients, as in fgmres: the
+            // dots, the update fused with |w'|^2 and the normalisation per problem, one
+            // synchronisation for the batch, and a second pass only where the loss of
+            // orthogonality estimate asks for it (reading C23)
+            const size_t R = (size_t)20 * blas_grid();
+            std::vector<char> in(P.size(), 0), again(P.size(), 0);
+            std::vector<double> hnv(P.size(), 0.0);
+            for (size_t t = 0; t < P.size(); ++t) in[t] = !(P[t].r.done || P[t].r.stop);
             for (int pass = 0; pass < 2; ++pass) {
-                for (auto& p : P) {
-                    if (p.r.done || p.r.stop) continue;
-                    ragged_sum(p, j + 1, c.data());
-                    std::vector<double2> nc(j + 1);
+                bool any_pass = false;
+                for (size_t t = 0; t < P.size(); ++t) {
+                    RaggedProb& p = P[t];
+                    if (!in[t] || (pass == 1 && !again[t])) continue;
+                    any_pass = true;
                     std::vector<const void*> vl(j + 1);
-                    for (int i = 0; i <= j; ++i) {
-                        p.r.H[i][j] += c[i];
-                        nc[i] = make_double2(-c[i].real(), -c[i].imag());
-                        vl[i] = p.h->oV[i]->p;
-                    }
-                    CK(launch_multi_axpy_reduce(0, j + 1, nc.data(), vl.data(), p.h->ow.p, fine_n(p.h), pass == 0,
-                                                p.h->red.dpart.as<double2>(), p.st));
-                    CK(cudaMemcpyAsync(p.h->red.hpart, p.h->red.dpart.p,
-                                       sizeof(double2) * p.h->red.grid * (pass == 0 ? j + 1 : 1),
-                                       cudaMemcpyDeviceToHost, p.st));
+                    for (int i = 0; i <= j; ++i) vl[i] = p.h->oV[i]->p;
+                    double2* gp = p.h->gs_part.as<double2>();
+                    double2* gc = p.h->gs_coef.as<double2>();
+                    const size_t n = fine_n(p.h);
+                    CK(launch_multi_dot(0, j + 1, vl.data(), p.h->ow.p, n, gp, p.st));
+                    CK(launch_multi_axpy_reduce_dev(0, j + 1, gp, gc + 32 * pass, vl.data(), p.h->ow.p, n, 0,
+                                                    gp + 2 * R, p.st));
+                    CK(launch_normalise(0, (const double*)(gp + 2 * R), (double*)(gc + 63), p.h->ow.p,
+                                        p.h->oV[j + 1]->p, n, p.st));
+                    CK(cudaMemcpyAsync(p.h->gs_hcoef, gc, sizeof(double2) * 64, cudaMemcpyDeviceToHost, p.st));
                 }
+                if (!any_pass) break;
                 TRY(sync_all());
+                bool more = false;
+                for (size_t t = 0; t < P.size(); ++t) {
+                    RaggedProb& p = P[t];
+                    if (!in[t] || (pass == 1 && !again[t])) continue;
+                    if (pass == 0) TRY(coarse_status(p.h));
+                    const double2* hc = p.h->gs_hcoef + 32 * pass;
+                    double c2 = 0;
+                    for (int i = 0; i <= j; ++i) {
+                        p.r.H[i][j] += cplx(hc[i].x, hc[i].y);
+                        c2 += hc[i].x * hc[i].x + hc[i].y * hc[i].y;
+                    }
+                    hnv[t] = reinterpret_cast<const double*>(p.h->gs_hcoef + 63)[0];
+                    again[t] = pass == 0 && hnv[t] > 0 &&
+                               2.2e-16 * std::sqrt(hnv[t] * hnv[t] + c2) > kReorthLoss * hnv[t];
+                    more = more || again[t];
+                }
+                if (!more) break;
             }
-            for (auto& p : P) {
+            for (size_t t = 0; t < P.size(); ++t) {
+                RaggedProb& p = P[t];
                 RhsState& r = p.r;
                 if (r.done || r.stop) continue;
-                const double hn = std::sqrt(ragged_norm_value(p));
+                const double hn = hnv[t];
                 r.H[j + 1][j] = hn;
                 r.iters++;
                 givens_column(r.H, r.cs, r.sn, r.g, j);
                 r.jend = j;
                 const double est = std::abs(r.g[j + 1]);
                 if (!std::isfinite(est)) return fail(AMG_NAN, "ragged solve: non-finite Arnoldi coefficient");
-                if (hn == 0 || est <= tol * r.bnorm || r.iters >= maxit) {
-                    r.stop = true;
-                } else {
-                    CK(launch_axpby(0, make_double2(1.0 / hn, 0), p.h->ow.p, make_double2(0, 0),
-                                    p.h->oV[j + 1]->p, fine_n(p.h), p.st));
-                }
+                if (hn == 0 || est <= tol * r.bnorm || r.iters >= maxit) r.stop = true;   // else v_{j+1} is in place
             }
         }
         // x += Z y

@@ -239,6 +239,30 @@ def test_config1_solution_matches_dense_lu():
     f.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_near_exact_preconditioner_second_gram_schmidt_pass(prec):
+    # many SAP sweeps and a coarse solve to 1e-13 make the cycle nearly exact, so
+    # w = D M v lies almost in span V (|w'| / |w| below 1e-7) and one classical
+    # Gram-Schmidt pass no longer keeps the basis orthogonal to 1e-9: the outer
+    # solver projects a second time; the solve still reaches the FP64 tolerance and
+    # matches the dense solution
+    dims = (4, 4, 4, 4)
+    f = Field(dims, 0.3, 1, 0.124, 1.0)
+    c = f.c
+    p = _params(c, (2, 2, 2, 2), 8, prec, n_init=2, n_adapt=1, sap_iters=40, mr_iters=24,
+                coarse_tol=1e-13, coarse_maxit=1000)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 1, 8))])
+    b = li.rhs(dims, 3)
+    x = to_dev(b) * 0
+    st, info = c.amg_solve(h, to_dev(b), x, 1, 1e-10, 100)
+    assert info.converged == 1 and info.true_rel_residual <= 1e-10
+    D = odirac.dense_matrix(f.U, 0.124, 1.0)
+    xd = np.linalg.solve(D, b.reshape(-1))
+    assert np.linalg.norm(from_dev(x, (f.V * 12,)) - xd) <= 1e-9 * np.linalg.norm(xd)
+    c.amg_hierarchy_destroy(h)
+    f.close()
+
+
 def test_checkpoint_roundtrip(tmp_path):
     dims = (4, 4, 4, 4)
     f = Field(dims, 0.3, 1, 0.124, 1.0)
