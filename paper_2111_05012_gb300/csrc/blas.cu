@@ -45,13 +45,21 @@ __global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, d
     for (int j = 0; j < 2 * NQ; ++j) acc[j] = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         V y = b[i];
+        const double yr = y.x, yi = y.y;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             V x = ((const V*)a.p[j])[i];
-            acc[2 * j] += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
-            acc[2 * j + 1] += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
+            const double xr = x.x, xi = x.y;
+            // conj(x) y as nested fused multiply-adds (two FP64 instructions per real accumulation)
+            acc[2 * j] = fma(xr, yr, acc[2 * j]);
+            acc[2 * j] = fma(xi, yi, acc[2 * j]);
+            acc[2 * j + 1] = fma(xr, yi, acc[2 * j + 1]);
+            acc[2 * j + 1] = fma(-xi, yr, acc[2 * j + 1]);
         }
-        if (NB) acc[2 * K] += (double)y.x * (double)y.x + (double)y.y * (double)y.y;
+        if (NB) {
+            acc[2 * K] = fma(yr, yr, acc[2 * K]);
+            acc[2 * K] = fma(yi, yi, acc[2 * K]);
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -135,8 +143,10 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const T cr = cre[j], ci = cim[j];
-            re += cr * xs[j].x - ci * xs[j].y;
-            im += cr * xs[j].y + ci * xs[j].x;
+            re = fma(cr, xs[j].x, re);
+            re = fma(-ci, xs[j].y, re);
+            im = fma(cr, xs[j].y, im);
+            im = fma(ci, xs[j].x, im);
         }
         o.x = re;
         o.y = im;
@@ -144,11 +154,18 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
         if constexpr (DOT) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                acc[2 * j] += (double)xs[j].x * (double)re + (double)xs[j].y * (double)im;
-                acc[2 * j + 1] += (double)xs[j].x * (double)im - (double)xs[j].y * (double)re;
+                const double xr = xs[j].x, xi = xs[j].y;
+                acc[2 * j] = fma(xr, (double)re, acc[2 * j]);
+                acc[2 * j] = fma(xi, (double)im, acc[2 * j]);
+                acc[2 * j + 1] = fma(xr, (double)im, acc[2 * j + 1]);
+                acc[2 * j + 1] = fma(-xi, (double)re, acc[2 * j + 1]);
             }
         }
-        if constexpr (NRM) acc[DOT ? 2 * K : 0] += (double)re * (double)re + (double)im * (double)im;
+        if constexpr (NRM) {
+            double& an = acc[DOT ? 2 * K : 0];
+            an = fma((double)re, (double)re, an);
+            an = fma((double)im, (double)im, an);
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -190,7 +207,8 @@ __global__ void norm2_kernel(const V* __restrict__ a, size_t n, double* partials
     double acc = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         V x = a[i];
-        acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+        acc = fma((double)x.x, (double)x.x, acc);
+        acc = fma((double)x.y, (double)x.y, acc);
     }
     acc = warp_sum(acc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -265,8 +283,10 @@ __global__ void multi_axpy_kernel(int k, CoefList c, PtrList x, V* y, size_t n) 
         for (int j = 0; j < k; ++j) {
             V a = ((const V*)x.p[j])[i];
             T cr = (T)c.c[j].x, ci = (T)c.c[j].y;
-            re += cr * a.x - ci * a.y;
-            im += cr * a.y + ci * a.x;
+            re = fma(cr, a.x, re);
+            re = fma(-ci, a.y, re);
+            im = fma(cr, a.y, im);
+            im = fma(ci, a.x, im);
         }
         o.x = re;
         o.y = im;

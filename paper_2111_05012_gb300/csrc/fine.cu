@@ -539,7 +539,7 @@ __global__ void spinor_axpy_mixed_kernel(Geom g, int k, ZList z, void* x) {
             SpinorIO<P32>::load(z.p[j], g.V, s, v);
             const cx<double> cj = {z.c[j].x, z.c[j].y};
 #pragma unroll
-            for (int q = 0; q < 12; ++q) acc[q] = acc[q] + cj * ccast<double>(v[q]);
+            for (int q = 0; q < 12; ++q) cfma(acc[q], cj, ccast<double>(v[q]));
         }
         SpinorIO<P64>::store(x, g.V, s, acc);
     }

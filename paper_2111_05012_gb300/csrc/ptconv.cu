@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kT) ptconv_forward_kernel(Geom g, int cin, con
                         for (int t = 0; t < 4; ++t) {
                             const cx<float> ws = wd[sp * 4 + t];
 #pragma unroll
-                            for (int col = 0; col < 3; ++col) acc[a][3 * sp + col] = acc[a][3 * sp + col] + ws * phi[3 * t + col];
+                            for (int col = 0; col < 3; ++col) cfma(acc[a][3 * sp + col], ws, phi[3 * t + col]);
                         }
                 }
             }
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kT) ptconv_wgrad_kernel(Geom g, const void* __
                 for (int t = 0; t < 4; ++t)
 #pragma unroll
                     for (int col = 0; col < 3; ++col)
-                        acc[a][sp * 4 + t] = acc[a][sp * 4 + t] + cmulc(phi[3 * t + col], gv[3 * sp + col]);
+                        cfmac(acc[a][sp * 4 + t], phi[3 * t + col], gv[3 * sp + col]);
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
