@@ -67,6 +67,8 @@ struct CoarseLevel {
     int nc = 0;
     int prec = 1;        // vector / arithmetic precision: 0 FP64, 1 FP32
     bool opbf = false;   // operator additionally stored in bfloat16 (B16) and applied from there
+    bool op32 = false;   // FP64 coarsest level whose Galerkin operator comes from an FP32 level: its
+                         // entries are FP32-exact, so B is stored in FP32 and widened in the kernels
     DevBuf B, B16;
     DevBuf tci;                 // bfloat16 stencil in the tensor-core operand layout (multi-RHS apply)
     DevBuf tcx;                 // packed bfloat16 vectors of one tensor-core launch
@@ -76,7 +78,8 @@ struct CoarseLevel {
     DevBuf cvecs;
     std::vector<DevBuf> gV, gZ;
     DevBuf gw, gr, gt;
-    int kprec() const { return opbf ? 2 : prec; }   // precision code of the stencil kernels
+    int kprec() const { return opbf ? 2 : op32 ? 3 : prec; }   // precision code of the stencil kernels
+    int bprec() const { return op32 ? 1 : prec; }               // storage precision of B
     const void* op() const { return opbf ? B16.p : B.p; }
 };
 
@@ -917,8 +920,11 @@ amg_status build_levels(amg_hierarchy* h) {
         const bool last = l + 1 == h->p.nlevels - 1;
         L.opbf = last ? h->p.prec_coarsest == AMG_BF16 : h->p.prec_coarse == AMG_BF16;
         L.prec = last ? (h->p.prec_coarsest == AMG_F64 ? 0 : 1) : (h->p.prec_coarse == 0 ? 0 : 1);
+        // the level whose vectors make this stencil: the fine level (test-vector precision) or level l
+        const int producer = l == 0 ? h->vp : h->lev[l].prec;
+        L.op32 = last && L.prec == 0 && producer == 1;
         const size_t ne = (size_t)L.g.V * 9 * L.nc * L.nc;
-        CK(L.B.ensure(ne * coarse_elem_bytes(L.prec)));
+        CK(L.B.ensure(ne * coarse_elem_bytes(L.bprec())));
         if (L.opbf) CK(L.B16.ensure(ne * 4));
         cur = L.g;
     }
@@ -944,7 +950,7 @@ amg_status orthonormalise_and_galerkin(amg_hierarchy* h, cudaStream_t s) {
     }
     amg_dirac* d = h->d;
     CoarseLevel& L = L1(h);
-    CK(launch_galerkin_fine(h->vp, L.prec, g, h->blk[0], h->p.nvec[0], h->vecs0.p, d->gauge->U[h->vp].p,
+    CK(launch_galerkin_fine(h->vp, L.bprec(), g, h->blk[0], h->p.nvec[0], h->vecs0.p, d->gauge->U[h->vp].p,
                             d->C[h->vp].p, d->kappa, L.B.p, s));
     if (L.opbf) CK(launch_complex_to_bf16(L.B.p, L.B16.p, (size_t)L.g.V * 9 * L.nc * L.nc, s));
     if (L.opbf && coarse_tc_supported(L.nc)) {
@@ -1003,7 +1009,7 @@ amg_status upload_cvecs(amg_hierarchy* h, int l, const double* host, cudaStream_
 amg_status galerkin_c(amg_hierarchy* h, int l, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
     CoarseLevel& N = h->lev[l + 1];
-    CK(launch_galerkin_coarse(L.prec, N.prec, L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, L.B.p, N.B.p, s));
+    CK(launch_galerkin_coarse(L.prec, N.bprec(), L.g, h->blk[l], L.nc, h->p.nvec[l], L.cvecs.p, L.B.p, N.B.p, s));
     if (N.opbf) CK(launch_complex_to_bf16(N.B.p, N.B16.p, (size_t)N.g.V * 9 * N.nc * N.nc, s));
     if (N.opbf && coarse_tc_supported(N.nc)) {
         CK(N.tci.ensure(coarse_tc_image_bytes(N.g.V, N.nc)));
@@ -1790,7 +1796,7 @@ amg_status amg_get_coarse_op(amg_hierarchy* h, int level, double* host_out) {
     DevBuf tmp;
     size_t bytes = (size_t)L.g.V * 9 * L.nc * L.nc * 2 * sizeof(double);
     CK(tmp.ensure(bytes));
-    CK(launch_coarse_op_export(L.prec, L.g.V, L.nc, L.B.p, tmp.as<double>(), 0));
+    CK(launch_coarse_op_export(L.bprec(), L.g.V, L.nc, L.B.p, tmp.as<double>(), 0));
     CK(cudaMemcpy(host_out, tmp.p, bytes, cudaMemcpyDeviceToHost));
     return AMG_OK;
 }

@@ -35,13 +35,19 @@ DEV int cneighbour(const CGeom& g, int X, int d, int c[4]) {
 // One CTA per coarse site; the 9 neighbour vectors are gathered into shared
 // memory, each warp then produces output rows (lanes stride over 9*Nc).
 // sap: hops that cross a block boundary of size sb are dropped (D_SAP).
-template <typename TC, bool BF> DEV cx<TC> ldb(const void* B, size_t i) { return ldc<TC>(B, i); }
-template <> DEV cx<float> ldb<float, true>(const void* B, size_t i) {
+// operator entry i in the storage ST: 0 the arithmetic precision TC, 1 bfloat16
+// (TC = float), 2 FP32 widened to TC = double (the entries are FP32-exact)
+template <typename TC, int ST> DEV cx<TC> ldb(const void* B, size_t i) { return ldc<TC>(B, i); }
+template <> DEV cx<float> ldb<float, 1>(const void* B, size_t i) {
     float2 f = __bfloat1622float2(__ldg((const __nv_bfloat162*)B + i));
     return {f.x, f.y};
 }
+template <> DEV cx<double> ldb<double, 2>(const void* B, size_t i) {
+    float2 f = __ldg((const float2*)B + i);
+    return {(double)f.x, (double)f.y};
+}
 
-template <typename TC, bool RESID, bool BF = false>
+template <typename TC, bool RESID, int BF = 0>
 __global__ void coarse_apply_kernel(CGeom g, int nc, int sap, int4 sb, const void* __restrict__ B,
                                     const void* __restrict__ in, void* out, const void* __restrict__ b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -134,15 +140,20 @@ cudaError_t launch_coarse_apply(int cprec, const GeomH& gh, int nc, const BlockH
     int sap = sb != nullptr;
     dim3 grid(g.V < nsm() * 8 ? g.V : nsm() * 8, nrhs);
     int th = 256;
-    if (cprec == 0) {
+    if (cprec == 0 || cprec == 3) {   // FP64 vectors; operator FP64 (0) or FP32-exact stored in FP32 (3)
         size_t smem = (size_t)9 * nc * sizeof(cx<double>);
-        if (b) (note_launch(), coarse_apply_kernel<double, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
-        else (note_launch(), coarse_apply_kernel<double, false><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+        if (cprec == 3) {
+            if (b) (note_launch(), coarse_apply_kernel<double, true, 2><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+            else (note_launch(), coarse_apply_kernel<double, false, 2><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+        } else {
+            if (b) (note_launch(), coarse_apply_kernel<double, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+            else (note_launch(), coarse_apply_kernel<double, false><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+        }
     } else {
         size_t smem = (size_t)9 * nc * sizeof(cx<float>);
         if (cprec == 2) {   // FP32 vectors, bfloat16 operator
-            if (b) (note_launch(), coarse_apply_kernel<float, true, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
-            else (note_launch(), coarse_apply_kernel<float, false, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+            if (b) (note_launch(), coarse_apply_kernel<float, true, 1><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
+            else (note_launch(), coarse_apply_kernel<float, false, 1><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
         } else {
             if (b) (note_launch(), coarse_apply_kernel<float, true><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));
             else (note_launch(), coarse_apply_kernel<float, false><<<grid, th, smem, st>>>(g, nc, sap, blk, B, in, out, b));

@@ -191,8 +191,8 @@ DEV int coarse_neighbour(const Args& a, int X, int d) {
 // complex entries (BF16 storage, FP32 arithmetic) or 1 FP64 complex entry,
 // multiplied into acc with the matching entries x[0 .. per-1] of the row's
 // neighbour block (shared memory, 16-byte aligned)
-template <typename TC, bool BF> struct OpWord;
-template <> struct OpWord<float, false> {
+template <typename TC, int ST> struct OpWord;   // ST: 0 as TC, 1 bfloat16, 2 FP32 widened to FP64
+template <> struct OpWord<float, 0> {
     static constexpr int per = 2;
     DEV static void mac(uint4 v, const cx<float>* x, cx<float>& acc) {
         const float4 o = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
@@ -202,7 +202,7 @@ template <> struct OpWord<float, false> {
         cfma(acc, cx<float>{o.z, o.w}, cx<float>{xv.z, xv.w});
     }
 };
-template <> struct OpWord<float, true> {
+template <> struct OpWord<float, 1> {
     static constexpr int per = 4;
     DEV static void mac(uint4 v, const cx<float>* x, cx<float>& acc) {
         const unsigned u[4] = {v.x, v.y, v.z, v.w};
@@ -215,7 +215,15 @@ template <> struct OpWord<float, true> {
         }
     }
 };
-template <> struct OpWord<double, false> {
+template <> struct OpWord<double, 2> {   // FP32-exact entries stored in FP32, FP64 arithmetic
+    static constexpr int per = 2;
+    DEV static void mac(uint4 v, const cx<double>* x, cx<double>& acc) {
+        const double2 x0 = *reinterpret_cast<const double2*>(x), x1 = *reinterpret_cast<const double2*>(x + 1);
+        cfma(acc, cx<double>{(double)__uint_as_float(v.x), (double)__uint_as_float(v.y)}, cx<double>{x0.x, x0.y});
+        cfma(acc, cx<double>{(double)__uint_as_float(v.z), (double)__uint_as_float(v.w)}, cx<double>{x1.x, x1.y});
+    }
+};
+template <> struct OpWord<double, 0> {
     static constexpr int per = 1;
     DEV static void mac(uint4 v, const cx<double>* x, cx<double>& acc) {
         const double2 o = make_double2(__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z));
@@ -233,7 +241,7 @@ template <> struct OpWord<double, false> {
 // into registers (kU coalesced 16-byte loads per lane and row in flight) --
 // the operator is read exactly once and never passes through shared memory.
 // Contains __syncthreads(): called by all threads of the CTA.
-template <typename TC, bool BF>
+template <typename TC, int BF>
 DEV void stencil_rows(const Args& a, cx<TC>* xbuf, int* nbr, const void* xin, void* yout, const void* w, int r0,
                       int r1, cx<TC>& dotp) {
     using W = OpWord<TC, BF>;
@@ -299,7 +307,7 @@ DEV void stencil_rows(const Args& a, cx<TC>* xbuf, int* nbr, const void* xin, vo
     }
 }
 
-template <typename TC, bool BF>
+template <typename TC, int BF>
 __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
     __shared__ cx<double> red_sh[kMaxQ * kWarps];
     __shared__ cx<double> res[kMaxQ];
@@ -569,16 +577,19 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     a.part = (double2*)part;
     a.bar = (GridBar*)state;
     if (nc % 2 != 0) return cudaErrorInvalidValue;
-    // cprec: 0 FP64, 1 FP32, 2 FP32 vectors with a bfloat16 operator
-    const int eb = cprec == 0 ? 16 : 8;
-    a.row_bytes = 9 * nc * (cprec == 2 ? 4 : eb);
+    // cprec: 0 FP64, 1 FP32, 2 FP32 vectors with a bfloat16 operator, 3 FP64 vectors with an
+    // FP32-stored operator (FP32-exact entries)
+    if (cprec < 0 || cprec > 3) return cudaErrorInvalidValue;
+    const int eb = (cprec == 0 || cprec == 3) ? 16 : 8;                        // vector entry
+    a.row_bytes = 9 * nc * (cprec == 2 ? 4 : cprec == 3 ? 8 : eb);             // operator entry
     if (a.row_bytes % 16 != 0) return cudaErrorInvalidValue;   // rows are read in 16-byte words
     const int block_bytes = 9 * nc * eb;                                  // one site's neighbour blocks
     a.xgroup = kXBytes / block_bytes;
     if (a.xgroup < 1) return cudaErrorInvalidValue;
-    const void* fn = cprec == 0   ? (const void*)coarse_bicgstab_kernel<double, false>
-                     : cprec == 1 ? (const void*)coarse_bicgstab_kernel<float, false>
-                                  : (const void*)coarse_bicgstab_kernel<float, true>;
+    const void* fn = cprec == 0   ? (const void*)coarse_bicgstab_kernel<double, 0>
+                     : cprec == 3 ? (const void*)coarse_bicgstab_kernel<double, 2>
+                     : cprec == 1 ? (const void*)coarse_bicgstab_kernel<float, 0>
+                                  : (const void*)coarse_bicgstab_kernel<float, 1>;
     const int smem = a.xgroup * (block_bytes + 9 * (int)sizeof(int));
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
