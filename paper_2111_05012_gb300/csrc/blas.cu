@@ -114,22 +114,21 @@ DEV void coefficients_from_partials(const double2* src, int k, double2* out, dou
 }
 
 template <typename V, int K, int MODE>   // MODE 0: |y|^2; 1: dots; 2: dots and |y|^2 (quantity K)
-__global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, double2* partials,
-                                         const double2* csrc, double2* cused) {
+__global__ void multi_axpy_reduce_kernel(PtrList x, V* y, size_t n, double2* partials, const double2* csrc,
+                                         double2* cused) {
     using T = typename VT<V>::T;
     constexpr bool DOT = MODE >= 1, NRM = MODE != 1;
     constexpr int NA = (DOT ? 2 * K : 0) + (NRM ? (DOT ? 2 : 1) : 0);
     __shared__ double red[NA * 32];
     __shared__ double2 cdev[K];
-    // coefficients: from the launch (host sums) or, with csrc, minus the sums of the
-    // partials a previous reduction left there (no host round trip)
-    if (csrc) coefficients_from_partials(csrc, K, cdev, cused);
+    // coefficients: minus the sums of the partials a previous reduction left at csrc
+    // (summed here, so no host round trip)
+    coefficients_from_partials(csrc, K, cdev, cused);
     T cre[K], cim[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const double2 cj = csrc ? cdev[j] : c.c[j];
-        cre[j] = (T)cj.x;
-        cim[j] = (T)cj.y;
+        cre[j] = (T)cdev[j].x;
+        cim[j] = (T)cdev[j].y;
     }
     double acc[NA];
 #pragma unroll
@@ -192,13 +191,13 @@ __global__ void multi_axpy_reduce_kernel(CoefList c, PtrList x, V* y, size_t n, 
 }
 
 template <typename V, int K, int MODE>
-void multi_axpy_reduce_launch(int k, const CoefList& cl, const PtrList& pl, V* y, size_t n, double2* partials,
-                              const double2* csrc, double2* cused, cudaStream_t st) {
+void multi_axpy_reduce_launch(int k, const PtrList& pl, V* y, size_t n, double2* partials, const double2* csrc,
+                              double2* cused, cudaStream_t st) {
     if constexpr (K > 1) {
-        if (k < K) return multi_axpy_reduce_launch<V, K - 1, MODE>(k, cl, pl, y, n, partials, csrc, cused, st);
+        if (k < K) return multi_axpy_reduce_launch<V, K - 1, MODE>(k, pl, y, n, partials, csrc, cused, st);
     }
-    (note_launch(), multi_axpy_reduce_kernel<V, K, MODE><<<blas_grid_size(), kBT, 0, st>>>(cl, pl, y, n, partials,
-                                                                                           csrc, cused));
+    (note_launch(), multi_axpy_reduce_kernel<V, K, MODE><<<blas_grid_size(), kBT, 0, st>>>(pl, y, n, partials, csrc,
+                                                                                           cused));
 }
 
 template <typename V>
@@ -361,11 +360,10 @@ cudaError_t launch_scale_real(int prec, double a, const void* x, void* y, size_t
 cudaError_t launch_multi_axpy_reduce_dev(int prec, int k, const double2* csrc, double2* cused, const void* const* x,
                                          void* y, size_t n, int mode, double2* partials, cudaStream_t st) {
     if (k < 1 || k > kMaxDots || (mode == 2 && k >= kMaxDots) || !csrc) return cudaErrorInvalidValue;
-    CoefList cl;
     PtrList pl;
     for (int j = 0; j < k; ++j) pl.p[j] = x[j];
 #define MAR(V, M) \
-    multi_axpy_reduce_launch<V, (M == 2 ? kMaxDots - 1 : kMaxDots), M>(k, cl, pl, (V*)y, n, partials, csrc, cused, st)
+    multi_axpy_reduce_launch<V, (M == 2 ? kMaxDots - 1 : kMaxDots), M>(k, pl, (V*)y, n, partials, csrc, cused, st)
     if (prec == 0) {
         if (mode == 0) MAR(double2, 0);
         else if (mode == 1) MAR(double2, 1);
@@ -379,26 +377,4 @@ cudaError_t launch_multi_axpy_reduce_dev(int prec, int k, const double2* csrc, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
-                                     int mode, double2* partials, cudaStream_t st) {
-    if (k < 1 || k > kMaxDots || (mode == 2 && k >= kMaxDots)) return cudaErrorInvalidValue;
-    CoefList cl;
-    PtrList pl;
-    for (int j = 0; j < k; ++j) {
-        cl.c[j] = c[j];
-        pl.p[j] = x[j];
-    }
-#define MAR(V, M) \
-    multi_axpy_reduce_launch<V, (M == 2 ? kMaxDots - 1 : kMaxDots), M>(k, cl, pl, (V*)y, n, partials, nullptr, nullptr, st)
-    if (prec == 0) {
-        if (mode == 0) MAR(double2, 0);
-        else if (mode == 1) MAR(double2, 1);
-        else MAR(double2, 2);
-    } else {
-        if (mode == 0) MAR(float2, 0);
-        else if (mode == 1) MAR(float2, 1);
-        else MAR(float2, 2);
-    }
-#undef MAR
-    return cudaGetLastError();
-}
+

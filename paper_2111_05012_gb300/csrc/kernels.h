@@ -142,9 +142,11 @@ cudaError_t launch_multi_axpy(int prec, int k, const double2* c, const void* con
 // y += sum_{j<k} c_j x_j (k <= 20), then in the same pass per-CTA partials of
 // mode 0: |y_new|^2 (double [grid]); 1: <x_j, y_new> (double2 [k][grid]);
 // 2: both, |y_new|^2 as quantity k (double2 (n2, 0), k <= 19)
-// as launch_multi_axpy_reduce, but the k coefficients are minus the sums of the k
-// quantities of blas_grid() partials at csrc (a previous multi_dot / dot-mode reduction),
-// summed on the device; the sums used are stored in cused[0..k) (if not NULL)
+// y += sum_j c_j x_j (j < k) fused with the next reduction (mode 0: |y|^2 as blas_grid()
+// double partials; 1: the k dots <x_j, y>; 2: both, |y|^2 as quantity k), where the
+// coefficients c_j are minus the sums of the k quantities of blas_grid() partials at csrc
+// (a previous multi_dot or dot-mode reduction), summed on the device in a fixed order;
+// the sums used are stored in cused[0..k) (if not NULL)
 cudaError_t launch_multi_axpy_reduce_dev(int prec, int k, const double2* csrc, double2* cused, const void* const* x,
                                          void* y, size_t n, int mode, double2* partials, cudaStream_t s);
 // y = x / |x| with |x|^2 the sum of the blas_grid() double partials of a norm reduction
@@ -153,8 +155,6 @@ cudaError_t launch_normalise(int prec, const double* norm_partials, double* hn, 
                              cudaStream_t s);
 // y = a x, a real
 cudaError_t launch_scale_real(int prec, double a, const void* x, void* y, size_t n, cudaStream_t s);
-cudaError_t launch_multi_axpy_reduce(int prec, int k, const double2* c, const void* const* x, void* y, size_t n,
-                                     int mode, double2* partials, cudaStream_t s);
 // multi_dot plus |b|^2 as quantity k (double2 (n2, 0)), k <= 19
 cudaError_t launch_multi_dot_norm(int prec, int k, const void* const* a, const void* b, size_t n, double2* partials,
                                   cudaStream_t s);
