@@ -367,7 +367,12 @@ amg_status amg_hierarchy_set_nn(amg_hierarchy* h, amg_nn* nn);
  * ||b - D x|| / ||b|| <= tol (recomputed at every restart and at exit) or
  * maxit outer steps.  Up to 12 right-hand sides are solved in lockstep: one
  * batched cycle (restriction, coarse solves, prolongation, SAP over all of
- * them) and one batched Arnoldi product per step.  x is an input initial
+ * them) and one batched Arnoldi product per step.  The Arnoldi basis is
+ * orthogonalised by classical Gram-Schmidt in FP64 with the coefficients
+ * summed on the device (one host synchronisation per step), with a second
+ * pass wherever eps ||w|| / ||w'|| would exceed 1e-9.  With outer_solver = 1
+ * the paper's flexible BiCGStab runs instead, one right-hand side at a
+ * time.  x is an input initial
  * guess if use_x0 != 0, else overwritten.  info (may be NULL) receives, over
  * all right-hand sides, the largest iteration count and true residual, the
  * summed phase times and whether all converged.  Returns AMG_NOT_CONVERGED
