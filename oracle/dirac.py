@@ -125,6 +125,57 @@ class WilsonClover:
         return psi * g5
 
 
+def apply_at(U: np.ndarray, kappa: float, csw: float, psi: np.ndarray, sites,
+             antiperiodic_t: bool = True) -> np.ndarray:
+    """(D psi)(x) of Eq. 1 at the listed sites only, each written out from its
+    own neighbourhood: the four clover leaves of every mu-nu plane around x
+    (reading C1), then the eight hops with their spin projectors and the
+    boundary phase on the t wrap (reading C3).  For checking a whole-lattice
+    result on a sample of sites at sizes where the whole-lattice oracle is too
+    slow.  U: (Lt,Lz,Ly,Lx,4,3,3); psi: (Lt,Lz,Ly,Lx,12); sites: (t,z,y,x)
+    tuples.  Returns (len(sites), 12)."""
+    lt, lz, ly, lx = U.shape[:4]
+    ext = (lx, ly, lz, lt)                       # extent in direction mu = 0..3
+
+    def idx(c):                                  # c = [x, y, z, t] -> array index
+        return (c[3] % lt, c[2] % lz, c[1] % ly, c[0] % lx)
+
+    def lnk(c, mu):
+        return U[idx(c) + (mu,)]
+
+    def mv(c, mu, s):
+        d = list(c)
+        d[mu] += s
+        return d
+
+    out = np.zeros((len(sites), 12), dtype=np.complex128)
+    for k, (t, z, y, x) in enumerate(sites):
+        c = [x, y, z, t]
+        F = np.zeros((12, 12), dtype=np.complex128)
+        if csw != 0.0:
+            for mu, nu in _PLANES:
+                xm, xn = mv(c, mu, -1), mv(c, nu, -1)
+                q = lnk(c, mu) @ lnk(mv(c, mu, 1), nu) @ _dag(lnk(mv(c, nu, 1), mu)) @ _dag(lnk(c, nu))
+                q = q + lnk(c, nu) @ _dag(lnk(mv(xm, nu, 1), mu)) @ _dag(lnk(xm, nu)) @ lnk(xm, mu)
+                q = q + _dag(lnk(xm, mu)) @ _dag(lnk(mv(xm, nu, -1), nu)) @ lnk(mv(xm, nu, -1), mu) @ lnk(xn, nu)
+                q = q + _dag(lnk(xn, nu)) @ lnk(xn, mu) @ lnk(mv(xn, mu, 1), nu) @ _dag(lnk(c, mu))
+                f = (q - _dag(q)) / 8j
+                f = f - np.trace(f) / 3.0 * np.eye(3)
+                F += np.kron(sigma_munu(mu, nu), f)
+        r = (np.eye(12) - kappa * csw * F) @ psi[idx(c)]
+        for mu in range(4):
+            for s in (1, -1):
+                nb = mv(c, mu, s)
+                wraps = (c[3] == lt - 1) if s > 0 else (c[3] == 0)
+                ph = -1.0 if (antiperiodic_t and mu == 3 and wraps) else 1.0
+                p = ph * psi[idx(nb)].reshape(4, 3)
+                u = lnk(c, mu) if s > 0 else _dag(lnk(nb, mu))   # U_mu(x) or U_mu(x - mu)^dag
+                proj = ID4 - GAMMA[mu] if s > 0 else ID4 + GAMMA[mu]
+                r = r - kappa * (proj @ (p @ u.T)).reshape(12)
+        out[k] = r
+    return out
+
+
 def site_index(x, y, z, t, dims):
     lx, ly, lz, lt = dims
     return x + lx * (y + ly * (z + lz * t))

@@ -94,3 +94,25 @@ def test_apply_D_config2_size():
         f.c.amg_apply_D(f.d, x, y, 1, prec)
         assert rel(from_dev(y, f.shape4 + (12,)), ref) < TOL[prec]
     f.close()
+
+
+def test_apply_D_config3_size_sampled():
+    # the 32^3 x 64 field the stencil benchmark times (exp(0.6iH) links, seed 3, kappa
+    # 0.130, c_sw 1.0, the benchmark's right-hand side), whole-lattice launches in FP64,
+    # FP32 and FP16, checked at 256 seeded random sites against the oracle evaluated site
+    # by site (the whole-lattice oracle is too slow at 2.1 M sites)
+    dims = (32, 32, 32, 64)
+    f = Field(dims, 0.6, 3, 0.130, 1.0)
+    psi = li.rhs(dims, 3)
+    rng = np.random.default_rng(33)
+    sites = [tuple(int(rng.integers(0, n)) for n in f.shape4) for _ in range(256)]
+    sites += [(0, 0, 0, 0), (f.shape4[0] - 1, f.shape4[1] - 1, f.shape4[2] - 1, f.shape4[3] - 1)]
+    ref = odirac.apply_at(f.U, 0.130, 1.0, psi.reshape(f.shape4 + (12,)), sites, True)
+    ti = tuple(np.array(sites).T)
+    for prec in (0, 1, 2):
+        x = to_dev(psi, DT[prec])
+        y = x.clone()
+        f.c.amg_apply_D(f.d, x, y, 1, prec)
+        got = from_dev(y, f.shape4 + (12,))[ti]
+        assert rel(got, ref) < TOL[prec], prec
+    f.close()

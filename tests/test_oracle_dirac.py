@@ -154,3 +154,18 @@ def test_dsap_equals_d_with_cut_links():
     # D = D_SAP + the face hops
     full = op.apply_sap(psi, block) + sum(op.block_hop(psi, mu, s, block) for mu in range(4) for s in (1, -1))
     assert np.abs(full - op.apply(psi)).max() < 1e-14
+
+
+@pytest.mark.parametrize("dims, eps, seed, kappa, ap", [((4, 4, 4, 4), 0.3, 1, 0.124, True),
+                                                        ((4, 6, 4, 8), 0.6, 7, 0.130, True),
+                                                        ((6, 4, 4, 4), 0.6, 2, 0.130, False)])
+def test_apply_at_matches_whole_lattice(dims, eps, seed, kappa, ap):
+    # the per-site evaluation (used to sample large lattices) against the whole-lattice
+    # operator at every site, including the t-wrap sites and periodic t
+    U = li.gauge_field(dims, eps, seed)
+    op = dirac.WilsonClover(U, kappa, 1.0, ap)
+    psi = _field(dims, 4)
+    ref = op.apply(psi).reshape(-1, 12)
+    sites = [tuple(s) for s in np.ndindex(op.shape4)]
+    got = dirac.apply_at(U, kappa, 1.0, psi, sites, ap)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
