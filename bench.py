@@ -4,7 +4,9 @@ right-hand side for the adaptive-multigrid Wilson-clover solver.
 Workload (synthetic stand-in for the paper's 32^3x64 / 64^3x64 ensembles):
 16^3 x 32 lattice, links exp(0.6 i H) (seed 2), kappa = 0.130, c_sw = 1.0,
 antiperiodic in t; two-level multigrid with 4^4 blocks and 24 test vectors
-(48 chiral), FP32 smoother / coarse operator, FP64 outer flexible GMRES(16).
+(48 chiral), FP32 smoother / coarse operator, test vectors stored in half
+precision (per-site scale) for restriction and prolongation, FP64 outer
+flexible GMRES(16).
 One step = one solve of a fresh complex Gaussian right-hand side.  The setup
 (null-space vectors, Galerkin operator) runs once before the timed region and
 is reported separately.
@@ -97,6 +99,19 @@ class ClockSampler:
         reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.samples)}
+
+
+def max_over_ranks(x, world):
+    """The largest x over the ranks of the default process group (x for one
+    rank): the job's time is the slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_info():
@@ -729,11 +744,7 @@ def main():
         torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     per_rhs = ms / (args.steps * world)
     ok = all(i["converged"] == 1 and i["true_rel_residual"] <= TOL for i in infos)
 
