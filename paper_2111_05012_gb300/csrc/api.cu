@@ -327,12 +327,6 @@ amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_z
 // ---------------------------------------------------------------- coarse solve
 CoarseLevel& L1(amg_hierarchy* h) { return h->lev[1]; }
 
-amg_status coarse_apply(amg_hierarchy* h, int l, const void* in, void* out, const void* b, cudaStream_t s) {
-    CoarseLevel& L = h->lev[l];
-    CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), in, out, b, 1, s));
-    return AMG_OK;
-}
-
 // BiCGStab(l) (Sleijpen-Fokkema) on the coarsest level to relative tolerance
 // coarse_tol: one persistent cooperative launch per right-hand side, no host
 // synchronisation.
@@ -1317,17 +1311,6 @@ struct RaggedProb {
 };
 
 // partial sums of the last reduction launched for problem p (k values)
-void ragged_sum(RaggedProb& p, int k, cplx* out) {
-    Reducer& red = p.h->red;
-    for (int i = 0; i < k; ++i) {
-        double re = 0, im = 0;
-        for (int t = 0; t < red.grid; ++t) {
-            re += red.hpart[(size_t)i * red.grid + t].x;
-            im += red.hpart[(size_t)i * red.grid + t].y;
-        }
-        out[i] = cplx(re, im);
-    }
-}
 amg_status ragged_norm_launch(RaggedProb& p, const void* v) {
     Reducer& red = p.h->red;
     CK(launch_norm2(0, v, fine_n(p.h), (double*)red.dpart.p, p.st));

@@ -74,7 +74,6 @@ DEV void tm_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 DEV void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 DEV void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-DEV void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // D (tmem) (+)= A (smem desc) . B (smem desc)^T, bf16 x bf16 -> f32
 DEV void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
