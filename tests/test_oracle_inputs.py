@@ -1,19 +1,23 @@
 """Pins of the seeded input generator (published SplitMix64 outputs, SU(3) properties)."""
+import os
+
 import numpy as np
 
 import lqcd_inputs as li
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
 
 def test_splitmix64_published_sequence():
-    # SplitMix64 started from state 0 (Steele, Lea, Flood 2014; Vigna's reference
-    # splitmix64.c): the first outputs are mix64(k * 0x9E3779B97F4A7C15), k = 1, 2, 3.
+    # SplitMix64 started from state 0: the first outputs are mix64(k * 0x9E3779B97F4A7C15),
+    # k = 1, 2, 3; the published values (with their source) are in golden/splitmix64_state0.txt
+    with open(os.path.join(GOLDEN, "splitmix64_state0.txt")) as fh:
+        want = [int(line, 16) for line in fh if line.strip() and not line.startswith("#")]
     g = np.uint64(0x9E3779B97F4A7C15)
     with np.errstate(over="ignore"):
-        z = np.array([g, g * np.uint64(2), g * np.uint64(3)], dtype=np.uint64)
+        z = np.array([g * np.uint64(k) for k in range(1, len(want) + 1)], dtype=np.uint64)
     out = li._mix64(z)
-    assert int(out[0]) == 0xE220A8397B1DCDAF
-    assert int(out[1]) == 0x6E789E6AA1B965F4
-    assert int(out[2]) == 0x06C45D188009454F
+    assert [int(v) for v in out] == want
 
 
 def test_counter_mode_is_position_independent():
