@@ -22,11 +22,7 @@ import sys
 import threading
 import time
 
-# the FP64 oracle legs report the cores they use: keep numpy's BLAS on one
-# thread unless the caller chose otherwise (must precede the numpy import)
-os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-
-import numpy as np  # noqa: E402
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
