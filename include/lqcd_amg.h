@@ -155,6 +155,41 @@ void amg_lattice_destroy(amg_lattice* lat);
 amg_status amg_gauge_create(amg_lattice* lat, const double* U_host, amg_gauge** out);
 void amg_gauge_destroy(amg_gauge* g);
 
+/* Seeded synthetic inputs.  The paper's experiments (Sec. 5) use gauge
+ * ensembles that are not distributed with it; the workloads of this library
+ * stand in for them with U_mu(x) = exp(i eps H), H = (A + A^dag)/2 minus its
+ * trace / 3, A a 3x3 complex matrix with N(0, 1) real and imaginary parts.
+ * Random numbers: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) in counter
+ * mode -- word n of stream (seed, id) is mix64(key + (n + 1) * G) with
+ * G = 0x9E3779B97F4A7C15 and key = mix64(seed * G + id); a word w gives the
+ * double ((w >> 11) + 1) * 2^-53 in (0, 1]; complex normal m is the
+ * Box-Muller pair of words 2m and 2m + 1: sqrt(-2 ln u0) (cos, sin)(2 pi u1).
+ * Generated on the device; every value is a pure function of (seed, id, m),
+ * so a host implementation of the same definition reproduces it to the
+ * rounding of ln, sqrt, cos and sin. */
+#define AMG_RNG_STREAM_GAUGE 1     /* link entries: complex normal 9 (4 site + mu) + row-major entry */
+#define AMG_RNG_STREAM_RHS 2       /* Gaussian right-hand sides (seed + 1000 by convention) */
+#define AMG_RNG_STREAM_TESTVEC 3   /* initial test vectors (seed + 2000 + 1000 level by convention) */
+#define AMG_RNG_STREAM_NN 6        /* training errors e0 of the learned preconditioner */
+
+/* Gauge field U_mu(x) = exp(i eps H_mu(x)) with A drawn from stream
+ * (seed, AMG_RNG_STREAM_GAUGE); the exponential is evaluated in FP64 from the
+ * eigenvalues of eps H (unitary, det 1 to rounding).  Same handle as
+ * amg_gauge_create, without a host copy of the field.  AMG_EINVAL for a
+ * NULL argument or non-finite eps, AMG_ENOMEM / AMG_ECUDA on device failure. */
+amg_status amg_gauge_random(amg_lattice* lat, double eps, uint64_t seed, amg_gauge** out);
+
+/* Copy the FP64 links of g to host memory in the canonical gauge layout
+ * (V*4*9 complex doubles, caller-owned). */
+amg_status amg_gauge_get(amg_gauge* g, double* host_out);
+
+/* Complex normals start .. start+count-1 of stream (seed, stream) written to
+ * the device array out as (re, im) doubles (2*count doubles, caller-owned),
+ * on stream s.  A canonical fine field of volume V is count = 12 V; field k
+ * of a stream starts at start = 12 V k.  AMG_EINVAL for a NULL output with
+ * count > 0 or a negative stream id. */
+amg_status amg_random_normal(uint64_t seed, int stream, uint64_t start, uint64_t count, double* out, amg_stream s);
+
 /* Wilson-clover operator of Eq. 1 with hopping parameter kappa and clover
  * coefficient csw.  Builds the clover term F(x) on the device in FP64 from
  * the links: F = -kappa csw sum_{mu<nu} sigma_munu F_munu, F_munu the
@@ -216,8 +251,9 @@ amg_status amg_apply_Dsap(amg_dirac* d, const int block[4], const void* in, void
  * operator D_c = <I|D|J> (Eq. 7) is built, then n_adapt passes v <- M v
  * follow.  init_vecs[l] is a host array of nvec[l] canonical vectors of
  * level l (doubles: fine [site][spin][colour][re, im], coarse
- * [site][Nc][re, im]), one array for every level 0..nlevels-2; the random
- * numbers of the setup are these inputs.  With three or more grids, level
+ * [site][Nc][re, im]), one array for every level 0..nlevels-2, each in host
+ * or device memory (copied with cudaMemcpyDefault); the random numbers of
+ * the setup are these inputs (amg_random_normal draws them on the device).  With three or more grids, level
  * l >= 1 is set up the same way with its own SAP and cycle, right after its
  * stencil is first built; every later change of level l's stencil rebuilds
  * the stencils below it from their unchanged vectors.
@@ -352,6 +388,31 @@ amg_status amg_nn_apply(amg_nn* nn, const float* in, float* out, amg_stream s);
  * (canonical float fields, device) for the loss mean ||N(r) - e||^2/||e||^2;
  * loss_out (may be NULL) receives the batch loss before the step. */
 amg_status amg_nn_train_step(amg_nn* nn, const float* r, const float* e, int npairs, double lr, double* loss_out,
+                             amg_stream s);
+
+/* Training run of amg_learned_train. */
+typedef struct {
+    int npairs;      /* (residual, error) pairs generated and trained on [4096] */
+    int batch;       /* pairs per Adam step; npairs / batch steps are taken [16] */
+    double lr;       /* Adam learning rate (betas 0.9 / 0.999, eps 1e-8) [1e-3] */
+    uint64_t seed;   /* e0 of pair k: canonical field k of stream (seed, AMG_RNG_STREAM_NN) [5] */
+} amg_train_params;
+
+/* Fill p with the defaults listed above. */
+void amg_train_params_default(amg_train_params* p);
+
+/* Train nn on (residual, error) pairs that the solver itself makes on its own
+ * gauge field, all on the device: for pair k, e0 = Gaussian field k of stream
+ * (seed, AMG_RNG_STREAM_NN), e = e0 - M D e0 (the error one application of the
+ * multigrid preconditioner M of Sec. 3 leaves, with D and M as in
+ * amg_apply_D / amg_precondition in FP64), r = D e; the pairs (r, e) are
+ * rounded to FP32 and every `batch` of them makes one amg_nn_train_step.
+ * losses (host, may be NULL) receives npairs / batch batch losses, in order.
+ * nn must have been created on the hierarchy's operator.  Synchronises the
+ * stream.  The paper has no learned preconditioner; this is the task's
+ * extension of the preconditioner slot of Sec. 3 (see amg_hierarchy_set_nn
+ * for its use in a solve). */
+amg_status amg_learned_train(amg_hierarchy* h, amg_nn* nn, const amg_train_params* p, double* losses,
                              amg_stream s);
 
 /* Use the network inside the solve's preconditioner (NULL removes it):

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libamg.so")
 
-SOURCES = ["fine.cu", "transfer.cu", "coarse.cu", "coarse_mg.cu", "coarse_tc.cu", "coarse_solver.cu", "blas.cu", "api.cu", "noalloc.cu", "ptconv.cu", "nn_api.cu"]
+SOURCES = ["fine.cu", "transfer.cu", "coarse.cu", "coarse_mg.cu", "coarse_tc.cu", "coarse_solver.cu", "blas.cu", "api.cu", "noalloc.cu", "ptconv.cu", "nn_api.cu", "inputs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

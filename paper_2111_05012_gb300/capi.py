@@ -77,6 +77,11 @@ class amg_solve_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class amg_train_params(ctypes.Structure):
+    _fields_ = [("npairs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
 _vp = ctypes.c_void_p
 _ip = ctypes.POINTER(ctypes.c_int)
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -92,6 +97,9 @@ PROTOTYPES = {
     "amg_lattice_destroy": (None, [_vp]),
     "amg_gauge_create": (_i, [_vp, _dp, ctypes.POINTER(_vp)]),
     "amg_gauge_destroy": (None, [_vp]),
+    "amg_gauge_random": (_i, [_vp, _d, ctypes.c_uint64, ctypes.POINTER(_vp)]),
+    "amg_gauge_get": (_i, [_vp, _dp]),
+    "amg_random_normal": (_i, [ctypes.c_uint64, _i, ctypes.c_uint64, ctypes.c_uint64, _vp, _vp]),
     "amg_dirac_create": (_i, [_vp, _d, _d, ctypes.POINTER(_vp)]),
     "amg_dirac_destroy": (None, [_vp]),
     "amg_dirac_get_clover": (_i, [_vp, _dp]),
@@ -125,6 +133,8 @@ PROTOTYPES = {
     "amg_nn_apply": (_i, [_vp, _vp, _vp, _vp]),
     "amg_nn_train_step": (_i, [_vp, _vp, _vp, _i, _d, _dp, _vp]),
     "amg_hierarchy_set_nn": (_i, [_vp, _vp]),
+    "amg_train_params_default": (None, [ctypes.POINTER(amg_train_params)]),
+    "amg_learned_train": (_i, [_vp, _vp, ctypes.POINTER(amg_train_params), _dp, _vp]),
 }
 
 _lib = None
@@ -212,6 +222,23 @@ def amg_gauge_destroy(h):
     load().amg_gauge_destroy(h)
 
 
+def amg_gauge_random(lat, eps, seed):
+    h = _vp()
+    _check(load().amg_gauge_random(lat, float(eps), int(seed), ctypes.byref(h)))
+    return h
+
+
+def amg_gauge_get(g, volume):
+    out = np.empty((volume, 4, 3, 3, 2), dtype=np.float64)
+    _check(load().amg_gauge_get(g, out.ctypes.data_as(_dp)))
+    return out
+
+
+def amg_random_normal(seed, stream_id, start, count, out, stream=None):
+    """Complex normals start..start+count-1 of (seed, stream_id) into the device tensor out (2*count doubles)."""
+    _check(load().amg_random_normal(int(seed), int(stream_id), int(start), int(count), _ptr(out), _stream(stream)))
+
+
 def amg_dirac_create(gauge, kappa, csw):
     h = _vp()
     _check(load().amg_dirac_create(gauge, float(kappa), float(csw), ctypes.byref(h)))
@@ -257,12 +284,21 @@ def amg_apply_Dsap(d, block, inp, out, nrhs=1, prec=AMG_F64, stream=None):
 
 
 def _vec_list(vecs):
-    """Pointer array of AMG_MAX_LEVELS entries (NULL past the given levels)."""
-    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in vecs]
-    if len(arrs) > AMG_MAX_LEVELS:
+    """Pointer array of AMG_MAX_LEVELS entries (NULL past the given levels);
+    each entry a host array (float64) or a float64 device tensor."""
+    if len(vecs) > AMG_MAX_LEVELS:
         raise ValueError("more vector sets than levels")
-    lst = (_dp * AMG_MAX_LEVELS)(*[a.ctypes.data_as(_dp) for a in arrs])
-    return arrs, lst
+    keep, ptrs = [], []
+    for v in vecs:
+        if hasattr(v, "data_ptr"):
+            keep.append(v)
+            ptrs.append(ctypes.cast(_ptr(v), _dp))
+        else:
+            a = np.ascontiguousarray(v, dtype=np.float64)
+            keep.append(a)
+            ptrs.append(a.ctypes.data_as(_dp))
+    lst = (_dp * AMG_MAX_LEVELS)(*ptrs)
+    return keep, lst
 
 
 def amg_setup(d, params, init_vecs):
@@ -415,3 +451,17 @@ def amg_nn_train_step(nn, r, e, npairs, lr=1e-3, stream=None):
 
 def amg_hierarchy_set_nn(h, nn):
     _check(load().amg_hierarchy_set_nn(h, nn))
+
+
+def amg_train_params_default():
+    p = amg_train_params()
+    load().amg_train_params_default(ctypes.byref(p))
+    return p
+
+
+def amg_learned_train(h, nn, params=None, stream=None):
+    """Generate (residual, error) pairs with the solver and train nn on them; returns the batch losses."""
+    p = params or amg_train_params_default()
+    losses = np.zeros(max(1, p.npairs // p.batch), dtype=np.float64)
+    _check(load().amg_learned_train(h, nn, ctypes.byref(p), losses.ctypes.data_as(_dp), _stream(stream)))
+    return losses

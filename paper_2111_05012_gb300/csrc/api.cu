@@ -76,6 +76,7 @@ struct CoarseLevel {
     // levels between the fine and the coarsest grid: the level's own test
     // vectors (coarsening to the next level) and its FGMRES(inter_m) space
     DevBuf cvecs;
+    DevBuf cvecs_next;          // (0-b): the pass's new vectors while M still reads cvecs
     std::vector<DevBuf> gV, gZ;
     DevBuf gw, gr, gt;
     int kprec() const { return opbf ? 2 : op32 ? 3 : prec; }   // precision code of the stencil kernels
@@ -191,6 +192,7 @@ struct amg_hierarchy {
     BlockH blk[AMG_MAX_LEVELS - 1];
     DevBuf vecs0;
     DevBuf vecs16;   // half-precision copy of vecs0 for restriction / prolongation (rp == 2)
+    DevBuf vecs_next;   // (0-b): the pass's new vectors while the cycle still reads vecs0 (rp != 2)
     std::vector<CoarseLevel> lev;   // lev[l] for l = 1..nlevels-1 (lev[0] unused)
     // fine workspaces per precision: b, x
     DevBuf fb[3], fx[3];
@@ -328,8 +330,9 @@ amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_z
 CoarseLevel& L1(amg_hierarchy* h) { return h->lev[1]; }
 
 // BiCGStab(l) (Sleijpen-Fokkema) on the coarsest level to relative tolerance
-// coarse_tol: one persistent cooperative launch per right-hand side, no host
-// synchronisation.
+// coarse_tol: one persistent cooperative launch per group of up to
+// coarse_solver_max_rhs() right-hand sides in lockstep (the operator streamed
+// once per stencil pass for the group), no host synchronisation.
 amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int nb, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
     const int ell = h->p.coarse_ell;
@@ -341,13 +344,15 @@ amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int 
         U[j] = w[4 + ell + j]->p;
     }
     const size_t cv = coarse_n(L) * coarse_elem_bytes(L.prec);
-    for (int q = 0; q < nb; ++q) {
+    const int group = h->graph_mode ? 1 : coarse_solver_max_rhs();
+    for (int q = 0, k = 0; q < nb; q += group, ++k) {
+        const int ng = std::min(group, nb - q);
         CK(cudaMemsetAsync(L.cs_state.p, 0, 12, s));
         CK(launch_coarse_bicgstab(L.kprec(), L.g, L.nc, L.op(), (const char*)b + q * cv, (char*)x + q * cv, w[2]->p, R,
                                   U, ell, h->p.coarse_tol, h->p.coarse_maxit, L.cs_part.p, L.cs_state.p,
-                                  h->graph_mode ? 8 : 0, s));
-        // error word of this solve (a later one would overwrite it): fold into word 2 of the host mirror
-        CK(cudaMemcpyAsync(h->hstate + 4 * (q % 16), L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
+                                  h->graph_mode ? 8 : 0, s, ng));
+        // error word of this launch (a later one would overwrite it): fold into word 2 of the host mirror
+        CK(cudaMemcpyAsync(h->hstate + 4 * (k % 16), L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
     }
     return AMG_OK;
 }
@@ -865,8 +870,10 @@ amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
         }
         size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
         int nv = 4 + 2 * (h->p.coarse_ell + 1);
+        // [0] bc and [1] xc hold the batch; the solver's rt, R_j, U_j one lockstep group
+        const int ng = l == h->p.nlevels - 1 ? std::min(nb, coarse_solver_max_rhs()) : 1;
         while ((int)h->cw[l].size() < nv) h->cw[l].push_back(new DevBuf());
-        for (int k = 0; k < nv; ++k) CK(h->cw[l][k]->ensure(bytes * (k < 2 ? nb : 1)));
+        for (int k = 0; k < nv; ++k) CK(h->cw[l][k]->ensure(bytes * (k < 2 ? nb : ng)));
     }
     for (int l = 1; l + 1 < h->p.nlevels; ++l) {
         CoarseLevel& L = h->lev[l];
@@ -960,7 +967,7 @@ amg_status upload_vectors(amg_hierarchy* h, const double* host, cudaStream_t s) 
     CK(h->canon.ensure(cb));
     const size_t vb = fine_spinor_bytes(h->vp, g.V);
     for (int i = 0; i < h->p.nvec[0]; ++i) {
-        CK(cudaMemcpyAsync(h->canon.p, host + (size_t)i * g.V * 24, cb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->canon.p, host + (size_t)i * g.V * 24, cb, cudaMemcpyDefault, s));
         if (h->vp == 0) {
             CK(launch_pack_spinor(0, g, h->canon.p, (char*)h->vecs0.p + i * vb, 1, s));
         } else {
@@ -989,10 +996,10 @@ amg_status upload_cvecs(amg_hierarchy* h, int l, const double* host, cudaStream_
     CoarseLevel& L = h->lev[l];
     const size_t n = coarse_n(L) * h->p.nvec[l];
     if (L.prec == 0) {
-        CK(cudaMemcpyAsync(L.cvecs.p, host, n * 16, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(L.cvecs.p, host, n * 16, cudaMemcpyDefault, s));
     } else {
         CK(h->canon.ensure(n * 16));
-        CK(cudaMemcpyAsync(h->canon.p, host, n * 16, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->canon.p, host, n * 16, cudaMemcpyDefault, s));
         CK(launch_convert_flat(0, 1, h->canon.p, L.cvecs.p, n, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -1057,15 +1064,19 @@ amg_status setup_coarse_level(amg_hierarchy* h, int l, const double* const* init
         }
     TRY(ortho_galerkin_c(h, l, s));
     if (l + 2 < h->p.nlevels) TRY(setup_coarse_level(h, l + 1, init, s));
+    // every vector of a pass goes through the same cycle M_l (built from the vectors the pass
+    // starts with): the new vectors are collected apart and replace the old ones at its end
+    if (h->p.n_adapt > 0) CK(L.cvecs_next.ensure(vb * h->p.nvec[l]));
     for (int k = 0; k < h->p.n_adapt; ++k) {
         for (int i = 0; i < h->p.nvec[l]; ++i) {
-            void* vi = (char*)L.cvecs.p + i * vb;
-            TRY(vcycle_c(h, l, vi, L.gt.p, s));
-            TRY(normalise_c(h, l, L.gt.p, vi, s));
+            TRY(vcycle_c(h, l, (char*)L.cvecs.p + i * vb, L.gt.p, s));
+            TRY(normalise_c(h, l, L.gt.p, (char*)L.cvecs_next.p + i * vb, s));
         }
+        L.cvecs.swap(L.cvecs_next);
         TRY(ortho_galerkin_c(h, l, s));
         TRY(refresh_c(h, l + 1, s));
     }
+    L.cvecs_next.release();
     return AMG_OK;
 }
 
@@ -1480,6 +1491,7 @@ const GeomH* amg_internal_geom(const amg_dirac* d) { return &d->gauge->lat->g; }
 const void* amg_internal_links(const amg_dirac* d, int prec) { return d->gauge->U[prec].p; }
 const void* amg_internal_clover(const amg_dirac* d, int prec) { return d->C[prec].p; }
 double amg_internal_kappa(const amg_dirac* d) { return d->kappa; }
+amg_dirac* amg_internal_hierarchy_dirac(amg_hierarchy* h) { return h->d; }
 void amg_internal_set_error(const char* msg) { g_err = msg; }
 
 // ================================================================ C ABI
@@ -1517,6 +1529,7 @@ void amg_params_default(amg_params* p) {
     p->prec_vectors = AMG_F32;
 }
 
+
 amg_status amg_lattice_create(const int dims[4], int antiperiodic_t, amg_lattice** out) {
     if (!dims || !out) return fail(AMG_EINVAL, "NULL argument");
     long long V = 1;
@@ -1534,28 +1547,66 @@ amg_status amg_lattice_create(const int dims[4], int antiperiodic_t, amg_lattice
 }
 void amg_lattice_destroy(amg_lattice* l) { delete l; }
 
-amg_status amg_gauge_create(amg_lattice* lat, const double* U_host, amg_gauge** out) {
-    if (!lat || !U_host || !out) return fail(AMG_EINVAL, "NULL argument");
+// gauge handle from canonical double links already on the device
+static amg_status gauge_from_device(amg_lattice* lat, const double* canon, amg_gauge** out) {
     const GeomH& g = lat->g;
     amg_gauge* G = new amg_gauge();
     G->lat = lat;
-    DevBuf canon;
-    auto cleanup = [&](amg_status st) {
-        delete G;
-        return st;
-    };
-    size_t cb = (size_t)g.V * 4 * 18 * sizeof(double);
-    if (canon.ensure(cb) != cudaSuccess) return cleanup(fail(AMG_ENOMEM, "gauge: device allocation failed"));
-    if (cudaMemcpy(canon.p, U_host, cb, cudaMemcpyHostToDevice) != cudaSuccess)
-        return cleanup(fail(AMG_ECUDA, "gauge: upload failed"));
     for (int pr = 0; pr < 4; ++pr) {
-        if (G->U[pr].ensure(fine_gauge_bytes(pr, g.V)) != cudaSuccess)
-            return cleanup(fail(AMG_ENOMEM, "gauge: device allocation failed"));
-        if (launch_gauge_convert(pr, g, canon.as<double>(), G->U[pr].p, 0) != cudaSuccess)
-            return cleanup(fail(AMG_ECUDA, "gauge: conversion kernel failed"));
+        if (G->U[pr].ensure(fine_gauge_bytes(pr, g.V)) != cudaSuccess) {
+            delete G;
+            return fail(AMG_ENOMEM, "gauge: device allocation failed");
+        }
+        if (launch_gauge_convert(pr, g, canon, G->U[pr].p, 0) != cudaSuccess) {
+            delete G;
+            return fail(AMG_ECUDA, "gauge: conversion kernel failed");
+        }
     }
-    if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(AMG_ECUDA, "gauge: conversion failed"));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        delete G;
+        return fail(AMG_ECUDA, "gauge: conversion failed");
+    }
     *out = G;
+    return AMG_OK;
+}
+
+amg_status amg_gauge_create(amg_lattice* lat, const double* U_host, amg_gauge** out) {
+    if (!lat || !U_host || !out) return fail(AMG_EINVAL, "NULL argument");
+    const GeomH& g = lat->g;
+    DevBuf canon;
+    size_t cb = (size_t)g.V * 4 * 18 * sizeof(double);
+    if (canon.ensure(cb) != cudaSuccess) return fail(AMG_ENOMEM, "gauge: device allocation failed");
+    if (cudaMemcpy(canon.p, U_host, cb, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(AMG_ECUDA, "gauge: upload failed");
+    return gauge_from_device(lat, canon.as<double>(), out);
+}
+
+amg_status amg_gauge_random(amg_lattice* lat, double eps, uint64_t seed, amg_gauge** out) {
+    if (!lat || !out) return fail(AMG_EINVAL, "NULL argument");
+    if (!std::isfinite(eps)) return fail(AMG_EINVAL, "eps must be finite");
+    const GeomH& g = lat->g;
+    DevBuf canon;
+    if (canon.ensure((size_t)g.V * 4 * 18 * sizeof(double)) != cudaSuccess)
+        return fail(AMG_ENOMEM, "gauge: device allocation failed");
+    CK(launch_gauge_random(g, eps, seed, AMG_RNG_STREAM_GAUGE, canon.as<double>(), 0));
+    return gauge_from_device(lat, canon.as<double>(), out);
+}
+
+amg_status amg_gauge_get(amg_gauge* G, double* host_out) {
+    if (!G || !host_out) return fail(AMG_EINVAL, "NULL argument");
+    const GeomH& g = G->lat->g;
+    DevBuf canon;
+    const size_t cb = (size_t)g.V * 4 * 18 * sizeof(double);
+    CK(canon.ensure(cb));
+    CK(launch_gauge_unpack64(g, G->U[0].p, canon.as<double>(), 0));
+    CK(cudaMemcpy(host_out, canon.p, cb, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+}
+
+amg_status amg_random_normal(uint64_t seed, int stream, uint64_t start, uint64_t count, double* out, amg_stream s) {
+    if (!out && count) return fail(AMG_EINVAL, "NULL output");
+    if (stream < 0) return fail(AMG_EINVAL, "stream must be >= 0");
+    CK(launch_random_normal(seed, (uint64_t)stream, start, count, out, (cudaStream_t)s));
     return AMG_OK;
 }
 void amg_gauge_destroy(amg_gauge* g) { delete g; }
@@ -1710,16 +1761,24 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
         }
         TRY(orthonormalise_and_galerkin(h, s));
         if (h->p.nlevels > 2) TRY(setup_coarse_level(h, 1, init_vecs, s));
-        // (0-b): v <- M v with the current hierarchy, then rebuild
+        // (0-b): v <- M v with the current hierarchy, then rebuild.  Every vector of a pass goes
+        // through the same M: when restriction and prolongation read vecs0 itself, the new
+        // vectors are collected apart and replace vecs0 at the end of the pass; with
+        // half-precision transfer vectors (vecs16, rewritten only by the rebuild) they can
+        // overwrite vecs0 in place
+        const bool apart = h->rp != 2;
+        if (apart && h->p.n_adapt > 0) CK(h->vecs_next.ensure(vb * h->p.nvec[0]));
         for (int k = 0; k < h->p.n_adapt; ++k) {
             for (int i = 0; i < h->p.nvec[0]; ++i) {
                 void* vi = (char*)h->vecs0.p + i * vb;
                 TRY(vcycle0(h, vp, vi, h->tmpv.p, 1, s));
-                TRY(normalise_into(h, vp, h->tmpv.p, vi, s));
+                TRY(normalise_into(h, vp, h->tmpv.p, apart ? (char*)h->vecs_next.p + i * vb : vi, s));
             }
+            if (apart) h->vecs0.swap(h->vecs_next);
             TRY(orthonormalise_and_galerkin(h, s));
             TRY(refresh_c(h, 1, s));
         }
+        h->vecs_next.release();
         CK(cudaStreamSynchronize(s));
         return AMG_OK;
     };

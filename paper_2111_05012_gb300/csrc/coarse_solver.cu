@@ -17,6 +17,14 @@
 // memory; the neighbour blocks of the CTA's coarse sites are gathered into
 // shared memory once per pass.
 //
+// Several right-hand sides (up to kMaxNB) are solved in lockstep by one
+// launch: every stencil pass streams each operator word once and applies it
+// to all of them, while the BiCGStab(l) scalars, the stopping test and the
+// vector updates stay per right-hand side, so each one follows exactly the
+// iterates of its own single solve (same rows per CTA, same summation order).
+// A right-hand side that has converged is frozen (no more updates of its
+// vectors or scalars) while the others go on.
+//
 // Grid barriers spin with a bounded count; on timeout the
 // kernel records AMG_TIMEOUT in the status word and every CTA returns.
 #include "common.cuh"
@@ -27,7 +35,8 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxEll = 4;
-constexpr int kMaxQ = (kMaxEll + 1) * (kMaxEll + 1) + 2;   // reduced quantities per barrier
+constexpr int kMaxNB = 4;                                   // right-hand sides per launch
+constexpr int kMaxQ = (kMaxEll + 1) * (kMaxEll + 1) + 2;   // reduced quantities per barrier (>= 2 kMaxNB)
 constexpr long long kSpinLimit = 40000000;                    // ~ seconds of polling
 constexpr int kU = 7;                                         // 16-byte operator words per lane in flight per row
 constexpr int kXBytes = 96 * 1024;                            // shared memory for one group's neighbour blocks
@@ -58,6 +67,7 @@ template <typename TC> DEV void st(void* p, size_t i, cx<TC> v) { ((typename V2<
 struct Args {
     int L[4];
     int Vc, nc, ell, maxit;
+    int nb;          // right-hand sides of this launch; vector r of a field starts r * Vc * nc entries in
     double tol;
     const void* B;
     const void* b;
@@ -232,22 +242,30 @@ template <> struct OpWord<double, 0> {
     }
 };
 
-// y(row) = sum_{d,col} B[row][d][col] x(nbr(X, d))[col] for the rows [r0, r1)
-// of this CTA; returns the per-thread partial <w, y> in dotp (w != nullptr).
-// The CTA's sites are taken in groups of a.xgroup: the nine neighbour blocks
-// of every site of the group are gathered into shared memory (generic loads
-// through L2, since other CTAs wrote the vector), then each warp computes two
-// rows at a time, streaming their operator words straight from global memory
-// into registers (kU coalesced 16-byte loads per lane and row in flight) --
-// the operator is read exactly once and never passes through shared memory.
+// y_r(row) = sum_{d,col} B[row][d][col] x_r(nbr(X, d))[col] for the rows [r0, r1)
+// of this CTA and the a.nb right-hand sides r; returns the per-thread partials
+// <w_r, y_r> in dotp[r] (w != nullptr).  The CTA's sites are taken in groups of
+// a.xgroup: the nine neighbour blocks of every site of the group are gathered
+// into shared memory for every right-hand side (generic loads through L2,
+// since other CTAs wrote the vectors), then each warp computes two rows at a
+// time, streaming their operator words straight from global memory into
+// registers (kU coalesced 16-byte loads per lane and row in flight) and
+// applying each word to all right-hand sides -- the operator is read exactly
+// once per pass and never passes through shared memory.
 // Contains __syncthreads(): called by all threads of the CTA.
-template <typename TC, int BF>
+template <typename TC, int BF, int NB>
 DEV void stencil_rows(const Args& a, cx<TC>* xbuf, int* nbr, const void* xin, void* yout, const void* w, int r0,
-                      int r1, cx<TC>& dotp) {
+                      int r1, cx<TC> (&dotp)[NB]) {
     using W = OpWord<TC, BF>;
+    // operator words in flight per lane and row: each word feeds NB right-hand sides, so fewer
+    // are needed to cover the latency (and the accumulators take the registers)
+    constexpr int KU = NB == 1 ? kU : NB == 2 ? 4 : 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
-    const int nc = a.nc, K = 9 * nc, nw = K / W::per;
+    const int nc = a.nc, K = 9 * nc, nw = K / W::per, nb = a.nb;
+    const size_t n = (size_t)a.Vc * nc;                     // entries per vector
     const int wseg = nc * (int)sizeof(cx<TC>) / 16;   // 16-byte words per neighbour segment
+    const size_t wvec = n * sizeof(cx<TC>) / 16;       // 16-byte words per vector
+    const int xs_r = a.xgroup * K;                     // xbuf entries per right-hand side
     const int Xa = r0 / nc, Xb = r1 > r0 ? (r1 - 1) / nc : Xa - 1;
     for (int Xg = Xa; Xg <= Xb; Xg += a.xgroup) {
         const int gs = min(a.xgroup, Xb - Xg + 1);
@@ -257,9 +275,11 @@ DEV void stencil_rows(const Args& a, cx<TC>* xbuf, int* nbr, const void* xin, vo
         {
             const uint4* xg = (const uint4*)xin;
             uint4* xs = (uint4*)xbuf;
-            for (int p = tid; p < gs * 9 * wseg; p += kThreads) {
-                const int sd = p / wseg, q = p - sd * wseg;
-                xs[p] = __ldcg(xg + (size_t)nbr[sd] * wseg + q);
+            const int per_r = gs * 9 * wseg;
+            for (int p = tid; p < nb * per_r; p += kThreads) {
+                const int r = p / per_r, pp = p - r * per_r;
+                const int sd = pp / wseg, q = pp - sd * wseg;
+                xs[(size_t)r * (xs_r * sizeof(cx<TC>) / 16) + pp] = __ldcg(xg + r * wvec + (size_t)nbr[sd] * wseg + q);
             }
         }
         __syncthreads();
@@ -267,68 +287,185 @@ DEV void stencil_rows(const Args& a, cx<TC>* xbuf, int* nbr, const void* xin, vo
         for (int rA = ra + 2 * warp; rA < rb; rA += 2 * kWarps) {
             const int rB = rA + 1;
             const bool hasB = rB < rb;
-            cx<TC> wA = czero<TC>(), wB = czero<TC>();
-            if (w && lane == 0) {   // loaded now, used after the row sums
-                wA = ld<TC>(w, rA);
-                if (hasB) wB = ld<TC>(w, rB);
+            cx<TC> wA1 = czero<TC>(), wB1 = czero<TC>();
+            if (NB == 1 && w && lane == 0) {   // loaded now, used after the row sums
+                wA1 = ld<TC>(w, rA);
+                if (hasB) wB1 = ld<TC>(w, rB);
             }
             const uint4* opA = (const uint4*)((const unsigned char*)a.B + (size_t)rA * a.row_bytes);
             const uint4* opB = opA + nw;
             const cx<TC>* xA = xbuf + (size_t)(rA / nc - Xg) * K;
             const cx<TC>* xB = xbuf + (size_t)(rB / nc - Xg) * K;
-            cx<TC> accA = czero<TC>(), accB = czero<TC>();
-            for (int k0 = 0; k0 < nw; k0 += 32 * kU) {
-                uint4 va[kU], vb[kU];
+            cx<TC> accA[NB], accB[NB];
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
+            for (int r = 0; r < NB; ++r) accA[r] = accB[r] = czero<TC>();
+            for (int k0 = 0; k0 < nw; k0 += 32 * KU) {
+                uint4 va[KU], vb[KU];
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
                     const int k = k0 + lane + 32 * u;
                     va[u] = k < nw ? __ldg(opA + k) : make_uint4(0u, 0u, 0u, 0u);
                     vb[u] = (hasB && k < nw) ? __ldg(opB + k) : make_uint4(0u, 0u, 0u, 0u);
                 }
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
+                for (int u = 0; u < KU; ++u) {
                     const int k = k0 + lane + 32 * u;
                     if (k < nw) {
-                        W::mac(va[u], xA + (size_t)k * W::per, accA);
-                        if (hasB) W::mac(vb[u], xB + (size_t)k * W::per, accB);
+#pragma unroll
+                        for (int r = 0; r < NB; ++r) {
+                            if (r < nb) {
+                                W::mac(va[u], xA + (size_t)r * xs_r + (size_t)k * W::per, accA[r]);
+                                if (hasB) W::mac(vb[u], xB + (size_t)r * xs_r + (size_t)k * W::per, accB[r]);
+                            }
+                        }
                     }
                 }
             }
-            accA.re = warp_sum(accA.re);
-            accA.im = warp_sum(accA.im);
-            accB.re = warp_sum(accB.re);
-            accB.im = warp_sum(accB.im);
-            if (lane == 0) {
-                st<TC>(yout, rA, accA);
-                if (hasB) st<TC>(yout, rB, accB);
-                if (w) dotp = dotp + cmulc(wA, accA) + cmulc(wB, accB);
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                if (r >= nb) break;
+                accA[r].re = warp_sum(accA[r].re);
+                accA[r].im = warp_sum(accA[r].im);
+                accB[r].re = warp_sum(accB[r].re);
+                accB[r].im = warp_sum(accB[r].im);
+                if (lane == 0) {
+                    st<TC>(yout, r * n + rA, accA[r]);
+                    if (hasB) st<TC>(yout, r * n + rB, accB[r]);
+                    if (w) {
+                        const cx<TC> wa = NB == 1 ? wA1 : ld<TC>(w, r * n + rA);
+                        const cx<TC> wb = NB == 1 ? wB1 : (hasB ? ld<TC>(w, r * n + rB) : czero<TC>());
+                        dotp[r] = dotp[r] + cmulc(wa, accA[r]) + cmulc(wb, accB[r]);
+                    }
+                }
             }
         }
     }
 }
 
-template <typename TC, int BF>
+// Scalar algebra of the minimal-residual part for one right-hand side from its
+// Gram matrix G_pq = <R_p, R_q> (res, packed upper triangle p <= q): Gram-Schmidt
+// of R_1..R_ell expressed in the original basis, Rt_j = sum_k C[j][k] R_k
+// (k = 1..j), tau_ij = <Rt_i, Rt_j>/sigma_i; writes the update coefficients of
+// x, R_0 and U_0.  Runs in one thread, in the solver's precision ST.  Returns
+// false on a breakdown (sigma_j <= 0).
+template <typename ST>
+DEV bool mr_coefficients(const cx<double>* res, int ell, cx<double>* out_x, cx<double>* out_r, cx<double>* out_g) {
+    cx<ST> C[kMaxEll + 1][kMaxEll + 1];
+    ST sigma[kMaxEll + 1];
+    cx<ST> gp[kMaxEll + 1], g[kMaxEll + 1], gpp[kMaxEll + 1], tau[kMaxEll + 1][kMaxEll + 1];
+    auto G = [&](int p, int q) -> cx<ST> {   // <R_p, R_q>
+        return ccast<ST>(p <= q ? res[p * (ell + 1) + q] : conj(res[q * (ell + 1) + p]));
+    };
+    // loops run to the compile-time bound kMaxEll with guards, in the same order as
+    // the algorithm's loops to ell, so that every array lives in registers
+#pragma unroll
+    for (int j = 0; j <= kMaxEll; ++j)
+#pragma unroll
+        for (int k = 0; k <= kMaxEll; ++k) C[j][k] = czero<ST>();
+    bool ok = true;
+#pragma unroll
+    for (int j = 1; j <= kMaxEll; ++j) {
+        if (j > ell) break;
+        C[j][j] = {1, 0};
+#pragma unroll
+        for (int i = 1; i < j; ++i) {
+            cx<ST> t = czero<ST>();
+#pragma unroll
+            for (int p = 1; p <= i; ++p)
+#pragma unroll
+                for (int q = 1; q <= j; ++q) t = t + conj(C[i][p]) * C[j][q] * G(p, q);
+            tau[i][j] = (ST(1) / sigma[i]) * t;
+#pragma unroll
+            for (int k = 1; k <= i; ++k) C[j][k] = C[j][k] - tau[i][j] * C[i][k];
+        }
+        ST sg = 0;
+        cx<ST> t0 = czero<ST>();
+#pragma unroll
+        for (int p = 1; p <= j; ++p) {
+#pragma unroll
+            for (int q = 1; q <= j; ++q) sg += (conj(C[j][p]) * C[j][q] * G(p, q)).re;
+            t0 = t0 + conj(C[j][p]) * G(p, 0);
+        }
+        sigma[j] = sg;
+        if (!(sg > 0)) ok = false;
+        gp[j] = (ST(1) / (sg > 0 ? sg : ST(1))) * t0;
+    }
+#pragma unroll
+    for (int j = 0; j <= kMaxEll; ++j) g[j] = gpp[j] = czero<ST>();
+#pragma unroll
+    for (int j = 1; j <= kMaxEll; ++j)
+        if (j == ell) g[j] = gp[j];
+#pragma unroll
+    for (int j = kMaxEll - 1; j >= 1; --j) {
+        if (j >= ell) continue;
+        cx<ST> t = gp[j];
+#pragma unroll
+        for (int i = j + 1; i <= kMaxEll; ++i)
+            if (i <= ell) t = t - tau[j][i] * g[i];
+        g[j] = t;
+    }
+#pragma unroll
+    for (int j = 1; j < kMaxEll; ++j) {
+        if (j >= ell) break;
+        cx<ST> t = g[j + 1];
+#pragma unroll
+        for (int i = j + 1; i < kMaxEll; ++i)
+            if (i < ell) t = t + tau[j][i] * g[i + 1];
+        gpp[j] = t;
+    }
+    // x += g1 R0 + sum_{j<ell} gpp_j Rt_j ; R0 -= sum_j gp_j Rt_j ; U0 -= sum_j g_j U_j
+    cx<ST> tx[kMaxEll + 1], tr[kMaxEll + 1];
+#pragma unroll
+    for (int k = 0; k <= kMaxEll; ++k) tx[k] = tr[k] = czero<ST>();
+    tx[0] = g[1];
+#pragma unroll
+    for (int j = 1; j < kMaxEll; ++j)
+#pragma unroll
+        for (int k = 1; k <= j; ++k)
+            if (j < ell) tx[k] = tx[k] + gpp[j] * C[j][k];
+#pragma unroll
+    for (int j = 1; j <= kMaxEll; ++j)
+#pragma unroll
+        for (int k = 1; k <= j; ++k)
+            if (j <= ell) tr[k] = tr[k] + gp[j] * C[j][k];
+#pragma unroll
+    for (int k = 0; k <= kMaxEll; ++k) {
+        if (k > ell) break;
+        out_x[k] = ccast<double>(tx[k]);
+        out_r[k] = ccast<double>(tr[k]);
+        out_g[k] = ccast<double>(g[k]);
+    }
+    return ok;
+}
+
+template <typename TC, int BF, int NB>
 __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
+    using SC = TC;   // BiCG scalars in the solver's precision
     __shared__ cx<double> red_sh[kMaxQ * kWarps];
     __shared__ cx<double> res[kMaxQ];
+    // per right-hand side scalars, owned by thread 0 (kept as doubles: exact for SC = float too)
+    __shared__ cx<double> s_rho0[NB], s_rho1[NB], s_alpha[NB], s_omega[NB], s_beta[NB];
+    __shared__ double s_bn2[NB];
+    __shared__ int s_act[NB], s_any, s_bad;
+    __shared__ cx<double> s_cx[NB][kMaxEll + 1], s_cr[NB][kMaxEll + 1], s_g[NB][kMaxEll + 1];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    cx<TC>* xbuf = (cx<TC>*)dyn_smem;                                    // xgroup x 9 neighbour blocks
-    int* nbr = (int*)(dyn_smem + (size_t)a.xgroup * 9 * a.nc * sizeof(cx<TC>));   // their sites
-    const int ell = a.ell;
-    const int n = a.Vc * a.nc;
+    cx<TC>* xbuf = (cx<TC>*)dyn_smem;   // [NB][xgroup x 9 neighbour blocks]
+    int* nbr = (int*)(dyn_smem + (size_t)NB * a.xgroup * 9 * a.nc * sizeof(cx<TC>));   // their sites
+    const int ell = a.ell, nb = a.nb;
+    const size_t n = (size_t)a.Vc * a.nc;
     int r0, r1;
-    my_rows(n, r0, r1);
+    my_rows((int)n, r0, r1);
     const int tid = threadIdx.x;
     // initial state: x = 0, R0 = b, rt = b, U0 = 0
-    for (int i = r0 + tid; i < r1; i += kThreads) {
-        cx<TC> bi = ld<TC>(a.b, i);
-        st<TC>(a.x, i, czero<TC>());
-        st<TC>(a.R[0], i, bi);
-        st<TC>(a.rt, i, bi);
-        st<TC>(a.U[0], i, czero<TC>());
-    }
-    // BiCG scalars in the solver's precision: identical in every thread
-    using SC = TC;
+    for (int r = 0; r < nb; ++r)
+        for (int i = r0 + tid; i < r1; i += kThreads) {
+            const size_t k = r * n + i;
+            cx<TC> bi = ld<TC>(a.b, k);
+            st<TC>(a.x, k, czero<TC>());
+            st<TC>(a.R[0], k, bi);
+            st<TC>(a.rt, k, bi);
+            st<TC>(a.U[0], k, czero<TC>());
+        }
     // n / d with both scaled by max(|d.re|, |d.im|) first: the BiCG scalars are
     // squares of the residual scale, so |d|^2 would underflow (FP32) for the
     // small right-hand sides a non-normalising outer solver hands down
@@ -339,168 +476,47 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
         const SC inv = SC(1) / norm2(ds);
         return {(ns.re * ds.re + ns.im * ds.im) * inv, (ns.im * ds.re - ns.re * ds.im) * inv};
     };
-    cx<SC> rho0 = {SC(1), SC(0)}, alpha = {SC(0), SC(0)}, omega = {SC(1), SC(0)};
-    double bn2 = -1;
+    if (tid < NB) {
+        s_rho0[tid] = s_rho1[tid] = s_omega[tid] = {1.0, 0.0};
+        s_alpha[tid] = s_beta[tid] = {0.0, 0.0};
+        s_bn2[tid] = -1;
+        s_act[tid] = tid < nb;
+    }
+    __syncthreads();
     int cycle = 0;
     for (;; ++cycle) {
-        // |R0|^2 and rho1 = <rt, R0> in one reduction
+        // |R0|^2 and rho1 = <rt, R0> of every right-hand side in one reduction
         {
-            cx<TC> v[2] = {czero<TC>(), czero<TC>()};
-            for (int i = r0 + tid; i < r1; i += kThreads) {
-                cx<TC> ri = ld<TC>(a.R[0], i);
-                v[0].re += norm2(ri);
-                v[1] = v[1] + cmulc(ld<TC>(a.rt, i), ri);
-            }
-            if (!grid_reduce<2, TC>(a, v, 2, red_sh, res)) return;
-        }
-        const double rn2 = res[0].re;
-        if (bn2 < 0) bn2 = rn2;
-        if (!(rn2 == rn2)) {   // NaN
-            if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
-            return;
-        }
-        if (rn2 <= a.tol * a.tol * bn2 || cycle >= a.maxit) break;
-        cx<SC> rho1 = ccast<SC>(res[1]);
-        rho0 = SC(-1) * omega * rho0;
-        for (int j = 0; j < ell; ++j) {
-            const cx<SC> beta = cdiv(alpha * rho1, rho0);
-            rho0 = rho1;
-            for (int i = r0 + tid; i < r1; i += kThreads)
-                for (int q = 0; q <= j; ++q) {
-                    cx<TC> u = ld<TC>(a.U[q], i);
-                    st<TC>(a.U[q], i, ld<TC>(a.R[q], i) - ccast<TC>(beta) * u);
-                }
-            if (!grid_sync(a.bar)) return;
-            // U_{j+1} = A U_j and gamma = <rt, U_{j+1}>
-            {
-                cx<TC> v[1] = {czero<TC>()};
-                stencil_rows<TC, BF>(a, xbuf, nbr, a.U[j], a.U[j + 1], a.rt, r0, r1, v[0]);
-                if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
-            }
-            alpha = cdiv(rho0, ccast<SC>(res[0]));
-            for (int i = r0 + tid; i < r1; i += kThreads) {
-                for (int q = 0; q <= j; ++q)
-                    st<TC>(a.R[q], i, ld<TC>(a.R[q], i) - ccast<TC>(alpha) * ld<TC>(a.U[q + 1], i));
-                st<TC>(a.x, i, ld<TC>(a.x, i) + ccast<TC>(alpha) * ld<TC>(a.U[0], i));
-            }
-            if (!grid_sync(a.bar)) return;
-            // R_{j+1} = A R_j; the next BiCG step needs rho1 = <rt, R_{j+1}>
-            {
-                cx<TC> v[1] = {czero<TC>()};
-                stencil_rows<TC, BF>(a, xbuf, nbr, a.R[j], a.R[j + 1], a.rt, r0, r1, v[0]);
-                if (j + 1 < ell) {
-                    if (!grid_reduce<1, TC>(a, v, 1, red_sh, res)) return;
-                    rho1 = ccast<SC>(res[0]);
+            cx<TC> v[2 * NB];
+#pragma unroll
+            for (int q = 0; q < 2 * NB; ++q) v[q] = czero<TC>();
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                if (r >= nb) break;
+                for (int i = r0 + tid; i < r1; i += kThreads) {
+                    cx<TC> ri = ld<TC>(a.R[0], r * n + i);
+                    v[2 * r].re += norm2(ri);
+                    v[2 * r + 1] = v[2 * r + 1] + cmulc(ld<TC>(a.rt, r * n + i), ri);
                 }
             }
+            if (!grid_reduce<2 * NB, TC>(a, v, 2 * nb, red_sh, res)) return;
         }
-        // minimal-residual part from the Gram matrix G_pq = <R_p, R_q>, p, q = 0..ell
-        {
-            cx<TC> v[kMaxQ];
-            int nq = (ell + 1) * (ell + 1);
-            for (int q = 0; q < nq; ++q) v[q] = czero<TC>();
-            for (int i = r0 + tid; i < r1; i += kThreads) {
-                cx<TC> rv[kMaxEll + 1];
-                for (int p = 0; p <= ell; ++p) rv[p] = ld<TC>(a.R[p], i);
-                for (int p = 0; p <= ell; ++p)
-                    for (int q = p; q <= ell; ++q) v[p * (ell + 1) + q] = v[p * (ell + 1) + q] + cmulc(rv[p], rv[q]);
-            }
-            if (!grid_reduce<kMaxQ, TC>(a, v, nq, red_sh, res)) return;
-        }
-        // Gram-Schmidt of R_1..R_ell expressed in the original basis:
-        // Rt_j = sum_k C[j][k] R_k (k = 1..j), tau_ij = <Rt_i, Rt_j>/sigma_i.
-        // One thread evaluates the scalar algebra; the update coefficients are
-        // broadcast through shared memory.
-        __shared__ cx<double> s_cx[kMaxEll + 1], s_cr[kMaxEll + 1], s_g[kMaxEll + 1];
-        __shared__ int s_bad;
-        // scalars in the solver's precision (FP32 for the FP32 coarse solve)
-        using ST = TC;
         if (tid == 0) {
-            cx<ST> C[kMaxEll + 1][kMaxEll + 1];
-            ST sigma[kMaxEll + 1];
-            cx<ST> gp[kMaxEll + 1], g[kMaxEll + 1], gpp[kMaxEll + 1], tau[kMaxEll + 1][kMaxEll + 1];
-            auto G = [&](int p, int q) -> cx<ST> {   // <R_p, R_q>
-                return ccast<ST>(p <= q ? res[p * (ell + 1) + q] : conj(res[q * (ell + 1) + p]));
-            };
-            // loops run to the compile-time bound kMaxEll with guards, in the same order as
-            // the algorithm's loops to ell, so that every array lives in registers
-#pragma unroll
-            for (int j = 0; j <= kMaxEll; ++j)
-#pragma unroll
-                for (int k = 0; k <= kMaxEll; ++k) C[j][k] = czero<ST>();
-            int bad = 0;
-#pragma unroll
-            for (int j = 1; j <= kMaxEll; ++j) {
-                if (j > ell) break;
-                C[j][j] = {1, 0};
-#pragma unroll
-                for (int i = 1; i < j; ++i) {
-                    cx<ST> t = czero<ST>();
-#pragma unroll
-                    for (int p = 1; p <= i; ++p)
-#pragma unroll
-                        for (int q = 1; q <= j; ++q) t = t + conj(C[i][p]) * C[j][q] * G(p, q);
-                    tau[i][j] = (ST(1) / sigma[i]) * t;
-#pragma unroll
-                    for (int k = 1; k <= i; ++k) C[j][k] = C[j][k] - tau[i][j] * C[i][k];
+            int any = 0, bad = 0;
+            for (int r = 0; r < nb; ++r) {
+                if (!s_act[r]) continue;
+                const double rn2 = res[2 * r].re;
+                if (s_bn2[r] < 0) s_bn2[r] = rn2;
+                if (!(rn2 == rn2)) bad = 1;   // NaN
+                if (rn2 <= a.tol * a.tol * s_bn2[r] || cycle >= a.maxit) {
+                    s_act[r] = 0;   // converged (or out of cycles): frozen from here on
+                    continue;
                 }
-                ST sg = 0;
-                cx<ST> t0 = czero<ST>();
-#pragma unroll
-                for (int p = 1; p <= j; ++p) {
-#pragma unroll
-                    for (int q = 1; q <= j; ++q) sg += (conj(C[j][p]) * C[j][q] * G(p, q)).re;
-                    t0 = t0 + conj(C[j][p]) * G(p, 0);
-                }
-                sigma[j] = sg;
-                if (!(sg > 0)) bad = 1;
-                gp[j] = (ST(1) / (sg > 0 ? sg : ST(1))) * t0;
+                any = 1;
+                s_rho1[r] = ccast<double>(ccast<SC>(res[2 * r + 1]));
+                s_rho0[r] = ccast<double>(SC(-1) * ccast<SC>(s_omega[r]) * ccast<SC>(s_rho0[r]));
             }
-#pragma unroll
-            for (int j = 0; j <= kMaxEll; ++j) g[j] = gpp[j] = czero<ST>();
-#pragma unroll
-            for (int j = 1; j <= kMaxEll; ++j)
-                if (j == ell) g[j] = gp[j];
-#pragma unroll
-            for (int j = kMaxEll - 1; j >= 1; --j) {
-                if (j >= ell) continue;
-                cx<ST> t = gp[j];
-#pragma unroll
-                for (int i = j + 1; i <= kMaxEll; ++i)
-                    if (i <= ell) t = t - tau[j][i] * g[i];
-                g[j] = t;
-            }
-#pragma unroll
-            for (int j = 1; j < kMaxEll; ++j) {
-                if (j >= ell) break;
-                cx<ST> t = g[j + 1];
-#pragma unroll
-                for (int i = j + 1; i < kMaxEll; ++i)
-                    if (i < ell) t = t + tau[j][i] * g[i + 1];
-                gpp[j] = t;
-            }
-            // x += g1 R0 + sum_{j<ell} gpp_j Rt_j ; R0 -= sum_j gp_j Rt_j ; U0 -= sum_j g_j U_j
-            cx<ST> tx[kMaxEll + 1], tr[kMaxEll + 1];
-#pragma unroll
-            for (int k = 0; k <= kMaxEll; ++k) tx[k] = tr[k] = czero<ST>();
-            tx[0] = g[1];
-#pragma unroll
-            for (int j = 1; j < kMaxEll; ++j)
-#pragma unroll
-                for (int k = 1; k <= j; ++k)
-                    if (j < ell) tx[k] = tx[k] + gpp[j] * C[j][k];
-#pragma unroll
-            for (int j = 1; j <= kMaxEll; ++j)
-#pragma unroll
-                for (int k = 1; k <= j; ++k)
-                    if (j <= ell) tr[k] = tr[k] + gp[j] * C[j][k];
-#pragma unroll
-            for (int k = 0; k <= kMaxEll; ++k) {
-                if (k > ell) break;
-                s_cx[k] = ccast<double>(tx[k]);
-                s_cr[k] = ccast<double>(tr[k]);
-                s_g[k] = ccast<double>(g[k]);
-            }
+            s_any = any;
             s_bad = bad;
         }
         __syncthreads();
@@ -508,28 +524,106 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
             return;
         }
-        omega = ccast<SC>(s_g[ell]);
-        cx<SC> cx_[kMaxEll + 1], cr[kMaxEll + 1], g[kMaxEll + 1];
-#pragma unroll
-        for (int k = 0; k <= kMaxEll; ++k) {
-            cx_[k] = k <= ell ? ccast<SC>(s_cx[k]) : czero<SC>();
-            cr[k] = k <= ell ? ccast<SC>(s_cr[k]) : czero<SC>();
-            g[k] = k <= ell ? ccast<SC>(s_g[k]) : czero<SC>();
-        }
-        for (int i = r0 + tid; i < r1; i += kThreads) {
-            cx<TC> xv = ld<TC>(a.x, i), r0v = ld<TC>(a.R[0], i), u0 = ld<TC>(a.U[0], i);
-            xv = xv + ccast<TC>(cx_[0]) * r0v;
-#pragma unroll
-            for (int k = 1; k <= kMaxEll; ++k) {
-                if (k > ell) break;
-                cx<TC> rk = ld<TC>(a.R[k], i);
-                xv = xv + ccast<TC>(cx_[k]) * rk;
-                r0v = r0v - ccast<TC>(cr[k]) * rk;
-                u0 = u0 - ccast<TC>(g[k]) * ld<TC>(a.U[k], i);
+        if (!s_any) break;
+        for (int j = 0; j < ell; ++j) {
+            if (tid == 0)
+                for (int r = 0; r < nb; ++r) {
+                    if (!s_act[r]) continue;
+                    s_beta[r] = ccast<double>(
+                        cdiv(ccast<SC>(s_alpha[r]) * ccast<SC>(s_rho1[r]), ccast<SC>(s_rho0[r])));
+                    s_rho0[r] = s_rho1[r];
+                }
+            __syncthreads();
+            for (int r = 0; r < nb; ++r) {
+                if (!s_act[r]) continue;
+                const cx<TC> beta = ccast<TC>(s_beta[r]);
+                for (int i = r0 + tid; i < r1; i += kThreads)
+                    for (int q = 0; q <= j; ++q) {
+                        cx<TC> u = ld<TC>(a.U[q], r * n + i);
+                        st<TC>(a.U[q], r * n + i, ld<TC>(a.R[q], r * n + i) - beta * u);
+                    }
             }
-            st<TC>(a.x, i, xv);
-            st<TC>(a.R[0], i, r0v);
-            st<TC>(a.U[0], i, u0);
+            if (!grid_sync(a.bar)) return;
+            // U_{j+1} = A U_j and gamma = <rt, U_{j+1}>
+            {
+                cx<TC> d[NB];
+#pragma unroll
+                for (int r = 0; r < NB; ++r) d[r] = czero<TC>();
+                stencil_rows<TC, BF, NB>(a, xbuf, nbr, a.U[j], a.U[j + 1], a.rt, r0, r1, d);
+                if (!grid_reduce<NB, TC>(a, d, nb, red_sh, res)) return;
+            }
+            if (tid == 0)
+                for (int r = 0; r < nb; ++r)
+                    if (s_act[r]) s_alpha[r] = ccast<double>(cdiv(ccast<SC>(s_rho0[r]), ccast<SC>(res[r])));
+            __syncthreads();
+            for (int r = 0; r < nb; ++r) {
+                if (!s_act[r]) continue;
+                const cx<TC> alpha = ccast<TC>(s_alpha[r]);
+                for (int i = r0 + tid; i < r1; i += kThreads) {
+                    const size_t k = r * n + i;
+                    for (int q = 0; q <= j; ++q)
+                        st<TC>(a.R[q], k, ld<TC>(a.R[q], k) - alpha * ld<TC>(a.U[q + 1], k));
+                    st<TC>(a.x, k, ld<TC>(a.x, k) + alpha * ld<TC>(a.U[0], k));
+                }
+            }
+            if (!grid_sync(a.bar)) return;
+            // R_{j+1} = A R_j; the next BiCG step needs rho1 = <rt, R_{j+1}>
+            {
+                cx<TC> d[NB];
+#pragma unroll
+                for (int r = 0; r < NB; ++r) d[r] = czero<TC>();
+                stencil_rows<TC, BF, NB>(a, xbuf, nbr, a.R[j], a.R[j + 1], a.rt, r0, r1, d);
+                if (j + 1 < ell) {
+                    if (!grid_reduce<NB, TC>(a, d, nb, red_sh, res)) return;
+                    if (tid == 0)
+                        for (int r = 0; r < nb; ++r)
+                            if (s_act[r]) s_rho1[r] = ccast<double>(ccast<SC>(res[r]));
+                }
+            }
+        }
+        // minimal-residual part from the Gram matrix G_pq = <R_p, R_q>, p, q = 0..ell, of
+        // each active right-hand side (one reduction each); thread 0 evaluates the scalar
+        // algebra and broadcasts the update coefficients through shared memory
+        for (int r = 0; r < nb; ++r) {
+            if (!s_act[r]) continue;
+            cx<TC> v[kMaxQ];
+            const int nq = (ell + 1) * (ell + 1);
+            for (int q = 0; q < nq; ++q) v[q] = czero<TC>();
+            for (int i = r0 + tid; i < r1; i += kThreads) {
+                cx<TC> rv[kMaxEll + 1];
+                for (int p = 0; p <= ell; ++p) rv[p] = ld<TC>(a.R[p], r * n + i);
+                for (int p = 0; p <= ell; ++p)
+                    for (int q = p; q <= ell; ++q) v[p * (ell + 1) + q] = v[p * (ell + 1) + q] + cmulc(rv[p], rv[q]);
+            }
+            if (!grid_reduce<kMaxQ, TC>(a, v, nq, red_sh, res)) return;
+            if (tid == 0) {
+                s_bad = mr_coefficients<SC>(res, ell, s_cx[r], s_cr[r], s_g[r]) ? 0 : 1;
+                s_omega[r] = s_g[r][ell];
+            }
+            __syncthreads();
+            if (s_bad) {
+                if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
+                return;
+            }
+        }
+        for (int r = 0; r < nb; ++r) {
+            if (!s_act[r]) continue;
+            for (int i = r0 + tid; i < r1; i += kThreads) {
+                const size_t kk = r * n + i;
+                cx<TC> xv = ld<TC>(a.x, kk), r0v = ld<TC>(a.R[0], kk), u0 = ld<TC>(a.U[0], kk);
+                xv = xv + ccast<TC>(s_cx[r][0]) * r0v;
+#pragma unroll
+                for (int k = 1; k <= kMaxEll; ++k) {
+                    if (k > ell) break;
+                    cx<TC> rk = ld<TC>(a.R[k], kk);
+                    xv = xv + ccast<TC>(s_cx[r][k]) * rk;
+                    r0v = r0v - ccast<TC>(s_cr[r][k]) * rk;
+                    u0 = u0 - ccast<TC>(s_g[r][k]) * ld<TC>(a.U[k], kk);
+                }
+                st<TC>(a.x, kk, xv);
+                st<TC>(a.R[0], kk, r0v);
+                st<TC>(a.U[0], kk, u0);
+            }
         }
     }
     if (blockIdx.x == 0 && tid == 0) a.bar->cycles += cycle;
@@ -545,7 +639,16 @@ int coop_grid(const void* fn, int smem) {
     return sms;
 }
 
+template <int NB> const void* solver_fn(int cprec) {
+    return cprec == 0   ? (const void*)coarse_bicgstab_kernel<double, 0, NB>
+           : cprec == 3 ? (const void*)coarse_bicgstab_kernel<double, 2, NB>
+           : cprec == 1 ? (const void*)coarse_bicgstab_kernel<float, 0, NB>
+                        : (const void*)coarse_bicgstab_kernel<float, 1, NB>;
+}
+
 }  // namespace
+
+int coarse_solver_max_rhs() { return kMaxNB; }
 
 size_t coarse_solver_state_bytes() { return sizeof(GridBar) + 64; }
 size_t coarse_solver_partial_bytes() {
@@ -555,11 +658,15 @@ size_t coarse_solver_partial_bytes() {
     return sizeof(double2) * (size_t)kMaxQ * sms;
 }
 
+
 cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
                                    void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
-                                   void* part, void* state, int cluster, cudaStream_t s) {
+                                   void* part, void* state, int cluster, cudaStream_t s, int nb) {
     if (ell < 1 || ell > kMaxEll) return cudaErrorInvalidValue;
+    if (nb < 1 || nb > kMaxNB) return cudaErrorInvalidValue;
+    const int NB = nb == 1 ? 1 : nb == 2 ? 2 : 4;   // compiled batch widths
     Args a;
+    a.nb = nb;
     for (int i = 0; i < 4; ++i) a.L[i] = gc.L[i];
     a.Vc = gc.V;
     a.nc = nc;
@@ -584,13 +691,10 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     a.row_bytes = 9 * nc * (cprec == 2 ? 4 : cprec == 3 ? 8 : eb);             // operator entry
     if (a.row_bytes % 16 != 0) return cudaErrorInvalidValue;   // rows are read in 16-byte words
     const int block_bytes = 9 * nc * eb;                                  // one site's neighbour blocks
-    a.xgroup = kXBytes / block_bytes;
+    a.xgroup = kXBytes / (block_bytes * NB);
     if (a.xgroup < 1) return cudaErrorInvalidValue;
-    const void* fn = cprec == 0   ? (const void*)coarse_bicgstab_kernel<double, 0>
-                     : cprec == 3 ? (const void*)coarse_bicgstab_kernel<double, 2>
-                     : cprec == 1 ? (const void*)coarse_bicgstab_kernel<float, 0>
-                                  : (const void*)coarse_bicgstab_kernel<float, 1>;
-    const int smem = a.xgroup * (block_bytes + 9 * (int)sizeof(int));
+    const void* fn = NB == 1 ? solver_fn<1>(cprec) : NB == 2 ? solver_fn<2>(cprec) : solver_fn<4>(cprec);
+    const int smem = a.xgroup * (NB * block_bytes + 9 * (int)sizeof(int));
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

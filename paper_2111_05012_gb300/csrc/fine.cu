@@ -594,15 +594,19 @@ template <> struct DomainVec<double> {
 template <class P, int MAXT>
 __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode,
                                                         const void* __restrict__ U, const void* __restrict__ C,
-                                                        const void* __restrict__ b, void* x, typename P::T kappa) {
+                                                        const void* __restrict__ b, void* x, typename P::T kappa,
+                                                        int rhs_fast) {
     using T = typename P::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int vbp = blockDim.x;
     cx<T>* rsh = reinterpret_cast<cx<T>*>(smem_raw);          // [12][vbp]
     T* red = reinterpret_cast<T*>(rsh + 12 * vbp);             // [3][32]
 
-    // domain of this CTA: the k-th domain of the given colour
-    const int k = blockIdx.x;
+    // domain of this CTA: the k-th domain of the given colour; right-hand side r of a batch.
+    // rhs_fast: r is the fast grid index, so the CTAs of one domain for all right-hand sides
+    // run together and share the domain's links and clover in L1/L2
+    const int k = rhs_fast ? blockIdx.y : blockIdx.x;
+    const int rr = rhs_fast ? blockIdx.x : blockIdx.y;
     const int h0 = bk.C[0] / 2;
     int rest = k / h0;
     int X1 = rest % bk.C[1];
@@ -617,9 +621,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
     int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
     const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
     cx<T> r[12], z[12], Ar[12];
-    // right-hand side blockIdx.y of a batch
-    b = (const char*)b + blockIdx.y * spinor_bytes<P>(g.V);
-    x = (char*)x + blockIdx.y * spinor_bytes<P>(g.V);
+    b = (const char*)b + rr * spinor_bytes<P>(g.V);
+    x = (char*)x + rr * spinor_bytes<P>(g.V);
     if (active) {
         s = block_site(g, bk, Xi, l, c);
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
@@ -776,7 +779,8 @@ template <> struct Staged<P16> {
 template <class P>
 __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
     sap_half_staged_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode, const void* __restrict__ U,
-                           const void* __restrict__ C, const void* __restrict__ b, void* x, float kappa) {
+                           const void* __restrict__ C, const void* __restrict__ b, void* x, float kappa,
+                           int rhs_fast) {
     using S = Staged<P>;
     using LC = typename S::LC;
     using CC = typename S::CC;
@@ -787,7 +791,8 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
     cx<float>* rsh = reinterpret_cast<cx<float>*>(sc + (size_t)S::kCloverChunks * vbp);   // [12][vbp]
     float* red = reinterpret_cast<float*>(rsh + 12 * vbp);                      // [2][3][32]
 
-    const int k = blockIdx.x;
+    const int k = rhs_fast ? blockIdx.y : blockIdx.x;
+    const int rr = rhs_fast ? blockIdx.x : blockIdx.y;
     const int h0 = bk.C[0] / 2;
     int rest = k / h0;
     int X1 = rest % bk.C[1];
@@ -802,9 +807,8 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
     int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
     const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
     cx<float> r[12], z[12], Ar[12];
-    // right-hand side blockIdx.y of a batch
-    b = (const char*)b + blockIdx.y * spinor_bytes<P>(g.V);
-    x = (char*)x + blockIdx.y * spinor_bytes<P>(g.V);
+    b = (const char*)b + rr * spinor_bytes<P>(g.V);
+    x = (char*)x + rr * spinor_bytes<P>(g.V);
     if (active) {
         s = block_site(g, bk, Xi, l, c);
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
@@ -941,8 +945,11 @@ cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, 
     cudaError_t e =
         cudaFuncSetAttribute(sap_half_staged_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    (note_launch(), sap_half_staged_kernel<P><<<dim3(bk.Vc / 2, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                          (float)kappa));
+    const int ndom = bk.Vc / 2;
+    const int fast = nrhs > 1 && ndom <= 65535;
+    const dim3 grid = fast ? dim3(nrhs, ndom) : dim3(ndom, nrhs);
+    (note_launch(), sap_half_staged_kernel<P><<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                          (float)kappa, fast));
     return cudaGetLastError();
 }
 
@@ -955,18 +962,21 @@ cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr
     if (threads > 512) return cudaErrorInvalidValue;
     size_t smem = (size_t)12 * threads * sizeof(cx<typename P::T>) + 3 * 32 * sizeof(typename P::T);
     int ndom = bk.Vc / 2;
+    // right-hand side as the fast grid index when the domains fit the y dimension
+    const int fast = nrhs > 1 && ndom <= 65535;
+    const dim3 grid = fast ? dim3(nrhs, ndom) : dim3(ndom, nrhs);
     if (threads <= 256) {
         cudaError_t e =
             cudaFuncSetAttribute(sap_half_kernel<P, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        (note_launch(), sap_half_kernel<P, 256><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                         (typename P::T)kappa));
+        (note_launch(), sap_half_kernel<P, 256><<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                         (typename P::T)kappa, fast));
     } else {
         cudaError_t e =
             cudaFuncSetAttribute(sap_half_kernel<P, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        (note_launch(), sap_half_kernel<P, 512><<<dim3(ndom, nrhs), threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                         (typename P::T)kappa));
+        (note_launch(), sap_half_kernel<P, 512><<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
+                                                                         (typename P::T)kappa, fast));
     }
     return cudaGetLastError();
 }

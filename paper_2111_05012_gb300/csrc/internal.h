@@ -31,6 +31,19 @@ struct DevBuf {
         return e;
     }
     template <typename T> T* as() const { return (T*)p; }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void swap(DevBuf& o) noexcept {
+        void* tp = p;
+        p = o.p;
+        o.p = tp;
+        size_t tn = n;
+        n = o.n;
+        o.n = tn;
+    }
 };
 
 #define AMG_NN_MAX_LAYERS 4
@@ -58,6 +71,7 @@ struct amg_nn {
 
 // accessors implemented in api.cu
 const GeomH* amg_internal_geom(const amg_dirac* d);
+amg_dirac* amg_internal_hierarchy_dirac(amg_hierarchy* h);
 const void* amg_internal_links(const amg_dirac* d, int prec);
 void amg_internal_set_error(const char* msg);
 

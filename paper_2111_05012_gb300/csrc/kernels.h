@@ -31,6 +31,16 @@ cudaError_t launch_convert_spinor(int prec_in, int prec_out, const GeomH& g, con
                                   cudaStream_t s);
 // canonical double gauge [site][mu][3][3][2] (device) -> internal of prec
 cudaError_t launch_gauge_convert(int prec, const GeomH& g, const double* canon, void* internal, cudaStream_t s);
+// ---- seeded inputs (inputs.cu): counter-based SplitMix64, Box-Muller, exp(i eps H) links ----
+uint64_t rng_stream_key(uint64_t seed, uint64_t stream);
+// complex normals start .. start+count-1 of the (seed, stream) generator, (re, im) doubles
+cudaError_t launch_random_normal(uint64_t seed, uint64_t stream, uint64_t start, uint64_t count, double* out,
+                                 cudaStream_t s);
+// canonical double links [site][mu][3][3][2] = exp(i eps H(site, mu)) from the (seed, stream) generator
+cudaError_t launch_gauge_random(const GeomH& g, double eps, uint64_t seed, uint64_t stream, double* canon,
+                                cudaStream_t s);
+// internal P64 links -> canonical doubles
+cudaError_t launch_gauge_unpack64(const GeomH& g, const void* U64, double* canon, cudaStream_t s);
 // FP64 clover build from the internal P64 gauge; writes the packed clover of prec
 cudaError_t launch_clover_build(int prec, const GeomH& g, const void* U64, double kappa, double csw, void* clover,
                                 cudaStream_t s);
@@ -104,11 +114,15 @@ cudaError_t launch_coarse_sap_half(int kprec, const GeomH& g, const BlockH& bh, 
 // device scratch of coarse_solver_partial_bytes() / coarse_solver_state_bytes(); the first 12
 // bytes of state must be zero before the launch; state word 3 accumulates the cycle count,
 // word 2 is nonzero on failure (1 = barrier timeout, 2 = breakdown / non-finite)
+// nb (1..coarse_solver_max_rhs()) right-hand sides in lockstep: b, x, rt, R[j], U[j] each hold nb
+// vectors one after another; every stencil pass reads the operator once for all of them, and each
+// right-hand side keeps its own scalars and stopping test (its iterates are those of a single solve)
 size_t coarse_solver_state_bytes();
 size_t coarse_solver_partial_bytes();
+int coarse_solver_max_rhs();
 cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
                                    void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
-                                   void* part, void* state, int cluster, cudaStream_t s);
+                                   void* part, void* state, int cluster, cudaStream_t s, int nb = 1);
 // multi-RHS coarse stencil on the tensor cores (coarse_tc.cu): bfloat16 operands, FP32
 // accumulation; needs Nc % 16 == 0 and Nc <= 64.  The operator is first copied into the
 // tensor-core operand image ([V][2Nc][9Nc] bfloat16 in 8 x 8 core-matrix order) from its

@@ -289,4 +289,51 @@ amg_status amg_nn_train_step(amg_nn* nn, const float* r, const float* e, int npa
     return AMG_OK;
 }
 
+void amg_train_params_default(amg_train_params* p) {
+    if (!p) return;
+    p->npairs = 4096;
+    p->batch = 16;
+    p->lr = 1e-3;
+    p->seed = 5;
+}
+
+amg_status amg_learned_train(amg_hierarchy* h, amg_nn* nn, const amg_train_params* p, double* losses,
+                             amg_stream stream) {
+    if (!h || !nn || !p || p->npairs < 1 || p->batch < 1 || !(p->lr > 0))
+        return nfail(AMG_EINVAL, "amg_learned_train: bad argument");
+    amg_dirac* d = amg_internal_hierarchy_dirac(h);
+    if (d != nn->d) return nfail(AMG_EINVAL, "amg_learned_train: network and hierarchy use different operators");
+    cudaStream_t s = (cudaStream_t)stream;
+    const GeomH& g = geom(nn);
+    const size_t n = (size_t)g.V * 12;   // complex numbers per field
+    const size_t f64 = n * 16, f32 = n * 8;
+    DevBuf e0, w, e1, r1, rb, eb;
+    NCK(e0.ensure(f64));
+    NCK(w.ensure(f64));
+    NCK(e1.ensure(f64));
+    NCK(r1.ensure(f64));
+    NCK(rb.ensure(f32 * p->batch));
+    NCK(eb.ensure(f32 * p->batch));
+    const int steps = p->npairs / p->batch;
+    if (steps < 1) return nfail(AMG_EINVAL, "amg_learned_train: npairs < batch");
+    for (int st = 0; st < steps; ++st) {
+        for (int q = 0; q < p->batch; ++q) {
+            const uint64_t k = (uint64_t)st * p->batch + q;
+            // e0: Gaussian field k of stream (seed, AMG_RNG_STREAM_NN); e = e0 - M D e0, r = D e
+            NCK(launch_random_normal(p->seed, AMG_RNG_STREAM_NN, k * n, n, e0.as<double>(), s));
+            NTRY(amg_apply_D(d, e0.p, w.p, 1, AMG_F64, stream));
+            NTRY(amg_precondition(h, w.as<double>(), e1.as<double>(), stream));
+            NCK(launch_axpby(0, make_double2(1, 0), e0.p, make_double2(-1, 0), e1.p, n, s));
+            NTRY(amg_apply_D(d, e1.p, r1.p, 1, AMG_F64, stream));
+            NCK(launch_convert_flat(0, 1, e1.p, (char*)eb.p + q * f32, n, s));
+            NCK(launch_convert_flat(0, 1, r1.p, (char*)rb.p + q * f32, n, s));
+        }
+        double loss = 0;
+        NTRY(amg_nn_train_step(nn, rb.as<float>(), eb.as<float>(), p->batch, p->lr, &loss, stream));
+        if (losses) losses[st] = loss;
+    }
+    NCK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
 }  // extern "C"

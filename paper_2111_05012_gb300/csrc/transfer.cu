@@ -4,6 +4,8 @@
 // operator D_c(I, J) = <I|D|J> (Eq. 7).  |X, s, i> is test vector i projected
 // to chirality s (spins 0,1 or 2,3) and restricted to block X; coarse dof
 // index I = s * nvec + i.  One CTA works on one block, one thread per site.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -136,11 +138,14 @@ __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __res
     const int nc = 2 * nvec;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const size_t vb = spinor_bytes<PV>(g.V);
-    fine = (const char*)fine + blockIdx.y * spinor_bytes<PF>(g.V);
-    coarse = (char*)coarse + blockIdx.y * (size_t)bk.Vc * nc * sizeof(cx<TC>);
+    // right-hand side = blockIdx.x (the fast grid index): the CTAs of one block for all
+    // right-hand sides of a batch are launched together and read the same test-vector lines
+    // at about the same time, so L2 serves the repeats and DRAM sees each line about once
+    fine = (const char*)fine + blockIdx.x * spinor_bytes<PF>(g.V);
+    coarse = (char*)coarse + blockIdx.x * (size_t)bk.Vc * nc * sizeof(cx<TC>);
     const int qi = transposed_index<NQ>(lane);
     const bool writer = (lane & (32 / NQ - 1)) == 0;
-    for (int Xi = blockIdx.x; Xi < bk.Vc; Xi += gridDim.x) {
+    for (int Xi = blockIdx.y; Xi < bk.Vc; Xi += gridDim.y) {
         const int l = threadIdx.x;
         const bool active = l < bk.Vb;
         int c[4], s = 0;
@@ -198,9 +203,10 @@ __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __rest
     cx<T>* xc = reinterpret_cast<cx<T>*>(smem_raw);   // [2*nvec]
     const int nc = 2 * nvec;
     const size_t vb = spinor_bytes<PV>(g.V);
-    coarse = (const char*)coarse + blockIdx.y * (size_t)bk.Vc * nc * sizeof(cx<TC>);
-    fine = (char*)fine + blockIdx.y * spinor_bytes<PF>(g.V);
-    for (int Xi = blockIdx.x; Xi < bk.Vc; Xi += gridDim.x) {
+    // right-hand side = blockIdx.x, as in restrict_kernel
+    coarse = (const char*)coarse + blockIdx.x * (size_t)bk.Vc * nc * sizeof(cx<TC>);
+    fine = (char*)fine + blockIdx.x * spinor_bytes<PF>(g.V);
+    for (int Xi = blockIdx.y; Xi < bk.Vc; Xi += gridDim.y) {
         for (int j = threadIdx.x; j < nc; j += blockDim.x)
             xc[j] = ccast<T>(CStore<TC>::ld(coarse, (size_t)Xi * nc + j));
         __syncthreads();
@@ -403,7 +409,8 @@ cudaError_t restrict_impl(const GeomH& gh, const BlockH& bh, int nvec, const voi
     Blocking bk = make_blocking(gh, bh);
     int th = threads_for(bk);
     size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<typename PF::T>);
-    (note_launch(), restrict_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, fine, coarse));
+    (note_launch(), restrict_kernel<PF, PV, TC><<<dim3(nrhs, std::min(bk.Vc, 65535)), th, smem, st>>>(g, bk, nvec, vecs,
+                                                                                                 fine, coarse));
     return cudaGetLastError();
 }
 template <class PF, class PV, typename TC>
@@ -413,7 +420,8 @@ cudaError_t prolong_impl(const GeomH& gh, const BlockH& bh, int nvec, const void
     Blocking bk = make_blocking(gh, bh);
     int th = threads_for(bk);
     size_t smem = (size_t)2 * nvec * sizeof(cx<typename PF::T>);
-    (note_launch(), prolong_kernel<PF, PV, TC><<<dim3(bk.Vc, nrhs), th, smem, st>>>(g, bk, nvec, vecs, coarse, fine));
+    (note_launch(), prolong_kernel<PF, PV, TC><<<dim3(nrhs, std::min(bk.Vc, 65535)), th, smem, st>>>(g, bk, nvec, vecs,
+                                                                                                coarse, fine));
     return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ MG_CASES = [
     ((4, 4, 4, 4), 0.3, 1, 0.124, (2, 2, 2, 2), 8),
     ((12, 12, 12, 12), 0.6, 101, 0.130, (3, 3, 3, 3), 6),   # 81-site blocks: padded CTA
     ((8, 4, 4, 8), 0.6, 5, 0.130, (2, 2, 2, 4), 5),
+    ((8, 8, 8, 8), 0.6, 2, 0.130, (4, 4, 4, 4), 24),      # the benchmark's 4^4 domains, Nc = 48
 ]
 
 
@@ -312,12 +313,15 @@ def test_batched_restrict_prolong(mgcase):
     c.amg_hierarchy_destroy(h)
 
 
-def test_twelve_point_sources_in_one_batched_solve():
+@pytest.mark.parametrize("coarse", ["f32", "bf16"])
+def test_twelve_point_sources_in_one_batched_solve(coarse):
     import torch
     dims = (8, 8, 8, 8)
     f = Field(dims, 0.5, 4, 0.129, 1.0)
     c = f.c
     p = _params(c, (4, 4, 4, 4), 8, 1, n_init=2, n_adapt=1)
+    if coarse == "bf16":
+        p.prec_coarsest = c.AMG_BF16
     h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 4, 8))])
     srcs = np.stack([li.point_source(dims, s, col) for s in range(4) for col in range(3)])
     b = to_dev(srcs)
@@ -366,3 +370,98 @@ def test_flexible_bicgstab_outer_solver(mgcase):
         r = b - f.op.apply(from_dev(x, f.shape4 + (12,)))
         assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
         c.amg_hierarchy_destroy(h)
+
+
+def _domain_gram_error(v, block):
+    """max |W^dag W - 1| over (domain, chirality), W the domain's test vectors."""
+    from oracle.lattice import to_blocks
+    n = v.shape[0]
+    w = np.stack([to_blocks(x, block) for x in v])             # (n, Ct,Cz,Cy,Cx, bt,bz,by,bx, 12)
+    nb = int(np.prod(w.shape[1:5]))
+    w = w.reshape(n, nb, -1, 2, 6).transpose(1, 3, 0, 2, 4).reshape(nb, 2, n, -1)
+    g = np.einsum("csik,csjk->csij", np.conj(w), w)
+    return np.abs(g - np.eye(n)).max()
+
+
+SETUP_CASES = [
+    # dims, eps, seed, kappa, block, nvec
+    ((4, 4, 4, 4), 0.3, 1, 0.124, (2, 2, 2, 2), 8),
+    ((8, 8, 8, 8), 0.6, 2, 0.130, (4, 4, 4, 4), 8),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SETUP_CASES)))
+def test_setup_fp64_matches_oracle(case):
+    # the adaptive setup of Sec. 3 (0-a: n_init SAP smoothings, each normalised;
+    # Gram-Schmidt; Galerkin; 0-b: v <- M v, Gram-Schmidt, Galerkin) run all in
+    # FP64 is deterministic up to summation order: its vectors and coarse
+    # operator match the oracle's setup from the same initial vectors
+    dims, eps, seed, kappa, block, nvec = SETUP_CASES[case]
+    f = Field(dims, eps, seed, kappa, 1.0)
+    c = f.c
+    op = odirac.WilsonClover(f.U, kappa, 1.0, True)
+    v0 = li.test_vectors(dims, seed, nvec)
+    p = _params(c, block, nvec, 0, n_init=1, n_adapt=1, prec_coarse=0)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(v0)])
+    hier = oamg.Hierarchy(op, oamg.AMGParams(blocks=[block], nvecs=[nvec], n_init=1, n_adapt=1))
+    hier.setup([v0.reshape((nvec,) + f.shape4 + (12,))])
+    got = c.amg_get_vectors(h, 0, nvec, f.V)
+    got = (got[..., 0] + 1j * got[..., 1]).reshape(hier.levels[0].vecs.shape)
+    assert rel(got, hier.levels[0].vecs) < 1e-8
+    B = c.amg_get_coarse_op(h, 1)
+    B = B[..., 0] + 1j * B[..., 1]
+    assert rel(B, hier.levels[1].op.B.reshape(B.shape)) < 1e-8
+    c.amg_hierarchy_destroy(h)
+    f.close()
+
+
+@pytest.mark.parametrize("vec_prec", ["f32", "f16"])
+def test_mixed_precision_setup_is_orthonormal_and_galerkin(vec_prec):
+    # the benchmark's setup (FP32 smoother, 4^4 blocks, 24 vectors, FP32 or
+    # half-precision test vectors in R/P): whatever vectors it ends with, they
+    # are orthonormal per (domain, chirality) to FP32 rounding (FP32 storage),
+    # and the coarse operator it built is P^dag D P for exactly those vectors
+    dims, block, nvec = (8, 8, 8, 8), (4, 4, 4, 4), 24
+    f = Field(dims, 0.6, 2, 0.130, 1.0)
+    c = f.c
+    op = odirac.WilsonClover(f.U, 0.130, 1.0, True)
+    kw = dict(n_init=1, n_adapt=1)
+    if vec_prec == "f16":
+        kw["prec_vectors"] = c.AMG_F16
+    h = c.amg_setup(f.d, _params(c, block, nvec, 1, **kw), [li.to_interleaved(li.test_vectors(dims, 2, nvec))])
+    got = c.amg_get_vectors(h, 0, nvec, f.V)
+    vr = (got[..., 0] + 1j * got[..., 1]).reshape((nvec,) + f.shape4 + (12,))
+    err = _domain_gram_error(vr, block)
+    assert err < (2e-6 if vec_prec == "f32" else 2e-3)
+    B = c.amg_get_coarse_op(h, 1)
+    B = B[..., 0] + 1j * B[..., 1]
+    assert rel(B, omg.coarse_operator(op, vr, block).B.reshape(B.shape)) < 2e-6
+    c.amg_hierarchy_destroy(h)
+    f.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, "bf16"])
+def test_lockstep_coarse_solves_equal_single_solves(prec):
+    # the coarse BiCGStab(2) of a batch runs in lockstep (up to four right-hand sides per
+    # launch, the operator streamed once per stencil pass for all of them) with per-RHS
+    # scalars and stopping tests: one outer step of a 5-RHS solve (a group of four and a
+    # group of one) gives each right-hand side exactly what its own solve gives
+    import torch
+    dims = (8, 8, 8, 8)
+    f = Field(dims, 0.6, 2, 0.130, 1.0)
+    c = f.c
+    p = _params(c, (4, 4, 4, 4), 8, 0 if prec == 0 else 1, n_init=1, n_adapt=1)
+    if prec == "bf16":
+        p.prec_coarsest = c.AMG_BF16
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 2, 8))])
+    nb = 5
+    B = to_dev(np.stack([li.rhs(dims, 50 + k) for k in range(nb)]))
+    X = torch.zeros_like(B)
+    c.amg_solve(h, B, X, nb, 1e-10, 1, raise_on_nonconv=False)
+    n = f.V * 24
+    for k in range(nb):
+        xk = torch.zeros(n, dtype=torch.float64, device="cuda")
+        c.amg_solve(h, B[k * n:(k + 1) * n].contiguous(), xk, 1, 1e-10, 1, raise_on_nonconv=False)
+        assert rel(from_dev(X[k * n:(k + 1) * n], (n // 2,)), from_dev(xk, (n // 2,))) < 1e-13
+    c.amg_hierarchy_destroy(h)
+    f.close()

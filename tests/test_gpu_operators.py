@@ -57,12 +57,14 @@ def test_apply_D_mixed_fp64_accurate(field):
     assert rel(from_dev(y, (2,) + field.shape4 + (12,)), ref) < 1e-13
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_apply_Dsap(field, prec):
     c = field.c
     blocks = [(2, 2, 2, 2)]
     if field.dims == (4, 6, 6, 10):
         blocks.append((2, 3, 3, 5))
+    if field.dims == (8, 8, 8, 8):
+        blocks.append((4, 4, 4, 4))          # the benchmark's 256-site domains
     psi = li.rhs(field.dims, 4)
     for blk in blocks:
         ref = field.op.apply_sap(psi.reshape(field.shape4 + (12,)), blk)

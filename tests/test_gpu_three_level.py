@@ -170,3 +170,27 @@ def test_three_level_checkpoint_and_missing_vectors(three, tmp_path):
         assert np.abs(B1 - B2).max() <= 1e-5 * np.abs(B1).max()
     c.amg_hierarchy_destroy(h)
     c.amg_hierarchy_destroy(h2)
+
+
+def test_three_grid_setup_fp64_matches_oracle(three):
+    # the adaptive setup of Sec. 3 on three grids, all in FP64: level 1 is set up (its own
+    # SAP smoothing, Gram-Schmidt, Galerkin, adaptive pass with its own cycle) right after
+    # its stencil is first built, then the level-0 adaptive pass rebuilds D_1 and, from the
+    # unchanged level-1 vectors, D_2; the GPU's vectors and stencils match the oracle's
+    f = three
+    c = f.c
+    h = c.amg_setup(f.d, _params(c, 0, n_init=1, n_adapt=1), f.init)
+    hier = oamg.Hierarchy(f.op, oamg.AMGParams(blocks=BLOCKS, nvecs=NVEC, n_init=1, n_adapt=1))
+    hier.setup([f.v0.reshape((NVEC[0],) + f.shape4 + (12,)), f.v1])
+    got0 = c.amg_get_vectors(h, 0, NVEC[0], f.V)
+    got0 = (got0[..., 0] + 1j * got0[..., 1]).reshape(hier.levels[0].vecs.shape)
+    assert rel(got0, hier.levels[0].vecs) < 1e-8
+    V1 = int(np.prod(f.cshape1))
+    got1 = c.amg_get_vectors(h, 1, NVEC[1], V1, 2 * NVEC[0])
+    got1 = (got1[..., 0] + 1j * got1[..., 1]).reshape(hier.levels[1].vecs.shape)
+    assert rel(got1, hier.levels[1].vecs) < 1e-8
+    for lev in (1, 2):
+        B = c.amg_get_coarse_op(h, lev)
+        B = B[..., 0] + 1j * B[..., 1]
+        assert rel(B, hier.levels[lev].op.B.reshape(B.shape)) < 1e-8
+    c.amg_hierarchy_destroy(h)
