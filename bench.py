@@ -294,7 +294,7 @@ def run_headline(args):
     import torch.distributed as dist
     rank, world, local = dist_info()
     pool = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.dims:
         pool = OraclePool()      # spawn before the first GPU call; workers build their samples meanwhile
     torch.cuda.set_device(local)
     if world > 1:
@@ -307,7 +307,12 @@ def run_headline(args):
     __graft_entry__.build()
     from paper_2111_05012_gb300 import capi
 
-    w = PROP
+    w = dict(PROP)
+    config = PROP_CONFIG
+    if args.dims:   # a smaller lattice of the same workload (profiling); the config says so
+        w["dims"] = tuple(int(v) for v in args.dims.split(","))
+        config = dict(PROP_CONFIG, lattice=list(w["dims"]),
+                      workload=PROP_CONFIG["workload"].replace("48^3x96", "x".join(map(str, w["dims"]))))
     dims = w["dims"]
     V = int(np.prod(dims))
     stream = torch.cuda.current_stream()
@@ -340,6 +345,7 @@ def run_headline(args):
     infos = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler() as clk:
+        torch.cuda.nvtx.range_push("timed")
         l0 = capi.amg_launch_count()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -349,6 +355,7 @@ def run_headline(args):
         ev1.record(stream)
         gpu_launches = capi.amg_launch_count() - l0
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
@@ -409,7 +416,7 @@ def run_headline(args):
     line = {
         "metric": METRIC, "value": per_rhs, "unit": "ms/RHS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f16+f64", "data": "synthetic", "config": PROP_CONFIG,
+        "vs_baseline": None, "dtype": "f32+f16+f64", "data": "synthetic", "config": config,
         "roofline": {"kernel": "sap_half_kernel<P32,256> (fused SAP half sweep)", "bound": "alu",
                      "achieved": sap_tflops, "peak": peak, "unit": "TFLOP/s", "frac": sap_tflops / peak,
                      "traffic": None,
@@ -460,8 +467,8 @@ def _setup_field(capi, dims, eps, seed, kappa, csw):
 def run_learned(args):
     """Learned preconditioner on 24^3x48 (exp(0.6iH), seed 5, kappa 0.130):
     train the 1-4-1 parallel-transport network on 4096 (residual, error)
-    pairs from the solver (e = (1 - M D) e0, r = D e), streamed in batches of
-    16, then solve 16 fresh Gaussian right-hand sides (seeds 4000-4015) with
+    pairs from the solver (e = (1 - M D) e0, r = D e; amg_learned_train,
+    batches of 16), then solve 16 fresh Gaussian right-hand sides (seeds 4000-4015) with
     and without it, and with the same method all in FP64."""
     import torch
     import __graft_entry__
@@ -484,24 +491,10 @@ def run_learned(args):
         W2[0, a, 0, range(4), range(4), 0] = 0.5
     nn = capi.amg_nn_create(d, channels, w + np.concatenate([W1.reshape(-1), W2.reshape(-1)]))
     npairs, batch = args.pairs, 16
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(5)
+    tp = capi.amg_train_params_default()
+    tp.npairs, tp.batch, tp.lr, tp.seed = npairs, batch, 1e-3, 5
     t0 = time.perf_counter()
-    losses = []
-    De0 = torch.empty(V * 24, dtype=torch.float64, device="cuda")
-    Me = torch.empty_like(De0)
-    for step in range(npairs // batch):
-        rs, es = [], []
-        for k in range(batch):
-            e0 = torch.randn(V * 24, dtype=torch.float64, device="cuda", generator=gen)
-            capi.amg_apply_D(d, e0, De0, 1, capi.AMG_F64)
-            capi.amg_precondition(h, De0, Me)
-            e1 = e0 - Me
-            r1 = torch.empty_like(e1)
-            capi.amg_apply_D(d, e1, r1, 1, capi.AMG_F64)
-            es.append(e1.float())
-            rs.append(r1.float())
-        losses.append(capi.amg_nn_train_step(nn, torch.cat(rs), torch.cat(es), batch, 1e-3))
+    losses = list(capi.amg_learned_train(h, nn, tp))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     res = {}
@@ -1012,6 +1005,8 @@ def main():
     ap.add_argument("--workload", default="propagator",
                     choices=["propagator", "solve16", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--dims", default=None,
+                    help="propagator workload on a smaller lattice Lx,Ly,Lz,Lt (profiling; not the headline)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1],
                     help="SAP kernel: 0 operator through L1/L2 (default), 1 staged in shared memory, -1 autotune")

@@ -99,7 +99,12 @@ typedef struct {
                                            memory (FP32/FP16, blocks <= 256 sites) [-1] */
     int outer_solver;                   /* 0: flexible GMRES(outer_m) [0]; 1: the paper's BiCGStab with
                                            flexible preconditioning (Sec. 3), one right-hand side at a
-                                           time; both stop on the FP64 true residual */
+                                           time; 2: the paper's comparison solver MBiCGs (Sec. 5,
+                                           Table 1): the same flexible BiCGStab preconditioned by
+                                           BiCGStab(coarse_ell) on the fine operator itself in the
+                                           smoother precision (FP32 or FP64), from zero to
+                                           mbicgs_tol or mbicgs_maxit cycles, no multigrid; all stop
+                                           on the FP64 true residual */
     int prec_vectors;                   /* fine test vectors as read by restriction and prolongation
                                            (Eqs. 5, 6): AMG_F16 stores them in half precision with a
                                            per-site scale (about half the bytes of each transfer); the
@@ -108,6 +113,8 @@ typedef struct {
                                            D_c stay consistent.  Any other value keeps the setup's
                                            precision (FP64 with an FP64 smoother, else FP32).  AMG_F16
                                            needs an FP32 or FP16 smoother [AMG_F32] */
+    double mbicgs_tol;                  /* MBiCGs inner solve: relative residual [1e-4] */
+    int mbicgs_maxit;                   /* MBiCGs inner solve: BiCGStab(l) cycles [50] */
 } amg_params;
 
 typedef struct {
@@ -322,8 +329,9 @@ amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, voi
 
 /* x = SAP(b) on the fine lattice (Sec. 3 listing: x = 0, r = b, n times
  * {x += M_e r; r = b - Dx; x += M_o r; r = b - Dx}, M = mr_iters minimal
- * residual steps per domain), in the smoother precision. Canonical vectors. */
-amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_stream s);
+ * residual steps per domain), in the smoother precision, for nrhs canonical
+ * vectors one after another (the batched kernels of a lockstep solve). */
+amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, int nrhs, amg_prec prec, amg_stream s);
 
 /* x = SAP(b) on coarse level 1 <= level <= nlevels-2 (three or more grids):
  * the same listing with the level's blocks as domains and D_SAP the level's

@@ -14,6 +14,9 @@
 * ``fbicgstab``: the paper's outer solver, BiCGStab with flexible
   preconditioning (Sec. 3), its listing's two misprints read as in the
   standard method (reading C11).
+* ``mbicgs``: the paper's comparison solver of Sec. 5 (Table 1, "MBiCGs"):
+  the same flexible BiCGStab preconditioned by a loose BiCGStab(l) solve of
+  the same system (reading C27).
 
 Inner products are <a, b> = a^dag b (numpy ``vdot``).
 """
@@ -247,6 +250,21 @@ def fbicgstab(apply_A, b, apply_M=None, tol: float = 1e-10, maxit: int = 1000, x
             beta = (alpha / omega) * rho_new / rho
             rho = rho_new
             p = r + beta * (p - omega * DMp)
+
+
+def mbicgs(apply_A, b, tol: float = 1e-10, maxit: int = 1000, inner_ell: int = 2, inner_tol: float = 1e-4,
+           inner_maxit: int = 50):
+    """Mixed-precision BiCGStab, the comparison solver of Sec. 5: the flexible
+    BiCGStab of the outer solve (``fbicgstab``) with, as its preconditioner,
+    BiCGStab(l) (Sleijpen-Fokkema, the algorithm of the coarse solve) on the
+    same operator, started from zero and stopped at relative residual
+    inner_tol or after inner_maxit cycles (reading C27).  The paper runs the
+    inner solve in single precision; the oracle runs it in FP64, its own
+    precision, so that it states what the method computes."""
+    def apply_M(v):
+        z, _ = bicgstab_l(apply_A, v, ell=inner_ell, tol=inner_tol, maxit=inner_maxit)
+        return z
+    return fbicgstab(apply_A, b, apply_M, tol=tol, maxit=maxit)
 
 
 def gmres_dense_reference(A: np.ndarray, b: np.ndarray, k: int) -> np.ndarray:

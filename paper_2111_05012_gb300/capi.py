@@ -50,6 +50,8 @@ class amg_params(ctypes.Structure):
         ("sap_variant", ctypes.c_int),
         ("outer_solver", ctypes.c_int),
         ("prec_vectors", ctypes.c_int),
+        ("mbicgs_tol", ctypes.c_double),
+        ("mbicgs_maxit", ctypes.c_int),
     ]
 
 
@@ -119,7 +121,7 @@ PROTOTYPES = {
     "amg_apply_coarse": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "amg_restrict": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "amg_prolong": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
-    "amg_sap": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "amg_sap": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "amg_sap_coarse": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
     "amg_precondition": (_i, [_vp, _vp, _vp, _vp]),
     "amg_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, ctypes.POINTER(amg_solve_info), _vp]),
@@ -365,8 +367,8 @@ def amg_prolong(h, coarsening, coarse, fine, nrhs=1, prec=AMG_F64, stream=None):
                               _stream(stream)))
 
 
-def amg_sap(h, b, x, prec=AMG_F32, stream=None):
-    _check(load().amg_sap(h, _ptr(b), _ptr(x), int(prec), _stream(stream)))
+def amg_sap(h, b, x, prec=AMG_F32, stream=None, nrhs=1):
+    _check(load().amg_sap(h, _ptr(b), _ptr(x), int(nrhs), int(prec), _stream(stream)))
 
 
 def amg_sap_coarse(h, level, b, x, nrhs=1, prec=AMG_F32, stream=None):

@@ -204,6 +204,7 @@ struct amg_hierarchy {
     DevBuf ob, ox, ow, orr;
     std::vector<DevBuf*> oV, oZ;
     DevBuf bv[6], bz[2];   // flexible BiCGStab: r, r~, p, s, t, D M p (FP64); M p, M s (Z precision)
+    std::vector<DevBuf> mb;   // MBiCGs inner BiCGStab(l): r~, R_0..R_l, U_0..U_l (smoother precision)
     DevBuf canon;   // canonical staging
     Reducer red;
     // outer Gram-Schmidt with device-side coefficients: per right-hand side three regions of
@@ -215,7 +216,8 @@ struct amg_hierarchy {
     int err_flag_host = 0;
     DevBuf err_flag;
     int coarse_cycles = 0;
-    int sap_variant[3] = {0, 0, 0};   // chosen SAP kernel per smoother precision
+    int sap_variant[3] = {0, 0, 0};      // chosen SAP kernel per smoother precision, one right-hand side
+    int sap_variant_nb[3] = {0, 0, 0};   // the same for batches (the staged kernel then takes two per CTA)
     amg_nn* nn = nullptr;             // learned correction after the cycle (FP32 smoother only)
     bool nn_off = false;              // set while falling back to the plain cycle
     int* hstate = nullptr;   // pinned mirror of the coarse solver state words (16 x 4 ints)
@@ -291,7 +293,11 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
         return fail(AMG_EINVAL, "a bfloat16 coarsest operator needs an even number of test vectors");
     if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
-    if (p->outer_solver != 0 && p->outer_solver != 1) return fail(AMG_EINVAL, "outer_solver must be 0 or 1");
+    if (p->outer_solver < 0 || p->outer_solver > 2) return fail(AMG_EINVAL, "outer_solver must be 0, 1 or 2");
+    if (p->outer_solver == 2 && p->prec_smoother == AMG_F16)
+        return fail(AMG_EINVAL, "MBiCGs (outer_solver 2) runs its inner BiCGStab in FP32 or FP64");
+    if (p->outer_solver == 2 && (!(p->mbicgs_tol > 0) || p->mbicgs_maxit < 1))
+        return fail(AMG_EINVAL, "MBiCGs needs mbicgs_tol > 0 and mbicgs_maxit >= 1");
     if (p->prec_vectors == AMG_F16 && p->prec_smoother == AMG_F64)
         return fail(AMG_EINVAL, "half-precision test vectors need an FP32 or FP16 smoother");
     if (p->sap_iters < 0 || p->mr_iters < 0) return fail(AMG_EINVAL, "sap_iters / mr_iters");
@@ -313,7 +319,7 @@ amg_status fine_D(amg_hierarchy* h, int prec, const void* in, void* out, const v
 amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_zero, int nb, cudaStream_t s) {
     amg_dirac* d = h->d;
     h->timer.start(PH_SMOOTH, s);
-    const int var = h->sap_variant[prec];
+    const int var = nb > 1 ? h->sap_variant_nb[prec] : h->sap_variant[prec];
     for (int i = 0; i < h->p.sap_iters; ++i) {
         const bool first = x_zero && i == 0;
         CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], 0, h->p.mr_iters, first ? 1 : 0,
@@ -548,13 +554,154 @@ amg_status vcycle0(amg_hierarchy* h, int prec, const void* b, void* x, int nb, c
     return AMG_OK;
 }
 
+// ---------------------------------------------------------------- MBiCGs preconditioner
+// Coefficients of the minimal-residual part of BiCGStab(l) from the Gram
+// matrix G_pq = <R_p, R_q> (p, q = 0..l): Gram-Schmidt of R_1..R_l in the
+// original basis (Rt_j = sum_k C[j][k] R_k, tau_ij = <Rt_i, Rt_j> / sigma_i),
+// then x += cx_0 R_0 + sum_k cx_k R_k, R_0 -= sum_k cr_k R_k,
+// U_0 -= sum_k cg_k U_k (the same algebra as the coarse solver's kernel).
+bool bicgstab_mr_coefficients(const std::vector<std::vector<cplx>>& G, int ell, std::vector<cplx>& cxv,
+                              std::vector<cplx>& crv, std::vector<cplx>& cgv) {
+    std::vector<std::vector<cplx>> C(ell + 1, std::vector<cplx>(ell + 1, cplx(0))),
+        tau(ell + 1, std::vector<cplx>(ell + 1, cplx(0)));
+    std::vector<double> sigma(ell + 1, 0.0);
+    std::vector<cplx> gp(ell + 1, cplx(0)), g(ell + 1, cplx(0)), gpp(ell + 1, cplx(0));
+    for (int j = 1; j <= ell; ++j) {
+        C[j][j] = 1;
+        for (int i = 1; i < j; ++i) {
+            cplx t = 0;
+            for (int p = 1; p <= i; ++p)
+                for (int q = 1; q <= j; ++q) t += std::conj(C[i][p]) * C[j][q] * G[p][q];
+            tau[i][j] = t / sigma[i];
+            for (int k = 1; k <= i; ++k) C[j][k] -= tau[i][j] * C[i][k];
+        }
+        double sg = 0;
+        cplx t0 = 0;
+        for (int p = 1; p <= j; ++p) {
+            for (int q = 1; q <= j; ++q) sg += (std::conj(C[j][p]) * C[j][q] * G[p][q]).real();
+            t0 += std::conj(C[j][p]) * G[p][0];
+        }
+        if (!(sg > 0)) return false;
+        sigma[j] = sg;
+        gp[j] = t0 / sg;
+    }
+    g[ell] = gp[ell];
+    for (int j = ell - 1; j >= 1; --j) {
+        cplx t = gp[j];
+        for (int i = j + 1; i <= ell; ++i) t -= tau[j][i] * g[i];
+        g[j] = t;
+    }
+    for (int j = 1; j < ell; ++j) {
+        cplx t = g[j + 1];
+        for (int i = j + 1; i < ell; ++i) t += tau[j][i] * g[i + 1];
+        gpp[j] = t;
+    }
+    cxv.assign(ell + 1, cplx(0));
+    crv.assign(ell + 1, cplx(0));
+    cgv = g;
+    cxv[0] = g[1];
+    for (int j = 1; j < ell; ++j)
+        for (int k = 1; k <= j; ++k) cxv[k] += gpp[j] * C[j][k];
+    for (int j = 1; j <= ell; ++j)
+        for (int k = 1; k <= j; ++k) crv[k] += gp[j] * C[j][k];
+    return true;
+}
+
+// x = BiCGStab(l)(D, b) on the fine lattice in precision prec (internal fields), from x = 0
+// to relative residual mbicgs_tol or mbicgs_maxit cycles: the preconditioner of the paper's
+// mixed-precision BiCGStab comparison solver (Sec. 5; reading C27).  Host-driven: every
+// cycle is 2l fine stencil passes, whose cost dwarfs the host synchronisations.
+amg_status fine_bicgstab_l(amg_hierarchy* h, int prec, const void* b, void* x, cudaStream_t s) {
+    const int ell = h->p.coarse_ell;
+    const size_t n = fine_n(h), fb = fsz(h, prec);
+    Reducer& red = h->red;
+    while ((int)h->mb.size() < 2 * ell + 3) h->mb.emplace_back();
+    for (auto& v : h->mb) CK(v.ensure(fb));
+    void* rt = h->mb[0].p;
+    std::vector<void*> R(ell + 1), U(ell + 1);
+    for (int j = 0; j <= ell; ++j) {
+        R[j] = h->mb[1 + j].p;
+        U[j] = h->mb[2 + ell + j].p;
+    }
+    const double2 one = make_double2(1, 0);
+    auto axpy = [&](cplx a, const void* xv, void* yv) -> amg_status {   // y += a x
+        CK(launch_axpby(prec, d2(a), xv, one, yv, n, s));
+        return AMG_OK;
+    };
+    CK(cudaMemsetAsync(x, 0, fb, s));
+    CK(cudaMemsetAsync(U[0], 0, fb, s));
+    CK(cudaMemcpyAsync(R[0], b, fb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(rt, b, fb, cudaMemcpyDeviceToDevice, s));
+    double bn2;
+    TRY(red.norm2(prec, b, n, &bn2, s));
+    if (!std::isfinite(bn2)) return fail(AMG_NAN, "MBiCGs: non-finite right-hand side");
+    if (bn2 == 0) return AMG_OK;
+    cplx rho0 = 1, alpha = 0, omega = 1;
+    const double tol2 = h->p.mbicgs_tol * h->p.mbicgs_tol * bn2;
+    for (int cycle = 0; cycle < h->p.mbicgs_maxit; ++cycle) {
+        double rn2;
+        TRY(red.norm2(prec, R[0], n, &rn2, s));
+        if (!std::isfinite(rn2)) return fail(AMG_NAN, "MBiCGs: non-finite inner residual");
+        if (rn2 <= tol2) break;
+        rho0 = -omega * rho0;
+        for (int j = 0; j < ell; ++j) {
+            cplx rho1;
+            TRY(red.dot(prec, rt, R[j], n, &rho1, s));
+            const cplx beta = alpha * rho1 / rho0;
+            rho0 = rho1;
+            for (int i = 0; i <= j; ++i) CK(launch_axpby(prec, one, R[i], d2(-beta), U[i], n, s));   // U_i = R_i - beta U_i
+            TRY(fine_D(h, prec, U[j], U[j + 1], nullptr, 1, s));
+            cplx gam;
+            TRY(red.dot(prec, rt, U[j + 1], n, &gam, s));
+            alpha = rho0 / gam;
+            if (!std::isfinite(alpha.real()) || !std::isfinite(alpha.imag()))
+                return fail(AMG_NAN, "MBiCGs: inner BiCGStab breakdown");
+            for (int i = 0; i <= j; ++i) TRY(axpy(-alpha, U[i + 1], R[i]));
+            TRY(fine_D(h, prec, R[j], R[j + 1], nullptr, 1, s));
+            TRY(axpy(alpha, U[0], x));
+        }
+        // Gram matrix of R_0..R_l, one row of dots per R_q
+        std::vector<std::vector<cplx>> G(ell + 1, std::vector<cplx>(ell + 1));
+        std::vector<const void*> Rl(R.begin(), R.end());
+        for (int q = 0; q <= ell; ++q) {
+            std::vector<cplx> row(ell + 1);
+            TRY(red.dots(prec, ell + 1, Rl.data(), R[q], n, row.data(), s));
+            for (int p = 0; p <= ell; ++p) G[p][q] = row[p];
+        }
+        std::vector<cplx> cxv, crv, cgv;
+        if (!bicgstab_mr_coefficients(G, ell, cxv, crv, cgv)) return fail(AMG_NAN, "MBiCGs: inner BiCGStab breakdown");
+        omega = cgv[ell];
+        TRY(axpy(cxv[0], R[0], x));
+        for (int k = 1; k <= ell; ++k) {
+            TRY(axpy(cxv[k], R[k], x));
+            TRY(axpy(-crv[k], R[k], R[0]));
+            TRY(axpy(-cgv[k], U[k], U[0]));
+        }
+    }
+    return AMG_OK;
+}
+
 // z = M v for FP64 internal fields v; z is written in the outer solver's Z
 // precision (FP64 for the all-FP64 path, else FP32: the cycle's output is
-// exact in FP32, so nothing is lost)
+// exact in FP32, so nothing is lost).  With outer_solver 2 (MBiCGs) M is the
+// inner BiCGStab(l) on the fine operator instead of the multigrid cycle.
 int zprec_of(amg_hierarchy* h) { return h->fp == 0 ? 0 : 1; }
 amg_status precondition64(amg_hierarchy* h, const void* v, void* z, int nb, cudaStream_t s) {
     const GeomH& g = fine_geom(h);
     int fp = h->fp;
+    if (h->p.outer_solver == 2) {
+        if (nb != 1) return fail(AMG_EINVAL, "MBiCGs preconditions one right-hand side at a time");
+        h->timer.start(PH_SMOOTH, s);
+        amg_status st;
+        if (fp == 0) {
+            st = fine_bicgstab_l(h, 0, v, z, s);
+        } else {
+            CK(launch_convert_spinor(0, 1, g, v, h->fb[1].p, 1, s));
+            st = fine_bicgstab_l(h, 1, h->fb[1].p, z, s);
+        }
+        h->timer.stop(s);
+        return st;
+    }
     if (fp == 0) return vcycle0(h, 0, v, z, nb, s);
     CK(launch_convert_spinor(0, fp, g, v, h->fb[fp].p, nb, s));
     if (fp == 1) {
@@ -896,7 +1043,7 @@ amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
     while ((int)h->oZ.size() < h->p.outer_m) h->oZ.push_back(new DevBuf());
     for (auto* v : h->oV) CK(v->ensure(fb64));
     for (auto* z : h->oZ) CK(z->ensure(fine_spinor_bytes(h->fp == 0 ? 0 : 1, g.V) * nb));
-    if (h->p.outer_solver == 1) {
+    if (h->p.outer_solver >= 1) {
         for (auto& v : h->bv) CK(v.ensure(fine_spinor_bytes(0, g.V)));
         for (auto& z : h->bz) CK(z.ensure(fine_spinor_bytes(h->fp == 0 ? 0 : 1, g.V)));
     }
@@ -1081,47 +1228,54 @@ amg_status setup_coarse_level(amg_hierarchy* h, int l, const double* const* init
 }
 
 // Autotuner: for every smoother precision the hierarchy uses, time the SAP
-// half-sweep variants on this lattice and blocking (zero fields, 3 timed
-// launches each after one warm-up) and keep the faster one.
+// half-sweep variants on this lattice and blocking (zero fields; one full SAP
+// iteration, both colours, per sample, the variants alternating so that drifts
+// of clock or cache state hit both alike; the median of 9 samples decides),
+// once for a single right-hand side and once for a batch of three (the staged
+// variant shares its staged operator between two right-hand sides per CTA; an
+// odd batch leaves half of its last CTAs idle, so three is its worst case), and
+// keep the faster variant for each.
 amg_status tune_kernels(amg_hierarchy* h) {
     const GeomH& g = fine_geom(h);
     amg_dirac* d = h->d;
     int precs[2] = {h->fp, h->vp};
     for (int pr : precs) {
-        if (h->p.sap_variant >= 0) {
-            h->sap_variant[pr] = sap_staged_supported(pr, h->blk[0]) ? h->p.sap_variant : 0;
+        const bool staged = sap_staged_supported(pr, h->blk[0]);
+        if (h->p.sap_variant >= 0 || !staged) {
+            h->sap_variant[pr] = h->sap_variant_nb[pr] = staged ? h->p.sap_variant : 0;
+            if (h->sap_variant[pr] < 0) h->sap_variant[pr] = h->sap_variant_nb[pr] = 0;
             continue;
         }
-        if (!sap_staged_supported(pr, h->blk[0])) {
-            h->sap_variant[pr] = 0;
-            continue;
-        }
-        CK(cudaMemset(h->fb[pr].p, 0, fine_spinor_bytes(pr, g.V)));
-        CK(cudaMemset(h->fx[pr].p, 0, fine_spinor_bytes(pr, g.V)));
+        const size_t fb = fine_spinor_bytes(pr, g.V);
+        DevBuf tb, tx;
+        CK(tb.ensure(3 * fb));
+        CK(tx.ensure(3 * fb));
+        CK(cudaMemset(tb.p, 0, 3 * fb));
+        CK(cudaMemset(tx.p, 0, 3 * fb));
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        // the two variants alternate (one full SAP iteration, both colours, per sample) so that
-        // drifts of clock or cache state hit both alike; the median of 9 samples decides
-        std::vector<float> t[2];
-        for (int rep = 0; rep < 10; ++rep) {
-            for (int v = 0; v <= 1; ++v) {
-                CK(cudaEventRecord(e0, 0));
-                for (int colour = 0; colour < 2; ++colour)
-                    CK(launch_sap_half_variant(v, pr, g, h->blk[0], colour, h->p.mr_iters, 0, d->gauge->U[pr].p,
-                                               d->C[pr].p, h->fb[pr].p, h->fx[pr].p, d->kappa, 1, 0));
-                CK(cudaEventRecord(e1, 0));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep > 0) t[v].push_back(ms);
+        for (int nrhs : {1, 3}) {
+            std::vector<float> t[2];
+            for (int rep = 0; rep < 10; ++rep) {
+                for (int v = 0; v <= 1; ++v) {
+                    CK(cudaEventRecord(e0, 0));
+                    for (int colour = 0; colour < 2; ++colour)
+                        CK(launch_sap_half_variant(v, pr, g, h->blk[0], colour, h->p.mr_iters, 0, d->gauge->U[pr].p,
+                                                   d->C[pr].p, tb.p, tx.p, d->kappa, nrhs, 0));
+                    CK(cudaEventRecord(e1, 0));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep > 0) t[v].push_back(ms);
+                }
             }
+            for (auto& tv : t) std::sort(tv.begin(), tv.end());
+            const int best_v = t[1][t[1].size() / 2] < t[0][t[0].size() / 2] ? 1 : 0;
+            (nrhs == 1 ? h->sap_variant : h->sap_variant_nb)[pr] = best_v;
         }
-        for (auto& tv : t) std::sort(tv.begin(), tv.end());
-        const int best_v = t[1][t[1].size() / 2] < t[0][t[0].size() / 2] ? 1 : 0;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        h->sap_variant[pr] = best_v;
     }
     return AMG_OK;
 }
@@ -1269,6 +1423,7 @@ amg_status outer_solve(amg_hierarchy* h, int nb, const void* b, void* x, bool x_
                        std::vector<amg_solve_info>& infos, cudaStream_t s) {
     if (h->p.outer_solver == 0) return fgmres(h, nb, b, x, x_nonzero, tol, maxit, infos, s);
     if (nb != 1) return fail(AMG_EINVAL, "flexible BiCGStab solves one right-hand side at a time");
+    // outer_solver 1: preconditioned by the multigrid cycle; 2 (MBiCGs): by BiCGStab(l) on D
     infos.assign(1, amg_solve_info());
     return fbicgstab(h, b, x, x_nonzero, tol, maxit, infos[0], s);
 }
@@ -1527,6 +1682,8 @@ void amg_params_default(amg_params* p) {
     p->sap_variant = -1;
     p->outer_solver = 0;
     p->prec_vectors = AMG_F32;
+    p->mbicgs_tol = 1e-4;
+    p->mbicgs_maxit = 50;
 }
 
 
@@ -2038,13 +2195,14 @@ amg_status amg_prolong(amg_hierarchy* h, int coarsening, const void* coarse, voi
     return AMG_OK;
 }
 
-amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, amg_prec prec, amg_stream s) {
-    if (!h || !b || !x || prec < 0 || prec > 2) return fail(AMG_EINVAL, "bad argument");
+amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, int nrhs, amg_prec prec, amg_stream s) {
+    if (!h || !b || !x || nrhs < 1 || prec < 0 || prec > 2) return fail(AMG_EINVAL, "bad argument");
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
-    CK(launch_pack_spinor(prec, g, b, h->fb[prec].p, 1, st));
-    TRY(fine_sap(h, prec, h->fb[prec].p, h->fx[prec].p, true, 1, st));
-    CK(launch_unpack_spinor(prec, g, h->fx[prec].p, x, 1, st));
+    if (nrhs > h->nb_cap) TRY(alloc_workspaces(h, nrhs));
+    CK(launch_pack_spinor(prec, g, b, h->fb[prec].p, nrhs, st));
+    TRY(fine_sap(h, prec, h->fb[prec].p, h->fx[prec].p, true, nrhs, st));
+    CK(launch_unpack_spinor(prec, g, h->fx[prec].p, x, nrhs, st));
     CK(cudaStreamSynchronize(st));
     return AMG_OK;
 }
@@ -2105,7 +2263,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     // right-hand sides solved in lockstep: up to 12, fewer if the batch's
     // workspaces (FGMRES basis, Z vectors, cycle fields) would not fit in 80%
     // of the free device memory
-    int kMaxBatch = h->p.outer_solver == 1 ? 1 : 12;
+    int kMaxBatch = h->p.outer_solver != 0 ? 1 : 12;
     {
         const size_t f64 = fine_spinor_bytes(0, g.V), fz = fine_spinor_bytes(zprec_of(h), g.V);
         size_t per = f64 * (h->p.outer_m + 1 + 4) + fz * h->p.outer_m;

@@ -776,23 +776,29 @@ template <> struct Staged<P16> {
     }
 };
 
-template <class P>
-__global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
+// NR right-hand sides per CTA (NR = 2 for batches): thread (slot, l) works on site l of the
+// domain for right-hand side NR * (pair index) + slot; the domain's operator is staged once
+// and shared by the slots, each slot has its own residual tile and block reduction.
+template <class P, int NR>
+__global__ void __launch_bounds__(256 * NR, (P::id == 2 && NR == 1) ? 2 : 1)
     sap_half_staged_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode, const void* __restrict__ U,
                            const void* __restrict__ C, const void* __restrict__ b, void* x, float kappa,
-                           int rhs_fast) {
+                           int rhs_fast, int nrhs) {
     using S = Staged<P>;
     using LC = typename S::LC;
     using CC = typename S::CC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int vbp = blockDim.x;
+    const int vbp = blockDim.x / NR;
+    const int slot = threadIdx.x / vbp;
     LC* sl = reinterpret_cast<LC*>(smem_raw);                                     // [4*3][vbp]
     CC* sc = reinterpret_cast<CC*>(sl + (size_t)4 * S::kLinkChunks * vbp);        // [kCloverChunks][vbp]
-    cx<float>* rsh = reinterpret_cast<cx<float>*>(sc + (size_t)S::kCloverChunks * vbp);   // [12][vbp]
-    float* red = reinterpret_cast<float*>(rsh + 12 * vbp);                      // [2][3][32]
+    cx<float>* rsh = reinterpret_cast<cx<float>*>(sc + (size_t)S::kCloverChunks * vbp) + (size_t)slot * 12 * vbp;
+    float* red = reinterpret_cast<float*>(reinterpret_cast<cx<float>*>(sc + (size_t)S::kCloverChunks * vbp) +
+                                          (size_t)NR * 12 * vbp) + slot * 192;   // [NR][2][3][32]
 
     const int k = rhs_fast ? blockIdx.y : blockIdx.x;
-    const int rr = rhs_fast ? blockIdx.x : blockIdx.y;
+    const int rr = NR * (rhs_fast ? blockIdx.x : blockIdx.y) + slot;
+    const bool rhs_ok = rr < nrhs;
     const int h0 = bk.C[0] / 2;
     int rest = k / h0;
     int X1 = rest % bk.C[1];
@@ -802,26 +808,34 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
     int X0 = 2 * (k % h0) + ((X1 + X2 + X3 + colour) & 1);
     const int Xi = X0 + bk.C[0] * (X1 + bk.C[1] * (X2 + bk.C[2] * X3));
 
-    const int l = threadIdx.x, lane = l & 31, warp = l >> 5, nw = (blockDim.x + 31) >> 5;
-    const bool active = l < bk.Vb;
+    const int l = threadIdx.x - slot * vbp, lane = l & 31, warp = l >> 5, nw = (vbp + 31) >> 5;
+    const bool site = l < bk.Vb;
+    const bool active = site && rhs_ok;
     int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
     const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
     cx<float> r[12], z[12], Ar[12];
-    b = (const char*)b + rr * spinor_bytes<P>(g.V);
-    x = (char*)x + rr * spinor_bytes<P>(g.V);
-    if (active) {
+    b = (const char*)b + (rhs_ok ? rr : 0) * spinor_bytes<P>(g.V);
+    x = (char*)x + (rhs_ok ? rr : 0) * spinor_bytes<P>(g.V);
+    if (site) {
         s = block_site(g, bk, Xi, l, c);
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
-        // stage this site's forward links and clover
-        const LC* gl = (const LC*)U;
+        // stage this site's forward links (slot 0) and clover (the last slot)
+        if (slot == 0) {
+            const LC* gl = (const LC*)U;
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu)
+            for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
-            for (int q = 0; q < S::kLinkChunks; ++q)
-                sl[(mu * S::kLinkChunks + q) * vbp + l] = __ldg(gl + ((size_t)mu * S::kLinkChunks + q) * g.V + s);
-        const CC* gc = (const CC*)C;
+                for (int q = 0; q < S::kLinkChunks; ++q)
+                    sl[(mu * S::kLinkChunks + q) * vbp + l] =
+                        __ldg(gl + ((size_t)mu * S::kLinkChunks + q) * g.V + s);
+        }
+        if (slot == NR - 1) {
+            const CC* gc = (const CC*)C;
 #pragma unroll
-        for (int q = 0; q < S::kCloverChunks; ++q) sc[q * vbp + l] = __ldg(gc + (size_t)q * g.V + s);
+            for (int q = 0; q < S::kCloverChunks; ++q) sc[q * vbp + l] = __ldg(gc + (size_t)q * g.V + s);
+        }
+    }
+    if (active) {
         // r = b - D x at this site (global operator; hops may leave the domain)
         SpinorIO<P>::load(b, g.V, s, r);
         if (x_mode != 1) {
@@ -927,11 +941,11 @@ __global__ void __launch_bounds__(256, P::id == 2 ? 2 : 1)
 }
 
 template <class P>
-size_t sap_staged_smem(int vbp) {
+size_t sap_staged_smem(int vbp, int nr = 1) {
     using S = Staged<P>;
     return (size_t)vbp * (4 * S::kLinkChunks * sizeof(typename S::LC) + S::kCloverChunks * sizeof(typename S::CC) +
-                          12 * sizeof(cx<float>)) +
-           2 * 96 * sizeof(float);
+                          nr * 12 * sizeof(cx<float>)) +
+           nr * 2 * 96 * sizeof(float);
 }
 
 template <class P>
@@ -941,15 +955,18 @@ cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, 
     Blocking bk = make_blocking(gh, bh);
     int threads = (bk.Vb + 31) / 32 * 32;
     if (threads > 256) return cudaErrorInvalidValue;
-    size_t smem = sap_staged_smem<P>(threads);
-    cudaError_t e =
-        cudaFuncSetAttribute(sap_half_staged_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int ndom = bk.Vc / 2;
-    const int fast = nrhs > 1 && ndom <= 65535;
-    const dim3 grid = fast ? dim3(nrhs, ndom) : dim3(ndom, nrhs);
-    (note_launch(), sap_half_staged_kernel<P><<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                          (float)kappa, fast));
+    // batches: two right-hand sides per CTA share the staged operator
+    const int nr = nrhs > 1 ? 2 : 1;
+    const int npair = (nrhs + nr - 1) / nr;
+    const int fast = npair > 1 && ndom <= 65535;
+    const dim3 grid = fast ? dim3(npair, ndom) : dim3(ndom, npair);
+    size_t smem = sap_staged_smem<P>(threads, nr);
+    auto fn = nr == 2 ? sap_half_staged_kernel<P, 2> : sap_half_staged_kernel<P, 1>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    (note_launch(), fn<<<grid, threads * nr, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x, (float)kappa, fast,
+                                                          nrhs));
     return cudaGetLastError();
 }
 

@@ -129,6 +129,7 @@ def test_bf16_coarse_operator(mgcase):
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_sap(mgcase, prec, variant):
+    import torch
     f = mgcase
     c = f.c
     h = c.amg_setup_from_vectors(f.d, _params(c, f.block, f.nvec, prec, sap_variant=variant),
@@ -141,6 +142,18 @@ def test_sap(mgcase, prec, variant):
     c.amg_sap(h, x, y, prec)
     tol = {0: 1e-11, 1: 1e-5, 2: 1e-2}[prec]
     assert rel(from_dev(y, f.shape4 + (12,)), ref) < tol
+    # a batch of three in one call (the lockstep kernels: right-hand side as the fast grid
+    # index; the staged variant takes two right-hand sides per CTA)
+    bs = np.stack([li.rhs(f.dims, 11 + k).reshape(f.shape4 + (12,)) for k in range(3)])
+    xb = to_dev(bs, dt)
+    yb = torch.zeros_like(xb)
+    c.amg_sap(h, xb, yb, prec, nrhs=3)
+    got = from_dev(yb, (3,) + f.shape4 + (12,))
+    for k in range(3):
+        refk = ref if k == 0 else osol.sap(f.op, f.block, bs[k], 4, 6)
+        assert rel(got[k], refk) < tol
+    # the batch gives each right-hand side what its own call gives
+    assert rel(got[0], from_dev(y, f.shape4 + (12,))) < (1e-14 if prec == 0 else 1e-6)
     c.amg_hierarchy_destroy(h)
 
 
@@ -440,8 +453,9 @@ def test_mixed_precision_setup_is_orthonormal_and_galerkin(vec_prec):
     f.close()
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1, "bf16"])
-def test_lockstep_coarse_solves_equal_single_solves(prec):
+def test_lockstep_coarse_solves_equal_single_solves(prec, variant):
     # the coarse BiCGStab(2) of a batch runs in lockstep (up to four right-hand sides per
     # launch, the operator streamed once per stencil pass for all of them) with per-RHS
     # scalars and stopping tests: one outer step of a 5-RHS solve (a group of four and a
@@ -450,7 +464,7 @@ def test_lockstep_coarse_solves_equal_single_solves(prec):
     dims = (8, 8, 8, 8)
     f = Field(dims, 0.6, 2, 0.130, 1.0)
     c = f.c
-    p = _params(c, (4, 4, 4, 4), 8, 0 if prec == 0 else 1, n_init=1, n_adapt=1)
+    p = _params(c, (4, 4, 4, 4), 8, 0 if prec == 0 else 1, n_init=1, n_adapt=1, sap_variant=variant)
     if prec == "bf16":
         p.prec_coarsest = c.AMG_BF16
     h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 2, 8))])
@@ -464,4 +478,35 @@ def test_lockstep_coarse_solves_equal_single_solves(prec):
         c.amg_solve(h, B[k * n:(k + 1) * n].contiguous(), xk, 1, 1e-10, 1, raise_on_nonconv=False)
         assert rel(from_dev(X[k * n:(k + 1) * n], (n // 2,)), from_dev(xk, (n // 2,))) < 1e-13
     c.amg_hierarchy_destroy(h)
+    f.close()
+
+
+@pytest.mark.parametrize("dims,eps,seed,kappa", [((4, 4, 4, 4), 0.3, 1, 0.124), ((8, 8, 8, 8), 0.6, 2, 0.130)])
+def test_mbicgs_matches_oracle(dims, eps, seed, kappa):
+    # the paper's comparison solver (Sec. 5): flexible BiCGStab preconditioned by BiCGStab(2)
+    # on D itself.  All in FP64 its iterates after two outer iterations match the oracle's;
+    # with the FP32 inner solve (the paper's mixed precision) it reaches the FP64 tolerance
+    import torch
+    f = Field(dims, eps, seed, kappa, 1.0)
+    c = f.c
+    op = odirac.WilsonClover(f.U, kappa, 1.0, True)
+    block = (2, 2, 2, 2) if dims[0] == 4 else (4, 4, 4, 4)
+    b = li.rhs(dims, 31).reshape(f.shape4 + (12,))
+    p = _params(c, block, 4, 0, outer_solver=2, mbicgs_tol=1e-4, mbicgs_maxit=50)
+    h = c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(li.test_vectors(dims, seed, 4))])
+    ref, _ = osol.mbicgs(op.apply, b, tol=1e-10, maxit=2, inner_ell=2, inner_tol=1e-4, inner_maxit=50)
+    x = to_dev(b) * 0
+    st, info = c.amg_solve(h, to_dev(b), x, 1, 1e-10, 2, raise_on_nonconv=False)
+    assert info.iters == 2
+    assert rel(from_dev(x, f.shape4 + (12,)), ref) < 1e-8
+    c.amg_hierarchy_destroy(h)
+    for prec in (0, 1):
+        p = _params(c, block, 4, prec, outer_solver=2, mbicgs_tol=1e-4, mbicgs_maxit=50)
+        h = c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(li.test_vectors(dims, seed, 4))])
+        x = to_dev(b) * 0
+        st, info = c.amg_solve(h, to_dev(b), x, 1, 1e-10, 100)
+        assert info.converged == 1 and info.true_rel_residual <= 1e-10
+        r = b - op.apply(from_dev(x, f.shape4 + (12,)))
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
+        c.amg_hierarchy_destroy(h)
     f.close()

@@ -112,24 +112,12 @@ def test_training_reduces_the_loss_and_the_solve_uses_the_network():
         W2[0, a, 0, range(4), range(4), 0] = 0.5
     w = w + np.concatenate([W1.reshape(-1), W2.reshape(-1)])
     nn = c.amg_nn_create(f.d, channels, w)
-    # (residual, error) pairs from the solver: e = (1 - M D) e0, r = D e
-    losses = []
-    for step in range(30):
-        es, rs = [], []
-        for k in range(4):
-            e0 = li.rhs(dims, 100 + step * 4 + k)
-            e0d = to_dev(e0)
-            De0 = torch.empty_like(e0d)
-            c.amg_apply_D(f.d, e0d, De0, 1, c.AMG_F64)
-            Me = torch.empty_like(e0d)
-            c.amg_precondition(h, De0, Me)
-            e1 = e0d - Me
-            r1 = torch.empty_like(e1)
-            c.amg_apply_D(f.d, e1, r1, 1, c.AMG_F64)
-            es.append(e1.float())
-            rs.append(r1.float())
-        loss = c.amg_nn_train_step(nn, torch.cat(rs), torch.cat(es), 4, 1e-3)
-        losses.append(loss)
+    # (residual, error) pairs from the solver, e = (1 - M D) e0, r = D e, generated and
+    # trained on behind the C ABI: 30 Adam steps of 4 pairs
+    tp = c.amg_train_params_default()
+    tp.npairs, tp.batch, tp.lr, tp.seed = 120, 4, 1e-3, 100
+    losses = c.amg_learned_train(h, nn, tp)
+    assert len(losses) == 30
     assert np.mean(losses[-3:]) < np.mean(losses[:3])
     # what the trained network gains: the error left by one application of the
     # preconditioner, |(1 - M' D) e0| with M' = M + N (1 - D M), against the
@@ -178,5 +166,50 @@ def test_broken_network_falls_back_to_plain_amg():
     assert info.nn_fallback == 1 and info.converged == 1 and info.true_rel_residual <= 1e-10
     c.amg_hierarchy_set_nn(h, None)
     c.amg_nn_destroy(nn)
+    c.amg_hierarchy_destroy(h)
+    f.close()
+
+
+def test_learned_train_equals_the_step_by_step_api():
+    # amg_learned_train does exactly what the caller could do with the other entry points:
+    # e0 = field k of stream (seed, AMG_RNG_STREAM_NN), e = e0 - M D e0, r = D e in FP64,
+    # rounded to FP32, one amg_nn_train_step per batch
+    import torch
+    dims = (4, 4, 4, 4)
+    f = Field(dims, 0.6, 5, 0.130, 1.0)
+    c = f.c
+    p = c.amg_params_default()
+    for mu in range(4):
+        p.block[0][mu] = 2
+    p.nvec[0] = 8
+    p.n_init, p.n_adapt = 1, 1
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 5, 8))])
+    w = _weights([1, 2, 1], 3, 0.05)
+    nn1 = c.amg_nn_create(f.d, [1, 2, 1], w)
+    nn2 = c.amg_nn_create(f.d, [1, 2, 1], w)
+    tp = c.amg_train_params_default()
+    tp.npairs, tp.batch, tp.lr, tp.seed = 6, 3, 1e-2, 77
+    l1 = c.amg_learned_train(h, nn1, tp)
+    n = f.V * 12
+    l2 = []
+    for st in range(2):
+        rs, es = [], []
+        for q in range(3):
+            e0 = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+            c.amg_random_normal(77, 6, (st * 3 + q) * n, n, e0)
+            De0, Me, r1 = torch.empty_like(e0), torch.empty_like(e0), torch.empty_like(e0)
+            c.amg_apply_D(f.d, e0, De0, 1, c.AMG_F64)
+            c.amg_precondition(h, De0, Me)
+            e1 = e0 - Me
+            c.amg_apply_D(f.d, e1, r1, 1, c.AMG_F64)
+            es.append(e1.float())
+            rs.append(r1.float())
+        l2.append(c.amg_nn_train_step(nn2, torch.cat(rs), torch.cat(es), 3, 1e-2))
+    assert np.allclose(l1, l2, rtol=1e-12, atol=0)
+    w1 = c.amg_nn_get_weights(nn1, [1, 2, 1], effective=False)
+    w2 = c.amg_nn_get_weights(nn2, [1, 2, 1], effective=False)
+    assert np.array_equal(w1, w2)
+    for nn in (nn1, nn2):
+        c.amg_nn_destroy(nn)
     c.amg_hierarchy_destroy(h)
     f.close()

@@ -169,3 +169,34 @@ def test_three_level_solve():
     assert h.nlevels == 3
     x, info = h.solve(b, 1e-10)
     assert info.converged and info.true_rel_residual <= 1e-10
+
+
+def test_mbicgs_exact_inner_solve_converges_in_one_step():
+    # an inner BiCGStab(2) run to 1e-14 makes the preconditioner A^{-1}: the flexible
+    # BiCGStab then takes one iteration to the exact solution
+    A, b = _rand_system(90, 6)
+    x, info = solvers.mbicgs(lambda v: A @ v, b, tol=1e-11, inner_tol=1e-14, inner_maxit=400)
+    assert info.converged and info.iters == 1
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_mbicgs_inner_solve_is_the_coarse_algorithm():
+    # the preconditioner applied to v is exactly bicgstab_l(A, v) with the inner settings:
+    # one outer iteration of mbicgs equals fbicgstab with that map (a pin of the wiring,
+    # against the pinned BiCGStab(l) and flexible BiCGStab)
+    A, b = _rand_system(70, 8)
+    M = lambda v: solvers.bicgstab_l(lambda u: A @ u, v, ell=2, tol=1e-3, maxit=20)[0]
+    x1, _ = solvers.mbicgs(lambda v: A @ v, b, tol=0.0, maxit=1, inner_ell=2, inner_tol=1e-3, inner_maxit=20)
+    x2, _ = solvers.fbicgstab(lambda v: A @ v, b, M, tol=0.0, maxit=1)
+    assert np.array_equal(x1, x2)
+
+
+def test_mbicgs_wilson_clover_matches_dense_lu():
+    dims = (4, 4, 4, 4)
+    U = li.gauge_field(dims, 0.3, 1)
+    op = dirac.WilsonClover(U, 0.124, 1.0)
+    b = li.rhs(dims, 1).reshape(op.shape4 + (12,))
+    x, info = solvers.mbicgs(op.apply, b, tol=1e-10, inner_tol=1e-4, inner_maxit=50)
+    assert info.converged and info.true_rel_residual <= 1e-10
+    xd = np.linalg.solve(dirac.dense_matrix(U, 0.124, 1.0), b.reshape(-1))
+    assert np.linalg.norm(x.reshape(-1) - xd) <= 1e-9 * np.linalg.norm(xd)
