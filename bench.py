@@ -155,7 +155,7 @@ def make_params(capi, prec_smoother, coarse="f32", outer="fgmres", sap_variant=-
     p = capi.amg_params_default()
     if vec == "f16":
         p.prec_vectors = capi.AMG_F16
-    p.outer_solver = 1 if outer == "fbicgstab" else 0
+    p.outer_solver = {"fgmres": 0, "fbicgstab": 1, "mbicgs": 2}[outer]
     p.sap_variant = sap_variant
     for k, v in (setup or {}).items():
         if v is not None:
@@ -326,6 +326,9 @@ def run_headline(args):
     gen_s = time.perf_counter() - t0
     p = make_params(capi, capi.AMG_F32, vec="f16", w=w, sap_variant=args.sap_variant)
     p.outer_m = w["outer_m"]
+    p.sap_eo = 1 if args.sap_eo else 0
+    if args.mr is not None:
+        p.mr_iters = args.mr
     t0 = time.perf_counter()
     h = capi.amg_setup(d, p, [init])
     torch.cuda.synchronize()
@@ -390,7 +393,15 @@ def run_headline(args):
     peak, sms, mhz = _fp32_fma_peak(torch)
     cycles = float(np.mean([i["cycles"] for i in infos]))
     smooth_ms = float(np.mean([i["ms_smoother"] for i in infos]))
-    flop_site = 1872 + 24 + p.mr_iters * (1494 + 336)
+    if p.sap_eo:
+        # even-odd domain solves: residual (1872 + 24), the Schur right-hand side and the odd
+        # reconstruction (each in-domain hops + one clover (inverse) on one site of a pair:
+        # 1494 per pair = 747 per site, twice), and per minimal-residual step the four
+        # parity blocks (hops and clover (inverse) on both sites of a pair, 2988) plus the
+        # dots and updates on the even site (336): 1578 per site
+        flop_site = 1872 + 24 + 2 * 747 + p.mr_iters * 1578
+    else:
+        flop_site = 1872 + 24 + p.mr_iters * (1494 + 336)
     flop_step = flop_site * (V / 2) * 2 * p.sap_iters * cycles * ns
     sap_tflops = flop_step / (smooth_ms * 1e-3) / 1e12
     hbm, kind = _peaks()
@@ -417,7 +428,8 @@ def run_headline(args):
         "metric": METRIC, "value": per_rhs, "unit": "ms/RHS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f16+f64", "data": "synthetic", "config": config,
-        "roofline": {"kernel": "sap_half_kernel<P32,256> (fused SAP half sweep)", "bound": "alu",
+        "roofline": {"kernel": ("sap_half_eo_kernel<P32> (fused SAP half sweep, even-odd domain solves)"
+                               if p.sap_eo else "sap_half_kernel<P32,256> (fused SAP half sweep)"), "bound": "alu",
                      "achieved": sap_tflops, "peak": peak, "unit": "TFLOP/s", "frac": sap_tflops / peak,
                      "traffic": None,
                      "peak_kind": f"FP32 FMA from unit counts: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
@@ -982,6 +994,12 @@ def run_solve16(args):
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
+    if args.outer == "mbicgs":
+        # no SAP in this solve: the smoother timer holds the inner BiCGStab(2) on D
+        line.pop("roofline")
+        line["config"]["workload"] = line["config"]["workload"].replace(
+            "2-level AMG 4^4 blocks, 24 test vectors, SAP(4) x MR(6), BiCGStab(2) coarse to 1e-2, FGMRES(16) FP64 outer",
+            "MBiCGs: flexible BiCGStab FP64 outer preconditioned by FP32 BiCGStab(2) on D to 1e-4 (no multigrid)")
     capi.amg_hierarchy_destroy(h)
     capi.amg_dirac_destroy(d)
     capi.amg_gauge_destroy(g)
@@ -1005,6 +1023,9 @@ def main():
     ap.add_argument("--workload", default="propagator",
                     choices=["propagator", "solve16", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--sap-eo", action="store_true",
+                    help="propagator: even-odd (Schur complement) SAP domain solves")
+    ap.add_argument("--mr", type=int, default=None, help="propagator: minimal-residual steps per domain solve")
     ap.add_argument("--dims", default=None,
                     help="propagator workload on a smaller lattice Lx,Ly,Lz,Lt (profiling; not the headline)")
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -1013,8 +1034,9 @@ def main():
     ap.add_argument("--n-init", type=int, default=None, help="setup (0-a) SAP applications (default: library's)")
     ap.add_argument("--n-adapt", type=int, default=None, help="setup (0-b) adaptive passes (default: library's)")
     ap.add_argument("--coarse-tol", type=float, default=None, help="coarsest solve tolerance (default: library's)")
-    ap.add_argument("--outer", default="fgmres", choices=["fgmres", "fbicgstab"],
-                    help="outer solver of the solve16 workload (fbicgstab: the paper's flexible BiCGStab)")
+    ap.add_argument("--outer", default="fgmres", choices=["fgmres", "fbicgstab", "mbicgs"],
+                    help="outer solver of the solve16 workload (fbicgstab: the paper's flexible BiCGStab; "
+                         "mbicgs: the paper's mixed-precision BiCGStab comparison solver, no multigrid)")
     ap.add_argument("--vec-prec", default="f16", choices=["f32", "f16"],
                     help="solve16: test vectors as restriction and prolongation read them (f16: half storage "
                          "with a per-site scale, FP32 arithmetic; f32: the setup's precision)")

@@ -115,6 +115,14 @@ typedef struct {
                                            needs an FP32 or FP16 smoother [AMG_F32] */
     double mbicgs_tol;                  /* MBiCGs inner solve: relative residual [1e-4] */
     int mbicgs_maxit;                   /* MBiCGs inner solve: BiCGStab(l) cycles [50] */
+    int sap_eo;                         /* 1: the fine-level SAP domain solves in even-odd (Schur
+                                           complement) form -- mr_iters minimal-residual steps on
+                                           S = A_ee - H_eo A_oo^{-1} H_oe over the even sites of the
+                                           domain, then z_o = A_oo^{-1}(r_o - H_oe z_e) exactly (H the
+                                           in-domain hops, A = 1 + F); needs an even block extent in
+                                           x; the clover inverse is built once per operator and
+                                           precision.  Not in the paper (an addition beside the SAP
+                                           listing of Sec. 3).  0: the paper's MR on D_SAP [0] */
 } amg_params;
 
 typedef struct {
@@ -224,8 +232,11 @@ amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_pr
  * the library allocates on first use; this variant keeps those two fields in
  * one static device array of 24 MiB (12 MiB each) that every GPU loading the
  * library holds until exit.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) once for that device; make that first
- * call before any stream capture.  Every call shares the array, so calls that
+ * device address (cudaGetSymbolAddress) once for that device and keeps it for
+ * the life of the process; make that first call before any stream capture.
+ * Resetting the device (cudaDeviceReset) or otherwise recreating its primary
+ * context after that first call is not supported: the array may then live at
+ * another address.  Every call shares the array, so calls that
  * overlap on the GPU (different streams, or host threads) race: serialise
  * them.  nrhs * fine_field_bytes(prec) must be <= 12 MiB, where a field is
  * 192 (AMG_F64), 96 (AMG_F32) or 52 (AMG_F16) bytes per site; larger calls

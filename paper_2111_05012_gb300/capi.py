@@ -52,6 +52,7 @@ class amg_params(ctypes.Structure):
         ("prec_vectors", ctypes.c_int),
         ("mbicgs_tol", ctypes.c_double),
         ("mbicgs_maxit", ctypes.c_int),
+        ("sap_eo", ctypes.c_int),
     ]
 
 

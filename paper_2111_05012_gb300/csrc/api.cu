@@ -57,6 +57,7 @@ struct amg_dirac {
     amg_gauge* gauge;
     double kappa, csw;
     DevBuf C[4];
+    DevBuf Ci[3];    // clover inverse A^{-1} by precision (F64, F32, F16), built when an even-odd smoother needs it
     DevBuf in, out;   // call scratch for the canonical-layout entry points
 };
 
@@ -77,6 +78,7 @@ struct CoarseLevel {
     // vectors (coarsening to the next level) and its FGMRES(inter_m) space
     DevBuf cvecs;
     DevBuf cvecs_next;          // (0-b): the pass's new vectors while M still reads cvecs
+    int xgroup = 0;             // coarsest solver's shared-memory tile (coarse sites per gather), tuned
     std::vector<DevBuf> gV, gZ;
     DevBuf gw, gr, gt;
     int kprec() const { return opbf ? 2 : op32 ? 3 : prec; }   // precision code of the stencil kernels
@@ -193,6 +195,7 @@ struct amg_hierarchy {
     DevBuf vecs0;
     DevBuf vecs16;   // half-precision copy of vecs0 for restriction / prolongation (rp == 2)
     DevBuf vecs_next;   // (0-b): the pass's new vectors while the cycle still reads vecs0 (rp != 2)
+    DevBuf tmpg;        // setup: smoothed / cycled outputs of a group of test vectors
     std::vector<CoarseLevel> lev;   // lev[l] for l = 1..nlevels-1 (lev[0] unused)
     // fine workspaces per precision: b, x
     DevBuf fb[3], fx[3];
@@ -294,6 +297,13 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
     if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
     if (p->outer_solver < 0 || p->outer_solver > 2) return fail(AMG_EINVAL, "outer_solver must be 0, 1 or 2");
+    if (p->sap_eo != 0 && p->sap_eo != 1) return fail(AMG_EINVAL, "sap_eo must be 0 or 1");
+    if (p->sap_eo) {
+        BlockH b0;
+        for (int mu = 0; mu < 4; ++mu) b0.b[mu] = p->block[0][mu];
+        if (!sap_eo_supported(b0))
+            return fail(AMG_EINVAL, "even-odd SAP needs an even block extent in x and at most 512 sites per block");
+    }
     if (p->outer_solver == 2 && p->prec_smoother == AMG_F16)
         return fail(AMG_EINVAL, "MBiCGs (outer_solver 2) runs its inner BiCGStab in FP32 or FP64");
     if (p->outer_solver == 2 && (!(p->mbicgs_tol > 0) || p->mbicgs_maxit < 1))
@@ -322,10 +332,15 @@ amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_z
     const int var = nb > 1 ? h->sap_variant_nb[prec] : h->sap_variant[prec];
     for (int i = 0; i < h->p.sap_iters; ++i) {
         const bool first = x_zero && i == 0;
-        CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], 0, h->p.mr_iters, first ? 1 : 0,
-                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, nb, s));
-        CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], 1, h->p.mr_iters, first ? 2 : 0,
-                                   d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, nb, s));
+        for (int colour = 0; colour < 2; ++colour) {
+            const int x_mode = first ? (colour == 0 ? 1 : 2) : 0;
+            if (h->p.sap_eo)
+                CK(launch_sap_half_eo(prec, fine_geom(h), h->blk[0], colour, h->p.mr_iters, x_mode,
+                                      d->gauge->U[prec].p, d->C[prec].p, d->Ci[prec].p, b, x, d->kappa, nb, s));
+            else
+                CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], colour, h->p.mr_iters, x_mode,
+                                           d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, nb, s));
+        }
     }
     if (h->p.sap_iters == 0 && x_zero) CK(cudaMemsetAsync(x, 0, fsz(h, prec) * nb, s));
     h->timer.stop(s);
@@ -356,7 +371,7 @@ amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int 
         CK(cudaMemsetAsync(L.cs_state.p, 0, 12, s));
         CK(launch_coarse_bicgstab(L.kprec(), L.g, L.nc, L.op(), (const char*)b + q * cv, (char*)x + q * cv, w[2]->p, R,
                                   U, ell, h->p.coarse_tol, h->p.coarse_maxit, L.cs_part.p, L.cs_state.p,
-                                  h->graph_mode ? 8 : 0, s, ng));
+                                  h->graph_mode ? 8 : 0, s, ng, L.xgroup));
         // error word of this launch (a later one would overwrite it): fold into word 2 of the host mirror
         CK(cudaMemcpyAsync(h->hstate + 4 * (k % 16), L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
     }
@@ -985,6 +1000,28 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
 
 // ---------------------------------------------------------------- setup pieces
 // (Re)size the batch-dependent workspaces for nb right-hand sides.
+// the coarse levels' solver fields for a batch of nb right-hand sides: [0] bc and [1] xc hold
+// the batch, the coarsest solver's rt, R_j, U_j one lockstep group
+constexpr int kSetupGroup = 4;   // test vectors per batched smoother / cycle call of the setup
+
+amg_status alloc_coarse_workspaces(amg_hierarchy* h, int nb) {
+    h->cw.resize(h->p.nlevels);
+    for (int l = 1; l < h->p.nlevels; ++l) {
+        CoarseLevel& L = h->lev[l];
+        CK(L.cs_part.ensure(coarse_solver_partial_bytes()));
+        if (!L.cs_state.p) {
+            CK(L.cs_state.ensure(coarse_solver_state_bytes()));
+            CK(cudaMemset(L.cs_state.p, 0, coarse_solver_state_bytes()));
+        }
+        size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
+        int nv = 4 + 2 * (h->p.coarse_ell + 1);
+        const int ng = l == h->p.nlevels - 1 ? std::min(nb, coarse_solver_max_rhs()) : 1;
+        while ((int)h->cw[l].size() < nv) h->cw[l].push_back(new DevBuf());
+        for (int k = 0; k < nv; ++k) CK(h->cw[l][k]->ensure(bytes * (k < 2 ? nb : ng)));
+    }
+    return AMG_OK;
+}
+
 amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
     const GeomH& g = fine_geom(h);
     if (nb > h->nb_cap) h->clear_graphs();   // buffers may move: captured graphs would be stale
@@ -1007,21 +1044,7 @@ amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
         CK(cudaMallocHost(&h->hstate, 16 * 16));
         std::memset(h->hstate, 0, 16 * 16);
     }
-    h->cw.resize(h->p.nlevels);
-    for (int l = 1; l < h->p.nlevels; ++l) {
-        CoarseLevel& L = h->lev[l];
-        CK(L.cs_part.ensure(coarse_solver_partial_bytes()));
-        if (!L.cs_state.p) {
-            CK(L.cs_state.ensure(coarse_solver_state_bytes()));
-            CK(cudaMemset(L.cs_state.p, 0, coarse_solver_state_bytes()));
-        }
-        size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
-        int nv = 4 + 2 * (h->p.coarse_ell + 1);
-        // [0] bc and [1] xc hold the batch; the solver's rt, R_j, U_j one lockstep group
-        const int ng = l == h->p.nlevels - 1 ? std::min(nb, coarse_solver_max_rhs()) : 1;
-        while ((int)h->cw[l].size() < nv) h->cw[l].push_back(new DevBuf());
-        for (int k = 0; k < nv; ++k) CK(h->cw[l][k]->ensure(bytes * (k < 2 ? nb : ng)));
-    }
+    TRY(alloc_coarse_workspaces(h, nb));
     for (int l = 1; l + 1 < h->p.nlevels; ++l) {
         CoarseLevel& L = h->lev[l];
         const size_t bytes = coarse_n(L) * coarse_elem_bytes(L.prec);
@@ -1277,6 +1300,104 @@ amg_status tune_kernels(amg_hierarchy* h) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
+    // launch shape of the stencil (threads per CTA x grid cap) for the precisions the solve
+    // applies D in: the smoother's (relaxed products) and FP64 (true residual)
+    {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int pr : {h->fp, 0}) {
+            const int cand[][2] = {{256, 16}, {128, 16}, {256, 4}, {256, 64}, {128, 8}, {128, 64}};
+            float best = 1e30f;
+            int bt = 256, bs = 16;
+            for (const auto& c : cand) {
+                dirac_set_shape(pr, c[0], c[1]);
+                std::vector<float> t;
+                for (int rep = 0; rep < 4; ++rep) {
+                    CK(cudaEventRecord(e0, 0));
+                    CK(launch_dirac(pr, g, nullptr, d->gauge->U[pr].p, d->C[pr].p, h->fx[pr].p, h->fb[pr].p, nullptr,
+                                    d->kappa, 1, 0));
+                    CK(cudaEventRecord(e1, 0));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep > 0) t.push_back(ms);
+                }
+                std::sort(t.begin(), t.end());
+                if (t[t.size() / 2] < best) {
+                    best = t[t.size() / 2];
+                    bt = c[0];
+                    bs = c[1];
+                }
+            }
+            dirac_set_shape(pr, bt, bs);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    return AMG_OK;
+}
+
+// Autotuner, second part (once the coarsest operator exists): the shared-memory tile of the
+// coarsest solver -- coarse sites whose neighbour blocks are gathered per step -- timed over
+// two BiCGStab(l) cycles (tolerance 0) on a fixed nonzero right-hand side per candidate.
+amg_status tune_coarse_tile(amg_hierarchy* h) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    // shared-memory tile of the coarsest solver: two BiCGStab(l) cycles (tolerance 0) on
+    // a fixed nonzero right-hand side for each candidate
+    const int lc = h->p.nlevels - 1;
+    CoarseLevel& L = h->lev[lc];
+    auto& w = h->cw[lc];
+    const int ell = h->p.coarse_ell;
+    void* R[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* Uv[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int j = 0; j <= ell; ++j) {
+        R[j] = w[3 + j]->p;
+        Uv[j] = w[4 + ell + j]->p;
+    }
+    CK(cudaMemset(w[0]->p, 0x3c, coarse_n(L) * coarse_elem_bytes(L.prec)));
+    const int xmax = coarse_solver_max_xgroup(L.kprec(), L.nc, 1);
+    std::vector<int> xs = {0};
+    for (int xg : {xmax / 2, 4, 2, 1})
+        if (xg >= 1 && xg < xmax && std::find(xs.begin(), xs.end(), xg) == xs.end()) xs.push_back(xg);
+    float best = 1e30f;
+    int bx = 0;
+    for (int xg : xs) {
+        std::vector<float> t;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaMemset(L.cs_state.p, 0, 12));
+            CK(cudaEventRecord(e0, 0));
+            CK(launch_coarse_bicgstab(L.kprec(), L.g, L.nc, L.op(), w[0]->p, w[1]->p, w[2]->p, R, Uv, ell, 0.0, 2,
+                                      L.cs_part.p, L.cs_state.p, 0, 0, 1, xg));
+            CK(cudaEventRecord(e1, 0));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        if (t[t.size() / 2] < best) {
+            best = t[t.size() / 2];
+            bx = xg;
+        }
+    }
+    L.xgroup = bx;
+    CK(cudaMemset(L.cs_state.p, 0, 16));
+
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return AMG_OK;
+}
+
+// A^{-1} of precision prec on the operator (FP64 inversion, once per precision)
+amg_status ensure_clover_inverse(amg_dirac* d, int prec) {
+    if (d->Ci[prec].p) return AMG_OK;
+    const GeomH& g = d->gauge->lat->g;
+    CK(d->Ci[prec].ensure(fine_clover_bytes(prec, g.V)));
+    CK(launch_clover_invert(prec, g, d->C[0].p, d->Ci[prec].p, 0));
+    CK(cudaStreamSynchronize(0));
     return AMG_OK;
 }
 
@@ -1291,6 +1412,7 @@ amg_status hierarchy_init(amg_dirac* d, const amg_params* p, amg_hierarchy** out
     h->rp = p->prec_vectors == AMG_F16 ? 2 : h->vp;
     *hp = h;
     amg_status st = build_levels(h);
+    if (st == AMG_OK && p->sap_eo) st = ensure_clover_inverse(d, h->fp);
     if (st == AMG_OK) st = alloc_workspaces(h, 1);
     if (st == AMG_OK) st = tune_kernels(h);
     if (st != AMG_OK) {
@@ -1684,6 +1806,7 @@ void amg_params_default(amg_params* p) {
     p->prec_vectors = AMG_F32;
     p->mbicgs_tol = 1e-4;
     p->mbicgs_maxit = 50;
+    p->sap_eo = 0;
 }
 
 
@@ -1890,6 +2013,7 @@ amg_status amg_setup_from_vectors(amg_dirac* d, const amg_params* p, const doubl
         if (st == AMG_OK) st = ortho_galerkin_c(h, l, s);
     }
     if (st == AMG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(AMG_ECUDA, "setup failed");
+    if (st == AMG_OK) st = tune_coarse_tile(h);
     if (st != AMG_OK) {
         delete h;
         return st;
@@ -1908,12 +2032,18 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
         const GeomH& g = fine_geom(h);
         const int vp = h->vp;
         const size_t vb = fine_spinor_bytes(vp, g.V);
+        // the test vectors go through the smoother and the cycle kSetupGroup at a time (the
+        // batched kernels give each vector exactly what a call of its own gives)
+        const int nv = h->p.nvec[0];
+        const int G = std::min(nv, kSetupGroup);
+        CK(h->tmpg.ensure(vb * G));
         // (0-a): v <- SAP(v), normalised
         for (int k = 0; k < h->p.n_init; ++k) {
-            for (int i = 0; i < h->p.nvec[0]; ++i) {
-                void* vi = (char*)h->vecs0.p + i * vb;
-                TRY(fine_sap(h, vp, vi, h->tmpv.p, true, 1, s));
-                TRY(normalise_into(h, vp, h->tmpv.p, vi, s));
+            for (int i = 0; i < nv; i += G) {
+                const int ng = std::min(G, nv - i);
+                TRY(fine_sap(h, vp, (char*)h->vecs0.p + i * vb, h->tmpg.p, true, ng, s));
+                for (int q = 0; q < ng; ++q)
+                    TRY(normalise_into(h, vp, (char*)h->tmpg.p + q * vb, (char*)h->vecs0.p + (i + q) * vb, s));
             }
         }
         TRY(orthonormalise_and_galerkin(h, s));
@@ -1924,18 +2054,24 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
         // half-precision transfer vectors (vecs16, rewritten only by the rebuild) they can
         // overwrite vecs0 in place
         const bool apart = h->rp != 2;
-        if (apart && h->p.n_adapt > 0) CK(h->vecs_next.ensure(vb * h->p.nvec[0]));
+        if (apart && h->p.n_adapt > 0) CK(h->vecs_next.ensure(vb * nv));
+        if (h->p.n_adapt > 0) TRY(alloc_coarse_workspaces(h, G));
         for (int k = 0; k < h->p.n_adapt; ++k) {
-            for (int i = 0; i < h->p.nvec[0]; ++i) {
-                void* vi = (char*)h->vecs0.p + i * vb;
-                TRY(vcycle0(h, vp, vi, h->tmpv.p, 1, s));
-                TRY(normalise_into(h, vp, h->tmpv.p, apart ? (char*)h->vecs_next.p + i * vb : vi, s));
+            for (int i = 0; i < nv; i += G) {
+                const int ng = std::min(G, nv - i);
+                TRY(vcycle0(h, vp, (char*)h->vecs0.p + i * vb, h->tmpg.p, ng, s));
+                for (int q = 0; q < ng; ++q) {
+                    void* dst = (char*)(apart ? h->vecs_next.p : h->vecs0.p) + (i + q) * vb;
+                    TRY(normalise_into(h, vp, (char*)h->tmpg.p + q * vb, dst, s));
+                }
             }
             if (apart) h->vecs0.swap(h->vecs_next);
             TRY(orthonormalise_and_galerkin(h, s));
             TRY(refresh_c(h, 1, s));
         }
         h->vecs_next.release();
+        h->tmpg.release();
+        TRY(tune_coarse_tile(h));
         CK(cudaStreamSynchronize(s));
         return AMG_OK;
     };

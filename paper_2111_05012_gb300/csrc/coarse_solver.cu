@@ -649,6 +649,11 @@ template <int NB> const void* solver_fn(int cprec) {
 }  // namespace
 
 int coarse_solver_max_rhs() { return kMaxNB; }
+int coarse_solver_max_xgroup(int cprec, int nc, int nb) {
+    const int NB = nb <= 1 ? 1 : nb == 2 ? 2 : 4;
+    const int eb = (cprec == 0 || cprec == 3) ? 16 : 8;
+    return kXBytes / (9 * nc * eb * NB);
+}
 
 size_t coarse_solver_state_bytes() { return sizeof(GridBar) + 64; }
 size_t coarse_solver_partial_bytes() {
@@ -661,7 +666,7 @@ size_t coarse_solver_partial_bytes() {
 
 cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
                                    void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
-                                   void* part, void* state, int cluster, cudaStream_t s, int nb) {
+                                   void* part, void* state, int cluster, cudaStream_t s, int nb, int xgroup) {
     if (ell < 1 || ell > kMaxEll) return cudaErrorInvalidValue;
     if (nb < 1 || nb > kMaxNB) return cudaErrorInvalidValue;
     const int NB = nb == 1 ? 1 : nb == 2 ? 2 : 4;   // compiled batch widths
@@ -692,6 +697,7 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     if (a.row_bytes % 16 != 0) return cudaErrorInvalidValue;   // rows are read in 16-byte words
     const int block_bytes = 9 * nc * eb;                                  // one site's neighbour blocks
     a.xgroup = kXBytes / (block_bytes * NB);
+    if (xgroup > 0 && xgroup < a.xgroup) a.xgroup = xgroup;
     if (a.xgroup < 1) return cudaErrorInvalidValue;
     const void* fn = NB == 1 ? solver_fn<1>(cprec) : NB == 2 ? solver_fn<2>(cprec) : solver_fn<4>(cprec);
     const int smem = a.xgroup * (NB * block_bytes + 9 * (int)sizeof(int));

@@ -283,12 +283,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) coarse_tc_kernel(TcArgs a, TcPl
             if (pendA[s2]) mb_wait(&barA[s2], phA[s2]);
             if (pendB[s2]) mb_wait(&barB[s2], phB[s2]);
         }
+        // a timed-out wait for the MMAs (fail 2) left them possibly still writing the
+        // accumulator: wait for their commit once more (phM was flipped after the failed
+        // wait); if that also gives up, the accumulator is not released (fail 3)
+        if (*fail == 2 && !mb_wait(barM, phM ^ 1)) *fail = 3;
         atomicExch(a.err, 1);
     }
     tc_before();
     __syncthreads();
     tc_after();
-    if (warp == 0) tm_dealloc(tmem, 32);
+    if (warp == 0 && *fail != 3) tm_dealloc(tmem, 32);
 }
 
 // operator image: row m = 32 w + l holds Re (l < 16) or Im (l >= 16) of

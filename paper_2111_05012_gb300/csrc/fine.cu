@@ -33,7 +33,7 @@ Blocking make_blocking(const GeomH& g, const BlockH& b) {
     return k;
 }
 
-int grid_for(int n, int threads) {
+int device_sms() {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -41,6 +41,10 @@ int grid_for(int n, int threads) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
+    return sms;
+}
+int grid_for(int n, int threads) {
+    const int sms = device_sms();
     int g = (n + threads - 1) / threads;
     int cap = sms * 16;
     return g < cap ? (g > 0 ? g : 1) : cap;
@@ -156,6 +160,41 @@ DEV void path4(const M3 a, const M3 b, const M3 c, const M3 d, M3 out) {
     m3_mul(t2, d, out);
 }
 
+// store the packed clover of one site (per chirality block: 6 real diagonal entries, then the
+// 15 lower-triangle entries as (re, im) pairs) in the layout of precision P
+template <class P>
+DEV void clover_store(const double (&pr)[2][36], void* out, int V, int s) {
+    if (P::id == 0) {
+        double2* p = (double2*)out;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 18; ++q) p[(size_t)(18 * b + q) * V + s] = make_double2(pr[b][2 * q], pr[b][2 * q + 1]);
+    } else if (P::id == 3) {
+        float4* p = (float4*)out;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 18; ++q) {
+                dfloat v0 = split_double(pr[b][2 * q]), v1 = split_double(pr[b][2 * q + 1]);
+                p[(size_t)(18 * b + q) * V + s] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+            }
+    } else if (P::id == 1) {
+        float4* p = (float4*)out;
+        for (int b = 0; b < 2; ++b)
+            for (int q = 0; q < 9; ++q)
+                p[(size_t)(9 * b + q) * V + s] = make_float4((float)pr[b][4 * q], (float)pr[b][4 * q + 1],
+                                                               (float)pr[b][4 * q + 2], (float)pr[b][4 * q + 3]);
+    } else {
+        uint4* p = (uint4*)out;
+        for (int q = 0; q < 9; ++q) {
+            uint4 t;
+            __half2* h = reinterpret_cast<__half2*>(&t);
+            for (int w = 0; w < 4; ++w) {
+                int hidx = 8 * q + 2 * w;   // halves hidx, hidx+1 of the 72
+                h[w] = __floats2half2_rn((float)pr[hidx / 36][hidx % 36], (float)pr[(hidx + 1) / 36][(hidx + 1) % 36]);
+            }
+            p[(size_t)q * V + s] = t;
+        }
+    }
+}
+
 template <class P>
 __global__ void clover_build_kernel(Geom g, const void* U64, double kappa, double csw, void* out) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
@@ -242,35 +281,7 @@ __global__ void clover_build_kernel(Geom g, const void* U64, double kappa, doubl
                     pr[b][2 * q + 1] = A[b][i][j].im;
                 }
         }
-        if (P::id == 0) {
-            double2* p = (double2*)out;
-            for (int b = 0; b < 2; ++b)
-                for (int q = 0; q < 18; ++q) p[(size_t)(18 * b + q) * g.V + s] = make_double2(pr[b][2 * q], pr[b][2 * q + 1]);
-        } else if (P::id == 3) {
-            float4* p = (float4*)out;
-            for (int b = 0; b < 2; ++b)
-                for (int q = 0; q < 18; ++q) {
-                    dfloat v0 = split_double(pr[b][2 * q]), v1 = split_double(pr[b][2 * q + 1]);
-                    p[(size_t)(18 * b + q) * g.V + s] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
-                }
-        } else if (P::id == 1) {
-            float4* p = (float4*)out;
-            for (int b = 0; b < 2; ++b)
-                for (int q = 0; q < 9; ++q)
-                    p[(size_t)(9 * b + q) * g.V + s] = make_float4((float)pr[b][4 * q], (float)pr[b][4 * q + 1],
-                                                                   (float)pr[b][4 * q + 2], (float)pr[b][4 * q + 3]);
-        } else {
-            uint4* p = (uint4*)out;
-            for (int q = 0; q < 9; ++q) {
-                uint4 t;
-                __half2* h = reinterpret_cast<__half2*>(&t);
-                for (int w = 0; w < 4; ++w) {
-                    int hidx = 8 * q + 2 * w;   // halves hidx, hidx+1 of the 72
-                    h[w] = __floats2half2_rn((float)pr[hidx / 36][hidx % 36], (float)pr[(hidx + 1) / 36][(hidx + 1) % 36]);
-                }
-                p[(size_t)q * g.V + s] = t;
-            }
-        }
+        clover_store<P>(pr, out, g.V, s);
     }
 }
 
@@ -579,6 +590,77 @@ template <> struct DomainVec<double> {
     }
 };
 
+// A^{-1} per site from the FP64 clover (A = 1 + F: two Hermitian 6x6 blocks, each inverted
+// by Gauss-Jordan elimination with partial pivoting in FP64; the inverse is Hermitian and is
+// stored in the clover's packed form, from the mean of its lower and conjugated upper triangle)
+template <class P>
+__global__ void clover_invert_kernel(Geom g, const void* C64, void* out) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        double pr[2][36];
+        const double2* src = (const double2*)C64;
+        for (int b = 0; b < 2; ++b) {
+            for (int q = 0; q < 18; ++q) {
+                double2 t = src[(size_t)(18 * b + q) * g.V + s];
+                pr[b][2 * q] = t.x;
+                pr[b][2 * q + 1] = t.y;
+            }
+            cx<double> M[6][6], R[6][6];
+            for (int i = 0; i < 6; ++i) {
+                M[i][i] = {pr[b][i], 0.0};
+                for (int j = 0; j < i; ++j) {
+                    const int q = 3 + i * (i - 1) / 2 + j;
+                    M[i][j] = {pr[b][2 * q], pr[b][2 * q + 1]};
+                    M[j][i] = conj(M[i][j]);
+                }
+                for (int j = 0; j < 6; ++j) R[i][j] = {i == j ? 1.0 : 0.0, 0.0};
+            }
+            for (int c = 0; c < 6; ++c) {
+                int piv = c;
+                double best = norm2(M[c][c]);
+                for (int i = c + 1; i < 6; ++i)
+                    if (norm2(M[i][c]) > best) {
+                        best = norm2(M[i][c]);
+                        piv = i;
+                    }
+                if (piv != c)
+                    for (int j = 0; j < 6; ++j) {
+                        cx<double> t = M[c][j];
+                        M[c][j] = M[piv][j];
+                        M[piv][j] = t;
+                        t = R[c][j];
+                        R[c][j] = R[piv][j];
+                        R[piv][j] = t;
+                    }
+                const cx<double> d = M[c][c];
+                const double dn = norm2(d);
+                const cx<double> inv = {d.re / dn, -d.im / dn};
+                for (int j = 0; j < 6; ++j) {
+                    M[c][j] = inv * M[c][j];
+                    R[c][j] = inv * R[c][j];
+                }
+                for (int i = 0; i < 6; ++i) {
+                    if (i == c) continue;
+                    const cx<double> f = M[i][c];
+                    for (int j = 0; j < 6; ++j) {
+                        M[i][j] = M[i][j] - f * M[c][j];
+                        R[i][j] = R[i][j] - f * R[c][j];
+                    }
+                }
+            }
+            for (int i = 0; i < 6; ++i) {
+                pr[b][i] = R[i][i].re;
+                for (int j = 0; j < i; ++j) {
+                    const int q = 3 + i * (i - 1) / 2 + j;
+                    const cx<double> h = 0.5 * (R[i][j] + conj(R[j][i]));
+                    pr[b][2 * q] = h.re;
+                    pr[b][2 * q + 1] = h.im;
+                }
+            }
+        }
+        clover_store<P>(pr, out, g.V, s);
+    }
+}
+
 // ------------------------------------------------------------ SAP half sweep
 // One CTA per domain of the given colour, one thread per site of the domain.
 // Computes r = b - D x on the domain (the residual of the SAP listing, needed
@@ -600,7 +682,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int vbp = blockDim.x;
     cx<T>* rsh = reinterpret_cast<cx<T>*>(smem_raw);          // [12][vbp]
-    T* red = reinterpret_cast<T*>(rsh + 12 * vbp);             // [3][32]
+    T* red = reinterpret_cast<T*>(rsh + 12 * vbp);             // [2][3][32]
 
     // domain of this CTA: the k-th domain of the given colour; right-hand side r of a batch.
     // rhs_fast: r is the fast grid index, so the CTAs of one domain for all right-hand sides
@@ -690,7 +772,24 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
                 part[2] = fma(Ar[q].im, Ar[q].im, part[2]);
             }
         }
-        block_sum<T, 3>(part, red);
+        // one-barrier block reduction into buffer (it & 1): the loop's top barrier keeps the
+        // other buffer's readers of the previous step apart from its next writers
+        {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+            T* rb = red + (it & 1) * 96;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                T v = warp_sum(part[q]);
+                if (lane == 0) rb[q * 32 + warp] = v;
+            }
+            __syncthreads();
+            part[0] = part[1] = part[2] = T(0);
+            for (int w = 0; w < nw; ++w) {
+                part[0] += rb[w];
+                part[1] += rb[32 + w];
+                part[2] += rb[64 + w];
+            }
+        }
         cx<T> alpha = czero<T>();
         if (part[2] > T(0)) alpha = {part[0] / part[2], part[1] / part[2]};
         if (active) {
@@ -710,6 +809,190 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
             for (int q = 0; q < 12; ++q) z[q] = z[q] + x0[q];
         }
         SpinorIO<P>::store(x, g.V, s, z);
+    }
+}
+
+// ------------------------------------------------------------ SAP half sweep, even-odd domain solves
+// The half sweep of sap_half_kernel with each domain solve in Schur-complement
+// form (reading C28): with the domain operator split by site parity,
+// D_SAP = [[A_ee, H_eo], [H_oe, A_oo]] (H the in-domain hops, A = 1 + F),
+//   rho = r_e - H_eo A_oo^{-1} r_o,  nmr minimal-residual steps on
+//   S = A_ee - H_eo A_oo^{-1} H_oe from z_e = 0,  z_o = A_oo^{-1} (r_o - H_oe z_e).
+// One CTA per domain of the given colour, one thread per pair of x-neighbouring
+// sites (one even, one odd: the block's x extent is even), so both parity
+// phases of a step keep every warp busy.  The domain tile of shared memory
+// holds rho (later z) on even sites and A_oo^{-1} H_oe rho on odd sites; the
+// odd sites' residual r_o waits in a second tile for the reconstruction.
+template <class P>
+__global__ void __launch_bounds__(128, P::id == 0 ? 2 : 4)
+    sap_half_eo_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode, const void* __restrict__ U,
+                       const void* __restrict__ C, const void* __restrict__ Ci, const void* __restrict__ b, void* x,
+                       typename P::T kappa, int rhs_fast) {
+    using T = typename P::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int vbp = 2 * blockDim.x;                           // domain sites (padded)
+    cx<T>* sh = reinterpret_cast<cx<T>*>(smem_raw);          // [12][vbp] by domain site
+    cx<T>* ros = sh + 12 * vbp;                               // [12][blockDim.x] r_o of each pair
+    T* red = reinterpret_cast<T*>(ros + 12 * blockDim.x);     // [3][32]
+
+    const int k = rhs_fast ? blockIdx.y : blockIdx.x;
+    const int rr = rhs_fast ? blockIdx.x : blockIdx.y;
+    const int h0 = bk.C[0] / 2;
+    int rest = k / h0;
+    int X1 = rest % bk.C[1];
+    rest /= bk.C[1];
+    int X2 = rest % bk.C[2];
+    int X3 = rest / bk.C[2];
+    int X0 = 2 * (k % h0) + ((X1 + X2 + X3 + colour) & 1);
+    const int Xi = X0 + bk.C[0] * (X1 + bk.C[1] * (X2 + bk.C[2] * X3));
+    b = (const char*)b + rr * spinor_bytes<P>(g.V);
+    x = (char*)x + rr * spinor_bytes<P>(g.V);
+
+    const int t = threadIdx.x;
+    const bool active = 2 * t < bk.Vb;
+    const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
+    // the pair's sites: domain indices le (even parity) and lo (odd), global sites se, so
+    int le = 0, lo = 0, se = 0, so = 0, ce[4] = {0, 0, 0, 0}, co[4] = {0, 0, 0, 0}, lce[4], lco[4];
+    if (active) {
+        int c0[4], c1[4];
+        const int s0 = block_site(g, bk, Xi, 2 * t, c0);
+        const int s1 = block_site(g, bk, Xi, 2 * t + 1, c1);
+        const bool first_even = ((c0[0] + c0[1] + c0[2] + c0[3]) & 1) == 0;
+        le = first_even ? 2 * t : 2 * t + 1;
+        lo = first_even ? 2 * t + 1 : 2 * t;
+        se = first_even ? s0 : s1;
+        so = first_even ? s1 : s0;
+        for (int mu = 0; mu < 4; ++mu) {
+            ce[mu] = first_even ? c0[mu] : c1[mu];
+            co[mu] = first_even ? c1[mu] : c0[mu];
+            lce[mu] = ce[mu] % bk.b[mu];
+            lco[mu] = co[mu] % bk.b[mu];
+        }
+    }
+    // r = b - D x at one site (hops may leave the domain; x_mode as in sap_half_kernel)
+    auto residual = [&](int s, const int (&c)[4], const int (&lc)[4], cx<T> (&r)[12]) {
+        SpinorIO<P>::load(b, g.V, s, r);
+        if (x_mode == 1) return;
+        cx<T> psi[12], acc[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = czero<T>();
+        if (x_mode == 0) {
+            SpinorIO<P>::load(x, g.V, s, psi);
+            clover_apply<P>(C, g.V, s, psi, acc);
+        }
+        int cc[4] = {c[0], c[1], c[2], c[3]};
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            float ph;
+            cx<T> u[3][3];
+            if (x_mode == 0 || lc[mu] == bk.b[mu] - 1) {
+                int n = neighbour(g, s, cc, mu, +1, ph);
+                SpinorIO<P>::load(x, g.V, n, psi);
+                GaugeIO<P>::load(U, g.V, mu, s, u);
+                hop_accum<T>(acc, psi, u, mu, +1, -kappa * T(ph));
+            }
+            if (x_mode == 0 || lc[mu] == 0) {
+                int n = neighbour(g, s, cc, mu, -1, ph);
+                SpinorIO<P>::load(x, g.V, n, psi);
+                GaugeIO<P>::load(U, g.V, mu, n, u);
+                hop_accum<T>(acc, psi, u, mu, -1, -kappa * T(ph));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) r[q] = r[q] - acc[q];
+    };
+    // acc += coeff * (in-domain hops of site s from the tile)
+    auto tile_hops = [&](int s, int l, const int (&lc)[4], T coeff, cx<T> (&acc)[12]) {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            cx<T> u[3][3], psi[12];
+            if (lc[mu] != bk.b[mu] - 1) {
+                DomainVec<T>::get(sh, vbp, l + lstr[mu], psi);
+                GaugeIO<P>::load(U, g.V, mu, s, u);
+                hop_accum<T>(acc, psi, u, mu, +1, coeff);
+            }
+            if (lc[mu] != 0) {
+                DomainVec<T>::get(sh, vbp, l - lstr[mu], psi);
+                GaugeIO<P>::load(U, g.V, mu, s - g.stride[mu], u);
+                hop_accum<T>(acc, psi, u, mu, -1, coeff);
+            }
+        }
+    };
+    cx<T> rho[12], z[12], v[12];
+    if (active) {
+        // r_o -> A_oo^{-1} r_o in the tile; r_o kept for the reconstruction
+        residual(so, co, lco, v);
+        DomainVec<T>::put(ros, blockDim.x, t, v);
+        cx<T> w[12];
+        clover_apply<P>(Ci, g.V, so, v, w);
+        DomainVec<T>::put(sh, vbp, lo, w);
+        residual(se, ce, lce, rho);
+    }
+    __syncthreads();
+    if (active) {
+        // rho = r_e - H_eo A_oo^{-1} r_o  (H = -kappa * hop terms)
+        tile_hops(se, le, lce, kappa, rho);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) z[q] = czero<T>();
+    }
+    for (int it = 0; it < nmr; ++it) {
+        if (active) DomainVec<T>::put(sh, vbp, le, rho);
+        __syncthreads();
+        // odd sites: w = A_oo^{-1} H_oe rho
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) v[q] = czero<T>();
+            tile_hops(so, lo, lco, -kappa, v);
+            cx<T> w[12];
+            clover_apply<P>(Ci, g.V, so, v, w);
+            DomainVec<T>::put(sh, vbp, lo, w);
+        }
+        __syncthreads();
+        // even sites: S rho = A_ee rho - H_eo w
+        T part[3] = {T(0), T(0), T(0)};
+        if (active) {
+            clover_apply<P>(C, g.V, se, rho, v);
+            tile_hops(se, le, lce, kappa, v);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                part[0] = fma(v[q].re, rho[q].re, part[0]);
+                part[0] = fma(v[q].im, rho[q].im, part[0]);
+                part[1] = fma(v[q].re, rho[q].im, part[1]);
+                part[1] = fma(-v[q].im, rho[q].re, part[1]);
+                part[2] = fma(v[q].re, v[q].re, part[2]);
+                part[2] = fma(v[q].im, v[q].im, part[2]);
+            }
+        }
+        block_sum<T, 3>(part, red);
+        cx<T> alpha = czero<T>();
+        if (part[2] > T(0)) alpha = {part[0] / part[2], part[1] / part[2]};
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                cfma(z[q], alpha, rho[q]);
+                cfma(rho[q], -alpha, v[q]);
+            }
+        }
+    }
+    // z_o = A_oo^{-1} (r_o - H_oe z_e), then x += z on both sites
+    if (active) DomainVec<T>::put(sh, vbp, le, z);
+    __syncthreads();
+    if (active) {
+        DomainVec<T>::get(ros, blockDim.x, t, v);
+        tile_hops(so, lo, lco, kappa, v);
+        cx<T> zo[12];
+        clover_apply<P>(Ci, g.V, so, v, zo);
+        if (x_mode == 0) {
+            cx<T> x0[12];
+            SpinorIO<P>::load(x, g.V, se, x0);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) z[q] = z[q] + x0[q];
+            SpinorIO<P>::load(x, g.V, so, x0);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) zo[q] = zo[q] + x0[q];
+        }
+        SpinorIO<P>::store(x, g.V, se, z);
+        SpinorIO<P>::store(x, g.V, so, zo);
     }
 }
 
@@ -977,7 +1260,7 @@ cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr
     Blocking bk = make_blocking(gh, bh);
     int threads = (bk.Vb + 31) / 32 * 32;
     if (threads > 512) return cudaErrorInvalidValue;
-    size_t smem = (size_t)12 * threads * sizeof(cx<typename P::T>) + 3 * 32 * sizeof(typename P::T);
+    size_t smem = (size_t)12 * threads * sizeof(cx<typename P::T>) + 2 * 3 * 32 * sizeof(typename P::T);
     int ndom = bk.Vc / 2;
     // right-hand side as the fast grid index when the domains fit the y dimension
     const int fast = nrhs > 1 && ndom <= 65535;
@@ -998,6 +1281,13 @@ cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr
     return cudaGetLastError();
 }
 
+// launch shape of the stencil per precision, chosen by the autotuner (dirac_set_shape):
+// threads per CTA and the grid cap in CTAs per SM (grid-stride loop beyond it)
+struct DiracShape {
+    int threads, per_sm;
+};
+DiracShape g_dirac_shape[3] = {{kThreads, 16}, {kThreads, 16}, {kThreads, 16}};
+
 template <class P>
 cudaError_t dirac_impl(const GeomH& gh, const BlockH* sb, const void* U, const void* C, const void* in, void* out,
                        const void* b, double kappa, int nrhs, cudaStream_t st) {
@@ -1005,14 +1295,19 @@ cudaError_t dirac_impl(const GeomH& gh, const BlockH* sb, const void* U, const v
     Blocking bk;
     BlockH one = {{1, 1, 1, 1}};
     bk = make_blocking(gh, sb ? *sb : one);
-    dim3 grid(grid_for(g.V, kThreads), nrhs);
+    const DiracShape sh = g_dirac_shape[P::id];
+    int blocks = (g.V + sh.threads - 1) / sh.threads;
+    const int cap = device_sms() * sh.per_sm;
+    if (blocks > cap) blocks = cap;
+    dim3 grid(blocks, nrhs);
+    const int th = sh.threads;
     using T = typename P::T;
     if (sb) {
-        if (b) (note_launch(), dirac_kernel<P, true, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
-        else (note_launch(), dirac_kernel<P, true, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+        if (b) (note_launch(), dirac_kernel<P, true, true><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+        else (note_launch(), dirac_kernel<P, true, false><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
     } else {
-        if (b) (note_launch(), dirac_kernel<P, false, true><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
-        else (note_launch(), dirac_kernel<P, false, false><<<grid, kThreads, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+        if (b) (note_launch(), dirac_kernel<P, false, true><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+        else (note_launch(), dirac_kernel<P, false, false><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
     }
     return cudaGetLastError();
 }
@@ -1148,6 +1443,14 @@ cudaError_t launch_clover_expand(const GeomH& gh, const void* C64, double* out, 
     (note_launch(), clover_expand_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, C64, out));
     return cudaGetLastError();
 }
+void dirac_set_shape(int prec, int threads, int per_sm) {
+    if (prec < 0 || prec > 2 || threads < 32 || threads > kThreads || threads % 32 || per_sm < 1) return;
+    g_dirac_shape[prec] = {threads, per_sm};
+}
+void dirac_get_shape(int prec, int* threads, int* per_sm) {
+    *threads = g_dirac_shape[prec].threads;
+    *per_sm = g_dirac_shape[prec].per_sm;
+}
 cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sb, const void* U, const void* C, const void* in,
                          void* out, const void* b, double kappa, int nrhs, cudaStream_t st) {
     if (prec == 0) return dirac_impl<P64>(g, sb, U, C, in, out, b, kappa, nrhs, st);
@@ -1173,6 +1476,48 @@ cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, c
     (note_launch(), spinor_axpy_mixed_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x));
     return cudaGetLastError();
 }
+template <class P>
+cudaError_t sap_half_eo_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
+                             const void* C, const void* Ci, const void* b, void* x, double kappa, int nrhs,
+                             cudaStream_t st) {
+    Geom g = make_geom(gh);
+    Blocking bk = make_blocking(gh, bh);
+    if (bk.b[0] % 2 != 0) return cudaErrorInvalidValue;   // pairs of x-neighbours of opposite parity
+    const int threads = ((bk.Vb / 2) + 31) / 32 * 32;
+    if (threads > 256) return cudaErrorInvalidValue;
+    using T = typename P::T;
+    const size_t smem = (size_t)12 * (2 * threads) * sizeof(cx<T>) + (size_t)12 * threads * sizeof(cx<T>) +
+                        3 * 32 * sizeof(T);
+    const int ndom = bk.Vc / 2;
+    const int fast = nrhs > 1 && ndom <= 65535;
+    const dim3 grid = fast ? dim3(nrhs, ndom) : dim3(ndom, nrhs);
+    cudaError_t e = cudaFuncSetAttribute(sap_half_eo_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    (note_launch(), sap_half_eo_kernel<P><<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, Ci, b, x,
+                                                                      (T)kappa, fast));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sap_half_eo(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode,
+                               const void* U, const void* C, const void* Ci, const void* b, void* x, double kappa,
+                               int nrhs, cudaStream_t st) {
+    if (prec == 0) return sap_half_eo_impl<P64>(g, bk, colour, nmr, x_mode, U, C, Ci, b, x, kappa, nrhs, st);
+    if (prec == 1) return sap_half_eo_impl<P32>(g, bk, colour, nmr, x_mode, U, C, Ci, b, x, kappa, nrhs, st);
+    return sap_half_eo_impl<P16>(g, bk, colour, nmr, x_mode, U, C, Ci, b, x, kappa, nrhs, st);
+}
+bool sap_eo_supported(const BlockH& bk) {
+    const int vb = bk.b[0] * bk.b[1] * bk.b[2] * bk.b[3];
+    return bk.b[0] % 2 == 0 && vb <= 512;
+}
+cudaError_t launch_clover_invert(int prec, const GeomH& gh, const void* C64, void* out, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    int grid = grid_for(g.V, 128);
+    if (prec == 0) (note_launch(), clover_invert_kernel<P64><<<grid, 128, 0, st>>>(g, C64, out));
+    else if (prec == 1) (note_launch(), clover_invert_kernel<P32><<<grid, 128, 0, st>>>(g, C64, out));
+    else (note_launch(), clover_invert_kernel<P16><<<grid, 128, 0, st>>>(g, C64, out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const BlockH& bk, int colour, int nmr,
                                     int x_mode, const void* U, const void* C, const void* b, void* x, double kappa,
                                     int nrhs, cudaStream_t st) {

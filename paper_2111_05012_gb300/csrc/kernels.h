@@ -47,6 +47,10 @@ cudaError_t launch_clover_build(int prec, const GeomH& g, const void* U64, doubl
 // internal P64 clover -> [site][2][6][6][2] doubles (device)
 cudaError_t launch_clover_expand(const GeomH& g, const void* C64, double* out, cudaStream_t s);
 
+// launch shape of launch_dirac per precision (0..2): threads per CTA (a multiple of 32, <= 256)
+// and the grid cap in CTAs per SM; set by the autotuner, process-wide
+void dirac_set_shape(int prec, int threads, int per_sm);
+void dirac_get_shape(int prec, int* threads, int* per_sm);
 // out = D in (sap_block != NULL: hops between blocks removed); if b != NULL, out = b - D in
 cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sap_block, const void* U, const void* C,
                          const void* in, void* out, const void* b, double kappa, int nrhs, cudaStream_t s);
@@ -69,6 +73,14 @@ cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const
                                     int x_mode, const void* U, const void* C, const void* b, void* x, double kappa,
                                     int nrhs, cudaStream_t s);
 bool sap_staged_supported(int prec, const BlockH& bk);
+// the half sweep with even-odd (Schur complement) domain solves; Ci = clover inverse of prec
+// (launch_clover_invert); needs an even block extent in x and at most 512 sites per block
+cudaError_t launch_sap_half_eo(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode,
+                               const void* U, const void* C, const void* Ci, const void* b, void* x, double kappa,
+                               int nrhs, cudaStream_t s);
+bool sap_eo_supported(const BlockH& bk);
+// A^{-1} per site (two Hermitian 6x6 blocks) from the FP64 clover, stored in the clover layout of prec (0..2)
+cudaError_t launch_clover_invert(int prec, const GeomH& g, const void* C64, void* out, cudaStream_t s);
 
 // ---- transfer (fine level 0 -> 1) ----
 // fprec: field precision (0/1/2), vprec: test-vector precision (0/1), cprec: coarse precision (0/1)
@@ -120,9 +132,13 @@ cudaError_t launch_coarse_sap_half(int kprec, const GeomH& g, const BlockH& bh, 
 size_t coarse_solver_state_bytes();
 size_t coarse_solver_partial_bytes();
 int coarse_solver_max_rhs();
+// xgroup: coarse sites whose neighbour blocks are gathered into shared memory per step (the
+// tile; 0 = as many as fit)
 cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
                                    void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
-                                   void* part, void* state, int cluster, cudaStream_t s, int nb = 1);
+                                   void* part, void* state, int cluster, cudaStream_t s, int nb = 1,
+                                   int xgroup = 0);
+int coarse_solver_max_xgroup(int cprec, int nc, int nb);
 // multi-RHS coarse stencil on the tensor cores (coarse_tc.cu): bfloat16 operands, FP32
 // accumulation; needs Nc % 16 == 0 and Nc <= 64.  The operator is first copied into the
 // tensor-core operand image ([V][2Nc][9Nc] bfloat16 in 8 x 8 core-matrix order) from its

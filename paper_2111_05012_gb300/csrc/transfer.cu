@@ -240,49 +240,68 @@ __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __rest
 }
 
 // ------------------------------------------------------------ orthonormalisation
-// Per (block, chirality): Gram-Schmidt over i = 0..nvec-1 in index order,
-// every vector projected against the previous ones twice, in FP64.
+// Per (block, chirality): Gram-Schmidt over i = 0..nvec-1 in index order, every
+// vector projected twice against the previous ones, in FP64.  Each projection
+// takes the coefficients <v_j, w> of all previous vectors in one pass (classical
+// form: per-warp sums into shared memory, one barrier, one cross-warp sum per
+// coefficient), then subtracts them in a second pass over the vectors; projected
+// twice, this gives the QR factor with a positive diagonal to rounding, the same
+// vectors as projecting one vector after another.
 template <class PV>
 __global__ void orthonormalise_kernel(Geom g, Blocking bk, int nvec, void* vecs, int* err) {
     __shared__ double red[3 * 32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<double>* part = reinterpret_cast<cx<double>*>(smem_raw);   // [nwarps][nvec]
+    cx<double>* coef = part + (size_t)(blockDim.x / 32) * nvec;    // [nvec]
     const int Xi = blockIdx.x, chi = blockIdx.y;
-    const int l = threadIdx.x;
+    const int l = threadIdx.x, lane = l & 31, warp = l >> 5, nw = blockDim.x >> 5;
     const bool active = l < bk.Vb;
     const size_t vb = spinor_bytes<PV>(g.V);
     int c[4], s = 0;
     if (active) s = block_site(g, bk, Xi, l, c);
+    auto load_half = [&](int j, cx<double> (&q)[6]) {
+        if (active) {
+            cx<typename PV::T> u[12];
+            SpinorIO<PV>::load_rw((const char*)vecs + j * vb, g.V, s, u);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) q[k] = ccast<double>(u[6 * chi + k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) q[k] = czero<double>();
+        }
+    };
     for (int i = 0; i < nvec; ++i) {
         cx<double> w[6];
-        cx<typename PV::T> v[12];
-        if (active) {
-            SpinorIO<PV>::load_rw((const char*)vecs + i * vb, g.V, s, v);
-            for (int k = 0; k < 6; ++k) w[k] = ccast<double>(v[6 * chi + k]);
-        } else {
-            for (int k = 0; k < 6; ++k) w[k] = czero<double>();
-        }
+        load_half(i, w);
         double n0[1] = {0};
         for (int k = 0; k < 6; ++k) n0[0] += norm2(w[k]);
         block_sum<double, 1>(n0, red);
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < 2 && i > 0; ++pass) {
             for (int j = 0; j < i; ++j) {
                 cx<double> q[6];
-                if (active) {
-                    cx<typename PV::T> u[12];
-                    SpinorIO<PV>::load_rw((const char*)vecs + j * vb, g.V, s, u);
-                    for (int k = 0; k < 6; ++k) q[k] = ccast<double>(u[6 * chi + k]);
-                } else {
-                    for (int k = 0; k < 6; ++k) q[k] = czero<double>();
-                }
-                double d[2] = {0, 0};
-                for (int k = 0; k < 6; ++k) {
-                    cx<double> t = cmulc(q[k], w[k]);
-                    d[0] += t.re;
-                    d[1] += t.im;
-                }
-                block_sum<double, 2>(d, red);
-                cx<double> cc = {d[0], d[1]};
+                load_half(j, q);
+                cx<double> d = czero<double>();
+#pragma unroll
+                for (int k = 0; k < 6; ++k) d = d + cmulc(q[k], w[k]);
+                d.re = warp_sum(d.re);
+                d.im = warp_sum(d.im);
+                if (lane == 0) part[warp * nvec + j] = d;
+            }
+            __syncthreads();
+            for (int j = l; j < i; j += blockDim.x) {
+                cx<double> t = czero<double>();
+                for (int ww = 0; ww < nw; ++ww) t = t + part[ww * nvec + j];
+                coef[j] = t;
+            }
+            __syncthreads();
+            for (int j = 0; j < i; ++j) {
+                cx<double> q[6];
+                load_half(j, q);
+                const cx<double> cc = coef[j];
+#pragma unroll
                 for (int k = 0; k < 6; ++k) w[k] = w[k] - cc * q[k];
             }
+            __syncthreads();   // part / coef are rewritten by the next pass
         }
         double nn[1] = {0};
         for (int k = 0; k < 6; ++k) nn[0] += norm2(w[k]);
@@ -305,96 +324,123 @@ __global__ void orthonormalise_kernel(Geom g, Blocking bk, int nvec, void* vecs,
 }
 
 // ------------------------------------------------------------ Galerkin operator
-// CTA (block Xi, column J = (t, j)): for every direction d the field
+// CTA (block Xi, pair of columns J = (t, j)): for every direction d the fields
 // T_d = H_d P_t v_j on the sites of Xi (H_0 = D_SAP on the block, H_{+-mu} =
-// the hops of D leaving Xi through its +-mu face) is formed and projected on
-// all basis vectors of Xi: B[Xi][I][d][J] = <Xi, I| T_d>.
+// the hops of D leaving Xi through its +-mu face) are formed for both columns
+// and projected on all basis vectors of Xi: B[Xi][I][d][J] = <Xi, I| T_d>.
+// Each test-vector load serves both columns; in a face direction only the
+// face sites of the block (a quarter of them for 4^4 blocks) load anything,
+// and a warp without face sites skips the direction; the four projections of
+// a vector (two columns x two chiralities) are summed over the warp by one
+// transposed shuffle reduction.
 template <class PV, typename TC>
 __global__ void galerkin_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
                                 const void* __restrict__ U, const void* __restrict__ C, typename PV::T kappa,
                                 void* B) {
     using T = typename PV::T;
+    constexpr int NQ = 8;   // per vector: column a / b x chirality 0 / 1 x (re, im)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = 2 * nvec;
-    cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);   // [nwarps][nc]
+    T* partf = reinterpret_cast<T*>(smem_raw);   // [nwarps][2 columns][nc] complex
+    cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int Xi = blockIdx.x, J = blockIdx.y;
-    const int t = J / nvec, j = J % nvec;
+    const int Xi = blockIdx.x, Ja = 2 * blockIdx.y, Jb = Ja + 1;
+    const bool hasB = Jb < nc;
+    const int ta = Ja / nvec, ja = Ja % nvec, tb = hasB ? Jb / nvec : 0, jb = hasB ? Jb % nvec : 0;
     const size_t vb = spinor_bytes<PV>(g.V);
-    const char* vj = (const char*)vecs + j * vb;
+    const char* va = (const char*)vecs + ja * vb;
+    const char* vbp = (const char*)vecs + jb * vb;
     const int l = threadIdx.x;
     const bool active = l < bk.Vb;
+    const int qi = transposed_index<NQ>(lane);
+    const bool writer = (lane & (32 / NQ - 1)) == 0;
     int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
     if (active) {
         s = block_site(g, bk, Xi, l, c);
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
     }
-    auto load_proj = [&](int site, cx<T> v[12]) {
-        SpinorIO<PV>::load(vj, g.V, site, v);
+    auto load_proj = [&](const char* v, int t, int site, cx<T> out[12]) {
+        SpinorIO<PV>::load(v, g.V, site, out);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[6 * (1 - t) + k] = czero<T>();
+        for (int k = 0; k < 6; ++k) out[6 * (1 - t) + k] = czero<T>();
+    };
+    // acc_a += coeff (1 - dir gamma_mu) W P_ta v_ja(n), acc_b likewise (one link load)
+    auto hop2 = [&](int n, int linksite, int mu, int dir, T coeff, cx<T> (&acc_a)[12], cx<T> (&acc_b)[12]) {
+        cx<T> psi[12], u[3][3];
+        GaugeIO<PV>::load(U, g.V, mu, linksite, u);
+        load_proj(va, ta, n, psi);
+        hop_accum<T>(acc_a, psi, u, mu, dir, coeff);
+        if (hasB) {
+            load_proj(vbp, tb, n, psi);
+            hop_accum<T>(acc_b, psi, u, mu, dir, coeff);
+        }
     };
     for (int d = 0; d < 9; ++d) {
-        cx<T> Tv[12];
+        const int mu = d == 0 ? 0 : (d - 1) % 4;
+        const int dir = d <= 4 ? +1 : -1;
+        const bool face = d == 0 || (dir > 0 ? (lc[mu] == bk.b[mu] - 1) : (lc[mu] == 0));
+        const bool work = active && face;
+        cx<T> Ta[12], Tb[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) Tv[k] = czero<T>();
-        if (active) {
-            cx<T> psi[12], u[3][3];
+        for (int k = 0; k < 12; ++k) Ta[k] = Tb[k] = czero<T>();
+        if (work) {
             float ph;
             if (d == 0) {
-                load_proj(s, psi);
-                clover_apply<PV>(C, g.V, s, psi, Tv);
-                for (int mu = 0; mu < 4; ++mu) {
-                    if (lc[mu] != bk.b[mu] - 1) {
-                        int n = neighbour(g, s, c, mu, +1, ph);
-                        load_proj(n, psi);
-                        GaugeIO<PV>::load(U, g.V, mu, s, u);
-                        hop_accum<T>(Tv, psi, u, mu, +1, -kappa * T(ph));
+                cx<T> psi[12];
+                load_proj(va, ta, s, psi);
+                clover_apply<PV>(C, g.V, s, psi, Ta);
+                if (hasB) {
+                    load_proj(vbp, tb, s, psi);
+                    clover_apply<PV>(C, g.V, s, psi, Tb);
+                }
+                for (int m = 0; m < 4; ++m) {
+                    if (lc[m] != bk.b[m] - 1) {
+                        int n = neighbour(g, s, c, m, +1, ph);
+                        hop2(n, s, m, +1, -kappa * T(ph), Ta, Tb);
                     }
-                    if (lc[mu] != 0) {
-                        int n = neighbour(g, s, c, mu, -1, ph);
-                        load_proj(n, psi);
-                        GaugeIO<PV>::load(U, g.V, mu, n, u);
-                        hop_accum<T>(Tv, psi, u, mu, -1, -kappa * T(ph));
+                    if (lc[m] != 0) {
+                        int n = neighbour(g, s, c, m, -1, ph);
+                        hop2(n, n, m, -1, -kappa * T(ph), Ta, Tb);
                     }
                 }
             } else {
-                const int mu = (d - 1) % 4;
-                const int dir = d <= 4 ? +1 : -1;
-                const bool face = dir > 0 ? (lc[mu] == bk.b[mu] - 1) : (lc[mu] == 0);
-                if (face) {
-                    int n = neighbour(g, s, c, mu, dir, ph);
-                    load_proj(n, psi);
-                    GaugeIO<PV>::load(U, g.V, mu, dir > 0 ? s : n, u);
-                    hop_accum<T>(Tv, psi, u, mu, dir, -kappa * T(ph));
-                }
+                int n = neighbour(g, s, c, mu, dir, ph);
+                hop2(n, dir > 0 ? s : n, mu, dir, -kappa * T(ph), Ta, Tb);
             }
         }
+        const bool wwork = __any_sync(0xffffffffu, work);
         for (int i = 0; i < nvec; ++i) {
-            cx<T> d0 = czero<T>(), d1 = czero<T>();
-            if (active) {
+            if (!wwork) {   // no face site in this warp: its partial sums are zero
+                if (lane < 4) part[(warp * 2 + (lane >> 1)) * nc + (lane & 1) * nvec + i] = czero<T>();
+                continue;
+            }
+            cx<T> d0a = czero<T>(), d1a = czero<T>(), d0b = czero<T>(), d1b = czero<T>();
+            if (work) {
                 cx<T> v[12];
                 SpinorIO<PV>::load((const char*)vecs + i * vb, g.V, s, v);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    d0 = d0 + cmulc(v[k], Tv[k]);
-                    d1 = d1 + cmulc(v[6 + k], Tv[6 + k]);
+                    cfmac(d0a, v[k], Ta[k]);
+                    cfmac(d1a, v[6 + k], Ta[6 + k]);
+                    cfmac(d0b, v[k], Tb[k]);
+                    cfmac(d1b, v[6 + k], Tb[6 + k]);
                 }
             }
-            d0.re = warp_sum(d0.re);
-            d0.im = warp_sum(d0.im);
-            d1.re = warp_sum(d1.re);
-            d1.im = warp_sum(d1.im);
-            if (lane == 0) {
-                part[warp * nc + i] = d0;
-                part[warp * nc + nvec + i] = d1;
+            T q[NQ] = {d0a.re, d0a.im, d1a.re, d1a.im, d0b.re, d0b.im, d1b.re, d1b.im};
+            const T tot = transposed_warp_sum<NQ>(q, lane);
+            if (writer) {
+                const int col = qi >> 2, comp = qi & 3;
+                const int row = (comp < 2 ? 0 : nvec) + i;
+                partf[2 * ((warp * 2 + col) * nc + row) + (comp & 1)] = tot;
             }
         }
         __syncthreads();
-        for (int row = threadIdx.x; row < nc; row += blockDim.x) {
+        for (int r = threadIdx.x; r < 2 * nc; r += blockDim.x) {
+            const int col = r / nc, row = r % nc;
+            if (col == 1 && !hasB) continue;
             cx<T> acc = czero<T>();
-            for (int w = 0; w < nw; ++w) acc = acc + part[w * nc + row];
-            CStore<TC>::st(B, (((size_t)Xi * nc + row) * 9 + d) * nc + J, ccast<TC>(acc));
+            for (int w = 0; w < nw; ++w) acc = acc + part[(w * 2 + col) * nc + row];
+            CStore<TC>::st(B, (((size_t)Xi * nc + row) * 9 + d) * nc + (col ? Jb : Ja), ccast<TC>(acc));
         }
         __syncthreads();
     }
@@ -464,8 +510,9 @@ cudaError_t launch_orthonormalise_fine(int vprec, const GeomH& gh, const BlockH&
     Blocking bk = make_blocking(gh, bh);
     dim3 grid(bk.Vc, 2);
     int th = threads_for(bk);
-    if (vprec == 0) (note_launch(), orthonormalise_kernel<P64><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err));
-    else (note_launch(), orthonormalise_kernel<P32><<<grid, th, 0, st>>>(g, bk, nvec, vecs, err));
+    const size_t smem = ((size_t)(th / 32) + 1) * nvec * sizeof(cx<double>);
+    if (vprec == 0) (note_launch(), orthonormalise_kernel<P64><<<grid, th, smem, st>>>(g, bk, nvec, vecs, err));
+    else (note_launch(), orthonormalise_kernel<P32><<<grid, th, smem, st>>>(g, bk, nvec, vecs, err));
     return cudaGetLastError();
 }
 cudaError_t launch_galerkin_fine(int vprec, int cprec, const GeomH& gh, const BlockH& bh, int nvec, const void* vecs,
@@ -473,13 +520,13 @@ cudaError_t launch_galerkin_fine(int vprec, int cprec, const GeomH& gh, const Bl
     Geom g = make_geom(gh);
     Blocking bk = make_blocking(gh, bh);
     int th = threads_for(bk);
-    dim3 grid(bk.Vc, 2 * nvec);
+    dim3 grid(bk.Vc, nvec);   // pairs of columns
     if (vprec == 0) {
-        size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<double>);
+        size_t smem = (size_t)(th / 32) * 2 * 2 * nvec * sizeof(cx<double>);
         if (cprec == 0) (note_launch(), galerkin_kernel<P64, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B));
         else (note_launch(), galerkin_kernel<P64, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, kappa, B));
     } else {
-        size_t smem = (size_t)(th / 32) * 2 * nvec * sizeof(cx<float>);
+        size_t smem = (size_t)(th / 32) * 2 * 2 * nvec * sizeof(cx<float>);
         if (cprec == 0) (note_launch(), galerkin_kernel<P32, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B));
         else (note_launch(), galerkin_kernel<P32, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B));
     }

@@ -510,3 +510,57 @@ def test_mbicgs_matches_oracle(dims, eps, seed, kappa):
         assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
         c.amg_hierarchy_destroy(h)
     f.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_sap_even_odd(mgcase, prec):
+    # SAP with the even-odd (Schur complement) domain solves (reading C28) against the
+    # oracle's sap_eo, one right-hand side and a batch of three; the blocking's x extent
+    # must be even (81-site 3^4 blocks are rejected)
+    import torch
+    from oracle import evenodd
+    f = mgcase
+    c = f.c
+    p = _params(c, f.block, f.nvec, prec, sap_eo=1)
+    if f.block[0] % 2:
+        with pytest.raises(c.AMGError) as e:
+            c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(f.v0)])
+        assert e.value.status == c.AMG_EINVAL
+        return
+    h = c.amg_setup_from_vectors(f.d, p, [li.to_interleaved(f.v0)])
+    dt = "float64" if prec == 0 else "float32"
+    tol = {0: 1e-11, 1: 1e-5, 2: 1e-2}[prec]
+    bs = np.stack([li.rhs(f.dims, 61 + k).reshape(f.shape4 + (12,)) for k in range(3)])
+    refs = [evenodd.sap_eo(f.op, f.block, bs[k], 4, 6) for k in range(3)]
+    x = to_dev(bs[0], dt)
+    y = torch.zeros_like(x)
+    c.amg_sap(h, x, y, prec)
+    assert rel(from_dev(y, f.shape4 + (12,)), refs[0]) < tol
+    xb = to_dev(bs, dt)
+    yb = torch.zeros_like(xb)
+    c.amg_sap(h, xb, yb, prec, nrhs=3)
+    got = from_dev(yb, (3,) + f.shape4 + (12,))
+    for k in range(3):
+        assert rel(got[k], refs[k]) < tol
+    c.amg_hierarchy_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_with_even_odd_smoother(prec):
+    import torch
+    dims = (8, 8, 8, 8)
+    f = Field(dims, 0.5, 4, 0.129, 1.0)
+    c = f.c
+    p = _params(c, (4, 4, 4, 4), 8, prec, n_init=2, n_adapt=1, sap_eo=1)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 4, 8))])
+    b = np.stack([li.rhs(dims, 70 + k) for k in range(2)])
+    x = torch.zeros(b.size * 2, dtype=torch.float64, device="cuda")
+    st, info = c.amg_solve(h, to_dev(b), x, 2, 1e-10, 100)
+    assert info.converged == 1 and info.true_rel_residual <= 1e-10
+    op = odirac.WilsonClover(f.U, 0.129, 1.0)
+    xs = from_dev(x, (2,) + f.shape4 + (12,))
+    for k in range(2):
+        r = b[k].reshape(f.shape4 + (12,)) - op.apply(xs[k])
+        assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1.05e-10
+    c.amg_hierarchy_destroy(h)
+    f.close()
