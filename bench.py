@@ -329,6 +329,9 @@ def run_headline(args):
     p.sap_eo = 1 if args.sap_eo else 0
     if args.mr is not None:
         p.mr_iters = args.mr
+    if args.prop_coarse == "bf16":
+        p.prec_coarsest = capi.AMG_BF16
+        p.coarse_tc = 1 if args.coarse_tc else 0
     t0 = time.perf_counter()
     h = capi.amg_setup(d, p, [init])
     torch.cuda.synchronize()
@@ -1023,14 +1026,19 @@ def main():
     ap.add_argument("--workload", default="propagator",
                     choices=["propagator", "solve16", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--prop-coarse", default="f32", choices=["f32", "bf16"],
+                    help="propagator: coarsest operator storage (bf16: bfloat16 entries)")
+    ap.add_argument("--coarse-tc", action="store_true",
+                    help="propagator with --prop-coarse bf16: batched coarse solves with the stencil on the tensor cores")
     ap.add_argument("--sap-eo", action="store_true",
                     help="propagator: even-odd (Schur complement) SAP domain solves")
     ap.add_argument("--mr", type=int, default=None, help="propagator: minimal-residual steps per domain solve")
     ap.add_argument("--dims", default=None,
                     help="propagator workload on a smaller lattice Lx,Ly,Lz,Lt (profiling; not the headline)")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1],
-                    help="SAP kernel: 0 operator through L1/L2 (default), 1 staged in shared memory, -1 autotune")
+    ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1, 2],
+                    help="SAP kernel: 0 operator through L1/L2 (default), 1 staged in shared memory, "
+                         "2 two right-hand sides of a batch per CTA, -1 autotune")
     ap.add_argument("--n-init", type=int, default=None, help="setup (0-a) SAP applications (default: library's)")
     ap.add_argument("--n-adapt", type=int, default=None, help="setup (0-b) adaptive passes (default: library's)")
     ap.add_argument("--coarse-tol", type=float, default=None, help="coarsest solve tolerance (default: library's)")

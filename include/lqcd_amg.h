@@ -94,9 +94,13 @@ typedef struct {
                                            FP32 vectors and arithmetic with the coarse operator
                                            stored in bfloat16 (half the bytes per stencil sweep)
                                            [AMG_F32] */
-    int sap_variant;                    /* SAP kernel: -1 autotune at setup (times both, keeps the faster),
+    int sap_variant;                    /* SAP kernel: -1 autotune at setup (times the variants for one
+                                           right-hand side and for a batch, keeps the fastest of each),
                                            0 operator read from global memory, 1 operator staged in shared
-                                           memory (FP32/FP16, blocks <= 256 sites) [-1] */
+                                           memory (FP32/FP16, blocks <= 256 sites; two right-hand sides
+                                           per CTA in a batch), 2 as 0 but two right-hand sides of a batch
+                                           per CTA sharing the operator in L1 (FP32/FP16, <= 256 sites)
+                                           [-1] */
     int outer_solver;                   /* 0: flexible GMRES(outer_m) [0]; 1: the paper's BiCGStab with
                                            flexible preconditioning (Sec. 3), one right-hand side at a
                                            time; 2: the paper's comparison solver MBiCGs (Sec. 5,
@@ -123,6 +127,12 @@ typedef struct {
                                            x; the clover inverse is built once per operator and
                                            precision.  Not in the paper (an addition beside the SAP
                                            listing of Sec. 3).  0: the paper's MR on D_SAP [0] */
+    int coarse_tc;                      /* 1: a batch of 2..16 right-hand sides on a coarsest level stored
+                                           in bfloat16 (prec_coarsest = AMG_BF16, Nc % 16 == 0) runs its
+                                           coarse BiCGStab(l) in lockstep with every stencil pass on the
+                                           tensor cores (bfloat16 operands including the vectors, FP32
+                                           accumulation); 0: the persistent SIMT solver for every batch
+                                           (four right-hand sides per launch) [0] */
 } amg_params;
 
 typedef struct {

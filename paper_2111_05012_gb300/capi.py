@@ -53,6 +53,7 @@ class amg_params(ctypes.Structure):
         ("mbicgs_tol", ctypes.c_double),
         ("mbicgs_maxit", ctypes.c_int),
         ("sap_eo", ctypes.c_int),
+        ("coarse_tc", ctypes.c_int),
     ]
 
 

@@ -79,6 +79,8 @@ struct CoarseLevel {
     DevBuf cvecs;
     DevBuf cvecs_next;          // (0-b): the pass's new vectors while M still reads cvecs
     int xgroup = 0;             // coarsest solver's shared-memory tile (coarse sites per gather), tuned
+    std::vector<DevBuf> tcw;    // tensor-core coarse solve: r~, R_0..R_l, U_0..U_l (one batch each)
+    DevBuf tcerr;
     std::vector<DevBuf> gV, gZ;
     DevBuf gw, gr, gt;
     int kprec() const { return opbf ? 2 : op32 ? 3 : prec; }   // precision code of the stencil kernels
@@ -111,6 +113,29 @@ struct Reducer {
         CK(cudaMemcpyAsync(hpart, dpart.p, sizeof(double2) * grid * k, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         for (int j = 0; j < k; ++j) {
+            double re = 0, im = 0;
+            for (int q = 0; q < grid; ++q) {
+                re += hpart[j * grid + q].x;
+                im += hpart[j * grid + q].y;
+            }
+            out[j] = cplx(re, im);
+        }
+        return AMG_OK;
+    }
+    // for r < nb: k dots <a_r[j], b_r> (a_r = a + r * stride entries, likewise b), one
+    // synchronisation for the batch; out[r * k + j]; k * nb <= 20 * capacity
+    amg_status batch_dots(int prec, int nb, int k, const void* const* a, const void* b, size_t stride, size_t n,
+                          cplx* out, cudaStream_t s) {
+        const size_t eb = prec == 0 ? 16 : 8;
+        std::vector<const void*> ar(k);
+        for (int r = 0; r < nb; ++r) {
+            for (int j = 0; j < k; ++j) ar[j] = (const char*)a[j] + r * stride * eb;
+            CK(launch_multi_dot(prec, k, ar.data(), (const char*)b + r * stride * eb, n,
+                                dpart.as<double2>() + (size_t)r * k * grid, s));
+        }
+        CK(cudaMemcpyAsync(hpart, dpart.p, sizeof(double2) * grid * k * nb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int j = 0; j < k * nb; ++j) {
             double re = 0, im = 0;
             for (int q = 0; q < grid; ++q) {
                 re += hpart[j * grid + q].x;
@@ -224,6 +249,7 @@ struct amg_hierarchy {
     amg_nn* nn = nullptr;             // learned correction after the cycle (FP32 smoother only)
     bool nn_off = false;              // set while falling back to the plain cycle
     int* hstate = nullptr;   // pinned mirror of the coarse solver state words (16 x 4 ints)
+    int tc_cycles = 0;       // coarsest-level cycles of the tensor-core solver in the current solve
     int nb_cap = 0;          // batch width the workspaces are sized for
     // ragged solves: step j of the outer solver (Z_j = M V_j, w = D Z_j) captured as a CUDA graph
     bool graph_mode = false;   // set while capturing: coarse solves run as one cluster
@@ -297,6 +323,7 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
     if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
     if (p->outer_solver < 0 || p->outer_solver > 2) return fail(AMG_EINVAL, "outer_solver must be 0, 1 or 2");
+    if (p->sap_variant < -1 || p->sap_variant > 2) return fail(AMG_EINVAL, "sap_variant must be -1, 0, 1 or 2");
     if (p->sap_eo != 0 && p->sap_eo != 1) return fail(AMG_EINVAL, "sap_eo must be 0 or 1");
     if (p->sap_eo) {
         BlockH b0;
@@ -354,8 +381,15 @@ CoarseLevel& L1(amg_hierarchy* h) { return h->lev[1]; }
 // coarse_tol: one persistent cooperative launch per group of up to
 // coarse_solver_max_rhs() right-hand sides in lockstep (the operator streamed
 // once per stencil pass for the group), no host synchronisation.
+amg_status coarse_bicgstab_tc(amg_hierarchy* h, int l, const void* b, void* x, int nb, cudaStream_t s);
+bool bicgstab_mr_coefficients(const std::vector<std::vector<cplx>>& G, int ell, std::vector<cplx>& cxv,
+                              std::vector<cplx>& crv, std::vector<cplx>& cgv);
 amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int nb, cudaStream_t s) {
     CoarseLevel& L = h->lev[l];
+    // batches on a bfloat16 coarsest level: the stencil passes on the tensor cores
+    if (h->p.coarse_tc && nb >= 2 && !h->graph_mode && L.opbf && L.prec == 1 && coarse_tc_supported(L.nc) &&
+        nb <= 16 && L.tci.p)
+        return coarse_bicgstab_tc(h, l, b, x, nb, s);
     const int ell = h->p.coarse_ell;
     auto& w = h->cw[l];   // [0] bc, [1] xc (nb vectors each), [2] rt, [3..3+ell] R, [4+ell..4+2ell] U
     void* R[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -375,6 +409,131 @@ amg_status coarse_bicgstab(amg_hierarchy* h, int l, const void* b, void* x, int 
         // error word of this launch (a later one would overwrite it): fold into word 2 of the host mirror
         CK(cudaMemcpyAsync(h->hstate + 4 * (k % 16), L.cs_state.p, 16, cudaMemcpyDeviceToHost, s));
     }
+    return AMG_OK;
+}
+
+// BiCGStab(l) (Sleijpen-Fokkema) in lockstep over a batch of nb right-hand sides on a
+// coarsest level stored in bfloat16, every stencil pass on the tensor cores: one
+// launch_coarse_apply_tc for the whole batch (bfloat16 operands, FP32 accumulation in tensor
+// memory).  The vector updates run on the FP32 pipe, the per-RHS scalars on the host (one
+// synchronisation per reduction for the batch); each right-hand side keeps its own scalars and
+// stopping test and is frozen once it has converged.  The MMA rounds the vectors to bfloat16
+// (reading C18), so the recursive residual drifts from the true one by ~1e-3: the coarse
+// tolerance of 1e-2 stays reachable.
+amg_status coarse_bicgstab_tc(amg_hierarchy* h, int l, const void* b, void* x, int nb, cudaStream_t s) {
+    CoarseLevel& L = h->lev[l];
+    const int ell = h->p.coarse_ell;
+    const size_t n = coarse_n(L), vb = n * sizeof(float2);
+    while ((int)L.tcw.size() < 2 * ell + 3) L.tcw.emplace_back();
+    for (auto& v : L.tcw) CK(v.ensure(vb * nb));
+    CK(L.tcx.ensure(coarse_tc_pack_bytes(L.g.V, L.nc)));
+    CK(L.tcerr.ensure(sizeof(int)));
+    CK(cudaMemsetAsync(L.tcerr.p, 0, sizeof(int), s));
+    void* rt = L.tcw[0].p;
+    std::vector<void*> R(ell + 1), U(ell + 1);
+    for (int j = 0; j <= ell; ++j) {
+        R[j] = L.tcw[1 + j].p;
+        U[j] = L.tcw[2 + ell + j].p;
+    }
+    auto F = [&](const void* base, int r) { return (char*)base + r * vb; };
+    const double2 one = make_double2(1, 0);
+    Reducer& red = h->red;
+    TRY(red.init(std::max(nb, 2)));
+    CK(cudaMemsetAsync(x, 0, vb * nb, s));
+    CK(cudaMemsetAsync(U[0], 0, vb * nb, s));
+    CK(cudaMemcpyAsync(R[0], b, vb * nb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(rt, b, vb * nb, cudaMemcpyDeviceToDevice, s));
+    std::vector<cplx> rho0(nb, 1.0), rho1(nb, 0.0), alpha(nb, 0.0), omega(nb, 1.0);
+    std::vector<double> bn2(nb, -1.0);
+    std::vector<char> act(nb, 1);
+    auto stencil = [&](const void* in, void* out) -> amg_status {
+        CK(launch_coarse_apply_tc(L.g, L.nc, L.tci.p, in, out, nullptr, nb, L.tcx.p, L.tcerr.as<int>(), s));
+        return AMG_OK;
+    };
+    int cycle = 0;
+    for (;; ++cycle) {
+        // |R_0|^2 and <r~, R_0> per right-hand side
+        std::vector<cplx> q(2 * nb);
+        {
+            const void* a2[2] = {R[0], rt};
+            TRY(red.batch_dots(1, nb, 2, a2, R[0], n, n, q.data(), s));
+        }
+        bool any = false;
+        for (int r = 0; r < nb; ++r) {
+            if (!act[r]) continue;
+            const double rn2 = q[2 * r].real();
+            if (bn2[r] < 0) bn2[r] = rn2;
+            if (!std::isfinite(rn2)) return fail(AMG_NAN, "coarse solver: non-finite residual");
+            if (rn2 <= h->p.coarse_tol * h->p.coarse_tol * bn2[r] || cycle >= h->p.coarse_maxit) {
+                act[r] = 0;
+                continue;
+            }
+            any = true;
+            rho1[r] = q[2 * r + 1];
+            rho0[r] = -omega[r] * rho0[r];
+        }
+        if (!any) break;
+        for (int j = 0; j < ell; ++j) {
+            for (int r = 0; r < nb; ++r) {
+                if (!act[r]) continue;
+                const cplx beta = alpha[r] * rho1[r] / rho0[r];
+                rho0[r] = rho1[r];
+                for (int i = 0; i <= j; ++i) CK(launch_axpby(1, one, F(R[i], r), d2(-beta), F(U[i], r), n, s));
+            }
+            TRY(stencil(U[j], U[j + 1]));
+            std::vector<cplx> gam(nb);
+            {
+                const void* a1[1] = {rt};
+                TRY(red.batch_dots(1, nb, 1, a1, U[j + 1], n, n, gam.data(), s));
+            }
+            for (int r = 0; r < nb; ++r) {
+                if (!act[r]) continue;
+                alpha[r] = rho0[r] / gam[r];
+                if (!std::isfinite(alpha[r].real()) || !std::isfinite(alpha[r].imag()))
+                    return fail(AMG_NAN, "coarse solver: BiCGStab breakdown");
+                for (int i = 0; i <= j; ++i) CK(launch_axpby(1, d2(-alpha[r]), F(U[i + 1], r), one, F(R[i], r), n, s));
+                CK(launch_axpby(1, d2(alpha[r]), F(U[0], r), one, F(x, r), n, s));
+            }
+            TRY(stencil(R[j], R[j + 1]));
+            if (j + 1 < ell) {
+                std::vector<cplx> r1(nb);
+                const void* a1[1] = {rt};
+                TRY(red.batch_dots(1, nb, 1, a1, R[j + 1], n, n, r1.data(), s));
+                for (int r = 0; r < nb; ++r)
+                    if (act[r]) rho1[r] = r1[r];
+            }
+        }
+        // Gram matrices G_pq = <R_p, R_q> of every right-hand side, then the minimal-residual part
+        std::vector<cplx> gm((size_t)nb * (ell + 1) * (ell + 1));
+        for (int qq = 0; qq <= ell; ++qq) {
+            std::vector<cplx> row((size_t)nb * (ell + 1));
+            std::vector<const void*> al(R.begin(), R.end());
+            TRY(red.batch_dots(1, nb, ell + 1, al.data(), R[qq], n, n, row.data(), s));
+            for (int r = 0; r < nb; ++r)
+                for (int p = 0; p <= ell; ++p) gm[((size_t)r * (ell + 1) + p) * (ell + 1) + qq] = row[r * (ell + 1) + p];
+        }
+        for (int r = 0; r < nb; ++r) {
+            if (!act[r]) continue;
+            std::vector<std::vector<cplx>> G(ell + 1, std::vector<cplx>(ell + 1));
+            for (int p = 0; p <= ell; ++p)
+                for (int qq = 0; qq <= ell; ++qq) G[p][qq] = gm[((size_t)r * (ell + 1) + p) * (ell + 1) + qq];
+            std::vector<cplx> cxv, crv, cgv;
+            if (!bicgstab_mr_coefficients(G, ell, cxv, crv, cgv))
+                return fail(AMG_NAN, "coarse solver: BiCGStab breakdown");
+            omega[r] = cgv[ell];
+            CK(launch_axpby(1, d2(cxv[0]), F(R[0], r), one, F(x, r), n, s));
+            for (int k = 1; k <= ell; ++k) {
+                CK(launch_axpby(1, d2(cxv[k]), F(R[k], r), one, F(x, r), n, s));
+                CK(launch_axpby(1, d2(-crv[k]), F(R[k], r), one, F(R[0], r), n, s));
+                CK(launch_axpby(1, d2(-cgv[k]), F(U[k], r), one, F(U[0], r), n, s));
+            }
+        }
+    }
+    int terr = 0;
+    CK(cudaMemcpyAsync(&terr, L.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (terr) return fail(AMG_TIMEOUT, "tensor-core coarse stencil: a bounded wait gave up");
+    h->tc_cycles += cycle;
     return AMG_OK;
 }
 
@@ -1035,9 +1194,12 @@ amg_status alloc_workspaces(amg_hierarchy* h, int nb) {
         h->gs_cap = nb;
     }
     CK(h->err_flag.ensure(sizeof(int)));
+    // the batch runs its cycle in the smoother precision and its relaxed products in FP32; the
+    // other precisions need one field each (conversions, the autotuner)
     for (int pr = 0; pr < 3; ++pr) {
-        CK(h->fb[pr].ensure(fine_spinor_bytes(pr, g.V) * nb));
-        CK(h->fx[pr].ensure(fine_spinor_bytes(pr, g.V) * nb));
+        const int nf = (pr == h->fp || pr == 1) ? nb : 1;
+        CK(h->fb[pr].ensure(fine_spinor_bytes(pr, g.V) * nf));
+        CK(h->fx[pr].ensure(fine_spinor_bytes(pr, g.V) * nf));
     }
     CK(h->tmpv.ensure(fine_spinor_bytes(h->vp, g.V)));
     if (!h->hstate) {
@@ -1264,9 +1426,14 @@ amg_status tune_kernels(amg_hierarchy* h) {
     int precs[2] = {h->fp, h->vp};
     for (int pr : precs) {
         const bool staged = sap_staged_supported(pr, h->blk[0]);
-        if (h->p.sap_variant >= 0 || !staged) {
-            h->sap_variant[pr] = h->sap_variant_nb[pr] = staged ? h->p.sap_variant : 0;
-            if (h->sap_variant[pr] < 0) h->sap_variant[pr] = h->sap_variant_nb[pr] = 0;
+        if (h->p.sap_variant >= 0) {
+            // variant 2 (two right-hand sides per CTA) only differs from 0 for batches
+            h->sap_variant[pr] = h->p.sap_variant == 2 ? 0 : h->p.sap_variant;
+            h->sap_variant_nb[pr] = h->p.sap_variant;
+            if (!staged) {
+                if (h->sap_variant[pr] == 1) h->sap_variant[pr] = 0;
+                if (h->sap_variant_nb[pr] == 1) h->sap_variant_nb[pr] = 0;
+            }
             continue;
         }
         const size_t fb = fine_spinor_bytes(pr, g.V);
@@ -1279,9 +1446,14 @@ amg_status tune_kernels(amg_hierarchy* h) {
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         for (int nrhs : {1, 3}) {
-            std::vector<float> t[2];
+            // candidates: 0 operator through L1/L2, 1 staged (if the blocking allows), and for
+            // batches 2 (two right-hand sides per CTA through L1)
+            std::vector<int> vs = {0};
+            if (staged) vs.push_back(1);
+            if (nrhs > 1) vs.push_back(2);
+            std::vector<float> t[3];
             for (int rep = 0; rep < 10; ++rep) {
-                for (int v = 0; v <= 1; ++v) {
+                for (int v : vs) {
                     CK(cudaEventRecord(e0, 0));
                     for (int colour = 0; colour < 2; ++colour)
                         CK(launch_sap_half_variant(v, pr, g, h->blk[0], colour, h->p.mr_iters, 0, d->gauge->U[pr].p,
@@ -1293,8 +1465,15 @@ amg_status tune_kernels(amg_hierarchy* h) {
                     if (rep > 0) t[v].push_back(ms);
                 }
             }
-            for (auto& tv : t) std::sort(tv.begin(), tv.end());
-            const int best_v = t[1][t[1].size() / 2] < t[0][t[0].size() / 2] ? 1 : 0;
+            int best_v = 0;
+            float best_t = 1e30f;
+            for (int v : vs) {
+                std::sort(t[v].begin(), t[v].end());
+                if (t[v][t[v].size() / 2] < best_t) {
+                    best_t = t[v][t[v].size() / 2];
+                    best_v = v;
+                }
+            }
             (nrhs == 1 ? h->sap_variant : h->sap_variant_nb)[pr] = best_v;
         }
         cudaEventDestroy(e0);
@@ -1307,13 +1486,13 @@ amg_status tune_kernels(amg_hierarchy* h) {
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         for (int pr : {h->fp, 0}) {
-            const int cand[][2] = {{256, 16}, {128, 16}, {256, 4}, {256, 64}, {128, 8}, {128, 64}};
+            const int cand[][2] = {{256, 16}, {128, 16}, {256, 4}, {128, 64}};
             float best = 1e30f;
             int bt = 256, bs = 16;
             for (const auto& c : cand) {
                 dirac_set_shape(pr, c[0], c[1]);
                 std::vector<float> t;
-                for (int rep = 0; rep < 4; ++rep) {
+                for (int rep = 0; rep < 3; ++rep) {
                     CK(cudaEventRecord(e0, 0));
                     CK(launch_dirac(pr, g, nullptr, d->gauge->U[pr].p, d->C[pr].p, h->fx[pr].p, h->fb[pr].p, nullptr,
                                     d->kappa, 1, 0));
@@ -1807,6 +1986,7 @@ void amg_params_default(amg_params* p) {
     p->mbicgs_tol = 1e-4;
     p->mbicgs_maxit = 50;
     p->sap_eo = 0;
+    p->coarse_tc = 0;
 }
 
 
@@ -2014,6 +2194,7 @@ amg_status amg_setup_from_vectors(amg_dirac* d, const amg_params* p, const doubl
     }
     if (st == AMG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(AMG_ECUDA, "setup failed");
     if (st == AMG_OK) st = tune_coarse_tile(h);
+    if (st == AMG_OK && h->rp == 2) h->vecs0.release();   // the solves read the half-precision copy
     if (st != AMG_OK) {
         delete h;
         return st;
@@ -2072,6 +2253,7 @@ amg_status amg_setup(amg_dirac* d, const amg_params* p, const double* const* ini
         h->vecs_next.release();
         h->tmpg.release();
         TRY(tune_coarse_tile(h));
+        if (h->rp == 2) h->vecs0.release();   // the solves read the half-precision copy
         CK(cudaStreamSynchronize(s));
         return AMG_OK;
     };
@@ -2109,12 +2291,19 @@ amg_status amg_get_vectors(amg_hierarchy* h, int coarsening, double* host_out) {
         return AMG_OK;
     }
     const GeomH& g = fine_geom(h);
-    const size_t vb = fine_spinor_bytes(h->vp, g.V);
     const size_t cb = (size_t)g.V * 24 * sizeof(double);
     CK(h->canon.ensure(cb));
+    // after a setup with half-precision transfer vectors only their copy remains (the FP32
+    // vectors held exactly the rounded values)
+    const bool from16 = !h->vecs0.p && h->rp == 2;
+    const int vprec = from16 ? 2 : h->vp;
+    const size_t vb = fine_spinor_bytes(vprec, g.V);
     for (int i = 0; i < h->p.nvec[0]; ++i) {
-        const void* vi = (const char*)h->vecs0.p + i * vb;
-        if (h->vp == 0) {
+        const void* vi = (const char*)(from16 ? h->vecs16.p : h->vecs0.p) + i * vb;
+        if (from16) {
+            CK(launch_convert_spinor(2, 0, g, vi, h->fb[0].p, 1, 0));
+            CK(launch_unpack_spinor(0, g, h->fb[0].p, h->canon.p, 1, 0));
+        } else if (h->vp == 0) {
             CK(launch_unpack_spinor(0, g, vi, h->canon.p, 1, 0));
         } else {
             CK(launch_convert_spinor(1, 0, g, vi, h->fb[0].p, 1, 0));
@@ -2336,6 +2525,8 @@ amg_status amg_sap(amg_hierarchy* h, const void* b, void* x, int nrhs, amg_prec 
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
     if (nrhs > h->nb_cap) TRY(alloc_workspaces(h, nrhs));
+    CK(h->fb[prec].ensure(fine_spinor_bytes(prec, g.V) * nrhs));
+    CK(h->fx[prec].ensure(fine_spinor_bytes(prec, g.V) * nrhs));
     CK(launch_pack_spinor(prec, g, b, h->fb[prec].p, nrhs, st));
     TRY(fine_sap(h, prec, h->fb[prec].p, h->fx[prec].p, true, nrhs, st));
     CK(launch_unpack_spinor(prec, g, h->fx[prec].p, x, nrhs, st));
@@ -2403,7 +2594,8 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     {
         const size_t f64 = fine_spinor_bytes(0, g.V), fz = fine_spinor_bytes(zprec_of(h), g.V);
         size_t per = f64 * (h->p.outer_m + 1 + 4) + fz * h->p.outer_m;
-        for (int pr = 0; pr < 3; ++pr) per += 2 * fine_spinor_bytes(pr, g.V);
+        for (int pr = 0; pr < 3; ++pr)
+            if (pr == h->fp || pr == 1) per += 2 * fine_spinor_bytes(pr, g.V);
         size_t have = 0, total = 0;
         if (cudaMemGetInfo(&have, &total) == cudaSuccess) {
             // memory the current batch capacity already holds counts as available
@@ -2425,6 +2617,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         TRY(alloc_workspaces(h, nb));
         for (int l = 1; l < h->p.nlevels; ++l) CK(cudaMemsetAsync(h->lev[l].cs_state.p, 0, 16, st));
         std::memset(h->hstate, 0, 16 * 16);
+        h->tc_cycles = 0;
         const double* br = b + (size_t)r0 * g.V * 24;
         double* xr = x + (size_t)r0 * g.V * 24;
         CK(launch_pack_spinor(0, g, br, h->ob.p, nb, st));
@@ -2452,7 +2645,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         CK(cudaMemcpyAsync(h->hstate + 60, h->lev[h->p.nlevels - 1].cs_state.p, 16, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         TRY(coarse_status(h));
-        h->coarse_cycles = h->hstate[63];
+        h->coarse_cycles = h->hstate[63] + h->tc_cycles;
         if (rs == AMG_NOT_CONVERGED) worst = rs;
         for (auto& i : infos) {
             agg.iters = std::max(agg.iters, i.iters);

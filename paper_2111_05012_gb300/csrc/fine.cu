@@ -673,22 +673,27 @@ __global__ void clover_invert_kernel(Geom g, const void* C64, void* out) {
 // iterate elsewhere (first odd half sweep after an even sweep from zero).
 // 256-thread FP32/FP16 variant: 128 registers, two CTAs per SM (no spills);
 // the FP64 variant keeps one CTA per SM (it would spill at 128 registers)
-template <class P, int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode,
+// NR right-hand sides per CTA (NR = 2 for batches, variant 2): thread (slot, l) works on site l
+// for right-hand side NR * (pair index) + slot; both slots read the same domain's links and
+// clover in lockstep, so one domain's operator occupies the SM's L1 instead of two domains'.
+template <class P, int MAXT, int NR>
+__global__ void __launch_bounds__(MAXT * NR, (MAXT == 256 && NR == 1 && P::id != 0) ? 2 : 1) sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode,
                                                         const void* __restrict__ U, const void* __restrict__ C,
                                                         const void* __restrict__ b, void* x, typename P::T kappa,
-                                                        int rhs_fast) {
+                                                        int rhs_fast, int nrhs) {
     using T = typename P::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int vbp = blockDim.x;
-    cx<T>* rsh = reinterpret_cast<cx<T>*>(smem_raw);          // [12][vbp]
-    T* red = reinterpret_cast<T*>(rsh + 12 * vbp);             // [2][3][32]
+    const int vbp = blockDim.x / NR;
+    const int slot = NR == 1 ? 0 : threadIdx.x / vbp;
+    cx<T>* rsh = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)slot * 12 * vbp;      // [NR][12][vbp]
+    T* red = reinterpret_cast<T*>(reinterpret_cast<cx<T>*>(smem_raw) + (size_t)NR * 12 * vbp) + slot * 192;   // [NR][2][3][32]
 
-    // domain of this CTA: the k-th domain of the given colour; right-hand side r of a batch.
-    // rhs_fast: r is the fast grid index, so the CTAs of one domain for all right-hand sides
-    // run together and share the domain's links and clover in L1/L2
+    // domain of this CTA: the k-th domain of the given colour; right-hand side rr of a batch.
+    // rhs_fast: the right-hand side is the fast grid index, so the CTAs of one domain for all
+    // right-hand sides run together and share the domain's links and clover in L1/L2
     const int k = rhs_fast ? blockIdx.y : blockIdx.x;
-    const int rr = rhs_fast ? blockIdx.x : blockIdx.y;
+    const int rr = NR * (rhs_fast ? blockIdx.x : blockIdx.y) + slot;
+    const bool rhs_ok = rr < nrhs;
     const int h0 = bk.C[0] / 2;
     int rest = k / h0;
     int X1 = rest % bk.C[1];
@@ -698,13 +703,13 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
     int X0 = 2 * (k % h0) + ((X1 + X2 + X3 + colour) & 1);
     const int Xi = X0 + bk.C[0] * (X1 + bk.C[1] * (X2 + bk.C[2] * X3));
 
-    const int l = threadIdx.x;
-    const bool active = l < bk.Vb;
+    const int l = threadIdx.x - slot * vbp;
+    const bool active = l < bk.Vb && rhs_ok;
     int c[4] = {0, 0, 0, 0}, lc[4] = {0, 0, 0, 0}, s = 0;
     const int lstr[4] = {1, bk.b[0], bk.b[0] * bk.b[1], bk.b[0] * bk.b[1] * bk.b[2]};
     cx<T> r[12], z[12], Ar[12];
-    b = (const char*)b + rr * spinor_bytes<P>(g.V);
-    x = (char*)x + rr * spinor_bytes<P>(g.V);
+    b = (const char*)b + (rhs_ok ? rr : 0) * spinor_bytes<P>(g.V);
+    x = (char*)x + (rhs_ok ? rr : 0) * spinor_bytes<P>(g.V);
     if (active) {
         s = block_site(g, bk, Xi, l, c);
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
@@ -775,7 +780,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT == 256 && P::id != 0) ? 2 : 1) sap
         // one-barrier block reduction into buffer (it & 1): the loop's top barrier keeps the
         // other buffer's readers of the previous step apart from its next writers
         {
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+            const int lane = l & 31, warp = l >> 5, nw = (vbp + 31) >> 5;
             T* rb = red + (it & 1) * 96;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -1255,28 +1260,41 @@ cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, 
 
 template <class P>
 cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
-                          const void* C, const void* b, void* x, double kappa, int nrhs, cudaStream_t st) {
+                          const void* C, const void* b, void* x, double kappa, int nrhs, cudaStream_t st,
+                          bool pair = false) {
     Geom g = make_geom(gh);
     Blocking bk = make_blocking(gh, bh);
     int threads = (bk.Vb + 31) / 32 * 32;
     if (threads > 512) return cudaErrorInvalidValue;
-    size_t smem = (size_t)12 * threads * sizeof(cx<typename P::T>) + 2 * 3 * 32 * sizeof(typename P::T);
+    // two right-hand sides per CTA (variant 2, batches, FP32/FP16, blocks of <= 256 sites)
+    const int nr = (pair && nrhs > 1 && threads <= 256 && P::id != 0) ? 2 : 1;
+    size_t smem = (size_t)nr * 12 * threads * sizeof(cx<typename P::T>) + nr * 2 * 3 * 32 * sizeof(typename P::T);
     int ndom = bk.Vc / 2;
+    const int ngrp = (nrhs + nr - 1) / nr;
     // right-hand side as the fast grid index when the domains fit the y dimension
-    const int fast = nrhs > 1 && ndom <= 65535;
-    const dim3 grid = fast ? dim3(nrhs, ndom) : dim3(ndom, nrhs);
+    const int fast = ngrp > 1 && ndom <= 65535;
+    const dim3 grid = fast ? dim3(ngrp, ndom) : dim3(ndom, ngrp);
+    const typename P::T kp = (typename P::T)kappa;
+    if constexpr (P::id != 0) {
+        if (nr == 2) {
+            auto fn = sap_half_kernel<P, 256, 2>;
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            (note_launch(), fn<<<grid, 2 * threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x, kp, fast,
+                                                                 nrhs));
+            return cudaGetLastError();
+        }
+    }
     if (threads <= 256) {
-        cudaError_t e =
-            cudaFuncSetAttribute(sap_half_kernel<P, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto fn = sap_half_kernel<P, 256, 1>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        (note_launch(), sap_half_kernel<P, 256><<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                         (typename P::T)kappa, fast));
+        (note_launch(), fn<<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x, kp, fast, nrhs));
     } else {
-        cudaError_t e =
-            cudaFuncSetAttribute(sap_half_kernel<P, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto fn = sap_half_kernel<P, 512, 1>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        (note_launch(), sap_half_kernel<P, 512><<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x,
-                                                                         (typename P::T)kappa, fast));
+        (note_launch(), fn<<<grid, threads, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x, kp, fast, nrhs));
     }
     return cudaGetLastError();
 }
@@ -1525,9 +1543,10 @@ cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const
         return sap_half_staged_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
     if (variant == 1 && prec == 2)
         return sap_half_staged_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
-    if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
-    if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
-    return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st);
+    const bool pair = variant == 2;
+    if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st, pair);
+    if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st, pair);
+    return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st, pair);
 }
 bool sap_staged_supported(int prec, const BlockH& bk) {
     int vb = bk.b[0] * bk.b[1] * bk.b[2] * bk.b[3];

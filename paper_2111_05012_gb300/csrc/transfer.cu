@@ -240,13 +240,16 @@ __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __rest
 }
 
 // ------------------------------------------------------------ orthonormalisation
-// Per (block, chirality): Gram-Schmidt over i = 0..nvec-1 in index order, every
-// vector projected twice against the previous ones, in FP64.  Each projection
-// takes the coefficients <v_j, w> of all previous vectors in one pass (classical
-// form: per-warp sums into shared memory, one barrier, one cross-warp sum per
-// coefficient), then subtracts them in a second pass over the vectors; projected
-// twice, this gives the QR factor with a positive diagonal to rounding, the same
-// vectors as projecting one vector after another.
+// Per (block, chirality): Gram-Schmidt over i = 0..nvec-1 in index order against
+// the previous (orthonormal) vectors, in FP64.  Each projection takes the
+// coefficients <v_j, w> of all previous vectors in one pass (classical form:
+// per-warp sums into shared memory, one barrier, one cross-warp sum per
+// coefficient), then subtracts them in a second pass over the vectors.  A second
+// projection follows only if the first removed more than three quarters of
+// |w|^2: against an orthonormal set one projection leaves w orthogonal to about
+// eps |w0| / |w| <= 2 eps otherwise (the DGKS test).  Either way the result is
+// the QR factor with a positive diagonal to rounding, the vectors that
+// projecting one vector after another gives.
 template <class PV>
 __global__ void orthonormalise_kernel(Geom g, Blocking bk, int nvec, void* vecs, int* err) {
     __shared__ double red[3 * 32];
@@ -277,6 +280,12 @@ __global__ void orthonormalise_kernel(Geom g, Blocking bk, int nvec, void* vecs,
         for (int k = 0; k < 6; ++k) n0[0] += norm2(w[k]);
         block_sum<double, 1>(n0, red);
         for (int pass = 0; pass < 2 && i > 0; ++pass) {
+            if (pass == 1) {   // a second projection only after a large cancellation
+                double n1[1] = {0};
+                for (int k = 0; k < 6; ++k) n1[0] += norm2(w[k]);
+                block_sum<double, 1>(n1, red);
+                if (n1[0] > 0.25 * n0[0]) break;
+            }
             for (int j = 0; j < i; ++j) {
                 cx<double> q[6];
                 load_half(j, q);

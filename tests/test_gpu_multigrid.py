@@ -126,7 +126,7 @@ def test_bf16_coarse_operator(mgcase):
     c.amg_hierarchy_destroy(h)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_sap(mgcase, prec, variant):
     import torch
@@ -453,7 +453,7 @@ def test_mixed_precision_setup_is_orthonormal_and_galerkin(vec_prec):
     f.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1, "bf16"])
 def test_lockstep_coarse_solves_equal_single_solves(prec, variant):
     # the coarse BiCGStab(2) of a batch runs in lockstep (up to four right-hand sides per
@@ -562,5 +562,37 @@ def test_solve_with_even_odd_smoother(prec):
     for k in range(2):
         r = b[k].reshape(f.shape4 + (12,)) - op.apply(xs[k])
         assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1.05e-10
+    c.amg_hierarchy_destroy(h)
+    f.close()
+
+
+@pytest.mark.parametrize("nvec", [8, 24])
+def test_tensor_core_coarse_solve_in_a_batch(nvec):
+    # coarse_tc = 1: a batch on a bfloat16 coarsest level runs its BiCGStab(2) with every stencil
+    # pass on the tensor cores (tcgen05, bfloat16 vectors and operator, FP32 accumulation); the
+    # outer solve still reaches the FP64 tolerance, and the solutions are those of the single
+    # solves (the persistent SIMT coarse solver) to the tolerance
+    import torch
+    dims = (8, 8, 8, 8)
+    f = Field(dims, 0.6, 2, 0.130, 1.0)
+    c = f.c
+    p = _params(c, (4, 4, 4, 4), nvec, 1, n_init=1, n_adapt=1, coarse_tc=1)
+    p.prec_coarsest = c.AMG_BF16
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 2, nvec))])
+    nb = 4
+    bs = np.stack([li.rhs(dims, 80 + k) for k in range(nb)])
+    B = to_dev(bs)
+    X = torch.zeros_like(B)
+    st, info = c.amg_solve(h, B, X, nb, 1e-10, 100)
+    assert info.converged == 1 and info.true_rel_residual <= 1e-10 and info.coarse_cycles > 0
+    op = odirac.WilsonClover(f.U, 0.130, 1.0)
+    n = f.V * 24
+    xs = from_dev(X, (nb,) + f.shape4 + (12,))
+    for k in range(nb):
+        r = bs[k].reshape(f.shape4 + (12,)) - op.apply(xs[k])
+        assert np.linalg.norm(r) / np.linalg.norm(bs[k]) <= 1.05e-10
+        xk = torch.zeros(n, dtype=torch.float64, device="cuda")
+        c.amg_solve(h, B[k * n:(k + 1) * n].contiguous(), xk, 1, 1e-10, 100)
+        assert rel(from_dev(xk, f.shape4 + (12,)), xs[k]) < 1e-8
     c.amg_hierarchy_destroy(h)
     f.close()
