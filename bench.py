@@ -5,9 +5,10 @@ Headline workload (the largest single-GPU configuration; synthetic stand-in
 for the paper's gauge ensembles): a 48^3 x 96 lattice, links exp(0.5 i H)
 (seed 4), kappa = 0.129, c_sw = 1.0, antiperiodic in t; the 12 spin-colour
 point sources at the origin; two-level multigrid with 4^4 blocks and 24 test
-vectors (48 chiral), FP32 smoother and coarse operator, test vectors stored
-in half precision with a per-site scale for restriction and prolongation,
-FP64 outer flexible GMRES(8).  The gauge field and the initial test vectors
+vectors (48 chiral), FP32 smoother, bfloat16 coarse operator whose batched
+coarse solves run their stencil on the tensor cores, test vectors stored in
+half precision with a per-site scale for restriction and prolongation, FP64
+outer flexible GMRES(8).  The gauge field and the initial test vectors
 are drawn on the device by the library's counter-based generator.
 One step = one call of amg_solve on all 12 sources (x = 0 each time).  The
 setup (test vectors, Galerkin operator) runs once before the timed region and
@@ -43,7 +44,8 @@ PROP_CONFIG = {
                 "(n_init 3, n_adapt 2), SAP(4) x MR(6) smoother, BiCGStab(2) coarse solve to 1e-2, "
                 "FP64 outer flexible GMRES(8) to a true residual of 1e-10",
     "lattice": [48, 48, 48, 96], "rhs_per_step": 12,
-    "precision": "FP32 smoother and coarse operator, FP16 test vectors (per-site scale) in restriction and "
+    "precision": "FP32 smoother, bfloat16 coarse operator with the batched coarse solves' stencil on the tensor "
+                 "cores (tcgen05, FP32 accumulation), FP16 test vectors (per-site scale) in restriction and "
                  "prolongation, FP64 outer solver",
     "l2": "working set > L2 (no flush)",
 }
@@ -331,7 +333,7 @@ def run_headline(args):
         p.mr_iters = args.mr
     if args.prop_coarse == "bf16":
         p.prec_coarsest = capi.AMG_BF16
-        p.coarse_tc = 1 if args.coarse_tc else 0
+        p.coarse_tc = 0 if args.no_coarse_tc else 1
     t0 = time.perf_counter()
     h = capi.amg_setup(d, p, [init])
     torch.cuda.synchronize()
@@ -419,13 +421,27 @@ def run_headline(args):
                                  "frac_hbm": 672 * V / (ms_d * 1e-3) / 1e9 / hbm}
     cdims, nc = capi.amg_level_info(h, 1)
     vc = int(np.prod(cdims))
-    xc = torch.randn(vc * nc * 2, dtype=torch.float32, device="cuda")
+    xc = torch.randn(4 * vc * nc * 2, dtype=torch.float32, device="cuda")
+    bf = p.prec_coarsest == capi.AMG_BF16
     capi.amg_coarse_time(h, 1, xc, 1, capi.AMG_F32, 3, stream=stream)
     ms_c = capi.amg_coarse_time(h, 1, xc, 1, capi.AMG_F32, 10, stream=stream)
-    cbytes = vc * (9 * nc * nc * 8 + 2 * nc * 8)
-    kern["coarse_apply_kernel<F32>"] = {"ms": ms_c, "coarse_sites": vc, "nc": nc, "bytes": cbytes,
-                                        "gb_per_s": cbytes / (ms_c * 1e-3) / 1e9,
-                                        "frac_hbm": cbytes / (ms_c * 1e-3) / 1e9 / hbm}
+    cbytes = vc * (9 * nc * nc * (4 if bf else 8) + 2 * nc * 8)
+    kern["coarse_apply_kernel<%s>" % ("BF16 operator, FP32 vectors" if bf else "F32")] = {
+        "ms": ms_c, "coarse_sites": vc, "nc": nc, "bytes": cbytes, "gb_per_s": cbytes / (ms_c * 1e-3) / 1e9,
+        "frac_hbm": cbytes / (ms_c * 1e-3) / 1e9 / hbm}
+    if bf:
+        # the tensor-core stencil over a lockstep group of four right-hand sides (as the batched coarse
+        # solves run it): operand image 2Nc x 9Nc bfloat16 per coarse site + the vectors in and out;
+        # useful work 8 * 9 * Nc^2 flop per site and right-hand side against the measured bf16 peak
+        bf_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+        capi.amg_coarse_time(h, 1, xc, 4, capi.AMG_BF16, 3, stream=stream)
+        ms_t = capi.amg_coarse_time(h, 1, xc, 4, capi.AMG_BF16, 10, stream=stream)
+        tbytes = vc * (2 * nc * 9 * nc * 2 + 2 * 4 * nc * 8)
+        tflops = 8.0 * 9 * nc * nc * 4 * vc / (ms_t * 1e-3) / 1e12
+        kern["coarse_tc_kernel (4 RHS)"] = {"ms": ms_t, "bytes": tbytes, "gb_per_s": tbytes / (ms_t * 1e-3) / 1e9,
+                                            "frac_hbm": tbytes / (ms_t * 1e-3) / 1e9 / hbm,
+                                            "useful_tflops": tflops, "frac_bf16_peak": tflops / bf_peak}
     del x32, xc
     line = {
         "metric": METRIC, "value": per_rhs, "unit": "ms/RHS", "n_gpus": world, "steps": args.steps,
@@ -1026,10 +1042,10 @@ def main():
     ap.add_argument("--workload", default="propagator",
                     choices=["propagator", "solve16", "learned", "dirac", "mixed3", "ragged", "coarse_tc"])
     ap.add_argument("--pairs", type=int, default=4096)
-    ap.add_argument("--prop-coarse", default="f32", choices=["f32", "bf16"],
-                    help="propagator: coarsest operator storage (bf16: bfloat16 entries)")
-    ap.add_argument("--coarse-tc", action="store_true",
-                    help="propagator with --prop-coarse bf16: batched coarse solves with the stencil on the tensor cores")
+    ap.add_argument("--prop-coarse", default="bf16", choices=["f32", "bf16"],
+                    help="propagator: coarsest operator storage (bf16, the default: bfloat16 entries)")
+    ap.add_argument("--no-coarse-tc", action="store_true",
+                    help="propagator with bf16: batched coarse solves on the SIMT solver instead of the tensor cores")
     ap.add_argument("--sap-eo", action="store_true",
                     help="propagator: even-odd (Schur complement) SAP domain solves")
     ap.add_argument("--mr", type=int, default=None, help="propagator: minimal-residual steps per domain solve")
