@@ -712,8 +712,10 @@ def run_ragged(args):
     100 + i) on 8^4 (4^4 blocks), 12^4 (3^4 blocks) or 16^3x32 (4^4 blocks)
     for i % 3 = 0, 1, 2; links exp(0.6iH), kappa 0.130, c_sw 1.0, 24 test
     vectors, FP32 smoother.  The initial test vectors are drawn once per
-    lattice size.  One amg_solve_ragged call (graphs captured in a warm-up
-    call on other right-hand sides) against the same 64 solves issued one
+    lattice size.  One amg_solve_ragged call in its fused form (one launch
+    per phase of an Arnoldi step over per-problem descriptors; a warm-up call
+    on other right-hand sides first) against the same batch on the stream
+    pool with per-problem step graphs, and the same 64 solves issued one
     after another through amg_solve."""
     import torch
     import __graft_entry__
@@ -755,6 +757,19 @@ def run_ragged(args):
         ragged_ms = (time.perf_counter() - t0) * 1e3
         launches = capi.amg_launch_count() - l0
     ok = all(i.converged == 1 and i.true_rel_residual <= TOL for i in infos)
+    # the same batch on the stream pool with per-problem step graphs (the unfused form)
+    capi.amg_set_ragged_fusion(False)
+    capi.amg_solve_ragged(hs, warm_b, [torch.zeros_like(b) for b in warm_b], TOL, 300)   # captures the graphs
+    Xp = [torch.zeros_like(b) for b in B]
+    torch.cuda.synchronize()
+    lp0 = capi.amg_launch_count()
+    t0 = time.perf_counter()
+    st, infos_pool = capi.amg_solve_ragged(hs, B, Xp, TOL, 300, stream=stream)
+    torch.cuda.synchronize()
+    pool_ms = (time.perf_counter() - t0) * 1e3
+    pool_launches = capi.amg_launch_count() - lp0
+    capi.amg_set_ragged_fusion(True)
+    del Xp
     # the same solves one after another
     for x in X:
         x.zero_()
@@ -797,9 +812,13 @@ def run_ragged(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "ragged batch of 64 single-RHS solves on 8^4 / 12^4 / 16^3x32 (gauge seeds "
                                    "100-163, exp(0.6iH), kappa 0.130, csw 1.0), 2-level AMG, 24 test vectors, "
-                                   "FP32 smoother, lockstep FGMRES(16) on 16 streams with CUDA-graph steps",
+                                   "FP32 smoother, lockstep FGMRES(16), one launch per phase over per-problem "
+                                   "descriptors",
                        "problems": n, "total_sites": sites, "setup_s": setup_s, "converged": ok,
                        "ragged_ms": ragged_ms, "sequential_ms": seq_ms, "sequential_converged": all(seq),
+                       "stream_pool_ms": pool_ms, "stream_pool_launches": pool_launches,
+                       "stream_pool_converged": all(i.converged == 1 for i in infos_pool),
+                       "speedup_vs_stream_pool": pool_ms / ragged_ms,
                        "speedup_vs_sequential": seq_ms / ragged_ms, "plain_fp64_sequential_sample": fp64,
                        "outer_iters": [int(i.iters) for i in infos]},
             "gpu_launches": launches, "clocks": clk.summary()}

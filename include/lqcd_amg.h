@@ -369,17 +369,26 @@ amg_status amg_precondition(amg_hierarchy* h, const double* b, double* x, amg_st
  * two-grid hierarchy; no hierarchy twice, none with a learned correction)
  * solved to ||b_i - D_i x_i|| <= tol ||b_i|| in FP64 from x_i = 0, as
  * amg_solve does for one right-hand side.  The problems' outer flexible
- * GMRES steps run in lockstep on a pool of up to 16 streams with one host
- * synchronisation per phase for all of them; each problem's preconditioner
- * and Arnoldi product of step j are captured into a CUDA graph on first use
- * (kept in the hierarchy until its workspaces grow or its learned correction
- * changes) and replayed; the coarse BiCGStab(l) then runs as one
- * thread-block cluster per problem.  b[i], x[i]: canonical double device
- * vectors of problem i.  infos (may be NULL) receives n records.  Ordered
- * after earlier work on stream s; synchronises.  No counterpart in the
- * paper (a batch of independent solves of Sec. 3). */
+ * GMRES steps run in lockstep with one host synchronisation per step for all
+ * of them.  Fused form (the default, when every problem has an FP32
+ * smoother, FP32 coarse vectors, the same coarse operator storage, test-vector
+ * precision, sap_iters and mr_iters, blocks of at most 256 sites and
+ * outer_m <= 19): each phase of an Arnoldi step -- the FP64 -> FP32 copy of
+ * V_j, restriction, the coarse BiCGStab(l) (one thread-block cluster per
+ * problem), prolongation, each SAP half sweep, the Arnoldi product and the
+ * Gram-Schmidt pass -- is one kernel launch over a table of per-problem
+ * descriptors, whatever n is.  Otherwise (or after amg_set_ragged_fusion(0))
+ * each problem's step runs on a pool of up to 16 streams, captured into a
+ * CUDA graph on first use (kept in the hierarchy until its workspaces grow
+ * or its learned correction changes) and replayed.  b[i], x[i]: canonical
+ * double device vectors of problem i.  infos (may be NULL) receives n
+ * records.  Ordered after earlier work on stream s; synchronises.  No
+ * counterpart in the paper (a batch of independent solves of Sec. 3). */
 amg_status amg_solve_ragged(amg_hierarchy* const* h, const double* const* b, double* const* x, int n, double tol,
                             int maxit, amg_solve_info* infos, amg_stream s);
+/* Process-wide switch of amg_solve_ragged between the fused form (on = 1, the
+ * default) and the stream pool (on = 0). */
+void amg_set_ragged_fusion(int on);
 
 /* ---- learned preconditioner -------------------------------------------- */
 /* The paper's preconditioner slot (Sec. 3 steps (1)-(2)) extended by a

@@ -129,6 +129,7 @@ PROTOTYPES = {
     "amg_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, ctypes.POINTER(amg_solve_info), _vp]),
     "amg_solve_ragged": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _d, _i,
                               ctypes.POINTER(amg_solve_info), _vp]),
+    "amg_set_ragged_fusion": (None, [_i]),
     "amg_nn_create": (_i, [_vp, _i, _ip, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
     "amg_nn_destroy": (None, [_vp]),
     "amg_nn_get_weights": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_float)]),
@@ -389,6 +390,10 @@ def amg_solve(h, b, x, nrhs=1, tol=1e-10, maxit=500, use_x0=False, stream=None, 
     if st != AMG_OK and (st != AMG_NOT_CONVERGED or raise_on_nonconv):
         _check(st)
     return st, info
+
+
+def amg_set_ragged_fusion(on):
+    load().amg_set_ragged_fusion(1 if on else 0)
 
 
 def amg_solve_ragged(hs, bs, xs, tol=1e-10, maxit=500, stream=None, raise_on_nonconv=True):

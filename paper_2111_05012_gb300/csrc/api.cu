@@ -1775,6 +1775,11 @@ struct RaggedProb {
     cudaStream_t st = nullptr;
     RhsState r;
     bool started = false;   // true residual of x = 0 is b itself on the first cycle
+    int coarse_cycles = 0;  // coarsest-level cycles (fused batches)
+    // fused batches: the canonical vectors and the least-squares solution of the last cycle
+    const double* bcanon = nullptr;
+    double* xcanon = nullptr;
+    std::vector<double2> y;
 };
 
 // partial sums of the last reduction launched for problem p (k values)
@@ -1940,6 +1945,359 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
     return AMG_OK;
 }
 
+
+// ---------------------------------------------------------------- fused ragged batch
+// The same lockstep flexible GMRES with every phase of an Arnoldi step issued
+// as ONE launch for all active problems: a table of per-problem descriptors
+// (ragged_dev_fill) and per-phase prefix tables of CTA offsets split each grid
+// among the problems, so a problem of 4^4 sites and one of 16^3 x 32 share a
+// launch.  Per step: FP64 -> FP32 copy of V_j, restriction, the coarse
+// BiCGStab(l) (one thread-block cluster per problem in one launch), prolongation,
+// 2 sap_iters SAP half sweeps, the FP64-accurate Arnoldi product and a
+// classical Gram-Schmidt pass -- 2 sap_iters + 8 kernels for the whole batch,
+// whatever its size.  Used when every problem has an FP32 smoother, FP32
+// coarse vectors, the same coarse operator storage and test-vector precision,
+// blocks of at most 256 sites and outer_m < 20 (else the stream pool above).
+bool g_ragged_fused = true;   // amg_set_ragged_fusion
+
+struct FusedBatch {
+    enum { T_SITE, T_BLK, T_DOM, T_BLAS, NT };
+    static constexpr int kSlots = 4;   // host staging slots, reused in turn once their copy is done
+    size_t db = 0, sb = 0, slot_bytes = 0;
+    int cap = 0, next = 0;
+    DevBuf desc, off, cargs, cstate, coef;
+    char* hstage = nullptr;      // pinned: kSlots x (descriptors, offset tables)
+    cudaEvent_t ev[kSlots] = {};
+    char* hstate = nullptr;      // pinned: coarse solver state words, Gram-Schmidt coefficients,
+    double2* hcoef = nullptr;    // coarse solver arguments (rewritten once per step, after a sync)
+    void* hcargs = nullptr;
+    int max_vb = 0, max_nvec = 0;
+    ~FusedBatch() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        if (hstage) cudaFreeHost(hstage);
+        if (hstate) cudaFreeHost(hstate);
+        if (hcoef) cudaFreeHost(hcoef);
+        if (hcargs) cudaFreeHost(hcargs);
+    }
+    // two device regions of cap problems each: the step's active set (0), and the sets of the
+    // restart phases and of a second Gram-Schmidt pass (1)
+    amg_status alloc(int n) {
+        db = ragged_dev_bytes();
+        sb = coarse_solver_state_bytes();
+        cap = n;
+        slot_bytes = (db * n + sizeof(int) * NT * (n + 1) + 255) / 256 * 256;
+        CK(desc.ensure(2 * db * n));
+        CK(off.ensure(sizeof(int) * 2 * NT * (n + 1)));
+        CK(cargs.ensure(coarse_solver_desc_bytes() * n));
+        CK(cstate.ensure(sb * n));
+        CK(coef.ensure(sizeof(double2) * 64 * n));
+        CK(cudaMallocHost((void**)&hstage, slot_bytes * kSlots));
+        for (auto& e : ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK(cudaMallocHost((void**)&hstate, sb * n));
+        CK(cudaMallocHost((void**)&hcoef, sizeof(double2) * 64 * n));
+        CK(cudaMallocHost(&hcargs, coarse_solver_desc_bytes() * n));
+        return AMG_OK;
+    }
+    const void* d(int region) const { return (const char*)desc.p + region * db * cap; }
+    const int* o(int region, int t) const { return off.as<int>() + (region * NT + t) * (cap + 1); }
+};
+
+bool fusable(const std::vector<RaggedProb>& P) {
+    const amg_hierarchy* h0 = P[0].h;
+    for (const auto& p : P) {
+        const amg_hierarchy* h = p.h;
+        const CoarseLevel& L = h->lev[1];
+        int vb = 1;
+        for (int mu = 0; mu < 4; ++mu) vb *= h->blk[0].b[mu];
+        if (h->fp != 1 || h->p.sap_eo || L.prec != 1 || L.kprec() != h0->lev[1].kprec() || h->rp != h0->rp ||
+            vb > 256 || h->p.outer_m + 1 > 20 || h->p.coarse_ell > 4 || h->nn)
+            return false;
+        if (h->p.sap_iters != h0->p.sap_iters || h->p.mr_iters != h0->p.mr_iters) return false;
+        if (!h->d->gauge->U[3].p || !h->d->C[3].p || !h->d->gauge->U[1].p || !h->d->C[1].p) return false;
+    }
+    return true;
+}
+
+// descriptors and CTA offset tables of the problems idx at Arnoldi step j into region r
+// (uploaded on st); the Gram-Schmidt coefficients of problem i live at coef + 64 i
+amg_status fused_tables(FusedBatch& F, std::vector<RaggedProb>& P, const std::vector<int>& idx, int j, int r,
+                        int tot[FusedBatch::NT], cudaStream_t st) {
+    const int na = (int)idx.size(), stride = F.cap + 1;
+    // a staging slot whose last upload has been done
+    const int slot = F.next;
+    F.next = (F.next + 1) % FusedBatch::kSlots;
+    CK(cudaEventSynchronize(F.ev[slot]));
+    char* hd = F.hstage + slot * F.slot_bytes;
+    int* ho = reinterpret_cast<int*>(hd + F.db * F.cap);
+    for (int t = 0; t < FusedBatch::NT; ++t) tot[t] = 0;
+    for (int a = 0; a < na; ++a) {
+        amg_hierarchy* h = P[idx[a]].h;
+        amg_dirac* d = h->d;
+        const GeomH& g = fine_geom(h);
+        CoarseLevel& L = h->lev[1];
+        RaggedProbH q = {};
+        q.g = g;
+        q.blk = h->blk[0];
+        q.nvec = h->p.nvec[0];
+        q.kappa = d->kappa;
+        q.U32 = d->gauge->U[1].p;
+        q.C32 = d->C[1].p;
+        q.Udd = d->gauge->U[3].p;
+        q.Cdd = d->C[3].p;
+        q.vecs = rp_vecs(h);
+        q.v = h->oV[j]->p;
+        q.f32 = h->fb[1].p;
+        q.bc = h->cw[1][0]->p;
+        q.xc = h->cw[1][1]->p;
+        q.z = h->oZ[j]->p;
+        q.w = h->ow.p;
+        for (int i = 0; i <= j; ++i) q.basis[i] = h->oV[i]->p;
+        q.nbasis = j + 1;
+        q.vnext = h->oV[j + 1]->p;
+        q.gs_part = h->gs_part.as<double2>();
+        q.gs_coef = F.coef.as<double2>() + 64 * (size_t)idx[a];
+        q.n = fine_n(h);
+        q.R = (size_t)20 * blas_grid();
+        q.U64 = d->gauge->U[0].p;
+        q.C64 = d->C[0].p;
+        q.b64 = h->ob.p;
+        q.x64 = h->ox.p;
+        q.r64 = h->orr.p;
+        q.rsrc = P[idx[a]].started ? h->orr.p : h->ob.p;
+        q.npart = reinterpret_cast<double*>(h->gs_part.as<double2>() + 2 * q.R);
+        q.nval = reinterpret_cast<double*>(F.coef.as<double2>() + 64 * (size_t)idx[a] + 62);
+        q.k = (int)P[idx[a]].y.size();
+        for (int i = 0; i < q.k; ++i) {
+            q.zb[i] = h->oZ[i]->p;
+            q.yc[i] = P[idx[a]].y[i];
+        }
+        q.canon_in = P[idx[a]].bcanon;
+        q.canon_out = P[idx[a]].xcanon;
+        int vb = 1;
+        for (int mu = 0; mu < 4; ++mu) vb *= h->blk[0].b[mu];
+        q.sap_nr = ragged_sap_nr(vb, F.max_vb);
+        if (ragged_dev_fill(hd + (size_t)a * F.db, q) != 0)
+            return fail(AMG_EINVAL, "ragged solve: bad problem descriptor");
+        const int nt[FusedBatch::NT] = {ragged_site_ctas(g.V), L.g.V, (L.g.V / 2 + q.sap_nr - 1) / q.sap_nr,
+                                        ragged_blas_ctas(q.n)};
+        for (int t = 0; t < FusedBatch::NT; ++t) {
+            ho[t * stride + a] = tot[t];
+            tot[t] += nt[t];
+        }
+    }
+    for (int t = 0; t < FusedBatch::NT; ++t) ho[t * stride + na] = tot[t];
+    CK(cudaMemcpyAsync((char*)F.desc.p + (size_t)r * F.cap * F.db, hd, na * F.db, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(F.off.as<int>() + r * FusedBatch::NT * stride, ho, sizeof(int) * FusedBatch::NT * stride,
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(F.ev[slot], st));
+    return AMG_OK;
+}
+
+// Z_j = M V_j and w = D Z_j for the problems of region 0 (na of them, step tables tot)
+amg_status fused_precondition(FusedBatch& F, std::vector<RaggedProb>& P, const std::vector<int>& act,
+                              const int tot[FusedBatch::NT], cudaStream_t st) {
+    const int na = (int)act.size();
+    const void* d = F.d(0);
+    amg_hierarchy* h0 = P[act[0]].h;
+    CK(launch_convert_ragged(d, F.o(0, FusedBatch::T_SITE), na, tot[FusedBatch::T_SITE], st));
+    CK(launch_restrict_ragged(h0->rp, d, F.o(0, FusedBatch::T_BLK), na, tot[FusedBatch::T_BLK], F.max_vb, F.max_nvec,
+                              st));
+    std::vector<CoarseSolveDesc> cd(na);
+    for (int a = 0; a < na; ++a) {
+        amg_hierarchy* h = P[act[a]].h;
+        CoarseLevel& L = h->lev[1];
+        auto& w = h->cw[1];
+        const int ell = h->p.coarse_ell;
+        CoarseSolveDesc& c = cd[a];
+        c.cprec = L.kprec();
+        c.gc = L.g;
+        c.nc = L.nc;
+        c.B = L.op();
+        c.b = w[0]->p;
+        c.x = w[1]->p;
+        c.rt = w[2]->p;
+        for (int k = 0; k < 5; ++k) {
+            c.R[k] = k <= ell ? w[3 + k]->p : nullptr;
+            c.U[k] = k <= ell ? w[4 + ell + k]->p : nullptr;
+        }
+        c.ell = ell;
+        c.tol = h->p.coarse_tol;
+        c.maxit = h->p.coarse_maxit;
+        c.part = L.cs_part.p;
+        c.state = (char*)F.cstate.p + a * F.sb;
+        c.xgroup = L.xgroup;
+    }
+    CK(cudaMemsetAsync(F.cstate.p, 0, F.sb * na, st));
+    CK(launch_coarse_bicgstab_multi(cd.data(), na, F.hcargs, F.cargs.p, st));
+    CK(cudaMemcpyAsync(F.hstate, F.cstate.p, F.sb * na, cudaMemcpyDeviceToHost, st));
+    CK(launch_prolong_ragged(h0->rp, d, F.o(0, FusedBatch::T_BLK), na, tot[FusedBatch::T_BLK], F.max_vb, F.max_nvec,
+                             st));
+    for (int i = 0; i < h0->p.sap_iters; ++i)
+        for (int colour = 0; colour < 2; ++colour)
+            CK(launch_sap_half_ragged(d, F.o(0, FusedBatch::T_DOM), na, tot[FusedBatch::T_DOM], F.max_vb, colour,
+                                      h0->p.mr_iters, st));
+    CK(launch_dirac_mixed_ragged(d, F.o(0, FusedBatch::T_SITE), na, tot[FusedBatch::T_SITE], st));
+    return AMG_OK;
+}
+
+amg_status fgmres_fused(std::vector<RaggedProb>& P, cudaStream_t st, double tol, int maxit) {
+    const int n = (int)P.size();
+    FusedBatch F;
+    TRY(F.alloc(n));
+    int mmax = 0;
+    for (auto& p : P) {
+        p.st = st;
+        mmax = std::max(mmax, p.h->p.outer_m);
+        int vb = 1;
+        for (int mu = 0; mu < 4; ++mu) vb *= p.h->blk[0].b[mu];
+        F.max_vb = std::max(F.max_vb, vb);
+        F.max_nvec = std::max(F.max_nvec, p.h->p.nvec[0]);
+    }
+    int tot0[FusedBatch::NT], tot1[FusedBatch::NT];
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    // b and x = 0 in the internal layout
+    TRY(fused_tables(F, P, all, 0, 1, tot1, st));
+    CK(launch_pack_ragged(F.d(1), F.o(1, FusedBatch::T_SITE), n, tot1[FusedBatch::T_SITE], st));
+    bool first = true;
+    while (true) {
+        // true FP64 residual of every unfinished problem (b itself while x = 0), its norm and
+        // V_0 = r / |r|: three launches for the set, one synchronisation
+        std::vector<int> set;
+        for (int i = 0; i < n; ++i)
+            if (!P[i].r.done) set.push_back(i);
+        if (set.empty()) break;
+        TRY(fused_tables(F, P, set, 0, 1, tot1, st));
+        const int ns = (int)set.size();
+        if (!first) CK(launch_resid_ragged(F.d(1), F.o(1, FusedBatch::T_SITE), ns, tot1[FusedBatch::T_SITE], st));
+        CK(launch_norm_v0_ragged(F.d(1), F.o(1, FusedBatch::T_BLAS), ns, tot1[FusedBatch::T_BLAS], st));
+        CK(cudaMemcpyAsync(F.hcoef, F.coef.p, sizeof(double2) * 64 * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int i : set) {
+            RaggedProb& p = P[i];
+            RhsState& r = p.r;
+            const double nv = reinterpret_cast<const double*>(F.hcoef + 64 * i + 62)[0];
+            if (first) {
+                r.bnorm = nv;
+                if (!std::isfinite(r.bnorm)) return fail(AMG_NAN, "ragged solve: non-finite right-hand side");
+                if (r.bnorm == 0) {
+                    r.done = r.conv = true;
+                    continue;
+                }
+            }
+            p.started = true;
+            r.rn = nv;
+            if (!std::isfinite(r.rn)) return fail(AMG_NAN, "ragged solve: non-finite residual");
+            r.rel = r.rn / r.bnorm;
+            r.done = r.conv = r.rn <= tol * r.bnorm;
+            if (!r.conv && r.iters >= maxit) r.done = true;
+            if (r.done) continue;
+            any = true;
+            if (r.iters > 0) r.restarts++;
+            const int m = p.h->p.outer_m;
+            r.H.assign(m + 1, std::vector<cplx>(m, cplx(0)));
+            r.cs.assign(m, 0.0);
+            r.sn.assign(m, cplx(0));
+            r.g.assign(m + 1, cplx(0));
+            r.g[0] = r.rn;
+            r.jend = -1;
+            r.stop = false;
+        }
+        first = false;
+        if (!any) break;
+        for (int j = 0; j < mmax; ++j) {
+            std::vector<int> act;
+            for (int i = 0; i < n; ++i) {
+                RaggedProb& p = P[i];
+                if (p.r.done || p.r.stop) continue;
+                if (j >= p.h->p.outer_m) {
+                    p.r.stop = true;
+                    continue;
+                }
+                act.push_back(i);
+            }
+            if (act.empty()) break;
+            const int na = (int)act.size();
+            TRY(fused_tables(F, P, act, j, 0, tot0, st));
+            TRY(fused_precondition(F, P, act, tot0, st));
+            // classical Gram-Schmidt in FP64 (reading C23), one launch per kernel for the batch;
+            // a second pass only for the problems whose loss-of-orthogonality estimate asks for it
+            CK(launch_gs_ragged(j + 1, F.d(0), F.o(0, FusedBatch::T_BLAS), na, tot0[FusedBatch::T_BLAS], 0, st));
+            CK(cudaMemcpyAsync(F.hcoef, F.coef.p, sizeof(double2) * 64 * n, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int a = 0; a < na; ++a) {
+                const int* w = reinterpret_cast<const int*>(F.hstate + a * F.sb);
+                if (w[2] == 1) return fail(AMG_TIMEOUT, "coarse solver: grid barrier timed out");
+                if (w[2] != 0) return fail(AMG_NAN, "coarse solver: breakdown or non-finite residual");
+                P[act[a]].coarse_cycles += w[3];
+            }
+            std::vector<int> again;
+            std::vector<double> hnv(n, 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                const std::vector<int>& set = pass == 0 ? act : again;
+                std::vector<int> more;
+                for (int i : set) {
+                    RaggedProb& p = P[i];
+                    const double2* hc = F.hcoef + 64 * i + 32 * pass;
+                    double c2 = 0;
+                    for (int k = 0; k <= j; ++k) {
+                        p.r.H[k][j] += cplx(hc[k].x, hc[k].y);
+                        c2 += hc[k].x * hc[k].x + hc[k].y * hc[k].y;
+                    }
+                    hnv[i] = reinterpret_cast<const double*>(F.hcoef + 64 * i + 63)[0];
+                    if (pass == 0 && hnv[i] > 0 && 2.2e-16 * std::sqrt(hnv[i] * hnv[i] + c2) > kReorthLoss * hnv[i])
+                        more.push_back(i);
+                }
+                if (pass == 1 || more.empty()) break;
+                again = more;
+                TRY(fused_tables(F, P, again, j, 1, tot1, st));
+                CK(launch_gs_ragged(j + 1, F.d(1), F.o(1, FusedBatch::T_BLAS), (int)again.size(),
+                                    tot1[FusedBatch::T_BLAS], 1, st));
+                CK(cudaMemcpyAsync(F.hcoef, F.coef.p, sizeof(double2) * 64 * n, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            }
+            for (int i : act) {
+                RhsState& r = P[i].r;
+                const double hn = hnv[i];
+                r.H[j + 1][j] = hn;
+                r.iters++;
+                givens_column(r.H, r.cs, r.sn, r.g, j);
+                r.jend = j;
+                const double est = std::abs(r.g[j + 1]);
+                if (!std::isfinite(est)) return fail(AMG_NAN, "ragged solve: non-finite Arnoldi coefficient");
+                if (hn == 0 || est <= tol * r.bnorm || r.iters >= maxit) r.stop = true;
+            }
+        }
+        // x += Z y: one launch for every problem that took steps in this cycle
+        std::vector<int> upd;
+        for (int i = 0; i < n; ++i) {
+            RaggedProb& p = P[i];
+            RhsState& r = p.r;
+            p.y.clear();
+            if (r.done || r.jend < 0) continue;
+            const int k = r.jend + 1;
+            std::vector<cplx> y(k);
+            for (int a = k - 1; a >= 0; --a) {
+                cplx t = r.g[a];
+                for (int cc = a + 1; cc < k; ++cc) t -= r.H[a][cc] * y[cc];
+                y[a] = t / r.H[a][a];
+            }
+            p.y.resize(k);
+            for (int a = 0; a < k; ++a) p.y[a] = d2(y[a]);
+            upd.push_back(i);
+        }
+        if (!upd.empty()) {
+            TRY(fused_tables(F, P, upd, 0, 1, tot1, st));
+            CK(launch_xupdate_ragged(F.d(1), F.o(1, FusedBatch::T_SITE), (int)upd.size(), tot1[FusedBatch::T_SITE],
+                                     st));
+        }
+    }
+    TRY(fused_tables(F, P, all, 0, 1, tot1, st));
+    CK(launch_unpack_ragged(F.d(1), F.o(1, FusedBatch::T_SITE), n, tot1[FusedBatch::T_SITE], st));
+    return AMG_OK;
+}
 }  // namespace
 
 // accessors used by the allocation-free entry point (noalloc.cu)
@@ -2676,6 +3034,8 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     return worst;
 }
 
+void amg_set_ragged_fusion(int on) { g_ragged_fused = on != 0; }
+
 amg_status amg_solve_ragged(amg_hierarchy* const* hs, const double* const* b, double* const* x, int n, double tol,
                             int maxit, amg_solve_info* infos, amg_stream s) {
     if (!hs || !b || !x || n < 1 || !(tol > 0) || maxit < 1) return fail(AMG_EINVAL, "bad argument");
@@ -2688,9 +3048,12 @@ amg_status amg_solve_ragged(amg_hierarchy* const* hs, const double* const* b, do
             if (hs[k] == hs[i]) return fail(AMG_EINVAL, "a hierarchy appears twice in the ragged batch");
     }
     cudaStream_t user = (cudaStream_t)s;
-    const int ns = std::min(n, 16);
-    std::vector<cudaStream_t> streams(ns, nullptr);
     std::vector<RaggedProb> P(n);
+    for (int i = 0; i < n; ++i) P[i].h = hs[i];
+    // one launch per phase for the whole batch where the problems allow it, else a stream pool
+    const bool fused = g_ragged_fused && fusable(P);
+    const int ns = fused ? 1 : std::min(n, 16);
+    std::vector<cudaStream_t> streams(ns, nullptr);
     cudaEvent_t ev = nullptr;
     auto t_all = std::chrono::steady_clock::now();
     auto body = [&]() -> amg_status {
@@ -2702,15 +3065,25 @@ amg_status amg_solve_ragged(amg_hierarchy* const* hs, const double* const* b, do
         }
         for (int i = 0; i < n; ++i) {
             RaggedProb& p = P[i];
-            p.h = hs[i];
             p.st = streams[i % ns];
             TRY(alloc_workspaces(p.h, 1));
             p.h->timer.on = false;
+            if (fused) {
+                // the fused form packs b, zeroes x and unpacks x in batch launches
+                p.bcanon = b[i];
+                p.xcanon = x[i];
+                continue;
+            }
             for (int l = 1; l < p.h->p.nlevels; ++l) CK(cudaMemsetAsync(p.h->lev[l].cs_state.p, 0, 16, p.st));
             std::memset(p.h->hstate, 0, 16 * 16);
             const GeomH& g = fine_geom(p.h);
             CK(launch_pack_spinor(0, g, b[i], p.h->ob.p, 1, p.st));
             CK(cudaMemsetAsync(p.h->ox.p, 0, fine_spinor_bytes(0, g.V), p.st));
+        }
+        if (fused) {
+            TRY(fgmres_fused(P, streams[0], tol, maxit));
+            CK(cudaStreamSynchronize(streams[0]));
+            return AMG_OK;
         }
         TRY(fgmres_ragged(P, streams, tol, maxit));
         for (int i = 0; i < n; ++i) {
@@ -2742,7 +3115,7 @@ amg_status amg_solve_ragged(amg_hierarchy* const* hs, const double* const* b, do
             infos[i].true_rel_residual = r.bnorm == 0 ? 0.0 : r.rel;
             infos[i].ms_total = ms;
             infos[i].ms_other = ms;
-            infos[i].coarse_cycles = P[i].h->hstate[63];
+            infos[i].coarse_cycles = fused ? P[i].coarse_cycles : P[i].h->hstate[63];
         }
     }
     if (!all) return fail(AMG_NOT_CONVERGED, "ragged solve: some problem did not reach the tolerance");

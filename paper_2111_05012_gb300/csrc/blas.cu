@@ -36,14 +36,15 @@ struct CoefList {
 // K dots <a_j, b>, K a compile-time constant so that only K accumulation
 // chains are issued (FP64 arithmetic is scarce on this part)
 // K dots <a_j, b> (quantities 0..K-1) and, with NB, |b|^2 as quantity K (imaginary part 0)
-template <typename V, int K, bool NB>
-__global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, double2* partials) {
+// (the body of one CTA bx of gx; PL: anything with an indexable member p of vector pointers)
+template <typename V, int K, bool NB, class PL>
+DEV void multi_dot_body(const PL& a, const V* __restrict__ b, size_t n, double2* partials, int bx, int gx) {
     constexpr int NQ = K + (NB ? 1 : 0);
     __shared__ double red[2 * NQ * 32];
     double acc[2 * NQ];
 #pragma unroll
     for (int j = 0; j < 2 * NQ; ++j) acc[j] = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = bx * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gx * blockDim.x) {
         V y = b[i];
         const double yr = y.x, yi = y.y;
 #pragma unroll
@@ -74,8 +75,12 @@ __global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, d
             re += red[(2 * j) * 32 + w];
             im += red[(2 * j + 1) * 32 + w];
         }
-        partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(re, im);
+        partials[(size_t)j * gx + bx] = make_double2(re, im);
     }
+}
+template <typename V, int K, bool NB>
+__global__ void multi_dot_kernel(PtrList a, const V* __restrict__ b, size_t n, double2* partials) {
+    multi_dot_body<V, K, NB>(a, b, n, partials, blockIdx.x, gridDim.x);
 }
 
 template <typename V, int K>
@@ -94,12 +99,12 @@ void multi_dot_launch(int k, bool nb, const PtrList& pl, const V* b, size_t n, d
 // one warp per quantity, lanes striding (fixed order: every CTA of the launch
 // gets bitwise the same sums); out[j] = -sum (the update coefficient), and CTA
 // 0 stores +sum in used[j] for the host's Hessenberg column
-DEV void coefficients_from_partials(const double2* src, int k, double2* out, double2* used) {
+DEV void coefficients_from_partials(const double2* src, int k, double2* out, double2* used, int bx, int gx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = warp; j < k; j += nw) {
         double re = 0, im = 0;
-        for (int t = lane; t < (int)gridDim.x; t += 32) {
-            const double2 v = __ldcg(src + (size_t)j * gridDim.x + t);
+        for (int t = lane; t < gx; t += 32) {
+            const double2 v = __ldcg(src + (size_t)j * gx + t);
             re += v.x;
             im += v.y;
         }
@@ -107,15 +112,15 @@ DEV void coefficients_from_partials(const double2* src, int k, double2* out, dou
         im = warp_sum(im);
         if (lane == 0) {
             out[j] = make_double2(-re, -im);
-            if (blockIdx.x == 0 && used) used[j] = make_double2(re, im);
+            if (bx == 0 && used) used[j] = make_double2(re, im);
         }
     }
     __syncthreads();
 }
 
-template <typename V, int K, int MODE>   // MODE 0: |y|^2; 1: dots; 2: dots and |y|^2 (quantity K)
-__global__ void multi_axpy_reduce_kernel(PtrList x, V* y, size_t n, double2* partials, const double2* csrc,
-                                         double2* cused) {
+template <typename V, int K, int MODE, class PL>   // MODE 0: |y|^2; 1: dots; 2: dots and |y|^2 (quantity K)
+DEV void multi_axpy_reduce_body(const PL& x, V* y, size_t n, double2* partials, const double2* csrc, double2* cused,
+                                int bx, int gx) {
     using T = typename VT<V>::T;
     constexpr bool DOT = MODE >= 1, NRM = MODE != 1;
     constexpr int NA = (DOT ? 2 * K : 0) + (NRM ? (DOT ? 2 : 1) : 0);
@@ -123,7 +128,7 @@ __global__ void multi_axpy_reduce_kernel(PtrList x, V* y, size_t n, double2* par
     __shared__ double2 cdev[K];
     // coefficients: minus the sums of the partials a previous reduction left at csrc
     // (summed here, so no host round trip)
-    coefficients_from_partials(csrc, K, cdev, cused);
+    coefficients_from_partials(csrc, K, cdev, cused, bx, gx);
     T cre[K], cim[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -133,7 +138,7 @@ __global__ void multi_axpy_reduce_kernel(PtrList x, V* y, size_t n, double2* par
     double acc[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) acc[j] = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = bx * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gx * blockDim.x) {
         V xs[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) xs[j] = ((const V*)x.p[j])[i];
@@ -181,13 +186,18 @@ __global__ void multi_axpy_reduce_kernel(PtrList x, V* y, size_t n, double2* par
                 re += red[(2 * j) * 32 + w];
                 im += red[(2 * j + 1) * 32 + w];
             }
-            partials[(size_t)j * gridDim.x + blockIdx.x] = make_double2(re, im);
+            partials[(size_t)j * gx + bx] = make_double2(re, im);
         }
     } else if (threadIdx.x == 0) {
         double t = 0;
         for (int w = 0; w < nw; ++w) t += red[w];
-        reinterpret_cast<double*>(partials)[blockIdx.x] = t;
+        reinterpret_cast<double*>(partials)[bx] = t;
     }
+}
+template <typename V, int K, int MODE>
+__global__ void multi_axpy_reduce_kernel(PtrList x, V* y, size_t n, double2* partials, const double2* csrc,
+                                         double2* cused) {
+    multi_axpy_reduce_body<V, K, MODE>(x, y, n, partials, csrc, cused, blockIdx.x, gridDim.x);
 }
 
 template <typename V, int K, int MODE>
@@ -201,10 +211,10 @@ void multi_axpy_reduce_launch(int k, const PtrList& pl, V* y, size_t n, double2*
 }
 
 template <typename V>
-__global__ void norm2_kernel(const V* __restrict__ a, size_t n, double* partials) {
+DEV void norm2_body(const V* __restrict__ a, size_t n, double* partials, int bx, int gx) {
     __shared__ double red[32];
     double acc = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = bx * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gx * blockDim.x) {
         V x = a[i];
         acc = fma((double)x.x, (double)x.x, acc);
         acc = fma((double)x.y, (double)x.y, acc);
@@ -216,8 +226,12 @@ __global__ void norm2_kernel(const V* __restrict__ a, size_t n, double* partials
     if (threadIdx.x == 0) {
         double t = 0;
         for (int w = 0; w < nw; ++w) t += red[w];
-        partials[blockIdx.x] = t;
+        partials[bx] = t;
     }
+}
+template <typename V>
+__global__ void norm2_kernel(const V* __restrict__ a, size_t n, double* partials) {
+    norm2_body<V>(a, n, partials, blockIdx.x, gridDim.x);
 }
 
 template <typename V>
@@ -237,27 +251,31 @@ __global__ void axpby_kernel(double2 al, const V* __restrict__ x, double2 be, V*
 // norm reduction of the same grid); y = 0 if |x| = 0.  CTA 0 stores |x| in hn.
 // Two multiplications per complex entry.
 template <typename V>
-__global__ void normalise_kernel(const double* src, double* hn, const V* __restrict__ x, V* y, size_t n) {
+DEV void normalise_body(const double* src, double* hn, const V* __restrict__ x, V* y, size_t n, int bx, int gx) {
     using T = typename VT<V>::T;
     __shared__ double s_inv;
     if (threadIdx.x < 32) {
         double t = 0;
-        for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) t += __ldcg(src + k);
+        for (int k = threadIdx.x; k < gx; k += 32) t += __ldcg(src + k);
         t = warp_sum(t);
         if (threadIdx.x == 0) {
             const double h = sqrt(t);
             s_inv = h > 0 ? 1.0 / h : 0.0;
-            if (blockIdx.x == 0) *hn = h;
+            if (bx == 0) *hn = h;
         }
     }
     __syncthreads();
     const T a = (T)s_inv;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = bx * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gx * blockDim.x) {
         V v = x[i];
         v.x *= a;
         v.y *= a;
         y[i] = v;
     }
+}
+template <typename V>
+__global__ void normalise_kernel(const double* src, double* hn, const V* __restrict__ x, V* y, size_t n) {
+    normalise_body<V>(src, hn, x, y, n, blockIdx.x, gridDim.x);
 }
 
 // y = a x for a real a (two multiplications per complex entry)
@@ -291,6 +309,63 @@ __global__ void multi_axpy_kernel(int k, CoefList c, PtrList x, V* y, size_t n) 
         o.y = im;
         y[i] = o;
     }
+}
+
+// ---- ragged batch: one Gram-Schmidt pass for every problem, one launch per step
+// (per problem: basis V_0..V_j, w, its own partials and coefficients; CTA ranges
+// from the prefix table, the same ranges in all three launches of a pass)
+struct BasisView {
+    const void* const* p;
+};
+template <int K>
+__global__ void __launch_bounds__(kBT) gs_dot_ragged_kernel(const RaggedDev* __restrict__ d,
+                                                            const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    multi_dot_body<double2, K, false>(BasisView{q.basis}, (const double2*)q.w, q.n, q.gs_part, bx, gx);
+}
+template <int K>
+__global__ void __launch_bounds__(kBT) gs_update_ragged_kernel(const RaggedDev* __restrict__ d,
+                                                               const int* __restrict__ off, int np, int pass) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    multi_axpy_reduce_body<double2, K, 0>(BasisView{q.basis}, (double2*)q.w, q.n, q.gs_part + 2 * q.R, q.gs_part,
+                                          q.gs_coef + 32 * pass, bx, gx);
+}
+__global__ void __launch_bounds__(kBT) gs_normalise_ragged_kernel(const RaggedDev* __restrict__ d,
+                                                                  const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    normalise_body<double2>((const double*)(q.gs_part + 2 * q.R), (double*)(q.gs_coef + 63), (const double2*)q.w,
+                            (double2*)q.vnext, q.n, bx, gx);
+}
+// restart: |rsrc|^2 partials, then basis[0] = rsrc / |rsrc| and nval = |rsrc|
+__global__ void __launch_bounds__(kBT) rnorm_ragged_kernel(const RaggedDev* __restrict__ d,
+                                                           const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    norm2_body<double2>((const double2*)q.rsrc, q.n, q.npart, bx, gx);
+}
+__global__ void __launch_bounds__(kBT) rnormalise_ragged_kernel(const RaggedDev* __restrict__ d,
+                                                                const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    normalise_body<double2>(q.npart, q.nval, (const double2*)q.rsrc, (double2*)const_cast<void*>(q.basis[0]), q.n,
+                            bx, gx);
+}
+template <int K>
+void gs_ragged_launch(int k, int step, const RaggedDev* d, const int* off, int np, int ctas, int pass,
+                      cudaStream_t st) {
+    if constexpr (K > 1) {
+        if (k < K) return gs_ragged_launch<K - 1>(k, step, d, off, np, ctas, pass, st);
+    }
+    if (step == 0) (note_launch(), gs_dot_ragged_kernel<K><<<ctas, kBT, 0, st>>>(d, off, np));
+    else (note_launch(), gs_update_ragged_kernel<K><<<ctas, kBT, 0, st>>>(d, off, np, pass));
 }
 
 }  // namespace
@@ -377,4 +452,26 @@ cudaError_t launch_multi_axpy_reduce_dev(int prec, int k, const double2* csrc, d
     return cudaGetLastError();
 }
 
-
+// one classical Gram-Schmidt pass of step j (k = j + 1 basis vectors) for every problem of a
+// ragged batch: partial dots <V_i, w>; w -= sum_i h_i V_i with |w'|^2 partials (h_i stored in
+// gs_coef[32 pass + i]); V_{j+1} = w' / |w'| (|w'| in gs_coef[63])
+cudaError_t launch_gs_ragged(int k, const void* d, const int* off, int np, int ctas, int pass, cudaStream_t st) {
+    if (k < 1 || k > kMaxDots || ctas < 1) return cudaErrorInvalidValue;
+    const RaggedDev* dd = (const RaggedDev*)d;
+    gs_ragged_launch<kMaxDots>(k, 0, dd, off, np, ctas, pass, st);
+    gs_ragged_launch<kMaxDots>(k, 1, dd, off, np, ctas, pass, st);
+    (note_launch(), gs_normalise_ragged_kernel<<<ctas, kBT, 0, st>>>(dd, off, np));
+    return cudaGetLastError();
+}
+int ragged_blas_ctas(size_t n) {
+    const size_t per = (size_t)kBT * 16;   // about 16 entries per thread
+    size_t c = (n + per - 1) / per;
+    const size_t cap = (size_t)blas_grid_size();
+    return (int)(c < 1 ? 1 : (c > cap ? cap : c));
+}
+cudaError_t launch_norm_v0_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    const RaggedDev* dd = (const RaggedDev*)d;
+    (note_launch(), rnorm_ragged_kernel<<<ctas, kBT, 0, st>>>(dd, off, np));
+    (note_launch(), rnormalise_ragged_kernel<<<ctas, kBT, 0, st>>>(dd, off, np));
+    return cudaGetLastError();
+}

@@ -27,6 +27,8 @@
 //
 // Grid barriers spin with a bounded count; on timeout the
 // kernel records AMG_TIMEOUT in the status word and every CTA returns.
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -75,10 +77,12 @@ struct Args {
     void* rt;
     void* R[kMaxEll + 1];
     void* U[kMaxEll + 1];
-    double2* part;   // [kMaxQ][gridDim.x]
+    double2* part;   // [kMaxQ][ncta]
     GridBar* bar;
     int row_bytes;   // 9 * nc * (bytes per operator entry), a multiple of 16
     int xgroup;      // coarse sites whose neighbour blocks are staged in shared memory at once
+    int cta, ncta;   // this CTA's index among the solve's CTAs and their number (the grid, or one
+                     // cluster of a launch that solves several problems, one per cluster)
 };
 
 DEV unsigned ld_acquire(const unsigned* p) {
@@ -98,12 +102,12 @@ DEV unsigned atom_add_acqrel(unsigned* p, unsigned v) {
 // One acquire-release atomic per CTA, then a bounded spin on the top bit; the
 // CTA's writes are published by __syncthreads + the releasing atomic.
 // Returns false if it gave up (then the caller returns).
-DEV bool grid_sync(GridBar* gb) {
+DEV bool grid_sync(GridBar* gb, int cta, int ncta) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile int* verr = &gb->err;
-        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        const unsigned inc = cta == 0 ? 0x80000000u - ((unsigned)ncta - 1u) : 1u;
         const unsigned old = atom_add_acqrel(&gb->count, inc);
         int ok = 1;
         long long it = 0;
@@ -140,9 +144,9 @@ DEV bool grid_reduce(const Args& a, cx<AT> (&v)[NQ], int nq, cx<double>* red_sh,
     if (threadIdx.x < nq) {
         cx<double> t = czero<double>();
         for (int w = 0; w < kWarps; ++w) t = t + red_sh[threadIdx.x * kWarps + w];
-        a.part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = make_double2(t.re, t.im);
+        a.part[(size_t)threadIdx.x * a.ncta + a.cta] = make_double2(t.re, t.im);
     }
-    if (!grid_sync(a.bar)) return false;
+    if (!grid_sync(a.bar, a.cta, a.ncta)) return false;
     // one warp per quantity, lanes stride over the CTA partials (fixed order)
     for (int q = warp; q < nq; q += kWarps) {
         double re = 0, im = 0;
@@ -153,15 +157,15 @@ DEV bool grid_reduce(const Args& a, cx<AT> (&v)[NQ], int nq, cx<double>* red_sh,
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int i = lane + 32 * k;
-            t[k] = i < (int)gridDim.x ? __ldcg(a.part + (size_t)q * gridDim.x + i) : make_double2(0.0, 0.0);
+            t[k] = i < a.ncta ? __ldcg(a.part + (size_t)q * a.ncta + i) : make_double2(0.0, 0.0);
         }
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             re += t[k].x;
             im += t[k].y;
         }
-        for (int i = lane + 32 * kPer; i < (int)gridDim.x; i += 32) {
-            double2 u = __ldcg(a.part + (size_t)q * gridDim.x + i);
+        for (int i = lane + 32 * kPer; i < a.ncta; i += 32) {
+            double2 u = __ldcg(a.part + (size_t)q * a.ncta + i);
             re += u.x;
             im += u.y;
         }
@@ -174,9 +178,9 @@ DEV bool grid_reduce(const Args& a, cx<AT> (&v)[NQ], int nq, cx<double>* red_sh,
 }
 
 // row range owned by this CTA
-DEV void my_rows(int nrows, int& r0, int& r1) {
-    int per = (nrows + gridDim.x - 1) / gridDim.x;
-    r0 = blockIdx.x * per;
+DEV void my_rows(int nrows, int cta, int ncta, int& r0, int& r1) {
+    int per = (nrows + ncta - 1) / ncta;
+    r0 = cta * per;
     r1 = min(nrows, r0 + per);
     if (r0 > nrows) r0 = nrows;
 }
@@ -439,7 +443,7 @@ DEV bool mr_coefficients(const cx<double>* res, int ell, cx<double>* out_x, cx<d
 }
 
 template <typename TC, int BF, int NB>
-__global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
+DEV void coarse_bicgstab_body(Args& a) {
     using SC = TC;   // BiCG scalars in the solver's precision
     __shared__ cx<double> red_sh[kMaxQ * kWarps];
     __shared__ cx<double> res[kMaxQ];
@@ -454,7 +458,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
     const int ell = a.ell, nb = a.nb;
     const size_t n = (size_t)a.Vc * a.nc;
     int r0, r1;
-    my_rows((int)n, r0, r1);
+    my_rows((int)n, a.cta, a.ncta, r0, r1);
     const int tid = threadIdx.x;
     // initial state: x = 0, R0 = b, rt = b, U0 = 0
     for (int r = 0; r < nb; ++r)
@@ -521,7 +525,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
         }
         __syncthreads();
         if (s_bad) {
-            if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
+            if (a.cta == 0 && tid == 0) atomicExch(&a.bar->err, 2);
             return;
         }
         if (!s_any) break;
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
                         st<TC>(a.U[q], r * n + i, ld<TC>(a.R[q], r * n + i) - beta * u);
                     }
             }
-            if (!grid_sync(a.bar)) return;
+            if (!grid_sync(a.bar, a.cta, a.ncta)) return;
             // U_{j+1} = A U_j and gamma = <rt, U_{j+1}>
             {
                 cx<TC> d[NB];
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
                     st<TC>(a.x, k, ld<TC>(a.x, k) + alpha * ld<TC>(a.U[0], k));
                 }
             }
-            if (!grid_sync(a.bar)) return;
+            if (!grid_sync(a.bar, a.cta, a.ncta)) return;
             // R_{j+1} = A R_j; the next BiCG step needs rho1 = <rt, R_{j+1}>
             {
                 cx<TC> d[NB];
@@ -602,7 +606,7 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             }
             __syncthreads();
             if (s_bad) {
-                if (blockIdx.x == 0 && tid == 0) atomicExch(&a.bar->err, 2);
+                if (a.cta == 0 && tid == 0) atomicExch(&a.bar->err, 2);
                 return;
             }
         }
@@ -626,7 +630,24 @@ __global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
             }
         }
     }
-    if (blockIdx.x == 0 && tid == 0) a.bar->cycles += cycle;
+    if (a.cta == 0 && tid == 0) a.bar->cycles += cycle;
+}
+
+template <typename TC, int BF, int NB>
+__global__ void __launch_bounds__(kThreads) coarse_bicgstab_kernel(Args a) {
+    a.cta = blockIdx.x;
+    a.ncta = gridDim.x;
+    coarse_bicgstab_body<TC, BF, NB>(a);
+}
+
+// several independent problems in one launch: cluster c (csize CTAs) solves problem c with
+// the arguments descs[c]; its barriers and reductions involve only its own CTAs
+template <typename TC, int BF>
+__global__ void __launch_bounds__(kThreads) coarse_bicgstab_multi_kernel(const Args* __restrict__ descs, int csize) {
+    Args a = descs[blockIdx.x / csize];
+    a.cta = blockIdx.x % csize;
+    a.ncta = csize;
+    coarse_bicgstab_body<TC, BF, 1>(a);
 }
 
 // one CTA per SM (152 barrier participants on GB300), if the kernel fits
@@ -664,13 +685,13 @@ size_t coarse_solver_partial_bytes() {
 }
 
 
-cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
-                                   void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
-                                   void* part, void* state, int cluster, cudaStream_t s, int nb, int xgroup) {
+// the kernel arguments of one solve and its dynamic shared memory (cudaSuccess if valid)
+static cudaError_t make_args(Args& a, int& smem, int cprec, const GeomH& gc, int nc, const void* B, const void* b,
+                             void* x, void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
+                             void* part, void* state, int nb, int xgroup) {
     if (ell < 1 || ell > kMaxEll) return cudaErrorInvalidValue;
     if (nb < 1 || nb > kMaxNB) return cudaErrorInvalidValue;
     const int NB = nb == 1 ? 1 : nb == 2 ? 2 : 4;   // compiled batch widths
-    Args a;
     a.nb = nb;
     for (int i = 0; i < 4; ++i) a.L[i] = gc.L[i];
     a.Vc = gc.V;
@@ -699,10 +720,23 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     a.xgroup = kXBytes / (block_bytes * NB);
     if (xgroup > 0 && xgroup < a.xgroup) a.xgroup = xgroup;
     if (a.xgroup < 1) return cudaErrorInvalidValue;
-    const void* fn = NB == 1 ? solver_fn<1>(cprec) : NB == 2 ? solver_fn<2>(cprec) : solver_fn<4>(cprec);
-    const int smem = a.xgroup * (NB * block_bytes + 9 * (int)sizeof(int));
+    smem = a.xgroup * (NB * block_bytes + 9 * (int)sizeof(int));
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    a.cta = 0;
+    a.ncta = 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const void* B, const void* b, void* x,
+                                   void* rt, void* const* R, void* const* U, int ell, double tol, int maxit,
+                                   void* part, void* state, int cluster, cudaStream_t s, int nb, int xgroup) {
+    Args a;
+    int smem = 0;
+    cudaError_t e = make_args(a, smem, cprec, gc, nc, B, b, x, rt, R, U, ell, tol, maxit, part, state, nb, xgroup);
+    if (e != cudaSuccess) return e;
+    const int NB = nb == 1 ? 1 : nb == 2 ? 2 : 4;
+    const void* fn = NB == 1 ? solver_fn<1>(cprec) : NB == 2 ? solver_fn<2>(cprec) : solver_fn<4>(cprec);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     void* params[] = {&a};
     if (cluster > 0) {
@@ -736,4 +770,55 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
     if (grid < 1) return cudaErrorInvalidConfiguration;
     note_launch();
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), params, smem, s);
+}
+
+size_t coarse_solver_desc_bytes() { return sizeof(Args); }
+
+cudaError_t launch_coarse_bicgstab_multi(const CoarseSolveDesc* d, int n, void* host_args, void* dev_args,
+                                         cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    const int cprec = d[0].cprec;
+    Args* args = (Args*)host_args;
+    int smem = 0;
+    for (int i = 0; i < n; ++i) {
+        if (d[i].cprec != cprec) return cudaErrorInvalidValue;   // one kernel instance for the launch
+        int sm = 0;
+        cudaError_t e = make_args(args[i], sm, d[i].cprec, d[i].gc, d[i].nc, d[i].B, d[i].b, d[i].x, d[i].rt, d[i].R,
+                                  d[i].U, d[i].ell, d[i].tol, d[i].maxit, d[i].part, d[i].state, 1, d[i].xgroup);
+        if (e != cudaSuccess) return e;
+        smem = sm > smem ? sm : smem;
+    }
+    cudaError_t e = cudaMemcpyAsync(dev_args, args, sizeof(Args) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const void* fn = cprec == 0   ? (const void*)coarse_bicgstab_multi_kernel<double, 0>
+                     : cprec == 3 ? (const void*)coarse_bicgstab_multi_kernel<double, 2>
+                     : cprec == 1 ? (const void*)coarse_bicgstab_multi_kernel<float, 0>
+                                  : (const void*)coarse_bicgstab_multi_kernel<float, 1>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int cl = 8;
+    for (; cl > 1; cl /= 2) {   // largest power-of-two cluster that fits
+        at[0].val.clusterDim.x = cl;
+        cfg.gridDim = dim3(cl);
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0) break;
+        cudaGetLastError();
+    }
+    at[0].val.clusterDim.x = cl;
+    cfg.gridDim = dim3(cl * n);
+    const Args* dp = (const Args*)dev_args;
+    int csize = cl;
+    void* params[] = {&dp, &csize};
+    note_launch();
+    return cudaLaunchKernelExC(&cfg, fn, params);
 }

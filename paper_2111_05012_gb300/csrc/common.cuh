@@ -547,3 +547,65 @@ DEV void block_sum(T (&v)[NV], T* scratch) {
     }
     __syncthreads();
 }
+
+// ---------------------------------------------------------------- ragged batches
+// One problem of a ragged batch of independent solves (own lattice, operator
+// and two-grid hierarchy), as the kernels of a fused phase read it: every
+// phase is one launch whose CTAs are split among the problems by prefix
+// offsets (off[p] .. off[p+1]-1 belong to problem p).  Filled on the host by
+// ragged_dev_fill.  Precisions are fixed for the fused path: FP32 smoother
+// and coarse vectors, FP64 outer vectors.
+constexpr int kRaggedMaxBasis = 20;
+struct RaggedDev {
+    Geom g;
+    Blocking bk;
+    int nvec;
+    float kappa32;
+    double kappa;
+    const void* U32;   // FP32 links, clover
+    const void* C32;
+    const void* Udd;   // double-float links, clover (FP64-accurate Arnoldi product)
+    const void* Cdd;
+    const void* vecs;  // test vectors (storage of the batch's vector precision)
+    const void* v;     // V_j, FP64 internal
+    void* f32;         // V_j in FP32
+    void* bc;          // coarse right-hand side, FP32 [Vc][2 nvec]
+    void* xc;          // coarse solution
+    void* z;           // Z_j = M V_j, FP32 internal
+    void* w;           // D Z_j, FP64 internal
+    const void* basis[kRaggedMaxBasis];   // V_0 .. V_j (flat FP64 complex)
+    void* vnext;       // V_{j+1}
+    double2* gs_part;  // Gram-Schmidt partials [quantity][n_blas]; the norm partials at gs_part + 2 R
+    double2* gs_coef;  // [0..31] Hessenberg coefficients of pass 0, [32..] of pass 1, [63] |w'|
+    size_t n;          // complex entries of a fine field
+    size_t R;          // offset of the norm partials (in double2)
+    // restart phases: true residual, its norm, V_0 = r / |r|, x += Z y, layout changes
+    const void* U64;   // FP64 links, clover
+    const void* C64;
+    const void* b64;   // right-hand side, iterate, residual (FP64 internal)
+    void* x64;
+    void* r64;
+    const void* rsrc;  // the vector whose norm is taken and normalised into basis[0]: r64, or b64 when x = 0
+    double* npart;     // norm partials [n_blas]
+    double* nval;      // its norm
+    const void* zb[kRaggedMaxBasis];   // Z_0 .. Z_{k-1} (FP32 internal) and the coefficients y
+    double2 yc[kRaggedMaxBasis];
+    int k;
+    const double* canon_in;   // canonical right-hand side and solution
+    double* canon_out;
+    int sap_nr;               // domains per CTA in the SAP half sweep (1 or 2)
+};
+
+// problem p and CTA index within it of this CTA for a prefix-offset table of np problems
+DEV void ragged_locate(const int* __restrict__ off, int np, int& p, int& bx, int& gx) {
+    int lo = 0, hi = np - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    p = lo;
+    bx = b - __ldg(off + lo);
+    gx = __ldg(off + lo + 1) - __ldg(off + lo);
+}

@@ -2,6 +2,8 @@
 // Wilson-clover stencil of Eq. 1 (full and domain-decomposed D_SAP) and the
 // fused SAP half sweep (Sec. 3, SAP listing with minimal-residual domain
 // solves).
+#include <cstring>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -317,16 +319,10 @@ __global__ void clover_expand_kernel(Geom g, const void* C64, double* out) {
 // FP32 / FP16: three CTAs per SM (the stencil streams from HBM and needs the
 // warps); FP64: two (register cap 128)
 template <class P, bool SAP, bool RESID>
-__global__ void __launch_bounds__(kThreads, P::id == 0 ? 2 : 3) dirac_kernel(Geom g, Blocking bk, const void* __restrict__ U,
-                                                         const void* __restrict__ C, const void* in, void* out,
-                                                         const void* b, typename P::T kappa) {
+DEV void dirac_site(const Geom& g, const Blocking& bk, const void* __restrict__ U, const void* __restrict__ C,
+                    const char* src, char* dst, const char* bsrc, typename P::T kappa, int s) {
     using T = typename P::T;
-    const int r = blockIdx.y;
-    const size_t fb = spinor_bytes<P>(g.V);
-    const char* src = (const char*)in + r * fb;
-    char* dst = (char*)out + r * fb;
-    const char* bsrc = RESID ? (const char*)b + r * fb : nullptr;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    {
         int c[4];
         site_coords(g, s, c);
         cx<T> psi[12], acc[12];
@@ -355,6 +351,57 @@ __global__ void __launch_bounds__(kThreads, P::id == 0 ? 2 : 3) dirac_kernel(Geo
             for (int k = 0; k < 12; ++k) acc[k] = psi[k] - acc[k];
         }
         SpinorIO<P>::store(dst, g.V, s, acc);
+    }
+}
+template <class P, bool SAP, bool RESID>
+__global__ void __launch_bounds__(kThreads, P::id == 0 ? 2 : 3) dirac_kernel(Geom g, Blocking bk, const void* __restrict__ U,
+                                                         const void* __restrict__ C, const void* in, void* out,
+                                                         const void* b, typename P::T kappa) {
+    const int r = blockIdx.y;
+    const size_t fb = spinor_bytes<P>(g.V);
+    const char* src = (const char*)in + r * fb;
+    char* dst = (char*)out + r * fb;
+    const char* bsrc = RESID ? (const char*)b + r * fb : nullptr;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x)
+        dirac_site<P, SAP, RESID>(g, bk, U, C, src, dst, bsrc, kappa, s);
+}
+
+// ragged batch, restart phases (site loops over each problem's lattice)
+__global__ void __launch_bounds__(kThreads, 2)
+    resid_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x)
+        dirac_site<P64, false, true>(q.g, q.bk, q.U64, q.C64, (const char*)q.x64, (char*)q.r64, (const char*)q.b64,
+                                     q.kappa, s);
+}
+__global__ void pack_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x) {
+        cx<double> v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = {q.canon_in[(size_t)s * 24 + 2 * k], q.canon_in[(size_t)s * 24 + 2 * k + 1]};
+        SpinorIO<P64>::store(const_cast<void*>(q.b64), q.g.V, s, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = {0.0, 0.0};
+        SpinorIO<P64>::store(q.x64, q.g.V, s, v);
+    }
+}
+__global__ void unpack_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x) {
+        cx<double> v[12];
+        SpinorIO<P64>::load(q.x64, q.g.V, s, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            q.canon_out[(size_t)s * 24 + 2 * k] = v[k].re;
+            q.canon_out[(size_t)s * 24 + 2 * k + 1] = v[k].im;
+        }
     }
 }
 
@@ -439,13 +486,10 @@ DEV void cfa_edag(int mu, cfa v0, cfa v1, cfa& y0, cfa& y1) {
 // sum of two exact-float complex values as an exact pair per component
 DEV cfa cfa_sum(cfa a, cfa b) { return {fa_two_sum(a.re.hi, b.re.hi), fa_two_sum(a.im.hi, b.im.hi)}; }
 
-__global__ void __launch_bounds__(kThreads, 2) dirac_mixed_kernel(Geom g, const void* __restrict__ U,
-                                                               const void* __restrict__ C, const void* in,
-                                                               void* out, dfloat kappa) {
-    const int r = blockIdx.y;
-    const char* src = (const char*)in + r * spinor_bytes<P32>(g.V);
-    char* dst = (char*)out + r * spinor_bytes<P64>(g.V);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+// out(s) = (D in)(s) for one site s
+DEV void dirac_mixed_site(const Geom& g, const void* __restrict__ U, const void* __restrict__ C, const char* src,
+                          char* dst, dfloat kappa, int s) {
+    {
         int c[4];
         site_coords(g, s, c);
         cx<float> pf[12];
@@ -535,6 +579,42 @@ __global__ void __launch_bounds__(kThreads, 2) dirac_mixed_kernel(Geom g, const 
     }
 }
 
+__global__ void __launch_bounds__(kThreads, 2) dirac_mixed_kernel(Geom g, const void* __restrict__ U,
+                                                               const void* __restrict__ C, const void* in,
+                                                               void* out, dfloat kappa) {
+    const int r = blockIdx.y;
+    const char* src = (const char*)in + r * spinor_bytes<P32>(g.V);
+    char* dst = (char*)out + r * spinor_bytes<P64>(g.V);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x)
+        dirac_mixed_site(g, U, C, src, dst, kappa, s);
+}
+
+// ragged batch: w = D z (FP32 z, FP64-accurate product) for every problem in one launch
+__global__ void __launch_bounds__(kThreads, 2)
+    dirac_mixed_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    const dfloat kappa = split_double(q.kappa);
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x)
+        dirac_mixed_site(q.g, q.Udd, q.Cdd, (const char*)q.z, (char*)q.w, kappa, s);
+}
+
+// ragged batch: f32 = (float) v for every problem in one launch
+__global__ void convert_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x) {
+        cx<double> v[12];
+        cx<float> w[12];
+        SpinorIO<P64>::load(q.v, q.g.V, s, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = ccast<float>(v[k]);
+        SpinorIO<P32>::store(q.f32, q.g.V, s, w);
+    }
+}
+
 // x (FP64 internal) += sum_j c_j z_j for FP32 internal z_j: site by site,
 // because the two internal layouts order the complex components differently
 struct ZList {
@@ -553,6 +633,25 @@ __global__ void spinor_axpy_mixed_kernel(Geom g, int k, ZList z, void* x) {
             for (int q = 0; q < 12; ++q) cfma(acc[q], cj, ccast<double>(v[q]));
         }
         SpinorIO<P64>::store(x, g.V, s, acc);
+    }
+}
+
+// ragged batch: x64 += sum_{i<k} yc_i Z_i for every problem (k and y per problem)
+__global__ void xupdate_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x) {
+        cx<double> acc[12];
+        SpinorIO<P64>::load_rw(q.x64, q.g.V, s, acc);
+        for (int j = 0; j < q.k; ++j) {
+            cx<float> v[12];
+            SpinorIO<P32>::load(q.zb[j], q.g.V, s, v);
+            const cx<double> cj = {q.yc[j].x, q.yc[j].y};
+#pragma unroll
+            for (int t = 0; t < 12; ++t) cfma(acc[t], cj, ccast<double>(v[t]));
+        }
+        SpinorIO<P64>::store(q.x64, q.g.V, s, acc);
     }
 }
 
@@ -676,24 +775,22 @@ __global__ void clover_invert_kernel(Geom g, const void* C64, void* out) {
 // NR right-hand sides per CTA (NR = 2 for batches, variant 2): thread (slot, l) works on site l
 // for right-hand side NR * (pair index) + slot; both slots read the same domain's links and
 // clover in lockstep, so one domain's operator occupies the SM's L1 instead of two domains'.
-template <class P, int MAXT, int NR>
-__global__ void __launch_bounds__(MAXT * NR, (MAXT == 256 && NR == 1 && P::id != 0) ? 2 : 1) sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode,
-                                                        const void* __restrict__ U, const void* __restrict__ C,
-                                                        const void* __restrict__ b, void* x, typename P::T kappa,
-                                                        int rhs_fast, int nrhs) {
+// The body of one CTA: domain k of the given colour, right-hand sides NR * rpair + slot; with
+// DS the NR slots take domains NR * k + slot of right-hand side rpair instead (small domains
+// of a ragged batch, two to a CTA)
+template <class P, int NR, bool DS = false>
+DEV void sap_half_body(const Geom& g, const Blocking& bk, int colour, int nmr, int x_mode,
+                       const void* __restrict__ U, const void* __restrict__ C, const void* __restrict__ b, void* x,
+                       typename P::T kappa, int k0, int rpair, int nrhs) {
     using T = typename P::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int vbp = blockDim.x / NR;
     const int slot = NR == 1 ? 0 : threadIdx.x / vbp;
     cx<T>* rsh = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)slot * 12 * vbp;      // [NR][12][vbp]
     T* red = reinterpret_cast<T*>(reinterpret_cast<cx<T>*>(smem_raw) + (size_t)NR * 12 * vbp) + slot * 192;   // [NR][2][3][32]
-
-    // domain of this CTA: the k-th domain of the given colour; right-hand side rr of a batch.
-    // rhs_fast: the right-hand side is the fast grid index, so the CTAs of one domain for all
-    // right-hand sides run together and share the domain's links and clover in L1/L2
-    const int k = rhs_fast ? blockIdx.y : blockIdx.x;
-    const int rr = NR * (rhs_fast ? blockIdx.x : blockIdx.y) + slot;
-    const bool rhs_ok = rr < nrhs;
+    const int rr = DS ? rpair : NR * rpair + slot;
+    const int k = DS ? NR * k0 + slot : k0;
+    const bool rhs_ok = rr < nrhs && (!DS || k < bk.Vc / 2);
     const int h0 = bk.C[0] / 2;
     int rest = k / h0;
     int X1 = rest % bk.C[1];
@@ -815,6 +912,32 @@ __global__ void __launch_bounds__(MAXT * NR, (MAXT == 256 && NR == 1 && P::id !=
         }
         SpinorIO<P>::store(x, g.V, s, z);
     }
+}
+
+// domain of a CTA: the k-th domain of the given colour; right-hand side group of a batch.
+// rhs_fast: the right-hand side is the fast grid index, so the CTAs of one domain for all
+// right-hand sides run together and share the domain's links and clover in L1/L2
+template <class P, int MAXT, int NR>
+__global__ void __launch_bounds__(MAXT * NR, (MAXT == 256 && NR == 1 && P::id != 0) ? 2 : 1)
+    sap_half_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode, const void* __restrict__ U,
+                    const void* __restrict__ C, const void* __restrict__ b, void* x, typename P::T kappa,
+                    int rhs_fast, int nrhs) {
+    sap_half_body<P, NR>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, rhs_fast ? blockIdx.y : blockIdx.x,
+                         rhs_fast ? blockIdx.x : blockIdx.y, nrhs);
+}
+
+// the half sweep for every problem of a ragged batch in one launch: CTA ranges per problem
+// from the prefix table off (the problem's domains of this colour, sap_nr to a CTA), FP32,
+// right-hand side V_j in f32, iterate Z_j in z.  blockDim covers the largest domain; a
+// problem whose domains fit half of it takes two domains per CTA (sap_nr = 2)
+__global__ void __launch_bounds__(256, 2)
+    sap_half_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np, int colour,
+                           int nmr) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    if (q.sap_nr == 2) sap_half_body<P32, 2, true>(q.g, q.bk, colour, nmr, 0, q.U32, q.C32, q.f32, q.z, q.kappa32, bx, 0, 1);
+    else sap_half_body<P32, 1>(q.g, q.bk, colour, nmr, 0, q.U32, q.C32, q.f32, q.z, q.kappa32, bx, 0, 1);
 }
 
 // ------------------------------------------------------------ SAP half sweep, even-odd domain solves
@@ -1557,4 +1680,100 @@ cudaError_t launch_sap_half(int prec, const GeomH& g, const BlockH& bk, int colo
     if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, 1, st);
     if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, 1, st);
     return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, 1, st);
+}
+
+// ---------------------------------------------------------------- ragged batches
+size_t ragged_dev_bytes() { return sizeof(RaggedDev); }
+
+int ragged_dev_fill(void* dst, const RaggedProbH& h) {
+    if (h.nbasis < 1 || h.nbasis > kRaggedMaxBasis) return -1;
+    RaggedDev q = {};
+    q.g = make_geom(h.g);
+    q.bk = make_blocking(h.g, h.blk);
+    q.nvec = h.nvec;
+    q.kappa = h.kappa;
+    q.kappa32 = (float)h.kappa;
+    q.U32 = h.U32;
+    q.C32 = h.C32;
+    q.Udd = h.Udd;
+    q.Cdd = h.Cdd;
+    q.vecs = h.vecs;
+    q.v = h.v;
+    q.f32 = h.f32;
+    q.bc = h.bc;
+    q.xc = h.xc;
+    q.z = h.z;
+    q.w = h.w;
+    for (int i = 0; i < h.nbasis; ++i) q.basis[i] = h.basis[i];
+    q.vnext = h.vnext;
+    q.gs_part = h.gs_part;
+    q.gs_coef = h.gs_coef;
+    q.n = h.n;
+    q.R = h.R;
+    q.U64 = h.U64;
+    q.C64 = h.C64;
+    q.b64 = h.b64;
+    q.x64 = h.x64;
+    q.r64 = h.r64;
+    q.rsrc = h.rsrc;
+    q.npart = h.npart;
+    q.nval = h.nval;
+    if (h.k < 0 || h.k > kRaggedMaxBasis) return -1;
+    q.k = h.k;
+    for (int i = 0; i < h.k; ++i) {
+        q.zb[i] = h.zb[i];
+        q.yc[i] = h.yc[i];
+    }
+    q.canon_in = h.canon_in;
+    q.canon_out = h.canon_out;
+    if (h.sap_nr != 1 && h.sap_nr != 2) return -1;
+    q.sap_nr = h.sap_nr;
+    memcpy(dst, &q, sizeof q);
+    return 0;
+}
+
+int ragged_site_ctas(int V) {
+    int c = (V + kThreads - 1) / kThreads;
+    return c < 1 ? 1 : c;
+}
+
+cudaError_t launch_convert_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    (note_launch(), convert_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+    return cudaGetLastError();
+}
+cudaError_t launch_dirac_mixed_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    (note_launch(), dirac_mixed_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+    return cudaGetLastError();
+}
+int ragged_sap_threads(int max_vb) {
+    const int t = (max_vb + 31) / 32 * 32;
+    return t > 128 ? 256 : 2 * t;
+}
+int ragged_sap_nr(int vb, int max_vb) {
+    const int half = ragged_sap_threads(max_vb) / 2;   // a multiple of 32
+    return vb <= half ? 2 : 1;
+}
+cudaError_t launch_sap_half_ragged(const void* d, const int* off, int np, int ctas, int max_vb, int colour, int nmr,
+                                   cudaStream_t st) {
+    const int threads = ragged_sap_threads(max_vb);
+    if (max_vb > 256 || ctas < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)12 * threads * sizeof(cx<float>) + 2 * 2 * 3 * 32 * sizeof(float);
+    (note_launch(), sap_half_ragged_kernel<<<ctas, threads, smem, st>>>((const RaggedDev*)d, off, np, colour, nmr));
+    return cudaGetLastError();
+}
+cudaError_t launch_pack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    (note_launch(), pack_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+    return cudaGetLastError();
+}
+cudaError_t launch_unpack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    (note_launch(), unpack_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+    return cudaGetLastError();
+}
+cudaError_t launch_resid_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    (note_launch(), resid_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+    return cudaGetLastError();
+}
+cudaError_t launch_xupdate_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    (note_launch(), xupdate_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+    return cudaGetLastError();
 }

@@ -139,6 +139,31 @@ cudaError_t launch_coarse_bicgstab(int cprec, const GeomH& gc, int nc, const voi
                                    void* part, void* state, int cluster, cudaStream_t s, int nb = 1,
                                    int xgroup = 0);
 int coarse_solver_max_xgroup(int cprec, int nc, int nb);
+// several independent single-RHS solves in one launch, one thread-block cluster per problem
+// (each with its own vectors, operator, partials and state word); dev_args is device scratch of
+// n * coarse_solver_desc_bytes(); all problems share cprec
+struct CoarseSolveDesc {
+    int cprec;
+    GeomH gc;
+    int nc;
+    const void* B;
+    const void* b;
+    void* x;
+    void* rt;
+    void* R[5];
+    void* U[5];
+    int ell;
+    double tol;
+    int maxit;
+    void* part;
+    void* state;
+    int xgroup;
+};
+size_t coarse_solver_desc_bytes();
+// host_args: pinned host staging of n * coarse_solver_desc_bytes() (not rewritten before the
+// copy on s is done); dev_args: device memory of the same size
+cudaError_t launch_coarse_bicgstab_multi(const CoarseSolveDesc* d, int n, void* host_args, void* dev_args,
+                                         cudaStream_t s);
 // multi-RHS coarse stencil on the tensor cores (coarse_tc.cu): bfloat16 operands, FP32
 // accumulation; needs Nc % 16 == 0 and Nc <= 64.  The operator is first copied into the
 // tensor-core operand image ([V][2Nc][9Nc] bfloat16 in 8 x 8 core-matrix order) from its
@@ -188,3 +213,78 @@ cudaError_t launch_scale_real(int prec, double a, const void* x, void* y, size_t
 // multi_dot plus |b|^2 as quantity k (double2 (n2, 0)), k <= 19
 cudaError_t launch_multi_dot_norm(int prec, int k, const void* const* a, const void* b, size_t n, double2* partials,
                                   cudaStream_t s);
+
+// ---- ragged batch: one launch per phase over per-problem descriptors ----
+// One problem of a fused ragged batch (host view of the device descriptor; every pointer is
+// device memory owned by the problem's hierarchy).  The fused path fixes the precisions:
+// FP32 smoother, FP32 coarse vectors and operator, FP64 outer vectors; the test vectors may
+// be stored in any vector precision (the same for the whole batch).
+struct RaggedProbH {
+    GeomH g;
+    BlockH blk;
+    int nvec;
+    double kappa;
+    const void* U32;            // FP32 links and clover
+    const void* C32;
+    const void* Udd;            // double-float links and clover
+    const void* Cdd;
+    const void* vecs;           // test vectors
+    const void* v;              // V_j (FP64 internal)
+    void* f32;                  // V_j in FP32
+    void* bc;                   // coarse right-hand side / solution, FP32 [Vc][2 nvec]
+    void* xc;
+    void* z;                    // Z_j = M V_j (FP32 internal)
+    void* w;                    // D Z_j (FP64 internal)
+    const void* basis[20];      // V_0 .. V_j
+    int nbasis;                 // j + 1
+    void* vnext;                // V_{j+1}
+    double2* gs_part;           // Gram-Schmidt partials (2 R + ctas doubles2 at least)
+    double2* gs_coef;           // 64 double2: pass-0 coefficients, pass-1 at 32, |w'| at 63
+    size_t n;                   // complex entries of a fine field
+    size_t R;                   // offset of the norm partials in gs_part (double2)
+    const void* U64;            // FP64 links and clover (true residual)
+    const void* C64;
+    const void* b64;            // right-hand side, iterate, residual (FP64 internal)
+    void* x64;
+    void* r64;
+    const void* rsrc;           // vector normalised into basis[0] (r64, or b64 while x = 0)
+    double* npart;              // its norm: partials (ragged_blas_ctas(n) doubles) and value
+    double* nval;
+    const void* zb[20];         // x += sum_{i<k} yc[i] zb[i] (FP32 internal Z_i)
+    double2 yc[20];
+    int k;
+    const double* canon_in;     // canonical right-hand side (packed into b64) and solution
+    double* canon_out;
+    int sap_nr;                 // ragged_sap_nr(block sites, largest block of the batch)
+};
+size_t ragged_dev_bytes();
+// writes the device descriptor of h to dst (ragged_dev_bytes() bytes of host memory); -1 if invalid
+int ragged_dev_fill(void* dst, const RaggedProbH& h);
+// CTAs a problem takes in the site-loop phases (conversion, Arnoldi product) and in the BLAS phases
+int ragged_site_ctas(int V);
+int ragged_blas_ctas(size_t n);
+// every launcher: d = device array of np descriptors, off = device prefix table of np + 1 CTA
+// offsets for that phase (off[np] = ctas); blocks of up to 256 sites
+cudaError_t launch_convert_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);        // f32 = v
+cudaError_t launch_restrict_ragged(int vprec, const void* d, const int* off, int np, int ctas, int max_vb,
+                                   int max_nvec, cudaStream_t s);                                        // bc = R f32
+cudaError_t launch_prolong_ragged(int vprec, const void* d, const int* off, int np, int ctas, int max_vb,
+                                  int max_nvec, cudaStream_t s);                                         // z = P xc
+// one SAP half sweep (x_mode 0) with right-hand side f32 and iterate z: CTAs of
+// ragged_sap_threads(max_vb) threads, a problem with blocks of vb sites taking
+// ceil(Vc / 2 / ragged_sap_nr(vb, max_vb)) of them
+int ragged_sap_threads(int max_vb);
+int ragged_sap_nr(int vb, int max_vb);
+cudaError_t launch_sap_half_ragged(const void* d, const int* off, int np, int ctas, int max_vb, int colour, int nmr,
+                                   cudaStream_t s);
+cudaError_t launch_dirac_mixed_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);    // w = D z
+// one classical Gram-Schmidt pass against k = j + 1 basis vectors, then V_{j+1} = w' / |w'|
+cudaError_t launch_gs_ragged(int k, const void* d, const int* off, int np, int ctas, int pass, cudaStream_t s);
+// restart phases of a fused ragged batch (tables of the problems concerned):
+// b64 = canon_in and x64 = 0; canon_out = x64; r64 = b64 - D x64 (FP64); the norm of rsrc into
+// nval and basis[0] = rsrc / |rsrc| (two launches); x64 += sum_i yc[i] zb[i]
+cudaError_t launch_pack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
+cudaError_t launch_unpack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
+cudaError_t launch_resid_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
+cudaError_t launch_norm_v0_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
+cudaError_t launch_xupdate_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);

@@ -128,8 +128,8 @@ template <int N> DEV int transposed_index(int lane) {
 // group of test vectors (their loads in flight together), summed over the warp
 // by transposed shuffles and over the warps in shared memory.
 template <class PF, class PV, typename TC>
-__global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
-                                const void* __restrict__ fine, void* coarse) {
+DEV void restrict_body(const Geom& g, const Blocking& bk, int nvec, const void* __restrict__ vecs,
+                       const void* __restrict__ fine, void* coarse, int by, int gy) {
     using T = typename PF::T;
     constexpr int G = kVecGroup<PV>, NQ = 4 * G;   // per vector: d0.re, d0.im, d1.re, d1.im
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,14 +138,9 @@ __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __res
     const int nc = 2 * nvec;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const size_t vb = spinor_bytes<PV>(g.V);
-    // right-hand side = blockIdx.x (the fast grid index): the CTAs of one block for all
-    // right-hand sides of a batch are launched together and read the same test-vector lines
-    // at about the same time, so L2 serves the repeats and DRAM sees each line about once
-    fine = (const char*)fine + blockIdx.x * spinor_bytes<PF>(g.V);
-    coarse = (char*)coarse + blockIdx.x * (size_t)bk.Vc * nc * sizeof(cx<TC>);
     const int qi = transposed_index<NQ>(lane);
     const bool writer = (lane & (32 / NQ - 1)) == 0;
-    for (int Xi = blockIdx.y; Xi < bk.Vc; Xi += gridDim.y) {
+    for (int Xi = by; Xi < bk.Vc; Xi += gy) {
         const int l = threadIdx.x;
         const bool active = l < bk.Vb;
         int c[4], s = 0;
@@ -191,22 +186,38 @@ __global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __res
     }
 }
 
+// right-hand side = blockIdx.x (the fast grid index): the CTAs of one block for all
+// right-hand sides of a batch are launched together and read the same test-vector lines
+// at about the same time, so L2 serves the repeats and DRAM sees each line about once
+template <class PF, class PV, typename TC>
+__global__ void restrict_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
+                                const void* __restrict__ fine, void* coarse) {
+    restrict_body<PF, PV, TC>(g, bk, nvec, vecs, (const char*)fine + blockIdx.x * spinor_bytes<PF>(g.V),
+                              (char*)coarse + blockIdx.x * (size_t)bk.Vc * 2 * nvec * sizeof(cx<TC>), blockIdx.y,
+                              gridDim.y);
+}
+// ragged batch: bc = R f32 for every problem in one launch (one CTA per block)
+template <class PV>
+__global__ void restrict_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    restrict_body<P32, PV, float>(q.g, q.bk, q.nvec, q.vecs, q.f32, q.bc, bx, gx);
+}
+
 // ------------------------------------------------------------ prolongation
 // One CTA per block, one thread per site: psi'(x) = sum_{s,i} x_c(X, s, i) P_s v_i(x)
 // with the loads of a group of test vectors in flight together.
 template <class PF, class PV, typename TC>
-__global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
-                               const void* __restrict__ coarse, void* fine) {
+DEV void prolong_body(const Geom& g, const Blocking& bk, int nvec, const void* __restrict__ vecs,
+                      const void* __restrict__ coarse, void* fine, int by, int gy) {
     using T = typename PF::T;
     constexpr int G = kVecGroup<PV>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* xc = reinterpret_cast<cx<T>*>(smem_raw);   // [2*nvec]
     const int nc = 2 * nvec;
     const size_t vb = spinor_bytes<PV>(g.V);
-    // right-hand side = blockIdx.x, as in restrict_kernel
-    coarse = (const char*)coarse + blockIdx.x * (size_t)bk.Vc * nc * sizeof(cx<TC>);
-    fine = (char*)fine + blockIdx.x * spinor_bytes<PF>(g.V);
-    for (int Xi = blockIdx.y; Xi < bk.Vc; Xi += gridDim.y) {
+    for (int Xi = by; Xi < bk.Vc; Xi += gy) {
         for (int j = threadIdx.x; j < nc; j += blockDim.x)
             xc[j] = ccast<T>(CStore<TC>::ld(coarse, (size_t)Xi * nc + j));
         __syncthreads();
@@ -237,6 +248,23 @@ __global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __rest
         }
         __syncthreads();
     }
+}
+
+// right-hand side = blockIdx.x, as in restrict_kernel
+template <class PF, class PV, typename TC>
+__global__ void prolong_kernel(Geom g, Blocking bk, int nvec, const void* __restrict__ vecs,
+                               const void* __restrict__ coarse, void* fine) {
+    prolong_body<PF, PV, TC>(g, bk, nvec, vecs,
+                             (const char*)coarse + blockIdx.x * (size_t)bk.Vc * 2 * nvec * sizeof(cx<TC>),
+                             (char*)fine + blockIdx.x * spinor_bytes<PF>(g.V), blockIdx.y, gridDim.y);
+}
+// ragged batch: z = P xc for every problem in one launch (one CTA per block)
+template <class PV>
+__global__ void prolong_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    prolong_body<P32, PV, float>(q.g, q.bk, q.nvec, q.vecs, q.xc, q.z, bx, gx);
 }
 
 // ------------------------------------------------------------ orthonormalisation
@@ -539,5 +567,28 @@ cudaError_t launch_galerkin_fine(int vprec, int cprec, const GeomH& gh, const Bl
         if (cprec == 0) (note_launch(), galerkin_kernel<P32, double><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B));
         else (note_launch(), galerkin_kernel<P32, float><<<grid, th, smem, st>>>(g, bk, nvec, vecs, U, C, (float)kappa, B));
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- ragged batches
+// blockDim: the largest problem's block, rounded up to whole warps; shared memory for that many warps
+cudaError_t launch_restrict_ragged(int vprec, const void* d, const int* off, int np, int ctas, int max_vb, int max_nvec,
+                                   cudaStream_t st) {
+    const int th = (max_vb + 31) / 32 * 32;
+    const size_t smem = (size_t)(th / 32) * 2 * max_nvec * sizeof(cx<float>);
+    const RaggedDev* dd = (const RaggedDev*)d;
+    if (vprec == 0) (note_launch(), restrict_ragged_kernel<P64><<<ctas, th, smem, st>>>(dd, off, np));
+    else if (vprec == 1) (note_launch(), restrict_ragged_kernel<P32><<<ctas, th, smem, st>>>(dd, off, np));
+    else (note_launch(), restrict_ragged_kernel<P16><<<ctas, th, smem, st>>>(dd, off, np));
+    return cudaGetLastError();
+}
+cudaError_t launch_prolong_ragged(int vprec, const void* d, const int* off, int np, int ctas, int max_vb, int max_nvec,
+                                  cudaStream_t st) {
+    const int th = (max_vb + 31) / 32 * 32;
+    const size_t smem = (size_t)2 * max_nvec * sizeof(cx<float>);
+    const RaggedDev* dd = (const RaggedDev*)d;
+    if (vprec == 0) (note_launch(), prolong_ragged_kernel<P64><<<ctas, th, smem, st>>>(dd, off, np));
+    else if (vprec == 1) (note_launch(), prolong_ragged_kernel<P32><<<ctas, th, smem, st>>>(dd, off, np));
+    else (note_launch(), prolong_ragged_kernel<P16><<<ctas, th, smem, st>>>(dd, off, np));
     return cudaGetLastError();
 }
