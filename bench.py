@@ -593,12 +593,14 @@ def run_dirac(args):
     hbm, kind = _peaks()
     stream = torch.cuda.current_stream()
     per = {}
-    # f64x: float input, FP64 output, links / clover as float hi/lo pairs (full 3x3: 4 x 144 B)
-    bytes_site = {"f64": 1536, "f32": 672, "f16": 344, "f64x": 96 + 192 + 4 * 144 + 576}
+    # f64x: float input, FP64 output, links / clover as float hi/lo pairs (full 3x3: 4 x 144 B);
+    # f64d: the same arithmetic on FP64 input (every value split into a float pair)
+    bytes_site = {"f64": 1536, "f32": 672, "f16": 344, "f64x": 96 + 192 + 4 * 144 + 576,
+                  "f64d": 192 + 192 + 4 * 144 + 576}
     with ClockSampler() as clk:
         for name, prec in (("f64", capi.AMG_F64), ("f32", capi.AMG_F32), ("f16", capi.AMG_F16),
-                           ("f64x", capi.AMG_F64X)):
-            x = torch.from_numpy(psi).to(torch.float64 if name == "f64" else torch.float32).cuda()
+                           ("f64x", capi.AMG_F64X), ("f64d", capi.AMG_F64D)):
+            x = torch.from_numpy(psi).to(torch.float64 if name in ("f64", "f64d") else torch.float32).cuda()
             capi.amg_dirac_time(d, x, 1, prec, args.warmup, stream=stream)          # warm-up launches
             l0 = capi.amg_launch_count()
             ms = capi.amg_dirac_time(d, x, 1, prec, args.steps, stream=stream)
@@ -707,6 +709,66 @@ def run_mixed3(args):
     print(json.dumps(line), flush=True)
 
 
+def _ragged_pool(capi, hs, warm_b, B, stream):
+    """The ragged batch on the stream pool with per-problem step graphs."""
+    import torch
+    capi.amg_set_ragged_fusion(False)
+    try:
+        capi.amg_solve_ragged(hs, warm_b, [torch.zeros_like(b) for b in warm_b], TOL, 300)   # captures the graphs
+        Xp = [torch.zeros_like(b) for b in B]
+        torch.cuda.synchronize()
+        l0 = capi.amg_launch_count()
+        t0 = time.perf_counter()
+        st, infos = capi.amg_solve_ragged(hs, B, Xp, TOL, 300, stream=stream)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3, capi.amg_launch_count() - l0, infos
+    finally:
+        capi.amg_set_ragged_fusion(True)
+
+
+def _ragged_sequential(capi, hs, B, X, stream):
+    """The batch's solves issued one after another through amg_solve."""
+    import torch
+    for x in X:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ok = []
+    for h, b, x in zip(hs, B, X):
+        st, info = capi.amg_solve(h, b, x, 1, TOL, 300, stream=stream)
+        ok.append(info.converged == 1 and info.true_rel_residual <= TOL)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1e3, ok
+
+
+def _ragged_fp64(capi, shapes, probs, init, B, stream, ragged_ms_per_rhs):
+    """The plain method all in FP64 on two problems of each size, one after another."""
+    import torch
+    sample = list(range(6))
+    h64 = []
+    for i in sample:
+        dims, block = shapes[i % 3]
+        p = capi.amg_params_default()
+        for mu in range(4):
+            p.block[0][mu] = block[mu]
+        p.nvec[0] = 24
+        p.prec_smoother = p.prec_coarsest = capi.AMG_F64
+        h64.append(capi.amg_setup(probs[i][3], p, [init[dims]]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ok64 = []
+    for i, hh in zip(sample, h64):
+        x = torch.zeros_like(B[i])
+        st, info = capi.amg_solve(hh, B[i], x, 1, TOL, 300, stream=stream)
+        ok64.append(info.converged == 1 and info.true_rel_residual <= TOL)
+    torch.cuda.synchronize()
+    ms64 = (time.perf_counter() - t0) * 1e3
+    for hh in h64:
+        capi.amg_hierarchy_destroy(hh)
+    return {"problems": sample, "ms_per_rhs": ms64 / len(sample), "converged": all(ok64),
+            "ragged_ms_per_rhs_same_mix": ragged_ms_per_rhs}
+
+
 def run_ragged(args):
     """Ragged batch: 64 independent single-RHS solves, problem i (gauge seed
     100 + i) on 8^4 (4^4 blocks), 12^4 (3^4 blocks) or 16^3x32 (4^4 blocks)
@@ -752,61 +814,25 @@ def run_ragged(args):
     with ClockSampler() as clk:
         l0 = capi.amg_launch_count()
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed")
         st, infos = capi.amg_solve_ragged(hs, B, X, TOL, 300, stream=stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ragged_ms = (time.perf_counter() - t0) * 1e3
         launches = capi.amg_launch_count() - l0
     ok = all(i.converged == 1 and i.true_rel_residual <= TOL for i in infos)
     # the same batch on the stream pool with per-problem step graphs (the unfused form)
-    capi.amg_set_ragged_fusion(False)
-    capi.amg_solve_ragged(hs, warm_b, [torch.zeros_like(b) for b in warm_b], TOL, 300)   # captures the graphs
-    Xp = [torch.zeros_like(b) for b in B]
-    torch.cuda.synchronize()
-    lp0 = capi.amg_launch_count()
-    t0 = time.perf_counter()
-    st, infos_pool = capi.amg_solve_ragged(hs, B, Xp, TOL, 300, stream=stream)
-    torch.cuda.synchronize()
-    pool_ms = (time.perf_counter() - t0) * 1e3
-    pool_launches = capi.amg_launch_count() - lp0
-    capi.amg_set_ragged_fusion(True)
-    del Xp
+    pool_ms, pool_launches, infos_pool = None, None, []
+    if not args.fused_only:
+        pool_ms, pool_launches, infos_pool = _ragged_pool(capi, hs, warm_b, B, stream)
     # the same solves one after another
-    for x in X:
-        x.zero_()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    seq = []
-    for h, b, x in zip(hs, B, X):
-        st, info = capi.amg_solve(h, b, x, 1, TOL, 300, stream=stream)
-        seq.append(info.converged == 1 and info.true_rel_residual <= TOL)
-    torch.cuda.synchronize()
-    seq_ms = (time.perf_counter() - t0) * 1e3
+    seq_ms, seq = None, []
+    if not args.fused_only:
+        seq_ms, seq = _ragged_sequential(capi, hs, B, X, stream)
     # the plain method all in FP64 on a sample of the batch (two problems of each size), one after another
     fp64 = None
-    if not args.no_fp64_compare:
-        sample = list(range(6))
-        h64 = []
-        for i in sample:
-            dims, block = shapes[i % 3]
-            p = capi.amg_params_default()
-            for mu in range(4):
-                p.block[0][mu] = block[mu]
-            p.nvec[0] = 24
-            p.prec_smoother = p.prec_coarsest = capi.AMG_F64
-            h64.append(capi.amg_setup(probs[i][3], p, [init[dims]]))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ok64 = []
-        for i, hh in zip(sample, h64):
-            x = torch.zeros_like(B[i])
-            st, info = capi.amg_solve(hh, B[i], x, 1, TOL, 300, stream=stream)
-            ok64.append(info.converged == 1 and info.true_rel_residual <= TOL)
-        torch.cuda.synchronize()
-        ms64 = (time.perf_counter() - t0) * 1e3
-        for hh in h64:
-            capi.amg_hierarchy_destroy(hh)
-        fp64 = {"problems": sample, "ms_per_rhs": ms64 / len(sample), "converged": all(ok64),
-                "ragged_ms_per_rhs_same_mix": ragged_ms / n}
+    if not args.no_fp64_compare and not args.fused_only:
+        fp64 = _ragged_fp64(capi, shapes, probs, init, B, stream, ragged_ms / n)
     line = {"metric": METRIC, "value": ragged_ms / n, "unit": "ms/RHS", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": ragged_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
@@ -818,8 +844,9 @@ def run_ragged(args):
                        "ragged_ms": ragged_ms, "sequential_ms": seq_ms, "sequential_converged": all(seq),
                        "stream_pool_ms": pool_ms, "stream_pool_launches": pool_launches,
                        "stream_pool_converged": all(i.converged == 1 for i in infos_pool),
-                       "speedup_vs_stream_pool": pool_ms / ragged_ms,
-                       "speedup_vs_sequential": seq_ms / ragged_ms, "plain_fp64_sequential_sample": fp64,
+                       "speedup_vs_stream_pool": pool_ms / ragged_ms if pool_ms else None,
+                       "speedup_vs_sequential": seq_ms / ragged_ms if seq_ms else None,
+                       "plain_fp64_sequential_sample": fp64,
                        "outer_iters": [int(i.iters) for i in infos]},
             "gpu_launches": launches, "clocks": clk.summary()}
     for dims, lat, g, d, h in probs:
@@ -1071,6 +1098,8 @@ def main():
     ap.add_argument("--dims", default=None,
                     help="propagator workload on a smaller lattice Lx,Ly,Lz,Lt (profiling; not the headline)")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--fused-only", action="store_true",
+                    help="ragged workload: time the fused batch only (no stream-pool or one-by-one comparison)")
     ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1, 2],
                     help="SAP kernel: 0 operator through L1/L2 (default), 1 staged in shared memory, "
                          "2 two right-hand sides of a batch per CTA, -1 autotune")

@@ -56,9 +56,12 @@ typedef enum {
     AMG_F32 = 1,   /* float storage and arithmetic */
     AMG_F16 = 2,   /* fine fields stored as half with a per-site float scale, float arithmetic */
     AMG_BF16 = 3,  /* coarse operator stored as bfloat16, float accumulation */
-    AMG_F64X = 4   /* amg_apply_D only: float input (taken as exact), double output, FP64-accurate
+    AMG_F64X = 4,  /* amg_apply_D only: float input (taken as exact), double output, FP64-accurate
                       double-float arithmetic with FP64 links and clover (the outer solver's Arnoldi
                       product for vectors produced by the FP32 preconditioner) */
+    AMG_F64D = 5   /* amg_apply_D only: double input and output, every input value split into a float
+                      pair, the same double-float arithmetic (about 46 significant bits; the outer
+                      solver's true residual b - D x when the smoother is not FP64) */
 } amg_prec;
 
 #define AMG_MAX_LEVELS 4
@@ -229,8 +232,9 @@ void amg_dirac_destroy(amg_dirac* d);
 amg_status amg_dirac_get_clover(amg_dirac* d, double* host_out);
 
 /* out = D in (Eq. 1) for nrhs canonical fine vectors (device pointers).
- * prec selects the storage/arithmetic of D and the element type of in/out.
- * in and out must not alias. */
+ * prec selects the storage/arithmetic of D and the element type of in/out:
+ * double for AMG_F64 and AMG_F64D, float for AMG_F32 / AMG_F16, float in and
+ * double out for AMG_F64X.  in and out must not alias. */
 amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s);
 
 /* out = D in, exactly as amg_apply_D, but without allocating device memory.

@@ -15,7 +15,7 @@ import numpy as np
 from .build import LIB
 
 AMG_OK, AMG_EINVAL, AMG_ENOMEM, AMG_ECUDA, AMG_NOT_CONVERGED, AMG_NAN, AMG_TIMEOUT, AMG_EIO = range(8)
-AMG_F64, AMG_F32, AMG_F16, AMG_BF16, AMG_F64X = range(5)
+AMG_F64, AMG_F32, AMG_F16, AMG_BF16, AMG_F64X, AMG_F64D = range(6)
 AMG_MAX_LEVELS = 4
 
 STATUS_NAMES = {0: "AMG_OK", 1: "AMG_EINVAL", 2: "AMG_ENOMEM", 3: "AMG_ECUDA", 4: "AMG_NOT_CONVERGED",

@@ -59,6 +59,7 @@ struct amg_dirac {
     DevBuf C[4];
     DevBuf Ci[3];    // clover inverse A^{-1} by precision (F64, F32, F16), built when an even-odd smoother needs it
     DevBuf in, out;   // call scratch for the canonical-layout entry points
+    DevBuf split;     // AMG_F64D: the FP32 parts hi, lo of the input
 };
 
 namespace {
@@ -243,6 +244,7 @@ struct amg_hierarchy {
     PhaseTimer timer;
     int err_flag_host = 0;
     DevBuf err_flag;
+    DevBuf ac_in, ac_out;   // amg_apply_coarse: vectors converted to the level's precision (kept)
     int coarse_cycles = 0;
     int sap_variant[3] = {0, 0, 0};      // chosen SAP kernel per smoother precision, one right-hand side
     int sap_variant_nb[3] = {0, 0, 0};   // the same for batches (the staged kernel then takes two per CTA)
@@ -351,6 +353,20 @@ amg_status fine_D(amg_hierarchy* h, int prec, const void* in, void* out, const v
     amg_dirac* d = h->d;
     CK(launch_dirac(prec, fine_geom(h), nullptr, d->gauge->U[prec].p, d->C[prec].p, in, out, b, d->kappa, nb, s));
     return AMG_OK;
+}
+
+// r = b - D x for FP64 internal x and b (the outer solver's true residual, reading C29): the
+// double-float stencil where the FP64-valued link and clover pairs exist (FP32 smoother),
+// else the FP64 stencil
+amg_status true_residual(amg_hierarchy* h, const void* x, void* r, const void* b, int nb, cudaStream_t s) {
+    amg_dirac* d = h->d;
+    if (h->fp != 0 && d->gauge->U[3].p && d->C[3].p && d->gauge->U[1].p && d->C[1].p) {
+        // x split into the FP32 workspaces (free between cycles; nb fields each when fp != 0)
+        CK(launch_dirac_dd(fine_geom(h), d->gauge->U[3].p, d->C[3].p, d->gauge->U[1].p, d->C[1].p, x, r, b,
+                           d->kappa, nb, h->fb[1].p, h->fx[1].p, s));
+        return AMG_OK;
+    }
+    return fine_D(h, 0, x, r, b, nb, s);
 }
 
 amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_zero, int nb, cudaStream_t s) {
@@ -986,7 +1002,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             x_is_zero = false;
         } else {
             h->timer.start(PH_RESID, s);
-            TRY(fine_D(h, 0, x, h->orr.p, b, nb, s));   // r = b - D x
+            TRY(true_residual(h, x, h->orr.p, b, nb, s));   // r = b - D x
             h->timer.stop(s);
             TRY(batch_norms(h, nb, h->orr.p, rn2, s));
         }
@@ -1644,7 +1660,7 @@ amg_status fbicgstab(amg_hierarchy* h, const void* b, void* x, bool x_nonzero, d
             x_is_zero = false;
         } else {
             h->timer.start(PH_RESID, s);
-            TRY(fine_D(h, 0, x, r, b, 1, s));
+            TRY(true_residual(h, x, r, b, 1, s));
             h->timer.stop(s);
             double rn2;
             TRY(red.norm2(0, r, n, &rn2, s));
@@ -1817,7 +1833,7 @@ amg_status fgmres_ragged(std::vector<RaggedProb>& P, const std::vector<cudaStrea
         for (auto& p : P) {
             if (p.r.done) continue;
             if (p.started) {
-                TRY(fine_D(p.h, 0, p.h->ox.p, p.h->orr.p, p.h->ob.p, 1, p.st));
+                TRY(true_residual(p.h, p.h->ox.p, p.h->orr.p, p.h->ob.p, 1, p.st));
                 TRY(ragged_norm_launch(p, p.h->orr.p));
             }
         }
@@ -2048,6 +2064,7 @@ amg_status fused_tables(FusedBatch& F, std::vector<RaggedProb>& P, const std::ve
         q.vecs = rp_vecs(h);
         q.v = h->oV[j]->p;
         q.f32 = h->fb[1].p;
+        q.f32b = h->fx[1].p;
         q.bc = h->cw[1][0]->p;
         q.xc = h->cw[1][1]->p;
         q.z = h->oZ[j]->p;
@@ -2479,7 +2496,19 @@ static amg_status apply_fine_canonical(amg_dirac* d, const BlockH* sb, const voi
         CK(launch_unpack_spinor(0, g, d->out.p, out, nrhs, s));
         return AMG_OK;
     }
-    if (prec < 0 || prec > 2) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32, AMG_F16 (or AMG_F64X for D)");
+    if (prec == AMG_F64D && !sb) {
+        CK(d->in.ensure(fine_spinor_bytes(0, g.V) * nrhs));
+        CK(d->out.ensure(fine_spinor_bytes(0, g.V) * nrhs));
+        CK(launch_pack_spinor(0, g, in, d->in.p, nrhs, s));
+        const size_t f32 = fine_spinor_bytes(1, g.V) * nrhs;
+        CK(d->split.ensure(2 * f32));
+        CK(launch_dirac_dd(g, d->gauge->U[3].p, d->C[3].p, d->gauge->U[1].p, d->C[1].p, d->in.p, d->out.p, nullptr,
+                           d->kappa, nrhs, d->split.p, (char*)d->split.p + f32, s));
+        CK(launch_unpack_spinor(0, g, d->out.p, out, nrhs, s));
+        return AMG_OK;
+    }
+    if (prec < 0 || prec > 2)
+        return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32, AMG_F16 (or AMG_F64X / AMG_F64D for D)");
     size_t fb = fine_spinor_bytes(prec, g.V) * nrhs;
     CK(d->in.ensure(fb));
     CK(d->out.ensure(fb));
@@ -2496,14 +2525,16 @@ amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_pr
 amg_status amg_dirac_time(amg_dirac* d, const void* in, int nrhs, amg_prec prec, int reps, amg_stream s,
                           float* ms_per_apply) {
     if (!d || !in || !ms_per_apply || nrhs < 1 || reps < 1) return fail(AMG_EINVAL, "bad argument");
-    if (prec < 0 || prec > 4 || prec == AMG_BF16) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32, AMG_F16 or AMG_F64X");
+    if (prec < 0 || prec > 5 || prec == AMG_BF16)
+        return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32, AMG_F16, AMG_F64X or AMG_F64D");
     const GeomH& g = d->gauge->lat->g;
     cudaStream_t st = (cudaStream_t)s;
-    const bool mixed = prec == AMG_F64X;
-    const int pin = mixed ? 1 : prec, pout = mixed ? 0 : prec;
+    const bool mixed = prec == AMG_F64X, dd = prec == AMG_F64D;
+    const int pin = mixed ? 1 : dd ? 0 : prec, pout = mixed || dd ? 0 : prec;
     CK(d->in.ensure(fine_spinor_bytes(pin, g.V) * nrhs));
     CK(d->out.ensure(fine_spinor_bytes(pout, g.V) * nrhs));
     CK(launch_pack_spinor(pin, g, in, d->in.p, nrhs, st));
+    if (dd) CK(d->split.ensure(2 * fine_spinor_bytes(1, g.V) * nrhs));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -2511,6 +2542,9 @@ amg_status amg_dirac_time(amg_dirac* d, const void* in, int nrhs, amg_prec prec,
     cudaError_t err = cudaEventRecord(e0, st);
     for (int i = 0; err == cudaSuccess && i < reps; ++i)
         err = mixed ? launch_dirac_mixed(g, d->gauge->U[3].p, d->C[3].p, d->in.p, d->out.p, d->kappa, nrhs, st)
+              : dd  ? launch_dirac_dd(g, d->gauge->U[3].p, d->C[3].p, d->gauge->U[1].p, d->C[1].p, d->in.p, d->out.p,
+                                      nullptr, d->kappa, nrhs, d->split.p,
+                                      (char*)d->split.p + fine_spinor_bytes(1, g.V) * nrhs, st)
                     : launch_dirac(prec, g, nullptr, d->gauge->U[prec].p, d->C[prec].p, d->in.p, d->out.p, nullptr,
                                    d->kappa, nrhs, st);
     if (err == cudaSuccess) err = cudaEventRecord(e1, st);
@@ -2763,14 +2797,14 @@ amg_status amg_apply_coarse(amg_hierarchy* h, int level, const void* in, void* o
         CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), in, out, nullptr, nrhs, st));
         return AMG_OK;
     }
+    // vectors in another precision than the level's: converted through scratch that the
+    // hierarchy keeps (grown when needed; stream-ordered, no synchronisation)
     size_t n = coarse_n(L) * nrhs;
-    DevBuf a, b;
-    CK(a.ensure(n * coarse_elem_bytes(L.prec)));
-    CK(b.ensure(n * coarse_elem_bytes(L.prec)));
-    CK(launch_convert_flat(vprec, L.prec, in, a.p, n, st));
-    CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), a.p, b.p, nullptr, nrhs, st));
-    CK(launch_convert_flat(L.prec, vprec, b.p, out, n, st));
-    CK(cudaStreamSynchronize(st));
+    CK(h->ac_in.ensure(n * coarse_elem_bytes(L.prec)));
+    CK(h->ac_out.ensure(n * coarse_elem_bytes(L.prec)));
+    CK(launch_convert_flat(vprec, L.prec, in, h->ac_in.p, n, st));
+    CK(launch_coarse_apply(L.kprec(), L.g, L.nc, nullptr, L.op(), h->ac_in.p, h->ac_out.p, nullptr, nrhs, st));
+    CK(launch_convert_flat(L.prec, vprec, h->ac_out.p, out, n, st));
     return AMG_OK;
 }
 

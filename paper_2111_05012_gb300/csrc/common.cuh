@@ -569,6 +569,7 @@ struct RaggedDev {
     const void* vecs;  // test vectors (storage of the batch's vector precision)
     const void* v;     // V_j, FP64 internal
     void* f32;         // V_j in FP32
+    void* f32b;        // FP32 scratch (the low part of x in the true residual)
     void* bc;          // coarse right-hand side, FP32 [Vc][2 nvec]
     void* xc;          // coarse solution
     void* z;           // Z_j = M V_j, FP32 internal

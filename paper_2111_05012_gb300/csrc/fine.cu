@@ -367,15 +367,6 @@ __global__ void __launch_bounds__(kThreads, P::id == 0 ? 2 : 3) dirac_kernel(Geo
 }
 
 // ragged batch, restart phases (site loops over each problem's lattice)
-__global__ void __launch_bounds__(kThreads, 2)
-    resid_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
-    int p, bx, gx;
-    ragged_locate(off, np, p, bx, gx);
-    const RaggedDev& q = d[p];
-    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x)
-        dirac_site<P64, false, true>(q.g, q.bk, q.U64, q.C64, (const char*)q.x64, (char*)q.r64, (const char*)q.b64,
-                                     q.kappa, s);
-}
 __global__ void pack_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
     int p, bx, gx;
     ragged_locate(off, np, p, bx, gx);
@@ -486,14 +477,42 @@ DEV void cfa_edag(int mu, cfa v0, cfa v1, cfa& y0, cfa& y1) {
 // sum of two exact-float complex values as an exact pair per component
 DEV cfa cfa_sum(cfa a, cfa b) { return {fa_two_sum(a.re.hi, b.re.hi), fa_two_sum(a.im.hi, b.im.hi)}; }
 
-// out(s) = (D in)(s) for one site s
+// MODE 0: out(s) = (D in)(s) for one site s.
+// MODE 1: out(s) = b(s) - (D (in + lo))(s) for an FP64 vector split into float parts in + lo
+// (split_kernel): D in in the pair arithmetic, D lo in plain FP32 with the FP32 links and
+// clover U32 / C32 (lo is 2^-24 of in or less, so FP32 rounding of that part stays below
+// 2^-47 relative), its result the starting value of the pair accumulators.
+// MODE 2: out(s) = (D (in + lo))(s), the same without b.
+template <int MODE = 0>
 DEV void dirac_mixed_site(const Geom& g, const void* __restrict__ U, const void* __restrict__ C, const char* src,
-                          char* dst, dfloat kappa, int s) {
+                          char* dst, dfloat kappa, int s, const void* __restrict__ U32 = nullptr,
+                          const void* __restrict__ C32 = nullptr, const char* srclo = nullptr,
+                          const char* bsrc = nullptr, float kappa32 = 0.f) {
     {
         int c[4];
         site_coords(g, s, c);
         cx<float> pf[12];
         cfa acc[12];
+        if constexpr (MODE >= 1) {
+            cx<float> lo[12];
+            SpinorIO<P32>::load(srclo, g.V, s, pf);
+            clover_apply<P32>(C32, g.V, s, pf, lo);
+#pragma unroll 1
+            for (int mu = 0; mu < 4; ++mu) {
+                float ph;
+                cx<float> u[3][3];
+                int n = neighbour(g, s, c, mu, +1, ph);
+                SpinorIO<P32>::load(srclo, g.V, n, pf);
+                GaugeIO<P32>::load(U32, g.V, mu, s, u);
+                hop_accum<float>(lo, pf, u, mu, +1, -kappa32 * ph);
+                n = neighbour(g, s, c, mu, -1, ph);
+                SpinorIO<P32>::load(srclo, g.V, n, pf);
+                GaugeIO<P32>::load(U32, g.V, mu, n, u);
+                hop_accum<float>(lo, pf, u, mu, -1, -kappa32 * ph);
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = cfa_exact(lo[k]);
+        }
         SpinorIO<P32>::load(src, g.V, s, pf);
         // clover: two packed Hermitian 6x6 blocks
 #pragma unroll
@@ -503,7 +522,11 @@ DEV void dirac_mixed_site(const Geom& g, const void* __restrict__ U, const void*
             cfa* o = acc + 6 * b;
             const cx<float>* z = pf + 6 * b;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) o[i] = {fa_mul(pr[i], fa{z[i].re, 0.f}), fa_mul(pr[i], fa{z[i].im, 0.f})};
+            for (int i = 0; i < 6; ++i) {
+                const cfa d = {fa_mul(pr[i], fa{z[i].re, 0.f}), fa_mul(pr[i], fa{z[i].im, 0.f})};
+                if constexpr (MODE >= 1) cfa_add(o[i], d);
+                else o[i] = d;
+            }
 #pragma unroll
             for (int i = 1; i < 6; ++i)
 #pragma unroll
@@ -575,6 +598,12 @@ DEV void dirac_mixed_site(const Geom& g, const void* __restrict__ U, const void*
 #pragma unroll
         for (int k = 0; k < 12; ++k)
             o[k] = {(double)acc[k].re.hi + (double)acc[k].re.lo, (double)acc[k].im.hi + (double)acc[k].im.lo};
+        if constexpr (MODE == 1) {
+            cx<double> bv[12];
+            SpinorIO<P64>::load(bsrc, g.V, s, bv);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) o[k] = bv[k] - o[k];
+        }
         SpinorIO<P64>::store(dst, g.V, s, o);
     }
 }
@@ -613,6 +642,97 @@ __global__ void convert_ragged_kernel(const RaggedDev* __restrict__ d, const int
         for (int k = 0; k < 12; ++k) w[k] = ccast<float>(v[k]);
         SpinorIO<P32>::store(q.f32, q.g.V, s, w);
     }
+}
+
+// ------------------------------------------------------------ FP64 vectors in the pair arithmetic
+// D x (or b - D x) for FP64 x: x is first split into float parts hi + lo
+// (split_kernel), then dirac_mixed_site<1> takes D hi in the pair arithmetic
+// and D lo in plain FP32 (~46 significant bits; the outer solver's true
+// residual on the FP32 pipe, FP64 arithmetic running at a small fraction of
+// the FP32 rate here).
+// The split takes integer and FP32 instructions only (double-precision conversions and
+// subtractions would run on the scarce FP64 pipe): hi = the leading 24 significant bits of
+// x (truncated, exact), lo = the next 23 bits, |x - (hi + lo)| < 2^-46 |x|.  Values below
+// 2^-126 in magnitude are dropped, lo below 2^-81 |x| scale likewise (absolute errors under
+// 1e-31 against vectors of order one); infinities and NaNs stay infinite or NaN in hi.
+DEV fa split_double_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hw = (unsigned)(b >> 32), sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7FF);   // biased exponent
+    if (e < 1023 - 126) return {0.f, 0.f};
+    if (e >= 1023 + 128) return {__uint_as_float(sign | 0x7F800000u | ((e == 2047 && (b << 12)) ? 0x400000u : 0u)), 0.f};
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+    float lo = 0.f;
+    const int le = e - 1075 + 6 + 127;   // float exponent of 2^(e - 1075 + 6)
+    if (le > 0) {
+        // the 23 bits below hi as an exact float in [0, 2^23), scaled into place
+        const float m = __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)((b & 0x1FFFFFFFull) >> 6)), 8388608.f);
+        lo = __fmul_rn(m, __uint_as_float((unsigned)le << 23));
+        if (sign) lo = -lo;
+    }
+    return {hi, lo};
+}
+__global__ void split_kernel(Geom g, const void* __restrict__ in, void* hi, void* lo) {
+    const int r = blockIdx.y;
+    const char* src = (const char*)in + r * spinor_bytes<P64>(g.V);
+    char* dh = (char*)hi + r * spinor_bytes<P32>(g.V);
+    char* dl = (char*)lo + r * spinor_bytes<P32>(g.V);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        cx<double> v[12];
+        cx<float> h[12], l[12];
+        SpinorIO<P64>::load(src, g.V, s, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const fa re = split_double_bits(v[k].re), im = split_double_bits(v[k].im);
+            h[k] = {re.hi, im.hi};
+            l[k] = {re.lo, im.lo};
+        }
+        SpinorIO<P32>::store(dh, g.V, s, h);
+        SpinorIO<P32>::store(dl, g.V, s, l);
+    }
+}
+template <bool RESID>
+__global__ void __launch_bounds__(kThreads, 2)
+    dirac_hilo_kernel(Geom g, const void* __restrict__ Udd, const void* __restrict__ Cdd,
+                      const void* __restrict__ U32, const void* __restrict__ C32, const void* hi, const void* lo,
+                      void* out, const void* b, dfloat kappa, float kappa32) {
+    const int r = blockIdx.y;
+    const char* sh = (const char*)hi + r * spinor_bytes<P32>(g.V);
+    const char* sl = (const char*)lo + r * spinor_bytes<P32>(g.V);
+    char* dst = (char*)out + r * spinor_bytes<P64>(g.V);
+    const char* bs = RESID ? (const char*)b + r * spinor_bytes<P64>(g.V) : nullptr;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x)
+        dirac_mixed_site<RESID ? 1 : 2>(g, Udd, Cdd, sh, dst, kappa, s, U32, C32, sl, bs, kappa32);
+}
+
+// ragged batch, true residual r = b - D x: x split into f32 (hi) and f32b (lo), then the pair stencil
+__global__ void split_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x) {
+        cx<double> v[12];
+        cx<float> h[12], l[12];
+        SpinorIO<P64>::load(q.x64, q.g.V, s, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const fa re = split_double_bits(v[k].re), im = split_double_bits(v[k].im);
+            h[k] = {re.hi, im.hi};
+            l[k] = {re.lo, im.lo};
+        }
+        SpinorIO<P32>::store(q.f32, q.g.V, s, h);
+        SpinorIO<P32>::store(q.f32b, q.g.V, s, l);
+    }
+}
+__global__ void __launch_bounds__(kThreads, 2)
+    resid_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    const dfloat kappa = split_double(q.kappa);
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x)
+        dirac_mixed_site<1>(q.g, q.Udd, q.Cdd, (const char*)q.f32, (char*)q.r64, kappa, s, q.U32, q.C32,
+                            (const char*)q.f32b, (const char*)q.b64, q.kappa32);
 }
 
 // x (FP64 internal) += sum_j c_j z_j for FP32 internal z_j: site by site,
@@ -1700,6 +1820,7 @@ int ragged_dev_fill(void* dst, const RaggedProbH& h) {
     q.vecs = h.vecs;
     q.v = h.v;
     q.f32 = h.f32;
+    q.f32b = h.f32b;
     q.bc = h.bc;
     q.xc = h.xc;
     q.z = h.z;
@@ -1770,10 +1891,26 @@ cudaError_t launch_unpack_ragged(const void* d, const int* off, int np, int ctas
     return cudaGetLastError();
 }
 cudaError_t launch_resid_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+    (note_launch(), split_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
     (note_launch(), resid_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
     return cudaGetLastError();
 }
 cudaError_t launch_xupdate_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
     (note_launch(), xupdate_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+    return cudaGetLastError();
+}
+cudaError_t launch_dirac_dd(const GeomH& gh, const void* Udd, const void* Cdd, const void* U32, const void* C32,
+                            const void* in64, void* out64, const void* b64, double kappa, int nrhs, void* hi,
+                            void* lo, cudaStream_t st) {
+    Geom g = make_geom(gh);
+    dim3 grid(grid_for(g.V, kThreads), nrhs);
+    (note_launch(), split_kernel<<<grid, kThreads, 0, st>>>(g, in64, hi, lo));
+    if (b64)
+        (note_launch(), dirac_hilo_kernel<true><<<grid, kThreads, 0, st>>>(g, Udd, Cdd, U32, C32, hi, lo, out64, b64,
+                                                                            split_double(kappa), (float)kappa));
+    else
+        (note_launch(), dirac_hilo_kernel<false><<<grid, kThreads, 0, st>>>(g, Udd, Cdd, U32, C32, hi, lo, out64,
+                                                                             nullptr, split_double(kappa),
+                                                                             (float)kappa));
     return cudaGetLastError();
 }

@@ -58,6 +58,13 @@ cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sap_block, cons
 // Udd / Cdd are the prec-3 (float hi/lo pair) link and clover fields
 cudaError_t launch_dirac_mixed(const GeomH& g, const void* Udd, const void* Cdd, const void* in32, void* out64,
                                double kappa, int nrhs, cudaStream_t s);
+// out (FP64 internal) = D in, or b - D in when b != NULL, for FP64 internal in: in split into
+// float parts hi + lo (FP32 internal scratch fields, nrhs each), D hi in double-float arithmetic
+// with the prec-3 link and clover fields, D lo in FP32 with the FP32 fields (about 46
+// significant bits; the outer solver's true residual)
+cudaError_t launch_dirac_dd(const GeomH& g, const void* Udd, const void* Cdd, const void* U32, const void* C32,
+                            const void* in64, void* out64, const void* b64, double kappa, int nrhs, void* hi,
+                            void* lo, cudaStream_t s);
 // x (FP64 internal) += sum_j c[j] z[j] for k <= 20 FP32 internal fields z[j] (site-wise)
 cudaError_t launch_spinor_axpy_mixed(const GeomH& g, int k, const double2* c, const void* const* z, void* x,
                                      cudaStream_t s);
@@ -231,6 +238,7 @@ struct RaggedProbH {
     const void* vecs;           // test vectors
     const void* v;              // V_j (FP64 internal)
     void* f32;                  // V_j in FP32
+    void* f32b;                 // FP32 scratch field
     void* bc;                   // coarse right-hand side / solution, FP32 [Vc][2 nvec]
     void* xc;
     void* z;                    // Z_j = M V_j (FP32 internal)
@@ -281,7 +289,8 @@ cudaError_t launch_dirac_mixed_ragged(const void* d, const int* off, int np, int
 // one classical Gram-Schmidt pass against k = j + 1 basis vectors, then V_{j+1} = w' / |w'|
 cudaError_t launch_gs_ragged(int k, const void* d, const int* off, int np, int ctas, int pass, cudaStream_t s);
 // restart phases of a fused ragged batch (tables of the problems concerned):
-// b64 = canon_in and x64 = 0; canon_out = x64; r64 = b64 - D x64 (FP64); the norm of rsrc into
+// b64 = canon_in and x64 = 0; canon_out = x64; r64 = b64 - D x64 (two launches: x64 split into
+// f32 + f32b, then the pair stencil, as launch_dirac_dd); the norm of rsrc into
 // nval and basis[0] = rsrc / |rsrc| (two launches); x64 += sum_i yc[i] zb[i]
 cudaError_t launch_pack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
 cudaError_t launch_unpack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);

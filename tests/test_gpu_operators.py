@@ -57,6 +57,28 @@ def test_apply_D_mixed_fp64_accurate(field):
     assert rel(from_dev(y, (2,) + field.shape4 + (12,)), ref) < 1e-13
 
 
+def test_apply_D_double_float_on_fp64_vectors(field):
+    # FP64 input, every value split into a float pair, double-float stencil (the outer
+    # solver's true residual): within 1e-13 of the oracle's D on the same input
+    c = field.c
+    psi = np.stack([li.rhs(field.dims, 6, i) for i in range(2)])
+    x = to_dev(psi)
+    ref = np.stack([field.op.apply(p.reshape(field.shape4 + (12,))) for p in psi])
+    import torch
+    y = torch.zeros_like(x)
+    c.amg_apply_D(field.d, x, y, 2, c.AMG_F64D)
+    assert rel(from_dev(y, (2,) + field.shape4 + (12,)), ref) < 1e-13
+    # values spread over 30 decades (a propagator decays away from its source): the split
+    # keeps every value to 2^-46 relative down to 2^-81, so the result stays within 1e-13
+    rng = np.random.default_rng(3)
+    wide = psi[0] * 10.0 ** -rng.integers(0, 30, size=psi[0].shape)
+    x = to_dev(wide[None])
+    y = torch.zeros_like(x)
+    c.amg_apply_D(field.d, x, y, 1, c.AMG_F64D)
+    ref = field.op.apply(wide.reshape(field.shape4 + (12,)))
+    assert rel(from_dev(y, field.shape4 + (12,)), ref) < 1e-13
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_apply_Dsap(field, prec):
     c = field.c
