@@ -153,6 +153,12 @@ def dist_info():
     return rank, world, local
 
 
+SAP_KERNEL_NAMES = {0: "sap_half_kernel<P32,256> (fused SAP half sweep)",
+                    1: "sap_half_staged_kernel<P32> (fused SAP half sweep, operator staged in shared memory)",
+                    2: "sap_half_kernel<P32,256,2> (fused SAP half sweep, two right-hand sides per CTA)",
+                    3: "sap_half_staged_kernel<P32,P16> (fused SAP half sweep, FP16 operator staged in shared memory)"}
+
+
 def make_params(capi, prec_smoother, coarse="f32", outer="fgmres", sap_variant=-1, setup=None, vec="f32", w=None):
     p = capi.amg_params_default()
     if vec == "f16":
@@ -448,7 +454,8 @@ def run_headline(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f16+f64", "data": "synthetic", "config": config,
         "roofline": {"kernel": ("sap_half_eo_kernel<P32> (fused SAP half sweep, even-odd domain solves)"
-                               if p.sap_eo else "sap_half_kernel<P32,256> (fused SAP half sweep)"), "bound": "alu",
+                               if p.sap_eo else SAP_KERNEL_NAMES.get(args.sap_variant, "sap_half (autotuned)")),
+                     "bound": "alu",
                      "achieved": sap_tflops, "peak": peak, "unit": "TFLOP/s", "frac": sap_tflops / peak,
                      "traffic": None,
                      "peak_kind": f"FP32 FMA from unit counts: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
@@ -1046,8 +1053,7 @@ def run_solve16(args):
                    "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
         # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one sap_half_kernel<P32,256> launch on this
         # workload, from an ncu --set full capture of this kernel (91.18 + 2.66 MB); only for variant 0
-        "roofline": {"kernel": {0: "sap_half_kernel<P32,256>",
-                                1: "sap_half_staged_kernel<P32>"}.get(args.sap_variant, "sap_half (autotuned)"),
+        "roofline": {"kernel": SAP_KERNEL_NAMES.get(args.sap_variant, "sap_half (autotuned)"),
                      "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": 93.8e6 if (args.sap_variant == 0 and args.prec == "f32") else None,
@@ -1100,7 +1106,7 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--fused-only", action="store_true",
                     help="ragged workload: time the fused batch only (no stream-pool or one-by-one comparison)")
-    ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1, 2],
+    ap.add_argument("--sap-variant", type=int, default=0, choices=[-1, 0, 1, 2, 3],
                     help="SAP kernel: 0 operator through L1/L2 (default), 1 staged in shared memory, "
                          "2 two right-hand sides of a batch per CTA, -1 autotune")
     ap.add_argument("--n-init", type=int, default=None, help="setup (0-a) SAP applications (default: library's)")

@@ -102,7 +102,9 @@ typedef struct {
                                            0 operator read from global memory, 1 operator staged in shared
                                            memory (FP32/FP16, blocks <= 256 sites; two right-hand sides
                                            per CTA in a batch), 2 as 0 but two right-hand sides of a batch
-                                           per CTA sharing the operator in L1 (FP32/FP16, <= 256 sites)
+                                           per CTA sharing the operator in L1 (FP32/FP16, <= 256 sites),
+                                           3 FP32 smoother with the operator staged in shared memory from
+                                           its FP16 copy (<= 256 sites; residual with the FP32 operator)
                                            [-1] */
     int outer_solver;                   /* 0: flexible GMRES(outer_m) [0]; 1: the paper's BiCGStab with
                                            flexible preconditioning (Sec. 3), one right-hand side at a

@@ -325,7 +325,7 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
     if (p->coarse_ell < 1 || p->coarse_ell > 4) return fail(AMG_EINVAL, "coarse_ell must be 1..4");
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
     if (p->outer_solver < 0 || p->outer_solver > 2) return fail(AMG_EINVAL, "outer_solver must be 0, 1 or 2");
-    if (p->sap_variant < -1 || p->sap_variant > 2) return fail(AMG_EINVAL, "sap_variant must be -1, 0, 1 or 2");
+    if (p->sap_variant < -1 || p->sap_variant > 3) return fail(AMG_EINVAL, "sap_variant must be -1, 0, 1, 2 or 3");
     if (p->sap_eo != 0 && p->sap_eo != 1) return fail(AMG_EINVAL, "sap_eo must be 0 or 1");
     if (p->sap_eo) {
         BlockH b0;
@@ -369,6 +369,17 @@ amg_status true_residual(amg_hierarchy* h, const void* x, void* r, const void* b
     return fine_D(h, 0, x, r, b, nb, s);
 }
 
+// one SAP half sweep with kernel variant var (0-2: launch_sap_half_variant; 3: FP32 vectors
+// with the domain operator staged from its FP16 copy)
+cudaError_t sap_half_launch(amg_dirac* d, int var, int prec, const GeomH& g, const BlockH& bk, int colour, int nmr,
+                            int x_mode, const void* b, void* x, int nb, cudaStream_t s) {
+    if (var == 3 && prec == 1)
+        return launch_sap_half_staged16(g, bk, colour, nmr, x_mode, d->gauge->U[1].p, d->C[1].p, d->gauge->U[2].p,
+                                        d->C[2].p, b, x, d->kappa, nb, s);
+    return launch_sap_half_variant(var == 3 ? 1 : var, prec, g, bk, colour, nmr, x_mode, d->gauge->U[prec].p,
+                                   d->C[prec].p, b, x, d->kappa, nb, s);
+}
+
 amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_zero, int nb, cudaStream_t s) {
     amg_dirac* d = h->d;
     h->timer.start(PH_SMOOTH, s);
@@ -381,8 +392,8 @@ amg_status fine_sap(amg_hierarchy* h, int prec, const void* b, void* x, bool x_z
                 CK(launch_sap_half_eo(prec, fine_geom(h), h->blk[0], colour, h->p.mr_iters, x_mode,
                                       d->gauge->U[prec].p, d->C[prec].p, d->Ci[prec].p, b, x, d->kappa, nb, s));
             else
-                CK(launch_sap_half_variant(var, prec, fine_geom(h), h->blk[0], colour, h->p.mr_iters, x_mode,
-                                           d->gauge->U[prec].p, d->C[prec].p, b, x, d->kappa, nb, s));
+                CK(sap_half_launch(d, var, prec, fine_geom(h), h->blk[0], colour, h->p.mr_iters, x_mode, b, x, nb,
+                                   s));
         }
     }
     if (h->p.sap_iters == 0 && x_zero) CK(cudaMemsetAsync(x, 0, fsz(h, prec) * nb, s));
@@ -1156,7 +1167,7 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
                 zl[i] = (const char*)h->oZ[i]->p + q * fsz(h, zprec_of(h));
             }
             if (zprec_of(h) == 0) CK(launch_multi_axpy(0, k, yc.data(), zl.data(), F(x, q), n, s));
-            else CK(launch_spinor_axpy_mixed(fine_geom(h), k, yc.data(), zl.data(), F(x, q), s));
+            else CK(launch_spinor_axpy_mixed(fine_geom(h), k, yc.data(), zl.data(), F(x, q), s, true));
         }
     }
     infos.assign(nb, amg_solve_info());
@@ -1443,13 +1454,12 @@ amg_status tune_kernels(amg_hierarchy* h) {
     for (int pr : precs) {
         const bool staged = sap_staged_supported(pr, h->blk[0]);
         if (h->p.sap_variant >= 0) {
-            // variant 2 (two right-hand sides per CTA) only differs from 0 for batches
+            // variant 2 (two right-hand sides per CTA) only differs from 0 for batches; the
+            // staged variants need a blocking that fits, 3 an FP32 smoother
             h->sap_variant[pr] = h->p.sap_variant == 2 ? 0 : h->p.sap_variant;
             h->sap_variant_nb[pr] = h->p.sap_variant;
-            if (!staged) {
-                if (h->sap_variant[pr] == 1) h->sap_variant[pr] = 0;
-                if (h->sap_variant_nb[pr] == 1) h->sap_variant_nb[pr] = 0;
-            }
+            for (int* v : {&h->sap_variant[pr], &h->sap_variant_nb[pr]})
+                if ((!staged && (*v == 1 || *v == 3)) || (*v == 3 && pr != 1)) *v = 0;
             continue;
         }
         const size_t fb = fine_spinor_bytes(pr, g.V);
@@ -1467,13 +1477,13 @@ amg_status tune_kernels(amg_hierarchy* h) {
             std::vector<int> vs = {0};
             if (staged) vs.push_back(1);
             if (nrhs > 1) vs.push_back(2);
-            std::vector<float> t[3];
+            if (staged && pr == 1) vs.push_back(3);
+            std::vector<float> t[4];
             for (int rep = 0; rep < 10; ++rep) {
                 for (int v : vs) {
                     CK(cudaEventRecord(e0, 0));
                     for (int colour = 0; colour < 2; ++colour)
-                        CK(launch_sap_half_variant(v, pr, g, h->blk[0], colour, h->p.mr_iters, 0, d->gauge->U[pr].p,
-                                                   d->C[pr].p, tb.p, tx.p, d->kappa, nrhs, 0));
+                        CK(sap_half_launch(d, v, pr, g, h->blk[0], colour, h->p.mr_iters, 0, tb.p, tx.p, nrhs, 0));
                     CK(cudaEventRecord(e1, 0));
                     CK(cudaEventSynchronize(e1));
                     float ms = 0;

@@ -94,6 +94,41 @@ HD dfloat split_double(double v) {
     float h = (float)v;
     return {h, (float)(v - (double)h)};
 }
+// FP64 <-> float pairs without FP64 instructions (double-precision conversions and
+// subtractions run on the scarce FP64 pipe here).  split_double_bits: hi = the leading 24
+// significant bits of v (truncated, exact), lo = the next 23 bits, |v - (hi + lo)| <
+// 2^-46 |v|.  Values below 2^-126 in magnitude are dropped, lo below 2^-81 |v| scale likewise
+// (absolute errors under 1e-31 against vectors of order one); infinities and NaNs stay
+// infinite or NaN in hi.
+DEV dfloat split_double_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hw = (unsigned)(b >> 32), sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7FF);   // biased exponent
+    if (e < 1023 - 126) return dfloat(0.f, 0.f);
+    if (e >= 1023 + 128) return dfloat(__uint_as_float(sign | 0x7F800000u | ((e == 2047 && (b << 12)) ? 0x400000u : 0u)), 0.f);
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+    float lo = 0.f;
+    const int le = e - 1075 + 6 + 127;   // float exponent of 2^(e - 1075 + 6)
+    if (le > 0) {
+        // the 23 bits below hi as an exact float in [0, 2^23), scaled into place
+        const float m = __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)((b & 0x1FFFFFFFull) >> 6)), 8388608.f);
+        lo = __fmul_rn(m, __uint_as_float((unsigned)le << 23));
+        if (sign) lo = -lo;
+    }
+    return dfloat(hi, lo);
+}
+// the double of a float (exact; zero and subnormal floats give zero), integer instructions only
+DEV double float_to_double_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    const unsigned long long ed = e == 255 ? 2047ull : (unsigned long long)(e + 896);
+    return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+// hi + lo rounded to a double: one FP64 addition
+DEV double pair_to_double(float hi, float lo) { return float_to_double_bits(hi) + float_to_double_bits(lo); }
+
 
 // ---------------------------------------------------------------- precision tags
 // A tag fixes the storage of fine fields (spinor, links, clover) and the

@@ -649,29 +649,8 @@ __global__ void convert_ragged_kernel(const RaggedDev* __restrict__ d, const int
 // (split_kernel), then dirac_mixed_site<1> takes D hi in the pair arithmetic
 // and D lo in plain FP32 (~46 significant bits; the outer solver's true
 // residual on the FP32 pipe, FP64 arithmetic running at a small fraction of
-// the FP32 rate here).
-// The split takes integer and FP32 instructions only (double-precision conversions and
-// subtractions would run on the scarce FP64 pipe): hi = the leading 24 significant bits of
-// x (truncated, exact), lo = the next 23 bits, |x - (hi + lo)| < 2^-46 |x|.  Values below
-// 2^-126 in magnitude are dropped, lo below 2^-81 |x| scale likewise (absolute errors under
-// 1e-31 against vectors of order one); infinities and NaNs stay infinite or NaN in hi.
-DEV fa split_double_bits(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned hw = (unsigned)(b >> 32), sign = hw & 0x80000000u;
-    const int e = (int)((hw >> 20) & 0x7FF);   // biased exponent
-    if (e < 1023 - 126) return {0.f, 0.f};
-    if (e >= 1023 + 128) return {__uint_as_float(sign | 0x7F800000u | ((e == 2047 && (b << 12)) ? 0x400000u : 0u)), 0.f};
-    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
-    float lo = 0.f;
-    const int le = e - 1075 + 6 + 127;   // float exponent of 2^(e - 1075 + 6)
-    if (le > 0) {
-        // the 23 bits below hi as an exact float in [0, 2^23), scaled into place
-        const float m = __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)((b & 0x1FFFFFFFull) >> 6)), 8388608.f);
-        lo = __fmul_rn(m, __uint_as_float((unsigned)le << 23));
-        if (sign) lo = -lo;
-    }
-    return {hi, lo};
-}
+// the FP32 rate here); the split is split_double_bits (integer and FP32
+// instructions only).
 __global__ void split_kernel(Geom g, const void* __restrict__ in, void* hi, void* lo) {
     const int r = blockIdx.y;
     const char* src = (const char*)in + r * spinor_bytes<P64>(g.V);
@@ -683,7 +662,7 @@ __global__ void split_kernel(Geom g, const void* __restrict__ in, void* hi, void
         SpinorIO<P64>::load(src, g.V, s, v);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            const fa re = split_double_bits(v[k].re), im = split_double_bits(v[k].im);
+            const dfloat re = split_double_bits(v[k].re), im = split_double_bits(v[k].im);
             h[k] = {re.hi, im.hi};
             l[k] = {re.lo, im.lo};
         }
@@ -716,7 +695,7 @@ __global__ void split_ragged_kernel(const RaggedDev* __restrict__ d, const int* 
         SpinorIO<P64>::load(q.x64, q.g.V, s, v);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            const fa re = split_double_bits(v[k].re), im = split_double_bits(v[k].im);
+            const dfloat re = split_double_bits(v[k].re), im = split_double_bits(v[k].im);
             h[k] = {re.hi, im.hi};
             l[k] = {re.lo, im.lo};
         }
@@ -752,6 +731,46 @@ __global__ void spinor_axpy_mixed_kernel(Geom g, int k, ZList z, void* x) {
 #pragma unroll
             for (int q = 0; q < 12; ++q) cfma(acc[q], cj, ccast<double>(v[q]));
         }
+        SpinorIO<P64>::store(x, g.V, s, acc);
+    }
+}
+
+// the same in pair arithmetic on the FP32 pipe: x split into float pairs (split_double_bits),
+// c_j split likewise, the products with the exact floats of z_j and the sums kept as pairs,
+// one FP64 addition per stored value
+DEV void pmac_exact(dfloat& a, dfloat c, float z) {
+    const float p = __fmul_rn(c.hi, z);
+    float e = fmaf(c.hi, z, -p);
+    e = fmaf(c.lo, z, e);
+    const dfloat t = two_sum(a.hi, p);
+    a.hi = t.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(t.lo, e));
+}
+__global__ void spinor_axpy_mixed_df_kernel(Geom g, int k, ZList z, void* x) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        cx<double> acc[12];
+        SpinorIO<P64>::load_rw(x, g.V, s, acc);
+        dfloat ar[12], ai[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            ar[q] = split_double_bits(acc[q].re);
+            ai[q] = split_double_bits(acc[q].im);
+        }
+        for (int j = 0; j < k; ++j) {
+            cx<float> v[12];
+            SpinorIO<P32>::load(z.p[j], g.V, s, v);
+            const dfloat cr = split_double_bits(z.c[j].x), ci = split_double_bits(z.c[j].y);
+            const dfloat nci(-ci.hi, -ci.lo);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                pmac_exact(ar[q], cr, v[q].re);
+                pmac_exact(ar[q], nci, v[q].im);
+                pmac_exact(ai[q], cr, v[q].im);
+                pmac_exact(ai[q], ci, v[q].re);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = {pair_to_double(ar[q].hi, ar[q].lo), pair_to_double(ai[q].hi, ai[q].lo)};
         SpinorIO<P64>::store(x, g.V, s, acc);
     }
 }
@@ -1310,12 +1329,15 @@ template <> struct Staged<P16> {
 // NR right-hand sides per CTA (NR = 2 for batches): thread (slot, l) works on site l of the
 // domain for right-hand side NR * (pair index) + slot; the domain's operator is staged once
 // and shared by the slots, each slot has its own residual tile and block reduction.
-template <class P, int NR>
-__global__ void __launch_bounds__(256 * NR, (P::id == 2 && NR == 1) ? 2 : 1)
+// PS: the storage the operator is staged from (US, UC: its link and clover fields); P32 vectors
+// with PS = P16 stage the FP16 copy of the operator (half the shared memory: two CTAs per SM)
+// while the residual b - D x still uses the FP32 operator U, C.
+template <class P, int NR, class PS = P>
+__global__ void __launch_bounds__(256 * NR, (PS::id == 2 && NR == 1) ? 2 : 1)
     sap_half_staged_kernel(Geom g, Blocking bk, int colour, int nmr, int x_mode, const void* __restrict__ U,
                            const void* __restrict__ C, const void* __restrict__ b, void* x, float kappa,
-                           int rhs_fast, int nrhs) {
-    using S = Staged<P>;
+                           int rhs_fast, int nrhs, const void* __restrict__ US, const void* __restrict__ CS) {
+    using S = Staged<PS>;
     using LC = typename S::LC;
     using CC = typename S::CC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1352,7 +1374,7 @@ __global__ void __launch_bounds__(256 * NR, (P::id == 2 && NR == 1) ? 2 : 1)
         for (int mu = 0; mu < 4; ++mu) lc[mu] = c[mu] % bk.b[mu];
         // stage this site's forward links (slot 0) and clover (the last slot)
         if (slot == 0) {
-            const LC* gl = (const LC*)U;
+            const LC* gl = (const LC*)US;
 #pragma unroll
             for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
@@ -1361,7 +1383,7 @@ __global__ void __launch_bounds__(256 * NR, (P::id == 2 && NR == 1) ? 2 : 1)
                         __ldg(gl + ((size_t)mu * S::kLinkChunks + q) * g.V + s);
         }
         if (slot == NR - 1) {
-            const CC* gc = (const CC*)C;
+            const CC* gc = (const CC*)CS;
 #pragma unroll
             for (int q = 0; q < S::kCloverChunks; ++q) sc[q * vbp + l] = __ldg(gc + (size_t)q * g.V + s);
         }
@@ -1479,9 +1501,12 @@ size_t sap_staged_smem(int vbp, int nr = 1) {
            nr * 2 * 96 * sizeof(float);
 }
 
-template <class P>
+template <class P, class PS = P>
 cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr, int x_mode, const void* U,
-                                 const void* C, const void* b, void* x, double kappa, int nrhs, cudaStream_t st) {
+                                 const void* C, const void* b, void* x, double kappa, int nrhs, cudaStream_t st,
+                                 const void* US = nullptr, const void* CS = nullptr) {
+    if (!US) US = U;
+    if (!CS) CS = C;
     Geom g = make_geom(gh);
     Blocking bk = make_blocking(gh, bh);
     int threads = (bk.Vb + 31) / 32 * 32;
@@ -1492,12 +1517,12 @@ cudaError_t sap_half_staged_impl(const GeomH& gh, const BlockH& bh, int colour, 
     const int npair = (nrhs + nr - 1) / nr;
     const int fast = npair > 1 && ndom <= 65535;
     const dim3 grid = fast ? dim3(npair, ndom) : dim3(ndom, npair);
-    size_t smem = sap_staged_smem<P>(threads, nr);
-    auto fn = nr == 2 ? sap_half_staged_kernel<P, 2> : sap_half_staged_kernel<P, 1>;
+    size_t smem = sap_staged_smem<PS>(threads, nr);
+    auto fn = nr == 2 ? sap_half_staged_kernel<P, 2, PS> : sap_half_staged_kernel<P, 1, PS>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     (note_launch(), fn<<<grid, threads * nr, smem, st>>>(g, bk, colour, nmr, x_mode, U, C, b, x, (float)kappa, fast,
-                                                          nrhs));
+                                                          nrhs, US, CS));
     return cudaGetLastError();
 }
 
@@ -1726,7 +1751,7 @@ cudaError_t launch_dirac_mixed(const GeomH& gh, const void* Udd, const void* Cdd
     return cudaGetLastError();
 }
 cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, const void* const* z, void* x,
-                                     cudaStream_t st) {
+                                     cudaStream_t st, bool pair) {
     if (k < 1 || k > 20) return cudaErrorInvalidValue;
     ZList zl;
     for (int j = 0; j < k; ++j) {
@@ -1734,7 +1759,8 @@ cudaError_t launch_spinor_axpy_mixed(const GeomH& gh, int k, const double2* c, c
         zl.c[j] = c[j];
     }
     Geom g = make_geom(gh);
-    (note_launch(), spinor_axpy_mixed_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x));
+    if (pair) (note_launch(), spinor_axpy_mixed_df_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x));
+    else (note_launch(), spinor_axpy_mixed_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, k, zl, x));
     return cudaGetLastError();
 }
 template <class P>
@@ -1790,6 +1816,11 @@ cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const
     if (prec == 0) return sap_half_impl<P64>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st, pair);
     if (prec == 1) return sap_half_impl<P32>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st, pair);
     return sap_half_impl<P16>(g, bk, colour, nmr, x_mode, U, C, b, x, kappa, nrhs, st, pair);
+}
+cudaError_t launch_sap_half_staged16(const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode,
+                                     const void* U32, const void* C32, const void* U16, const void* C16,
+                                     const void* b, void* x, double kappa, int nrhs, cudaStream_t st) {
+    return sap_half_staged_impl<P32, P16>(g, bk, colour, nmr, x_mode, U32, C32, b, x, kappa, nrhs, st, U16, C16);
 }
 bool sap_staged_supported(int prec, const BlockH& bk) {
     int vb = bk.b[0] * bk.b[1] * bk.b[2] * bk.b[3];

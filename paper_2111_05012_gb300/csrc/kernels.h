@@ -65,9 +65,10 @@ cudaError_t launch_dirac_mixed(const GeomH& g, const void* Udd, const void* Cdd,
 cudaError_t launch_dirac_dd(const GeomH& g, const void* Udd, const void* Cdd, const void* U32, const void* C32,
                             const void* in64, void* out64, const void* b64, double kappa, int nrhs, void* hi,
                             void* lo, cudaStream_t s);
-// x (FP64 internal) += sum_j c[j] z[j] for k <= 20 FP32 internal fields z[j] (site-wise)
+// x (FP64 internal) += sum_j c[j] z[j] for k <= 20 FP32 internal fields z[j] (site-wise); pair:
+// in double-float arithmetic on the FP32 pipe (about 46 significant bits) instead of FP64
 cudaError_t launch_spinor_axpy_mixed(const GeomH& g, int k, const double2* c, const void* const* z, void* x,
-                                     cudaStream_t s);
+                                     cudaStream_t s, bool pair = false);
 // one SAP half sweep on the domains of one colour (fused residual + MR):
 //   r = b - D x on the domain, z = MR_nmr(D_SAP, r), x += z
 //   x_mode 0: x holds the iterate; 1: x is zero everywhere; 2: x is zero on the active domains
@@ -80,6 +81,12 @@ cudaError_t launch_sap_half_variant(int variant, int prec, const GeomH& g, const
                                     int x_mode, const void* U, const void* C, const void* b, void* x, double kappa,
                                     int nrhs, cudaStream_t s);
 bool sap_staged_supported(int prec, const BlockH& bk);
+// variant 3 (FP32 smoother, blocks <= 256 sites): the domain operator staged in shared memory from
+// its FP16 copy (U16, C16: prec-2 fields), FP32 arithmetic and vectors; the residual b - D x uses
+// the FP32 operator
+cudaError_t launch_sap_half_staged16(const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode,
+                                     const void* U32, const void* C32, const void* U16, const void* C16,
+                                     const void* b, void* x, double kappa, int nrhs, cudaStream_t s);
 // the half sweep with even-odd (Schur complement) domain solves; Ci = clover inverse of prec
 // (launch_clover_invert); needs an even block extent in x and at most 512 sites per block
 cudaError_t launch_sap_half_eo(int prec, const GeomH& g, const BlockH& bk, int colour, int nmr, int x_mode,

@@ -126,7 +126,7 @@ def test_bf16_coarse_operator(mgcase):
     c.amg_hierarchy_destroy(h)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_sap(mgcase, prec, variant):
     import torch
@@ -141,6 +141,10 @@ def test_sap(mgcase, prec, variant):
     y = x.clone()
     c.amg_sap(h, x, y, prec)
     tol = {0: 1e-11, 1: 1e-5, 2: 1e-2}[prec]
+    if variant == 3 and prec == 1:
+        # FP32 vectors, the minimal-residual steps with the FP16 copy of the operator (entries
+        # rounded to 2^-11 relative): the FP16 smoother's tolerance
+        tol = 1e-2
     assert rel(from_dev(y, f.shape4 + (12,)), ref) < tol
     # a batch of three in one call (the lockstep kernels: right-hand side as the fast grid
     # index; the staged variant takes two right-hand sides per CTA)
@@ -453,7 +457,7 @@ def test_mixed_precision_setup_is_orthonormal_and_galerkin(vec_prec):
     f.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1, "bf16"])
 def test_lockstep_coarse_solves_equal_single_solves(prec, variant):
     # the coarse BiCGStab(2) of a batch runs in lockstep (up to four right-hand sides per
