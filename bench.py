@@ -153,6 +153,7 @@ def dist_info():
     return rank, world, local
 
 
+SAP_DRAM_BYTES_PER_SITE_RHS = 1378.0
 SAP_KERNEL_NAMES = {0: "sap_half_kernel<P32,256> (fused SAP half sweep)",
                     1: "sap_half_staged_kernel<P32> (fused SAP half sweep, operator staged in shared memory)",
                     2: "sap_half_kernel<P32,256,2> (fused SAP half sweep, two right-hand sides per CTA)",
@@ -415,6 +416,13 @@ def run_headline(args):
         flop_site = 1872 + 24 + p.mr_iters * (1494 + 336)
     flop_step = flop_site * (V / 2) * 2 * p.sap_iters * cycles * ns
     sap_tflops = flop_step / (smooth_ms * 1e-3) / 1e12
+    # DRAM traffic of one launch (one colour, the batch's right-hand sides), scaled from an ncu
+    # capture of sap_half_kernel<P32,256,1> on 24^3x48 with 12 right-hand sides per launch
+    # (dram__bytes_read.sum + dram__bytes_write.sum = 2.372 + 0.371 GB over 165,888 active sites x
+    # 12 right-hand sides = 1378 B per active site and right-hand side); variant 0 only
+    width = max(int(i.get("batch_width", 0)) for i in infos) or 1
+    sap_traffic = (SAP_DRAM_BYTES_PER_SITE_RHS * (V / 2) * width
+                   if (args.sap_variant == 0 and not p.sap_eo) else None)
     hbm, kind = _peaks()
     # the other kernels the metric names, timed alone on this workload's fields
     kern = {}
@@ -457,7 +465,7 @@ def run_headline(args):
                                if p.sap_eo else SAP_KERNEL_NAMES.get(args.sap_variant, "sap_half (autotuned)")),
                      "bound": "alu",
                      "achieved": sap_tflops, "peak": peak, "unit": "TFLOP/s", "frac": sap_tflops / peak,
-                     "traffic": None,
+                     "traffic": sap_traffic, "rhs_per_launch": width,
                      "peak_kind": f"FP32 FMA from unit counts: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
                      "flop_per_step": flop_step, "smoother_ms_per_step": smooth_ms},
         "kernels": kern,

@@ -158,6 +158,7 @@ typedef struct {
     double ms_products;         /* part of ms_other: the outer solver's products D z (FP64-accurate) */
     double ms_orthogonalisation;/* part of ms_other: FP64 Gram-Schmidt and normalisation (GPU time) */
     double ms_true_residual;    /* part of ms_other: FP64 b - D x at restarts and exit */
+    int batch_width;            /* right-hand sides per lockstep batch (largest batch of the call) */
 } amg_solve_info;
 
 /* Message of the last failed call on this thread ("" if none). */

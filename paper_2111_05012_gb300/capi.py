@@ -75,6 +75,7 @@ class amg_solve_info(ctypes.Structure):
         ("ms_products", ctypes.c_double),
         ("ms_orthogonalisation", ctypes.c_double),
         ("ms_true_residual", ctypes.c_double),
+        ("batch_width", ctypes.c_int),
     ]
 
     def as_dict(self):

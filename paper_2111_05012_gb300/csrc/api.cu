@@ -3057,6 +3057,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
             agg.true_rel_residual = std::max(agg.true_rel_residual, i.true_rel_residual);
         }
         agg.coarse_cycles += h->coarse_cycles;
+        agg.batch_width = std::max(agg.batch_width, nb);
         agg.used_nn = used_nn;
         agg.nn_fallback = agg.nn_fallback || fell_back;
     }
