@@ -46,7 +46,8 @@ PROP_CONFIG = {
     "lattice": [48, 48, 48, 96], "rhs_per_step": 12,
     "precision": "FP32 smoother, bfloat16 coarse operator with the batched coarse solves' stencil on the tensor "
                  "cores (tcgen05, FP32 accumulation), FP16 test vectors (per-site scale) in restriction and "
-                 "prolongation, FP64 outer solver",
+                 "prolongation, FP64 outer solver (Gram-Schmidt and true residual in FP64; Arnoldi products "
+                 "and the solution update in FP64-accurate double-float pair arithmetic)",
     "l2": "working set > L2 (no flush)",
 }
 # a second workload kept for comparison with earlier measurements: one Gaussian source on 16^3 x 32
@@ -322,6 +323,10 @@ def run_headline(args):
         w["dims"] = tuple(int(v) for v in args.dims.split(","))
         config = dict(PROP_CONFIG, lattice=list(w["dims"]),
                       workload=PROP_CONFIG["workload"].replace("48^3x96", "x".join(map(str, w["dims"]))))
+    if args.resid_pair:
+        config = dict(config, precision=config["precision"].replace(
+            "Gram-Schmidt and true residual in FP64; Arnoldi products and the solution update",
+            "Gram-Schmidt in FP64; Arnoldi products, the true residual and the solution update"))
     dims = w["dims"]
     V = int(np.prod(dims))
     stream = torch.cuda.current_stream()
@@ -341,6 +346,7 @@ def run_headline(args):
     if args.prop_coarse == "bf16":
         p.prec_coarsest = capi.AMG_BF16
         p.coarse_tc = 0 if args.no_coarse_tc else 1
+    p.resid_pair = 1 if args.resid_pair else 0
     t0 = time.perf_counter()
     h = capi.amg_setup(d, p, [init])
     torch.cuda.synchronize()
@@ -1106,6 +1112,9 @@ def main():
                     help="propagator: coarsest operator storage (bf16, the default: bfloat16 entries)")
     ap.add_argument("--no-coarse-tc", action="store_true",
                     help="propagator with bf16: batched coarse solves on the SIMT solver instead of the tensor cores")
+    ap.add_argument("--resid-pair", action="store_true",
+                    help="propagator: the outer solver's true residual in double-float pair arithmetic on the "
+                         "FP32 pipe (about 46 significant bits) instead of the FP64 stencil")
     ap.add_argument("--sap-eo", action="store_true",
                     help="propagator: even-odd (Schur complement) SAP domain solves")
     ap.add_argument("--mr", type=int, default=None, help="propagator: minimal-residual steps per domain solve")

@@ -138,6 +138,10 @@ typedef struct {
                                            tensor cores (bfloat16 operands including the vectors, FP32
                                            accumulation); 0: the persistent SIMT solver for every batch
                                            (four right-hand sides per launch) [0] */
+    int resid_pair;                     /* outer solver's true residual b - D x: 0 the FP64 stencil;
+                                           1 (smoother not FP64) x split into float parts and D in the
+                                           double-float pair arithmetic of the Arnoldi product on the
+                                           FP32 pipe, about 46 significant bits [0] */
 } amg_params;
 
 typedef struct {

@@ -54,6 +54,7 @@ class amg_params(ctypes.Structure):
         ("mbicgs_maxit", ctypes.c_int),
         ("sap_eo", ctypes.c_int),
         ("coarse_tc", ctypes.c_int),
+        ("resid_pair", ctypes.c_int),
     ]
 
 

@@ -326,6 +326,7 @@ amg_status check_params(const GeomH& g, const amg_params* p) {
     if (p->outer_m < 1 || p->outer_m > 19) return fail(AMG_EINVAL, "outer_m must be 1..19");
     if (p->outer_solver < 0 || p->outer_solver > 2) return fail(AMG_EINVAL, "outer_solver must be 0, 1 or 2");
     if (p->sap_variant < -1 || p->sap_variant > 3) return fail(AMG_EINVAL, "sap_variant must be -1, 0, 1, 2 or 3");
+    if (p->resid_pair != 0 && p->resid_pair != 1) return fail(AMG_EINVAL, "resid_pair must be 0 or 1");
     if (p->sap_eo != 0 && p->sap_eo != 1) return fail(AMG_EINVAL, "sap_eo must be 0 or 1");
     if (p->sap_eo) {
         BlockH b0;
@@ -360,7 +361,7 @@ amg_status fine_D(amg_hierarchy* h, int prec, const void* in, void* out, const v
 // else the FP64 stencil
 amg_status true_residual(amg_hierarchy* h, const void* x, void* r, const void* b, int nb, cudaStream_t s) {
     amg_dirac* d = h->d;
-    if (h->fp != 0 && d->gauge->U[3].p && d->C[3].p && d->gauge->U[1].p && d->C[1].p) {
+    if (h->p.resid_pair && h->fp != 0 && d->gauge->U[3].p && d->C[3].p && d->gauge->U[1].p && d->C[1].p) {
         // x split into the FP32 workspaces (free between cycles; nb fields each when fp != 0)
         CK(launch_dirac_dd(fine_geom(h), d->gauge->U[3].p, d->C[3].p, d->gauge->U[1].p, d->C[1].p, x, r, b,
                            d->kappa, nb, h->fb[1].p, h->fx[1].p, s));
@@ -2040,6 +2041,7 @@ bool fusable(const std::vector<RaggedProb>& P) {
             vb > 256 || h->p.outer_m + 1 > 20 || h->p.coarse_ell > 4 || h->nn)
             return false;
         if (h->p.sap_iters != h0->p.sap_iters || h->p.mr_iters != h0->p.mr_iters) return false;
+        if (h->p.resid_pair != h0->p.resid_pair) return false;
         if (!h->d->gauge->U[3].p || !h->d->C[3].p || !h->d->gauge->U[1].p || !h->d->C[1].p) return false;
     }
     return true;
@@ -2197,7 +2199,9 @@ amg_status fgmres_fused(std::vector<RaggedProb>& P, cudaStream_t st, double tol,
         if (set.empty()) break;
         TRY(fused_tables(F, P, set, 0, 1, tot1, st));
         const int ns = (int)set.size();
-        if (!first) CK(launch_resid_ragged(F.d(1), F.o(1, FusedBatch::T_SITE), ns, tot1[FusedBatch::T_SITE], st));
+        if (!first)
+            CK(launch_resid_ragged(F.d(1), F.o(1, FusedBatch::T_SITE), ns, tot1[FusedBatch::T_SITE],
+                                   P[0].h->p.resid_pair != 0, st));
         CK(launch_norm_v0_ragged(F.d(1), F.o(1, FusedBatch::T_BLAS), ns, tot1[FusedBatch::T_BLAS], st));
         CK(cudaMemcpyAsync(F.hcoef, F.coef.p, sizeof(double2) * 64 * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -2372,6 +2376,7 @@ void amg_params_default(amg_params* p) {
     p->mbicgs_maxit = 50;
     p->sap_eo = 0;
     p->coarse_tc = 0;
+    p->resid_pair = 0;
 }
 
 

@@ -367,6 +367,16 @@ __global__ void __launch_bounds__(kThreads, P::id == 0 ? 2 : 3) dirac_kernel(Geo
 }
 
 // ragged batch, restart phases (site loops over each problem's lattice)
+// r = b - D x with the FP64 stencil
+__global__ void __launch_bounds__(kThreads, 2)
+    resid64_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
+    int p, bx, gx;
+    ragged_locate(off, np, p, bx, gx);
+    const RaggedDev& q = d[p];
+    for (int s = bx * blockDim.x + threadIdx.x; s < q.g.V; s += gx * blockDim.x)
+        dirac_site<P64, false, true>(q.g, q.bk, q.U64, q.C64, (const char*)q.x64, (char*)q.r64, (const char*)q.b64,
+                                     q.kappa, s);
+}
 __global__ void pack_ragged_kernel(const RaggedDev* __restrict__ d, const int* __restrict__ off, int np) {
     int p, bx, gx;
     ragged_locate(off, np, p, bx, gx);
@@ -1921,7 +1931,11 @@ cudaError_t launch_unpack_ragged(const void* d, const int* off, int np, int ctas
     (note_launch(), unpack_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
     return cudaGetLastError();
 }
-cudaError_t launch_resid_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t st) {
+cudaError_t launch_resid_ragged(const void* d, const int* off, int np, int ctas, bool pair, cudaStream_t st) {
+    if (!pair) {
+        (note_launch(), resid64_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
+        return cudaGetLastError();
+    }
     (note_launch(), split_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
     (note_launch(), resid_ragged_kernel<<<ctas, kThreads, 0, st>>>((const RaggedDev*)d, off, np));
     return cudaGetLastError();

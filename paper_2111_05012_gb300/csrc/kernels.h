@@ -296,11 +296,11 @@ cudaError_t launch_dirac_mixed_ragged(const void* d, const int* off, int np, int
 // one classical Gram-Schmidt pass against k = j + 1 basis vectors, then V_{j+1} = w' / |w'|
 cudaError_t launch_gs_ragged(int k, const void* d, const int* off, int np, int ctas, int pass, cudaStream_t s);
 // restart phases of a fused ragged batch (tables of the problems concerned):
-// b64 = canon_in and x64 = 0; canon_out = x64; r64 = b64 - D x64 (two launches: x64 split into
-// f32 + f32b, then the pair stencil, as launch_dirac_dd); the norm of rsrc into
-// nval and basis[0] = rsrc / |rsrc| (two launches); x64 += sum_i yc[i] zb[i]
+// b64 = canon_in and x64 = 0; canon_out = x64; r64 = b64 - D x64 (the FP64 stencil, or with pair
+// two launches: x64 split into f32 + f32b, then the pair stencil, as launch_dirac_dd); the norm
+// of rsrc into nval and basis[0] = rsrc / |rsrc| (two launches); x64 += sum_i yc[i] zb[i]
 cudaError_t launch_pack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
 cudaError_t launch_unpack_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
-cudaError_t launch_resid_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
+cudaError_t launch_resid_ragged(const void* d, const int* off, int np, int ctas, bool pair, cudaStream_t s);
 cudaError_t launch_norm_v0_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);
 cudaError_t launch_xupdate_ragged(const void* d, const int* off, int np, int ctas, cudaStream_t s);

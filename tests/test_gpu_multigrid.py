@@ -330,15 +330,18 @@ def test_batched_restrict_prolong(mgcase):
     c.amg_hierarchy_destroy(h)
 
 
-@pytest.mark.parametrize("coarse", ["f32", "bf16"])
+@pytest.mark.parametrize("coarse", ["f32", "bf16", "bf16-pair-residual"])
 def test_twelve_point_sources_in_one_batched_solve(coarse):
+    # (bf16-pair-residual: the outer solver's true residual in double-float pair arithmetic;
+    # the oracle's FP64 D below re-checks every solution all the same)
     import torch
     dims = (8, 8, 8, 8)
     f = Field(dims, 0.5, 4, 0.129, 1.0)
     c = f.c
     p = _params(c, (4, 4, 4, 4), 8, 1, n_init=2, n_adapt=1)
-    if coarse == "bf16":
+    if coarse.startswith("bf16"):
         p.prec_coarsest = c.AMG_BF16
+    p.resid_pair = 1 if coarse.endswith("pair-residual") else 0
     h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 4, 8))])
     srcs = np.stack([li.point_source(dims, s, col) for s in range(4) for col in range(3)])
     b = to_dev(srcs)
