@@ -618,6 +618,9 @@ def run_dirac(args):
     # f64d: the same arithmetic on FP64 input (every value split into a float pair)
     bytes_site = {"f64": 1536, "f32": 672, "f16": 344, "f64x": 96 + 192 + 4 * 144 + 576,
                   "f64d": 192 + 192 + 4 * 144 + 576}
+    # the launch shapes the autotuner picks on this lattice (CTA size, grid cap, register budget)
+    shapes = {name: capi.amg_dirac_tune(d, prec)
+              for name, prec in (("f64", capi.AMG_F64), ("f32", capi.AMG_F32), ("f16", capi.AMG_F16))}
     with ClockSampler() as clk:
         for name, prec in (("f64", capi.AMG_F64), ("f32", capi.AMG_F32), ("f16", capi.AMG_F16),
                            ("f64x", capi.AMG_F64X), ("f64d", capi.AMG_F64D)):
@@ -629,6 +632,9 @@ def run_dirac(args):
             gbs = bytes_site[name] * V / (ms * 1e-3) / 1e9
             per[name] = {"ms_per_apply": ms, "gb_per_s": gbs, "frac_hbm": gbs / hbm, "bytes_per_site": bytes_site[name],
                          "gflops": 1872 * V / (ms * 1e-3) / 1e9, "launches": launches}
+            if name in shapes:
+                per[name]["launch_shape"] = dict(zip(("threads", "ctas_per_sm_cap", "regs_ctas_per_sm"),
+                                                     shapes[name]))
     f32 = per["f32"]
     line = {"metric": "Wilson-clover D application, kernel time (HBM roofline)", "value": f32["ms_per_apply"],
             "unit": "ms/apply", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

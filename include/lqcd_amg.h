@@ -265,6 +265,22 @@ amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_pr
  * amg_apply_D (element type double for AMG_F64, float otherwise). */
 amg_status amg_apply_D_noalloc(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s);
 
+/* Autotune the launch shape of the fine stencil in precision prec (AMG_F64,
+ * AMG_F32, AMG_F16) on d's lattice: CTA size and grid cap, and for FP32 / FP16
+ * the register budget (2 resident CTAs per SM, 128 registers, against the
+ * default).  The choice is process-wide and used by every later stencil
+ * launch of that precision (amg_setup runs the same tuner for the precisions
+ * a solve uses).  Outputs (may be NULL): threads per CTA, grid cap in CTAs
+ * per SM, register budget as resident CTAs per SM (0 = the default).
+ * Synchronises the device.  No counterpart in the paper. */
+amg_status amg_dirac_tune(amg_dirac* d, amg_prec prec, int* threads, int* per_sm, int* regs_ctas);
+
+/* Set the stencil's launch shape for prec by hand (process-wide, as amg_dirac_tune
+ * leaves it): threads per CTA (a multiple of 32, at most 256), grid cap in CTAs
+ * per SM (>= 1), register budget as resident CTAs per SM (0 or 3 = the
+ * precision's default, 2 = 128 registers; FP64 ignores it).  AMG_EINVAL otherwise. */
+amg_status amg_dirac_set_shape(amg_prec prec, int threads, int per_sm, int regs_ctas);
+
 /* Timing of the Eq. 1 stencil alone: packs the canonical input `in` (nrhs
  * fields, element type as for amg_apply_D) into the library's internal layout
  * once, then applies D to it `reps` times on stream s, bracketed by CUDA

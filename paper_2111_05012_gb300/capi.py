@@ -132,6 +132,8 @@ PROTOTYPES = {
     "amg_solve_ragged": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _d, _i,
                               ctypes.POINTER(amg_solve_info), _vp]),
     "amg_set_ragged_fusion": (None, [_i]),
+    "amg_dirac_tune": (_i, [_vp, _i, _ip, _ip, _ip]),
+    "amg_dirac_set_shape": (_i, [_i, _i, _i, _i]),
     "amg_nn_create": (_i, [_vp, _i, _ip, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
     "amg_nn_destroy": (None, [_vp]),
     "amg_nn_get_weights": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_float)]),
@@ -268,6 +270,17 @@ def amg_apply_D(d, inp, out, nrhs=1, prec=AMG_F64, stream=None):
 
 def amg_apply_D_noalloc(d, inp, out, nrhs=1, prec=AMG_F64, stream=None):
     _check(load().amg_apply_D_noalloc(d, _ptr(inp), _ptr(out), int(nrhs), int(prec), _stream(stream)))
+
+
+def amg_dirac_tune(d, prec):
+    """Autotune the stencil's launch shape for prec; returns (threads, per_sm, regs_ctas)."""
+    a, b, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().amg_dirac_tune(d, int(prec), ctypes.byref(a), ctypes.byref(b), ctypes.byref(m)))
+    return a.value, b.value, m.value
+
+
+def amg_dirac_set_shape(prec, threads, per_sm, regs_ctas=0):
+    _check(load().amg_dirac_set_shape(int(prec), int(threads), int(per_sm), int(regs_ctas)))
 
 
 def amg_dirac_time(d, inp, nrhs=1, prec=AMG_F32, reps=20, stream=None):

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <array>
 #include <vector>
 
 static std::atomic<unsigned long long> g_launches{0};
@@ -1448,6 +1449,49 @@ amg_status setup_coarse_level(amg_hierarchy* h, int l, const double* const* init
 // variant shares its staged operator between two right-hand sides per CTA; an
 // odd batch leaves half of its last CTAs idle, so three is its worst case), and
 // keep the faster variant for each.
+// Autotuner of the stencil's launch shape for precision pr (process-wide, dirac_set_shape):
+// CTA size x grid cap from four candidates, then for FP32 / FP16 the 128-register budget for
+// the best of them; median of two timed launches each on in -> out (fields of d's lattice)
+amg_status tune_dirac_shape(amg_dirac* d, int pr, const void* in, void* out) {
+    const GeomH& g = d->gauge->lat->g;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<std::array<int, 3>> cand = {{256, 16, 0}, {128, 16, 0}, {256, 4, 0}, {128, 64, 0}};
+    float best = 1e30f;
+    int bt = 256, bs = 16, bm = 0;
+    cudaError_t err = cudaSuccess;
+    for (size_t ci = 0; ci < cand.size() && err == cudaSuccess; ++ci) {
+        const auto c = cand[ci];
+        dirac_set_shape(pr, c[0], c[1], c[2]);
+        std::vector<float> t;
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+            err = cudaEventRecord(e0, 0);
+            if (err == cudaSuccess)
+                err = launch_dirac(pr, g, nullptr, d->gauge->U[pr].p, d->C[pr].p, in, out, nullptr, d->kappa, 1, 0);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t.push_back(ms);
+        }
+        if (err != cudaSuccess) break;
+        std::sort(t.begin(), t.end());
+        if (t[t.size() / 2] < best) {
+            best = t[t.size() / 2];
+            bt = c[0];
+            bs = c[1];
+            bm = c[2];
+        }
+        if (ci == 3 && pr != 0) cand.push_back({bt, bs, 2});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dirac_set_shape(pr, bt, bs, bm);
+    CK(err);
+    return AMG_OK;
+}
+
 amg_status tune_kernels(amg_hierarchy* h) {
     const GeomH& g = fine_geom(h);
     amg_dirac* d = h->d;
@@ -1506,41 +1550,9 @@ amg_status tune_kernels(amg_hierarchy* h) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    // launch shape of the stencil (threads per CTA x grid cap) for the precisions the solve
-    // applies D in: the smoother's (relaxed products) and FP64 (true residual)
-    {
-        cudaEvent_t e0, e1;
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        for (int pr : {h->fp, 0}) {
-            const int cand[][2] = {{256, 16}, {128, 16}, {256, 4}, {128, 64}};
-            float best = 1e30f;
-            int bt = 256, bs = 16;
-            for (const auto& c : cand) {
-                dirac_set_shape(pr, c[0], c[1]);
-                std::vector<float> t;
-                for (int rep = 0; rep < 3; ++rep) {
-                    CK(cudaEventRecord(e0, 0));
-                    CK(launch_dirac(pr, g, nullptr, d->gauge->U[pr].p, d->C[pr].p, h->fx[pr].p, h->fb[pr].p, nullptr,
-                                    d->kappa, 1, 0));
-                    CK(cudaEventRecord(e1, 0));
-                    CK(cudaEventSynchronize(e1));
-                    float ms = 0;
-                    CK(cudaEventElapsedTime(&ms, e0, e1));
-                    if (rep > 0) t.push_back(ms);
-                }
-                std::sort(t.begin(), t.end());
-                if (t[t.size() / 2] < best) {
-                    best = t[t.size() / 2];
-                    bt = c[0];
-                    bs = c[1];
-                }
-            }
-            dirac_set_shape(pr, bt, bs);
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
+    // launch shape of the stencil (threads per CTA x grid cap x register budget) for the
+    // precisions the solve applies D in: the smoother's (relaxed products) and FP64 (true residual)
+    for (int pr : {h->fp, 0}) TRY(tune_dirac_shape(d, pr, h->fx[pr].p, h->fb[pr].p));
     return AMG_OK;
 }
 
@@ -2535,6 +2547,30 @@ static amg_status apply_fine_canonical(amg_dirac* d, const BlockH* sb, const voi
 
 amg_status amg_apply_D(amg_dirac* d, const void* in, void* out, int nrhs, amg_prec prec, amg_stream s) {
     return apply_fine_canonical(d, nullptr, in, out, nrhs, prec, (cudaStream_t)s);
+}
+
+amg_status amg_dirac_set_shape(amg_prec prec, int threads, int per_sm, int regs_ctas) {
+    if (prec < 0 || prec > 2 || threads < 32 || threads > 256 || threads % 32 || per_sm < 1 ||
+        (regs_ctas != 0 && regs_ctas != 2 && regs_ctas != 3))
+        return fail(AMG_EINVAL, "bad stencil launch shape");
+    dirac_set_shape(prec, threads, per_sm, regs_ctas);
+    return AMG_OK;
+}
+
+amg_status amg_dirac_tune(amg_dirac* d, amg_prec prec, int* threads, int* per_sm, int* regs_ctas) {
+    if (!d || prec < 0 || prec > 2) return fail(AMG_EINVAL, "prec must be AMG_F64, AMG_F32 or AMG_F16");
+    const GeomH& g = d->gauge->lat->g;
+    DevBuf a, b;
+    CK(a.ensure(fine_spinor_bytes(prec, g.V)));
+    CK(b.ensure(fine_spinor_bytes(prec, g.V)));
+    CK(cudaMemset(a.p, 0, fine_spinor_bytes(prec, g.V)));
+    TRY(tune_dirac_shape(d, prec, a.p, b.p));
+    int t = 0, ps = 0, mb = 0;
+    dirac_get_shape(prec, &t, &ps, &mb);
+    if (threads) *threads = t;
+    if (per_sm) *per_sm = ps;
+    if (regs_ctas) *regs_ctas = mb;
+    return AMG_OK;
 }
 
 amg_status amg_dirac_time(amg_dirac* d, const void* in, int nrhs, amg_prec prec, int reps, amg_stream s,

@@ -353,8 +353,10 @@ DEV void dirac_site(const Geom& g, const Blocking& bk, const void* __restrict__ 
         SpinorIO<P>::store(dst, g.V, s, acc);
     }
 }
-template <class P, bool SAP, bool RESID>
-__global__ void __launch_bounds__(kThreads, P::id == 0 ? 2 : 3) dirac_kernel(Geom g, Blocking bk, const void* __restrict__ U,
+// MB: resident CTAs per SM the register budget is set for (launch bounds; 0 = the default of
+// the precision); the autotuner picks it with the CTA size and grid cap
+template <class P, bool SAP, bool RESID, int MB = 0>
+__global__ void __launch_bounds__(kThreads, MB ? MB : (P::id == 0 ? 2 : 3)) dirac_kernel(Geom g, Blocking bk, const void* __restrict__ U,
                                                          const void* __restrict__ C, const void* in, void* out,
                                                          const void* b, typename P::T kappa) {
     const int r = blockIdx.y;
@@ -1580,9 +1582,9 @@ cudaError_t sap_half_impl(const GeomH& gh, const BlockH& bh, int colour, int nmr
 // launch shape of the stencil per precision, chosen by the autotuner (dirac_set_shape):
 // threads per CTA and the grid cap in CTAs per SM (grid-stride loop beyond it)
 struct DiracShape {
-    int threads, per_sm;
+    int threads, per_sm, mb;   // mb: register budget as resident CTAs per SM (0 = the default)
 };
-DiracShape g_dirac_shape[3] = {{kThreads, 16}, {kThreads, 16}, {kThreads, 16}};
+DiracShape g_dirac_shape[3] = {{kThreads, 16, 0}, {kThreads, 16, 0}, {kThreads, 16, 0}};
 
 template <class P>
 cudaError_t dirac_impl(const GeomH& gh, const BlockH* sb, const void* U, const void* C, const void* in, void* out,
@@ -1601,10 +1603,17 @@ cudaError_t dirac_impl(const GeomH& gh, const BlockH* sb, const void* U, const v
     if (sb) {
         if (b) (note_launch(), dirac_kernel<P, true, true><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
         else (note_launch(), dirac_kernel<P, true, false><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
-    } else {
-        if (b) (note_launch(), dirac_kernel<P, false, true><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
-        else (note_launch(), dirac_kernel<P, false, false><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+        return cudaGetLastError();
     }
+    if constexpr (P::id != 0) {
+        if (sh.mb == 2) {
+            if (b) (note_launch(), dirac_kernel<P, false, true, 2><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+            else (note_launch(), dirac_kernel<P, false, false, 2><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+            return cudaGetLastError();
+        }
+    }
+    if (b) (note_launch(), dirac_kernel<P, false, true><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
+    else (note_launch(), dirac_kernel<P, false, false><<<grid, th, 0, st>>>(g, bk, U, C, in, out, b, (T)kappa));
     return cudaGetLastError();
 }
 
@@ -1739,13 +1748,15 @@ cudaError_t launch_clover_expand(const GeomH& gh, const void* C64, double* out, 
     (note_launch(), clover_expand_kernel<<<grid_for(g.V, kThreads), kThreads, 0, st>>>(g, C64, out));
     return cudaGetLastError();
 }
-void dirac_set_shape(int prec, int threads, int per_sm) {
+void dirac_set_shape(int prec, int threads, int per_sm, int mb) {
     if (prec < 0 || prec > 2 || threads < 32 || threads > kThreads || threads % 32 || per_sm < 1) return;
-    g_dirac_shape[prec] = {threads, per_sm};
+    if (mb != 0 && mb != 2 && mb != 3) return;
+    g_dirac_shape[prec] = {threads, per_sm, prec == 0 ? 0 : mb};
 }
-void dirac_get_shape(int prec, int* threads, int* per_sm) {
+void dirac_get_shape(int prec, int* threads, int* per_sm, int* mb) {
     *threads = g_dirac_shape[prec].threads;
     *per_sm = g_dirac_shape[prec].per_sm;
+    if (mb) *mb = g_dirac_shape[prec].mb;
 }
 cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sb, const void* U, const void* C, const void* in,
                          void* out, const void* b, double kappa, int nrhs, cudaStream_t st) {

@@ -47,10 +47,11 @@ cudaError_t launch_clover_build(int prec, const GeomH& g, const void* U64, doubl
 // internal P64 clover -> [site][2][6][6][2] doubles (device)
 cudaError_t launch_clover_expand(const GeomH& g, const void* C64, double* out, cudaStream_t s);
 
-// launch shape of launch_dirac per precision (0..2): threads per CTA (a multiple of 32, <= 256)
-// and the grid cap in CTAs per SM; set by the autotuner, process-wide
-void dirac_set_shape(int prec, int threads, int per_sm);
-void dirac_get_shape(int prec, int* threads, int* per_sm);
+// launch shape of launch_dirac per precision (0..2): threads per CTA (a multiple of 32, <= 256),
+// the grid cap in CTAs per SM, and the register budget as resident CTAs per SM (mb: 2 for FP32 /
+// FP16, 128 registers; 0 or 3 = the precision's default); set by the autotuner, process-wide
+void dirac_set_shape(int prec, int threads, int per_sm, int mb = 0);
+void dirac_get_shape(int prec, int* threads, int* per_sm, int* mb = nullptr);
 // out = D in (sap_block != NULL: hops between blocks removed); if b != NULL, out = b - D in
 cudaError_t launch_dirac(int prec, const GeomH& g, const BlockH* sap_block, const void* U, const void* C,
                          const void* in, void* out, const void* b, double kappa, int nrhs, cudaStream_t s);

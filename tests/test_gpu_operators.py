@@ -43,6 +43,28 @@ def test_apply_D(field, prec):
     assert rel(got, ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_apply_D_in_every_launch_shape(field, prec):
+    # the autotuner's candidates (CTA size x grid cap x register budget) give the same D,
+    # and the shape it picks is one of them
+    c = field.c
+    psi = np.stack([li.rhs(field.dims, 7, i) for i in range(2)])
+    ref = np.stack([field.op.apply(p.reshape(field.shape4 + (12,))) for p in psi])
+    x = to_dev(psi, DT[prec])
+    try:
+        for shape in [(256, 16, 0), (128, 16, 0), (256, 4, 0), (128, 64, 0), (256, 16, 2), (64, 1, 2)]:
+            c.amg_dirac_set_shape(prec, *shape)
+            y = x.clone()
+            c.amg_apply_D(field.d, x, y, 2, prec)
+            assert rel(from_dev(y, (2,) + field.shape4 + (12,)), ref) < TOL[prec]
+        t, ps, mb = c.amg_dirac_tune(field.d, prec)
+        assert t in (128, 256) and ps in (4, 16, 64) and mb in (0, 2)
+    finally:
+        c.amg_dirac_set_shape(prec, 256, 16, 0)
+    with pytest.raises(c.AMGError):
+        c.amg_dirac_set_shape(prec, 100, 16, 0)
+
+
 def test_apply_D_mixed_fp64_accurate(field):
     # FP32 input taken as exact, FP64-accurate double-float stencil, double output:
     # compared with the oracle applied to the same (FP32-rounded) input
