@@ -498,7 +498,11 @@ amg_status amg_hierarchy_set_nn(amg_hierarchy* h, amg_nn* nn);
  * summed on the device (one host synchronisation per step), with a second
  * pass wherever eps ||w|| / ||w'|| would exceed 1e-9.  With outer_solver = 1
  * the paper's flexible BiCGStab runs instead, one right-hand side at a
- * time.  x is an input initial
+ * time.  b and x may be device memory, or host memory (pinned, or pageable):
+ * then each batch's b is copied in on the hierarchy's copy stream while the
+ * previous batch solves, and its x copied out while the next batch solves
+ * (device staging of one batch of each; pinned memory lets the copies
+ * overlap the solves); the call returns with x in host memory.  x is an input initial
  * guess if use_x0 != 0, else overwritten.  info (may be NULL) receives, over
  * all right-hand sides, the largest iteration count and true residual, the
  * summed phase times and whether all converged.  Returns AMG_NOT_CONVERGED

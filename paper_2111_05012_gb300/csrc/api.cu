@@ -264,7 +264,18 @@ struct amg_hierarchy {
         gexec.clear();
         gkernels.clear();
     }
+    // amg_solve with host vectors: device staging of one batch of canonical b, a copy stream
+    // and its events (b staged, b consumed, x staged, x copied out).  x is staged in the last
+    // Arnoldi basis vector oV[outer_m] (free between solves, written only at a cycle's last
+    // step, which then waits for the copy-out: io_x_pending)
+    DevBuf io_b;
+    bool io_x_pending = false;
+    cudaStream_t io_st = nullptr;
+    cudaEvent_t io_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     ~amg_hierarchy() {
+        for (auto e : io_ev)
+            if (e) cudaEventDestroy(e);
+        if (io_st) cudaStreamDestroy(io_st);
         clear_graphs();
         if (hstate) cudaFreeHost(hstate);
         if (gs_hcoef) cudaFreeHost(gs_hcoef);
@@ -1068,6 +1079,9 @@ amg_status fgmres(amg_hierarchy* h, int nb, const void* b, void* x, bool x_nonze
             double2* const gc = h->gs_coef.as<double2>();
             std::vector<double> hnv(nb, 0.0);   // |w'| exactly as the normalisation used it
             std::vector<char> again(nb, 0);
+            // the last basis vector doubles as the copy-out staging of a host-vector solve's
+            // previous batch: wait for that copy before overwriting it
+            if (j + 1 == m && h->io_x_pending) CK(cudaStreamWaitEvent(s, h->io_ev[3], 0));
             for (int pass = 0; pass < 2; ++pass) {
                 h->timer.start(PH_ORTH, s);
                 bool any = false;
@@ -3030,6 +3044,29 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     if (!h || !b || !x || nrhs < 1 || !(tol > 0) || maxit < 1) return fail(AMG_EINVAL, "bad argument");
     const GeomH& g = fine_geom(h);
     cudaStream_t st = (cudaStream_t)s;
+    // host vectors (pinned or pageable): each batch's b is copied in on a copy stream while
+    // the previous batch solves, and its x copied out while the next one solves
+    auto on_host = [](const void* p) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return true;
+        }
+        return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+    };
+    const bool host_io = on_host(b) || on_host(x);
+    // the large copies go in 32 MB pieces: a copy engine serves its queue in order, and the
+    // solver's small device-to-host reads on s (the Hessenberg coefficients of every step)
+    // would otherwise wait behind a whole batch's vectors (tens of ms each)
+    auto copy_pieces = [](void* dst, const void* src, size_t bytes, cudaStream_t cs) -> cudaError_t {
+        constexpr size_t kPiece = size_t(32) << 20;
+        for (size_t o = 0; o < bytes; o += kPiece) {
+            cudaError_t e = cudaMemcpyAsync((char*)dst + o, (const char*)src + o, std::min(kPiece, bytes - o),
+                                            cudaMemcpyDefault, cs);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     // right-hand sides solved in lockstep: up to 12, fewer if the batch's
     // workspaces (FGMRES basis, Z vectors, cycle fields) would not fit in 80%
     // of the free device memory
@@ -3039,6 +3076,7 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         size_t per = f64 * (h->p.outer_m + 1 + 4) + fz * h->p.outer_m;
         for (int pr = 0; pr < 3; ++pr)
             if (pr == h->fp || pr == 1) per += 2 * fine_spinor_bytes(pr, g.V);
+        if (host_io) per += f64;   // canonical b staging
         size_t have = 0, total = 0;
         if (cudaMemGetInfo(&have, &total) == cudaSuccess) {
             // memory the current batch capacity already holds counts as available
@@ -3055,6 +3093,20 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
     auto t_all = std::chrono::steady_clock::now();
     h->timer.reset();
     h->timer.on = info != nullptr;
+    const size_t cb = fine_spinor_bytes(0, g.V);   // one canonical vector (192 B per site)
+    if (host_io) {
+        CK(h->io_b.ensure(cb * std::min(kMaxBatch, nrhs)));
+        if (!h->io_st) CK(cudaStreamCreateWithFlags(&h->io_st, cudaStreamNonBlocking));
+        for (auto& e : h->io_ev)
+            if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // work the caller queued on s before the call comes first; the first batch's b goes in
+        CK(cudaEventRecord(h->io_ev[1], st));
+        CK(cudaStreamWaitEvent(h->io_st, h->io_ev[1], 0));
+        CK(cudaEventRecord(h->io_ev[3], h->io_st));   // the x staging starts free
+        h->io_x_pending = true;
+        CK(copy_pieces(h->io_b.p, b, cb * std::min(kMaxBatch, nrhs), h->io_st));
+        CK(cudaEventRecord(h->io_ev[0], h->io_st));
+    }
     for (int r0 = 0; r0 < nrhs; r0 += kMaxBatch) {
         const int nb = std::min(kMaxBatch, nrhs - r0);
         TRY(alloc_workspaces(h, nb));
@@ -3063,9 +3115,31 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         h->tc_cycles = 0;
         const double* br = b + (size_t)r0 * g.V * 24;
         double* xr = x + (size_t)r0 * g.V * 24;
-        CK(launch_pack_spinor(0, g, br, h->ob.p, nb, st));
-        if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
-        else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
+        if (host_io) {
+            // b of this batch staged (io_ev[0]); once packed, the staging takes the next batch's b
+            CK(cudaStreamWaitEvent(st, h->io_ev[0], 0));
+            CK(launch_pack_spinor(0, g, h->io_b.p, h->ob.p, nb, st));
+            CK(cudaEventRecord(h->io_ev[1], st));
+            const int r1 = r0 + nb;
+            if (r1 < nrhs) {
+                CK(cudaStreamWaitEvent(h->io_st, h->io_ev[1], 0));
+                CK(copy_pieces(h->io_b.p, b + (size_t)r1 * g.V * 24, cb * std::min(kMaxBatch, nrhs - r1),
+                               h->io_st));
+                CK(cudaEventRecord(h->io_ev[0], h->io_st));
+            }
+            if (use_x0) {
+                void* xs = h->oV[h->p.outer_m]->p;
+                CK(cudaStreamWaitEvent(st, h->io_ev[3], 0));
+                CK(cudaMemcpyAsync(xs, xr, cb * nb, cudaMemcpyDefault, st));
+                CK(launch_pack_spinor(0, g, xs, h->ox.p, nb, st));
+            } else {
+                CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
+            }
+        } else {
+            CK(launch_pack_spinor(0, g, br, h->ob.p, nb, st));
+            if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
+            else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
+        }
         std::vector<amg_solve_info> infos;
         amg_status rs = outer_solve(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
         int used_nn = (h->nn && !h->nn_off) ? 1 : 0, fell_back = 0;
@@ -3074,7 +3148,13 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
             int prev = 0;
             for (auto& i : infos) prev = std::max(prev, i.iters);
             h->nn_off = true;
-            if (use_x0) CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
+            if (use_x0 && host_io) {
+                void* xs = h->oV[h->p.outer_m]->p;   // the first solve may have written it
+                CK(cudaMemcpyAsync(xs, xr, cb * nb, cudaMemcpyDefault, st));
+                CK(launch_pack_spinor(0, g, xs, h->ox.p, nb, st));
+            } else if (use_x0) {
+                CK(launch_pack_spinor(0, g, xr, h->ox.p, nb, st));
+            }
             else CK(cudaMemsetAsync(h->ox.p, 0, fine_spinor_bytes(0, g.V) * nb, st));
             std::memset(h->hstate, 0, 16 * 16);
             rs = outer_solve(h, nb, h->ob.p, h->ox.p, use_x0 != 0, tol, maxit, infos, st);
@@ -3083,8 +3163,25 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
             used_nn = 0;
             fell_back = 1;
         }
-        if (rs != AMG_OK && rs != AMG_NOT_CONVERGED) return rs;
-        CK(launch_unpack_spinor(0, g, h->ox.p, xr, nb, st));
+        if (rs != AMG_OK && rs != AMG_NOT_CONVERGED) {
+            if (host_io) {
+                cudaStreamSynchronize(h->io_st);
+                h->io_x_pending = false;
+            }
+            return rs;
+        }
+        if (host_io) {
+            // x staged once the previous batch's copy-out is done; copied out while the next solves
+            void* xs = h->oV[h->p.outer_m]->p;
+            CK(cudaStreamWaitEvent(st, h->io_ev[3], 0));
+            CK(launch_unpack_spinor(0, g, h->ox.p, xs, nb, st));
+            CK(cudaEventRecord(h->io_ev[2], st));
+            CK(cudaStreamWaitEvent(h->io_st, h->io_ev[2], 0));
+            CK(copy_pieces(xr, xs, cb * nb, h->io_st));
+            CK(cudaEventRecord(h->io_ev[3], h->io_st));
+        } else {
+            CK(launch_unpack_spinor(0, g, h->ox.p, xr, nb, st));
+        }
         CK(cudaMemcpyAsync(h->hstate + 60, h->lev[h->p.nlevels - 1].cs_state.p, 16, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         TRY(coarse_status(h));
@@ -3101,6 +3198,11 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, int nrhs, dou
         agg.batch_width = std::max(agg.batch_width, nb);
         agg.used_nn = used_nn;
         agg.nn_fallback = agg.nn_fallback || fell_back;
+    }
+    // the last batch's x is in the caller's memory when the call returns
+    if (host_io) {
+        CK(cudaStreamSynchronize(h->io_st));
+        h->io_x_pending = false;
     }
     if (info) {
         double ms[PH_NPH];

@@ -363,6 +363,43 @@ def test_twelve_point_sources_in_one_batched_solve(coarse):
     f.close()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_with_host_vectors(pinned):
+    # b and x in host memory: 13 sources make two lockstep batches (12 + 1), so the second
+    # batch's b is copied in while the first solves and the first x copied out while the second
+    # solves; the solutions equal those of the same call on device vectors, and an initial
+    # guess from host memory is taken
+    import torch
+    dims = (4, 4, 4, 4)
+    f = Field(dims, 0.3, 1, 0.124, 1.0)
+    c = f.c
+    p = _params(c, (2, 2, 2, 2), 8, 1, n_init=1, n_adapt=1)
+    h = c.amg_setup(f.d, p, [li.to_interleaved(li.test_vectors(dims, 1, 8))])
+    n = 13
+    srcs = np.stack([li.rhs(dims, 60 + k) for k in range(n)])
+    bd = to_dev(srcs)
+    xd = torch.zeros_like(bd)
+    c.amg_solve(h, bd, xd, n, 1e-10, 200)
+    hb = bd.cpu()
+    hx = torch.full_like(hb, float("nan"))
+    if pinned:
+        hb, hx = hb.pin_memory(), hx.pin_memory()
+    st, info = c.amg_solve(h, hb, hx, n, 1e-10, 200)
+    assert info.converged == 1 and info.true_rel_residual <= 1e-10
+    ref = xd.cpu()
+    assert float((hx - ref).abs().max()) <= 1e-12 * float(ref.abs().max())
+    op = odirac.WilsonClover(f.U, 0.124, 1.0)
+    xs = li.from_interleaved(hx.numpy().reshape((n,) + f.shape4 + (12, 2)))
+    for k in (0, 12):
+        r = srcs[k].reshape(f.shape4 + (12,)) - op.apply(xs[k])
+        assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(srcs[k])
+    # the converged solutions as initial guesses: no outer step is needed
+    st, info = c.amg_solve(h, hb, hx, n, 1e-10, 200, use_x0=True)
+    assert info.converged == 1 and info.iters == 0
+    c.amg_hierarchy_destroy(h)
+    f.close()
+
+
 def test_flexible_bicgstab_outer_solver(mgcase):
     # the paper's outer solver: FP64 iterates after two iterations match the
     # oracle's flexible BiCGStab preconditioned by its own cycle; solves reach
