@@ -1087,12 +1087,13 @@ def run_solve16(args):
                                 ("ms_coarse", "ms_smoother", "ms_restrict_prolong", "ms_other", "ms_products",
                                  "ms_orthogonalisation", "ms_true_residual")},
                    "coarse_cycles": float(np.mean([i["coarse_cycles"] for i in infos]))},
-        # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one sap_half_kernel<P32,256> launch on this
-        # workload, from an ncu --set full capture of this kernel (91.18 + 2.66 MB); only for variant 0
+        # traffic: the per-site DRAM count of the current kernel's capture (24^3x48, 12 right-hand
+        # sides per launch) scaled to this workload's launches (one right-hand side); variant 0 only
         "roofline": {"kernel": SAP_KERNEL_NAMES.get(args.sap_variant, "sap_half (autotuned)"),
                      "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": 93.8e6 if (args.sap_variant == 0 and args.prec == "f32") else None,
+                     "traffic": (SAP_DRAM_BYTES_PER_SITE_RHS * V / 2
+                                 if (args.sap_variant == 0 and args.prec == "f32") else None),
                      "peak_kind": f"FP32 FMA from unit counts: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
                      "avg_launch_us": sap_launch_us, "flop_per_launch": flop_launch,
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind},
