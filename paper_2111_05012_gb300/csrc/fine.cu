@@ -82,6 +82,81 @@ __global__ void unpack_kernel(Geom g, const void* internal, E* __restrict__ cano
         }
     }
 }
+// The same layout changes through a shared-memory tile of kTile sites: the canonical side of
+// kTile consecutive sites is one contiguous block (24 values per site), read or written with
+// 16-byte vector accesses by consecutive threads, while the internal side stays a coalesced
+// per-site access (the per-site loops above leave each warp access spread over 32 sites'
+// 192-byte records).  The tile pads each site's 24 values to 25 so that the per-site accesses
+// of a warp fall in different banks.  Needs a 16-byte aligned canonical pointer.
+constexpr int kTile = 128, kPad = 25;
+template <typename E> struct Vec16;
+template <> struct Vec16<double> {
+    using T = double2;
+    using E = double;
+    static constexpr int n = 2;
+    DEV static T make(const E* p) { return make_double2(p[0], p[1]); }
+    DEV static void put(E* p, T v) { p[0] = v.x; p[1] = v.y; }
+};
+template <> struct Vec16<float> {
+    using T = float4;
+    static constexpr int n = 4;
+    using E = float;
+    DEV static T make(const E* p) { return make_float4(p[0], p[1], p[2], p[3]); }
+    DEV static void put(E* p, T v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; p[3] = v.w; }
+};
+// padded tile position of canonical element i of the tile (vectors never straddle a site)
+DEV int tile_pos(int i) { return (i / 24) * kPad + i % 24; }
+
+template <class P, typename E>
+__global__ void __launch_bounds__(kTile) pack_tiled_kernel(Geom g, const E* __restrict__ canon, void* internal) {
+    using T = typename P::T;
+    using W = Vec16<E>;
+    __shared__ E tile[kTile * kPad];
+    const int r = blockIdx.y;
+    const E* src = canon + (size_t)r * g.V * 24;
+    char* dst = (char*)internal + (size_t)r * spinor_bytes<P>(g.V);
+    for (int s0 = blockIdx.x * kTile; s0 < g.V; s0 += gridDim.x * kTile) {
+        const int ns = min(kTile, g.V - s0);
+        const typename W::T* vs = reinterpret_cast<const typename W::T*>(src + (size_t)s0 * 24);
+        for (int i = threadIdx.x; i < ns * 24 / W::n; i += kTile) W::put(tile + tile_pos(i * W::n), vs[i]);
+        __syncthreads();
+        if (threadIdx.x < ns) {
+            cx<T> v[12];
+            const E* e = tile + threadIdx.x * kPad;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = {T(e[2 * k]), T(e[2 * k + 1])};
+            SpinorIO<P>::store(dst, g.V, s0 + threadIdx.x, v);
+        }
+        __syncthreads();
+    }
+}
+template <class P, typename E>
+__global__ void __launch_bounds__(kTile) unpack_tiled_kernel(Geom g, const void* internal, E* __restrict__ canon) {
+    using T = typename P::T;
+    using W = Vec16<E>;
+    __shared__ E tile[kTile * kPad];
+    const int r = blockIdx.y;
+    E* dst = canon + (size_t)r * g.V * 24;
+    const char* src = (const char*)internal + (size_t)r * spinor_bytes<P>(g.V);
+    for (int s0 = blockIdx.x * kTile; s0 < g.V; s0 += gridDim.x * kTile) {
+        const int ns = min(kTile, g.V - s0);
+        if (threadIdx.x < ns) {
+            cx<T> v[12];
+            SpinorIO<P>::load(src, g.V, s0 + threadIdx.x, v);
+            E* e = tile + threadIdx.x * kPad;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                e[2 * k] = E(v[k].re);
+                e[2 * k + 1] = E(v[k].im);
+            }
+        }
+        __syncthreads();
+        typename W::T* vd = reinterpret_cast<typename W::T*>(dst + (size_t)s0 * 24);
+        for (int i = threadIdx.x; i < ns * 24 / W::n; i += kTile) vd[i] = W::make(tile + tile_pos(i * W::n));
+        __syncthreads();
+    }
+}
+
 template <class Pi, class Po>
 __global__ void convert_kernel(Geom g, const void* in, void* out) {
     const int r = blockIdx.y;
@@ -1695,6 +1770,13 @@ cudaError_t launch_pack_spinor(int prec, const GeomH& gh, const void* canon, voi
                                cudaStream_t st) {
     Geom g = make_geom(gh);
     dim3 grid(grid_for(g.V, kThreads), nrhs);
+    if (((uintptr_t)canon & 15) == 0) {
+        const dim3 gt(grid_for(g.V, kTile), nrhs);
+        if (prec == 0) (note_launch(), pack_tiled_kernel<P64, double><<<gt, kTile, 0, st>>>(g, (const double*)canon, internal));
+        else if (prec == 1) (note_launch(), pack_tiled_kernel<P32, float><<<gt, kTile, 0, st>>>(g, (const float*)canon, internal));
+        else (note_launch(), pack_tiled_kernel<P16, float><<<gt, kTile, 0, st>>>(g, (const float*)canon, internal));
+        return cudaGetLastError();
+    }
     if (prec == 0) (note_launch(), pack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, (const double*)canon, internal, nrhs));
     else if (prec == 1) (note_launch(), pack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs));
     else (note_launch(), pack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, (const float*)canon, internal, nrhs));
@@ -1704,6 +1786,13 @@ cudaError_t launch_unpack_spinor(int prec, const GeomH& gh, const void* internal
                                  cudaStream_t st) {
     Geom g = make_geom(gh);
     dim3 grid(grid_for(g.V, kThreads), nrhs);
+    if (((uintptr_t)canon & 15) == 0) {
+        const dim3 gt(grid_for(g.V, kTile), nrhs);
+        if (prec == 0) (note_launch(), unpack_tiled_kernel<P64, double><<<gt, kTile, 0, st>>>(g, internal, (double*)canon));
+        else if (prec == 1) (note_launch(), unpack_tiled_kernel<P32, float><<<gt, kTile, 0, st>>>(g, internal, (float*)canon));
+        else (note_launch(), unpack_tiled_kernel<P16, float><<<gt, kTile, 0, st>>>(g, internal, (float*)canon));
+        return cudaGetLastError();
+    }
     if (prec == 0) (note_launch(), unpack_kernel<P64, double><<<grid, kThreads, 0, st>>>(g, internal, (double*)canon, nrhs));
     else if (prec == 1) (note_launch(), unpack_kernel<P32, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs));
     else (note_launch(), unpack_kernel<P16, float><<<grid, kThreads, 0, st>>>(g, internal, (float*)canon, nrhs));
